@@ -1,0 +1,780 @@
+/*
+ * nbgs_oracle.c -- FP64 sequential CPU reference of one NBGS time step.
+ *
+ * TEST INFRASTRUCTURE ONLY (see nbgs_oracle.h).  Plain, slow and written to
+ * be read next to the paper.  Compile with -ffp-contract=off: the hull
+ * predicate that decides which contacts exist must round exactly as written.
+ */
+#include "nbgs_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+struct oracle_scene {
+    oracle_params prm;
+    int64_t n;                     /* spheres */
+    double *x, *q, *v, *w;         /* position, quaternion (w,x,y,z), velocity, angular velocity */
+    double *r, *invm, *invI;       /* radius, 1/m, 1/I (sphere: I = 2/5 m r^2) */
+    double *h;                     /* hull expansion radius of this step */
+    int32_t nplanes;
+    double plane_n[ORACLE_MAX_PLANES][3];
+    double plane_c[ORACLE_MAX_PLANES];
+
+    /* contacts of the current step, canonical order */
+    int64_t nc, cap;
+    uint32_t *j1, *j2;
+    double *cn;                    /* normal, 3 per contact */
+    double *xi;                    /* signed distance */
+    double *la, *lb;               /* lever lengths: l_a = -la n, l_b = lb n */
+    int32_t *colour;
+    double *p;                     /* contact-frame impulse (p_n, p_t, p_o) = dt * lambda */
+    int32_t ncolours;
+    int coloured;
+
+    /* previous step's contacts for the warm start (canonical keys, world impulse) */
+    int64_t nprev;
+    uint64_t *prev_key;
+    double *prev_P;
+
+    double vmax_start;             /* max_i |v_i| at the start of the step */
+    double v_ref;
+    double *hist;                  /* R_k per sweep */
+    int32_t nhist, cap_hist;
+};
+
+/* ------------------------------------------------------------------ */
+/* small vector helpers                                                 */
+/* ------------------------------------------------------------------ */
+static double dot3(const double a[3], const double b[3]) { return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2]; }
+static double norm3(const double a[3]) { return sqrt(dot3(a, a)); }
+static void cross3(const double a[3], const double b[3], double c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static int is_finite_body(const oracle_scene* s, uint32_t i)
+{
+    return (int64_t)i < s->n && (s->invm[i] > 0.0 || s->invI[i] > 0.0);
+}
+
+/* splitmix64 (Steele, Lea & Flood, OOPSLA 2014; Vigna's reference
+ * formulation): one step of the Weyl sequence followed by the mix. */
+uint64_t oracle_splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Orthonormal tangent basis (t, o) of a unit normal n: the branchless
+ * construction of Duff et al., "Building an Orthonormal Basis, Revisited"
+ * (JCGT 6(1), 2017).  Sect. 2 only requires that t and o span the
+ * tangential plane; this fixes which pair is used. */
+void oracle_contact_frame(const double n[3], double t[3], double o[3])
+{
+    double sign = copysign(1.0, n[2]);
+    double a = -1.0 / (sign + n[2]);
+    double b = n[0] * n[1] * a;
+    t[0] = 1.0 + sign * n[0] * n[0] * a;
+    t[1] = sign * b;
+    t[2] = -sign * n[0];
+    o[0] = b;
+    o[1] = sign + n[1] * n[1] * a;
+    o[2] = -n[1];
+}
+
+/* One-contact problem F_j^{-1}(0, lambda_jbar) of Sect. 3 for a contact
+ * whose Delassus block in the contact frame is diag(w_n, w_t, w_t).
+ * b = post-velocity of the contact without its own reaction, normal
+ * component including the gap term xi'/dt.  Output p satisfies
+ *   b_n + w_n p_n >= 0  _|_  p_n >= 0                 (eq. nonpenetration)
+ *   |p_to| <= mu p_n,  |u_to| p_to = -mu p_n u_to     (eq. coulomb)
+ * with u = b + W p.  The normal part decouples because W is diagonal; the
+ * tangential part is the stick impulse, or its radial projection onto the
+ * friction disk when the stick impulse lies outside it. */
+void oracle_one_contact(double w_n, double w_t, double mu, const double b[3], double p[3])
+{
+    double pn = -b[0] / w_n;
+    if (!(pn > 0.0)) pn = 0.0;
+    double pt = -b[1] / w_t;
+    double po = -b[2] / w_t;
+    double lim = mu * pn;
+    double len = sqrt(pt * pt + po * po);
+    if (len > lim) {
+        if (len > 0.0) {
+            pt = pt * (lim / len);
+            po = po * (lim / len);
+        } else {
+            pt = 0.0;
+            po = 0.0;
+        }
+    }
+    p[0] = pn;
+    p[1] = pt;
+    p[2] = po;
+}
+
+/* ------------------------------------------------------------------ */
+/* scene lifecycle                                                      */
+/* ------------------------------------------------------------------ */
+void oracle_destroy_scene(oracle_scene* s)
+{
+    if (!s) return;
+    free(s->x); free(s->q); free(s->v); free(s->w);
+    free(s->r); free(s->invm); free(s->invI); free(s->h);
+    free(s->j1); free(s->j2); free(s->cn); free(s->xi); free(s->la); free(s->lb);
+    free(s->colour); free(s->p);
+    free(s->prev_key); free(s->prev_P);
+    free(s->hist);
+    free(s);
+}
+
+int oracle_create_scene(const oracle_params* prm, int64_t n,
+                        const double* pos, const double* vel, const double* angvel,
+                        const double* radius, const double* density,
+                        oracle_scene** out)
+{
+    if (!prm || !out || n < 0 || (n > 0 && (!pos || !vel || !angvel || !radius || !density))) return 1;
+    if (!(prm->dt > 0.0)) return 1;
+    oracle_scene* s = (oracle_scene*)calloc(1, sizeof(oracle_scene));
+    if (!s) return 2;
+    s->prm = *prm;
+    s->n = n;
+    size_t m = (size_t)(n > 0 ? n : 1);
+    s->x = (double*)malloc(3 * m * sizeof(double));
+    s->q = (double*)malloc(4 * m * sizeof(double));
+    s->v = (double*)malloc(3 * m * sizeof(double));
+    s->w = (double*)malloc(3 * m * sizeof(double));
+    s->r = (double*)malloc(m * sizeof(double));
+    s->invm = (double*)malloc(m * sizeof(double));
+    s->invI = (double*)malloc(m * sizeof(double));
+    s->h = (double*)malloc(m * sizeof(double));
+    s->cap_hist = 64;
+    s->hist = (double*)malloc((size_t)s->cap_hist * sizeof(double));
+    if (!s->x || !s->q || !s->v || !s->w || !s->r || !s->invm || !s->invI || !s->h || !s->hist) {
+        oracle_destroy_scene(s);
+        return 2;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            s->x[3 * i + k] = pos[3 * i + k];
+            s->v[3 * i + k] = vel[3 * i + k];
+            s->w[3 * i + k] = angvel[3 * i + k];
+        }
+        s->q[4 * i + 0] = 1.0;
+        s->q[4 * i + 1] = 0.0;
+        s->q[4 * i + 2] = 0.0;
+        s->q[4 * i + 3] = 0.0;
+        s->r[i] = radius[i];
+        /* Sect. 2: block-diagonal mass matrix; a homogeneous sphere has
+         * m = rho 4/3 pi r^3 and the isotropic inertia I = 2/5 m r^2. */
+        double mass = density[i] * (4.0 / 3.0) * M_PI * radius[i] * radius[i] * radius[i];
+        double inertia = 0.4 * mass * radius[i] * radius[i];
+        s->invm[i] = mass > 0.0 ? 1.0 / mass : 0.0;
+        s->invI[i] = inertia > 0.0 ? 1.0 / inertia : 0.0;
+    }
+    *out = s;
+    return 0;
+}
+
+int oracle_add_plane(oracle_scene* s, const double n[3], double c)
+{
+    if (!s || !n || s->nplanes >= ORACLE_MAX_PLANES) return 1;
+    int k = s->nplanes++;
+    s->plane_n[k][0] = n[0];
+    s->plane_n[k][1] = n[1];
+    s->plane_n[k][2] = n[2];
+    s->plane_c[k] = c;
+    return 0;
+}
+
+int oracle_set_mass_properties(oracle_scene* s, const double* invm, const double* invI)
+{
+    if (!s) return 1;
+    for (int64_t i = 0; i < s->n; ++i) {
+        if (invm) s->invm[i] = invm[i];
+        if (invI) s->invI[i] = invI[i];
+    }
+    return 0;
+}
+
+int oracle_set_bodies(oracle_scene* s, const double* pos, const double* quat,
+                      const double* vel, const double* angvel)
+{
+    if (!s) return 1;
+    if (pos) memcpy(s->x, pos, 3 * (size_t)s->n * sizeof(double));
+    if (quat) memcpy(s->q, quat, 4 * (size_t)s->n * sizeof(double));
+    if (vel) memcpy(s->v, vel, 3 * (size_t)s->n * sizeof(double));
+    if (angvel) memcpy(s->w, angvel, 3 * (size_t)s->n * sizeof(double));
+    return 0;
+}
+
+int oracle_get_bodies(const oracle_scene* s, double* pos, double* quat, double* vel, double* angvel)
+{
+    if (!s) return 1;
+    if (pos) memcpy(pos, s->x, 3 * (size_t)s->n * sizeof(double));
+    if (quat) memcpy(quat, s->q, 4 * (size_t)s->n * sizeof(double));
+    if (vel) memcpy(vel, s->v, 3 * (size_t)s->n * sizeof(double));
+    if (angvel) memcpy(angvel, s->w, 3 * (size_t)s->n * sizeof(double));
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* contact detection (Sect. 4), brute force over all pairs              */
+/* ------------------------------------------------------------------ */
+static int push_contact(oracle_scene* s, uint32_t a, uint32_t b, const double nrm[3],
+                        double xi, double la, double lb)
+{
+    if (s->nc == s->cap) {
+        int64_t nc = s->cap ? 2 * s->cap : 1024;
+        uint32_t* j1 = (uint32_t*)realloc(s->j1, (size_t)nc * sizeof(uint32_t));
+        if (j1) s->j1 = j1;
+        uint32_t* j2 = (uint32_t*)realloc(s->j2, (size_t)nc * sizeof(uint32_t));
+        if (j2) s->j2 = j2;
+        double* cn = (double*)realloc(s->cn, 3 * (size_t)nc * sizeof(double));
+        if (cn) s->cn = cn;
+        double* xv = (double*)realloc(s->xi, (size_t)nc * sizeof(double));
+        if (xv) s->xi = xv;
+        double* lav = (double*)realloc(s->la, (size_t)nc * sizeof(double));
+        if (lav) s->la = lav;
+        double* lbv = (double*)realloc(s->lb, (size_t)nc * sizeof(double));
+        if (lbv) s->lb = lbv;
+        int32_t* col = (int32_t*)realloc(s->colour, (size_t)nc * sizeof(int32_t));
+        if (col) s->colour = col;
+        double* pv = (double*)realloc(s->p, 3 * (size_t)nc * sizeof(double));
+        if (pv) s->p = pv;
+        if (!j1 || !j2 || !cn || !xv || !lav || !lbv || !col || !pv) return 2;
+        s->cap = nc;
+    }
+    int64_t k = s->nc++;
+    s->j1[k] = a;
+    s->j2[k] = b;
+    s->cn[3 * k + 0] = nrm[0];
+    s->cn[3 * k + 1] = nrm[1];
+    s->cn[3 * k + 2] = nrm[2];
+    s->xi[k] = xi;
+    s->la[k] = la;
+    s->lb[k] = lb;
+    s->colour[k] = -1;
+    s->p[3 * k + 0] = 0.0;
+    s->p[3 * k + 1] = 0.0;
+    s->p[3 * k + 2] = 0.0;
+    return 0;
+}
+
+int oracle_detect_contacts(oracle_scene* s, int64_t* n_contacts)
+{
+    if (!s) return 1;
+    const oracle_params* P = &s->prm;
+    const double dt = P->dt;
+
+    /* eq. (expansionradius): h_i = dt (|v_i| + |omega_i| r_i) + tau, with the
+     * velocities at the start of the step; a sphere's bounding radius is r. */
+    s->vmax_start = 0.0;
+    for (int64_t i = 0; i < s->n; ++i) {
+        double nv = norm3(&s->v[3 * i]);
+        double nw = norm3(&s->w[3 * i]);
+        s->h[i] = dt * (nv + nw * s->r[i]) + P->tau;
+        if (nv > s->vmax_start) s->vmax_start = nv;
+    }
+    double L[3];
+    for (int k = 0; k < 3; ++k) L[k] = P->box_hi[k] - P->box_lo[k];
+
+    s->nc = 0;
+    s->coloured = 0;
+    for (int64_t a = 0; a < s->n; ++a) {
+        /* Sphere-sphere pairs (a, b), a < b: j1 = a, j2 = b.  Eq. (contactpos)
+         * for two spheres: the point of S_b closest to x_a is
+         * x_hat = x_b + r_b n with n = (x_a - x_b)/|x_a - x_b| the outward
+         * normal of S_b, and xi = f_a(x_hat) = d - r_a - r_b. */
+        for (int64_t b = a + 1; b < s->n; ++b) {
+            double d3[3];
+            for (int k = 0; k < 3; ++k) {
+                double dk = s->x[3 * a + k] - s->x[3 * b + k];
+                if (P->periodic[k]) { /* minimum image */
+                    if (dk > 0.5 * L[k]) dk -= L[k];
+                    else if (dk < -0.5 * L[k]) dk += L[k];
+                }
+                d3[k] = dk;
+            }
+            double d = sqrt((d3[0] * d3[0] + d3[1] * d3[1]) + d3[2] * d3[2]);
+            /* Sect. 4: keep the pair iff the hulls intersect. */
+            if (((d - s->r[a]) - s->r[b]) <= (s->h[a] + s->h[b])) {
+                double nrm[3];
+                if (d > 0.0) {
+                    nrm[0] = d3[0] / d;
+                    nrm[1] = d3[1] / d;
+                    nrm[2] = d3[2] / d;
+                } else { /* coincident centres: the argmin is degenerate */
+                    nrm[0] = 0.0; nrm[1] = 0.0; nrm[2] = 1.0;
+                }
+                double xi = (d - s->r[a]) - s->r[b];
+                /* l_a = x_hat - x_a = -(d - r_b) n ;  l_b = x_hat - x_b = r_b n */
+                if (push_contact(s, (uint32_t)a, (uint32_t)b, nrm, xi, d - s->r[b], s->r[b])) return 2;
+            }
+        }
+        /* Sphere-wall pairs (a, wall k): j2 = n + k.  The wall solid is
+         * {y : n_k . y <= c_k}, its outward normal is n_k, the point of the
+         * solid closest to x_a is x_a - (n_k . x_a - c_k) n_k, and the walls
+         * have no velocity, so their hull radius is tau alone. */
+        for (int32_t k = 0; k < s->nplanes; ++k) {
+            const double* nk = s->plane_n[k];
+            double sd = ((nk[0] * s->x[3 * a + 0] + nk[1] * s->x[3 * a + 1]) + nk[2] * s->x[3 * a + 2]) - s->plane_c[k];
+            double xi = sd - s->r[a];
+            if (xi <= (s->h[a] + P->tau)) {
+                if (push_contact(s, (uint32_t)a, (uint32_t)(s->n + k), nk, xi, sd, 0.0)) return 2;
+            }
+        }
+    }
+    /* The loops above emit keys (j1 << 32) | j2 in ascending order, which is
+     * the canonical order every other part of the oracle relies on. */
+    if (n_contacts) *n_contacts = s->nc;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* colouring: sequential greedy in descending priority                  */
+/* ------------------------------------------------------------------ */
+typedef struct { uint64_t prio; uint64_t key; int64_t idx; } prio_item;
+
+static int cmp_prio_desc(const void* pa, const void* pb)
+{
+    const prio_item* a = (const prio_item*)pa;
+    const prio_item* b = (const prio_item*)pb;
+    if (a->prio != b->prio) return a->prio > b->prio ? -1 : 1;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return 0;
+}
+
+/* Two contacts conflict iff they share a body of finite mass (walls and
+ * infinite-mass bodies are never written by the sweep).  Contacts are taken
+ * in order of decreasing priority splitmix64(key ^ seed), ties to the lower
+ * key; each takes the smallest colour unused by its already-coloured
+ * conflicting contacts.  Contacts of one colour then touch disjoint finite
+ * bodies, so relaxing them in any order gives bit-identical results. */
+int oracle_colour_contacts(oracle_scene* s, int32_t* n_colours)
+{
+    if (!s) return 1;
+    const int64_t nc = s->nc, n = s->n;
+    int64_t* deg = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    prio_item* items = (prio_item*)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(prio_item));
+    if (!deg || !items) { free(deg); free(items); return 2; }
+    for (int64_t c = 0; c < nc; ++c) {
+        if (is_finite_body(s, s->j1[c])) deg[s->j1[c] + 1]++;
+        if (is_finite_body(s, s->j2[c])) deg[s->j2[c] + 1]++;
+    }
+    for (int64_t i = 0; i < n; ++i) deg[i + 1] += deg[i];
+    int64_t* adj = (int64_t*)malloc((size_t)(deg[n] > 0 ? deg[n] : 1) * sizeof(int64_t));
+    int64_t* fill = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!adj || !fill) { free(deg); free(items); free(adj); free(fill); return 2; }
+    for (int64_t c = 0; c < nc; ++c) {
+        uint32_t b[2] = { s->j1[c], s->j2[c] };
+        for (int e = 0; e < 2; ++e)
+            if (is_finite_body(s, b[e])) adj[deg[b[e]] + fill[b[e]]++] = c;
+    }
+    for (int64_t c = 0; c < nc; ++c) {
+        uint64_t key = ((uint64_t)s->j1[c] << 32) | s->j2[c];
+        items[c].key = key;
+        items[c].prio = oracle_splitmix64(key ^ s->prm.colour_seed);
+        items[c].idx = c;
+        s->colour[c] = -1;
+    }
+    qsort(items, (size_t)nc, sizeof(prio_item), cmp_prio_desc);
+
+    int64_t maxdeg = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (deg[i + 1] - deg[i] > maxdeg) maxdeg = deg[i + 1] - deg[i];
+    int64_t ncol_max = 2 * maxdeg + 2;
+    int64_t* mark = (int64_t*)malloc((size_t)ncol_max * sizeof(int64_t));
+    if (!mark) { free(deg); free(items); free(adj); free(fill); return 2; }
+    for (int64_t k = 0; k < ncol_max; ++k) mark[k] = -1;
+
+    int32_t ncolours = 0;
+    for (int64_t it = 0; it < nc; ++it) {
+        int64_t c = items[it].idx;
+        uint32_t b[2] = { s->j1[c], s->j2[c] };
+        for (int e = 0; e < 2; ++e) {
+            if (!is_finite_body(s, b[e])) continue;
+            for (int64_t k = deg[b[e]]; k < deg[b[e] + 1]; ++k) {
+                int64_t d = adj[k];
+                if (d != c && s->colour[d] >= 0) mark[s->colour[d]] = c;
+            }
+        }
+        int32_t col = 0;
+        while (mark[col] == c) ++col;
+        s->colour[c] = col;
+        if (col + 1 > ncolours) ncolours = col + 1;
+    }
+    free(deg); free(items); free(adj); free(fill); free(mark);
+    s->ncolours = ncolours;
+    s->coloured = 1;
+    if (n_colours) *n_colours = ncolours;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* NBGS solve (Sect. 5, Alg. 1 with one subdomain)                      */
+/* ------------------------------------------------------------------ */
+
+/* Per-contact constants of one step. */
+typedef struct {
+    uint32_t a, b;
+    int fa, fb;                 /* finite (mutable) bodies */
+    double n[3], t[3], o[3];
+    double la, lb;              /* l_a = -la n, l_b = lb n */
+    double bias;                /* xi'/dt */
+    double w_n, w_t;            /* contact-frame Delassus block diag(w_n, w_t, w_t) */
+} contact_k;
+
+static void build_contact(const oracle_scene* s, int64_t c, contact_k* k)
+{
+    k->a = s->j1[c];
+    k->b = s->j2[c];
+    k->fa = (int64_t)k->a < s->n;
+    k->fb = (int64_t)k->b < s->n;
+    for (int e = 0; e < 3; ++e) k->n[e] = s->cn[3 * c + e];
+    oracle_contact_frame(k->n, k->t, k->o);
+    k->la = s->la[c];
+    k->lb = s->lb[c];
+    /* eq. (nonpenetration): the gap term xi/dt; a penetration (xi < 0) is
+     * corrected with the scaled term beta xi/dt (Sect. 3). */
+    double xi = s->xi[c];
+    double xs = xi >= 0.0 ? xi : s->prm.beta * xi;
+    k->bias = xs / s->prm.dt;
+    /* W = J M^-1 J^T for the two bodies.  With levers parallel to n,
+     * (l x P) x l = |l|^2 (P - n (n.P)), so W = w_n 1 + (w_t - w_n)(1 - n n^T). */
+    double ima = k->fa ? s->invm[k->a] : 0.0, iIa = k->fa ? s->invI[k->a] : 0.0;
+    double imb = k->fb ? s->invm[k->b] : 0.0, iIb = k->fb ? s->invI[k->b] : 0.0;
+    k->w_n = ima + imb;
+    k->w_t = k->w_n + iIa * k->la * k->la + iIb * k->lb * k->lb;
+}
+
+/* Relative contact velocity u = v_a + w_a x l_a - v_b - w_b x l_b
+ * (Sect. 2), in world coordinates. */
+static void rel_velocity(const oracle_scene* s, const contact_k* k, double u[3])
+{
+    double la3[3] = { -k->la * k->n[0], -k->la * k->n[1], -k->la * k->n[2] };
+    double lb3[3] = { k->lb * k->n[0], k->lb * k->n[1], k->lb * k->n[2] };
+    double wa[3] = { 0, 0, 0 }, wb[3] = { 0, 0, 0 };
+    for (int e = 0; e < 3; ++e) u[e] = 0.0;
+    if (k->fa) {
+        cross3(&s->w[3 * k->a], la3, wa);
+        for (int e = 0; e < 3; ++e) u[e] += s->v[3 * k->a + e] + wa[e];
+    }
+    if (k->fb) {
+        cross3(&s->w[3 * k->b], lb3, wb);
+        for (int e = 0; e < 3; ++e) u[e] -= s->v[3 * k->b + e] + wb[e];
+    }
+}
+
+/* Apply a world-frame impulse P acting +P on j1 and -P on j2 at x_hat:
+ * the contact terms of eq. (wrench) times dt, divided by the mass matrix,
+ * added to the velocity accumulators in place (Sect. 6.3). */
+static void apply_impulse(oracle_scene* s, const contact_k* k, const double P[3])
+{
+    if (k->fa && (s->invm[k->a] > 0.0 || s->invI[k->a] > 0.0)) {
+        double la3[3] = { -k->la * k->n[0], -k->la * k->n[1], -k->la * k->n[2] };
+        double tq[3];
+        cross3(la3, P, tq);
+        for (int e = 0; e < 3; ++e) {
+            s->v[3 * k->a + e] += s->invm[k->a] * P[e];
+            s->w[3 * k->a + e] += s->invI[k->a] * tq[e];
+        }
+    }
+    if (k->fb && (s->invm[k->b] > 0.0 || s->invI[k->b] > 0.0)) {
+        double lb3[3] = { k->lb * k->n[0], k->lb * k->n[1], k->lb * k->n[2] };
+        double tq[3];
+        cross3(lb3, P, tq);
+        for (int e = 0; e < 3; ++e) {
+            s->v[3 * k->b + e] -= s->invm[k->b] * P[e];
+            s->w[3 * k->b + e] -= s->invI[k->b] * tq[e];
+        }
+    }
+}
+
+typedef struct { int32_t colour; int64_t idx; } order_item;
+static int cmp_order(const void* pa, const void* pb)
+{
+    const order_item* a = (const order_item*)pa;
+    const order_item* b = (const order_item*)pb;
+    if (a->colour != b->colour) return a->colour < b->colour ? -1 : 1;
+    return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);
+}
+
+static int64_t find_prev(const oracle_scene* s, uint64_t key)
+{
+    int64_t lo = 0, hi = s->nprev;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (s->prev_key[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < s->nprev && s->prev_key[lo] == key) ? lo : -1;
+}
+
+int oracle_solve_nbgs(oracle_scene* s, int32_t max_sweeps, double tol,
+                      int32_t* sweeps_done, double* residual)
+{
+    if (!s || max_sweeps < 0) return 1;
+    if (!s->coloured) {
+        int rc = oracle_colour_contacts(s, NULL);
+        if (rc) return rc;
+    }
+    const oracle_params* P = &s->prm;
+    const int64_t nc = s->nc;
+    contact_k* K = (contact_k*)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(contact_k));
+    order_item* ord = (order_item*)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(order_item));
+    if (!K || !ord) { free(K); free(ord); return 2; }
+    for (int64_t c = 0; c < nc; ++c) {
+        build_contact(s, c, &K[c]);
+        ord[c].colour = s->colour[c];
+        ord[c].idx = c;
+    }
+    /* Contact order of the sweep: colours ascending, canonical inside. */
+    qsort(ord, (size_t)nc, sizeof(order_item), cmp_order);
+
+    double gdt = norm3(P->gravity) * P->dt;
+    s->v_ref = s->vmax_start;
+    if (gdt > s->v_ref) s->v_ref = gdt;
+    if (1e-12 > s->v_ref) s->v_ref = 1e-12;
+
+    /* eq. (integrationscheme), velocity part without contact reactions:
+     * v += dt M^-1 f_ext with f_ext = m g; the gyroscopic term w x I w
+     * vanishes for the isotropic inertia of a sphere. */
+    for (int64_t i = 0; i < s->n; ++i)
+        if (s->invm[i] > 0.0)
+            for (int e = 0; e < 3; ++e) s->v[3 * i + e] += P->dt * P->gravity[e];
+
+    /* Alg. 1 starts from lambda = 0 "or any other initialization", in
+     * particular the previous step's reactions (Sect. 5). */
+    for (int64_t c = 0; c < nc; ++c) {
+        double* p = &s->p[3 * c];
+        p[0] = p[1] = p[2] = 0.0;
+        if (P->warm_start == ORACLE_WARM_PREV && s->nprev > 0) {
+            uint64_t key = ((uint64_t)s->j1[c] << 32) | s->j2[c];
+            int64_t k = find_prev(s, key);
+            if (k >= 0) {
+                const double* Pw = &s->prev_P[3 * k];
+                const contact_k* kc = &K[c];
+                double pn = dot3(kc->n, Pw);
+                if (!(pn > 0.0)) pn = 0.0;
+                double pt = dot3(kc->t, Pw), po = dot3(kc->o, Pw);
+                double lim = P->mu * pn, len = sqrt(pt * pt + po * po);
+                if (len > lim) {
+                    if (len > 0.0) { pt = pt * (lim / len); po = po * (lim / len); }
+                    else { pt = 0.0; po = 0.0; }
+                }
+                p[0] = pn; p[1] = pt; p[2] = po;
+            }
+        }
+    }
+    for (int64_t it = 0; it < nc; ++it) {
+        int64_t c = ord[it].idx;
+        const contact_k* k = &K[c];
+        const double* p = &s->p[3 * c];
+        if (p[0] == 0.0 && p[1] == 0.0 && p[2] == 0.0) continue;
+        double Pw[3];
+        for (int e = 0; e < 3; ++e) Pw[e] = p[0] * k->n[e] + p[1] * k->t[e] + p[2] * k->o[e];
+        apply_impulse(s, k, Pw);
+    }
+
+    s->nhist = 0;
+    int32_t k_done = 0;
+    double Rk = 0.0;
+    for (int32_t sweep = 0; sweep < max_sweeps; ++sweep) {
+        double rmax = 0.0;
+        for (int64_t it = 0; it < nc; ++it) {
+            int64_t c = ord[it].idx;
+            const contact_k* k = &K[c];
+            if (!(k->w_n > 0.0)) continue; /* two infinite masses: nothing moves */
+            double* p = &s->p[3 * c];
+            double u[3];
+            rel_velocity(s, k, u);
+            /* Remove the contact's own reaction to get the velocity given the
+             * other contacts' reactions lambda_jbar (Alg. 1, Alg. 2), and add
+             * the gap term of eq. (nonpenetration). */
+            double b[3];
+            b[0] = (dot3(k->n, u) - k->w_n * p[0]) + k->bias;
+            b[1] = dot3(k->t, u) - k->w_t * p[1];
+            b[2] = dot3(k->o, u) - k->w_t * p[2];
+            double y[3];
+            oracle_one_contact(k->w_n, k->w_t, P->mu, b, y);
+            /* Alg. 1: lambda_j <- omega y + (1 - omega) lambda_j */
+            double pnew[3], dp[3];
+            for (int e = 0; e < 3; ++e) {
+                pnew[e] = P->omega * y[e] + (1.0 - P->omega) * p[e];
+                dp[e] = pnew[e] - p[e];
+            }
+            double Pw[3];
+            for (int e = 0; e < 3; ++e) Pw[e] = dp[0] * k->n[e] + dp[1] * k->t[e] + dp[2] * k->o[e];
+            apply_impulse(s, k, Pw);
+            for (int e = 0; e < 3; ++e) p[e] = pnew[e];
+            /* velocity change at the contact caused by this relaxation */
+            double r1 = k->w_n * dp[0], r2 = k->w_t * dp[1], r3 = k->w_t * dp[2];
+            double rj = sqrt((r1 * r1 + r2 * r2) + r3 * r3);
+            if (rj > rmax) rmax = rj;
+        }
+        Rk = rmax / s->v_ref;
+        if (s->nhist == s->cap_hist) {
+            double* hh = (double*)realloc(s->hist, 2 * (size_t)s->cap_hist * sizeof(double));
+            if (!hh) { free(K); free(ord); return 2; }
+            s->hist = hh;
+            s->cap_hist *= 2;
+        }
+        s->hist[s->nhist++] = Rk;
+        k_done = sweep + 1;
+        if (tol > 0.0 && Rk <= tol) break;
+    }
+
+    /* Keep this step's reactions (world frame) for the next warm start. */
+    free(s->prev_key);
+    free(s->prev_P);
+    s->prev_key = (uint64_t*)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(uint64_t));
+    s->prev_P = (double*)malloc(3 * (size_t)(nc > 0 ? nc : 1) * sizeof(double));
+    if (!s->prev_key || !s->prev_P) { free(K); free(ord); s->nprev = 0; return 2; }
+    for (int64_t c = 0; c < nc; ++c) {
+        s->prev_key[c] = ((uint64_t)s->j1[c] << 32) | s->j2[c];
+        const double* p = &s->p[3 * c];
+        for (int e = 0; e < 3; ++e)
+            s->prev_P[3 * c + e] = p[0] * K[c].n[e] + p[1] * K[c].t[e] + p[2] * K[c].o[e];
+    }
+    s->nprev = nc;
+    free(K);
+    free(ord);
+    if (sweeps_done) *sweeps_done = k_done;
+    if (residual) *residual = Rk;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* time integration (Sect. 3, eq. integrationscheme)                    */
+/* ------------------------------------------------------------------ */
+int oracle_integrate(oracle_scene* s)
+{
+    if (!s) return 1;
+    const oracle_params* P = &s->prm;
+    const double dt = P->dt;
+    for (int64_t i = 0; i < s->n; ++i) {
+        double* x = &s->x[3 * i];
+        double* q = &s->q[4 * i];
+        const double* v = &s->v[3 * i];
+        const double* w = &s->w[3 * i];
+        for (int e = 0; e < 3; ++e) x[e] = x[e] + dt * v[e];
+        /* phi' = phi + dt Q(phi) omega' with the 4x3 block of Sect. 2
+         * (rows w, x, y, z; factor 1/2), then renormalisation (Sect. 3). */
+        double qw = q[0], qx = q[1], qy = q[2], qz = q[3];
+        double dw = 0.5 * (-qx * w[0] - qy * w[1] - qz * w[2]);
+        double dx = 0.5 * (qw * w[0] + qz * w[1] - qy * w[2]);
+        double dy = 0.5 * (-qz * w[0] + qw * w[1] + qx * w[2]);
+        double dz = 0.5 * (qy * w[0] - qx * w[1] + qw * w[2]);
+        qw += dt * dw; qx += dt * dx; qy += dt * dy; qz += dt * dz;
+        double qn = sqrt(((qw * qw + qx * qx) + qy * qy) + qz * qz);
+        q[0] = qw / qn; q[1] = qx / qn; q[2] = qy / qn; q[3] = qz / qn;
+        for (int e = 0; e < 3; ++e) {
+            if (!P->periodic[e]) continue;
+            double L = P->box_hi[e] - P->box_lo[e];
+            double sft = fmod(x[e] - P->box_lo[e], L);
+            if (sft < 0.0) sft += L;
+            x[e] = P->box_lo[e] + sft;
+        }
+    }
+    return 0;
+}
+
+int oracle_step(oracle_scene* s, int32_t max_sweeps, double tol, oracle_step_stats* st)
+{
+    /* Alg. 2: detection -> (filter: one process, nothing to filter) ->
+     * initialisation -> NBGS sweeps -> integration. */
+    int64_t nc = 0;
+    int32_t ncol = 0, done = 0;
+    double R = 0.0;
+    int rc = oracle_detect_contacts(s, &nc);
+    if (!rc) rc = oracle_colour_contacts(s, &ncol);
+    if (!rc) rc = oracle_solve_nbgs(s, max_sweeps, tol, &done, &R);
+    if (!rc) rc = oracle_integrate(s);
+    if (!rc && st) {
+        st->n_contacts = nc;
+        st->n_colours = ncol;
+        st->sweeps_done = done;
+        st->residual = R;
+        st->v_ref = s->v_ref;
+    }
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* read-out                                                             */
+/* ------------------------------------------------------------------ */
+int oracle_get_contacts(const oracle_scene* s, int64_t cap,
+                        uint32_t* j1, uint32_t* j2, int32_t* colour,
+                        double* normal, double* xi, double* impulse, int64_t* n_out)
+{
+    if (!s) return 1;
+    if (n_out) *n_out = s->nc;
+    int64_t m = s->nc < cap ? s->nc : cap;
+    for (int64_t c = 0; c < m; ++c) {
+        if (j1) j1[c] = s->j1[c];
+        if (j2) j2[c] = s->j2[c];
+        if (colour) colour[c] = s->colour[c];
+        if (xi) xi[c] = s->xi[c];
+        for (int e = 0; e < 3; ++e) {
+            if (normal) normal[3 * c + e] = s->cn[3 * c + e];
+            if (impulse) impulse[3 * c + e] = s->p[3 * c + e];
+        }
+    }
+    return 0;
+}
+
+int oracle_set_impulses(oracle_scene* s, const double* impulse)
+{
+    if (!s || !impulse) return 1;
+    memcpy(s->p, impulse, 3 * (size_t)s->nc * sizeof(double));
+    return 0;
+}
+
+int oracle_residual_history(const oracle_scene* s, double* out, int32_t cap, int32_t* n_out)
+{
+    if (!s) return 1;
+    if (n_out) *n_out = s->nhist;
+    for (int32_t k = 0; k < s->nhist && k < cap; ++k) out[k] = s->hist[k];
+    return 0;
+}
+
+/* Residuals of the discrete constraints eq. (nonpenetration) and
+ * eq. (coulomb) at the current velocities and impulses, scaled to
+ * velocity units by v_ref. */
+int oracle_final_residuals(const oracle_scene* s, oracle_residuals* out)
+{
+    if (!s || !out) return 1;
+    memset(out, 0, sizeof(*out));
+    double vr = s->v_ref > 0.0 ? s->v_ref : 1e-12;
+    for (int64_t c = 0; c < s->nc; ++c) {
+        contact_k k;
+        build_contact(s, c, &k);
+        if (!(k.w_n > 0.0)) continue;
+        const double* p = &s->p[3 * c];
+        double u[3];
+        rel_velocity(s, &k, u);
+        double un = dot3(k.n, u), ut = dot3(k.t, u), uo = dot3(k.o, u);
+        double gn = k.bias + un;
+        double r_np = (gn < 0.0 ? -gn : 0.0) / vr;
+        double ptl = sqrt(p[1] * p[1] + p[2] * p[2]);
+        double cone = ptl - s->prm.mu * p[0];
+        double r_cone = (cone > 0.0 ? cone : 0.0) * k.w_t / vr;
+        double m = k.w_n * p[0] < gn ? k.w_n * p[0] : gn;
+        double r_comp = fabs(m) / vr;
+        double utl = sqrt(ut * ut + uo * uo);
+        double e1 = utl * p[1] + s->prm.mu * p[0] * ut;
+        double e2 = utl * p[2] + s->prm.mu * p[0] * uo;
+        double r_diss = sqrt(e1 * e1 + e2 * e2) * k.w_t / (vr * vr);
+        if (r_np > out->non_penetration) out->non_penetration = r_np;
+        if (r_cone > out->cone) out->cone = r_cone;
+        if (r_comp > out->complementarity) out->complementarity = r_comp;
+        if (r_diss > out->dissipation) out->dissipation = r_diss;
+    }
+    return 0;
+}

@@ -1,0 +1,117 @@
+/*
+ * nbgs_oracle.h -- FP64 sequential CPU reference ("oracle") for one time step
+ * of the hard-contact granular method of Preclik & Ruede, "Ultrascale
+ * Simulations of Non-smooth Granular Dynamics" (arXiv:1501.05810).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library exists to check the CUDA path: only
+ * the test suite, the package smoke check and the CPU-baseline leg of the
+ * benchmark load it.  It shares no code, header, table or helper with the
+ * CUDA library; the two only see the same seeded input arrays.
+ *
+ * Everything is double precision, single-threaded and written for
+ * readability: O(N^2) brute-force contact detection, a sequential greedy
+ * colouring, and the nonlinear block Gauss-Seidel (NBGS) of Alg. 1 with a
+ * single subdomain, run contact by contact in colour order.
+ *
+ * Passages followed (section / equation / algorithm of the paper):
+ *   Sect. 2, eq. (wrench) and the Q(phi) block  - wrench and quaternion rate
+ *   Sect. 2, eq. (contactpos)                   - contact point, normal, gap
+ *   Sect. 3, eq. (integrationscheme)            - semi-implicit Euler step
+ *   Sect. 3, eq. (nonpenetration), eq. (coulomb)- one-contact constraints
+ *   Sect. 4, eq. (expansionradius)              - intersection hulls
+ *   Sect. 5, Alg. 1                             - subdomain NBGS, relaxation
+ *   Sect. 6.3 (velocity accumulators)           - in-place velocity updates
+ *   Sect. 6.6, Alg. 2                           - order of one time step
+ *
+ * Return codes: 0 = ok, 1 = invalid argument, 2 = out of memory.
+ * All pointers are host pointers.  Arrays of 3-vectors are n x 3 row-major;
+ * quaternions are n x 4 in (w, x, y, z) order.
+ */
+#ifndef NBGS_ORACLE_H
+#define NBGS_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORACLE_MAX_PLANES 16
+
+enum { ORACLE_WARM_NONE = 0, ORACLE_WARM_PREV = 1 };
+
+typedef struct oracle_params {
+    double dt;          /* time step */
+    double gravity[3];  /* external acceleration (force / mass) */
+    double mu;          /* Coulomb friction coefficient, every contact */
+    double omega;       /* relaxation parameter of Alg. 1 (1 = classic NBGS) */
+    double tau;         /* hull safety margin of eq. (expansionradius) */
+    double beta;        /* scale of the penetration-correction term, xi < 0 */
+    double box_lo[3];   /* domain box; used for periodic wrapping only */
+    double box_hi[3];
+    int32_t periodic[3];
+    int32_t warm_start; /* ORACLE_WARM_NONE or ORACLE_WARM_PREV */
+    uint64_t colour_seed;
+} oracle_params;
+
+typedef struct oracle_step_stats {
+    int64_t n_contacts;
+    int32_t n_colours;
+    int32_t sweeps_done;
+    double residual;    /* R_k of the last sweep */
+    double v_ref;
+} oracle_step_stats;
+
+typedef struct oracle_residuals {
+    double non_penetration;   /* max_j max(0, -(xi'/dt + u_n)) / v_ref        */
+    double cone;              /* max_j max(0, |p_to| - mu p_n) w_t / v_ref     */
+    double complementarity;   /* max_j |min(w_n p_n, xi'/dt + u_n)| / v_ref    */
+    double dissipation;       /* max_j | |u_to| p_to + mu p_n u_to | w_t/v_ref^2 */
+} oracle_residuals;
+
+typedef struct oracle_scene oracle_scene;
+
+int  oracle_create_scene(const oracle_params* prm, int64_t n,
+                         const double* pos, const double* vel, const double* angvel,
+                         const double* radius, const double* density,
+                         oracle_scene** out);
+void oracle_destroy_scene(oracle_scene* s);
+/* Half-space wall {y : n . y <= c}; n must be a unit vector pointing out of
+ * the wall solid.  Walls are bodies of infinite mass with index n_bodies + k. */
+int  oracle_add_plane(oracle_scene* s, const double n[3], double c);
+/* Override inverse mass / inverse inertia (e.g. 0 = locked rotation). */
+int  oracle_set_mass_properties(oracle_scene* s, const double* invm, const double* invI);
+int  oracle_set_bodies(oracle_scene* s, const double* pos, const double* quat,
+                       const double* vel, const double* angvel);
+int  oracle_get_bodies(const oracle_scene* s, double* pos, double* quat,
+                       double* vel, double* angvel);
+
+int  oracle_detect_contacts(oracle_scene* s, int64_t* n_contacts);
+int  oracle_colour_contacts(oracle_scene* s, int32_t* n_colours);
+int  oracle_solve_nbgs(oracle_scene* s, int32_t max_sweeps, double tol,
+                       int32_t* sweeps_done, double* residual);
+int  oracle_integrate(oracle_scene* s);
+int  oracle_step(oracle_scene* s, int32_t max_sweeps, double tol, oracle_step_stats* st);
+
+/* Contacts in canonical order (ascending (j1 << 32) | j2).  Any output
+ * pointer may be NULL.  impulse = (p_n, p_t, p_o) in the contact frame. */
+int  oracle_get_contacts(const oracle_scene* s, int64_t cap,
+                         uint32_t* j1, uint32_t* j2, int32_t* colour,
+                         double* normal, double* xi, double* impulse,
+                         int64_t* n_out);
+/* Overwrite the contact-frame impulses (canonical order, 3 per contact). */
+int  oracle_set_impulses(oracle_scene* s, const double* impulse);
+int  oracle_residual_history(const oracle_scene* s, double* out, int32_t cap,
+                             int32_t* n_out);
+int  oracle_final_residuals(const oracle_scene* s, oracle_residuals* out);
+
+/* Unit-level pieces, exported for the known-answer tests. */
+void     oracle_contact_frame(const double n[3], double t[3], double o[3]);
+void     oracle_one_contact(double w_n, double w_t, double mu, const double b[3],
+                            double p[3]);
+uint64_t oracle_splitmix64(uint64_t x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,265 @@
+"""Seeded synthetic scenes (inputs only).
+
+This module is the one place that both the CUDA path and the CPU oracle take
+their inputs from.  It holds no arithmetic of the method itself: it draws
+positions, velocities, radii and densities with ``numpy.random.default_rng``
+and lays out lattices and walls.  Masses, hulls, contacts and everything
+else are computed by each side on its own.
+
+A scene is a dict::
+
+    {"name": str,
+     "params": {dt, gravity, mu, omega, tau, beta, box_lo, box_hi, periodic,
+                warm_start, colour_seed, precision},
+     "pos": (n, 3) f64, "vel": (n, 3) f64, "angvel": (n, 3) f64,
+     "radius": (n,) f64, "density": (n,) f64,
+     "planes": [((nx, ny, nz), c), ...]}   # wall solid {y : n . y <= c}
+
+Workload shapes follow the paper's setups (granular gas, Sect. 7.2.1;
+hexagonal close packing, Sect. 7.2.2) scaled to one GPU.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def default_params(**kw) -> dict:
+    p = {
+        "dt": 1e-3,
+        "gravity": (0.0, 0.0, -9.81),
+        "mu": 0.5,
+        "omega": 1.0,
+        "tau": 0.005,
+        "beta": 1.0,
+        "box_lo": (0.0, 0.0, 0.0),
+        "box_hi": (1.0, 1.0, 1.0),
+        "periodic": (0, 0, 0),
+        "warm_start": "none",
+        "colour_seed": 0x5EED,
+        "precision": "fp64",
+    }
+    p.update(kw)
+    return p
+
+
+def box_walls(lo, hi, axes=(0, 1, 2)) -> list:
+    """Six (or fewer) half-space walls enclosing [lo, hi]; each wall solid is
+    {y : n . y <= c} with n the unit normal pointing into the box."""
+    planes = []
+    for a in axes:
+        n = [0.0, 0.0, 0.0]
+        n[a] = 1.0
+        planes.append((tuple(n), float(lo[a])))
+        n = [0.0, 0.0, 0.0]
+        n[a] = -1.0
+        planes.append((tuple(n), -float(hi[a])))
+    return planes
+
+
+def _scene(name, params, pos, vel, angvel, radius, density, planes):
+    n = len(radius)
+    return {
+        "name": name,
+        "params": params,
+        "pos": np.ascontiguousarray(pos, dtype=np.float64).reshape(n, 3),
+        "vel": np.ascontiguousarray(vel, dtype=np.float64).reshape(n, 3),
+        "angvel": np.ascontiguousarray(angvel, dtype=np.float64).reshape(n, 3),
+        "radius": np.ascontiguousarray(radius, dtype=np.float64).reshape(n),
+        "density": np.ascontiguousarray(density, dtype=np.float64).reshape(n),
+        "planes": list(planes),
+    }
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+
+def lattice_box(seed: int = 0, per_side: int = 10, spacing: float = 1.05, radius: float = 0.5,
+                jitter: float = 0.02, vel_sigma: float = 0.1, **params) -> dict:
+    """Monodisperse spheres on a jittered simple-cubic lattice inside a box of
+    side per_side * spacing with six walls; velocities N(0, vel_sigma^2).
+
+    per_side=10 is the 1,000-sphere FP64 workload: r = 0.5, density 1,
+    spacing 1.05, jitter U(-0.02, 0.02), gravity -9.81 z, mu = 0.5, dt = 1e-3,
+    50 sweeps per step.  The box side is 10 * 1.05 = 10.5 so that the
+    lattice fits without initial overlap."""
+    rng = np.random.default_rng(seed)
+    side = per_side * spacing
+    k = np.arange(per_side)
+    gx, gy, gz = np.meshgrid(k, k, k, indexing="ij")
+    base = (np.stack([gx, gy, gz], -1).reshape(-1, 3) + 0.5) * spacing
+    pos = base + rng.uniform(-jitter, jitter, base.shape)
+    n = len(pos)
+    vel = rng.normal(0.0, vel_sigma, (n, 3))
+    prm = default_params(box_lo=(0.0, 0.0, 0.0), box_hi=(side, side, side), **params)
+    return _scene(f"lattice_box_{n}", prm, pos, vel, np.zeros((n, 3)), np.full(n, radius),
+                  np.ones(n), box_walls((0, 0, 0), (side, side, side)))
+
+
+def config1(seed: int = 0) -> dict:
+    """1,000 spheres, FP64: the small parity workload."""
+    return lattice_box(seed, per_side=10, dt=1e-3, mu=0.5, tau=0.005, precision="fp64")
+
+
+def loose_pour(seed: int = 0, n: int = 1_000_000, r_lo: float = 0.4, r_hi: float = 0.6,
+               base: float = 100.0, height: float = 200.0, phi: float = 0.3, **params) -> dict:
+    """Polydisperse spheres r ~ U(r_lo, r_hi), density 1, on a jittered cubic
+    lattice at volume fraction phi filling a walled box from the floor up,
+    under gravity.  n = 1e6 with base 100 x 100 x 200 is the 1M-sphere pour;
+    smaller n shrink the base so the column keeps its shape."""
+    rng = np.random.default_rng(seed)
+    radius = rng.uniform(r_lo, r_hi, n)
+    mean_vol = 4.0 / 3.0 * math.pi * np.mean(radius ** 3)
+    s = max((mean_vol / phi) ** (1.0 / 3.0), 2.0 * r_hi * 1.0001)
+    if n != 1_000_000:
+        base = base * (n / 1_000_000) ** (1.0 / 3.0)
+        height = height * (n / 1_000_000) ** (1.0 / 3.0)
+    nx = max(1, int(base // s))
+    nz = int(math.ceil(n / (nx * nx)))
+    idx = np.arange(n)
+    ix, iy, iz = idx % nx, (idx // nx) % nx, idx // (nx * nx)
+    pos = (np.stack([ix, iy, iz], -1) + 0.5) * s
+    j = (s - 2.0 * r_hi) / 2.0
+    pos = pos + rng.uniform(-j, j, pos.shape)
+    height = max(height, (nz + 1) * s)
+    lo, hi = (0.0, 0.0, 0.0), (nx * s, nx * s, height)
+    prm = default_params(dt=5e-4, mu=0.5, tau=0.01 * r_lo, box_lo=lo, box_hi=hi, **params)
+    return _scene(f"loose_pour_{n}", prm, pos, np.zeros((n, 3)), np.zeros((n, 3)), radius,
+                  np.ones(n), box_walls(lo, hi))
+
+
+def hcp_packing(nx: int, ny: int, nz: int, radius: float = 0.5, density: float = 1.0,
+                tilt_deg: float = 0.0, g: float = 9.81, v0: float = 0.0, **params) -> dict:
+    """Hexagonal close packing of equal spheres (Sect. 7.2.2): periodic in x
+    and y, confined in z by two walls touching the first and last layer.
+    ny must be even.  Gravity of magnitude g is tilted by tilt_deg in the
+    x-z plane (a ramp); every sphere starts with velocity v0 along +x."""
+    if ny % 2:
+        raise ValueError("hcp_packing needs an even ny")
+    r = radius
+    i, j, k = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    x = (2.0 * i + ((j + k) % 2)) * r
+    y = math.sqrt(3.0) * (j + (k % 2) / 3.0) * r
+    z = r + 2.0 * math.sqrt(6.0) / 3.0 * k * r
+    pos = np.stack([x, y, z], -1)
+    n = len(pos)
+    Lx, Ly = 2.0 * r * nx, math.sqrt(3.0) * r * ny
+    top = 2.0 * r + 2.0 * math.sqrt(6.0) / 3.0 * (nz - 1) * r
+    th = math.radians(tilt_deg)
+    grav = (g * math.sin(th), 0.0, -g * math.cos(th))
+    vel = np.zeros((n, 3))
+    vel[:, 0] = v0
+    lo, hi = (0.0, 0.0, 0.0), (Lx, Ly, top)
+    prm = default_params(gravity=grav, box_lo=lo, box_hi=hi, periodic=(1, 1, 0), **params)
+    return _scene(f"hcp_{nx}x{ny}x{nz}", prm, pos, vel, np.zeros((n, 3)), np.full(n, r),
+                  np.full(n, density), box_walls(lo, hi, axes=(2,)))
+
+
+def dense_packing(n_target: int = 1_000_000, seed: int = 0, **params) -> dict:
+    """A dense packing of ~n_target spheres in contact: the hexagonal close
+    packing above with r = 0.5 (the mean radius of the 1M pour), x, y
+    periodic and walls on both z faces, n_x = n_y (even) and n_z chosen for
+    the count.  It carries n_x n_y (6 n_z - 1) contacts, so the sweeps
+    dominate the step: the regime the settled 1M-sphere packing is
+    measured in.  Gravity -9.81 z, mu = 0.5, dt = 5e-4."""
+    side = int(round(n_target ** (1.0 / 3.0)))
+    side += side % 2
+    nz = max(1, int(round(n_target / (side * side))))
+    params.setdefault("dt", 5e-4)
+    params.setdefault("mu", 0.5)
+    params.setdefault("tau", 0.005)
+    sc = hcp_packing(side, side, nz, radius=0.5, **params)
+    rng = np.random.default_rng(seed)
+    sc["vel"] = sc["vel"] + rng.normal(0.0, 1e-3, sc["vel"].shape)
+    sc["name"] = f"dense_hcp_{len(sc['radius'])}"
+    return sc
+
+
+def granular_gas(cells: int = 196, seed: int = 0, r_lo: float = 0.45, r_hi: float = 0.55,
+                 phi: float = 0.5, jitter: float = 0.01, **params) -> dict:
+    """Dense granular gas: FCC lattice of cells^3 * 4 spheres with
+    r ~ U(r_lo, r_hi) in a triply periodic cube sized so that the volume
+    fraction is exactly phi for the drawn radii; velocities N(0, 1) per
+    component, no gravity, mu = 0.3, dt = 1e-4.  cells = 196 gives
+    30,118,144 spheres."""
+    rng = np.random.default_rng(seed)
+    n = 4 * cells ** 3
+    radius = rng.uniform(r_lo, r_hi, n)
+    vol = 4.0 / 3.0 * math.pi * float(np.sum(radius ** 3))
+    side = (vol / phi) ** (1.0 / 3.0)
+    a = side / cells
+    c = np.arange(cells)
+    gx, gy, gz = np.meshgrid(c, c, c, indexing="ij")
+    corner = np.stack([gx, gy, gz], -1).reshape(-1, 1, 3).astype(np.float64)
+    basis = np.array([[0.25, 0.25, 0.25], [0.75, 0.75, 0.25], [0.75, 0.25, 0.75], [0.25, 0.75, 0.75]])
+    pos = ((corner + basis[None]) * a).reshape(-1, 3)
+    pos = pos + rng.uniform(-jitter, jitter, pos.shape)
+    pos = np.mod(pos, side)
+    vel = rng.normal(0.0, 1.0, (n, 3))
+    prm = default_params(dt=1e-4, gravity=(0.0, 0.0, 0.0), mu=0.3, tau=0.01 * r_lo,
+                         box_lo=(0.0, 0.0, 0.0), box_hi=(side, side, side), periodic=(1, 1, 1),
+                         **params)
+    return _scene(f"granular_gas_{n}", prm, pos, vel, np.zeros((n, 3)), radius, np.ones(n), [])
+
+
+# ---------------------------------------------------------------------------
+# Known-answer scenes
+# ---------------------------------------------------------------------------
+
+def sphere_on_plane(radius: float = 0.5, density: float = 1.0, gap: float = 0.0, **params) -> dict:
+    prm = default_params(box_lo=(-5, -5, -5), box_hi=(5, 5, 5), **params)
+    pos = np.array([[0.0, 0.0, radius + gap]])
+    return _scene("sphere_on_plane", prm, pos, np.zeros((1, 3)), np.zeros((1, 3)), [radius], [density],
+                  [((0.0, 0.0, 1.0), 0.0)])
+
+
+def head_on(ra: float = 0.5, rb: float = 0.4, rho_a: float = 1.0, rho_b: float = 2.0, gap: float = 0.01,
+            va: float = 1.0, vb: float = -0.5, **params) -> dict:
+    """Two spheres on the x axis approaching each other, gravity off."""
+    params.setdefault("gravity", (0.0, 0.0, 0.0))
+    prm = default_params(box_lo=(-5, -5, -5), box_hi=(5, 5, 5), **params)
+    pos = np.array([[-(ra + gap / 2), 0.0, 0.0], [rb + gap / 2, 0.0, 0.0]])
+    vel = np.array([[va, 0.0, 0.0], [vb, 0.0, 0.0]])
+    return _scene("head_on", prm, pos, vel, np.zeros((2, 3)), [ra, rb], [rho_a, rho_b], [])
+
+
+def sliding(v0: float = 1.0, radius: float = 0.5, **params) -> dict:
+    """A sphere resting on the floor z = 0 and moving along +x at v0."""
+    prm = default_params(box_lo=(-50, -5, -5), box_hi=(50, 5, 5), **params)
+    pos = np.array([[0.0, 0.0, radius]])
+    vel = np.array([[v0, 0.0, 0.0]])
+    return _scene("sliding", prm, pos, vel, np.zeros((1, 3)), [radius], [1.0], [((0.0, 0.0, 1.0), 0.0)])
+
+
+def column(k: int = 5, radius: float = 0.5, **params) -> dict:
+    """k equal spheres stacked in touching contact on the floor z = 0."""
+    prm = default_params(box_lo=(-5, -5, -1), box_hi=(5, 5, 2 * radius * k + 5), **params)
+    z = radius + 2.0 * radius * np.arange(k)
+    pos = np.stack([np.zeros(k), np.zeros(k), z], -1)
+    return _scene(f"column_{k}", prm, pos, np.zeros((k, 3)), np.zeros((k, 3)), np.full(k, radius),
+                  np.ones(k), [((0.0, 0.0, 1.0), 0.0)])
+
+
+def periodic_cloud(seed: int = 0, per_side: int = 6, spacing: float = 1.02, r_lo: float = 0.4,
+                   r_hi: float = 0.5, vel_sigma: float = 1.0, **params) -> dict:
+    """Triply periodic box of polydisperse spheres on a jittered cubic lattice
+    with random linear and angular velocities; gravity off, no walls."""
+    rng = np.random.default_rng(seed)
+    side = per_side * spacing
+    k = np.arange(per_side)
+    gx, gy, gz = np.meshgrid(k, k, k, indexing="ij")
+    pos = (np.stack([gx, gy, gz], -1).reshape(-1, 3) + 0.5) * spacing
+    n = len(pos)
+    radius = rng.uniform(r_lo, r_hi, n)
+    j = (spacing - 2 * r_hi) / 2.0 * 0.9
+    pos = pos + rng.uniform(-j, j, pos.shape)
+    vel = rng.normal(0.0, vel_sigma, (n, 3))
+    ang = rng.normal(0.0, vel_sigma, (n, 3))
+    params.setdefault("gravity", (0.0, 0.0, 0.0))
+    params.setdefault("dt", 1e-2)
+    params.setdefault("periodic", (1, 1, 1))
+    prm = default_params(box_lo=(0, 0, 0), box_hi=(side, side, side), **params)
+    return _scene(f"periodic_cloud_{n}", prm, pos, vel, ang, radius, rng.uniform(0.5, 2.0, n), [])

@@ -1,0 +1,439 @@
+"""Pins for the CPU oracle: every check here compares it with something other
+than itself -- a value the paper prints, a closed form, a conservation law,
+a library routine or brute force."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1501_05810_gb300 import scenes
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _run(oracle_mod, sc, steps, sweeps, tol=0.0, mass=None):
+    o = oracle_mod.OracleScene(sc)
+    if mass is not None:
+        o.set_mass_properties(*mass)
+    stats = [o.step(sweeps, tol) for _ in range(steps)]
+    return o, stats
+
+
+def _mass(sc):
+    r, rho = sc["radius"], sc["density"]
+    m = rho * 4.0 / 3.0 * math.pi * r ** 3
+    return m, 0.4 * m * r ** 2
+
+
+# ---------------------------------------------------------------------------
+# building blocks
+# ---------------------------------------------------------------------------
+
+def test_splitmix64_published_first_output(oracle_mod):
+    # First output of splitmix64 started from state 0, as published with the
+    # generator (Steele, Lea, Flood 2014; Vigna's reference implementation).
+    assert oracle_mod.splitmix64(0) == 0xE220A8397B1DCDAF
+
+
+def test_contact_frame_orthonormal_right_handed(oracle_mod):
+    rng = np.random.default_rng(1)
+    ns = [np.array([0.0, 0.0, 1.0]), np.array([0.0, 0.0, -1.0]),
+          np.array([1.0, 0.0, 0.0]), np.array([0.0, 1e-9, -1.0])]
+    ns += list(rng.normal(size=(200, 3)))
+    for n in ns:
+        n = n / np.linalg.norm(n)
+        t, o = oracle_mod.contact_frame(n)
+        B = np.stack([n, t, o])
+        assert np.allclose(B @ B.T, np.eye(3), atol=1e-14)
+        assert np.allclose(np.cross(t, o), n, atol=1e-14)
+    t, o = oracle_mod.contact_frame([0.0, 0.0, 1.0])
+    assert np.array_equal(t, [1.0, 0.0, 0.0]) and np.array_equal(o, [0.0, 1.0, 0.0])
+
+
+def _coulomb_violation(w_n, w_t, mu, b, p):
+    """Distance of (p, u = b + W p) from eq. (nonpenetration) + eq. (coulomb)."""
+    u = b + np.array([w_n, w_t, w_t]) * p
+    scale = max(1.0, np.abs(b).max())
+    viol = [max(0.0, -p[0]), max(0.0, -u[0]) / scale, abs(p[0] * u[0]) / scale ** 2 * w_n]
+    pt, ut = p[1:], u[1:]
+    viol.append(max(0.0, np.linalg.norm(pt) - mu * p[0]) * w_t / scale)
+    if np.linalg.norm(pt) < mu * p[0] * (1 - 1e-9):
+        viol.append(np.linalg.norm(ut) / scale)          # sticking: no slip
+    else:                                                 # sliding: max dissipation
+        viol.append(np.linalg.norm(np.linalg.norm(ut) * pt + mu * p[0] * ut) * w_t / scale ** 2)
+    return max(viol)
+
+
+def test_one_contact_satisfies_discrete_constraints(oracle_mod):
+    rng = np.random.default_rng(2)
+    for _ in range(2000):
+        w_n = rng.uniform(0.1, 10.0)
+        w_t = w_n * rng.uniform(1.0, 3.5)
+        mu = rng.choice([0.0, rng.uniform(0.05, 1.5)])
+        b = rng.normal(size=3) * rng.choice([1e-3, 1.0, 1e3])
+        p = oracle_mod.one_contact(w_n, w_t, mu, b)
+        assert _coulomb_violation(w_n, w_t, mu, b, p) < 1e-12
+
+
+def test_one_contact_matches_brute_force_minimiser(oracle_mod):
+    """The normal impulse minimises 1/2 w_n p_n^2 + b_n p_n over p_n >= 0 and
+    the tangential one minimises 1/2 w_t |p_t|^2 + b_t . p_t over the disk
+    |p_t| <= mu p_n (the maximum-dissipation form of eq. coulomb for a
+    diagonal W).  Both found here by grid search + golden-section polish."""
+    rng = np.random.default_rng(3)
+    for _ in range(40):
+        w_n = rng.uniform(0.2, 5.0)
+        w_t = w_n * rng.uniform(1.0, 3.5)
+        mu = rng.uniform(0.1, 1.0)
+        b = rng.normal(size=3)
+        b[0] = -abs(b[0]) if rng.uniform() < 0.8 else abs(b[0])
+        p = oracle_mod.one_contact(w_n, w_t, mu, b)
+        # normal part: 1-D grid
+        grid = np.linspace(0.0, 5.0, 200001)
+        pn = grid[np.argmin(0.5 * w_n * grid ** 2 + b[0] * grid)]
+        assert abs(pn - p[0]) < 5e-5
+        pn = p[0]
+        R = mu * pn
+        f = lambda x, y: 0.5 * w_t * (x * x + y * y) + b[1] * x + b[2] * y
+        rr, th = np.meshgrid(np.linspace(0, R, 401), np.linspace(0, 2 * np.pi, 1441), indexing="ij")
+        vals = f(rr * np.cos(th), rr * np.sin(th))
+        i, j = np.unravel_index(np.argmin(vals), vals.shape)
+        r0, t0 = rr[i, j], th[i, j]
+        # polish: alternate golden-section searches in r and theta
+        def gs(g, lo, hi):
+            phi = (math.sqrt(5) - 1) / 2
+            for _ in range(80):
+                a, c = hi - phi * (hi - lo), lo + phi * (hi - lo)
+                if g(a) < g(c):
+                    hi = c
+                else:
+                    lo = a
+            return 0.5 * (lo + hi)
+        for _ in range(6):
+            r0 = gs(lambda r: f(r * math.cos(t0), r * math.sin(t0)), 0.0, R)
+            t0 = gs(lambda t: f(r0 * math.cos(t), r0 * math.sin(t)), t0 - 0.05, t0 + 0.05)
+        bf = np.array([r0 * math.cos(t0), r0 * math.sin(t0)])
+        assert np.allclose(bf, p[1:], atol=1e-9 * max(1.0, R))
+
+
+# ---------------------------------------------------------------------------
+# contact detection (Sect. 4)
+# ---------------------------------------------------------------------------
+
+def _two_spheres(gap, ra=0.5, rb=0.3, va=(0, 0, 0), periodic=False, dt=1e-3, tau=0.01):
+    prm = scenes.default_params(dt=dt, tau=tau, gravity=(0, 0, 0), box_lo=(0, 0, 0), box_hi=(10, 10, 10),
+                                periodic=(1, 1, 1) if periodic else (0, 0, 0))
+    if periodic:
+        pos = [[0.2, 5.0, 5.0], [10.0 + 0.2 - (ra + rb + gap), 5.0, 5.0]]
+    else:
+        pos = [[5.0, 5.0, 5.0], [5.0 + ra + rb + gap, 5.0, 5.0]]
+    return scenes._scene("pair", prm, np.array(pos), np.array([va, (0, 0, 0)], float), np.zeros((2, 3)),
+                         [ra, rb], [1.0, 1.0], [])
+
+
+def test_pair_geometry_and_hull_threshold(oracle_mod):
+    # a single pair: normal outward from S_j2, x_hat on S_j2, xi = d - ra - rb
+    sc = _two_spheres(0.004, va=(2.0, 0.0, 0.0))
+    o = oracle_mod.OracleScene(sc)
+    assert o.detect_contacts() == 1
+    c = o.get_contacts()
+    assert (c["j1"][0], c["j2"][0]) == (0, 1)
+    assert np.allclose(c["normal"][0], [-1, 0, 0])
+    assert abs(c["xi"][0] - 0.004) < 1e-12
+    # hulls: h_a = dt*|v_a| + tau = 0.012, h_b = tau = 0.01: kept up to 0.022
+    for gap, keep in [(0.0219, 1), (0.0221, 0), (-0.05, 1)]:
+        o = oracle_mod.OracleScene(_two_spheres(gap, va=(2.0, 0.0, 0.0)))
+        assert o.detect_contacts() == keep, gap
+
+
+def test_periodic_minimum_image(oracle_mod):
+    o = oracle_mod.OracleScene(_two_spheres(0.001, periodic=True))
+    assert o.detect_contacts() == 1
+    c = o.get_contacts()
+    # body 0 sits just right of x = 0, body 1 just left of x = 10: the normal
+    # from S_1 to S_0 points along +x through the boundary
+    assert np.allclose(c["normal"][0], [1, 0, 0]) and abs(c["xi"][0] - 0.001) < 1e-12
+
+
+def test_detection_matches_kdtree(oracle_mod):
+    """Brute-force pairs vs scipy's cKDTree neighbour query with the same
+    keep predicate applied afterwards."""
+    spatial = pytest.importorskip("scipy.spatial")
+    sc = scenes.periodic_cloud(seed=4, per_side=7, periodic=(0, 0, 0), dt=5e-2)
+    o = oracle_mod.OracleScene(sc)
+    nc = o.detect_contacts()
+    c = o.get_contacts()
+    P = sc["params"]
+    v, w, r = sc["vel"], sc["angvel"], sc["radius"]
+    h = P["dt"] * (np.linalg.norm(v, axis=1) + np.linalg.norm(w, axis=1) * r) + P["tau"]
+    tree = spatial.cKDTree(sc["pos"])
+    pairs = np.array(sorted(tree.query_pairs(2 * r.max() + 2 * h.max() + 1e-9)))
+    a, b = pairs[:, 0], pairs[:, 1]
+    d3 = sc["pos"][a] - sc["pos"][b]
+    d = np.sqrt((d3[:, 0] * d3[:, 0] + d3[:, 1] * d3[:, 1]) + d3[:, 2] * d3[:, 2])
+    keep = ((d - r[a]) - r[b]) <= (h[a] + h[b])
+    ref = set(zip(a[keep].tolist(), b[keep].tolist()))
+    got = set(zip(c["j1"].tolist(), c["j2"].tolist()))
+    assert got == ref and nc == len(ref) and nc > 50
+    keys = (c["j1"].astype(np.uint64) << np.uint64(32)) | c["j2"].astype(np.uint64)
+    assert np.all(np.diff(keys.astype(np.float64)) > 0)   # canonical order
+
+
+def test_hcp_contact_count_formula(oracle_mod):
+    rows = [l.split() for l in open(os.path.join(HERE, "golden", "hcp_contact_count.txt"))
+            if l.strip() and not l.startswith("#")]
+    for nx, ny, nz, npart, ncont in [tuple(int(x) for x in r) for r in rows]:
+        assert nx * ny * nz == npart
+        assert nx * ny * (6 * nz - 1) == ncont
+    for nx, ny, nz in [(4, 4, 10), (4, 6, 3), (6, 4, 1), (5, 4, 2)]:
+        sc = scenes.hcp_packing(nx, ny, nz, dt=1e-5, tau=1e-3)
+        o = oracle_mod.OracleScene(sc)
+        assert o.detect_contacts() == nx * ny * (6 * nz - 1)
+        c = o.get_contacts()
+        deg = np.bincount(np.concatenate([c["j1"], c["j2"][c["j2"] < nx * ny * nz]]), minlength=nx * ny * nz)
+        assert deg.max() <= 12 + 1          # at most 12 sphere neighbours (+ one wall)
+
+
+# ---------------------------------------------------------------------------
+# colouring
+# ---------------------------------------------------------------------------
+
+def test_colouring_is_first_fit_in_priority_order(oracle_mod):
+    sc = scenes.hcp_packing(4, 4, 3, dt=1e-5, tau=1e-3)
+    o = oracle_mod.OracleScene(sc)
+    o.detect_contacts()
+    ncol = o.colour_contacts()
+    c = o.get_contacts()
+    n = len(sc["radius"])
+    j1, j2, col = c["j1"].astype(np.int64), c["j2"].astype(np.int64), c["colour"]
+    keys = (j1 << 32) | j2
+    seed = sc["params"]["colour_seed"]
+    prio = np.array([oracle_mod.splitmix64(int(k) ^ seed) for k in keys], dtype=np.uint64)
+    nbr = [set() for _ in range(len(keys))]
+    by_body = {}
+    for k in range(len(keys)):
+        for b in (j1[k], j2[k]):
+            if b < n:
+                by_body.setdefault(b, []).append(k)
+    for lst in by_body.values():
+        for x in lst:
+            nbr[x].update(y for y in lst if y != x)
+    assert ncol == col.max() + 1
+    for k in range(len(keys)):
+        higher = [d for d in nbr[k] if (prio[d], -keys[d]) > (prio[k], -keys[k])]
+        assert all(col[d] != col[k] for d in nbr[k])                    # proper colouring
+        assert set(range(col[k])) <= {col[d] for d in higher}          # first fit
+    # walls never conflict: two wall contacts of the floor may share a colour
+    floor = np.nonzero(j2 == n)[0]
+    assert len(set(col[floor].tolist())) < len(floor)
+
+
+# ---------------------------------------------------------------------------
+# known-answer tests
+# ---------------------------------------------------------------------------
+
+def test_T1_sphere_resting_on_plane(oracle_mod):
+    sc = scenes.sphere_on_plane(dt=1e-3)
+    o = oracle_mod.OracleScene(sc)
+    m, _ = _mass(sc)
+    for _ in range(1000):
+        o.step(10)
+    c = o.get_contacts()
+    b = o.get_bodies()
+    assert abs(b["pos"][0, 2] - 0.5) <= 1e-12
+    assert np.abs(b["vel"][0]).max() <= 1e-15
+    assert abs(c["impulse"][0, 0] - m[0] * 9.81 * 1e-3) <= 1e-15 * m[0]
+
+
+def test_T2_head_on_inelastic(oracle_mod):
+    sc = scenes.head_on(dt=0.01, gap=0.01)
+    ma, mb = _mass(sc)[0]
+    va, vb = 1.0, -0.5
+    o = oracle_mod.OracleScene(sc)
+    st = o.step(20)
+    assert st["n_contacts"] == 1
+    b = o.get_bodies()
+    # one step: the gap closes exactly: n.(v_a' - v_b') = -xi0/dt
+    rel = b["vel"][0, 0] - b["vel"][1, 0]
+    assert abs(rel - 0.01 / 0.01) < 1e-14
+    p = o.get_contacts()["impulse"][0, 0]
+    assert abs(p - 0.5 / (1 / ma + 1 / mb)) < 1e-14 * p
+    assert abs((b["pos"][1, 0] - b["pos"][0, 0]) - (0.5 + 0.4)) < 1e-14
+    o.step(20)
+    b = o.get_bodies()
+    vcm = (ma * va + mb * vb) / (ma + mb)
+    assert np.allclose(b["vel"][:, 0], vcm, rtol=1e-14, atol=1e-15)
+    assert np.abs(b["angvel"]).max() == 0.0
+
+
+def test_T3a_locked_block_stops_at_v0_over_mu_g(oracle_mod):
+    mu, g, v0, dt = 0.5, 9.81, 1.0, 1e-3
+    sc = scenes.sliding(v0=v0, mu=mu, dt=dt)
+    m, _ = _mass(sc)
+    o = oracle_mod.OracleScene(sc)
+    o.set_mass_properties(1.0 / m, np.zeros(1))
+    t_stop = None
+    for k in range(400):
+        o.step(5)
+        vx = o.get_bodies()["vel"][0, 0]
+        if k < 5:
+            assert abs(vx - (v0 - mu * g * dt * (k + 1))) < 1e-12   # dv = -mu g dt per step
+        if t_stop is None and vx == 0.0:
+            t_stop = (k + 1) * dt
+    assert t_stop is not None
+    assert v0 / (mu * g) - dt - 1e-12 <= t_stop <= v0 / (mu * g) + dt + 1e-12
+
+
+def test_T3b_free_sphere_rolls_at_five_sevenths(oracle_mod):
+    mu, g, v0, dt, r = 0.3, 9.81, 1.0, 1e-3, 0.5
+    sc = scenes.sliding(v0=v0, mu=mu, dt=dt, radius=r)
+    o = oracle_mod.OracleScene(sc)
+    t_roll = None
+    for k in range(300):
+        o.step(5)
+        b = o.get_bodies()
+        slip = b["vel"][0, 0] - r * b["angvel"][0, 1]
+        if t_roll is None and abs(slip) < 1e-12:
+            t_roll = (k + 1) * dt
+    assert abs(t_roll - 2 * v0 / (7 * mu * g)) <= dt
+    assert abs(b["vel"][0, 0] - 5.0 / 7.0 * v0) < 1e-12
+    assert abs(b["angvel"][0, 1] * r - 5.0 / 7.0 * v0) < 1e-12
+
+
+def _momenta(sc, b):
+    m, I = _mass(sc)
+    P = (m[:, None] * b["vel"]).sum(0)
+    L = (np.cross(b["pos"], m[:, None] * b["vel"]) + I[:, None] * b["angvel"]).sum(0)
+    return P, L
+
+
+def test_T4_momentum_conserved_without_gravity(oracle_mod):
+    sc = scenes.periodic_cloud(seed=5, per_side=5, periodic=(0, 0, 0), dt=2e-2)
+    o = oracle_mod.OracleScene(sc)
+    P0, L0 = _momenta(sc, o.get_bodies())
+    scaleP = (_mass(sc)[0][:, None] * np.abs(sc["vel"])).sum()
+    total = 0
+    for _ in range(10):
+        st = o.step(20)
+        total += st["n_contacts"]
+        P1, L1 = _momenta(sc, o.get_bodies())
+        assert np.abs(P1 - P0).max() <= 1e-13 * scaleP
+        assert np.abs(L1 - L0).max() <= 1e-12 * scaleP * 10
+    assert total > 100
+    # periodic box: linear momentum still conserved
+    sc = scenes.periodic_cloud(seed=6, per_side=5, dt=2e-2)
+    o = oracle_mod.OracleScene(sc)
+    P0, _ = _momenta(sc, o.get_bodies())
+    for _ in range(5):
+        o.step(20)
+    P1, _ = _momenta(sc, o.get_bodies())
+    assert np.abs(P1 - P0).max() <= 1e-13 * scaleP
+
+
+def test_T5_residuals_after_convergence(oracle_mod):
+    sc = scenes.hcp_packing(4, 4, 3, dt=1e-3, tau=1e-3, mu=0.4, tilt_deg=30.0, v0=0.1)
+    o = oracle_mod.OracleScene(sc)
+    o.detect_contacts()
+    o.colour_contacts()
+    o.solve_nbgs(1)
+    early = o.final_residuals()
+    assert early["non_penetration"] > 1e-4 and early["complementarity"] > 1e-4   # not trivially 0
+    o = oracle_mod.OracleScene(sc)
+    o.detect_contacts()
+    o.colour_contacts()
+    k, R = o.solve_nbgs(5000, 1e-10)
+    assert R <= 1e-10 and k < 5000
+    res = o.final_residuals()
+    assert max(res.values()) < 1e-7, res
+    hist = o.residual_history()
+    assert len(hist) == k and hist[-1] == R
+    c = o.get_contacts()
+    p = c["impulse"]
+    assert np.all(p[:, 0] >= 0.0)
+    assert np.all(np.hypot(p[:, 1], p[:, 2]) <= 0.4 * p[:, 0] * (1 + 1e-12) + 1e-300)
+
+
+def test_T6_column_converges_to_weights(oracle_mod):
+    kcol, dt, g = 6, 1e-3, 9.81
+    sc = scenes.column(kcol, dt=dt)
+    m = _mass(sc)[0][0]
+    for seed in (0, 1, 2):
+        sc["params"]["colour_seed"] = seed
+        o = oracle_mod.OracleScene(sc)
+        o.detect_contacts()
+        o.colour_contacts()
+        k, R = o.solve_nbgs(20000, 1e-13)
+        assert R <= 1e-13
+        c = o.get_contacts()
+        for j1, j2, p in zip(c["j1"], c["j2"], c["impulse"][:, 0]):
+            above = kcol - j1 if j2 == kcol else kcol - j2   # spheres resting on this contact
+            assert abs(p - above * m * g * dt) < 1e-9 * kcol * m * g * dt
+
+
+def test_relaxation_parameter(oracle_mod):
+    # one contact, one sweep: lambda = omega y + (1 - omega) 0  (Alg. 1)
+    for omega in (1.0, 0.75, 0.5):
+        sc = scenes.sphere_on_plane(dt=1e-3, omega=omega)
+        m = _mass(sc)[0][0]
+        o = oracle_mod.OracleScene(sc)
+        o.detect_contacts()
+        o.colour_contacts()
+        o.solve_nbgs(1)
+        assert abs(o.get_contacts()["impulse"][0, 0] - omega * m * 9.81e-3) < 1e-15 * m
+
+
+def test_warm_start_from_previous_step(oracle_mod):
+    sc = scenes.column(4, dt=1e-3, warm_start="prev")
+    o = oracle_mod.OracleScene(sc)
+    o.step(2000, 1e-12)
+    warm = o.step(2000, 1e-12)["sweeps_done"]      # starts at the converged impulses
+    sc["params"]["warm_start"] = "none"
+    o2 = oracle_mod.OracleScene(sc)
+    o2.step(2000, 1e-12)
+    cold = o2.step(2000, 1e-12)["sweeps_done"]
+    assert warm <= 5 and cold > 5 * warm
+
+
+# ---------------------------------------------------------------------------
+# integration (Sect. 3)
+# ---------------------------------------------------------------------------
+
+def test_free_flight_and_quaternion_rotation(oracle_mod):
+    dt, steps = 1e-3, 1000
+    w = np.array([0.3, -1.2, 2.0])
+    sc = scenes.sphere_on_plane(dt=dt, gravity=(0, 0, 0))
+    sc["pos"] = np.array([[0.0, 0.0, 3.0]])
+    sc["vel"] = np.array([[0.5, -0.25, 0.125]])
+    sc["angvel"] = w[None]
+    o = oracle_mod.OracleScene(sc)
+    for _ in range(steps):
+        o.step(5)
+    b = o.get_bodies()
+    assert np.allclose(b["pos"][0], [0.5, -0.25, 3.125], atol=1e-12)
+    q = b["quat"][0]
+    assert abs(np.linalg.norm(q) - 1.0) < 1e-15
+    # exact rotation: angle |w| t about w / |w|
+    ang = np.linalg.norm(w) * dt * steps
+    qe = np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * w / np.linalg.norm(w)])
+    assert min(np.abs(q - qe).max(), np.abs(q + qe).max()) < 5 * dt
+
+
+def test_periodic_wrap(oracle_mod):
+    sc = _two_spheres(1.0, periodic=True)
+    sc["vel"] = np.array([[-30.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    sc["params"]["dt"] = 0.01
+    o = oracle_mod.OracleScene(sc)
+    o.step(1)
+    x = o.get_bodies()["pos"][0, 0]
+    assert abs(x - (10.0 + 0.2 - 0.3)) < 1e-12 and 0.0 <= x < 10.0
+
+
+def test_config1_runs_clean(oracle_mod):
+    sc = scenes.config1(0)
+    o = oracle_mod.OracleScene(sc)
+    for _ in range(5):
+        st = o.step(50)
+    b = o.get_bodies()
+    assert np.all(np.isfinite(b["vel"])) and st["n_contacts"] > 0
+    assert np.allclose(np.linalg.norm(b["quat"], axis=1), 1.0, atol=1e-15)
