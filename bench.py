@@ -1,0 +1,280 @@
+"""Benchmark of the NBGS granular time step on GB300.
+
+A step is one nbgs_step(): contact detection, colouring, NBGS sweeps
+(100 or residual 1e-6) and integration.  The default workload is the dense
+1M-sphere packing (hexagonal close packing 100 x 100 x 100, r = 0.5,
+mu = 0.5, dt = 5e-4, FP32 sweeps, FP64 positions): the sweep-dominated
+regime of the settled 1M-sphere packing.  Its working set (~1 GB) is larger
+than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line.  value = contact updates per second of whole-step
+device time (CUDA events on the scene stream), summed over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "contact updates/s in NBGS sweeps"
+UNIT = "contact updates/s"
+SWEEPS, TOL = 100, 1e-6
+# algorithmic bytes per contact update of the sweep kernel (read + write of
+# what must move once): sphere-sphere and sphere-wall, FP32 / FP64
+BYTES = {"fp32": (168, 112), "fp64": (328, 216)}
+
+
+def workload(name: str):
+    from paper_1501_05810_gb300 import scenes
+    if name == "dense1m":
+        sc = scenes.dense_packing(1_000_000, seed=0, precision="fp32")
+        desc = ("dense packing of 1,000,000 spheres (HCP 100x100x100, r=0.5, periodic x,y, walls z), "
+                "gravity -9.81 z, mu=0.5, dt=5e-4, 100 sweeps or residual 1e-6, FP32 sweeps, FP64 positions")
+        return sc, desc
+    if name == "config1":
+        sc = scenes.config1(0)
+        return sc, "1,000 spheres in a 10.5^3 walled box, FP64, mu=0.5, dt=1e-3, 50 sweeps"
+    if name == "gas":
+        sc = scenes.granular_gas(cells=int(os.environ.get("NBGS_GAS_CELLS", "196")), seed=0, precision="fp32")
+        return sc, f"granular gas, {len(sc['radius']):,} spheres, FCC at phi=0.5, periodic, FP32 sweeps"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def count_contact_kinds(g, n):
+    c = g.get_contacts()
+    walls = int(np.count_nonzero(c["j2"] >= n))
+    return len(c["j2"]) - walls, walls
+
+
+def cpu_baseline(steps_budget_s: float = 15.0):
+    """The oracle, as it stands, on a bounded sample of the same workload:
+    a 24 x 24 x 10 cut of the dense packing (5,760 spheres), whole steps
+    (O(N^2) detection + 100 sweeps) for about steps_budget_s seconds."""
+    import oracle
+    from paper_1501_05810_gb300 import scenes
+    sc = scenes.hcp_packing(24, 24, 10, radius=0.5, dt=5e-4, mu=0.5, tau=0.005)
+    o = oracle.OracleScene(sc)
+    t0 = time.perf_counter()
+    updates, steps = 0, 0
+    while True:
+        st = o.step(SWEEPS, TOL)
+        updates += st["n_contacts"] * st["sweeps_done"]
+        steps += 1
+        if time.perf_counter() - t0 > steps_budget_s and steps >= 2:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} whole oracle steps (brute-force detection + {SWEEPS} sweeps / tol {TOL}) of a "
+                      f"5,760-sphere 24x24x10 cut of the dense packing, {updates:,} contact updates in {dt:.1f} s, "
+                      f"1 thread, host nproc={os.cpu_count()}"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    cb = cpu_baseline(min(20.0, 5.0 + 2.0 * args.steps))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "oracle on a 5,760-sphere cut of the dense 1M-sphere packing (the full "
+                                   "size needs O(N^2) detection)", "l2": "inputs smaller than L2 (CPU run)"},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="dense1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1501_05810_gb300 import nbgs
+    sc, desc = workload(args.workload)
+    prec = sc["params"].get("precision", "fp64")
+    n = len(sc["radius"])
+    stream = torch.cuda.Stream(device=local)
+    with torch.cuda.stream(stream):
+        g = nbgs.Scene(sc, device=f"cuda:{local}", stream=stream)
+        sweeps = 50 if args.workload == "config1" else SWEEPS
+        tol = 0.0 if args.workload == "config1" else TOL
+        for _ in range(max(args.warmup, 0)):
+            g.step(sweeps, tol)
+        n_ss, n_sw = count_contact_kinds(g, n)
+        g.enable_timing(True)
+        clocks = ClockSampler(local)
+        clocks.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        updates, stats = 0, []
+        for _ in range(args.steps):
+            st = g.step(sweeps, tol)
+            stats.append(st)
+            updates += st["n_contacts"] * st["sweeps_done"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ck = clocks.stop()
+        ms_total = e0.elapsed_time(e1)
+        phase_ms, launches = g.get_timings()
+        # end to end through the public API with host buffers: upload the
+        # state from pinned memory, step, read the state back
+        host = {k: torch.empty((n, d), dtype=torch.float64, pin_memory=True)
+                for k, d in (("pos", 3), ("quat", 4), ("vel", 3), ("angvel", 3))}
+        b = g.get_bodies()
+        for k in host:
+            host[k].copy_(torch.from_numpy(b[k]))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_updates = 0
+        for _ in range(args.e2e_steps):
+            g.set_bodies(host["pos"], host["quat"], host["vel"], host["angvel"])
+            st = g.step(sweeps, tol)
+            e2e_updates += st["n_contacts"] * st["sweeps_done"]
+            nbgs._call(g.h, "nbgs_get_bodies", *[host[k].data_ptr() for k in ("pos", "quat", "vel", "angvel")])
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+
+    t_max = ms_total
+    if dist:
+        t = torch.tensor([ms_total, float(updates)], device=f"cuda:{local}", dtype=torch.float64)
+        tt = t.clone()
+        dist.all_reduce(tt[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+        t_max, updates_all = float(tt[0]), float(tt[1])
+    else:
+        updates_all = float(updates)
+    value = updates_all / (t_max / 1e3)
+    sweeps_done = [s["sweeps_done"] for s in stats]
+    contacts = [s["n_contacts"] for s in stats]
+    solve_ms = phase_ms["solve"]
+    sweep_rate = updates / (solve_ms / 1e3) if solve_ms > 0 else None
+    b_ss, b_sw = BYTES[prec]
+    # dominant kernel: the persistent sweep kernel, one launch per solve
+    alg_bytes_per_launch = (n_ss * b_ss + n_sw * b_sw) * statistics.mean(sweeps_done)
+    per_launch_ms = solve_ms / max(1, launches["solve"])
+    peak, peak_src = read_peaks()
+    achieved = alg_bytes_per_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": desc, "spheres": n, "contacts": contacts[-1], "sweeps_per_step": sweeps,
+                   "tol": tol, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "steps_per_s": args.steps / (t_max / 1e3),
+        "sweep_updates_per_s": sweep_rate,
+        "sweeps_done": sweeps_done,
+        "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
+        "gpu_launches": int(sum(launches.values())),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": f"k_solve_persistent<{'float' if prec == 'fp32' else 'double'}>",
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                     "alg_bytes_per_launch": alg_bytes_per_launch, "launch_ms": per_launch_ms},
+        "clocks": ck,
+        "e2e": {"value": e2e_updates / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(13 * 8 * n), "d2h_bytes_per_step": int(13 * 8 * n),
+                "steps": args.e2e_steps},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "dense1m":
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    g.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,192 @@
+/*
+ * nbgs.h -- C ABI of the GB300 (sm_103a) hard-contact granular time step.
+ *
+ * One call of nbgs_step() advances a scene of spheres and half-space walls by
+ * one time step of the method of Preclik & Ruede, "Ultrascale Simulations of
+ * Non-smooth Granular Dynamics" (arXiv:1501.05810):
+ *
+ *   contact detection  (Sect. 4, eq. expansionradius, eq. contactpos)
+ *   -> contact colouring (replaces the subdomain numbers s_c(j) of Alg. 1:
+ *      contacts of one colour share no body of finite mass)
+ *   -> nonlinear block Gauss-Seidel sweeps (Sect. 5, Alg. 1 with one
+ *      subdomain and relaxation omega; one-contact problem of Sect. 3,
+ *      eq. nonpenetration and eq. coulomb; in-place velocity accumulators
+ *      of Sect. 6.3)
+ *   -> semi-implicit Euler integration (Sect. 3, eq. integrationscheme)
+ *
+ * in the order of Alg. 2 (Sect. 6.6), all on the GPU.
+ *
+ * Conventions
+ *   - Every function returns nbgs_status.  Nothing throws across the ABI.
+ *   - Work is enqueued on the scene's CUDA stream and is asynchronous unless
+ *     the function documents that it synchronises (it then returns host
+ *     values or writes host memory).
+ *   - Array arguments are double precision; 3-vectors are n x 3 row-major,
+ *     quaternions n x 4 in (w, x, y, z) order.  Input and output pointers may
+ *     be host or device memory (copied with cudaMemcpyDefault).
+ *   - The scene owns every device buffer, allocated through the caller's
+ *     allocator (or cudaMallocAsync on the scene stream when none is given).
+ *     Inputs are copied; outputs are copies.
+ *   - The first error sticks: later calls return it until the scene is
+ *     destroyed; nbgs_last_error() returns its text.
+ *   - A scene is not thread-safe.  Different scenes are independent.
+ *   - Device-side failures (capacity overflow, NaN, a timed-out wait) are
+ *     written to a device status word and reported by the next call that
+ *     synchronises.
+ */
+#ifndef NBGS_H
+#define NBGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum nbgs_status {
+    NBGS_OK = 0,
+    NBGS_EINVAL = 1,     /* bad argument or scene state                          */
+    NBGS_ENOMEM = 2,     /* the allocator returned NULL                          */
+    NBGS_ECUDA = 3,      /* a CUDA runtime call failed                           */
+    NBGS_ECAPACITY = 4,  /* more contacts / colours than the buffers hold        */
+    NBGS_ENOTCONV = 5,   /* tolerance not reached in max_sweeps; results valid   */
+    NBGS_ENAN = 6,       /* a NaN or Inf appeared in the state                   */
+    NBGS_ETIMEOUT = 7    /* a device-side wait gave up (grid barrier)            */
+} nbgs_status;
+
+enum { NBGS_FP64 = 0, NBGS_FP32 = 1 };           /* arithmetic of the sweeps      */
+enum { NBGS_WARM_NONE = 0, NBGS_WARM_PREV = 1 }; /* initial impulses of a solve   */
+enum {                                           /* scheduling of the colour sweeps */
+    NBGS_SOLVER_PERSISTENT = 0,  /* one cooperative launch per solve, grid barrier between colours */
+    NBGS_SOLVER_PER_COLOUR = 1   /* one launch per colour and sweep                              */
+};
+
+typedef struct nbgs_allocator {
+    void* ctx;
+    void* (*alloc)(void* ctx, size_t bytes, void* stream); /* returns NULL on failure */
+    void (*free)(void* ctx, void* ptr, void* stream);
+} nbgs_allocator;
+
+typedef struct nbgs_params {
+    double dt;            /* time step                                              */
+    double gravity[3];    /* external acceleration                                  */
+    double mu;            /* Coulomb coefficient of every contact                   */
+    double omega;         /* relaxation of Alg. 1, in (0, 2); 1 = classic NBGS      */
+    double tau;           /* hull safety margin of eq. expansionradius, > 0         */
+    double beta;          /* scale of the xi/dt term when xi < 0 (Sect. 3)          */
+    double box_lo[3];     /* domain box: the cell grid spans it; periodic axes wrap */
+    double box_hi[3];
+    int32_t periodic[3];  /* 1 = periodic along this axis (needs >= 3 grid cells)   */
+    int32_t precision;    /* NBGS_FP64 or NBGS_FP32 (positions are always FP64)     */
+    int32_t warm_start;   /* NBGS_WARM_NONE or NBGS_WARM_PREV                       */
+    int32_t solver;       /* NBGS_SOLVER_*                                          */
+    uint64_t colour_seed; /* priorities of the colouring: splitmix64(key ^ seed)    */
+    int32_t contacts_per_body; /* contact buffer capacity per body, 0 = default 8   */
+    int32_t reserved;
+} nbgs_params;
+
+typedef struct nbgs_step_stats {
+    int64_t n_contacts;
+    int32_t n_colours;
+    int32_t sweeps_done;
+    double residual;      /* R_k = max_j |velocity change at j| / v_ref, last sweep */
+    double v_ref;         /* max(max_i |v_i| at step start, |g| dt, 1e-12)          */
+} nbgs_step_stats;
+
+typedef struct nbgs_residuals {  /* maxima over contacts, dimensionless (/ v_ref)  */
+    double non_penetration;      /* max(0, -(xi'/dt + u_n))                         */
+    double cone;                 /* max(0, |p_to| - mu p_n) w_t                     */
+    double complementarity;      /* |min(w_n p_n, xi'/dt + u_n)|                    */
+    double dissipation;          /* | |u_to| p_to + mu p_n u_to | w_t / v_ref       */
+} nbgs_residuals;
+
+typedef struct nbgs_scene nbgs_scene;
+
+/* Create a scene of n spheres (Sect. 2: m = density 4/3 pi r^3,
+ * I = 2/5 m r^2, quaternion (1,0,0,0)).  pos, vel, angvel: n x 3; radius,
+ * density: n.  allocator may be NULL.  stream: a cudaStream_t or NULL for the
+ * legacy default stream.  Synchronises.  n = 0 is allowed. */
+nbgs_status nbgs_create_scene(const nbgs_params* params, int64_t n,
+                              const double* pos, const double* vel, const double* angvel,
+                              const double* radius, const double* density,
+                              const nbgs_allocator* allocator, void* stream,
+                              nbgs_scene** out);
+void nbgs_destroy_scene(nbgs_scene* scene);
+const char* nbgs_last_error(const nbgs_scene* scene);
+
+/* Add a wall: the half-space solid {y : n . y <= c}, n a unit vector
+ * pointing out of the solid (Sect. 6.4 "global bodies" of infinite mass).
+ * Wall k gets body index n_bodies + k.  At most 16 walls. */
+nbgs_status nbgs_add_plane(nbgs_scene* scene, const double n[3], double c);
+
+/* Replace 1/m and/or 1/I of every sphere (n doubles each, NULL = keep).
+ * 0 makes the quantity infinite (e.g. invI = 0 locks the rotation). */
+nbgs_status nbgs_set_mass_properties(nbgs_scene* scene, const double* invm, const double* invI);
+
+/* Overwrite / read the body state; NULL arrays are skipped.
+ * nbgs_get_bodies synchronises. */
+nbgs_status nbgs_set_bodies(nbgs_scene* scene, const double* pos, const double* quat,
+                            const double* vel, const double* angvel);
+nbgs_status nbgs_get_bodies(nbgs_scene* scene, double* pos, double* quat,
+                            double* vel, double* angvel);
+
+/* Sect. 4: hull radii h_i = dt(|v_i| + |w_i| r_i) + tau from the current
+ * velocities, uniform cell grid sorted by radix sort, narrow phase
+ * (sphere-sphere, sphere-wall).  A pair is kept iff
+ * (d - r_a) - r_b <= h_a + h_b (walls: h = tau).  Contacts are stored in
+ * canonical order of (j1 << 32) | j2, j1 < j2.  Synchronises once to read the
+ * contact count (grows the buffers and retries on overflow). */
+nbgs_status nbgs_detect_contacts(nbgs_scene* scene, int64_t* n_contacts /* nullable */);
+
+/* Jones-Plassmann colouring of the conflict graph (contacts sharing a body
+ * of finite mass) with priorities splitmix64(key ^ colour_seed); equal to
+ * sequential first-fit in decreasing priority.  Asynchronous unless
+ * n_colours is non-NULL. */
+nbgs_status nbgs_colour_contacts(nbgs_scene* scene, int32_t* n_colours /* nullable */);
+
+/* One NBGS solve (Alg. 1): v += dt g, apply the initial impulses, then up to
+ * max_sweeps sweeps over the colours; stop early once R_k <= tol (tol = 0:
+ * exactly max_sweeps).  Colours the contacts first if needed.  Asynchronous
+ * unless sweeps_done or residual is non-NULL.  Call once per step. */
+nbgs_status nbgs_solve_nbgs(nbgs_scene* scene, int32_t max_sweeps, double tol,
+                            int32_t* sweeps_done /* nullable */, double* residual /* nullable */);
+
+/* eq. integrationscheme: x += dt v, q += dt Q(q) w, renormalise q, wrap
+ * periodic axes into [lo, hi).  Asynchronous. */
+nbgs_status nbgs_integrate(nbgs_scene* scene);
+
+/* detect -> colour -> solve -> integrate (Alg. 2).  stats may be NULL
+ * (then only the detection synchronises). */
+nbgs_status nbgs_step(nbgs_scene* scene, int32_t max_sweeps, double tol, nbgs_step_stats* stats);
+
+/* Copy the contacts in canonical order.  Any output may be NULL; at most cap
+ * contacts are written; *n_out receives the count.  impulse = (p_n, p_t, p_o)
+ * of the last solve in the contact frame (n, t, o), t and o from the
+ * orthonormal-basis construction of Duff et al. (JCGT 2017).  Synchronises. */
+nbgs_status nbgs_get_contacts(nbgs_scene* scene, int64_t cap,
+                              uint32_t* j1, uint32_t* j2, int32_t* colour,
+                              double* normal, double* xi, double* impulse, int64_t* n_out);
+
+/* R_k of every sweep of the last solve.  Synchronises. */
+nbgs_status nbgs_residual_history(nbgs_scene* scene, double* out, int32_t cap, int32_t* n_out);
+
+/* FP64 residuals of eq. nonpenetration and eq. coulomb at the current
+ * velocities and impulses.  Synchronises. */
+nbgs_status nbgs_final_residuals(nbgs_scene* scene, nbgs_residuals* out);
+
+/* Wait for the scene's stream and report device-side errors. */
+nbgs_status nbgs_sync(nbgs_scene* scene);
+
+/* Device time of the phases of the calls since the last reset, measured
+ * with CUDA events on the scene stream when timing is enabled:
+ * ms[0] detect, ms[1] colour, ms[2] solve (all sweep kernels), ms[3]
+ * integrate; launches[0..3] count the kernel launches of each phase.
+ * nbgs_get_timings synchronises. */
+nbgs_status nbgs_enable_timing(nbgs_scene* scene, int32_t on);
+nbgs_status nbgs_get_timings(nbgs_scene* scene, double ms[4], int64_t launches[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

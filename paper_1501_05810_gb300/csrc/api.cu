@@ -1,0 +1,507 @@
+// api.cu -- the extern "C" entry points declared in include/nbgs.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <utility>
+
+#include "nbgs_internal.cuh"
+
+namespace nbgs {
+
+nbgs_status fail(nbgs_scene* s, nbgs_status st, const std::string& msg)
+{
+    if (s && s->status == NBGS_OK) {
+        s->status = st;
+        s->err = msg;
+    }
+    return st;
+}
+
+nbgs_status cuda_check(nbgs_scene* s, cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return NBGS_OK;
+    return fail(s, NBGS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void* dev_alloc(nbgs_scene* s, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (s->has_alloc) {
+        p = s->alloc.alloc(s->alloc.ctx, bytes, (void*)s->stream);
+    } else if (cudaMallocAsync(&p, bytes, s->stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dev_free(nbgs_scene* s, void* p)
+{
+    if (!p) return;
+    if (s->has_alloc) s->alloc.free(s->alloc.ctx, p, (void*)s->stream);
+    else cudaFreeAsync(p, s->stream);
+}
+
+template <class T>
+static bool take(nbgs_scene* s, T*& p, size_t count)
+{
+    p = (T*)dev_alloc(s, count * sizeof(T));
+    return p != nullptr;
+}
+
+int persistent_blocks(nbgs_scene* s);  // solve.cu
+
+static size_t rec_bytes(const nbgs_scene* s) { return s->fp32 ? 32 : 64; }
+static size_t vec4_bytes(const nbgs_scene* s) { return s->fp32 ? 16 : 32; }
+
+static bool alloc_contact_arrays(nbgs_scene* s, int64_t cap)
+{
+    const size_t c = (size_t)cap;
+    bool ok = take(s, s->cj1, c) && take(s, s->cj2, c) && take(s, s->cgeo, c) && take(s, s->clev, c) &&
+              take(s, s->cimp, c) && take(s, s->cworld, c) && take(s, s->prev_j2, c) && take(s, s->prev_P, c) &&
+              take(s, s->adj, 2 * c) && take(s, s->cstate, c) && take(s, s->cprio, c) && take(s, s->wl[0], c) &&
+              take(s, s->wl[1], c) && take(s, s->colour_key, c) && take(s, s->colour_key2, c) &&
+              take(s, s->perm, c) && take(s, s->perm_in, c);
+    if (!ok) return false;
+    s->srec = dev_alloc(s, c * rec_bytes(s));
+    s->sp = dev_alloc(s, c * vec4_bytes(s));
+    return s->srec && s->sp;
+}
+
+static void free_contact_arrays(nbgs_scene* s)
+{
+    void* ps[] = {s->cj1, s->cj2, s->cgeo, s->clev, s->cimp, s->cworld, s->prev_j2, s->prev_P, s->adj, s->cstate,
+                  s->cprio, s->wl[0], s->wl[1], s->colour_key, s->colour_key2, s->perm, s->perm_in, s->srec, s->sp};
+    for (void* p : ps) dev_free(s, p);
+}
+
+static bool alloc_sort_temps(nbgs_scene* s)
+{
+    const int64_t big = std::max<int64_t>(std::max<int64_t>(s->n, s->ccap), 1);
+    const int64_t nb = (big + 4095) / 4096;
+    s->radix_hist_len = 256 * nb;
+    const int64_t scan_len = std::max<int64_t>(s->radix_hist_len, s->n + 1);
+    s->scan_tmp_len = (scan_len + 4095) / 4096 + 1;
+    return take(s, s->radix_hist, (size_t)s->radix_hist_len + 1) && take(s, s->scan_tmp, (size_t)s->scan_tmp_len);
+}
+
+// Grow every contact-sized buffer to hold `need` contacts; the previous
+// step's contacts (warm start) are carried over.
+nbgs_status grow_contacts(nbgs_scene* s, int64_t need)
+{
+    int64_t cap = need + need / 4 + 1024;
+    if (cap > 0xFFFFFFF0LL) return fail(s, NBGS_ECAPACITY, "contact count exceeds 32-bit indexing");
+    uint32_t* old_j2 = s->prev_j2;
+    double4_32a* old_P = s->prev_P;
+    s->prev_j2 = nullptr;
+    s->prev_P = nullptr;
+    free_contact_arrays(s);
+    dev_free(s, s->radix_hist);
+    dev_free(s, s->scan_tmp);
+    s->ccap = cap;
+    if (!alloc_contact_arrays(s, cap) || !alloc_sort_temps(s)) {
+        dev_free(s, old_j2);
+        dev_free(s, old_P);
+        return fail(s, NBGS_ENOMEM, "grow_contacts: allocation failed");
+    }
+    if (s->have_prev && s->prev_count > 0) {
+        cudaMemcpyAsync(s->prev_j2, old_j2, s->prev_count * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s->stream);
+        cudaMemcpyAsync(s->prev_P, old_P, s->prev_count * sizeof(double4_32a), cudaMemcpyDeviceToDevice, s->stream);
+    }
+    dev_free(s, old_j2);
+    dev_free(s, old_P);
+    return cuda_check(s, cudaGetLastError(), "grow_contacts");
+}
+
+static void timing_collect(nbgs_scene* s)
+{
+    if (!s->timing) return;
+    for (int k = 0; k < 4; ++k) {
+        float ms = 0.f;
+        if (cudaEventQuery(s->ev[2 * k + 1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, s->ev[2 * k], s->ev[2 * k + 1]) == cudaSuccess)
+            s->phase_ms[k] += ms;
+        cudaGetLastError();
+    }
+}
+
+// Events of a phase are re-recorded each call: fold the finished pair into
+// the running sums before it is overwritten.
+static void timing_fold(nbgs_scene* s, int k)
+{
+    if (!s->timing) return;
+    float ms = 0.f;
+    cudaEventSynchronize(s->ev[2 * k + 1]);
+    if (cudaEventElapsedTime(&ms, s->ev[2 * k], s->ev[2 * k + 1]) == cudaSuccess) s->phase_ms[k] += ms;
+    cudaGetLastError();
+}
+
+static nbgs_status check_device_errors(nbgs_scene* s)
+{
+    nbgs_status rc = cuda_check(s, cudaMemcpyAsync(s->hinfo, s->info, offsetof(DevInfo, rk_bits),
+                                                   cudaMemcpyDeviceToHost, s->stream), "sync: info");
+    if (rc == NBGS_OK) rc = cuda_check(s, cudaStreamSynchronize(s->stream), "sync");
+    if (rc != NBGS_OK) return rc;
+    const uint32_t e = s->hinfo->err;
+    if (e & kErrTimeout) return fail(s, NBGS_ETIMEOUT, "a grid barrier wait timed out");
+    if (e & kErrNaN) return fail(s, NBGS_ENAN, "NaN or Inf in the body state");
+    if (e & kErrColours) return fail(s, NBGS_ECAPACITY, "more than 128 colours needed");
+    return NBGS_OK;
+}
+
+}  // namespace nbgs
+
+using namespace nbgs;
+
+#define NBGS_GUARD(s)                              \
+    do {                                           \
+        if (!(s)) return NBGS_EINVAL;              \
+        if ((s)->status != NBGS_OK) return (s)->status; \
+    } while (0)
+
+extern "C" {
+
+nbgs_status nbgs_create_scene(const nbgs_params* params, int64_t n, const double* pos, const double* vel,
+                              const double* angvel, const double* radius, const double* density,
+                              const nbgs_allocator* allocator, void* stream, nbgs_scene** out)
+{
+    if (!params || !out || n < 0 || n > 0x7FFFFFF0LL) return NBGS_EINVAL;
+    if (n > 0 && (!pos || !vel || !angvel || !radius || !density)) return NBGS_EINVAL;
+    if (!(params->dt > 0.0) || !(params->tau > 0.0) || !(params->omega > 0.0) || !(params->mu >= 0.0))
+        return NBGS_EINVAL;
+    if (params->precision != NBGS_FP64 && params->precision != NBGS_FP32) return NBGS_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!(params->box_hi[a] > params->box_lo[a])) return NBGS_EINVAL;
+    *out = nullptr;
+    nbgs_scene* s = new (std::nothrow) nbgs_scene();
+    if (!s) return NBGS_ENOMEM;
+    s->prm = *params;
+    s->n = n;
+    s->fp32 = params->precision == NBGS_FP32;
+    s->stream = (cudaStream_t)stream;
+    if (allocator && allocator->alloc && allocator->free) {
+        s->alloc = *allocator;
+        s->has_alloc = true;
+    }
+    nbgs_status rc = cuda_check(s, cudaGetDevice(&s->device), "cudaGetDevice");
+    if (rc == NBGS_OK)
+        rc = cuda_check(s, cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device), "SM count");
+    if (rc != NBGS_OK) {
+        delete s;
+        return rc;
+    }
+    // largest radius: cell size lower bound
+    double rmax = 0.0;
+    if (n > 0) {
+        cudaPointerAttributes at{};
+        bool dev_ptr = cudaPointerGetAttributes(&at, radius) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+        cudaGetLastError();
+        if (dev_ptr) {
+            double* h = (double*)malloc(n * sizeof(double));
+            if (!h || cudaMemcpy(h, radius, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                free(h);
+                delete s;
+                return NBGS_ECUDA;
+            }
+            for (int64_t i = 0; i < n; ++i) rmax = std::max(rmax, h[i]);
+            free(h);
+        } else {
+            for (int64_t i = 0; i < n; ++i) rmax = std::max(rmax, radius[i]);
+        }
+    }
+    s->r_max = rmax;
+    const double cs_min = 2.0 * (rmax + params->tau);
+    s->max_cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        const double L = params->box_hi[a] - params->box_lo[a];
+        double d = std::floor(L / cs_min);
+        if (d < 1.0) d = 1.0;
+        if (d > 2048.0) d = 2048.0;
+        s->dims_max[a] = (int)d;
+        s->max_cells *= (int64_t)d;
+    }
+    if (s->max_cells > (int64_t)1 << 31) {
+        delete s;
+        return NBGS_EINVAL;
+    }
+    s->key_bits = 1;
+    while (((int64_t)1 << s->key_bits) < s->max_cells) ++s->key_bits;
+    const int cpb = params->contacts_per_body > 0 ? params->contacts_per_body : 8;
+    s->ccap = std::max<int64_t>(1024, (int64_t)cpb * n);
+    const size_t nn = (size_t)std::max<int64_t>(n, 1);
+
+    bool ok = take(s, s->pos_r, nn) && take(s, s->quat, nn) && take(s, s->hull, nn) && take(s, s->finite, nn) &&
+              take(s, s->stage, 13 * nn) && take(s, s->cell_start, (size_t)s->max_cells) &&
+              take(s, s->cell_end, (size_t)s->max_cells) && take(s, s->keys[0], nn) && take(s, s->keys[1], nn) &&
+              take(s, s->vals[0], nn) && take(s, s->vals[1], nn) && take(s, s->cand, nn * kCandCap) &&
+              take(s, s->sph_cnt, nn) && take(s, s->row_cnt, nn) && take(s, s->row_off, nn + 1) &&
+              take(s, s->prev_row_off, nn + 1) && take(s, s->deg, nn + 1) && take(s, s->adj_off, nn + 1) &&
+              take(s, s->col_count, kMaxColours + 1) && take(s, s->col_off, kMaxColours + 1) &&
+              take(s, s->info, 1);
+    if (ok) {
+        s->vel = dev_alloc(s, 2 * nn * vec4_bytes(s));
+        ok = s->vel && alloc_contact_arrays(s, s->ccap) && alloc_sort_temps(s);
+    }
+    if (ok) ok = cudaMallocHost((void**)&s->hinfo, sizeof(DevInfo)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        nbgs_destroy_scene(s);
+        return NBGS_ENOMEM;
+    }
+    cudaMemsetAsync(s->info, 0, sizeof(DevInfo), s->stream);
+    cudaMemsetAsync(s->vel, 0, 2 * nn * vec4_bytes(s), s->stream);
+    cudaMemsetAsync(s->pos_r, 0, nn * sizeof(double4_32a), s->stream);
+    cudaMemsetAsync(s->cstate, 0xFF, s->ccap * sizeof(uint32_t), s->stream);
+    cudaMemsetAsync(s->row_off, 0, (nn + 1) * sizeof(uint32_t), s->stream);
+    cudaMemsetAsync(s->prev_row_off, 0, (nn + 1) * sizeof(uint32_t), s->stream);
+    for (int k = 0; k < 8; ++k) cudaEventCreate(&s->ev[k]);
+    s->coop_blocks = persistent_blocks(s);
+    if (n > 0) {
+        // identity quaternions: staged by the unpack kernel
+        double* q = (double*)malloc(4 * n * sizeof(double));
+        if (!q) {
+            nbgs_destroy_scene(s);
+            return NBGS_ENOMEM;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            q[4 * i] = 1.0;
+            q[4 * i + 1] = q[4 * i + 2] = q[4 * i + 3] = 0.0;
+        }
+        rc = run_set_mass(s, nullptr, nullptr, true, radius, density);
+        if (rc == NBGS_OK) rc = run_set_bodies(s, pos, q, vel, angvel);
+        if (rc == NBGS_OK) rc = cuda_check(s, cudaStreamSynchronize(s->stream), "create_scene");
+        free(q);
+        if (rc != NBGS_OK) {
+            nbgs_destroy_scene(s);
+            return rc;
+        }
+    } else {
+        rc = cuda_check(s, cudaStreamSynchronize(s->stream), "create_scene");
+        if (rc != NBGS_OK) {
+            nbgs_destroy_scene(s);
+            return rc;
+        }
+    }
+    *out = s;
+    return NBGS_OK;
+}
+
+void nbgs_destroy_scene(nbgs_scene* s)
+{
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    void* ps[] = {s->pos_r, s->quat, s->vel, s->hull, s->finite, s->stage, s->cell_start, s->cell_end, s->keys[0],
+                  s->keys[1], s->vals[0], s->vals[1], s->radix_hist, s->scan_tmp, s->cand, s->sph_cnt, s->row_cnt,
+                  s->row_off, s->prev_row_off, s->deg, s->adj_off, s->col_count, s->col_off, s->info};
+    for (void* p : ps) dev_free(s, p);
+    free_contact_arrays(s);
+    cudaStreamSynchronize(s->stream);
+    if (s->hinfo) cudaFreeHost(s->hinfo);
+    for (int k = 0; k < 8; ++k)
+        if (s->ev[k]) cudaEventDestroy(s->ev[k]);
+    cudaGetLastError();
+    delete s;
+}
+
+const char* nbgs_last_error(const nbgs_scene* s)
+{
+    if (!s) return "null scene";
+    return s->err.c_str();
+}
+
+nbgs_status nbgs_add_plane(nbgs_scene* s, const double n[3], double c)
+{
+    NBGS_GUARD(s);
+    if (!n || s->planes.count >= kMaxPlanes) return fail(s, NBGS_EINVAL, "add_plane: bad normal or too many walls");
+    const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(std::fabs(len - 1.0) < 1e-9)) return fail(s, NBGS_EINVAL, "add_plane: normal must be a unit vector");
+    const int k = s->planes.count++;
+    for (int e = 0; e < 3; ++e) s->planes.n[k][e] = n[e];
+    s->planes.c[k] = c;
+    s->detected = s->coloured = false;
+    return NBGS_OK;
+}
+
+nbgs_status nbgs_set_mass_properties(nbgs_scene* s, const double* invm, const double* invI)
+{
+    NBGS_GUARD(s);
+    return run_set_mass(s, invm, invI, false, nullptr, nullptr);
+}
+
+nbgs_status nbgs_set_bodies(nbgs_scene* s, const double* pos, const double* quat, const double* vel,
+                            const double* angvel)
+{
+    NBGS_GUARD(s);
+    s->have_prev = false;
+    s->solved = false;
+    return run_set_bodies(s, pos, quat, vel, angvel);
+}
+
+nbgs_status nbgs_get_bodies(nbgs_scene* s, double* pos, double* quat, double* vel, double* angvel)
+{
+    NBGS_GUARD(s);
+    return run_get_bodies(s, pos, quat, vel, angvel);
+}
+
+nbgs_status nbgs_detect_contacts(nbgs_scene* s, int64_t* n_contacts)
+{
+    NBGS_GUARD(s);
+    if (s->timing) timing_fold(s, 0);
+    nbgs_status rc = run_detect(s);
+    if (rc == NBGS_OK && n_contacts) *n_contacts = s->n_contacts;
+    return rc;
+}
+
+nbgs_status nbgs_colour_contacts(nbgs_scene* s, int32_t* n_colours)
+{
+    NBGS_GUARD(s);
+    if (s->timing && s->coloured) timing_fold(s, 1);
+    nbgs_status rc = run_colour(s);
+    if (rc == NBGS_OK && n_colours) {
+        uint32_t nc = 0;
+        rc = cuda_check(s, cudaMemcpyAsync(&nc, &s->info->n_colours, 4, cudaMemcpyDeviceToHost, s->stream), "colours");
+        if (rc == NBGS_OK) rc = check_device_errors(s);
+        if (rc == NBGS_OK) *n_colours = (int32_t)nc;
+    }
+    return rc;
+}
+
+nbgs_status nbgs_solve_nbgs(nbgs_scene* s, int32_t max_sweeps, double tol, int32_t* sweeps_done, double* residual)
+{
+    NBGS_GUARD(s);
+    if (!s->detected) return fail(s, NBGS_EINVAL, "solve_nbgs: call detect_contacts first");
+    if (max_sweeps < 0) return fail(s, NBGS_EINVAL, "solve_nbgs: max_sweeps < 0");
+    nbgs_status rc = run_solve(s, max_sweeps, tol);
+    if (rc != NBGS_OK) return rc;
+    if (sweeps_done || residual) {
+        rc = check_device_errors(s);
+        if (rc != NBGS_OK) return rc;
+        uint32_t k = s->hinfo->sweeps_done;
+        if (max_sweeps == 0) k = 0;
+        if (sweeps_done) *sweeps_done = (int32_t)k;
+        if (residual) *residual = s->hinfo->residual;
+    }
+    return NBGS_OK;
+}
+
+nbgs_status nbgs_integrate(nbgs_scene* s)
+{
+    NBGS_GUARD(s);
+    return run_integrate(s);
+}
+
+nbgs_status nbgs_step(nbgs_scene* s, int32_t max_sweeps, double tol, nbgs_step_stats* st)
+{
+    NBGS_GUARD(s);
+    if (s->timing) {
+        timing_fold(s, 1);
+        timing_fold(s, 2);
+        timing_fold(s, 3);
+    }
+    nbgs_status rc = nbgs_detect_contacts(s, nullptr);
+    if (rc == NBGS_OK) rc = run_colour(s);
+    if (rc == NBGS_OK) rc = run_solve(s, max_sweeps, tol);
+    if (rc == NBGS_OK) rc = run_integrate(s);
+    if (rc != NBGS_OK) return rc;
+    if (st) {
+        rc = cuda_check(s, cudaMemcpyAsync(s->hinfo, s->info, offsetof(DevInfo, rk_bits), cudaMemcpyDeviceToHost,
+                                           s->stream), "step stats");
+        if (rc == NBGS_OK) rc = check_device_errors(s);
+        if (rc != NBGS_OK) return rc;
+        st->n_contacts = s->n_contacts;
+        st->n_colours = (int32_t)s->hinfo->n_colours;
+        st->sweeps_done = max_sweeps == 0 ? 0 : (int32_t)s->hinfo->sweeps_done;
+        st->residual = s->hinfo->residual;
+        st->v_ref = s->hinfo->v_ref;
+    }
+    return NBGS_OK;
+}
+
+nbgs_status nbgs_get_contacts(nbgs_scene* s, int64_t cap, uint32_t* j1, uint32_t* j2, int32_t* colour,
+                              double* normal, double* xi, double* impulse, int64_t* n_out)
+{
+    NBGS_GUARD(s);
+    if (cap < 0) return fail(s, NBGS_EINVAL, "get_contacts: cap < 0");
+    if (n_out) *n_out = s->n_contacts;
+    nbgs_status rc = run_get_contacts(s, cap, j1, j2, colour, normal, xi, impulse);
+    if (rc == NBGS_OK) rc = check_device_errors(s);
+    return rc;
+}
+
+nbgs_status nbgs_residual_history(nbgs_scene* s, double* out, int32_t cap, int32_t* n_out)
+{
+    NBGS_GUARD(s);
+    nbgs_status rc = check_device_errors(s);
+    if (rc != NBGS_OK) return rc;
+    int32_t k = s->solved ? (int32_t)s->hinfo->sweeps_done : 0;
+    if (s->solved && s->last_sweeps == 0) k = 0;
+    if (k > kHistKept) k = kHistKept;
+    if (n_out) *n_out = k;
+    const int32_t m = std::min(k, cap);
+    if (m > 0 && out) {
+        unsigned long long* tmp = (unsigned long long*)malloc(m * sizeof(unsigned long long));
+        if (!tmp) return fail(s, NBGS_ENOMEM, "residual_history: host allocation");
+        rc = cuda_check(s, cudaMemcpy(tmp, s->info->rk_bits, m * sizeof(unsigned long long), cudaMemcpyDeviceToHost),
+                        "residual_history");
+        const double vr = s->hinfo->v_ref > 0 ? s->hinfo->v_ref : 1e-12;
+        for (int32_t i = 0; i < m && rc == NBGS_OK; ++i) {
+            double d;
+            std::memcpy(&d, &tmp[i], sizeof(double));
+            out[i] = d / vr;
+        }
+        free(tmp);
+    }
+    return rc;
+}
+
+nbgs_status nbgs_final_residuals(nbgs_scene* s, nbgs_residuals* out)
+{
+    NBGS_GUARD(s);
+    if (!out) return fail(s, NBGS_EINVAL, "final_residuals: null output");
+    nbgs_status rc = run_final_residuals(s, out);
+    if (rc == NBGS_OK) rc = check_device_errors(s);
+    return rc;
+}
+
+nbgs_status nbgs_sync(nbgs_scene* s)
+{
+    NBGS_GUARD(s);
+    return check_device_errors(s);
+}
+
+nbgs_status nbgs_enable_timing(nbgs_scene* s, int32_t on)
+{
+    NBGS_GUARD(s);
+    nbgs_status rc = cuda_check(s, cudaStreamSynchronize(s->stream), "enable_timing");
+    s->timing = on != 0;
+    for (int k = 0; k < 4; ++k) {
+        s->phase_ms[k] = 0.0;
+        s->phase_launches[k] = 0;
+    }
+    // mark every event pair as empty: record start and end back to back
+    for (int k = 0; k < 8; ++k) cudaEventRecord(s->ev[k], s->stream);
+    cudaStreamSynchronize(s->stream);
+    return rc;
+}
+
+nbgs_status nbgs_get_timings(nbgs_scene* s, double ms[4], int64_t launches[4])
+{
+    NBGS_GUARD(s);
+    nbgs_status rc = cuda_check(s, cudaStreamSynchronize(s->stream), "get_timings");
+    if (rc != NBGS_OK) return rc;
+    timing_collect(s);
+    for (int k = 0; k < 4; ++k) {
+        if (ms) ms[k] = s->phase_ms[k];
+        if (launches) launches[k] = s->phase_launches[k];
+        s->phase_ms[k] = 0.0;
+    }
+    // collected pairs must not be folded again
+    for (int k = 0; k < 8; ++k) cudaEventRecord(s->ev[k], s->stream);
+    cudaStreamSynchronize(s->stream);
+    return NBGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,292 @@
+// colour.cu -- contact colouring and the colour-ordered sweep records.
+//
+// The subdomain numbers s_c(j) of Alg. 1 become colours: two contacts that
+// share a body of finite mass never get the same colour, so all contacts of
+// one colour can be relaxed at once with in-place velocity updates and no
+// atomics, and the result equals the sequential NBGS in colour order.
+//
+//   k_colour_init   priority splitmix64(key ^ seed), body degrees
+//   scan + k_adj_fill  body -> contact incidence lists (finite bodies only)
+//   k_jp_round      Jones-Plassmann round: an uncoloured contact whose
+//                   priority beats every uncoloured neighbour takes the
+//                   smallest colour unused by its coloured neighbours; this
+//                   equals first-fit greedy in decreasing priority
+//   k_colour_keys   colour histogram
+//   radix pass      stable counting sort by colour -> permutation
+//   k_build_sweep   sweep records in colour order, initial impulses
+#include <utility>
+
+#include "nbgs_internal.cuh"
+
+namespace nbgs {
+
+__global__ void k_colour_init(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
+                              const uint8_t* __restrict__ finite, uint64_t seed, uint32_t* __restrict__ deg,
+                              uint64_t* __restrict__ prio, uint32_t* __restrict__ cstate, uint32_t* __restrict__ wl)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = cj1[c], b = cj2[c];
+        prio[c] = splitmix64((((uint64_t)a << 32) | b) ^ seed);
+        cstate[c] = kUncoloured;
+        wl[c] = (uint32_t)c;
+        if (finite[a]) atomicAdd(&deg[a], 1u);
+        if (b < n && finite[b]) atomicAdd(&deg[b], 1u);
+    }
+}
+
+__global__ void k_adj_fill(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
+                           const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
+                           uint32_t* __restrict__ fill, uint32_t* __restrict__ adj)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = cj1[c], b = cj2[c];
+        if (finite[a]) adj[adj_off[a] + atomicAdd(&fill[a], 1u)] = (uint32_t)c;
+        if (b < n && finite[b]) adj[adj_off[b] + atomicAdd(&fill[b], 1u)] = (uint32_t)c;
+    }
+}
+
+// (prio, key) of d beats that of c: higher priority, ties to the lower key.
+__device__ __forceinline__ bool beats(uint64_t pd, uint32_t d, uint64_t pc, uint32_t c, const uint32_t* cj1,
+                                      const uint32_t* cj2)
+{
+    if (pd != pc) return pd > pc;
+    const uint64_t kd = ((uint64_t)cj1[d] << 32) | cj2[d];
+    const uint64_t kc = ((uint64_t)cj1[c] << 32) | cj2[c];
+    return kd < kc;
+}
+
+// One Jones-Plassmann round.  cstate[d] = (round << 8) | colour, or
+// kUncoloured.  A neighbour stamped with the current round counts as
+// uncoloured here (it is being coloured concurrently and, being a local
+// maximum, necessarily beats c).
+__global__ void k_jp_round(uint32_t round, int64_t n, const uint32_t* __restrict__ wl_in,
+                           const uint32_t* __restrict__ cnt_in, uint32_t* __restrict__ wl_out,
+                           uint32_t* __restrict__ cnt_out, const uint32_t* __restrict__ cj1,
+                           const uint32_t* __restrict__ cj2, const uint8_t* __restrict__ finite,
+                           const uint32_t* __restrict__ adj_off, const uint32_t* __restrict__ adj,
+                           const uint64_t* __restrict__ prio, uint32_t* cstate, DevInfo* info)
+{
+    const uint32_t m = *cnt_in;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t base = blockIdx.x * blockDim.x; base < m; base += gridDim.x * blockDim.x) {
+        const uint32_t k = base + threadIdx.x;
+        bool pending = false;
+        if (k < m) {
+            const uint32_t c = wl_in[k];
+            const uint64_t pc = prio[c];
+            uint64_t used0 = 0, used1 = 0;
+            bool local_max = true;
+            const uint32_t bodies[2] = {cj1[c], cj2[c]};
+            for (int e = 0; e < 2 && local_max; ++e) {
+                const uint32_t b = bodies[e];
+                if (b >= n || !finite[b]) continue;
+                const uint32_t end = adj_off[b + 1];
+                for (uint32_t t = adj_off[b]; t < end; ++t) {
+                    const uint32_t d = adj[t];
+                    if (d == c) continue;
+                    const uint32_t sd = cstate[d];
+                    if (sd == kUncoloured || (sd >> 8) >= round) {
+                        if (beats(prio[d], d, pc, c, cj1, cj2)) {
+                            local_max = false;
+                            break;
+                        }
+                    } else {
+                        const uint32_t col = sd & 0xFFu;
+                        if (col < 64) used0 |= 1ull << col;
+                        else used1 |= 1ull << (col - 64);
+                    }
+                }
+            }
+            if (local_max) {
+                uint32_t col;
+                if (~used0) col = __ffsll((long long)~used0) - 1;
+                else if (~used1) col = 64 + __ffsll((long long)~used1) - 1;
+                else {
+                    atomicOr(&info->err, kErrColours);
+                    col = kMaxColours - 1;
+                }
+                cstate[c] = (round << 8) | col;
+            } else {
+                pending = true;
+            }
+        }
+        // warp-aggregated append of the contacts left for the next round
+        const uint32_t mask = __ballot_sync(0xffffffffu, pending);
+        if (mask) {
+            uint32_t basew = 0;
+            if (lane == 0) basew = atomicAdd(cnt_out, (uint32_t)__popc(mask));
+            basew = __shfl_sync(0xffffffffu, basew, 0);
+            if (pending) wl_out[basew + __popc(mask & ((1u << lane) - 1u))] = wl_in[k];
+        }
+    }
+}
+
+__global__ void k_colour_keys(int64_t C, const uint32_t* __restrict__ cstate, uint32_t* __restrict__ ckey,
+                              uint32_t* __restrict__ cval, uint32_t* __restrict__ col_count, DevInfo* info)
+{
+    __shared__ uint32_t h[kMaxColours];
+    for (int t = threadIdx.x; t < kMaxColours; t += blockDim.x) h[t] = 0;
+    __syncthreads();
+    uint32_t cmax = 0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t col = cstate[c] & 0xFFu;
+        ckey[c] = col;
+        cval[c] = (uint32_t)c;
+        atomicAdd(&h[col], 1u);
+        cmax = max(cmax, col + 1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kMaxColours; t += blockDim.x)
+        if (h[t]) atomicAdd(&col_count[t], h[t]);
+    for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_down_sync(0xffffffffu, cmax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&info->n_colours, cmax);
+}
+
+__global__ void k_colour_offsets(const uint32_t* __restrict__ col_count, uint32_t* __restrict__ col_off)
+{
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int c = 0; c < kMaxColours; ++c) {
+            col_off[c] = acc;
+            acc += col_count[c];
+        }
+        col_off[kMaxColours] = acc;
+    }
+}
+
+// Sweep record s <- canonical contact perm[s]; initial impulse from the
+// previous step (world frame, re-projected onto the new frame and the cone)
+// or zero.
+template <class R>
+__global__ void k_build_sweep(int64_t C, int64_t n, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cj1,
+                              const uint32_t* __restrict__ cj2, const double4_32a* __restrict__ cgeo,
+                              const double2* __restrict__ clev, double dt, double beta, double mu, int warm,
+                              const uint32_t* __restrict__ prev_row_off, const uint32_t* __restrict__ prev_j2,
+                              const double4_32a* __restrict__ prev_P, SweepRec<R>* __restrict__ rec,
+                              R4<R>* __restrict__ p)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < C; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = perm[s];
+        const uint32_t a = cj1[c], b = cj2[c];
+        const double4_32a g = cgeo[c];
+        const double2 l = clev[c];
+        // eq. (nonpenetration): gap term xi/dt, scaled by beta when xi < 0
+        const double xs = g.w >= 0.0 ? g.w : beta * g.w;
+        const double bias = xs / dt;
+        SweepRec<R> r;
+        if constexpr (sizeof(R) == 4) {
+            r.a = make_float4(__uint_as_float(a), __uint_as_float(b), (float)l.x, (float)l.y);
+            r.b = make_float4((float)g.x, (float)g.y, (float)g.z, (float)bias);
+        } else {
+            r.ids_bias = make_double2(__longlong_as_double((long long)(((uint64_t)b << 32) | a)), bias);
+            r.lev = make_double2(l.x, l.y);
+            r.nxy = make_double2(g.x, g.y);
+            r.nz_ = make_double2(g.z, 0.0);
+        }
+        rec[s] = r;
+        double pn = 0.0, pt = 0.0, po = 0.0;
+        if (warm) {
+            const uint32_t e = prev_row_off[a + 1];
+            for (uint32_t t = prev_row_off[a]; t < e; ++t) {
+                if (prev_j2[t] != b) continue;
+                const double4_32a P = prev_P[t];
+                double tx, ty, tz, ox, oy, oz;
+                tangent_basis<double>(g.x, g.y, g.z, tx, ty, tz, ox, oy, oz);
+                pn = g.x * P.x + g.y * P.y + g.z * P.z;
+                if (!(pn > 0.0)) pn = 0.0;
+                pt = tx * P.x + ty * P.y + tz * P.z;
+                po = ox * P.x + oy * P.y + oz * P.z;
+                const double lim = mu * pn, len = sqrt(pt * pt + po * po);
+                if (len > lim) {
+                    if (len > 0.0) {
+                        pt *= lim / len;
+                        po *= lim / len;
+                    } else {
+                        pt = po = 0.0;
+                    }
+                }
+                break;
+            }
+        }
+        R4<R> q;
+        q.x = (R)pn;
+        q.y = (R)pt;
+        q.z = (R)po;
+        q.w = (R)0;
+        p[s] = q;
+    }
+}
+
+nbgs_status run_colour(nbgs_scene* s)
+{
+    if (!s->detected) return fail(s, NBGS_EINVAL, "colour_contacts: call detect_contacts first");
+    cudaStream_t st = s->stream;
+    const int64_t C = s->n_contacts, n = s->n;
+    if (s->timing) cudaEventRecord(s->ev[2], st);
+    cudaMemsetAsync(s->col_count, 0, (kMaxColours + 1) * sizeof(uint32_t), st);
+    cudaMemsetAsync(&s->info->n_colours, 0, sizeof(uint32_t), st);
+    if (C > 0) {
+        const int T = 256;
+        const int gb = grid_for(C, T, 8, s->num_sms);
+        cudaMemsetAsync(s->deg, 0, (n + 1) * sizeof(uint32_t), st);
+        k_colour_init<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->prm.colour_seed, s->deg, s->cprio,
+                                        s->cstate, s->wl[0]);
+        nbgs_status rc = exclusive_scan_u32(s, s->deg, s->adj_off, n, nullptr);
+        if (rc != NBGS_OK) return rc;
+        cudaMemsetAsync(s->deg, 0, (n + 1) * sizeof(uint32_t), st);
+        k_adj_fill<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->deg, s->adj);
+        if (s->timing) s->phase_launches[1] += 5;
+        // Jones-Plassmann rounds; the host checks the worklist every few rounds
+        const uint32_t c32 = (uint32_t)C;
+        cudaMemcpyAsync(&s->info->wl_count[0], &c32, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+        uint32_t round = 0;
+        int cur = 0;
+        for (int batch = 0; batch < 64; ++batch) {
+            for (int r = 0; r < 6; ++r) {
+                ++round;
+                cudaMemsetAsync(&s->info->wl_count[1 - cur], 0, sizeof(uint32_t), st);
+                k_jp_round<<<gb, T, 0, st>>>(round, n, s->wl[cur], &s->info->wl_count[cur], s->wl[1 - cur],
+                                             &s->info->wl_count[1 - cur], s->cj1, s->cj2, s->finite, s->adj_off,
+                                             s->adj, s->cprio, s->cstate, s->info);
+                cur = 1 - cur;
+            }
+            if (s->timing) s->phase_launches[1] += 6;
+            uint32_t left = 0;
+            rc = cuda_check(s, cudaMemcpyAsync(&left, &s->info->wl_count[cur], sizeof(uint32_t),
+                                               cudaMemcpyDeviceToHost, st), "colour: worklist");
+            if (rc != NBGS_OK) return rc;
+            rc = cuda_check(s, cudaStreamSynchronize(st), "colour");
+            if (rc != NBGS_OK) return rc;
+            if (left == 0) break;
+            if (batch == 63) return fail(s, NBGS_ETIMEOUT, "colour: Jones-Plassmann did not finish in 384 rounds");
+        }
+        k_colour_keys<<<gb, T, 0, st>>>(C, s->cstate, s->colour_key, s->perm_in, s->col_count, s->info);
+        k_colour_offsets<<<1, 32, 0, st>>>(s->col_count, s->col_off);
+        // stable counting sort by colour (one 8-bit radix pass): contacts of a
+        // colour stay in canonical order
+        uint32_t *k0 = s->colour_key, *k1 = s->colour_key2, *v0 = s->perm_in, *v1 = s->perm;
+        rc = radix_sort_pairs(s, k0, v0, k1, v1, C, 8);
+        if (rc != NBGS_OK) return rc;
+        // radix_sort_pairs swapped the pointers: v0 now holds the sorted values
+        if (v0 != s->perm) std::swap(s->perm, s->perm_in);
+        if (v0 != s->perm) return fail(s, NBGS_EINVAL, "colour: permutation buffer mix-up");
+        const int warm = (s->prm.warm_start == NBGS_WARM_PREV && s->have_prev) ? 1 : 0;
+        if (s->fp32)
+            k_build_sweep<float><<<gb, T, 0, st>>>(C, n, s->perm, s->cj1, s->cj2, s->cgeo, s->clev, s->prm.dt,
+                                                   s->prm.beta, s->prm.mu, warm, s->prev_row_off, s->prev_j2,
+                                                   s->prev_P, (SweepRec<float>*)s->srec, (float4*)s->sp);
+        else
+            k_build_sweep<double><<<gb, T, 0, st>>>(C, n, s->perm, s->cj1, s->cj2, s->cgeo, s->clev, s->prm.dt,
+                                                    s->prm.beta, s->prm.mu, warm, s->prev_row_off, s->prev_j2,
+                                                    s->prev_P, (SweepRec<double>*)s->srec, (double4_32a*)s->sp);
+        if (s->timing) s->phase_launches[1] += 3;
+        s->n_colours = -1;  // known on the device; read lazily
+    } else {
+        s->n_colours = 0;
+    }
+    if (s->timing) cudaEventRecord(s->ev[3], st);
+    s->coloured = true;
+    return cuda_check(s, cudaGetLastError(), "colour");
+}
+
+}  // namespace nbgs

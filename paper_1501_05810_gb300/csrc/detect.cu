@@ -1,0 +1,613 @@
+// detect.cu -- contact detection (Sect. 4) on a uniform cell grid.
+//
+// Per step:
+//   k_hull          h_i = dt(|v_i| + |w_i| r_i) + tau       eq. (expansionradius)
+//                   + max h, max |v| (for the cell size and v_ref)
+//   k_grid_setup    cell width >= 2 (r_max + h_max), dims per axis
+//   k_cell_keys     linear cell index of every body
+//   radix sort      (cell, body) pairs, LSD, 8-bit digits, stable
+//   k_cell_ranges   [start, end) of every occupied cell
+//   k_narrow        per body i: bodies j > i in the 27 neighbour cells whose
+//                   hulls intersect, sorted by j; wall hull tests
+//   scan            contacts per body -> CSR offsets by j1
+//   k_write         canonical contact records (n, xi, lever lengths)
+//                   for sphere-sphere and sphere-wall pairs, eq. (contactpos)
+#include <utility>
+
+#include "nbgs_internal.cuh"
+
+namespace nbgs {
+
+int grid_for(int64_t work, int threads, int max_blocks_per_sm, int num_sms)
+{
+    int64_t b = (work + threads - 1) / threads;
+    int64_t cap = (int64_t)max_blocks_per_sm * (num_sms > 0 ? num_sms : 1);
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of u32 (reduce -> scan block sums -> downsweep)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// Exclusive block scan of one value per thread; returns the block total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& excl)
+{
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t block_tot;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    uint32_t inc = warp_incl_scan(v);
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = lane < nw ? warp_tot[lane] : 0;
+        uint32_t ti = warp_incl_scan(t);
+        if (lane < nw) warp_tot[lane] = ti - t;
+        if (lane == nw - 1) block_tot = ti;
+    }
+    __syncthreads();
+    excl = warp_tot[wid] + inc - v;
+    uint32_t total = block_tot;
+    __syncthreads();
+    return total;
+}
+
+__global__ void k_scan_reduce(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) acc += in[i];
+    }
+    uint32_t excl;
+    uint32_t tot = block_excl_scan(acc, excl);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(uint32_t* sums, int64_t nb)
+{
+    // single block: exclusive scan of the block sums in chunks
+    uint32_t carry = 0;
+    for (int64_t base = 0; base < nb; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        uint32_t v = i < nb ? sums[i] : 0;
+        uint32_t excl;
+        uint32_t tot = block_excl_scan(v, excl);
+        if (i < nb) sums[i] = carry + excl;
+        carry += tot;
+    }
+}
+
+__global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
+                            const uint32_t* __restrict__ sums, uint32_t* __restrict__ total_dst)
+{
+    __shared__ uint32_t tile[kScanTile];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        tile[k * kScanThreads + threadIdx.x] = i < n ? in[i] : 0;
+    }
+    __syncthreads();
+    uint32_t loc[kScanItems];
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        loc[k] = acc;
+        acc += tile[threadIdx.x * kScanItems + k];
+    }
+    uint32_t excl;
+    uint32_t tot = block_excl_scan(acc, excl);
+    const uint32_t off = sums[blockIdx.x] + excl;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) tile[threadIdx.x * kScanItems + k] = loc[k] + off;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) out[i] = tile[k * kScanThreads + threadIdx.x];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        uint32_t total = sums[blockIdx.x] + tot;
+        out[n] = total;
+        if (total_dst) *total_dst = total;
+    }
+}
+
+// out must hold n + 1 entries; out[n] receives the total (also *total_dst).
+nbgs_status exclusive_scan_u32(nbgs_scene* s, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dst)
+{
+    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb < 1) nb = 1;
+    if (nb > s->scan_tmp_len) return fail(s, NBGS_EINVAL, "scan: block-sum buffer too small");
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s->stream>>>(in, n, s->scan_tmp);
+    k_scan_top<<<1, 1024, 0, s->stream>>>(s->scan_tmp, nb);
+    k_scan_down<<<(unsigned)nb, kScanThreads, 0, s->stream>>>(in, out, n, s->scan_tmp, total_dst);
+    return cuda_check(s, cudaGetLastError(), "scan");
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort of (key, value) u32 pairs: 8-bit digits, one pass =
+// per-tile digit histogram -> scan (digit-major) -> stable scatter with
+// warp-level ranking (__match_any_sync), so equal keys keep input order.
+// ---------------------------------------------------------------------------
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;   // 4096
+constexpr int kWarps = kRadixThreads / 32;
+
+__global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist,
+                             int64_t nblocks)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+#pragma unroll 4
+    for (int k = 0; k < kRadixItems; ++k) {
+        int64_t i = base + (int64_t)k * kRadixThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+                uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist_scan,
+                int64_t nblocks)
+{
+    __shared__ uint32_t cnt[kWarps][256];
+    __shared__ uint32_t goff[256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < 256; d += kRadixThreads) {
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) cnt[ww][d] = 0;
+        goff[d] = hist_scan[(int64_t)d * nblocks + blockIdx.x];
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile + (int64_t)w * (kRadixItems * 32);
+    uint32_t key[kRadixItems], val[kRadixItems], rank[kRadixItems];
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        const bool valid = i < n;
+        key[r] = valid ? kin[i] : 0u;
+        val[r] = valid ? vin[i] : 0u;
+        const uint32_t d = (key[r] >> shift) & 255u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u);
+        const uint32_t before = cnt[w][d & 255u];
+        __syncwarp();
+        if (valid && (peers & lt) == 0) cnt[w][d] = before + __popc(peers);
+        __syncwarp();
+        rank[r] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    // exclusive prefix of each digit over the warps (warp order = input order)
+    for (int d = threadIdx.x; d < 256; d += kRadixThreads) {
+        uint32_t sum = 0;
+#pragma unroll
+        for (int ww = 0; ww < kWarps; ++ww) {
+            uint32_t t = cnt[ww][d];
+            cnt[ww][d] = sum;
+            sum += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        if (i < n) {
+            const uint32_t d = (key[r] >> shift) & 255u;
+            const uint32_t pos = goff[d] + cnt[w][d] + rank[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
+        }
+    }
+}
+
+nbgs_status radix_sort_pairs(nbgs_scene* s, uint32_t*& keys, uint32_t*& vals, uint32_t*& keys_alt,
+                             uint32_t*& vals_alt, int64_t n, int bits)
+{
+    if (n <= 1) return NBGS_OK;
+    const int64_t nb = (n + kRadixTile - 1) / kRadixTile;
+    if (256 * nb > s->radix_hist_len) return fail(s, NBGS_EINVAL, "radix sort: histogram buffer too small");
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_radix_hist<<<(unsigned)nb, kRadixThreads, 0, s->stream>>>(keys, n, shift, s->radix_hist, nb);
+        nbgs_status st = exclusive_scan_u32(s, s->radix_hist, s->radix_hist, 256 * nb, nullptr);
+        if (st != NBGS_OK) return st;
+        k_radix_scatter<<<(unsigned)nb, kRadixThreads, 0, s->stream>>>(keys, vals, keys_alt, vals_alt, n, shift,
+                                                                       s->radix_hist, nb);
+        uint32_t* t = keys;
+        keys = keys_alt;
+        keys_alt = t;
+        t = vals;
+        vals = vals_alt;
+        vals_alt = t;
+        if (s->timing) s->phase_launches[0] += 4;
+    }
+    return cuda_check(s, cudaGetLastError(), "radix sort");
+}
+
+// ---------------------------------------------------------------------------
+// detection kernels
+// ---------------------------------------------------------------------------
+struct GridArgs {
+    double lo[3], hi[3];
+    int periodic[3];
+    int dims_max[3];
+    double r_max, dt, tau;
+};
+
+__device__ __forceinline__ double norm_exact(double x, double y, double z)
+{
+    return xsqrt(xadd(xadd(xmul(x, x), xmul(y, y)), xmul(z, z)));
+}
+
+template <class R>
+__global__ void k_hull(int64_t n, const R4<R>* __restrict__ vel, const double4_32a* __restrict__ pos_r, double dt,
+                       double tau, double* __restrict__ hull, DevInfo* info)
+{
+    double hmax = 0.0, vmax = 0.0;
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const R4<R> v = vel[2 * i], w = vel[2 * i + 1];
+        const double r = pos_r[i].w;
+        const double nv = norm_exact((double)v.x, (double)v.y, (double)v.z);
+        const double nw = norm_exact((double)w.x, (double)w.y, (double)w.z);
+        // eq. (expansionradius): h = dt (|v| + |w| r) + tau
+        const double h = xadd(xmul(dt, xadd(nv, xmul(nw, r))), tau);
+        hull[i] = h;
+        if (!(h <= 1e300)) bad = true;
+        hmax = fmax(hmax, h);
+        vmax = fmax(vmax, nv);
+    }
+    // block max, then one atomic per block (non-negative doubles order like their bits)
+    __shared__ double sh[2][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        hmax = fmax(hmax, __shfl_down_sync(0xffffffffu, hmax, o));
+        vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
+    }
+    if (lane == 0) {
+        sh[0][wid] = hmax;
+        sh[1][wid] = vmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            hmax = fmax(hmax, sh[0][k]);
+            vmax = fmax(vmax, sh[1][k]);
+        }
+        atomicMax(&info->hmax_bits, (unsigned long long)__double_as_longlong(hmax));
+        atomicMax(&info->vmax_bits, (unsigned long long)__double_as_longlong(vmax));
+    }
+    if (bad) atomicOr(&info->err, kErrNaN);
+}
+
+__global__ void k_grid_setup(GridArgs g, DevInfo* info)
+{
+    const double hmax = __longlong_as_double((long long)info->hmax_bits);
+    // any kept pair has d <= r_a + r_b + h_a + h_b <= 2 (r_max + h_max)
+    const double need = 2.0 * (g.r_max + hmax) * (1.0 + 1e-9) + 1e-300;
+    uint32_t ncells = 1;
+    for (int a = 0; a < 3; ++a) {
+        const double L = g.hi[a] - g.lo[a];
+        double dd = floor(L / need);
+        int d = dd < 1.0 ? 1 : (dd > (double)g.dims_max[a] ? g.dims_max[a] : (int)dd);
+        if (g.periodic[a] && d < 3) atomicOr(&info->err, kErrGrid);
+        info->dims[a] = d;
+        info->cell_w[a] = L / d;
+        ncells *= (uint32_t)d;
+    }
+    info->ncells = ncells;
+}
+
+__global__ void k_clear_cells(uint32_t* __restrict__ cs, uint32_t* __restrict__ ce, const DevInfo* info)
+{
+    const uint32_t nc = info->ncells;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
+        cs[i] = 0;
+        ce[i] = 0;
+    }
+}
+
+__device__ __forceinline__ int cell_coord(double x, double lo, double w, int d)
+{
+    double f = floor((x - lo) / w);
+    int c = f < 0.0 ? 0 : (f > (double)(d - 1) ? d - 1 : (int)f);
+    return c;
+}
+
+__global__ void k_cell_keys(int64_t n, const double4_32a* __restrict__ pos_r, GridArgs g, const DevInfo* __restrict__ info,
+                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    const int d0 = info->dims[0], d1 = info->dims[1], d2 = info->dims[2];
+    const double w0 = info->cell_w[0], w1 = info->cell_w[1], w2 = info->cell_w[2];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double4_32a p = pos_r[i];
+        const int cx = cell_coord(p.x, g.lo[0], w0, d0);
+        const int cy = cell_coord(p.y, g.lo[1], w1, d1);
+        const int cz = cell_coord(p.z, g.lo[2], w2, d2);
+        keys[i] = ((uint32_t)cz * (uint32_t)d1 + (uint32_t)cy) * (uint32_t)d0 + (uint32_t)cx;
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void k_cell_ranges(int64_t n, const uint32_t* __restrict__ keys, uint32_t* __restrict__ cs,
+                              uint32_t* __restrict__ ce)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = keys[s];
+        if (s == 0 || keys[s - 1] != k) cs[k] = (uint32_t)s;
+        if (s == n - 1 || keys[s + 1] != k) ce[k] = (uint32_t)(s + 1);
+    }
+}
+
+// Minimum-image difference a - b along one axis (periodic: |d| <= L/2).
+__device__ __forceinline__ double min_image(double d, int periodic, double L)
+{
+    if (periodic) {
+        const double half = xmul(0.5, L);
+        if (d > half) d = xsub(d, L);
+        else if (d < -half) d = xadd(d, L);
+    }
+    return d;
+}
+
+__device__ __forceinline__ bool wall_kept(const Planes& P, int k, double4_32a p, double h, double tau, double& sd, double& xi)
+{
+    sd = xsub(xadd(xadd(xmul(P.n[k][0], p.x), xmul(P.n[k][1], p.y)), xmul(P.n[k][2], p.z)), P.c[k]);
+    xi = xsub(sd, p.w);
+    return xi <= xadd(h, tau);
+}
+
+// Per body i (visited in cell order for locality): hull-intersecting
+// partners j > i from the 27 neighbour cells, sorted ascending; wall count.
+__global__ void __launch_bounds__(128)
+k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ svals,
+         const double4_32a* __restrict__ pos_r, const double* __restrict__ hull, const uint32_t* __restrict__ cs,
+         const uint32_t* __restrict__ ce, GridArgs g, Planes planes, DevInfo* info, uint32_t* __restrict__ cand,
+         uint32_t* __restrict__ sph_cnt, uint32_t* __restrict__ row_cnt)
+{
+    const int d0 = info->dims[0], d1 = info->dims[1], d2 = info->dims[2];
+    const double L0 = g.hi[0] - g.lo[0], L1 = g.hi[1] - g.lo[1], L2 = g.hi[2] - g.lo[2];
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = svals[s];
+        const uint32_t key = skeys[s];
+        const int cx = (int)(key % (uint32_t)d0);
+        const int cy = (int)((key / (uint32_t)d0) % (uint32_t)d1);
+        const int cz = (int)(key / ((uint32_t)d0 * (uint32_t)d1));
+        const double4_32a pi = pos_r[i];
+        const double hi_ = hull[i];
+        uint32_t list[kCandCap];
+        int cnt = 0;
+        for (int dz = -1; dz <= 1; ++dz) {
+            int z = cz + dz;
+            if (z < 0 || z >= d2) {
+                if (!g.periodic[2] || d2 < 3) continue;
+                z = (z + d2) % d2;
+            }
+            for (int dy = -1; dy <= 1; ++dy) {
+                int y = cy + dy;
+                if (y < 0 || y >= d1) {
+                    if (!g.periodic[1] || d1 < 3) continue;
+                    y = (y + d1) % d1;
+                }
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int x = cx + dx;
+                    if (x < 0 || x >= d0) {
+                        if (!g.periodic[0] || d0 < 3) continue;
+                        x = (x + d0) % d0;
+                    }
+                    const uint32_t c = ((uint32_t)z * (uint32_t)d1 + (uint32_t)y) * (uint32_t)d0 + (uint32_t)x;
+                    const uint32_t e = ce[c];
+                    for (uint32_t t = cs[c]; t < e; ++t) {
+                        const uint32_t j = svals[t];
+                        if (j <= i) continue;
+                        const double4_32a pj = pos_r[j];
+                        const double dx3 = min_image(xsub(pi.x, pj.x), g.periodic[0], L0);
+                        const double dy3 = min_image(xsub(pi.y, pj.y), g.periodic[1], L1);
+                        const double dz3 = min_image(xsub(pi.z, pj.z), g.periodic[2], L2);
+                        const double d = norm_exact(dx3, dy3, dz3);
+                        // Sect. 4: keep the pair iff the hulls intersect
+                        if (xsub(xsub(d, pi.w), pj.w) <= xadd(hi_, hull[j])) {
+                            if (cnt < kCandCap) {
+                                // insertion keeps the list sorted by j
+                                int k = cnt;
+                                while (k > 0 && list[k - 1] > j) {
+                                    list[k] = list[k - 1];
+                                    --k;
+                                }
+                                list[k] = j;
+                            }
+                            ++cnt;
+                        }
+                    }
+                }
+            }
+        }
+        if (cnt > kCandCap) {
+            atomicOr(&info->err, kErrCand);
+            atomicMax(&info->cand_need, (uint32_t)cnt);
+            cnt = kCandCap;
+        }
+        uint32_t* out = cand + (int64_t)i * kCandCap;
+        for (int k = 0; k < cnt; ++k) out[k] = list[k];
+        int wcnt = 0;
+        for (int k = 0; k < planes.count; ++k) {
+            double sd, xi;
+            if (wall_kept(planes, k, pi, hi_, g.tau, sd, xi)) ++wcnt;
+        }
+        sph_cnt[i] = (uint32_t)cnt;
+        row_cnt[i] = (uint32_t)(cnt + wcnt);
+    }
+}
+
+// Canonical contact records: row i of the CSR holds (i, j) for the sorted
+// partners j, then the walls in the order they were added.
+__global__ void k_write_contacts(int64_t n, int64_t ccap, const uint32_t* __restrict__ svals,
+                                 const double4_32a* __restrict__ pos_r, const double* __restrict__ hull,
+                                 const uint32_t* __restrict__ cand, const uint32_t* __restrict__ sph_cnt,
+                                 const uint32_t* __restrict__ row_off, GridArgs g, Planes planes,
+                                 uint32_t* __restrict__ cj1, uint32_t* __restrict__ cj2, double4_32a* __restrict__ cgeo,
+                                 double2* __restrict__ clev)
+{
+    const double L0 = g.hi[0] - g.lo[0], L1 = g.hi[1] - g.lo[1], L2 = g.hi[2] - g.lo[2];
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = svals[s];
+        const double4_32a pi = pos_r[i];
+        int64_t idx = row_off[i];
+        const uint32_t ns = sph_cnt[i];
+        const uint32_t* lst = cand + (int64_t)i * kCandCap;
+        for (uint32_t k = 0; k < ns; ++k, ++idx) {
+            const uint32_t j = lst[k];
+            if (idx >= ccap) continue;
+            const double4_32a pj = pos_r[j];
+            const double dx3 = min_image(xsub(pi.x, pj.x), g.periodic[0], L0);
+            const double dy3 = min_image(xsub(pi.y, pj.y), g.periodic[1], L1);
+            const double dz3 = min_image(xsub(pi.z, pj.z), g.periodic[2], L2);
+            const double d = norm_exact(dx3, dy3, dz3);
+            double4_32a geo;
+            // eq. (contactpos) for spheres: n = (x_i - x_j)/d, the outward
+            // normal of S_j at its point closest to x_i; xi = d - r_i - r_j
+            if (d > 0.0) {
+                geo.x = xdiv(dx3, d);
+                geo.y = xdiv(dy3, d);
+                geo.z = xdiv(dz3, d);
+            } else {
+                geo.x = 0.0;
+                geo.y = 0.0;
+                geo.z = 1.0;
+            }
+            geo.w = xsub(xsub(d, pi.w), pj.w);
+            cj1[idx] = i;
+            cj2[idx] = j;
+            cgeo[idx] = geo;
+            clev[idx] = make_double2(xsub(d, pj.w), pj.w);
+        }
+        const double hi_ = hull[i];
+        for (int k = 0; k < planes.count; ++k) {
+            double sd, xi;
+            if (!wall_kept(planes, k, pi, hi_, g.tau, sd, xi)) continue;
+            if (idx < ccap) {
+                cj1[idx] = i;
+                cj2[idx] = (uint32_t)(n + k);
+                cgeo[idx] = make_double4_32a(planes.n[k][0], planes.n[k][1], planes.n[k][2], xi);
+                clev[idx] = make_double2(sd, 0.0);
+            }
+            ++idx;
+        }
+    }
+}
+
+static GridArgs grid_args(const nbgs_scene* s)
+{
+    GridArgs g;
+    for (int a = 0; a < 3; ++a) {
+        g.lo[a] = s->prm.box_lo[a];
+        g.hi[a] = s->prm.box_hi[a];
+        g.periodic[a] = s->prm.periodic[a];
+        g.dims_max[a] = s->dims_max[a];
+    }
+    g.r_max = s->r_max;
+    g.dt = s->prm.dt;
+    g.tau = s->prm.tau;
+    return g;
+}
+
+nbgs_status grow_contacts(nbgs_scene* s, int64_t need);  // api.cu
+
+nbgs_status run_detect(nbgs_scene* s)
+{
+    const int64_t n = s->n;
+    cudaStream_t st = s->stream;
+    if (s->timing) cudaEventRecord(s->ev[0], st);
+    // keep the previous step's contacts for the warm start
+    if (s->prm.warm_start == NBGS_WARM_PREV && s->solved) {
+        std::swap(s->row_off, s->prev_row_off);
+        std::swap(s->cj2, s->prev_j2);
+        std::swap(s->cworld, s->prev_P);
+        s->prev_count = s->n_contacts;
+        s->have_prev = true;
+    } else {
+        s->have_prev = false;
+    }
+    s->detected = s->coloured = s->solved = false;
+    s->n_contacts = 0;
+    cudaMemsetAsync(s->info, 0, offsetof(DevInfo, cell_w), st);   // hmax, vmax
+    cudaMemsetAsync(&s->info->n_contacts, 0, sizeof(uint32_t), st);
+    if (n == 0) {
+        cudaMemsetAsync(s->row_off, 0, sizeof(uint32_t), st);
+        s->detected = true;
+        return cuda_check(s, cudaGetLastError(), "detect");
+    }
+    const GridArgs g = grid_args(s);
+    const int T = 256;
+    const int gb = grid_for(n, T, 8, s->num_sms);
+    if (s->fp32)
+        k_hull<float><<<gb, T, 0, st>>>(n, (const float4*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hull, s->info);
+    else
+        k_hull<double><<<gb, T, 0, st>>>(n, (const double4_32a*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hull, s->info);
+    k_grid_setup<<<1, 1, 0, st>>>(g, s->info);
+    k_clear_cells<<<grid_for(s->max_cells, T, 8, s->num_sms), T, 0, st>>>(s->cell_start, s->cell_end, s->info);
+    k_cell_keys<<<gb, T, 0, st>>>(n, s->pos_r, g, s->info, s->keys[0], s->vals[0]);
+    if (s->timing) s->phase_launches[0] += 4;
+    nbgs_status rc = radix_sort_pairs(s, s->keys[0], s->vals[0], s->keys[1], s->vals[1], n, s->key_bits);
+    if (rc != NBGS_OK) return rc;
+    k_cell_ranges<<<gb, T, 0, st>>>(n, s->keys[0], s->cell_start, s->cell_end);
+    k_narrow<<<grid_for(n, 128, 16, s->num_sms), 128, 0, st>>>(n, s->keys[0], s->vals[0], s->pos_r, s->hull,
+                                                                 s->cell_start, s->cell_end, g, s->planes, s->info,
+                                                                 s->cand, s->sph_cnt, s->row_cnt);
+    rc = exclusive_scan_u32(s, s->row_cnt, s->row_off, n, &s->info->n_contacts);
+    if (rc != NBGS_OK) return rc;
+    if (s->timing) s->phase_launches[0] += 5;
+    // one synchronisation per step: the contact count sizes everything after
+    rc = cuda_check(s, cudaMemcpyAsync(s->hinfo, s->info, offsetof(DevInfo, rk_bits), cudaMemcpyDeviceToHost, st),
+                    "detect: read info");
+    if (rc != NBGS_OK) return rc;
+    rc = cuda_check(s, cudaStreamSynchronize(st), "detect");
+    if (rc != NBGS_OK) return rc;
+    const DevInfo& hi = *s->hinfo;
+    if (hi.err & kErrNaN) return fail(s, NBGS_ENAN, "detect: NaN or Inf in the velocities");
+    if (hi.err & kErrGrid) return fail(s, NBGS_EINVAL, "detect: a periodic axis holds fewer than 3 grid cells");
+    if (hi.err & kErrCand)
+        return fail(s, NBGS_ECAPACITY, "detect: a body has " + std::to_string(hi.cand_need) +
+                                           " hull neighbours above it (limit " + std::to_string(kCandCap) + ")");
+    const int64_t nc = hi.n_contacts;
+    if (nc > s->ccap) {
+        rc = grow_contacts(s, nc);
+        if (rc != NBGS_OK) return rc;
+    }
+    k_write_contacts<<<grid_for(n, T, 8, s->num_sms), T, 0, st>>>(n, s->ccap, s->vals[0], s->pos_r, s->hull, s->cand,
+                                                                  s->sph_cnt, s->row_off, g, s->planes, s->cj1,
+                                                                  s->cj2, s->cgeo, s->clev);
+    if (s->timing) {
+        s->phase_launches[0] += 1;
+        cudaEventRecord(s->ev[1], st);
+    }
+    s->n_contacts = nc;
+    s->detected = true;
+    return cuda_check(s, cudaGetLastError(), "detect");
+}
+
+}  // namespace nbgs

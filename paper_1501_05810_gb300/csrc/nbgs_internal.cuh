@@ -1,0 +1,285 @@
+// nbgs_internal.cuh -- shared declarations of the sm_103a NBGS library.
+//
+// Layout in HBM (one scene):
+//   bodies  pos_r  double4_32a[n]  (x, y, z, radius)          -- FP64 always
+//           quat   double4_32a[n]  (w, x, y, z)
+//           vel    R4[2n]      (v, 1/m), (omega, 1/I) adjacent per body:
+//                              32 B per body in FP32 (one sector), 64 B in FP64
+//           hull   double[n]   h_i of this step
+//   grid    cell_start/end u32[max_cells], keys/vals u32[n] x2 (radix sort)
+//   contacts (canonical, CSR by j1): cj1, cj2 u32; cgeo double4_32a (n, xi);
+//           clev double2 (la, lb) with lever arms l_a = -la n, l_b = lb n
+//   sweep   srec SweepRec<R>[C] in colour order; sp R4[C] impulses (p_n, p_t, p_o)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/nbgs.h"
+
+namespace nbgs {
+
+constexpr int kMaxPlanes = 16;
+constexpr int kMaxColours = 128;       // colour bitmask of two u64 words
+constexpr int kCandCap = 32;           // sphere candidates per body with j > i
+constexpr uint32_t kUncoloured = 0xFFFFFFFFu;
+constexpr int kMaxSweepsHist = 4096;   // residual slots: history, 3 rotating, 4 final
+constexpr int kHistKept = kMaxSweepsHist - 8;   // sweeps whose R_k is kept
+
+// Slot of max_j r_j for sweep k: its own slot for the first kHistKept
+// sweeps, then three slots used in rotation (the slot of sweep k + 1 is
+// cleared while sweep k runs; every reader of sweep k - 2 is done by then).
+__host__ __device__ __forceinline__ int rk_slot(int k) { return k < kHistKept ? k : kHistKept + k % 3; }
+
+// device error bits (DevInfo::err)
+enum : uint32_t {
+    kErrCand = 1u,        // more than kCandCap neighbours above i
+    kErrContacts = 2u,    // contact buffer too small
+    kErrColours = 4u,     // more than kMaxColours colours
+    kErrTimeout = 8u,     // a grid barrier wait gave up
+    kErrNaN = 16u,        // NaN / Inf in velocities or positions
+    kErrGrid = 32u        // periodic axis with fewer than 3 cells
+};
+
+struct Planes {
+    int count;
+    double n[kMaxPlanes][3];
+    double c[kMaxPlanes];
+};
+
+// Everything a step's kernels communicate through device memory.
+struct DevInfo {
+    unsigned long long hmax_bits;   // max hull radius (bits of a non-negative double)
+    unsigned long long vmax_bits;   // max |v_i| at the start of the step
+    double cell_w[3];
+    int dims[3];
+    uint32_t ncells;
+    uint32_t n_contacts;
+    uint32_t n_colours;
+    uint32_t err;
+    uint32_t cand_need;              // largest candidate count seen
+    uint32_t sweeps_done;
+    uint32_t wl_count[3];            // colouring worklist sizes (rotating)
+    uint32_t barrier_count;          // grid barrier arrival counter
+    uint32_t barrier_gen;            // grid barrier generation
+    uint32_t rounds;                 // colouring rounds used
+    double residual;                 // R of the last sweep
+    double v_ref;
+    unsigned long long rk_bits[kMaxSweepsHist];  // max_j r_j of sweep k (bits)
+};
+
+// ---------------------------------------------------------------------------
+// FP64 arithmetic with explicit round-to-nearest and no contraction: used
+// wherever a floating-point result decides an integer outcome (which pairs
+// become contacts), so that it rounds exactly as the expression is written.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double xadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double xsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double xdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double xsqrt(double a) { return __dsqrt_rn(a); }
+
+// splitmix64 (Steele, Lea & Flood 2014): Weyl increment, then the mixer.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <class R> struct Vec4;
+template <> struct Vec4<float> { using T = float4; };
+template <> struct Vec4<double> { using T = double4_32a; };
+template <class R> using R4 = typename Vec4<R>::T;
+
+// Tangent basis (t, o) of a unit normal n: Duff et al., "Building an
+// Orthonormal Basis, Revisited", JCGT 6(1) 2017 (branchless form).
+template <class R>
+__device__ __forceinline__ void tangent_basis(R nx, R ny, R nz, R& tx, R& ty, R& tz, R& ox, R& oy, R& oz)
+{
+    const R sign = copysign(R(1), nz);
+    const R a = R(-1) / (sign + nz);
+    const R b = nx * ny * a;
+    tx = R(1) + sign * nx * nx * a;
+    ty = sign * b;
+    tz = -sign * nx;
+    ox = b;
+    oy = sign + ny * ny * a;
+    oz = -ny;
+}
+
+// Sweep record of one contact in colour order: ids, lever lengths, normal and
+// gap term xi'/dt.  32 B in FP32, 64 B in FP64.
+template <class R> struct SweepRec;
+template <> struct __align__(16) SweepRec<float> {
+    float4 a;  // (j1 bits, j2 bits, la, lb)
+    float4 b;  // (nx, ny, nz, bias)
+};
+template <> struct __align__(16) SweepRec<double> {
+    double2 ids_bias;  // (j1 | j2 << 32 bits, bias)
+    double2 lev;       // (la, lb)
+    double2 nxy;       // (nx, ny)
+    double2 nz_;       // (nz, unused)
+};
+
+// Bounded grid-wide barrier for a cooperative launch (all blocks resident).
+// Returns false when the wait ran out (the error bit is set and every block
+// leaves at its next check).  Never spins without a limit.
+__device__ __forceinline__ bool grid_barrier(DevInfo* info, unsigned nblocks)
+{
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        volatile uint32_t* vgen = &info->barrier_gen;
+        volatile uint32_t* verr = &info->err;
+        const uint32_t gen = *vgen;
+        __threadfence();
+        const uint32_t arrived = atomicAdd(&info->barrier_count, 1u);
+        int good = 1;
+        if (arrived == nblocks - 1) {
+            info->barrier_count = 0;
+            __threadfence();
+            atomicAdd(&info->barrier_gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*vgen == gen) {
+                if ((*verr & kErrTimeout) || ++spins > 20000000LL) {  // ~1 s with the sleep below
+                    atomicOr(&info->err, kErrTimeout);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(40);
+            }
+        }
+        __threadfence();
+        ok = good && !(*verr & kErrTimeout);
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+}  // namespace nbgs
+
+// ---------------------------------------------------------------------------
+// Host-side scene
+// ---------------------------------------------------------------------------
+struct nbgs_scene {
+    nbgs_params prm;
+    int64_t n = 0;
+    nbgs::Planes planes{};
+    cudaStream_t stream = nullptr;
+    nbgs_allocator alloc{};
+    bool has_alloc = false;
+    nbgs_status status = NBGS_OK;
+    std::string err;
+    int device = 0;
+    int num_sms = 0;
+    double r_max = 0.0;
+    bool fp32 = false;
+
+    // bodies
+    double4_32a* pos_r = nullptr;
+    double4_32a* quat = nullptr;
+    void* vel = nullptr;          // R4[2n]
+    double* hull = nullptr;
+    uint8_t* finite = nullptr;    // body takes impulses (1/m > 0 or 1/I > 0)
+    double* stage = nullptr;      // 13 n doubles for state transfer
+    // grid
+    int dims_max[3] = {1, 1, 1};
+    int64_t max_cells = 1;
+    int key_bits = 1;
+    uint32_t* cell_start = nullptr;
+    uint32_t* cell_end = nullptr;
+    uint32_t* keys[2] = {nullptr, nullptr};
+    uint32_t* vals[2] = {nullptr, nullptr};
+    uint32_t* radix_hist = nullptr;
+    int64_t radix_hist_len = 0;
+    uint32_t* scan_tmp = nullptr;  // block sums of the scans
+    int64_t scan_tmp_len = 0;
+    // candidates
+    uint32_t* cand = nullptr;      // n * kCandCap
+    uint32_t* sph_cnt = nullptr;   // sphere contacts per body
+    uint32_t* row_cnt = nullptr;   // contacts per body (sphere + wall)
+    uint32_t* row_off = nullptr;   // n + 1
+    // contacts (canonical)
+    int64_t ccap = 0;
+    uint32_t* cj1 = nullptr;
+    uint32_t* cj2 = nullptr;
+    double4_32a* cgeo = nullptr;
+    double2* clev = nullptr;
+    double4_32a* cimp = nullptr;       // canonical (p_n, p_t, p_o, -) after the solve
+    double4_32a* cworld = nullptr;     // canonical world-frame impulse after the solve
+    // warm start: previous step (CSR by j1)
+    uint32_t* prev_row_off = nullptr;
+    uint32_t* prev_j2 = nullptr;
+    double4_32a* prev_P = nullptr;     // world-frame impulse
+    int64_t prev_count = 0;
+    bool have_prev = false;
+    // colouring
+    uint32_t* deg = nullptr;       // n + 1
+    uint32_t* adj_off = nullptr;   // n + 1
+    uint32_t* adj = nullptr;       // 2 ccap
+    uint32_t* cstate = nullptr;    // (round << 8) | colour
+    uint64_t* cprio = nullptr;
+    uint32_t* wl[2] = {nullptr, nullptr};
+    uint32_t* colour_key = nullptr;   // colour per contact (sort key)
+    uint32_t* colour_key2 = nullptr;
+    uint32_t* perm = nullptr;      // sweep slot -> canonical index
+    uint32_t* perm_in = nullptr;
+    uint32_t* col_count = nullptr; // kMaxColours + 1
+    uint32_t* col_off = nullptr;   // kMaxColours + 1
+    // sweep
+    void* srec = nullptr;
+    void* sp = nullptr;
+    // device info
+    nbgs::DevInfo* info = nullptr;
+    nbgs::DevInfo* hinfo = nullptr;   // pinned host copy
+    // state
+    int64_t n_contacts = 0;
+    int32_t n_colours = 0;
+    bool detected = false;
+    bool coloured = false;
+    bool solved = false;
+    int32_t last_sweeps = 0;
+    // timing
+    bool timing = false;
+    cudaEvent_t ev[8] = {};
+    double phase_ms[4] = {0, 0, 0, 0};
+    int64_t phase_launches[4] = {0, 0, 0, 0};
+    int coop_blocks = 0;           // resident blocks of the persistent sweep kernel
+    int coop_threads = 256;
+};
+
+namespace nbgs {
+
+// host helpers (api.cu)
+nbgs_status fail(nbgs_scene* s, nbgs_status st, const std::string& msg);
+nbgs_status cuda_check(nbgs_scene* s, cudaError_t e, const char* what);
+void* dev_alloc(nbgs_scene* s, size_t bytes);
+void dev_free(nbgs_scene* s, void* p);
+
+// phases (detect.cu / colour.cu / solve.cu / integrate.cu)
+nbgs_status run_detect(nbgs_scene* s);
+nbgs_status run_colour(nbgs_scene* s);
+nbgs_status run_solve(nbgs_scene* s, int max_sweeps, double tol);
+nbgs_status run_integrate(nbgs_scene* s);
+nbgs_status run_final_residuals(nbgs_scene* s, nbgs_residuals* out);
+nbgs_status run_set_bodies(nbgs_scene* s, const double* pos, const double* quat, const double* vel,
+                           const double* angvel);
+nbgs_status run_get_bodies(nbgs_scene* s, double* pos, double* quat, double* vel, double* angvel);
+nbgs_status run_set_mass(nbgs_scene* s, const double* invm, const double* invI, bool init,
+                         const double* radius, const double* density);
+nbgs_status run_get_contacts(nbgs_scene* s, int64_t cap, uint32_t* j1, uint32_t* j2, int32_t* colour,
+                             double* normal, double* xi, double* impulse);
+
+// primitives (detect.cu)
+nbgs_status exclusive_scan_u32(nbgs_scene* s, const uint32_t* in, uint32_t* out, int64_t n,
+                               uint32_t* total_dst);
+nbgs_status radix_sort_pairs(nbgs_scene* s, uint32_t*& keys, uint32_t*& vals, uint32_t*& keys_alt,
+                             uint32_t*& vals_alt, int64_t n, int bits);
+int grid_for(int64_t work, int threads, int max_blocks_per_sm, int num_sms);
+
+}  // namespace nbgs
