@@ -175,6 +175,35 @@ nbgs_status nbgs_residual_history(nbgs_scene* scene, double* out, int32_t cap, i
  * velocities and impulses.  Synchronises. */
 nbgs_status nbgs_final_residuals(nbgs_scene* scene, nbgs_residuals* out);
 
+/* Allocation-free variant of nbgs_final_residuals() for callers that cannot
+ * allocate device memory (fixed arenas, plugins handed only buffers,
+ * processes whose allocator belongs to someone else).  The paper has no
+ * counterpart: this entry point only repackages the residual evaluation.
+ *
+ * Inputs are device pointers in the layout nbgs_get_contacts() and
+ * nbgs_get_bodies() produce: j1, j2 (n_contacts; j2 >= n_bodies marks a
+ * wall), normal (n_contacts x 3), xi (n_contacts), impulse (n_contacts x 3,
+ * contact frame), vel and angvel (n_bodies x 3), radius, invm, invI
+ * (n_bodies).  dt, beta, mu and v_ref as in the scene and its step stats.
+ * out: device pointer to 4 doubles, written in nbgs_residuals order.
+ * Enqueued on `stream` (a cudaStream_t, NULL = legacy default stream).
+ *
+ * Scratch is a file-scope device array of 32 KiB held by every GPU that
+ * loads the library until the process exits; no memory is allocated.
+ * n_contacts may not exceed 2,097,152 (NBGS_ECAPACITY otherwise).  The
+ * first call on a device looks up the array's address (cudaGetSymbolAddress)
+ * with that device current: make that first call before any stream capture.
+ * All calls share the array, so calls that overlap on the GPU (different
+ * streams, or different host threads on one device) race and may return
+ * wrong maxima; serialise them.  Returns NBGS_EINVAL on bad arguments and
+ * NBGS_ECUDA if a launch fails. */
+nbgs_status nbgs_final_residuals_noalloc(int64_t n_bodies, int64_t n_contacts, const uint32_t* j1,
+                                         const uint32_t* j2, const double* normal, const double* xi,
+                                         const double* impulse, const double* vel, const double* angvel,
+                                         const double* radius, const double* invm, const double* invI,
+                                         double dt, double beta, double mu, double v_ref, double* out,
+                                         void* stream);
+
 /* Wait for the scene's stream and report device-side errors. */
 nbgs_status nbgs_sync(nbgs_scene* scene);
 

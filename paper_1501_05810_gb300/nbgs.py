@@ -74,6 +74,8 @@ _SIG = {
     "nbgs_sync": [_vp],
     "nbgs_enable_timing": [_vp, C.c_int32],
     "nbgs_get_timings": [_vp, _dp, _i64p],
+    "nbgs_final_residuals_noalloc": [C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                     C.c_double, C.c_double, C.c_double, C.c_double, _vp, _vp],
 }
 for _name, _args in _SIG.items():
     _f = getattr(_lib, _name)
