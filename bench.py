@@ -130,6 +130,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
+def measured_traffic(prec, contacts, sweeps):
+    """DRAM bytes per launch of the sweep kernel from the committed ncu
+    capture (profiles/traffic.json), scaled by the contact updates of one
+    launch; None when the kernel source changed since the capture."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    key = f"k_solve_persistent<{'float' if prec == 'fp32' else 'double'}>"
+    d = json.load(open(p)).get(key)
+    if not d:
+        return None
+    src = b"".join(open(os.path.join(ROOT, "paper_1501_05810_gb300", "csrc", f), "rb").read()
+                   for f in ("solve.cu", "nbgs_internal.cuh"))
+    if hashlib.sha256(src).hexdigest()[:16] != d["source_sha256_16"]:
+        return None
+    return d["dram_bytes_per_update"] * contacts * sweeps
+
+
 def count_contact_kinds(g, n):
     c = g.get_contacts()
     walls = int(np.count_nonzero(c["j2"] >= n))
@@ -269,12 +288,14 @@ def main():
     alg_bytes_per_launch = (n_ss * b_ss + n_sw * b_sw) * statistics.mean(sweeps_done)
     per_launch_ms = solve_ms / max(1, launches["solve"])
     peak, peak_src = read_peaks()
+    traffic = measured_traffic(prec, n_ss + n_sw, statistics.mean(sweeps_done))
     achieved = alg_bytes_per_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": desc, "spheres": n, "contacts": contacts[-1], "sweeps_per_step": sweeps,
+        "config": {"workload": desc, "spheres": n, "contacts": contacts[-1], "colours": stats[-1]["n_colours"],
+                   "sweeps_per_step": sweeps,
                    "tol": tol, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "steps_per_s": args.steps / (t_max / 1e3),
@@ -283,7 +304,7 @@ def main():
         "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
         "gpu_launches": int(sum(launches.values())),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "kernel": f"k_solve_persistent<{'float' if prec == 'fp32' else 'double'}>",
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                      "alg_bytes_per_launch": alg_bytes_per_launch, "launch_ms": per_launch_ms},

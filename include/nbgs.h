@@ -98,7 +98,7 @@ typedef struct nbgs_residuals {  /* maxima over contacts, dimensionless (/ v_ref
     double non_penetration;      /* max(0, -(xi'/dt + u_n))                         */
     double cone;                 /* max(0, |p_to| - mu p_n) w_t                     */
     double complementarity;      /* |min(w_n p_n, xi'/dt + u_n)|                    */
-    double dissipation;          /* | |u_to| p_to + mu p_n u_to | w_t / v_ref       */
+    double dissipation;          /* | |u_to| p_to + mu p_n u_to | w_t / v_ref^2     */
 } nbgs_residuals;
 
 typedef struct nbgs_scene nbgs_scene;
