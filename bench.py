@@ -152,7 +152,8 @@ def measured_traffic(prec, contacts, sweeps):
 def count_contact_kinds(g, n):
     c = g.get_contacts()
     walls = int(np.count_nonzero(c["j2"] >= n))
-    return len(c["j2"]) - walls, walls
+    sizes = np.bincount(c["colour"][c["colour"] >= 0]).tolist() if len(c["colour"]) else []
+    return len(c["j2"]) - walls, walls, sizes
 
 
 def cpu_baseline(steps_budget_s: float = 15.0):
@@ -202,6 +203,7 @@ def main():
     ap.add_argument("--workload", default="dense1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--sweep-flags", type=int, default=None, help="nbgs_params.sweep_flags override")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -219,6 +221,8 @@ def main():
 
     from paper_1501_05810_gb300 import nbgs
     sc, desc = workload(args.workload)
+    if args.sweep_flags is not None:
+        sc["params"]["sweep_flags"] = args.sweep_flags
     prec = sc["params"].get("precision", "fp64")
     n = len(sc["radius"])
     stream = torch.cuda.Stream(device=local)
@@ -228,7 +232,7 @@ def main():
         tol = 0.0 if args.workload == "config1" else TOL
         for _ in range(max(args.warmup, 0)):
             g.step(sweeps, tol)
-        n_ss, n_sw = count_contact_kinds(g, n)
+        n_ss, n_sw, colour_sizes = count_contact_kinds(g, n)
         g.enable_timing(True)
         clocks = ClockSampler(local)
         clocks.start()
@@ -282,11 +286,11 @@ def main():
     sweeps_done = [s["sweeps_done"] for s in stats]
     contacts = [s["n_contacts"] for s in stats]
     solve_ms = phase_ms["solve"]
-    sweep_rate = updates / (solve_ms / 1e3) if solve_ms > 0 else None
+    sweep_rate = updates / (phase_ms["sweep_kernel"] / 1e3) if phase_ms["sweep_kernel"] > 0 else None
     b_ss, b_sw = BYTES[prec]
     # dominant kernel: the persistent sweep kernel, one launch per solve
     alg_bytes_per_launch = (n_ss * b_ss + n_sw * b_sw) * statistics.mean(sweeps_done)
-    per_launch_ms = solve_ms / max(1, launches["solve"])
+    per_launch_ms = phase_ms["sweep_kernel"] / max(1, launches["sweep_kernel"])
     peak, peak_src = read_peaks()
     traffic = measured_traffic(prec, n_ss + n_sw, statistics.mean(sweeps_done))
     achieved = alg_bytes_per_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
@@ -294,7 +298,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": desc, "spheres": n, "contacts": contacts[-1], "colours": stats[-1]["n_colours"],
+        "config": {"workload": desc, "spheres": n, "contacts": contacts[-1], "colours": stats[-1]["n_colours"], "colour_sizes": colour_sizes,
                    "sweeps_per_step": sweeps,
                    "tol": tol, "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -302,7 +306,7 @@ def main():
         "sweep_updates_per_s": sweep_rate,
         "sweeps_done": sweeps_done,
         "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
-        "gpu_launches": int(sum(launches.values())),
+        "gpu_launches": int(sum(v for k, v in launches.items() if k != "sweep_kernel")),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "kernel": f"k_solve_persistent<{'float' if prec == 'fp32' else 'double'}>",

@@ -62,6 +62,13 @@ enum {                                           /* scheduling of the colour swe
     NBGS_SOLVER_PER_COLOUR = 1   /* one launch per colour and sweep                              */
 };
 
+enum {                                           /* nbgs_params.sweep_flags bits (persistent solver) */
+    NBGS_SWEEP_GLOBAL_SYNC = 1,  /* grid barrier after every colour instead of waiting only for the
+                                    blocks whose contacts share bodies with this block's contacts      */
+    NBGS_SWEEP_TMA_STAGE = 2     /* stage each block's chunk of the next colour (records, impulses)
+                                    in shared memory with bulk copies while it waits                   */
+};
+
 typedef struct nbgs_allocator {
     void* ctx;
     void* (*alloc)(void* ctx, size_t bytes, void* stream); /* returns NULL on failure */
@@ -83,7 +90,7 @@ typedef struct nbgs_params {
     int32_t solver;       /* NBGS_SOLVER_*                                          */
     uint64_t colour_seed; /* priorities of the colouring: splitmix64(key ^ seed)    */
     int32_t contacts_per_body; /* contact buffer capacity per body, 0 = default 8   */
-    int32_t reserved;
+    int32_t sweep_flags;  /* NBGS_SWEEP_*: scheduling details of the persistent solver */
 } nbgs_params;
 
 typedef struct nbgs_step_stats {
@@ -209,11 +216,12 @@ nbgs_status nbgs_sync(nbgs_scene* scene);
 
 /* Device time of the phases of the calls since the last reset, measured
  * with CUDA events on the scene stream when timing is enabled:
- * ms[0] detect, ms[1] colour, ms[2] solve (all sweep kernels), ms[3]
- * integrate; launches[0..3] count the kernel launches of each phase.
- * nbgs_get_timings synchronises. */
+ * ms[0] detect, ms[1] colour, ms[2] solve (everything nbgs_solve_nbgs
+ * enqueues), ms[3] integrate, ms[4] the sweep kernels alone (the
+ * persistent launch, or the per-colour launches); launches[k] counts the
+ * kernel launches of each.  nbgs_get_timings synchronises and resets. */
 nbgs_status nbgs_enable_timing(nbgs_scene* scene, int32_t on);
-nbgs_status nbgs_get_timings(nbgs_scene* scene, double ms[4], int64_t launches[4]);
+nbgs_status nbgs_get_timings(nbgs_scene* scene, double ms[5], int64_t launches[5]);
 
 #ifdef __cplusplus
 }

@@ -119,7 +119,7 @@ nbgs_status grow_contacts(nbgs_scene* s, int64_t need)
 static void timing_collect(nbgs_scene* s)
 {
     if (!s->timing) return;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         float ms = 0.f;
         if (cudaEventQuery(s->ev[2 * k + 1]) == cudaSuccess &&
             cudaEventElapsedTime(&ms, s->ev[2 * k], s->ev[2 * k + 1]) == cudaSuccess)
@@ -257,8 +257,15 @@ nbgs_status nbgs_create_scene(const nbgs_params* params, int64_t n, const double
     cudaMemsetAsync(s->cstate, 0xFF, s->ccap * sizeof(uint32_t), s->stream);
     cudaMemsetAsync(s->row_off, 0, (nn + 1) * sizeof(uint32_t), s->stream);
     cudaMemsetAsync(s->prev_row_off, 0, (nn + 1) * sizeof(uint32_t), s->stream);
-    for (int k = 0; k < 8; ++k) cudaEventCreate(&s->ev[k]);
+    for (int k = 0; k < 10; ++k) cudaEventCreate(&s->ev[k]);
     s->coop_blocks = persistent_blocks(s);
+    if (s->coop_blocks > 0) {
+        if (!take(s, s->dep, (size_t)kMaxColours * s->coop_blocks) || !take(s, s->prog, (size_t)s->coop_blocks) ||
+            !take(s, s->cstart, (size_t)kMaxColours * (s->coop_blocks + 1))) {
+            nbgs_destroy_scene(s);
+            return NBGS_ENOMEM;
+        }
+    }
     if (n > 0) {
         // identity quaternions: staged by the unpack kernel
         double* q = (double*)malloc(4 * n * sizeof(double));
@@ -295,12 +302,13 @@ void nbgs_destroy_scene(nbgs_scene* s)
     cudaStreamSynchronize(s->stream);
     void* ps[] = {s->pos_r, s->quat, s->vel, s->hull, s->finite, s->stage, s->cell_start, s->cell_end, s->keys[0],
                   s->keys[1], s->vals[0], s->vals[1], s->radix_hist, s->scan_tmp, s->cand, s->sph_cnt, s->row_cnt,
-                  s->row_off, s->prev_row_off, s->deg, s->adj_off, s->col_count, s->col_off, s->info};
+                  s->row_off, s->prev_row_off, s->deg, s->adj_off, s->col_count, s->col_off, s->info, s->dep,
+                  s->prog, s->cstart};
     for (void* p : ps) dev_free(s, p);
     free_contact_arrays(s);
     cudaStreamSynchronize(s->stream);
     if (s->hinfo) cudaFreeHost(s->hinfo);
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 10; ++k)
         if (s->ev[k]) cudaEventDestroy(s->ev[k]);
     cudaGetLastError();
     delete s;
@@ -400,6 +408,7 @@ nbgs_status nbgs_step(nbgs_scene* s, int32_t max_sweeps, double tol, nbgs_step_s
         timing_fold(s, 1);
         timing_fold(s, 2);
         timing_fold(s, 3);
+        timing_fold(s, 4);
     }
     nbgs_status rc = nbgs_detect_contacts(s, nullptr);
     if (rc == NBGS_OK) rc = run_colour(s);
@@ -477,29 +486,28 @@ nbgs_status nbgs_enable_timing(nbgs_scene* s, int32_t on)
     NBGS_GUARD(s);
     nbgs_status rc = cuda_check(s, cudaStreamSynchronize(s->stream), "enable_timing");
     s->timing = on != 0;
-    for (int k = 0; k < 4; ++k) {
-        s->phase_ms[k] = 0.0;
-        s->phase_launches[k] = 0;
-    }
+    for (int k = 0; k < 5; ++k) s->phase_ms[k] = 0.0;
+    for (int k = 0; k < 4; ++k) s->phase_launches[k] = 0;
+    s->sweep_launches = 0;
     // mark every event pair as empty: record start and end back to back
-    for (int k = 0; k < 8; ++k) cudaEventRecord(s->ev[k], s->stream);
+    for (int k = 0; k < 10; ++k) cudaEventRecord(s->ev[k], s->stream);
     cudaStreamSynchronize(s->stream);
     return rc;
 }
 
-nbgs_status nbgs_get_timings(nbgs_scene* s, double ms[4], int64_t launches[4])
+nbgs_status nbgs_get_timings(nbgs_scene* s, double ms[5], int64_t launches[5])
 {
     NBGS_GUARD(s);
     nbgs_status rc = cuda_check(s, cudaStreamSynchronize(s->stream), "get_timings");
     if (rc != NBGS_OK) return rc;
     timing_collect(s);
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         if (ms) ms[k] = s->phase_ms[k];
-        if (launches) launches[k] = s->phase_launches[k];
+        if (launches) launches[k] = k < 4 ? s->phase_launches[k] : s->sweep_launches;
         s->phase_ms[k] = 0.0;
     }
     // collected pairs must not be folded again
-    for (int k = 0; k < 8; ++k) cudaEventRecord(s->ev[k], s->stream);
+    for (int k = 0; k < 10; ++k) cudaEventRecord(s->ev[k], s->stream);
     cudaStreamSynchronize(s->stream);
     return NBGS_OK;
 }

@@ -267,9 +267,10 @@ nbgs_status run_colour(nbgs_scene* s)
         uint32_t *k0 = s->colour_key, *k1 = s->colour_key2, *v0 = s->perm_in, *v1 = s->perm;
         rc = radix_sort_pairs(s, k0, v0, k1, v1, C, 8);
         if (rc != NBGS_OK) return rc;
-        // radix_sort_pairs swapped the pointers: v0 now holds the sorted values
+        // radix_sort_pairs swapped the pointers: v0 / k0 now hold the sorted values / keys
         if (v0 != s->perm) std::swap(s->perm, s->perm_in);
         if (v0 != s->perm) return fail(s, NBGS_EINVAL, "colour: permutation buffer mix-up");
+        s->colour_sorted = k0;
         const int warm = (s->prm.warm_start == NBGS_WARM_PREV && s->have_prev) ? 1 : 0;
         if (s->fp32)
             k_build_sweep<float><<<gb, T, 0, st>>>(C, n, s->perm, s->cj1, s->cj2, s->cgeo, s->clev, s->prm.dt,

@@ -231,6 +231,10 @@ struct nbgs_scene {
     uint32_t* perm_in = nullptr;
     uint32_t* col_count = nullptr; // kMaxColours + 1
     uint32_t* col_off = nullptr;   // kMaxColours + 1
+    uint32_t* colour_sorted = nullptr;  // colour of each sweep slot (points into colour_key / colour_key2)
+    int2* dep = nullptr;           // kMaxColours x coop_blocks block windows [lo, hi] of each chunk
+    int* prog = nullptr;           // coop_blocks: last sweep phase each block completed
+    uint32_t* cstart = nullptr;    // kMaxColours x (coop_blocks + 1) chunk boundaries
     // sweep
     void* srec = nullptr;
     void* sp = nullptr;
@@ -246,9 +250,10 @@ struct nbgs_scene {
     int32_t last_sweeps = 0;
     // timing
     bool timing = false;
-    cudaEvent_t ev[8] = {};
-    double phase_ms[4] = {0, 0, 0, 0};
+    cudaEvent_t ev[10] = {};            // start/end of detect, colour, solve, integrate, sweep kernels
+    double phase_ms[5] = {0, 0, 0, 0, 0};
     int64_t phase_launches[4] = {0, 0, 0, 0};
+    int64_t sweep_launches = 0;
     int coop_blocks = 0;           // resident blocks of the persistent sweep kernel
     int coop_threads = 256;
 };

@@ -36,6 +36,10 @@ template <class R> struct SolveArgs {
     int max_sweeps;
     double tol;
     int warm;
+    int flags;           // NBGS_SWEEP_* bits
+    int* prog;           // per block: last sweep phase completed (local synchronisation)
+    const int2* dep;     // per (colour, block): window [lo, hi] of blocks sharing bodies with the chunk
+    const uint32_t* cstart;  // per colour, B + 1 chunk boundaries (sweep slots)
 };
 
 template <class R>
@@ -71,33 +75,40 @@ __device__ __forceinline__ void decode<double>(const SweepRec<double>& r, uint32
     nz = r.nz_.x;
 }
 
-template <class R>
-__device__ __forceinline__ void load_rec(const SweepRec<R>* rec, int64_t s, SweepRec<R>& r)
-{
-    r = rec[s];
-}
+// State of the two bodies of a contact, gathered before anything is stored.
+template <class R> struct Bodies {
+    R4<R> va, wa, vb, wb;
+};
 
-// Relax one contact; returns r_j.  apply_only: add the stored impulse p to
-// the bodies (initial impulses of a warm start) instead of relaxing.
-template <class R, bool apply_only>
-__device__ __forceinline__ R relax(const SolveArgs<R>& A, int64_t s)
+template <class R>
+__device__ __forceinline__ void gather(const SolveArgs<R>& A, const SweepRec<R>& rr, Bodies<R>& B)
 {
-    SweepRec<R> rr;
-    load_rec(A.rec, s, rr);
     uint32_t ia, ib;
     R la, lb, nx, ny, nz, bias;
     decode<R>(rr, ia, ib, la, lb, nx, ny, nz, bias);
-    const R4<R> pp = A.p[s];
-    R4<R> va = A.vel[2 * (int64_t)ia], wa = A.vel[2 * (int64_t)ia + 1];
-    const bool dyn_b = ib < (uint32_t)A.n;
-    R4<R> vb, wb;
-    if (dyn_b) {
-        vb = A.vel[2 * (int64_t)ib];
-        wb = A.vel[2 * (int64_t)ib + 1];
+    B.va = A.vel[2 * (int64_t)ia];
+    B.wa = A.vel[2 * (int64_t)ia + 1];
+    if (ib < (uint32_t)A.n) {
+        B.vb = A.vel[2 * (int64_t)ib];
+        B.wb = A.vel[2 * (int64_t)ib + 1];
     } else {
-        vb.x = vb.y = vb.z = vb.w = R(0);
-        wb = vb;
+        B.vb.x = B.vb.y = B.vb.z = B.vb.w = R(0);
+        B.wb = B.vb;
     }
+}
+
+// Relax one contact whose record, impulse and bodies are already loaded;
+// returns r_j.  apply_only: add the stored impulse p to the bodies (initial
+// impulses of a warm start) instead of relaxing.
+template <class R, bool apply_only>
+__device__ __forceinline__ R relax_gathered(const SolveArgs<R>& A, int64_t s, const SweepRec<R>& rr, const R4<R>& pp,
+                                            Bodies<R> B)
+{
+    uint32_t ia, ib;
+    R la, lb, nx, ny, nz, bias;
+    decode<R>(rr, ia, ib, la, lb, nx, ny, nz, bias);
+    R4<R> va = B.va, wa = B.wa, vb = B.vb, wb = B.wb;
+    const bool dyn_b = ib < (uint32_t)A.n;
     const R ima = va.w, iIa = wa.w, imb = vb.w, iIb = wb.w;
     R tx, ty, tz, ox, oy, oz;
     tangent_basis<R>(nx, ny, nz, tx, ty, tz, ox, oy, oz);
@@ -179,6 +190,40 @@ __device__ __forceinline__ R relax(const SolveArgs<R>& A, int64_t s)
     return sqrt(r1 * r1 + r2 * r2 + r3 * r3);
 }
 
+template <class R, bool apply_only>
+__device__ __forceinline__ R relax(const SolveArgs<R>& A, int64_t s)
+{
+    const SweepRec<R> rr = A.rec[s];
+    const R4<R> pp = A.p[s];
+    Bodies<R> B;
+    gather<R>(A, rr, B);
+    return relax_gathered<R, apply_only>(A, s, rr, pp, B);
+}
+
+// Two contacts of one colour: both gathers are issued before either store
+// (they touch disjoint finite bodies, so the order does not matter).
+template <class R, bool apply_only>
+__device__ __forceinline__ R relax_pair(const SolveArgs<R>& A, int64_t s0, int64_t s1)
+{
+    const SweepRec<R> r0 = A.rec[s0];
+    const R4<R> p0 = A.p[s0];
+    SweepRec<R> r1;
+    R4<R> p1;
+    if (s1 >= 0) {
+        r1 = A.rec[s1];
+        p1 = A.p[s1];
+    }
+    Bodies<R> B0, B1;
+    gather<R>(A, r0, B0);
+    if (s1 >= 0) gather<R>(A, r1, B1);
+    R r = relax_gathered<R, apply_only>(A, s0, r0, p0, B0);
+    if (s1 >= 0) {
+        const R q = relax_gathered<R, apply_only>(A, s1, r1, p1, B1);
+        r = q > r ? q : r;
+    }
+    return r;
+}
+
 template <class R>
 __device__ __forceinline__ void gravity_pass(const SolveArgs<R>& A, int64_t gtid, int64_t gstride)
 {
@@ -217,49 +262,423 @@ __device__ __forceinline__ double v_ref_of(const DevInfo* info, double gdt_norm)
     return fmax(v, 1e-12);
 }
 
-// Whole solve in one cooperative launch: gravity, warm-start impulses and
-// the sweeps, with a bounded grid barrier after every colour.
-template <class R>
-__global__ void __launch_bounds__(256) k_solve_persistent(SolveArgs<R> A)
+// ---------------------------------------------------------------------------
+// Whole solve in one cooperative launch: gravity, warm-start impulses and the
+// sweeps.  Block b owns the same contiguous chunk of every colour in every
+// sweep.  The next colour's records and impulses do not depend on the colour
+// being relaxed (records are read-only; a thread's impulses are written only
+// by that thread), so they are loaded before waiting at the grid barrier and
+// only the body gathers remain behind it.
+// ---------------------------------------------------------------------------
+constexpr int kPersistThreads = 256;
+
+// Shared-memory stage of one colour chunk: CAP records and impulses, 48 KiB.
+template <class R> struct Stage {
+    static constexpr int CAP = sizeof(R) == 4 ? 1024 : 512;
+    static constexpr int BYTES = CAP * (int)(sizeof(SweepRec<R>) + sizeof(R4<R>));
+};
+
+// Block b owns, in every colour, the contacts whose canonical index lies in
+// [ceil(b C / B), ceil((b + 1) C / B)): a contiguous range of the colour
+// (the colour sort is stable), balanced by contact count and local in body
+// index, so that a chunk's bodies are touched only by nearby blocks.
+__device__ __forceinline__ void colour_chunk(const uint32_t* cstart, int c, int64_t& b0, int64_t& b1)
 {
+    const uint32_t* row = cstart + (int64_t)c * (gridDim.x + 1);
+    b0 = row[blockIdx.x];
+    b1 = row[blockIdx.x + 1];
+}
+
+// --- TMA bulk copies (global -> shared) completed on an mbarrier -----------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the stage of the given parity; false (timeout bit set)
+// after ~2^31 SM clocks.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevInfo* info)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1LL << 31)) {
+            atomicOr(&info->err, kErrTimeout);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Thread 0 starts the copy of this block's chunk of colour c (its first CAP
+// contacts) into the stage; returns the number of staged contacts.
+template <class R>
+__device__ __forceinline__ int stage_issue(const SolveArgs<R>& A, int c, SweepRec<R>* srec, R4<R>* sp, uint64_t* bar)
+{
+    int64_t b0, b1;
+    colour_chunk(A.cstart, c, b0, b1);
+    const int m = (int)(b1 - b0 < Stage<R>::CAP ? b1 - b0 : Stage<R>::CAP);
+    if (threadIdx.x == 0 && m > 0) {
+        // the impulses were written through the generic proxy
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        const uint32_t br = (uint32_t)(m * sizeof(SweepRec<R>)), bp = (uint32_t)(m * sizeof(R4<R>));
+        mbar_expect_tx(bar, br + bp);
+        bulk_g2s(srec, A.rec + b0, br, bar);
+        bulk_g2s(sp, A.p + b0, bp, bar);
+    }
+    return m;
+}
+
+template <class R, bool apply_only>
+__device__ __forceinline__ R process_colour(const SolveArgs<R>& A, int c, int m, const SweepRec<R>* srec,
+                                            const R4<R>* sp)
+{
+    R rmax = R(0);
+    int64_t b0, b1;
+    colour_chunk(A.cstart, c, b0, b1);
+    const int T = blockDim.x;
+    // staged part: records and impulses from shared memory
+    for (int slot = threadIdx.x; slot < m; slot += T) {
+        const SweepRec<R> r0 = srec[slot];
+        const R4<R> p0 = sp[slot];
+        Bodies<R> B0;
+        gather<R>(A, r0, B0);
+        const R r = relax_gathered<R, apply_only>(A, b0 + slot, r0, p0, B0);
+        rmax = r > rmax ? r : rmax;
+    }
+    // the rest of the chunk straight from global memory
+    for (int64_t s = b0 + m + threadIdx.x; s < b1; s += T) {
+        const R r = relax<R, apply_only>(A, s);
+        rmax = r > rmax ? r : rmax;
+    }
+    return rmax;
+}
+
+// Split grid barrier: arrive (after this block's stores), do independent
+// work, then wait.  The wait gives up after ~2^31 SM clocks (about a
+// second), sets the timeout bit and returns false.
+__device__ __forceinline__ void barrier_arrive(DevInfo* info, unsigned nblocks, uint32_t* s_gen)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t* vgen = &info->barrier_gen;
+        const uint32_t gen = *vgen;
+        __threadfence();
+        const uint32_t arrived = atomicAdd(&info->barrier_count, 1u);
+        if (arrived == nblocks - 1) {
+            info->barrier_count = 0;
+            __threadfence();
+            atomicAdd(&info->barrier_gen, 1u);
+        }
+        *s_gen = gen;
+    }
+}
+
+__device__ __forceinline__ bool barrier_wait(DevInfo* info, const uint32_t* s_gen, int* s_ok)
+{
+    if (threadIdx.x == 0) {
+        volatile uint32_t* vgen = &info->barrier_gen;
+        volatile uint32_t* verr = &info->err;
+        const uint32_t gen = *s_gen;
+        int ok = 1;
+        const long long t0 = clock64();
+        while (*vgen == gen) {
+            if (*verr & kErrTimeout) {
+                ok = 0;
+                break;
+            }
+            if (clock64() - t0 > (1LL << 31)) {
+                atomicOr(&info->err, kErrTimeout);
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+template <class R> struct PersistMinBlocks {
+    static constexpr int value = sizeof(R) == 4 ? 4 : 2;   // FP64 needs more registers per thread
+};
+
+// Wait until every block in this chunk's window has completed sweep phase
+// g - 1 (it and all earlier phases): then every contact of another colour
+// that shares a body with this chunk is settled.  Warp 0 polls the progress
+// words; bounded like every other wait.
+__device__ __forceinline__ bool wait_deps(const int* prog, int2 win, int g, DevInfo* info, int* s_ok)
+{
+    if (threadIdx.x < 32) {
+        int ok = 1;
+        const int nblk = (int)gridDim.x, self = (int)blockIdx.x;
+        for (int off = win.x + (int)threadIdx.x; off <= win.y && ok; off += 32) {
+            if (off == 0) continue;
+            const int b = ((self + off) % nblk + nblk) % nblk;
+            volatile const int* pb = prog + b;
+            const long long t0 = clock64();
+            while (*pb < g - 1) {
+                if (((volatile uint32_t*)&info->err)[0] & kErrTimeout) {
+                    ok = 0;
+                    break;
+                }
+                if (clock64() - t0 > (1LL << 31)) {
+                    atomicOr(&info->err, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok = __all_sync(0xffffffffu, ok);
+        if (threadIdx.x == 0) *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Publish that this block finished sweep phase g (after all its stores).
+__device__ __forceinline__ void publish(int* prog, int g)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(prog + blockIdx.x, g);
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R>::value) k_solve_persistent(SolveArgs<R> A)
+{
+    extern __shared__ __align__(128) unsigned char stage_mem[];
+    SweepRec<R>* srec = reinterpret_cast<SweepRec<R>*>(stage_mem);
+    R4<R>* sp = reinterpret_cast<R4<R>*>(stage_mem + Stage<R>::CAP * sizeof(SweepRec<R>));
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_gen;
+    __shared__ int s_ok;
     const unsigned nb = gridDim.x;
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
     const int ncol = (int)A.info->n_colours;
     const double vref = v_ref_of(A.info, A.gdt_norm);
+    const bool stage = (A.flags & NBGS_SWEEP_TMA_STAGE) != 0;
+    const bool local = (A.flags & NBGS_SWEEP_GLOBAL_SYNC) == 0;
+    if (threadIdx.x == 0) mbar_init(&bar);
     gravity_pass<R>(A, gtid, gstride);
     if (!grid_barrier(A.info, nb)) return;
     if (A.warm) {
         for (int c = 0; c < ncol; ++c) {
-            const int64_t e = A.col_off[c + 1];
-            for (int64_t s = A.col_off[c] + gtid; s < e; s += gstride) relax<R, true>(A, s);
+            process_colour<R, true>(A, c, 0, srec, sp);
             if (!grid_barrier(A.info, nb)) return;
         }
     }
+    uint32_t parity = 0;
+    int m = (stage && ncol > 0) ? stage_issue<R>(A, 0, srec, sp, &bar) : 0;   // a copy is in flight iff m > 0
     int k = 0;
     double Rk = 0.0;
-    for (; k < A.max_sweeps; ++k) {
+    bool ok = true, synced = true;
+    for (; k < A.max_sweeps && ok; ++k) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && k + 1 >= kHistKept) A.info->rk_bits[rk_slot(k + 1)] = 0ull;
         R rmax = R(0);
         for (int c = 0; c < ncol; ++c) {
-            const int64_t e = A.col_off[c + 1];
-            for (int64_t s = A.col_off[c] + gtid; s < e; s += gstride) {
-                const R r = relax<R, false>(A, s);
-                rmax = r > rmax ? r : rmax;
+            const int g = k * ncol + c;
+            if (local && !wait_deps(A.prog, A.dep[c * (int)nb + blockIdx.x], g, A.info, &s_ok)) {
+                ok = false;
+                break;
             }
+            if (m > 0) {
+                if (!mbar_wait(&bar, parity, A.info)) {
+                    ok = false;
+                    break;
+                }
+                parity ^= 1u;
+            }
+            const R r = process_colour<R, false>(A, c, m, srec, sp);
+            rmax = r > rmax ? r : rmax;
             if (c == ncol - 1) block_max_to<R>(rmax, &A.info->rk_bits[rk_slot(k)]);
-            if (!grid_barrier(A.info, nb)) return;
+            const int cn = c + 1 < ncol ? c + 1 : 0;
+            if (local) {
+                publish(A.prog, g);   // its __syncthreads also ends every read of the stage
+                m = stage ? stage_issue<R>(A, cn, srec, sp, &bar) : 0;
+            } else {
+                barrier_arrive(A.info, nb, &s_gen);
+                m = stage ? stage_issue<R>(A, cn, srec, sp, &bar) : 0;
+                if (!barrier_wait(A.info, &s_gen, &s_ok)) {
+                    ok = false;
+                    break;
+                }
+            }
         }
-        Rk = __longlong_as_double((long long)((volatile unsigned long long*)A.info->rk_bits)[rk_slot(k)]) / vref;
-        if (A.tol > 0.0 && Rk <= A.tol) {
-            ++k;
-            break;
+        if (!ok) break;
+        synced = !local;
+        // R_k needs every block's contribution: a grid barrier per sweep when
+        // the tolerance is tested (and near the rotating residual slots)
+        if (local && ncol > 0 && (A.tol > 0.0 || k + 2 >= kHistKept)) {
+            if (!grid_barrier(A.info, nb)) {
+                ok = false;
+                break;
+            }
+            synced = true;
         }
+        if (synced) {
+            Rk = __longlong_as_double((long long)((volatile unsigned long long*)A.info->rk_bits)[rk_slot(k)]) / vref;
+            if (A.tol > 0.0 && Rk <= A.tol) {
+                ++k;
+                break;
+            }
+        }
+    }
+    // never leave with a copy into this block's shared memory in flight
+    if (m > 0) mbar_wait(&bar, parity, A.info);
+    if (!ok) return;
+    if (!synced && k > 0) {
+        if (!grid_barrier(A.info, nb)) return;
+        Rk = __longlong_as_double((long long)((volatile unsigned long long*)A.info->rk_bits)[rk_slot(k - 1)]) / vref;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.info->sweeps_done = (uint32_t)k;
         A.info->residual = Rk;
         A.info->v_ref = vref;
+    }
+}
+
+// --- block windows of the chunks (local synchronisation) -------------------
+// Blocks form a ring.  Body x is mapped to its home block ref(x) = x B / n;
+// the blocks whose chunks (any colour) hold a contact of x are recorded as
+// circular offsets from ref(x) in [-B/2, B/2), so the contacts that close a
+// periodic box (first and last bodies) stay neighbours on the ring.
+__device__ __forceinline__ int ring_off(int64_t d, int nblk)
+{
+    const int64_t h = nblk / 2;
+    return (int)((((d + h) % nblk) + nblk) % nblk - h);
+}
+
+// Block owning canonical contact k: floor(k B / C); home block of body x:
+// the block of its first canonical contact (row_off[x]).
+__device__ __forceinline__ int block_of(int64_t k, int64_t C, int nblk)
+{
+    const int64_t b = (k * nblk) / C;
+    return (int)(b < nblk ? b : nblk - 1);
+}
+
+// Chunk boundaries: cstart[c][b] = first slot of colour c whose canonical
+// index is >= ceil(b C / B) (binary search; perm is increasing in a colour).
+__global__ void k_chunk_starts(int64_t C, int nblk, const uint32_t* __restrict__ col_off,
+                               const uint32_t* __restrict__ perm, const DevInfo* __restrict__ info,
+                               uint32_t* __restrict__ cstart)
+{
+    const int ncol = (int)info->n_colours;
+    const int64_t total = (int64_t)ncol * (nblk + 1);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / (nblk + 1)), b = (int)(t % (nblk + 1));
+        const int64_t target = ((int64_t)b * C + nblk - 1) / nblk;
+        int64_t lo = col_off[c], hi = col_off[c + 1];
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)perm[mid] < target) lo = mid + 1;
+            else hi = mid;
+        }
+        cstart[t] = (uint32_t)lo;
+    }
+}
+
+// Pass 1: per finite body, min and max ring offset (from its home block) of
+// the blocks whose chunks hold a contact of the body.
+__global__ void k_body_blocks(int64_t C, int64_t n, int nblk, const uint32_t* __restrict__ perm,
+                              const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
+                              const uint32_t* __restrict__ row_off, const uint8_t* __restrict__ finite,
+                              int* __restrict__ dmin, int* __restrict__ dmax)
+{
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < C; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = perm[s];
+        const int b = block_of(k, C, nblk);
+        const uint32_t x = cj1[k], y = cj2[k];
+        if (finite[x]) {
+            const int d = ring_off(b - block_of(row_off[x], C, nblk), nblk);
+            atomicMin(&dmin[x], d);
+            atomicMax(&dmax[x], d);
+        }
+        if (y < n && finite[y]) {
+            const int d = ring_off(b - block_of(row_off[y], C, nblk), nblk);
+            atomicMin(&dmin[y], d);
+            atomicMax(&dmax[y], d);
+        }
+    }
+}
+
+// Pass 2: block b computes, for its chunk of every colour, the ring window
+// [lo, hi] (offsets from b) covering every block that touches one of the
+// chunk's bodies.
+__global__ void k_chunk_windows(int64_t C, int64_t n, const uint32_t* __restrict__ cstart,
+                                const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cj1,
+                                const uint32_t* __restrict__ cj2, const uint32_t* __restrict__ row_off,
+                                const uint8_t* __restrict__ finite, const int* __restrict__ dmin,
+                                const int* __restrict__ dmax, const DevInfo* __restrict__ info,
+                                int2* __restrict__ dep)
+{
+    __shared__ int slo[32], shi[32];
+    const int ncol = (int)info->n_colours;
+    const int nblk = gridDim.x;
+    const int self = blockIdx.x;
+    for (int c = 0; c < ncol; ++c) {
+        int64_t b0, b1;
+        colour_chunk(cstart, c, b0, b1);
+        int lo = 0, hi = 0;
+        for (int64_t s = b0 + threadIdx.x; s < b1; s += blockDim.x) {
+            const uint32_t k = perm[s];
+            const uint32_t xs[2] = {cj1[k], cj2[k]};
+            for (int e = 0; e < 2; ++e) {
+                const uint32_t x = xs[e];
+                if (x >= n || !finite[x]) continue;
+                const int l = ring_off((int64_t)block_of(row_off[x], C, nblk) + dmin[x] - self, nblk);
+                lo = min(lo, l);
+                hi = max(hi, l + (dmax[x] - dmin[x]));
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_down_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_down_sync(0xffffffffu, hi, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            slo[threadIdx.x >> 5] = lo;
+            shi[threadIdx.x >> 5] = hi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                lo = min(lo, slo[w]);
+                hi = max(hi, shi[w]);
+            }
+            if (hi - lo >= nblk) {   // the window covers the ring: every block
+                lo = -self;
+                hi = nblk - 1 - self;
+            }
+            dep[c * nblk + self] = make_int2(lo, hi);
+        }
+        __syncthreads();
     }
 }
 
@@ -280,8 +699,9 @@ __global__ void __launch_bounds__(256) k_relax_colour(SolveArgs<R> A, int colour
     if (!apply_only && A.info->sweeps_done != 0xFFFFFFFFu) return;  // converged earlier
     const int64_t b = A.col_off[colour], e = A.col_off[colour + 1];
     R rmax = R(0);
-    for (int64_t s = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < e; s += (int64_t)gridDim.x * blockDim.x) {
-        const R r = relax<R, apply_only>(A, s);
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < e; s += 2 * T) {
+        const R r = relax_pair<R, apply_only>(A, s, s + T < e ? s + T : -1);
         rmax = r > rmax ? r : rmax;
     }
     if (!apply_only) block_max_to<R>(rmax, &A.info->rk_bits[rk_slot(sweep)]);
@@ -337,6 +757,10 @@ static SolveArgs<R> make_args(nbgs_scene* s, int max_sweeps, double tol)
     A.max_sweeps = max_sweeps;
     A.tol = tol;
     A.warm = (s->prm.warm_start == NBGS_WARM_PREV && s->have_prev) ? 1 : 0;
+    A.flags = s->prm.sweep_flags;
+    A.prog = s->prog;
+    A.dep = s->dep;
+    A.cstart = s->cstart;
     return A;
 }
 
@@ -350,10 +774,35 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
     cudaMemsetAsync(&A.info->barrier_count, 0, 2 * sizeof(uint32_t), st);
     const uint32_t not_done = 0xFFFFFFFFu;
     if (s->prm.solver == NBGS_SOLVER_PERSISTENT) {
+        if (A.C > 0) {
+            const int T = 256, B = s->coop_blocks;
+            k_chunk_starts<<<grid_for((int64_t)kMaxColours * (B + 1), T, 8, s->num_sms), T, 0, st>>>(
+                A.C, B, s->col_off, s->perm, s->info, s->cstart);
+            if (s->timing) s->phase_launches[2] += 1;
+            if (!(s->prm.sweep_flags & NBGS_SWEEP_GLOBAL_SYNC)) {
+                int* dmin = (int*)s->deg;      // colouring scratch, free during the solve
+                int* dmax = (int*)s->adj_off;
+                cudaMemsetAsync(dmin, 0x7F, s->n * sizeof(int), st);   // large positive
+                cudaMemsetAsync(dmax, 0x80, s->n * sizeof(int), st);   // large negative
+                k_body_blocks<<<grid_for(A.C, T, 8, s->num_sms), T, 0, st>>>(A.C, s->n, B, s->perm, s->cj1, s->cj2,
+                                                                              s->row_off, s->finite, dmin, dmax);
+                k_chunk_windows<<<B, T, 0, st>>>(A.C, s->n, s->cstart, s->perm, s->cj1, s->cj2, s->row_off,
+                                                  s->finite, dmin, dmax, s->info, s->dep);
+                cudaMemsetAsync(s->prog, 0xFF, B * sizeof(int), st);
+                if (s->timing) s->phase_launches[2] += 2;
+            }
+        }
         void* args[] = {&A};
+        if (s->timing) cudaEventRecord(s->ev[8], st);
         cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_solve_persistent<R>, dim3(s->coop_blocks),
-                                                    dim3(s->coop_threads), args, 0, st);
-        if (s->timing) s->phase_launches[2] += 1;
+                                                    dim3(s->coop_threads), args,
+                                                    (s->prm.sweep_flags & NBGS_SWEEP_TMA_STAGE) ? Stage<R>::BYTES : 0,
+                                                    st);
+        if (s->timing) {
+            cudaEventRecord(s->ev[9], st);
+            s->phase_launches[2] += 1;
+            s->sweep_launches += 1;
+        }
         return cuda_check(s, e, "solve: cooperative launch");
     }
     // per-colour launches: needs the colour count on the host
@@ -364,6 +813,7 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
     if (rc == NBGS_OK) rc = cuda_check(s, cudaStreamSynchronize(st), "solve");
     if (rc != NBGS_OK) return rc;
     const int T = 256;
+    if (s->timing) cudaEventRecord(s->ev[8], st);
     k_gravity<R><<<grid_for(s->n, T, 8, s->num_sms), T, 0, st>>>(A);
     if (A.warm)
         for (uint32_t c = 0; c < ncol; ++c)
@@ -373,7 +823,12 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
             k_relax_colour<R, false><<<grid_for(A.C, T, 8, s->num_sms), T, 0, st>>>(A, (int)c, k);
         k_sweep_done<R><<<1, 32, 0, st>>>(A, k);
     }
-    if (s->timing) s->phase_launches[2] += 1 + (A.warm ? ncol : 0) + (int64_t)max_sweeps * (ncol + 1);
+    if (s->timing) {
+        cudaEventRecord(s->ev[9], st);
+        const int64_t l = 1 + (A.warm ? ncol : 0) + (int64_t)max_sweeps * (ncol + 1);
+        s->phase_launches[2] += l;
+        s->sweep_launches += l;
+    }
     return cuda_check(s, cudaGetLastError(), "solve");
 }
 
@@ -510,10 +965,17 @@ int persistent_blocks(nbgs_scene* s)
 {
     int coop = 0, occ = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
-    if (s->fp32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent<float>, s->coop_threads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent<double>, s->coop_threads, 0);
+    if (s->fp32) {
+        cudaFuncSetAttribute(k_solve_persistent<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Stage<float>::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent<float>, s->coop_threads,
+                                                      Stage<float>::BYTES);
+    } else {
+        cudaFuncSetAttribute(k_solve_persistent<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Stage<double>::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent<double>, s->coop_threads,
+                                                      Stage<double>::BYTES);
+    }
     cudaGetLastError();
     if (!coop || occ < 1) {
         s->prm.solver = NBGS_SOLVER_PER_COLOUR;

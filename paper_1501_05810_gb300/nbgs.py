@@ -27,6 +27,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ECAPACITY", "ENOTCONV", "ENA
 NBGS_FP64, NBGS_FP32 = 0, 1
 NBGS_WARM_NONE, NBGS_WARM_PREV = 0, 1
 NBGS_SOLVER_PERSISTENT, NBGS_SOLVER_PER_COLOUR = 0, 1
+NBGS_SWEEP_GLOBAL_SYNC, NBGS_SWEEP_TMA_STAGE = 1, 2
 
 
 class nbgs_allocator(C.Structure):
@@ -40,7 +41,7 @@ class nbgs_params(C.Structure):
                 ("tau", C.c_double), ("beta", C.c_double), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
                 ("periodic", C.c_int32 * 3), ("precision", C.c_int32), ("warm_start", C.c_int32),
                 ("solver", C.c_int32), ("colour_seed", C.c_uint64), ("contacts_per_body", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("sweep_flags", C.c_int32)]
 
 
 class nbgs_step_stats(C.Structure):
@@ -150,6 +151,7 @@ def make_params(p: dict, solver: str = "persistent") -> nbgs_params:
     o.solver = _SOLVER[p.get("solver", solver)]
     o.colour_seed = int(p.get("colour_seed", 0)) & 0xFFFFFFFFFFFFFFFF
     o.contacts_per_body = int(p.get("contacts_per_body", 0))
+    o.sweep_flags = int(p.get("sweep_flags", 0))
     return o
 
 
@@ -297,8 +299,8 @@ class Scene:
         _call(self.h, "nbgs_enable_timing", 1 if on else 0)
 
     def get_timings(self):
-        ms = (C.c_double * 4)()
-        la = (C.c_int64 * 4)()
+        ms = (C.c_double * 5)()
+        la = (C.c_int64 * 5)()
         _call(self.h, "nbgs_get_timings", ms, la)
-        names = ("detect", "colour", "solve", "integrate")
+        names = ("detect", "colour", "solve", "integrate", "sweep_kernel")
         return {k: ms[i] for i, k in enumerate(names)}, {k: la[i] for i, k in enumerate(names)}
