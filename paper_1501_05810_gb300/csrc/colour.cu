@@ -129,7 +129,11 @@ __global__ void k_colour_keys(int64_t C, const uint32_t* __restrict__ cstate, ui
     __syncthreads();
     uint32_t cmax = 0;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t col = cstate[c] & 0xFFu;
+        uint32_t col = cstate[c] & 0xFFu;
+        if (col >= (uint32_t)kMaxColours) {   // uncoloured or out of range: report, keep indices in bounds
+            atomicOr(&info->err, kErrColours);
+            col = kMaxColours - 1;
+        }
         ckey[c] = col;
         cval[c] = (uint32_t)c;
         atomicAdd(&h[col], 1u);
