@@ -167,6 +167,53 @@ nbgs_status nbgs_integrate(nbgs_scene* scene);
  * (then only the detection synchronises). */
 nbgs_status nbgs_step(nbgs_scene* scene, int32_t max_sweeps, double tol, nbgs_step_stats* stats);
 
+/* ------------------------------------------------------------------------
+ * Batched scenes: S independent walled-box scenes stepped together in the
+ * same kernels (one persistent sweep launch for all of them).  Bodies of
+ * scene s are [body_offset[s], body_offset[s+1]) of the arrays given to
+ * nbgs_create_batch; positions are in one common frame and the scene boxes
+ * should not overlap (contacts never cross scenes either way; overlapping
+ * boxes only cost detection time).  Each scene has six walls on the faces of
+ * its box (after any nbgs_add_plane walls, which apply to every scene), its
+ * own friction coefficient, its own v_ref and its own convergence test:
+ * with tol > 0 the contacts of a scene are no longer relaxed once that
+ * scene's R_k <= tol, so every scene ends exactly where a separate solve of
+ * that scene alone would (colouring priorities use scene-local keys).
+ * params.box_lo/box_hi must enclose every scene box; periodic axes are not
+ * allowed.  The returned scene works with every other entry point.
+ * ------------------------------------------------------------------------ */
+typedef struct nbgs_batch_desc {
+    int64_t n_scenes;
+    const int64_t* body_offset;  /* n_scenes + 1, increasing, body_offset[0] = 0 */
+    const double* box_lo;        /* n_scenes x 3 (host) */
+    const double* box_hi;        /* n_scenes x 3 (host) */
+    const double* mu;            /* n_scenes (host) */
+} nbgs_batch_desc;
+
+nbgs_status nbgs_create_batch(const nbgs_params* params, const nbgs_batch_desc* batch, int64_t n_bodies,
+                              const double* pos, const double* vel, const double* angvel,
+                              const double* radius, const double* density,
+                              const nbgs_allocator* allocator, void* stream, nbgs_scene** out);
+
+/* nbgs_step() plus per-scene results of its solve: sweeps_done[s] = sweeps
+ * scene s took to reach tol (max_sweeps if it did not), residual[s] = its
+ * R_k at that sweep.  Either output may be NULL (then nothing synchronises
+ * beyond nbgs_step itself).  For a plain scene, S = 1. */
+nbgs_status nbgs_batch_step(nbgs_scene* scene, int32_t max_sweeps, double tol, int32_t* sweeps_done,
+                            double* residual);
+
+/* Per-scene results of the last solve (see nbgs_batch_step).  Synchronises. */
+nbgs_status nbgs_get_scene_stats(nbgs_scene* scene, int32_t* sweeps_done, double* residual);
+
+/* Autotuner: times the solve of the current contacts (state saved and
+ * restored) under every sweep schedule (point-to-point or grid-barrier
+ * synchronisation, with or without shared-memory staging) and 1 to the
+ * maximum resident blocks per SM, keeps the fastest, and returns its
+ * sweep_flags and blocks per SM.  Call after nbgs_detect_contacts and
+ * nbgs_colour_contacts.  Synchronises. */
+nbgs_status nbgs_autotune(nbgs_scene* scene, int32_t max_sweeps, double tol, int32_t* sweep_flags,
+                          int32_t* blocks_per_sm);
+
 /* Copy the contacts in canonical order.  Any output may be NULL; at most cap
  * contacts are written; *n_out receives the count.  impulse = (p_n, p_t, p_o)
  * of the last solve in the contact frame (n, t, o), t and o from the

@@ -164,9 +164,39 @@ using namespace nbgs;
 
 extern "C" {
 
+static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_desc* batch, int64_t n,
+                                 const double* pos, const double* vel, const double* angvel, const double* radius,
+                                 const double* density, const nbgs_allocator* allocator, void* stream,
+                                 nbgs_scene** out);
+
 nbgs_status nbgs_create_scene(const nbgs_params* params, int64_t n, const double* pos, const double* vel,
                               const double* angvel, const double* radius, const double* density,
                               const nbgs_allocator* allocator, void* stream, nbgs_scene** out)
+{
+    return create_common(params, nullptr, n, pos, vel, angvel, radius, density, allocator, stream, out);
+}
+
+nbgs_status nbgs_create_batch(const nbgs_params* params, const nbgs_batch_desc* batch, int64_t n_bodies,
+                              const double* pos, const double* vel, const double* angvel, const double* radius,
+                              const double* density, const nbgs_allocator* allocator, void* stream, nbgs_scene** out)
+{
+    if (!batch || batch->n_scenes < 1 || !batch->body_offset || !batch->box_lo || !batch->box_hi || !batch->mu)
+        return NBGS_EINVAL;
+    if (batch->n_scenes > 0x7FFFFFF0LL / 6) return NBGS_EINVAL;
+    if (batch->body_offset[0] != 0 || batch->body_offset[batch->n_scenes] != n_bodies) return NBGS_EINVAL;
+    for (int64_t k = 0; k < batch->n_scenes; ++k) {
+        if (batch->body_offset[k + 1] < batch->body_offset[k] || !(batch->mu[k] >= 0.0)) return NBGS_EINVAL;
+        for (int a = 0; a < 3; ++a)
+            if (!(batch->box_hi[3 * k + a] > batch->box_lo[3 * k + a])) return NBGS_EINVAL;
+    }
+    if (!params || params->periodic[0] || params->periodic[1] || params->periodic[2]) return NBGS_EINVAL;
+    return create_common(params, batch, n_bodies, pos, vel, angvel, radius, density, allocator, stream, out);
+}
+
+static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_desc* batch, int64_t n,
+                                 const double* pos, const double* vel, const double* angvel, const double* radius,
+                                 const double* density, const nbgs_allocator* allocator, void* stream,
+                                 nbgs_scene** out)
 {
     if (!params || !out || n < 0 || n > 0x7FFFFFF0LL) return NBGS_EINVAL;
     if (n > 0 && (!pos || !vel || !angvel || !radius || !density)) return NBGS_EINVAL;
@@ -181,6 +211,11 @@ nbgs_status nbgs_create_scene(const nbgs_params* params, int64_t n, const double
     s->prm = *params;
     s->n = n;
     s->fp32 = params->precision == NBGS_FP32;
+    if (batch) {
+        s->batch = true;
+        s->n_scenes = batch->n_scenes;
+        s->prm.solver = NBGS_SOLVER_PERSISTENT;
+    }
     s->stream = (cudaStream_t)stream;
     if (allocator && allocator->alloc && allocator->free) {
         s->alloc = *allocator;
@@ -259,6 +294,55 @@ nbgs_status nbgs_create_scene(const nbgs_params* params, int64_t n, const double
     cudaMemsetAsync(s->prev_row_off, 0, (nn + 1) * sizeof(uint32_t), s->stream);
     for (int k = 0; k < 10; ++k) cudaEventCreate(&s->ev[k]);
     s->coop_blocks = persistent_blocks(s);
+    s->max_coop_blocks = s->coop_blocks;
+    if (s->batch && s->coop_blocks == 0) {
+        nbgs_destroy_scene(s);
+        return NBGS_EINVAL;   // batches need the cooperative persistent solver
+    }
+    if (s->batch) {
+        cudaStreamSynchronize(s->stream);   // stream-ordered allocations before the blocking copies
+        const size_t S = (size_t)s->n_scenes;
+        bool okb = take(s, s->scene_of, nn) && take(s, s->scene_off, S + 1) && take(s, s->scene_box, 6 * S) &&
+                   take(s, s->scene_mu, S) && take(s, s->scene_vmax, S) && take(s, s->scene_vref, S) &&
+                   take(s, s->scene_rk, 3 * S) && take(s, s->scene_done, S) && take(s, s->scene_res, S);
+        uint32_t* h_of = okb ? (uint32_t*)malloc(nn * sizeof(uint32_t)) : nullptr;
+        uint32_t* h_off = okb ? (uint32_t*)malloc((S + 1) * sizeof(uint32_t)) : nullptr;
+        double* h_box = okb ? (double*)malloc(6 * S * sizeof(double)) : nullptr;
+        if (!h_of || !h_off || !h_box) {
+            free(h_of);
+            free(h_off);
+            free(h_box);
+            nbgs_destroy_scene(s);
+            return NBGS_ENOMEM;
+        }
+        for (size_t k = 0; k < S; ++k) {
+            h_off[k] = (uint32_t)batch->body_offset[k];
+            for (int64_t i = batch->body_offset[k]; i < batch->body_offset[k + 1]; ++i) h_of[i] = (uint32_t)k;
+            for (int a = 0; a < 3; ++a) {
+                h_box[6 * k + a] = batch->box_lo[3 * k + a];
+                h_box[6 * k + 3 + a] = batch->box_hi[3 * k + a];
+            }
+        }
+        h_off[S] = (uint32_t)n;
+        rc = cuda_check(s, cudaMemcpy(s->scene_of, h_of, (size_t)n * sizeof(uint32_t), cudaMemcpyHostToDevice),
+                        "batch: scene ids");
+        if (rc == NBGS_OK)
+            rc = cuda_check(s, cudaMemcpy(s->scene_off, h_off, (S + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice),
+                            "batch: offsets");
+        if (rc == NBGS_OK)
+            rc = cuda_check(s, cudaMemcpy(s->scene_box, h_box, 6 * S * sizeof(double), cudaMemcpyHostToDevice),
+                            "batch: boxes");
+        if (rc == NBGS_OK)
+            rc = cuda_check(s, cudaMemcpy(s->scene_mu, batch->mu, S * sizeof(double), cudaMemcpyHostToDevice),
+                            "batch: mu");
+        free(h_of);
+        free(h_off);
+        free(h_box);
+        if (rc != NBGS_OK) {
+            nbgs_destroy_scene(s);
+            return rc;
+        }
+    }
     if (s->coop_blocks > 0) {
         if (!take(s, s->dep, (size_t)kMaxColours * s->coop_blocks) || !take(s, s->prog, (size_t)s->coop_blocks) ||
             !take(s, s->cstart, (size_t)kMaxColours * (s->coop_blocks + 1))) {
@@ -303,7 +387,8 @@ void nbgs_destroy_scene(nbgs_scene* s)
     void* ps[] = {s->pos_r, s->quat, s->vel, s->hull, s->finite, s->stage, s->cell_start, s->cell_end, s->keys[0],
                   s->keys[1], s->vals[0], s->vals[1], s->radix_hist, s->scan_tmp, s->cand, s->sph_cnt, s->row_cnt,
                   s->row_off, s->prev_row_off, s->deg, s->adj_off, s->col_count, s->col_off, s->info, s->dep,
-                  s->prog, s->cstart};
+                  s->prog, s->cstart, s->scene_of, s->scene_off, s->scene_box, s->scene_mu, s->scene_vmax,
+                  s->scene_vref, s->scene_rk, s->scene_done, s->scene_res};
     for (void* p : ps) dev_free(s, p);
     free_contact_arrays(s);
     cudaStreamSynchronize(s->stream);
@@ -426,6 +511,109 @@ nbgs_status nbgs_step(nbgs_scene* s, int32_t max_sweeps, double tol, nbgs_step_s
         st->residual = s->hinfo->residual;
         st->v_ref = s->hinfo->v_ref;
     }
+    return NBGS_OK;
+}
+
+nbgs_status nbgs_get_scene_stats(nbgs_scene* s, int32_t* sweeps_done, double* residual)
+{
+    NBGS_GUARD(s);
+    nbgs_status rc = check_device_errors(s);
+    if (rc != NBGS_OK) return rc;
+    if (!s->batch) {
+        if (sweeps_done) *sweeps_done = s->last_sweeps == 0 ? 0 : (int32_t)s->hinfo->sweeps_done;
+        if (residual) *residual = s->hinfo->residual;
+        return NBGS_OK;
+    }
+    if (sweeps_done) {
+        static_assert(sizeof(int32_t) == sizeof(uint32_t), "sweep counts");
+        rc = cuda_check(s, cudaMemcpy(sweeps_done, s->scene_done, s->n_scenes * sizeof(uint32_t), cudaMemcpyDefault),
+                        "scene stats");
+        if (rc == NBGS_OK && s->last_sweeps == 0)
+            for (int64_t k = 0; k < s->n_scenes; ++k) sweeps_done[k] = 0;
+    }
+    if (rc == NBGS_OK && residual)
+        rc = cuda_check(s, cudaMemcpy(residual, s->scene_res, s->n_scenes * sizeof(double), cudaMemcpyDefault),
+                        "scene stats");
+    return rc;
+}
+
+nbgs_status nbgs_batch_step(nbgs_scene* s, int32_t max_sweeps, double tol, int32_t* sweeps_done, double* residual)
+{
+    NBGS_GUARD(s);
+    nbgs_status rc = nbgs_step(s, max_sweeps, tol, nullptr);
+    if (rc == NBGS_OK && (sweeps_done || residual)) rc = nbgs_get_scene_stats(s, sweeps_done, residual);
+    return rc;
+}
+
+nbgs_status nbgs_autotune(nbgs_scene* s, int32_t max_sweeps, double tol, int32_t* sweep_flags, int32_t* blocks_per_sm)
+{
+    NBGS_GUARD(s);
+    if (!s->detected) return fail(s, NBGS_EINVAL, "autotune: call detect_contacts first");
+    if (s->prm.solver != NBGS_SOLVER_PERSISTENT || s->max_coop_blocks == 0)
+        return fail(s, NBGS_EINVAL, "autotune: needs the persistent solver");
+    nbgs_status rc = NBGS_OK;
+    if (!s->coloured) rc = run_colour(s);
+    if (rc != NBGS_OK) return rc;
+    cudaStream_t st = s->stream;
+    const size_t vb = 2 * (size_t)std::max<int64_t>(s->n, 1) * vec4_bytes(s);
+    const size_t pb = (size_t)std::max<int64_t>(s->n_contacts, 1) * vec4_bytes(s);
+    void* vsave = dev_alloc(s, vb);
+    void* psave = dev_alloc(s, pb);
+    if (!vsave || !psave) {
+        dev_free(s, vsave);
+        dev_free(s, psave);
+        return fail(s, NBGS_ENOMEM, "autotune: save buffers");
+    }
+    cudaMemcpyAsync(vsave, s->vel, vb, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(psave, s->sp, pb, cudaMemcpyDeviceToDevice, st);
+    const bool had_timing = s->timing;
+    s->timing = false;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int max_bps = std::max(1, s->max_coop_blocks / std::max(1, s->num_sms));
+    const int flags_list[4] = {0, NBGS_SWEEP_GLOBAL_SYNC, NBGS_SWEEP_TMA_STAGE,
+                               NBGS_SWEEP_GLOBAL_SYNC | NBGS_SWEEP_TMA_STAGE};
+    float best = 3.4e38f;
+    int best_flags = s->prm.sweep_flags, best_bps = max_bps;
+    for (int fi = 0; fi < 4 && rc == NBGS_OK; ++fi) {
+        for (int bps = 1; bps <= max_bps && rc == NBGS_OK; ++bps) {
+            s->prm.sweep_flags = flags_list[fi];
+            s->coop_blocks = bps * s->num_sms;
+            float t_min = 3.4e38f;
+            for (int rep = 0; rep < 2 && rc == NBGS_OK; ++rep) {
+                cudaMemcpyAsync(s->vel, vsave, vb, cudaMemcpyDeviceToDevice, st);
+                cudaMemcpyAsync(s->sp, psave, pb, cudaMemcpyDeviceToDevice, st);
+                s->coloured = true;
+                cudaEventRecord(e0, st);
+                rc = run_solve(s, max_sweeps, tol);
+                cudaEventRecord(e1, st);
+                if (rc == NBGS_OK) rc = check_device_errors(s);
+                float ms = 0.f;
+                if (rc == NBGS_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t_min = std::min(t_min, ms);
+            }
+            if (t_min < best) {
+                best = t_min;
+                best_flags = flags_list[fi];
+                best_bps = bps;
+            }
+        }
+    }
+    s->prm.sweep_flags = best_flags;
+    s->coop_blocks = best_bps * s->num_sms;
+    cudaMemcpyAsync(s->vel, vsave, vb, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(s->sp, psave, pb, cudaMemcpyDeviceToDevice, st);
+    cudaStreamSynchronize(st);
+    dev_free(s, vsave);
+    dev_free(s, psave);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->timing = had_timing;
+    s->coloured = true;
+    s->solved = false;
+    if (rc != NBGS_OK) return rc;
+    if (sweep_flags) *sweep_flags = best_flags;
+    if (blocks_per_sm) *blocks_per_sm = best_bps;
     return NBGS_OK;
 }
 

@@ -20,13 +20,31 @@
 
 namespace nbgs {
 
+// Key of a contact in its own scene's numbering (bodies from 0, walls
+// after the scene's bodies: shared planes, then the six box faces), so that
+// batched scenes are coloured exactly as each would be alone.
+__device__ __forceinline__ uint64_t local_key(uint32_t a, uint32_t b, const SceneView& V)
+{
+    if (!V.batch) return ((uint64_t)a << 32) | b;
+    const uint32_t s = V.scene_of[a];
+    const uint32_t off = V.scene_off[s], ns = V.scene_off[s + 1] - off;
+    uint64_t lb;
+    if (b < (uint64_t)V.n) {
+        lb = b - off;
+    } else {
+        const uint64_t w = b - (uint64_t)V.n;
+        lb = ns + (w < (uint64_t)V.nplanes ? w : V.nplanes + (w - V.nplanes - 6ull * s));
+    }
+    return ((uint64_t)(a - off) << 32) | lb;
+}
+
 __global__ void k_colour_init(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
-                              const uint8_t* __restrict__ finite, uint64_t seed, uint32_t* __restrict__ deg,
+                              const uint8_t* __restrict__ finite, uint64_t seed, SceneView V, uint32_t* __restrict__ deg,
                               uint64_t* __restrict__ prio, uint32_t* __restrict__ cstate, uint32_t* __restrict__ wl)
 {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t a = cj1[c], b = cj2[c];
-        prio[c] = splitmix64((((uint64_t)a << 32) | b) ^ seed);
+        prio[c] = splitmix64(local_key(a, b, V) ^ seed);
         cstate[c] = kUncoloured;
         wl[c] = (uint32_t)c;
         if (finite[a]) atomicAdd(&deg[a], 1u);
@@ -164,7 +182,8 @@ __global__ void k_colour_offsets(const uint32_t* __restrict__ col_count, uint32_
 template <class R>
 __global__ void k_build_sweep(int64_t C, int64_t n, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cj1,
                               const uint32_t* __restrict__ cj2, const double4_32a* __restrict__ cgeo,
-                              const double2* __restrict__ clev, double dt, double beta, double mu, int warm,
+                              const double2* __restrict__ clev, double dt, double beta, double mu_all, SceneView V,
+                              int warm,
                               const uint32_t* __restrict__ prev_row_off, const uint32_t* __restrict__ prev_j2,
                               const double4_32a* __restrict__ prev_P, SweepRec<R>* __restrict__ rec,
                               R4<R>* __restrict__ p)
@@ -194,6 +213,7 @@ __global__ void k_build_sweep(int64_t C, int64_t n, const uint32_t* __restrict__
             for (uint32_t t = prev_row_off[a]; t < e; ++t) {
                 if (prev_j2[t] != b) continue;
                 const double4_32a P = prev_P[t];
+                const double mu = V.batch ? V.mu[V.scene_of[a]] : mu_all;
                 double tx, ty, tz, ox, oy, oz;
                 tangent_basis<double>(g.x, g.y, g.z, tx, ty, tz, ox, oy, oz);
                 pn = g.x * P.x + g.y * P.y + g.z * P.z;
@@ -233,8 +253,8 @@ nbgs_status run_colour(nbgs_scene* s)
         const int T = 256;
         const int gb = grid_for(C, T, 8, s->num_sms);
         cudaMemsetAsync(s->deg, 0, (n + 1) * sizeof(uint32_t), st);
-        k_colour_init<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->prm.colour_seed, s->deg, s->cprio,
-                                        s->cstate, s->wl[0]);
+        k_colour_init<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->prm.colour_seed, scene_view(s), s->deg,
+                                        s->cprio, s->cstate, s->wl[0]);
         nbgs_status rc = exclusive_scan_u32(s, s->deg, s->adj_off, n, nullptr);
         if (rc != NBGS_OK) return rc;
         cudaMemsetAsync(s->deg, 0, (n + 1) * sizeof(uint32_t), st);
@@ -278,11 +298,13 @@ nbgs_status run_colour(nbgs_scene* s)
         const int warm = (s->prm.warm_start == NBGS_WARM_PREV && s->have_prev) ? 1 : 0;
         if (s->fp32)
             k_build_sweep<float><<<gb, T, 0, st>>>(C, n, s->perm, s->cj1, s->cj2, s->cgeo, s->clev, s->prm.dt,
-                                                   s->prm.beta, s->prm.mu, warm, s->prev_row_off, s->prev_j2,
+                                                   s->prm.beta, s->prm.mu, scene_view(s), warm, s->prev_row_off,
+                                                   s->prev_j2,
                                                    s->prev_P, (SweepRec<float>*)s->srec, (float4*)s->sp);
         else
             k_build_sweep<double><<<gb, T, 0, st>>>(C, n, s->perm, s->cj1, s->cj2, s->cgeo, s->clev, s->prm.dt,
-                                                    s->prm.beta, s->prm.mu, warm, s->prev_row_off, s->prev_j2,
+                                                    s->prm.beta, s->prm.mu, scene_view(s), warm, s->prev_row_off,
+                                                    s->prev_j2,
                                                     s->prev_P, (SweepRec<double>*)s->srec, (double4_32a*)s->sp);
         if (s->timing) s->phase_launches[1] += 3;
         s->n_colours = -1;  // known on the device; read lazily

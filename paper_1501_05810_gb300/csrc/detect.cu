@@ -265,7 +265,8 @@ __device__ __forceinline__ double norm_exact(double x, double y, double z)
 
 template <class R>
 __global__ void k_hull(int64_t n, const R4<R>* __restrict__ vel, const double4_32a* __restrict__ pos_r, double dt,
-                       double tau, double* __restrict__ hull, DevInfo* info)
+                       double tau, double* __restrict__ hull, DevInfo* info, const uint32_t* __restrict__ scene_of,
+                       unsigned long long* __restrict__ scene_vmax)
 {
     double hmax = 0.0, vmax = 0.0;
     bool bad = false;
@@ -278,6 +279,11 @@ __global__ void k_hull(int64_t n, const R4<R>* __restrict__ vel, const double4_3
         const double h = xadd(xmul(dt, xadd(nv, xmul(nw, r))), tau);
         hull[i] = h;
         if (!(h <= 1e300)) bad = true;
+        if (scene_of) {   // per-scene v_ref; the filter only saves atomics
+            unsigned long long* dst = scene_vmax + scene_of[i];
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(nv);
+            if (bits > *(volatile unsigned long long*)dst) atomicMax(dst, bits);
+        }
         hmax = fmax(hmax, h);
         vmax = fmax(vmax, nv);
     }
@@ -374,9 +380,10 @@ __device__ __forceinline__ double min_image(double d, int periodic, double L)
     return d;
 }
 
-__device__ __forceinline__ bool wall_kept(const Planes& P, int k, double4_32a p, double h, double tau, double& sd, double& xi)
+__device__ __forceinline__ bool wall_kept(const double nrm[3], double c, double4_32a p, double h, double tau, double& sd,
+                                          double& xi)
 {
-    sd = xsub(xadd(xadd(xmul(P.n[k][0], p.x), xmul(P.n[k][1], p.y)), xmul(P.n[k][2], p.z)), P.c[k]);
+    sd = xsub(xadd(xadd(xmul(nrm[0], p.x), xmul(nrm[1], p.y)), xmul(nrm[2], p.z)), c);
     xi = xsub(sd, p.w);
     return xi <= xadd(h, tau);
 }
@@ -386,8 +393,8 @@ __device__ __forceinline__ bool wall_kept(const Planes& P, int k, double4_32a p,
 __global__ void __launch_bounds__(128)
 k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ svals,
          const double4_32a* __restrict__ pos_r, const double* __restrict__ hull, const uint32_t* __restrict__ cs,
-         const uint32_t* __restrict__ ce, GridArgs g, Planes planes, DevInfo* info, uint32_t* __restrict__ cand,
-         uint32_t* __restrict__ sph_cnt, uint32_t* __restrict__ row_cnt)
+         const uint32_t* __restrict__ ce, GridArgs g, Planes planes, SceneView V, DevInfo* info,
+         uint32_t* __restrict__ cand, uint32_t* __restrict__ sph_cnt, uint32_t* __restrict__ row_cnt)
 {
     const int d0 = info->dims[0], d1 = info->dims[1], d2 = info->dims[2];
     const double L0 = g.hi[0] - g.lo[0], L1 = g.hi[1] - g.lo[1], L2 = g.hi[2] - g.lo[2];
@@ -399,6 +406,7 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
         const int cz = (int)(key / ((uint32_t)d0 * (uint32_t)d1));
         const double4_32a pi = pos_r[i];
         const double hi_ = hull[i];
+        const uint32_t si = V.batch ? V.scene_of[i] : 0u;
         uint32_t list[kCandCap];
         int cnt = 0;
         for (int dz = -1; dz <= 1; ++dz) {
@@ -424,6 +432,7 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
                     for (uint32_t t = cs[c]; t < e; ++t) {
                         const uint32_t j = svals[t];
                         if (j <= i) continue;
+                        if (V.batch && V.scene_of[j] != si) continue;   // scenes never touch
                         const double4_32a pj = pos_r[j];
                         const double dx3 = min_image(xsub(pi.x, pj.x), g.periodic[0], L0);
                         const double dy3 = min_image(xsub(pi.y, pj.y), g.periodic[1], L1);
@@ -454,9 +463,12 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
         uint32_t* out = cand + (int64_t)i * kCandCap;
         for (int k = 0; k < cnt; ++k) out[k] = list[k];
         int wcnt = 0;
-        for (int k = 0; k < planes.count; ++k) {
-            double sd, xi;
-            if (wall_kept(planes, k, pi, hi_, g.tau, sd, xi)) ++wcnt;
+        const int nwall = planes.count + (V.batch ? 6 : 0);
+        for (int k = 0; k < nwall; ++k) {
+            double nrm[3], c, sd, xi;
+            uint32_t widx;
+            wall_plane(planes, V, si, k, nrm, c, widx);
+            if (wall_kept(nrm, c, pi, hi_, g.tau, sd, xi)) ++wcnt;
         }
         sph_cnt[i] = (uint32_t)cnt;
         row_cnt[i] = (uint32_t)(cnt + wcnt);
@@ -468,7 +480,7 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
 __global__ void k_write_contacts(int64_t n, int64_t ccap, const uint32_t* __restrict__ svals,
                                  const double4_32a* __restrict__ pos_r, const double* __restrict__ hull,
                                  const uint32_t* __restrict__ cand, const uint32_t* __restrict__ sph_cnt,
-                                 const uint32_t* __restrict__ row_off, GridArgs g, Planes planes,
+                                 const uint32_t* __restrict__ row_off, GridArgs g, Planes planes, SceneView V,
                                  uint32_t* __restrict__ cj1, uint32_t* __restrict__ cj2, double4_32a* __restrict__ cgeo,
                                  double2* __restrict__ clev)
 {
@@ -506,18 +518,36 @@ __global__ void k_write_contacts(int64_t n, int64_t ccap, const uint32_t* __rest
             clev[idx] = make_double2(xsub(d, pj.w), pj.w);
         }
         const double hi_ = hull[i];
-        for (int k = 0; k < planes.count; ++k) {
-            double sd, xi;
-            if (!wall_kept(planes, k, pi, hi_, g.tau, sd, xi)) continue;
+        const uint32_t si = V.batch ? V.scene_of[i] : 0u;
+        const int nwall = planes.count + (V.batch ? 6 : 0);
+        for (int k = 0; k < nwall; ++k) {
+            double nrm[3], c, sd, xi;
+            uint32_t widx;
+            wall_plane(planes, V, si, k, nrm, c, widx);
+            if (!wall_kept(nrm, c, pi, hi_, g.tau, sd, xi)) continue;
             if (idx < ccap) {
                 cj1[idx] = i;
-                cj2[idx] = (uint32_t)(n + k);
-                cgeo[idx] = make_double4_32a(planes.n[k][0], planes.n[k][1], planes.n[k][2], xi);
+                cj2[idx] = widx;
+                cgeo[idx] = make_double4_32a(nrm[0], nrm[1], nrm[2], xi);
                 clev[idx] = make_double2(sd, 0.0);
             }
             ++idx;
         }
     }
+}
+
+SceneView scene_view(const nbgs_scene* s)
+{
+    SceneView v;
+    v.batch = s->batch ? 1 : 0;
+    v.nplanes = s->planes.count;
+    v.n = s->n;
+    v.scene_of = s->scene_of;
+    v.scene_off = s->scene_off;
+    v.box = s->scene_box;
+    v.mu = s->scene_mu;
+    v.vref = s->scene_vref;
+    return v;
 }
 
 static GridArgs grid_args(const nbgs_scene* s)
@@ -564,10 +594,13 @@ nbgs_status run_detect(nbgs_scene* s)
     const GridArgs g = grid_args(s);
     const int T = 256;
     const int gb = grid_for(n, T, 8, s->num_sms);
+    if (s->batch) cudaMemsetAsync(s->scene_vmax, 0, s->n_scenes * sizeof(unsigned long long), st);
     if (s->fp32)
-        k_hull<float><<<gb, T, 0, st>>>(n, (const float4*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hull, s->info);
+        k_hull<float><<<gb, T, 0, st>>>(n, (const float4*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hull, s->info,
+                                        s->scene_of, s->scene_vmax);
     else
-        k_hull<double><<<gb, T, 0, st>>>(n, (const double4_32a*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hull, s->info);
+        k_hull<double><<<gb, T, 0, st>>>(n, (const double4_32a*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hull,
+                                         s->info, s->scene_of, s->scene_vmax);
     k_grid_setup<<<1, 1, 0, st>>>(g, s->info);
     k_clear_cells<<<grid_for(s->max_cells, T, 8, s->num_sms), T, 0, st>>>(s->cell_start, s->cell_end, s->info);
     k_cell_keys<<<gb, T, 0, st>>>(n, s->pos_r, g, s->info, s->keys[0], s->vals[0]);
@@ -576,8 +609,9 @@ nbgs_status run_detect(nbgs_scene* s)
     if (rc != NBGS_OK) return rc;
     k_cell_ranges<<<gb, T, 0, st>>>(n, s->keys[0], s->cell_start, s->cell_end);
     k_narrow<<<grid_for(n, 128, 16, s->num_sms), 128, 0, st>>>(n, s->keys[0], s->vals[0], s->pos_r, s->hull,
-                                                                 s->cell_start, s->cell_end, g, s->planes, s->info,
-                                                                 s->cand, s->sph_cnt, s->row_cnt);
+                                                                 s->cell_start, s->cell_end, g, s->planes,
+                                                                 scene_view(s), s->info, s->cand, s->sph_cnt,
+                                                                 s->row_cnt);
     rc = exclusive_scan_u32(s, s->row_cnt, s->row_off, n, &s->info->n_contacts);
     if (rc != NBGS_OK) return rc;
     if (s->timing) s->phase_launches[0] += 5;
@@ -599,8 +633,8 @@ nbgs_status run_detect(nbgs_scene* s)
         if (rc != NBGS_OK) return rc;
     }
     k_write_contacts<<<grid_for(n, T, 8, s->num_sms), T, 0, st>>>(n, s->ccap, s->vals[0], s->pos_r, s->hull, s->cand,
-                                                                  s->sph_cnt, s->row_off, g, s->planes, s->cj1,
-                                                                  s->cj2, s->cgeo, s->clev);
+                                                                  s->sph_cnt, s->row_off, g, s->planes, scene_view(s),
+                                                                  s->cj1, s->cj2, s->cgeo, s->clev);
     if (s->timing) {
         s->phase_launches[0] += 1;
         cudaEventRecord(s->ev[1], st);

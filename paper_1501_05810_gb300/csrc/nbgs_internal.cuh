@@ -49,6 +49,44 @@ struct Planes {
     double c[kMaxPlanes];
 };
 
+// Batched scenes as the kernels see them (batch == 0: one plain scene).
+struct SceneView {
+    int batch;
+    int nplanes;                  // walls shared by every scene (nbgs_add_plane)
+    int64_t n;                    // bodies in total
+    const uint32_t* scene_of;     // n
+    const uint32_t* scene_off;    // S + 1
+    const double* box;            // S x 6
+    const double* mu;             // S
+    const double* vref;           // S
+};
+
+// Wall k of body i's scene: k < nplanes are the shared planes, then the six
+// faces of the scene box (+x at lo, -x at hi, +y, -y, +z, -z).  Body index
+// of the wall: n + k for shared planes, n + nplanes + 6 s + face.
+__device__ __forceinline__ void wall_plane(const Planes& P, const SceneView& V, uint32_t s, int k, double nrm[3],
+                                           double& c, uint32_t& index)
+{
+    if (k < P.count) {
+        nrm[0] = P.n[k][0];
+        nrm[1] = P.n[k][1];
+        nrm[2] = P.n[k][2];
+        c = P.c[k];
+        index = (uint32_t)(V.n + k);
+        return;
+    }
+    const int f = k - P.count, axis = f >> 1;
+    nrm[0] = nrm[1] = nrm[2] = 0.0;
+    if ((f & 1) == 0) {
+        nrm[axis] = 1.0;
+        c = V.box[6 * (int64_t)s + axis];
+    } else {
+        nrm[axis] = -1.0;
+        c = -V.box[6 * (int64_t)s + 3 + axis];
+    }
+    index = (uint32_t)(V.n + P.count + 6 * (int64_t)s + f);
+}
+
 // Everything a step's kernels communicate through device memory.
 struct DevInfo {
     unsigned long long hmax_bits;   // max hull radius (bits of a non-negative double)
@@ -180,6 +218,20 @@ struct nbgs_scene {
     double r_max = 0.0;
     bool fp32 = false;
 
+    // batched scenes (n_scenes == 1 and no arrays for a plain scene)
+    int64_t n_scenes = 1;
+    bool batch = false;
+    uint32_t* scene_of = nullptr;       // n: scene of each body
+    uint32_t* scene_off = nullptr;      // S + 1: first body of each scene
+    double* scene_box = nullptr;        // S x 6: lo xyz, hi xyz
+    double* scene_mu = nullptr;         // S
+    unsigned long long* scene_vmax = nullptr;  // S: max |v| at step start (bits)
+    double* scene_vref = nullptr;       // S
+    unsigned long long* scene_rk = nullptr;    // 3 x S rotating slots: max r_j / v_ref per sweep (bits)
+    uint32_t* scene_done = nullptr;     // S: sweeps to tolerance
+    double* scene_res = nullptr;        // S: R_k at that sweep
+    int max_coop_blocks = 0;            // occupancy limit of the persistent kernel
+
     // bodies
     double4_32a* pos_r = nullptr;
     double4_32a* quat = nullptr;
@@ -286,5 +338,6 @@ nbgs_status exclusive_scan_u32(nbgs_scene* s, const uint32_t* in, uint32_t* out,
 nbgs_status radix_sort_pairs(nbgs_scene* s, uint32_t*& keys, uint32_t*& vals, uint32_t*& keys_alt,
                              uint32_t*& vals_alt, int64_t n, int bits);
 int grid_for(int64_t work, int threads, int max_blocks_per_sm, int num_sms);
+SceneView scene_view(const nbgs_scene* s);
 
 }  // namespace nbgs

@@ -40,7 +40,16 @@ template <class R> struct SolveArgs {
     int* prog;           // per block: last sweep phase completed (local synchronisation)
     const int2* dep;     // per (colour, block): window [lo, hi] of blocks sharing bodies with the chunk
     const uint32_t* cstart;  // per colour, B + 1 chunk boundaries (sweep slots)
+    SceneView V;             // batched scenes (V.batch == 0: one scene)
+    int64_t nscene;
+    unsigned long long* scene_rk;   // 3 x S rotating slots of max r_j / v_ref_s
+    uint32_t* scene_done;
+    double* scene_res;
 };
+
+// Rotating per-scene residual slot of sweep k (three, so that clearing the
+// slot of sweep k + 1 while sweep k runs touches nothing still read).
+__host__ __device__ __forceinline__ int scene_slot(int k) { return k % 3; }
 
 template <class R>
 __device__ __forceinline__ void decode(const SweepRec<R>& r, uint32_t& a, uint32_t& b, R& la, R& lb, R& nx, R& ny, R& nz,
@@ -100,13 +109,27 @@ __device__ __forceinline__ void gather(const SolveArgs<R>& A, const SweepRec<R>&
 // Relax one contact whose record, impulse and bodies are already loaded;
 // returns r_j.  apply_only: add the stored impulse p to the bodies (initial
 // impulses of a warm start) instead of relaxing.
-template <class R, bool apply_only>
+template <class R, bool apply_only, bool Batch = false>
 __device__ __forceinline__ R relax_gathered(const SolveArgs<R>& A, int64_t s, const SweepRec<R>& rr, const R4<R>& pp,
-                                            Bodies<R> B)
+                                            Bodies<R> B, int sweep)
 {
     uint32_t ia, ib;
     R la, lb, nx, ny, nz, bias;
     decode<R>(rr, ia, ib, la, lb, nx, ny, nz, bias);
+    R mu = A.mu;
+    double vref_s = 1.0;
+    uint32_t scene = 0;
+    if (Batch) {
+        scene = A.V.scene_of[ia];
+        if (!apply_only && sweep > 0) {
+            // this scene met its tolerance in an earlier sweep: it is done
+            const double prev = __longlong_as_double(
+                (long long)A.scene_rk[scene_slot(sweep - 1) * A.nscene + scene]);
+            if (prev <= A.tol) return R(0);
+        }
+        mu = (R)A.V.mu[scene];
+        vref_s = A.V.vref[scene];
+    }
     R4<R> va = B.va, wa = B.wa, vb = B.vb, wb = B.wb;
     const bool dyn_b = ib < (uint32_t)A.n;
     const R ima = va.w, iIa = wa.w, imb = vb.w, iIb = wb.w;
@@ -136,7 +159,7 @@ __device__ __forceinline__ R relax_gathered(const SolveArgs<R>& A, int64_t s, co
         R yn = -bn / wn;
         yn = yn > R(0) ? yn : R(0);
         R yt = -bt / wt, yo = -bo / wt;
-        const R lim = A.mu * yn;
+        const R lim = mu * yn;
         const R len2 = yt * yt + yo * yo;
         if (len2 > lim * lim) {
             if (len2 > R(0)) {
@@ -187,23 +210,32 @@ __device__ __forceinline__ R relax_gathered(const SolveArgs<R>& A, int64_t s, co
         A.vel[2 * (int64_t)ib + 1] = wb;
     }
     const R r1 = wn * dn, r2 = wt * dt_, r3 = wt * do_;
-    return sqrt(r1 * r1 + r2 * r2 + r3 * r3);
+    const R r = sqrt(r1 * r1 + r2 * r2 + r3 * r3);
+    if (Batch && !apply_only) {
+        // per-scene R_k; the read filter only saves atomics
+        const double rn = (double)r / vref_s;
+        unsigned long long* dst = A.scene_rk + scene_slot(sweep) * A.nscene + scene;
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(rn);
+        if (bits > *(volatile unsigned long long*)dst) atomicMax(dst, bits);
+        return (R)rn;
+    }
+    return r;
 }
 
-template <class R, bool apply_only>
-__device__ __forceinline__ R relax(const SolveArgs<R>& A, int64_t s)
+template <class R, bool apply_only, bool Batch = false>
+__device__ __forceinline__ R relax(const SolveArgs<R>& A, int64_t s, int sweep)
 {
     const SweepRec<R> rr = A.rec[s];
     const R4<R> pp = A.p[s];
     Bodies<R> B;
     gather<R>(A, rr, B);
-    return relax_gathered<R, apply_only>(A, s, rr, pp, B);
+    return relax_gathered<R, apply_only, Batch>(A, s, rr, pp, B, sweep);
 }
 
 // Two contacts of one colour: both gathers are issued before either store
 // (they touch disjoint finite bodies, so the order does not matter).
 template <class R, bool apply_only>
-__device__ __forceinline__ R relax_pair(const SolveArgs<R>& A, int64_t s0, int64_t s1)
+__device__ __forceinline__ R relax_pair(const SolveArgs<R>& A, int64_t s0, int64_t s1, int sweep)
 {
     const SweepRec<R> r0 = A.rec[s0];
     const R4<R> p0 = A.p[s0];
@@ -216,9 +248,9 @@ __device__ __forceinline__ R relax_pair(const SolveArgs<R>& A, int64_t s0, int64
     Bodies<R> B0, B1;
     gather<R>(A, r0, B0);
     if (s1 >= 0) gather<R>(A, r1, B1);
-    R r = relax_gathered<R, apply_only>(A, s0, r0, p0, B0);
+    R r = relax_gathered<R, apply_only>(A, s0, r0, p0, B0, sweep);
     if (s1 >= 0) {
-        const R q = relax_gathered<R, apply_only>(A, s1, r1, p1, B1);
+        const R q = relax_gathered<R, apply_only>(A, s1, r1, p1, B1, sweep);
         r = q > r ? q : r;
     }
     return r;
@@ -351,9 +383,9 @@ __device__ __forceinline__ int stage_issue(const SolveArgs<R>& A, int c, SweepRe
     return m;
 }
 
-template <class R, bool apply_only>
+template <class R, bool apply_only, bool Batch>
 __device__ __forceinline__ R process_colour(const SolveArgs<R>& A, int c, int m, const SweepRec<R>* srec,
-                                            const R4<R>* sp)
+                                            const R4<R>* sp, int sweep)
 {
     R rmax = R(0);
     int64_t b0, b1;
@@ -365,12 +397,12 @@ __device__ __forceinline__ R process_colour(const SolveArgs<R>& A, int c, int m,
         const R4<R> p0 = sp[slot];
         Bodies<R> B0;
         gather<R>(A, r0, B0);
-        const R r = relax_gathered<R, apply_only>(A, b0 + slot, r0, p0, B0);
+        const R r = relax_gathered<R, apply_only, Batch>(A, b0 + slot, r0, p0, B0, sweep);
         rmax = r > rmax ? r : rmax;
     }
     // the rest of the chunk straight from global memory
     for (int64_t s = b0 + m + threadIdx.x; s < b1; s += T) {
-        const R r = relax<R, apply_only>(A, s);
+        const R r = relax<R, apply_only, Batch>(A, s, sweep);
         rmax = r > rmax ? r : rmax;
     }
     return rmax;
@@ -422,8 +454,9 @@ __device__ __forceinline__ bool barrier_wait(DevInfo* info, const uint32_t* s_ge
     return *s_ok != 0;
 }
 
-template <class R> struct PersistMinBlocks {
-    static constexpr int value = sizeof(R) == 4 ? 4 : 2;   // FP64 needs more registers per thread
+template <class R, bool Batch> struct PersistMinBlocks {
+    // FP64 and the per-scene bookkeeping of batches need more registers per thread
+    static constexpr int value = sizeof(R) == 4 ? (Batch ? 3 : 4) : 2;
 };
 
 // Wait until every block in this chunk's window has completed sweep phase
@@ -470,8 +503,8 @@ __device__ __forceinline__ void publish(int* prog, int g)
     }
 }
 
-template <class R>
-__global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R>::value) k_solve_persistent(SolveArgs<R> A)
+template <class R, bool Batch>
+__global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::value) k_solve_persistent(SolveArgs<R> A)
 {
     extern __shared__ __align__(128) unsigned char stage_mem[];
     SweepRec<R>* srec = reinterpret_cast<SweepRec<R>*>(stage_mem);
@@ -484,6 +517,7 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R>::value) k
     const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
     const int ncol = (int)A.info->n_colours;
     const double vref = v_ref_of(A.info, A.gdt_norm);
+    const double vnorm = Batch ? 1.0 : vref;   // batched residuals arrive already divided by v_ref_s
     const bool stage = (A.flags & NBGS_SWEEP_TMA_STAGE) != 0;
     const bool local = (A.flags & NBGS_SWEEP_GLOBAL_SYNC) == 0;
     if (threadIdx.x == 0) mbar_init(&bar);
@@ -491,7 +525,7 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R>::value) k
     if (!grid_barrier(A.info, nb)) return;
     if (A.warm) {
         for (int c = 0; c < ncol; ++c) {
-            process_colour<R, true>(A, c, 0, srec, sp);
+            process_colour<R, true, Batch>(A, c, 0, srec, sp, 0);
             if (!grid_barrier(A.info, nb)) return;
         }
     }
@@ -502,6 +536,8 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R>::value) k
     bool ok = true, synced = true;
     for (; k < A.max_sweeps && ok; ++k) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && k + 1 >= kHistKept) A.info->rk_bits[rk_slot(k + 1)] = 0ull;
+        if (Batch)   // the slot of sweep k + 1 is neither read nor written during sweep k
+            for (int64_t sc = gtid; sc < A.nscene; sc += gstride) A.scene_rk[scene_slot(k + 1) * A.nscene + sc] = 0ull;
         R rmax = R(0);
         for (int c = 0; c < ncol; ++c) {
             const int g = k * ncol + c;
@@ -516,7 +552,7 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R>::value) k
                 }
                 parity ^= 1u;
             }
-            const R r = process_colour<R, false>(A, c, m, srec, sp);
+            const R r = process_colour<R, false, Batch>(A, c, m, srec, sp, k);
             rmax = r > rmax ? r : rmax;
             if (c == ncol - 1) block_max_to<R>(rmax, &A.info->rk_bits[rk_slot(k)]);
             const int cn = c + 1 < ncol ? c + 1 : 0;
@@ -536,15 +572,25 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R>::value) k
         synced = !local;
         // R_k needs every block's contribution: a grid barrier per sweep when
         // the tolerance is tested (and near the rotating residual slots)
-        if (local && ncol > 0 && (A.tol > 0.0 || k + 2 >= kHistKept)) {
+        if (local && ncol > 0 && (A.tol > 0.0 || Batch || k + 2 >= kHistKept)) {
             if (!grid_barrier(A.info, nb)) {
                 ok = false;
                 break;
             }
             synced = true;
         }
+        if (synced && Batch && A.tol > 0.0) {   // scenes that met their tolerance in this sweep
+            for (int64_t sc = gtid; sc < A.nscene; sc += gstride) {
+                const double rs = __longlong_as_double(
+                    (long long)((volatile unsigned long long*)A.scene_rk)[scene_slot(k) * A.nscene + sc]);
+                if (A.scene_done[sc] == 0 && rs <= A.tol) {
+                    A.scene_done[sc] = (uint32_t)(k + 1);
+                    A.scene_res[sc] = rs;
+                }
+            }
+        }
         if (synced) {
-            Rk = __longlong_as_double((long long)((volatile unsigned long long*)A.info->rk_bits)[rk_slot(k)]) / vref;
+            Rk = __longlong_as_double((long long)((volatile unsigned long long*)A.info->rk_bits)[rk_slot(k)]) / vnorm;
             if (A.tol > 0.0 && Rk <= A.tol) {
                 ++k;
                 break;
@@ -556,7 +602,17 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R>::value) k
     if (!ok) return;
     if (!synced && k > 0) {
         if (!grid_barrier(A.info, nb)) return;
-        Rk = __longlong_as_double((long long)((volatile unsigned long long*)A.info->rk_bits)[rk_slot(k - 1)]) / vref;
+        Rk = __longlong_as_double((long long)((volatile unsigned long long*)A.info->rk_bits)[rk_slot(k - 1)]) / vnorm;
+    }
+    if (Batch) {   // scenes still short of their tolerance ran every sweep
+        for (int64_t sc = gtid; sc < A.nscene; sc += gstride) {
+            if (A.scene_done[sc] == 0) {
+                A.scene_done[sc] = (uint32_t)k;
+                A.scene_res[sc] = k > 0 ? __longlong_as_double((long long)((volatile unsigned long long*)
+                                                                               A.scene_rk)[scene_slot(k - 1) * A.nscene + sc])
+                                        : 0.0;
+            }
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.info->sweeps_done = (uint32_t)k;
@@ -701,7 +757,7 @@ __global__ void __launch_bounds__(256) k_relax_colour(SolveArgs<R> A, int colour
     R rmax = R(0);
     const int64_t T = (int64_t)gridDim.x * blockDim.x;
     for (int64_t s = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < e; s += 2 * T) {
-        const R r = relax_pair<R, apply_only>(A, s, s + T < e ? s + T : -1);
+        const R r = relax_pair<R, apply_only>(A, s, s + T < e ? s + T : -1, sweep);
         rmax = r > rmax ? r : rmax;
     }
     if (!apply_only) block_max_to<R>(rmax, &A.info->rk_bits[rk_slot(sweep)]);
@@ -717,6 +773,13 @@ __global__ void k_sweep_done(SolveArgs<R> A, int sweep)
     A.info->residual = Rk;
     A.info->v_ref = vref;
     if ((A.tol > 0.0 && Rk <= A.tol) || sweep + 1 == A.max_sweeps) A.info->sweeps_done = (uint32_t)(sweep + 1);
+}
+
+__global__ void k_scene_vref(int64_t S, const unsigned long long* __restrict__ vmax, double gdt_norm,
+                             double* __restrict__ vref)
+{
+    for (int64_t sc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sc < S; sc += (int64_t)gridDim.x * blockDim.x)
+        vref[sc] = fmax(fmax(__longlong_as_double((long long)vmax[sc]), gdt_norm), 1e-12);
 }
 
 // Canonical impulses (contact frame) and world-frame impulses for the next
@@ -761,6 +824,11 @@ static SolveArgs<R> make_args(nbgs_scene* s, int max_sweeps, double tol)
     A.prog = s->prog;
     A.dep = s->dep;
     A.cstart = s->cstart;
+    A.V = scene_view(s);
+    A.nscene = s->n_scenes;
+    A.scene_rk = s->scene_rk;
+    A.scene_done = s->scene_done;
+    A.scene_res = s->scene_res;
     return A;
 }
 
@@ -773,6 +841,14 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
     cudaMemsetAsync(A.info->rk_bits, 0, (size_t)(nk > 0 ? nk : 1) * sizeof(unsigned long long), st);
     cudaMemsetAsync(&A.info->barrier_count, 0, 2 * sizeof(uint32_t), st);
     const uint32_t not_done = 0xFFFFFFFFu;
+    if (s->batch) {
+        k_scene_vref<<<grid_for(s->n_scenes, 256, 8, s->num_sms), 256, 0, st>>>(s->n_scenes, s->scene_vmax, A.gdt_norm,
+                                                                               s->scene_vref);
+        cudaMemsetAsync(s->scene_rk, 0, 3 * s->n_scenes * sizeof(unsigned long long), st);
+        cudaMemsetAsync(s->scene_done, 0, s->n_scenes * sizeof(uint32_t), st);
+        cudaMemsetAsync(s->scene_res, 0, s->n_scenes * sizeof(double), st);
+        if (s->timing) s->phase_launches[2] += 1;
+    }
     if (s->prm.solver == NBGS_SOLVER_PERSISTENT) {
         if (A.C > 0) {
             const int T = 256, B = s->coop_blocks;
@@ -794,7 +870,8 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
         }
         void* args[] = {&A};
         if (s->timing) cudaEventRecord(s->ev[8], st);
-        cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_solve_persistent<R>, dim3(s->coop_blocks),
+        const void* fn = s->batch ? (const void*)k_solve_persistent<R, true> : (const void*)k_solve_persistent<R, false>;
+        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(s->coop_blocks),
                                                     dim3(s->coop_threads), args,
                                                     (s->prm.sweep_flags & NBGS_SWEEP_TMA_STAGE) ? Stage<R>::BYTES : 0,
                                                     st);
@@ -866,12 +943,14 @@ template <class R>
 __global__ void k_final_residuals(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
                                   const double4_32a* __restrict__ cgeo, const double2* __restrict__ clev,
                                   const double4_32a* __restrict__ cimp, const R4<R>* __restrict__ vel, double dt,
-                                  double beta, double mu, const DevInfo* info, unsigned long long* out)
+                                  double beta, double mu_all, SceneView V, const DevInfo* info, unsigned long long* out)
 {
     double m[4] = {0, 0, 0, 0};
-    const double vr = info->v_ref > 0.0 ? info->v_ref : 1e-12;
+    const double vr_all = info->v_ref > 0.0 ? info->v_ref : 1e-12;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t a = cj1[c], b = cj2[c];
+        const double vr = V.batch ? V.vref[V.scene_of[a]] : vr_all;
+        const double mu = V.batch ? V.mu[V.scene_of[a]] : mu_all;
         const double4_32a g = cgeo[c];
         const double2 l = clev[c];
         const double4_32a p = cimp[c];
@@ -932,11 +1011,11 @@ nbgs_status run_final_residuals(nbgs_scene* s, nbgs_residuals* out)
         if (s->fp32)
             k_final_residuals<float><<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(
                 C, s->n, s->cj1, s->cj2, s->cgeo, s->clev, s->cimp, (const float4*)s->vel, s->prm.dt, s->prm.beta,
-                s->prm.mu, s->info, slots);
+                s->prm.mu, scene_view(s), s->info, slots);
         else
             k_final_residuals<double><<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(
                 C, s->n, s->cj1, s->cj2, s->cgeo, s->clev, s->cimp, (const double4_32a*)s->vel, s->prm.dt, s->prm.beta,
-                s->prm.mu, s->info, slots);
+                s->prm.mu, scene_view(s), s->info, slots);
     }
     unsigned long long h[4];
     nbgs_status rc = cuda_check(s, cudaMemcpyAsync(h, slots, sizeof(h), cudaMemcpyDeviceToHost, st), "residuals");
@@ -965,17 +1044,27 @@ int persistent_blocks(nbgs_scene* s)
 {
     int coop = 0, occ = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
+    int occ_b = 0;
     if (s->fp32) {
-        cudaFuncSetAttribute(k_solve_persistent<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_solve_persistent<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              Stage<float>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent<float>, s->coop_threads,
+        cudaFuncSetAttribute(k_solve_persistent<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Stage<float>::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent<float, false>, s->coop_threads,
+                                                      Stage<float>::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_solve_persistent<float, true>, s->coop_threads,
                                                       Stage<float>::BYTES);
     } else {
-        cudaFuncSetAttribute(k_solve_persistent<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_solve_persistent<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              Stage<double>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent<double>, s->coop_threads,
+        cudaFuncSetAttribute(k_solve_persistent<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Stage<double>::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent<double, false>, s->coop_threads,
+                                                      Stage<double>::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_solve_persistent<double, true>, s->coop_threads,
                                                       Stage<double>::BYTES);
     }
+    if (s->batch) occ = occ_b;
     cudaGetLastError();
     if (!coop || occ < 1) {
         s->prm.solver = NBGS_SOLVER_PER_COLOUR;

@@ -44,6 +44,11 @@ class nbgs_params(C.Structure):
                 ("sweep_flags", C.c_int32)]
 
 
+class nbgs_batch_desc(C.Structure):
+    _fields_ = [("n_scenes", C.c_int64), ("body_offset", C.POINTER(C.c_int64)), ("box_lo", C.POINTER(C.c_double)),
+                ("box_hi", C.POINTER(C.c_double)), ("mu", C.POINTER(C.c_double))]
+
+
 class nbgs_step_stats(C.Structure):
     _fields_ = [("n_contacts", C.c_int64), ("n_colours", C.c_int32), ("sweeps_done", C.c_int32),
                 ("residual", C.c_double), ("v_ref", C.c_double)]
@@ -75,6 +80,11 @@ _SIG = {
     "nbgs_sync": [_vp],
     "nbgs_enable_timing": [_vp, C.c_int32],
     "nbgs_get_timings": [_vp, _dp, _i64p],
+    "nbgs_create_batch": [_P(nbgs_params), _P(nbgs_batch_desc), C.c_int64, _vp, _vp, _vp, _vp, _vp,
+                          _P(nbgs_allocator), _vp, _P(_vp)],
+    "nbgs_batch_step": [_vp, C.c_int32, C.c_double, _i32p, _dp],
+    "nbgs_get_scene_stats": [_vp, _i32p, _dp],
+    "nbgs_autotune": [_vp, C.c_int32, C.c_double, _i32p, _i32p],
     "nbgs_final_residuals_noalloc": [C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                      C.c_double, C.c_double, C.c_double, C.c_double, _vp, _vp],
 }
@@ -304,3 +314,66 @@ class Scene:
         _call(self.h, "nbgs_get_timings", ms, la)
         names = ("detect", "colour", "solve", "integrate", "sweep_kernel")
         return {k: ms[i] for i, k in enumerate(names)}, {k: la[i] for i, k in enumerate(names)}
+
+
+class BatchScene(Scene):
+    """Many independent walled-box scenes on the GPU in one nbgs_scene
+    (nbgs_create_batch).  ``scenes`` is a list of scene dicts whose boxes do
+    not overlap (see :func:`paper_1501_05810_gb300.scenes.layout_batch`);
+    each keeps its own mu; dt, gravity, tau, beta, omega, precision,
+    warm start and colour seed come from the first scene."""
+
+    def __init__(self, scenes: list, device="cuda:0", stream=None, use_torch_allocator: bool = True):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.n_scenes = len(scenes)
+        sizes = [len(sc["radius"]) for sc in scenes]
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        self.n = int(self.offsets[-1])
+        lo = np.array([sc["params"]["box_lo"] for sc in scenes], dtype=np.float64)
+        hi = np.array([sc["params"]["box_hi"] for sc in scenes], dtype=np.float64)
+        mu = np.array([sc["params"]["mu"] for sc in scenes], dtype=np.float64)
+        p = dict(scenes[0]["params"])
+        p["box_lo"] = tuple(lo.min(0) - 1.0)
+        p["box_hi"] = tuple(hi.max(0) + 1.0)
+        p["periodic"] = (0, 0, 0)
+        p["solver"] = "persistent"
+        self.params = make_params(p)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.allocator = TorchAllocator(self.device) if use_torch_allocator else None
+        cat = {k: np.ascontiguousarray(np.concatenate([sc[k] for sc in scenes]), dtype=np.float64)
+               for k in ("pos", "vel", "angvel", "radius", "density")}
+        self._keep = (self.offsets, np.ascontiguousarray(lo), np.ascontiguousarray(hi), np.ascontiguousarray(mu))
+        desc = nbgs_batch_desc(self.n_scenes, self.offsets.ctypes.data_as(C.POINTER(C.c_int64)),
+                               self._keep[1].ctypes.data_as(_dp), self._keep[2].ctypes.data_as(_dp),
+                               self._keep[3].ctypes.data_as(_dp))
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = _lib.nbgs_create_batch(C.byref(self.params), C.byref(desc), self.n,
+                                        *[_ptr(cat[k]) for k in ("pos", "vel", "angvel", "radius", "density")],
+                                        C.byref(self.allocator.struct) if self.allocator else None,
+                                        self.stream.cuda_stream, C.byref(h))
+        if st != NBGS_OK:
+            raise NBGSError(st, "nbgs_create_batch", "batch creation failed")
+        self.h = h
+
+    def step_scenes(self, max_sweeps: int, tol: float):
+        k = np.empty(self.n_scenes, np.int32)
+        r = np.empty(self.n_scenes)
+        _call(self.h, "nbgs_batch_step", int(max_sweeps), float(tol), k.ctypes.data_as(_i32p), r.ctypes.data_as(_dp))
+        return k, r
+
+    def scene_stats(self):
+        k = np.empty(self.n_scenes, np.int32)
+        r = np.empty(self.n_scenes)
+        _call(self.h, "nbgs_get_scene_stats", k.ctypes.data_as(_i32p), r.ctypes.data_as(_dp))
+        return k, r
+
+
+def autotune(scene: Scene, max_sweeps: int, tol: float):
+    """Pick the fastest sweep schedule and blocks per SM for the scene's
+    current contacts (nbgs_autotune); returns (sweep_flags, blocks_per_sm)."""
+    f, b = C.c_int32(), C.c_int32()
+    _call(scene.h, "nbgs_autotune", int(max_sweeps), float(tol), C.byref(f), C.byref(b))
+    return f.value, b.value

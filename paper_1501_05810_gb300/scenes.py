@@ -263,3 +263,63 @@ def periodic_cloud(seed: int = 0, per_side: int = 6, spacing: float = 1.02, r_lo
     params.setdefault("periodic", (1, 1, 1))
     prm = default_params(box_lo=(0, 0, 0), box_hi=(side, side, side), **params)
     return _scene(f"periodic_cloud_{n}", prm, pos, vel, ang, radius, rng.uniform(0.5, 2.0, n), [])
+
+
+# ---------------------------------------------------------------------------
+# Batched scenes
+# ---------------------------------------------------------------------------
+
+def batch_scene(seed: int, n: int, mu: float, r_lo: float = 0.4, r_hi: float = 0.6, phi: float = 0.3,
+                **params) -> dict:
+    """One walled-box scene of n polydisperse spheres on a jittered cubic
+    lattice at volume fraction phi, base side B = ceil((n V / phi / 2)^(1/3))
+    and height 2B, settling under gravity."""
+    rng = np.random.default_rng(seed)
+    radius = rng.uniform(r_lo, r_hi, n)
+    mean_vol = 4.0 / 3.0 * math.pi * np.mean(radius ** 3)
+    base = math.ceil((n * mean_vol / phi / 2.0) ** (1.0 / 3.0))
+    s = max((mean_vol / phi) ** (1.0 / 3.0), 2.0 * r_hi * 1.0001)
+    nx = max(1, int(base // s))
+    nz = int(math.ceil(n / (nx * nx)))
+    height = max(2.0 * base, (nz + 1) * s)
+    idx = np.arange(n)
+    ix, iy, iz = idx % nx, (idx // nx) % nx, idx // (nx * nx)
+    pos = (np.stack([ix, iy, iz], -1) + 0.5) * s
+    j = (s - 2.0 * r_hi) / 2.0
+    pos = pos + rng.uniform(-j, j, pos.shape)
+    lo, hi = (0.0, 0.0, 0.0), (nx * s, nx * s, height)
+    prm = default_params(dt=5e-4, mu=mu, tau=0.01 * r_lo, box_lo=lo, box_hi=hi, **params)
+    return _scene(f"batch_scene_{seed}_{n}", prm, pos, np.zeros((n, 3)), np.zeros((n, 3)), radius, np.ones(n),
+                  box_walls(lo, hi))
+
+
+def batch_scenes(n_scenes: int = 4096, seed: int = 0, n_lo: int = 200, n_hi: int = 20000, mu_lo: float = 0.2,
+                 mu_hi: float = 0.8, **params) -> list:
+    """n_scenes independent scenes with log-uniform sphere counts in
+    [n_lo, n_hi] and mu ~ U(mu_lo, mu_hi), laid out side by side."""
+    rng = np.random.default_rng(seed)
+    sizes = np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), n_scenes))).astype(int)
+    mus = rng.uniform(mu_lo, mu_hi, n_scenes)
+    scenes = [batch_scene(int(seed) * 1_000_003 + k, int(sizes[k]), float(mus[k]), **params) for k in range(n_scenes)]
+    return layout_batch(scenes)
+
+
+def layout_batch(scenes: list, gap: float = 4.0) -> list:
+    """Translate the scenes (positions, boxes, walls) onto a square grid in
+    the x-y plane with `gap` between boxes, so that no two boxes overlap."""
+    k = len(scenes)
+    cols = max(1, int(math.ceil(math.sqrt(k))))
+    size = max(max(sc["params"]["box_hi"][a] - sc["params"]["box_lo"][a] for a in (0, 1)) for sc in scenes)
+    out = []
+    for i, sc in enumerate(scenes):
+        shift = np.array([(i % cols) * (size + gap), (i // cols) * (size + gap), 0.0]) - np.array(sc["params"]["box_lo"])
+        prm = dict(sc["params"])
+        lo = tuple(np.array(prm["box_lo"]) + shift)
+        hi = tuple(np.array(prm["box_hi"]) + shift)
+        prm["box_lo"], prm["box_hi"] = lo, hi
+        t = dict(sc)
+        t["params"] = prm
+        t["pos"] = sc["pos"] + shift
+        t["planes"] = box_walls(lo, hi)
+        out.append(t)
+    return out

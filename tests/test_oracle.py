@@ -437,3 +437,19 @@ def test_config1_runs_clean(oracle_mod):
     b = o.get_bodies()
     assert np.all(np.isfinite(b["vel"])) and st["n_contacts"] > 0
     assert np.allclose(np.linalg.norm(b["quat"], axis=1), 1.0, atol=1e-15)
+
+
+def test_batch_layout_and_sizes():
+    from paper_1501_05810_gb300 import scenes as S
+    b = S.batch_scenes(64, seed=2, n_lo=200, n_hi=20000)
+    sizes = np.array([len(s["radius"]) for s in b])
+    assert sizes.min() >= 200 and sizes.max() <= 20000
+    # log-uniform: the median sits near the geometric mean of the bounds
+    assert 600 < np.median(sizes) < 6000
+    boxes = [(np.array(s["params"]["box_lo"]), np.array(s["params"]["box_hi"])) for s in b]
+    for i in range(len(boxes)):
+        lo, hi = boxes[i]
+        assert np.all(b[i]["pos"] - b[i]["radius"][:, None] >= lo - 1e-9)
+        for j in range(i):
+            lo2, hi2 = boxes[j]
+            assert np.any(hi <= lo2) or np.any(hi2 <= lo)   # disjoint boxes
