@@ -56,7 +56,11 @@ typedef enum nbgs_status {
 } nbgs_status;
 
 enum { NBGS_FP64 = 0, NBGS_FP32 = 1 };           /* arithmetic of the sweeps      */
-enum { NBGS_WARM_NONE = 0, NBGS_WARM_PREV = 1 }; /* initial impulses of a solve   */
+enum {                                           /* initial impulses of a solve */
+    NBGS_WARM_NONE = 0,  /* zero (Alg. 1)                                                  */
+    NBGS_WARM_PREV = 1,  /* the previous step's impulse of the same contact (Sect. 5)     */
+    NBGS_WARM_MLP = 2    /* previous-step impulse; the network of nbgs_mlp_load for new contacts */
+};
 enum {                                           /* scheduling of the colour sweeps */
     NBGS_SOLVER_PERSISTENT = 0,  /* one cooperative launch per solve, grid barrier between colours */
     NBGS_SOLVER_PER_COLOUR = 1   /* one launch per colour and sweep                              */
@@ -86,7 +90,7 @@ typedef struct nbgs_params {
     double box_hi[3];
     int32_t periodic[3];  /* 1 = periodic along this axis (needs >= 3 grid cells)   */
     int32_t precision;    /* NBGS_FP64 or NBGS_FP32 (positions are always FP64)     */
-    int32_t warm_start;   /* NBGS_WARM_NONE or NBGS_WARM_PREV                       */
+    int32_t warm_start;   /* NBGS_WARM_*                                            */
     int32_t solver;       /* NBGS_SOLVER_*                                          */
     uint64_t colour_seed; /* priorities of the colouring: splitmix64(key ^ seed)    */
     int32_t contacts_per_body; /* contact buffer capacity per body, 0 = default 8   */
@@ -213,6 +217,60 @@ nbgs_status nbgs_get_scene_stats(nbgs_scene* scene, int32_t* sweeps_done, double
  * nbgs_colour_contacts.  Synchronises. */
 nbgs_status nbgs_autotune(nbgs_scene* scene, int32_t max_sweeps, double tol, int32_t* sweep_flags,
                           int32_t* blocks_per_sm);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start.  A 12 -> 64 -> 64 -> 64 -> 3 multilayer perceptron
+ * with SiLU activations predicts each contact's converged impulse from
+ * local features; the sweeps then start from it (Sect. 5: "any other
+ * initialization can be used") and the NBGS residual judges it.  The paper
+ * has no network; this is an extension of its warm start.
+ *
+ * Parameters: 9,347 FP32 values, for each layer W (out x in, row-major)
+ * then b (out).  Features (12, dimensionless) in the frame n, e2, e3 with
+ * e2 = -u_t / |u_t| along the free tangential relative velocity (the
+ * contact frame's t when that is ~0), e3 = n x e2:
+ *   u_n/v_ref, |u_t|/v_ref, (xi/dt)/v_ref, previous impulse in (n, e2, e3)
+ *   times w_n/v_ref (3), log(w_n), w_t/w_n, r_a, r_b, mu,
+ *   (contacts at j1 + contacts at j2)/12,
+ * with u the relative velocity after the gravity kick and before any
+ * impulse.  Output: the impulse in (n, e2, e3) times w_n/v_ref, formed as
+ * inputs 3..5 (the previous impulse) plus the layers' correction (a skip
+ * connection, added in FP32); it is projected onto the friction cone.  The
+ * prediction is used for contacts that had no previous-step impulse (new
+ * contacts); contacts with one keep it, as does a non-finite output.
+ * ------------------------------------------------------------------------ */
+
+/* Change the warm start of later solves (NBGS_WARM_*).  The previous-step
+ * impulses are kept whenever the mode is not NBGS_WARM_NONE. */
+nbgs_status nbgs_set_warm_start(nbgs_scene* scene, int32_t warm_start);
+
+/* Copy the network into the scene (host or device pointer).  Required
+ * before a solve with warm_start = NBGS_WARM_MLP. */
+nbgs_status nbgs_mlp_load(nbgs_scene* scene, const float* theta, int64_t count /* 9347 */);
+
+/* Features of the current contacts (after nbgs_colour_contacts, before the
+ * solve): 16 floats per contact in canonical order -- the 12 inputs, then
+ * cos and sin of the angle of e2 in the contact frame (t, o), w_n and v_ref,
+ * to express a solved impulse in the network's frame and scale.  *n_out =
+ * contact count; nothing is written when out is NULL or cap < count.
+ * Synchronises. */
+nbgs_status nbgs_mlp_features(nbgs_scene* scene, float* out, int64_t cap, int64_t* n_out);
+
+/* Network on n rows of X (n x 12, device) -> Y (n x 3, device): tensor-core
+ * evaluation, BF16 operands and FP32 accumulation, as in the warm start.
+ * theta: device pointer.  Asynchronous on stream. */
+nbgs_status nbgs_mlp_infer(const float* theta, const float* X, float* Y, int64_t n, void* stream);
+
+/* Training: loss L = sum((Y - T)^2) / (2 n) over n rows and its gradient
+ * (FP32, device pointers; grad: 9347 floats, loss: one double, both
+ * overwritten).  Asynchronous on stream. */
+nbgs_status nbgs_mlp_grad(const float* theta, const float* X, const float* T, int64_t n, float* grad,
+                          double* loss, void* stream);
+
+/* One Adam step (Kingma & Ba) with bias correction for step >= 1; theta,
+ * grad, m, v: count floats on the device.  Asynchronous on stream. */
+nbgs_status nbgs_mlp_adam(float* theta, const float* grad, float* m, float* v, int64_t count, float lr,
+                          float beta1, float beta2, float eps, int32_t step, void* stream);
 
 /* Copy the contacts in canonical order.  Any output may be NULL; at most cap
  * contacts are written; *n_out receives the count.  impulse = (p_n, p_t, p_o)

@@ -203,6 +203,7 @@ static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_des
     if (!(params->dt > 0.0) || !(params->tau > 0.0) || !(params->omega > 0.0) || !(params->mu >= 0.0))
         return NBGS_EINVAL;
     if (params->precision != NBGS_FP64 && params->precision != NBGS_FP32) return NBGS_EINVAL;
+    if (params->warm_start < NBGS_WARM_NONE || params->warm_start > NBGS_WARM_MLP) return NBGS_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (!(params->box_hi[a] > params->box_lo[a])) return NBGS_EINVAL;
     *out = nullptr;
@@ -388,7 +389,7 @@ void nbgs_destroy_scene(nbgs_scene* s)
                   s->keys[1], s->vals[0], s->vals[1], s->radix_hist, s->scan_tmp, s->cand, s->sph_cnt, s->row_cnt,
                   s->row_off, s->prev_row_off, s->deg, s->adj_off, s->col_count, s->col_off, s->info, s->dep,
                   s->prog, s->cstart, s->scene_of, s->scene_off, s->scene_box, s->scene_mu, s->scene_vmax,
-                  s->scene_vref, s->scene_rk, s->scene_done, s->scene_res};
+                  s->scene_vref, s->scene_rk, s->scene_done, s->scene_res, s->mlp_theta};
     for (void* p : ps) dev_free(s, p);
     free_contact_arrays(s);
     cudaStreamSynchronize(s->stream);
@@ -511,6 +512,14 @@ nbgs_status nbgs_step(nbgs_scene* s, int32_t max_sweeps, double tol, nbgs_step_s
         st->residual = s->hinfo->residual;
         st->v_ref = s->hinfo->v_ref;
     }
+    return NBGS_OK;
+}
+
+nbgs_status nbgs_set_warm_start(nbgs_scene* s, int32_t warm_start)
+{
+    NBGS_GUARD(s);
+    if (warm_start < NBGS_WARM_NONE || warm_start > NBGS_WARM_MLP) return fail(s, NBGS_EINVAL, "set_warm_start: mode");
+    s->prm.warm_start = warm_start;
     return NBGS_OK;
 }
 

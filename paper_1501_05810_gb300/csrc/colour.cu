@@ -207,13 +207,14 @@ __global__ void k_build_sweep(int64_t C, int64_t n, const uint32_t* __restrict__
             r.nz_ = make_double2(g.z, 0.0);
         }
         rec[s] = r;
-        double pn = 0.0, pt = 0.0, po = 0.0;
+        double pn = 0.0, pt = 0.0, po = 0.0, found = 0.0;
         if (warm) {
             const uint32_t e = prev_row_off[a + 1];
             for (uint32_t t = prev_row_off[a]; t < e; ++t) {
                 if (prev_j2[t] != b) continue;
                 const double4_32a P = prev_P[t];
                 const double mu = V.batch ? V.mu[V.scene_of[a]] : mu_all;
+                found = 1.0;
                 double tx, ty, tz, ox, oy, oz;
                 tangent_basis<double>(g.x, g.y, g.z, tx, ty, tz, ox, oy, oz);
                 pn = g.x * P.x + g.y * P.y + g.z * P.z;
@@ -236,7 +237,7 @@ __global__ void k_build_sweep(int64_t C, int64_t n, const uint32_t* __restrict__
         q.x = (R)pn;
         q.y = (R)pt;
         q.z = (R)po;
-        q.w = (R)0;
+        q.w = (R)found;   // 1: the contact existed in the previous step (read by the network warm start)
         p[s] = q;
     }
 }
@@ -295,7 +296,7 @@ nbgs_status run_colour(nbgs_scene* s)
         if (v0 != s->perm) std::swap(s->perm, s->perm_in);
         if (v0 != s->perm) return fail(s, NBGS_EINVAL, "colour: permutation buffer mix-up");
         s->colour_sorted = k0;
-        const int warm = (s->prm.warm_start == NBGS_WARM_PREV && s->have_prev) ? 1 : 0;
+        const int warm = (s->prm.warm_start != NBGS_WARM_NONE && s->have_prev) ? 1 : 0;
         if (s->fp32)
             k_build_sweep<float><<<gb, T, 0, st>>>(C, n, s->perm, s->cj1, s->cj2, s->cgeo, s->clev, s->prm.dt,
                                                    s->prm.beta, s->prm.mu, scene_view(s), warm, s->prev_row_off,

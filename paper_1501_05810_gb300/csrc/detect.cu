@@ -573,7 +573,7 @@ nbgs_status run_detect(nbgs_scene* s)
     cudaStream_t st = s->stream;
     if (s->timing) cudaEventRecord(s->ev[0], st);
     // keep the previous step's contacts for the warm start
-    if (s->prm.warm_start == NBGS_WARM_PREV && s->solved) {
+    if (s->prm.warm_start != NBGS_WARM_NONE && s->solved) {
         std::swap(s->row_off, s->prev_row_off);
         std::swap(s->cj2, s->prev_j2);
         std::swap(s->cworld, s->prev_P);

@@ -287,6 +287,8 @@ struct nbgs_scene {
     int2* dep = nullptr;           // kMaxColours x coop_blocks block windows [lo, hi] of each chunk
     int* prog = nullptr;           // coop_blocks: last sweep phase each block completed
     uint32_t* cstart = nullptr;    // kMaxColours x (coop_blocks + 1) chunk boundaries
+    // learned warm start
+    float* mlp_theta = nullptr;    // 9,347 FP32 parameters
     // sweep
     void* srec = nullptr;
     void* sp = nullptr;
@@ -324,6 +326,7 @@ nbgs_status run_colour(nbgs_scene* s);
 nbgs_status run_solve(nbgs_scene* s, int max_sweeps, double tol);
 nbgs_status run_integrate(nbgs_scene* s);
 nbgs_status run_final_residuals(nbgs_scene* s, nbgs_residuals* out);
+nbgs_status run_mlp_prologue(nbgs_scene* s, int apply, float* feat_out);
 nbgs_status run_set_bodies(nbgs_scene* s, const double* pos, const double* quat, const double* vel,
                            const double* angvel);
 nbgs_status run_get_bodies(nbgs_scene* s, double* pos, double* quat, double* vel, double* angvel);

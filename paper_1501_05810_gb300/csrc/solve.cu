@@ -819,7 +819,7 @@ static SolveArgs<R> make_args(nbgs_scene* s, int max_sweeps, double tol)
     A.gdt_norm = sqrt((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]) * s->prm.dt;
     A.max_sweeps = max_sweeps;
     A.tol = tol;
-    A.warm = (s->prm.warm_start == NBGS_WARM_PREV && s->have_prev) ? 1 : 0;
+    A.warm = ((s->prm.warm_start == NBGS_WARM_PREV && s->have_prev) || s->prm.warm_start == NBGS_WARM_MLP) ? 1 : 0;
     A.flags = s->prm.sweep_flags;
     A.prog = s->prog;
     A.dep = s->dep;
@@ -848,6 +848,10 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
         cudaMemsetAsync(s->scene_done, 0, s->n_scenes * sizeof(uint32_t), st);
         cudaMemsetAsync(s->scene_res, 0, s->n_scenes * sizeof(double), st);
         if (s->timing) s->phase_launches[2] += 1;
+    }
+    if (s->prm.warm_start == NBGS_WARM_MLP) {
+        nbgs_status rc = run_mlp_prologue(s, 1, nullptr);
+        if (rc != NBGS_OK) return rc;
     }
     if (s->prm.solver == NBGS_SOLVER_PERSISTENT) {
         if (A.C > 0) {

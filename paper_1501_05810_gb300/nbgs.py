@@ -25,7 +25,7 @@ _lib = C.CDLL(LIB_PATH)
 NBGS_OK, NBGS_EINVAL, NBGS_ENOMEM, NBGS_ECUDA, NBGS_ECAPACITY, NBGS_ENOTCONV, NBGS_ENAN, NBGS_ETIMEOUT = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ECAPACITY", "ENOTCONV", "ENAN", "ETIMEOUT"]
 NBGS_FP64, NBGS_FP32 = 0, 1
-NBGS_WARM_NONE, NBGS_WARM_PREV = 0, 1
+NBGS_WARM_NONE, NBGS_WARM_PREV, NBGS_WARM_MLP = 0, 1, 2
 NBGS_SOLVER_PERSISTENT, NBGS_SOLVER_PER_COLOUR = 0, 1
 NBGS_SWEEP_GLOBAL_SYNC, NBGS_SWEEP_TMA_STAGE = 1, 2
 
@@ -85,6 +85,12 @@ _SIG = {
     "nbgs_batch_step": [_vp, C.c_int32, C.c_double, _i32p, _dp],
     "nbgs_get_scene_stats": [_vp, _i32p, _dp],
     "nbgs_autotune": [_vp, C.c_int32, C.c_double, _i32p, _i32p],
+    "nbgs_mlp_load": [_vp, _vp, C.c_int64],
+    "nbgs_set_warm_start": [_vp, C.c_int32],
+    "nbgs_mlp_features": [_vp, _vp, C.c_int64, _i64p],
+    "nbgs_mlp_infer": [_vp, _vp, _vp, C.c_int64, _vp],
+    "nbgs_mlp_grad": [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp],
+    "nbgs_mlp_adam": [_vp, _vp, _vp, _vp, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int32, _vp],
     "nbgs_final_residuals_noalloc": [C.c_int64, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                      C.c_double, C.c_double, C.c_double, C.c_double, _vp, _vp],
 }
@@ -157,7 +163,7 @@ def make_params(p: dict, solver: str = "persistent") -> nbgs_params:
     o.box_hi[:] = list(p.get("box_hi", (1.0, 1.0, 1.0)))
     o.periodic[:] = [int(b) for b in p.get("periodic", (0, 0, 0))]
     o.precision = _PREC[p.get("precision", "fp64")]
-    o.warm_start = NBGS_WARM_PREV if p.get("warm_start", "none") == "prev" else NBGS_WARM_NONE
+    o.warm_start = {"none": NBGS_WARM_NONE, "prev": NBGS_WARM_PREV, "mlp": NBGS_WARM_MLP}[p.get("warm_start", "none")]
     o.solver = _SOLVER[p.get("solver", solver)]
     o.colour_seed = int(p.get("colour_seed", 0)) & 0xFFFFFFFFFFFFFFFF
     o.contacts_per_body = int(p.get("contacts_per_body", 0))
@@ -304,6 +310,18 @@ class Scene:
         r = nbgs_residuals()
         _call(self.h, "nbgs_final_residuals", C.byref(r))
         return {f: getattr(r, f) for f, _ in nbgs_residuals._fields_}
+
+    def mlp_load(self, theta):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        _call(self.h, "nbgs_mlp_load", _ptr(a), a.size)
+        self.sync()
+
+    def mlp_features(self) -> np.ndarray:
+        n = C.c_int64()
+        _call(self.h, "nbgs_mlp_features", None, 0, C.byref(n))
+        out = np.empty((n.value, 16), np.float32)
+        _call(self.h, "nbgs_mlp_features", _ptr(out), n.value, C.byref(n))
+        return out
 
     def enable_timing(self, on: bool = True):
         _call(self.h, "nbgs_enable_timing", 1 if on else 0)

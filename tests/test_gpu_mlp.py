@@ -1,0 +1,113 @@
+"""Learned warm start on the GPU against the FP64 references in oracle/:
+tensor-core inference (BF16 operands, FP32 accumulation), FP32 training
+gradients and Adam, and the per-contact feature map."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_1501_05810_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1501_05810_gb300 import build
+    build.build()
+    from paper_1501_05810_gb300 import nbgs, warmstart
+    return torch, nbgs, warmstart
+
+
+def _forward_bf16(theta, X):
+    """The FP64 reference with the GPU's roundings: BF16 weights, inputs and
+    hidden activations, exact sums."""
+    layers = omlp.unflatten(theta)
+    a = omlp.bf16_round(X)
+    for li, (W, b) in enumerate(layers):
+        z = a @ omlp.bf16_round(W).T + np.asarray(b, dtype=np.float32)
+        a = omlp.bf16_round(omlp.silu(z)) if li < 3 else z + X[:, 3:6]   # skip added in FP32
+    return a
+
+
+def test_tensor_core_inference_matches_reference(env):
+    torch, nb, ws = env
+    rng = np.random.default_rng(0)
+    theta = ws.init_params(3) + rng.normal(0, 0.02, ws.N_PARAMS).astype(np.float32)
+    for n in (1, 16, 17, 1000, 4099):          # partial warps and blocks
+        X = rng.normal(0, 1.0, (n, 12)).astype(np.float32)
+        Y = ws.infer(theta, X)
+        ref = _forward_bf16(theta.astype(np.float64), X.astype(np.float64))
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(Y - ref).max() <= 2e-2 * scale, (n, np.abs(Y - ref).max())
+        full = omlp.forward(theta.astype(np.float64), X.astype(np.float64))[0]
+        assert np.abs(Y - full).max() <= 6e-2 * scale     # BF16 versus exact
+
+
+def test_training_gradient_matches_reference(env):
+    torch, nb, ws = env
+    rng = np.random.default_rng(1)
+    theta = ws.init_params(4)
+    n = 1000                                             # 31 full tiles of 32 and a ragged one
+    X = rng.normal(size=(n, 12)).astype(np.float32)
+    T = rng.normal(size=(n, 3)).astype(np.float32)
+    dev = torch.device("cuda:0")
+    th, Xd, Td = (torch.as_tensor(a, device=dev) for a in (theta, X, T))
+    g = torch.zeros(ws.N_PARAMS, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    assert nb.library().nbgs_mlp_grad(th.data_ptr(), Xd.data_ptr(), Td.data_ptr(), n, g.data_ptr(), loss.data_ptr(),
+                                      torch.cuda.current_stream().cuda_stream) == nb.NBGS_OK
+    L, G = omlp.loss_and_grad(theta.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
+    assert abs(loss.item() - L) <= 1e-5 * L
+    gg = g.cpu().numpy()
+    assert np.abs(gg - G).max() <= 2e-4 * np.abs(G).max()
+    assert np.dot(gg, G) / (np.linalg.norm(gg) * np.linalg.norm(G)) > 1 - 1e-6
+
+
+def test_adam_step_matches_reference(env):
+    torch, nb, ws = env
+    rng = np.random.default_rng(2)
+    th0 = rng.normal(size=ws.N_PARAMS).astype(np.float32)
+    m0 = rng.normal(0, 0.1, ws.N_PARAMS).astype(np.float32)
+    v0 = np.abs(rng.normal(0, 0.1, ws.N_PARAMS)).astype(np.float32)
+    gr = rng.normal(size=ws.N_PARAMS).astype(np.float32)
+    dev = torch.device("cuda:0")
+    th, m, v, g = (torch.as_tensor(a, device=dev).clone() for a in (th0, m0, v0, gr))
+    assert nb.library().nbgs_mlp_adam(th.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), ws.N_PARAMS, 1e-3,
+                                      0.9, 0.999, 1e-8, 7, torch.cuda.current_stream().cuda_stream) == nb.NBGS_OK
+    rt, rm, rv = omlp.adam(th0.astype(np.float64), gr.astype(np.float64), m0.astype(np.float64),
+                           v0.astype(np.float64), 7, lr=1e-3)
+    assert np.allclose(th.cpu().numpy(), rt, atol=1e-6) and np.allclose(m.cpu().numpy(), rm, atol=1e-6)
+
+
+def test_features_match_reference(env, oracle_mod):
+    torch, nb, ws = env
+    sc = scenes.lattice_box(seed=5, per_side=5, spacing=1.02, vel_sigma=1.0, dt=2e-2, tau=0.01, warm_start="prev")
+    sc["angvel"] = np.random.default_rng(6).normal(0, 1.0, sc["vel"].shape)
+    g = nb.Scene(sc)
+    o = oracle_mod.OracleScene(sc)
+    g.step(30)
+    o.step(30)
+    prev = o.get_contacts()
+    start = o.get_bodies()
+    o.detect_contacts()
+    co = o.get_contacts()
+    g.set_bodies(start["pos"], start["quat"], start["vel"], start["angvel"])   # same start, FP rounding aside
+    # set_bodies drops the previous-step impulses of the GPU scene: rerun the
+    # previous step there from the oracle's previous start instead
+    g2 = nb.Scene(sc)
+    g2.step(30)
+    g2.detect_contacts()
+    g2.colour_contacts()
+    F = g2.mlp_features()
+    r, rho = sc["radius"], sc["density"]
+    mass = rho * 4.0 / 3.0 * math.pi * r ** 3
+    vref = max(np.linalg.norm(start["vel"], axis=1).max(), 9.81 * sc["params"]["dt"], 1e-12)
+    ref = omlp.contact_features(co, start, r, 1.0 / mass, 1.0 / (0.4 * mass * r * r), sc["params"], vref, prev)
+    assert len(F) == len(ref) > 100
+    scale = np.maximum(1.0, np.abs(ref).max(0))
+    assert np.all(np.abs(F - ref).max(0) <= 1e-5 * scale), np.abs(F - ref).max(0) / scale
