@@ -47,9 +47,24 @@ def workload(name: str):
         sc = scenes.config1(0)
         return sc, "1,000 spheres in a 10.5^3 walled box, FP64, mu=0.5, dt=1e-3, 50 sweeps"
     if name == "gas":
-        sc = scenes.granular_gas(cells=int(os.environ.get("NBGS_GAS_CELLS", "196")), seed=0, precision="fp32")
-        return sc, f"granular gas, {len(sc['radius']):,} spheres, FCC at phi=0.5, periodic, FP32 sweeps"
+        sc = scenes.granular_gas(cells=196, seed=0, precision="fp32", contacts_per_body=2)
+        return sc, (f"dense granular gas, {len(sc['radius']):,} spheres r~U(0.45,0.55), FCC start at phi=0.5, "
+                    "triply periodic, v~N(0,1), mu=0.3, dt=1e-4, 50 sweeps, FP32 sweeps, FP64 positions")
+    if name == "ramp":
+        sc = scenes.hcp_packing(100, 100, 100, dt=1e-5, tau=0.005, mu=0.85, tilt_deg=30.0, v0=0.1, omega=0.75,
+                                precision="fp32")
+        return sc, ("HCP ramp (Sect. 7.2.2 shape): 1,000,000 spheres r=0.5, periodic x,y, walls z, gravity tilted "
+                    "30 deg, mu=0.85, v0=0.1 downhill, omega=0.75, dt=1e-5, 100 sweeps, FP32 sweeps")
+    if name == "batch":
+        bs = scenes.batch_scenes(4096, seed=0, precision="fp32", contacts_per_body=4)
+        return bs, (f"4,096 walled-box scenes, {sum(len(b['radius']) for b in bs):,} spheres in total, sizes "
+                    "log-uniform in [200, 20000], r~U(0.4,0.6), mu~U(0.2,0.8), settling under gravity, dt=5e-4, "
+                    "residual 1e-6 per scene (max 100 sweeps), one persistent sweep launch for all scenes")
     raise SystemExit(f"unknown workload {name}")
+
+
+# sweeps and tolerance per workload: (max_sweeps, tol)
+SOLVE = {"dense1m": (100, 1e-6), "config1": (50, 0.0), "gas": (50, 0.0), "ramp": (100, 0.0), "batch": (100, 1e-6)}
 
 
 def read_peaks():
@@ -204,6 +219,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--sweep-flags", type=int, default=None, help="nbgs_params.sweep_flags override")
+    ap.add_argument("--warm", default=None, choices=["none", "prev"], help="warm start of the solves")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -221,15 +237,24 @@ def main():
 
     from paper_1501_05810_gb300 import nbgs
     sc, desc = workload(args.workload)
+    batch = isinstance(sc, list)
+    first = sc[0] if batch else sc
     if args.sweep_flags is not None:
-        sc["params"]["sweep_flags"] = args.sweep_flags
-    prec = sc["params"].get("precision", "fp64")
-    n = len(sc["radius"])
+        for x in (sc if batch else [sc]):
+            x["params"]["sweep_flags"] = args.sweep_flags
+    if args.warm is not None:
+        for x in (sc if batch else [sc]):
+            x["params"]["warm_start"] = args.warm
+        desc += f", warm start {args.warm}"
+    prec = first["params"].get("precision", "fp64")
     stream = torch.cuda.Stream(device=local)
     with torch.cuda.stream(stream):
-        g = nbgs.Scene(sc, device=f"cuda:{local}", stream=stream)
-        sweeps = 50 if args.workload == "config1" else SWEEPS
-        tol = 0.0 if args.workload == "config1" else TOL
+        if batch:
+            g = nbgs.BatchScene(sc, device=f"cuda:{local}", stream=stream)
+        else:
+            g = nbgs.Scene(sc, device=f"cuda:{local}", stream=stream)
+        n = g.n
+        sweeps, tol = SOLVE[args.workload]
         for _ in range(max(args.warmup, 0)):
             g.step(sweeps, tol)
         n_ss, n_sw, colour_sizes = count_contact_kinds(g, n)

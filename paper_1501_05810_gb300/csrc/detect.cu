@@ -12,6 +12,8 @@
 //   scan            contacts per body -> CSR offsets by j1
 //   k_write         canonical contact records (n, xi, lever lengths)
 //                   for sphere-sphere and sphere-wall pairs, eq. (contactpos)
+#include <algorithm>
+#include <cmath>
 #include <utility>
 
 #include "nbgs_internal.cuh"
@@ -256,6 +258,9 @@ struct GridArgs {
     int periodic[3];
     int dims_max[3];
     double r_max, dt, tau;
+    float Lf[3];         // box extents in FP32
+    float margin;        // FP32 pre-filter margin: 1e-4 + 1e-6 max(L)
+    double pos_err;      // bound on the error of an FP32 relative position (2^-22 max(L))
 };
 
 __device__ __forceinline__ double norm_exact(double x, double y, double z)
@@ -265,19 +270,23 @@ __device__ __forceinline__ double norm_exact(double x, double y, double z)
 
 template <class R>
 __global__ void k_hull(int64_t n, const R4<R>* __restrict__ vel, const double4_32a* __restrict__ pos_r, double dt,
-                       double tau, double* __restrict__ hull, DevInfo* info, const uint32_t* __restrict__ scene_of,
-                       unsigned long long* __restrict__ scene_vmax)
+                       double tau, double* __restrict__ hull, float4* __restrict__ p32, GridArgs g, DevInfo* info,
+                       const uint32_t* __restrict__ scene_of, unsigned long long* __restrict__ scene_vmax)
 {
     double hmax = 0.0, vmax = 0.0;
     bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const R4<R> v = vel[2 * i], w = vel[2 * i + 1];
-        const double r = pos_r[i].w;
+        const double4_32a x = pos_r[i];
+        const double r = x.w;
         const double nv = norm_exact((double)v.x, (double)v.y, (double)v.z);
         const double nw = norm_exact((double)w.x, (double)w.y, (double)w.z);
         // eq. (expansionradius): h = dt (|v| + |w| r) + tau
         const double h = xadd(xmul(dt, xadd(nv, xmul(nw, r))), tau);
         hull[i] = h;
+        // FP32 relative position and reach r + h: cell keys and the narrow phase's
+        // conservative pre-filter run on these (FP64 throughput is scarce)
+        p32[i] = make_float4((float)(x.x - g.lo[0]), (float)(x.y - g.lo[1]), (float)(x.z - g.lo[2]), (float)(r + h));
         if (!(h <= 1e300)) bad = true;
         if (scene_of) {   // per-scene v_ref; the filter only saves atomics
             unsigned long long* dst = scene_vmax + scene_of[i];
@@ -313,8 +322,10 @@ __global__ void k_hull(int64_t n, const R4<R>* __restrict__ vel, const double4_3
 __global__ void k_grid_setup(GridArgs g, DevInfo* info)
 {
     const double hmax = __longlong_as_double((long long)info->hmax_bits);
-    // any kept pair has d <= r_a + r_b + h_a + h_b <= 2 (r_max + h_max)
-    const double need = 2.0 * (g.r_max + hmax) * (1.0 + 1e-9) + 1e-300;
+    // any kept pair has d <= r_a + r_b + h_a + h_b <= 2 (r_max + h_max); the
+    // cell keys come from FP32 positions with error <= pos_err, so a cell at
+    // least need + 4 pos_err wide keeps every such pair in adjacent cells
+    const double need = 2.0 * (g.r_max + hmax) * (1.0 + 1e-9) + 4.0 * g.pos_err + 1e-300;
     uint32_t ncells = 1;
     for (int a = 0; a < 3; ++a) {
         const double L = g.hi[a] - g.lo[a];
@@ -323,6 +334,7 @@ __global__ void k_grid_setup(GridArgs g, DevInfo* info)
         if (g.periodic[a] && d < 3) atomicOr(&info->err, kErrGrid);
         info->dims[a] = d;
         info->cell_w[a] = L / d;
+        info->inv_wf[a] = (float)(d / L);
         ncells *= (uint32_t)d;
     }
     info->ncells = ncells;
@@ -337,23 +349,20 @@ __global__ void k_clear_cells(uint32_t* __restrict__ cs, uint32_t* __restrict__ 
     }
 }
 
-__device__ __forceinline__ int cell_coord(double x, double lo, double w, int d)
+__device__ __forceinline__ int cell_coord(float x, float inv_w, int d)
 {
-    double f = floor((x - lo) / w);
-    int c = f < 0.0 ? 0 : (f > (double)(d - 1) ? d - 1 : (int)f);
-    return c;
+    const float f = floorf(x * inv_w);
+    return f < 0.f ? 0 : (f > (float)(d - 1) ? d - 1 : (int)f);
 }
 
-__global__ void k_cell_keys(int64_t n, const double4_32a* __restrict__ pos_r, GridArgs g, const DevInfo* __restrict__ info,
+__global__ void k_cell_keys(int64_t n, const float4* __restrict__ p32, const DevInfo* __restrict__ info,
                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
 {
     const int d0 = info->dims[0], d1 = info->dims[1], d2 = info->dims[2];
-    const double w0 = info->cell_w[0], w1 = info->cell_w[1], w2 = info->cell_w[2];
+    const float i0 = info->inv_wf[0], i1 = info->inv_wf[1], i2 = info->inv_wf[2];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double4_32a p = pos_r[i];
-        const int cx = cell_coord(p.x, g.lo[0], w0, d0);
-        const int cy = cell_coord(p.y, g.lo[1], w1, d1);
-        const int cz = cell_coord(p.z, g.lo[2], w2, d2);
+        const float4 p = p32[i];
+        const int cx = cell_coord(p.x, i0, d0), cy = cell_coord(p.y, i1, d1), cz = cell_coord(p.z, i2, d2);
         keys[i] = ((uint32_t)cz * (uint32_t)d1 + (uint32_t)cy) * (uint32_t)d0 + (uint32_t)cx;
         vals[i] = (uint32_t)i;
     }
@@ -392,7 +401,8 @@ __device__ __forceinline__ bool wall_kept(const double nrm[3], double c, double4
 // partners j > i from the 27 neighbour cells, sorted ascending; wall count.
 __global__ void __launch_bounds__(128)
 k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ svals,
-         const double4_32a* __restrict__ pos_r, const double* __restrict__ hull, const uint32_t* __restrict__ cs,
+         const double4_32a* __restrict__ pos_r, const double* __restrict__ hull, const float4* __restrict__ p32,
+         const uint32_t* __restrict__ cs,
          const uint32_t* __restrict__ ce, GridArgs g, Planes planes, SceneView V, DevInfo* info,
          uint32_t* __restrict__ cand, uint32_t* __restrict__ sph_cnt, uint32_t* __restrict__ row_cnt)
 {
@@ -406,6 +416,7 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
         const int cz = (int)(key / ((uint32_t)d0 * (uint32_t)d1));
         const double4_32a pi = pos_r[i];
         const double hi_ = hull[i];
+        const float4 qi = p32[i];
         const uint32_t si = V.batch ? V.scene_of[i] : 0u;
         uint32_t list[kCandCap];
         int cnt = 0;
@@ -433,6 +444,23 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
                         const uint32_t j = svals[t];
                         if (j <= i) continue;
                         if (V.batch && V.scene_of[j] != si) continue;   // scenes never touch
+                        // Conservative FP32 pre-filter (FP64 throughput is scarce on this
+                        // GPU).  R = r_a + h_a + r_b + h_b bounds d for every kept pair.
+                        // The FP32 relative positions are off by at most pos_err per
+                        // coordinate, the minimum image adds an ulp of L, so the FP32
+                        // distance is within 1e-6 max(L) of d; the FP32 square and reach
+                        // add relative errors below 4e-7 and 1.2e-7, covered by the extra
+                        // 1e-4 while R < ~385.  So (fl(R) + margin)^2 >= fl(d^2) for every
+                        // kept pair; only the pairs that pass take the exact FP64 test.
+                        {
+                            const float4 qj = p32[j];
+                            float fx = qi.x - qj.x, fy = qi.y - qj.y, fz = qi.z - qj.z;
+                            if (g.periodic[0]) fx = fx > 0.5f * g.Lf[0] ? fx - g.Lf[0] : (fx < -0.5f * g.Lf[0] ? fx + g.Lf[0] : fx);
+                            if (g.periodic[1]) fy = fy > 0.5f * g.Lf[1] ? fy - g.Lf[1] : (fy < -0.5f * g.Lf[1] ? fy + g.Lf[1] : fy);
+                            if (g.periodic[2]) fz = fz > 0.5f * g.Lf[2] ? fz - g.Lf[2] : (fz < -0.5f * g.Lf[2] ? fz + g.Lf[2] : fz);
+                            const float rr = qi.w + qj.w + g.margin;
+                            if (fx * fx + fy * fy + fz * fz > rr * rr) continue;
+                        }
                         const double4_32a pj = pos_r[j];
                         const double dx3 = min_image(xsub(pi.x, pj.x), g.periodic[0], L0);
                         const double dy3 = min_image(xsub(pi.y, pj.y), g.periodic[1], L1);
@@ -562,6 +590,13 @@ static GridArgs grid_args(const nbgs_scene* s)
     g.r_max = s->r_max;
     g.dt = s->prm.dt;
     g.tau = s->prm.tau;
+    double lmax = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        g.Lf[a] = (float)(g.hi[a] - g.lo[a]);
+        lmax = std::max(lmax, g.hi[a] - g.lo[a]);
+    }
+    g.margin = (float)(1e-4 + 1e-6 * lmax);
+    g.pos_err = std::ldexp(lmax, -22);
     return g;
 }
 
@@ -596,20 +631,20 @@ nbgs_status run_detect(nbgs_scene* s)
     const int gb = grid_for(n, T, 8, s->num_sms);
     if (s->batch) cudaMemsetAsync(s->scene_vmax, 0, s->n_scenes * sizeof(unsigned long long), st);
     if (s->fp32)
-        k_hull<float><<<gb, T, 0, st>>>(n, (const float4*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hull, s->info,
-                                        s->scene_of, s->scene_vmax);
+        k_hull<float><<<gb, T, 0, st>>>(n, (const float4*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hull, s->p32,
+                                        g, s->info, s->scene_of, s->scene_vmax);
     else
         k_hull<double><<<gb, T, 0, st>>>(n, (const double4_32a*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hull,
-                                         s->info, s->scene_of, s->scene_vmax);
+                                         s->p32, g, s->info, s->scene_of, s->scene_vmax);
     k_grid_setup<<<1, 1, 0, st>>>(g, s->info);
     k_clear_cells<<<grid_for(s->max_cells, T, 8, s->num_sms), T, 0, st>>>(s->cell_start, s->cell_end, s->info);
-    k_cell_keys<<<gb, T, 0, st>>>(n, s->pos_r, g, s->info, s->keys[0], s->vals[0]);
+    k_cell_keys<<<gb, T, 0, st>>>(n, s->p32, s->info, s->keys[0], s->vals[0]);
     if (s->timing) s->phase_launches[0] += 4;
     nbgs_status rc = radix_sort_pairs(s, s->keys[0], s->vals[0], s->keys[1], s->vals[1], n, s->key_bits);
     if (rc != NBGS_OK) return rc;
     k_cell_ranges<<<gb, T, 0, st>>>(n, s->keys[0], s->cell_start, s->cell_end);
     k_narrow<<<grid_for(n, 128, 16, s->num_sms), 128, 0, st>>>(n, s->keys[0], s->vals[0], s->pos_r, s->hull,
-                                                                 s->cell_start, s->cell_end, g, s->planes,
+                                                                 s->p32, s->cell_start, s->cell_end, g, s->planes,
                                                                  scene_view(s), s->info, s->cand, s->sph_cnt,
                                                                  s->row_cnt);
     rc = exclusive_scan_u32(s, s->row_cnt, s->row_off, n, &s->info->n_contacts);

@@ -21,31 +21,35 @@ __global__ void k_integrate(int64_t n, double4_32a* __restrict__ pos_r, double4_
         x.y += dt * (double)v.y;
         x.z += dt * (double)v.z;
         double4_32a q = quat[i];
-        const double wx = w.x, wy = w.y, wz = w.z;
-        const double dw = 0.5 * (-q.y * wx - q.z * wy - q.w * wz);
-        const double dx = 0.5 * (q.x * wx + q.w * wy - q.z * wz);
-        const double dy = 0.5 * (-q.w * wx + q.x * wy + q.y * wz);
-        const double dz = 0.5 * (q.z * wx - q.y * wy + q.x * wz);
-        q.x += dt * dw;
-        q.y += dt * dx;
-        q.z += dt * dy;
-        q.w += dt * dz;
-        const double inv = 1.0 / sqrt(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-        q.x *= inv;
-        q.y *= inv;
-        q.z *= inv;
-        q.w *= inv;
-        if (periodic.x) {
+        {
+            // quaternion update in the sweep precision (FP64 is scarce on this
+            // GPU; orientations of spheres never feed back into the dynamics)
+            using Q = R;
+            Q qw = (Q)q.x, qx = (Q)q.y, qy = (Q)q.z, qz = (Q)q.w;
+            const Q wx = w.x, wy = w.y, wz = w.z, hdt = (Q)(0.5 * dt);
+            const Q dw = -qx * wx - qy * wy - qz * wz;
+            const Q dx = qw * wx + qz * wy - qy * wz;
+            const Q dy = -qz * wx + qw * wy + qx * wz;
+            const Q dz = qy * wx - qx * wy + qw * wz;
+            qw += hdt * dw;
+            qx += hdt * dx;
+            qy += hdt * dy;
+            qz += hdt * dz;
+            const Q inv = Q(1) / sqrt(qw * qw + qx * qx + qy * qy + qz * qz);
+            q = make_double4_32a(qw * inv, qx * inv, qy * inv, qz * inv);
+        }
+        // periodic wrap into [lo, hi); only bodies that left the box pay for fmod
+        if (periodic.x && !(x.x >= lo.x && x.x < lo.x + L.x)) {
             double s = fmod(x.x - lo.x, L.x);
             if (s < 0.0) s += L.x;
             x.x = lo.x + s;
         }
-        if (periodic.y) {
+        if (periodic.y && !(x.y >= lo.y && x.y < lo.y + L.y)) {
             double s = fmod(x.y - lo.y, L.y);
             if (s < 0.0) s += L.y;
             x.y = lo.y + s;
         }
-        if (periodic.z) {
+        if (periodic.z && !(x.z >= lo.z && x.z < lo.z + L.z)) {
             double s = fmod(x.z - lo.z, L.z);
             if (s < 0.0) s += L.z;
             x.z = lo.z + s;

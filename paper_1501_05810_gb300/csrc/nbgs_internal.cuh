@@ -92,6 +92,7 @@ struct DevInfo {
     unsigned long long hmax_bits;   // max hull radius (bits of a non-negative double)
     unsigned long long vmax_bits;   // max |v_i| at the start of the step
     double cell_w[3];
+    float inv_wf[3];                 // 1 / cell width, FP32 (cell keys from the FP32 positions)
     int dims[3];
     uint32_t ncells;
     uint32_t n_contacts;
@@ -237,6 +238,7 @@ struct nbgs_scene {
     double4_32a* quat = nullptr;
     void* vel = nullptr;          // R4[2n]
     double* hull = nullptr;
+    float4* p32 = nullptr;        // (x - lo, y - lo, z - lo, r + h) in FP32: cell keys and the narrow-phase pre-filter
     uint8_t* finite = nullptr;    // body takes impulses (1/m > 0 or 1/I > 0)
     double* stage = nullptr;      // 13 n doubles for state transfer
     // grid
