@@ -306,7 +306,7 @@ constexpr int kPersistThreads = 256;
 
 // Shared-memory stage of one colour chunk: CAP records and impulses, 48 KiB.
 template <class R> struct Stage {
-    static constexpr int CAP = sizeof(R) == 4 ? 1024 : 512;
+    static constexpr int CAP = sizeof(R) == 4 ? 256 : 128;
     static constexpr int BYTES = CAP * (int)(sizeof(SweepRec<R>) + sizeof(R4<R>));
 };
 
@@ -541,7 +541,11 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
         R rmax = R(0);
         for (int c = 0; c < ncol; ++c) {
             const int g = k * ncol + c;
-            if (local && !wait_deps(A.prog, A.dep[c * (int)nb + blockIdx.x], g, A.info, &s_ok)) {
+            int64_t cb0, cb1;
+            colour_chunk(A.cstart, c, cb0, cb1);
+            // an empty chunk touches no body: nothing to wait for (this block's
+            // own earlier phases are complete, which is all a neighbour needs)
+            if (local && cb1 > cb0 && !wait_deps(A.prog, A.dep[c * (int)nb + blockIdx.x], g, A.info, &s_ok)) {
                 ok = false;
                 break;
             }
