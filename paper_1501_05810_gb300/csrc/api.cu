@@ -64,6 +64,7 @@ static bool alloc_contact_arrays(nbgs_scene* s, int64_t cap)
               take(s, s->cimp, c) && take(s, s->cworld, c) && take(s, s->prev_j2, c) && take(s, s->prev_P, c) &&
               take(s, s->adj, 2 * c) && take(s, s->cstate, c) && take(s, s->cprio, c) && take(s, s->wl[0], c) &&
               take(s, s->wl[1], c) && take(s, s->colour_key, c) && take(s, s->colour_key2, c) &&
+              take(s, s->pmask, c) && take(s, s->blocker, c) && take(s, s->cinfo, c) &&
               take(s, s->perm, c) && take(s, s->perm_in, c);
     if (!ok) return false;
     s->srec = dev_alloc(s, c * rec_bytes(s));
@@ -74,7 +75,8 @@ static bool alloc_contact_arrays(nbgs_scene* s, int64_t cap)
 static void free_contact_arrays(nbgs_scene* s)
 {
     void* ps[] = {s->cj1, s->cj2, s->cgeo, s->clev, s->cimp, s->cworld, s->prev_j2, s->prev_P, s->adj, s->cstate,
-                  s->cprio, s->wl[0], s->wl[1], s->colour_key, s->colour_key2, s->perm, s->perm_in, s->srec, s->sp};
+                  s->cprio, s->wl[0], s->wl[1], s->colour_key, s->colour_key2, s->perm, s->perm_in, s->srec, s->sp,
+                  s->pmask, s->blocker, s->cinfo};
     for (void* p : ps) dev_free(s, p);
 }
 

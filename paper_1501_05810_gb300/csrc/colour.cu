@@ -7,6 +7,7 @@
 //
 //   k_colour_init   priority splitmix64(key ^ seed), body degrees
 //   scan + k_adj_fill  body -> contact incidence lists (finite bodies only)
+//   k_pred_masks    per contact: which incident contacts beat it
 //   k_jp_round      Jones-Plassmann round: an uncoloured contact whose
 //                   priority beats every uncoloured neighbour takes the
 //                   smallest colour unused by its coloured neighbours; this
@@ -73,69 +74,189 @@ __device__ __forceinline__ bool beats(uint64_t pd, uint32_t d, uint64_t pc, uint
     return kd < kc;
 }
 
-// One Jones-Plassmann round.  cstate[d] = (round << 8) | colour, or
-// kUncoloured.  A neighbour stamped with the current round counts as
-// uncoloured here (it is being coloured concurrently and, being a local
-// maximum, necessarily beats c).
-__global__ void k_jp_round(uint32_t round, int64_t n, const uint32_t* __restrict__ wl_in,
-                           const uint32_t* __restrict__ cnt_in, uint32_t* __restrict__ wl_out,
-                           uint32_t* __restrict__ cnt_out, const uint32_t* __restrict__ cj1,
-                           const uint32_t* __restrict__ cj2, const uint8_t* __restrict__ finite,
-                           const uint32_t* __restrict__ adj_off, const uint32_t* __restrict__ adj,
-                           const uint64_t* __restrict__ prio, uint32_t* cstate, DevInfo* info)
+// Predecessor masks: bit j of pmask[c] is set when entry j of the
+// concatenated incidence lists of c's bodies (first body, then second) holds
+// a contact that beats c.  blocker[c] = the weakest such contact (kUncoloured:
+// none), cinfo[c] = (start, length) of the two lists.  pmask = ~0 marks a
+// contact with more than 64 entries, which compares priorities whenever it
+// is examined.
+__global__ void k_pred_masks(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
+                             const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
+                             const uint32_t* __restrict__ adj, const uint64_t* __restrict__ prio,
+                             uint64_t* __restrict__ pmask, uint32_t* __restrict__ blocker, uint4* __restrict__ cinfo)
 {
-    const uint32_t m = *cnt_in;
-    const int lane = threadIdx.x & 31;
-    for (uint32_t base = blockIdx.x * blockDim.x; base < m; base += gridDim.x * blockDim.x) {
-        const uint32_t k = base + threadIdx.x;
-        bool pending = false;
-        if (k < m) {
-            const uint32_t c = wl_in[k];
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t a = cj1[c], b = cj2[c];
+        const bool fa = finite[a], fb = b < n && finite[b];
+        const uint32_t a0 = fa ? adj_off[a] : 0, na = fa ? adj_off[a + 1] - a0 : 0;
+        const uint32_t b0 = fb ? adj_off[b] : 0, nb = fb ? adj_off[b + 1] - b0 : 0;
+        uint64_t m = 0;
+        uint32_t first = kUncoloured;
+        if (na + nb > 64) {
+            m = ~0ull;
+        } else {
             const uint64_t pc = prio[c];
-            uint64_t used0 = 0, used1 = 0;
-            bool local_max = true;
-            const uint32_t bodies[2] = {cj1[c], cj2[c]};
-            for (int e = 0; e < 2 && local_max; ++e) {
-                const uint32_t b = bodies[e];
-                if (b >= n || !finite[b]) continue;
-                const uint32_t end = adj_off[b + 1];
-                for (uint32_t t = adj_off[b]; t < end; ++t) {
-                    const uint32_t d = adj[t];
-                    if (d == c) continue;
-                    const uint32_t sd = cstate[d];
-                    if (sd == kUncoloured || (sd >> 8) >= round) {
-                        if (beats(prio[d], d, pc, c, cj1, cj2)) {
-                            local_max = false;
-                            break;
-                        }
-                    } else {
-                        const uint32_t col = sd & 0xFFu;
-                        if (col < 64) used0 |= 1ull << col;
-                        else used1 |= 1ull << (col - 64);
+            uint64_t pfirst = 0;
+            for (uint32_t j = 0; j < na + nb; ++j) {
+                const uint32_t d = j < na ? adj[a0 + j] : adj[b0 + j - na];
+                const uint64_t pd = prio[d];
+                if (d != (uint32_t)c && beats(pd, d, pc, (uint32_t)c, cj1, cj2)) {
+                    if (!m || beats(pfirst, first, pd, d, cj1, cj2)) {
+                        first = d;
+                        pfirst = pd;
                     }
+                    m |= 1ull << j;
                 }
             }
-            if (local_max) {
-                uint32_t col;
-                if (~used0) col = __ffsll((long long)~used0) - 1;
-                else if (~used1) col = 64 + __ffsll((long long)~used1) - 1;
-                else {
-                    atomicOr(&info->err, kErrColours);
-                    col = kMaxColours - 1;
-                }
-                cstate[c] = (round << 8) | col;
-            } else {
-                pending = true;
+        }
+        pmask[c] = m;
+        blocker[c] = first;
+        cinfo[c] = make_uint4(a0, na, b0, nb);
+    }
+}
+
+// cstate[d] = (round << 8) | colour, or kUncoloured.  Within round r a
+// contact coloured in round r still counts as uncoloured, so every decision
+// of the round sees the state at its start.
+__device__ __forceinline__ bool uncoloured_now(uint32_t sd, uint32_t round)
+{
+    return sd == kUncoloured || (sd >> 8) >= round;
+}
+
+// One warp examines contact c: its lanes cover the incidence entries.  If a
+// predecessor is still uncoloured, c waits (its blocker becomes the
+// uncoloured predecessor of lowest priority); otherwise c is a local maximum and takes the smallest
+// colour none of its predecessors has (every coloured neighbour is a
+// predecessor: the others wait for c).  Returns whether c waits.
+__device__ bool jp_examine(uint32_t c, uint32_t round, int lane, const uint32_t* __restrict__ cj1,
+                           const uint32_t* __restrict__ cj2, const uint32_t* __restrict__ adj,
+                           const uint64_t* __restrict__ prio, const uint64_t* __restrict__ pmask,
+                           uint32_t* __restrict__ blocker, const uint4* __restrict__ cinfo, uint32_t* cstate,
+                           DevInfo* info)
+{
+    const uint4 ci = cinfo[c];
+    const uint32_t len = ci.y + ci.w;
+    const uint64_t pm = pmask[c];
+    const bool slow = pm == ~0ull;
+    const uint64_t pc = slow ? prio[c] : 0;
+    uint32_t used[4] = {0u, 0u, 0u, 0u};
+    for (uint32_t j0 = 0; j0 < len; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        bool pred = false, unc = false;
+        uint32_t d = 0, sd = kUncoloured;
+        if (j < len) {
+            d = j < ci.y ? adj[ci.x + j] : adj[ci.z + j - ci.y];
+            pred = slow ? (d != c && beats(prio[d], d, pc, c, cj1, cj2)) : ((pm >> j) & 1ull) != 0;
+            if (pred) {
+                sd = cstate[d];
+                unc = uncoloured_now(sd, round);
             }
         }
-        // warp-aggregated append of the contacts left for the next round
-        const uint32_t mask = __ballot_sync(0xffffffffu, pending);
-        if (mask) {
-            uint32_t basew = 0;
-            if (lane == 0) basew = atomicAdd(cnt_out, (uint32_t)__popc(mask));
-            basew = __shfl_sync(0xffffffffu, basew, 0);
-            if (pending) wl_out[basew + __popc(mask & ((1u << lane) - 1u))] = wl_in[k];
+        const uint32_t wait = __ballot_sync(0xffffffffu, pred && unc);
+        if (wait) {
+            if (!slow) {
+                // wait for the weakest uncoloured predecessor: it tends to be
+                // coloured last, so c is examined again fewer times
+                const uint64_t pd = (pred && unc) ? prio[d] : ~0ull;
+                uint64_t pmin = pd;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const uint64_t y = __shfl_xor_sync(0xffffffffu, pmin, o);
+                    pmin = y < pmin ? y : pmin;
+                }
+                const uint32_t at = __ballot_sync(0xffffffffu, (pred && unc) && pd == pmin);
+                if (lane == __ffs(at) - 1) blocker[c] = d;
+            }
+            return true;
         }
+        if (pred) {
+            const uint32_t col = sd & 0xFFu;
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                if ((col >> 5) == (uint32_t)w) used[w] |= 1u << (col & 31u);
+        }
+    }
+    uint32_t col = kMaxColours;
+#pragma unroll
+    for (int w = 3; w >= 0; --w) {
+        const uint32_t u = __reduce_or_sync(0xffffffffu, used[w]);
+        if (~u) col = 32u * w + (__ffs(~u) - 1);
+    }
+    if (lane == 0) {
+        if (col >= kMaxColours) {
+            atomicOr(&info->err, kErrColours);
+            col = kMaxColours - 1;
+        }
+        cstate[c] = (round << 8) | col;
+    }
+    return false;
+}
+
+// Appends val to list for every lane with pred set (one shared-memory
+// counter update per warp).
+__device__ __forceinline__ void warp_push(bool pred, uint32_t val, uint32_t* list, uint32_t* count, int lane)
+{
+    const uint32_t mask = __ballot_sync(0xffffffffu, pred);
+    uint32_t b = 0;
+    if (lane == 0 && mask) b = atomicAdd(count, (uint32_t)__popc(mask));
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if (pred) list[b + __popc(mask & ((1u << lane) - 1u))] = val;
+}
+
+// One Jones-Plassmann round over the worklist, a tile of kJpItems per thread
+// at a time.  Phase 1, a thread per contact: a contact whose remembered
+// blocker is still uncoloured waits (two loads).  Phase 2, a warp per
+// remaining contact (jp_examine).  The waiting contacts of the tile go to
+// wl_out with one global counter update.
+constexpr int kJpThreads = 256;
+constexpr int kJpItems = 4;
+
+__global__ void __launch_bounds__(kJpThreads) k_jp_round(uint32_t round, const uint32_t* __restrict__ wl_in,
+                                  const uint32_t* __restrict__ cnt_in, uint32_t* __restrict__ wl_out,
+                                  uint32_t* __restrict__ cnt_out, const uint32_t* __restrict__ cj1,
+                                  const uint32_t* __restrict__ cj2, const uint32_t* __restrict__ adj,
+                                  const uint64_t* __restrict__ prio, const uint64_t* __restrict__ pmask,
+                                  uint32_t* __restrict__ blocker, const uint4* __restrict__ cinfo,
+                                  uint32_t* cstate, DevInfo* info)
+{
+    __shared__ uint32_t s_exam[kJpThreads * kJpItems];
+    __shared__ uint32_t s_keep[kJpThreads * kJpItems];
+    __shared__ uint32_t s_nexam, s_nkeep, s_base;
+    const uint32_t m = *cnt_in;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr uint32_t nwarps = kJpThreads / 32, tile = kJpThreads * kJpItems;
+    for (uint32_t base = blockIdx.x * tile; base < m; base += gridDim.x * tile) {
+        if (threadIdx.x == 0) {
+            s_nexam = 0;
+            s_nkeep = 0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kJpItems; ++i) {
+            const uint32_t k = base + i * kJpThreads + threadIdx.x;
+            uint32_t c = 0;
+            bool waits = false;
+            if (k < m) {
+                c = wl_in[k];
+                const uint32_t bl = blocker[c];
+                waits = bl != kUncoloured && uncoloured_now(cstate[bl], round);
+            }
+            warp_push(waits, c, s_keep, &s_nkeep, lane);
+            warp_push(k < m && !waits, c, s_exam, &s_nexam, lane);
+        }
+        __syncthreads();
+        const uint32_t ne = s_nexam;
+        for (uint32_t e = warp; e < ne; e += nwarps) {
+            const uint32_t c = s_exam[e];
+            if (jp_examine(c, round, lane, cj1, cj2, adj, prio, pmask, blocker, cinfo, cstate, info) && lane == 0)
+                s_keep[atomicAdd(&s_nkeep, 1u)] = c;
+        }
+        __syncthreads();
+        const uint32_t nk = s_nkeep;
+        if (threadIdx.x == 0) s_base = nk ? atomicAdd(cnt_out, nk) : 0u;
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < nk; t += kJpThreads) wl_out[s_base + t] = s_keep[t];
+        __syncthreads();   // the shared lists are refilled by the next tile
     }
 }
 
@@ -260,9 +381,12 @@ nbgs_status run_colour(nbgs_scene* s)
         if (rc != NBGS_OK) return rc;
         cudaMemsetAsync(s->deg, 0, (n + 1) * sizeof(uint32_t), st);
         k_adj_fill<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->deg, s->adj);
+        k_pred_masks<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->adj, s->cprio, s->pmask,
+                                       s->blocker, s->cinfo);
         if (s->timing) s->phase_launches[1] += 5;
         // Jones-Plassmann rounds; the host checks the worklist every few rounds
         const uint32_t c32 = (uint32_t)C;
+        const int gbr = grid_for((C + kJpItems - 1) / kJpItems, kJpThreads, 8, s->num_sms);
         cudaMemcpyAsync(&s->info->wl_count[0], &c32, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
         uint32_t round = 0;
         int cur = 0;
@@ -270,9 +394,9 @@ nbgs_status run_colour(nbgs_scene* s)
             for (int r = 0; r < 6; ++r) {
                 ++round;
                 cudaMemsetAsync(&s->info->wl_count[1 - cur], 0, sizeof(uint32_t), st);
-                k_jp_round<<<gb, T, 0, st>>>(round, n, s->wl[cur], &s->info->wl_count[cur], s->wl[1 - cur],
-                                             &s->info->wl_count[1 - cur], s->cj1, s->cj2, s->finite, s->adj_off,
-                                             s->adj, s->cprio, s->cstate, s->info);
+                k_jp_round<<<gbr, kJpThreads, 0, st>>>(round, s->wl[cur], &s->info->wl_count[cur], s->wl[1 - cur],
+                                                       &s->info->wl_count[1 - cur], s->cj1, s->cj2, s->adj, s->cprio,
+                                                       s->pmask, s->blocker, s->cinfo, s->cstate, s->info);
                 cur = 1 - cur;
             }
             if (s->timing) s->phase_launches[1] += 6;

@@ -278,6 +278,9 @@ struct nbgs_scene {
     uint32_t* adj = nullptr;       // 2 ccap
     uint32_t* cstate = nullptr;    // (round << 8) | colour
     uint64_t* cprio = nullptr;
+    uint64_t* pmask = nullptr;     // colouring: predecessor bits over the incidence entries
+    uint32_t* blocker = nullptr;   // colouring: the predecessor a contact waits for
+    uint4* cinfo = nullptr;        // colouring: incidence list starts and lengths
     uint32_t* wl[2] = {nullptr, nullptr};
     uint32_t* colour_key = nullptr;   // colour per contact (sort key)
     uint32_t* colour_key2 = nullptr;
