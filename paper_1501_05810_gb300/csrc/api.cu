@@ -64,7 +64,7 @@ static bool alloc_contact_arrays(nbgs_scene* s, int64_t cap)
               take(s, s->cimp, c) && take(s, s->cworld, c) && take(s, s->prev_j2, c) && take(s, s->prev_P, c) &&
               take(s, s->adj, 2 * c) && take(s, s->cstate, c) && take(s, s->cprio, c) && take(s, s->wl[0], c) &&
               take(s, s->wl[1], c) && take(s, s->colour_key, c) && take(s, s->colour_key2, c) &&
-              take(s, s->pmask, c) && take(s, s->blocker, c) && take(s, s->cinfo, c) &&
+              take(s, s->pmask, c) && take(s, s->whead, c) && take(s, s->wnext, c) && take(s, s->poff, c + 1) &&
               take(s, s->perm, c) && take(s, s->perm_in, c);
     if (!ok) return false;
     s->srec = dev_alloc(s, c * rec_bytes(s));
@@ -76,7 +76,7 @@ static void free_contact_arrays(nbgs_scene* s)
 {
     void* ps[] = {s->cj1, s->cj2, s->cgeo, s->clev, s->cimp, s->cworld, s->prev_j2, s->prev_P, s->adj, s->cstate,
                   s->cprio, s->wl[0], s->wl[1], s->colour_key, s->colour_key2, s->perm, s->perm_in, s->srec, s->sp,
-                  s->pmask, s->blocker, s->cinfo};
+                  s->pmask, s->whead, s->wnext, s->poff};
     for (void* p : ps) dev_free(s, p);
 }
 
@@ -85,9 +85,21 @@ static bool alloc_sort_temps(nbgs_scene* s)
     const int64_t big = std::max<int64_t>(std::max<int64_t>(s->n, s->ccap), 1);
     const int64_t nb = (big + 4095) / 4096;
     s->radix_hist_len = 256 * nb;
-    const int64_t scan_len = std::max<int64_t>(s->radix_hist_len, s->n + 1);
+    const int64_t scan_len = std::max<int64_t>(std::max<int64_t>(s->radix_hist_len, s->n + 1), s->ccap + 1);
     s->scan_tmp_len = (scan_len + 4095) / 4096 + 1;
     return take(s, s->radix_hist, (size_t)s->radix_hist_len + 1) && take(s, s->scan_tmp, (size_t)s->scan_tmp_len);
+}
+
+// Grow the predecessor-list buffer of the colouring to `need` entries.
+nbgs_status grow_preds(nbgs_scene* s, int64_t need)
+{
+    if (need <= s->preds_cap) return NBGS_OK;
+    const int64_t cap = need + need / 4 + 4096;
+    dev_free(s, s->preds);
+    s->preds = (uint2*)dev_alloc(s, (size_t)cap * sizeof(uint2));
+    s->preds_cap = s->preds ? cap : 0;
+    if (!s->preds) return fail(s, NBGS_ENOMEM, "colour: predecessor lists: allocation failed");
+    return NBGS_OK;
 }
 
 // Grow every contact-sized buffer to hold `need` contacts; the previous
@@ -392,7 +404,7 @@ void nbgs_destroy_scene(nbgs_scene* s)
                   s->keys[1], s->vals[0], s->vals[1], s->radix_hist, s->scan_tmp, s->cand, s->sph_cnt, s->row_cnt,
                   s->row_off, s->prev_row_off, s->deg, s->adj_off, s->col_count, s->col_off, s->info, s->dep,
                   s->prog, s->cstart, s->scene_of, s->scene_off, s->scene_box, s->scene_mu, s->scene_vmax,
-                  s->scene_vref, s->scene_rk, s->scene_done, s->scene_res, s->mlp_theta};
+                  s->scene_vref, s->scene_rk, s->scene_done, s->scene_res, s->mlp_theta, s->preds};
     for (void* p : ps) dev_free(s, p);
     free_contact_arrays(s);
     cudaStreamSynchronize(s->stream);

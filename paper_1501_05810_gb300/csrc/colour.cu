@@ -7,11 +7,13 @@
 //
 //   k_colour_init   priority splitmix64(key ^ seed), body degrees
 //   scan + k_adj_fill  body -> contact incidence lists (finite bodies only)
-//   k_pred_masks    per contact: which incident contacts beat it
-//   k_jp_round      Jones-Plassmann round: an uncoloured contact whose
-//                   priority beats every uncoloured neighbour takes the
-//                   smallest colour unused by its coloured neighbours; this
-//                   equals first-fit greedy in decreasing priority
+//   k_pred_count, scan, k_pred_lists
+//                   per contact: the incident contacts that beat it (its
+//                   predecessors); it waits on the weakest
+//   k_jp_round      a contact whose predecessors are all coloured takes the
+//                   smallest colour none of them has: first-fit greedy in
+//                   decreasing priority, as Jones-Plassmann rounds give it,
+//                   driven by waiting lists
 //   k_colour_keys   colour histogram
 //   radix pass      stable counting sort by colour -> permutation
 //   k_build_sweep   sweep records in colour order, initial impulses
@@ -41,13 +43,12 @@ __device__ __forceinline__ uint64_t local_key(uint32_t a, uint32_t b, const Scen
 
 __global__ void k_colour_init(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
                               const uint8_t* __restrict__ finite, uint64_t seed, SceneView V, uint32_t* __restrict__ deg,
-                              uint64_t* __restrict__ prio, uint32_t* __restrict__ cstate, uint32_t* __restrict__ wl)
+                              uint64_t* __restrict__ prio, uint32_t* __restrict__ cstate)
 {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t a = cj1[c], b = cj2[c];
         prio[c] = splitmix64(local_key(a, b, V) ^ seed);
         cstate[c] = kUncoloured;
-        wl[c] = (uint32_t)c;
         if (finite[a]) atomicAdd(&deg[a], 1u);
         if (b < n && finite[b]) atomicAdd(&deg[b], 1u);
     }
@@ -74,188 +75,280 @@ __device__ __forceinline__ bool beats(uint64_t pd, uint32_t d, uint64_t pc, uint
     return kd < kc;
 }
 
-// Predecessor masks: bit j of pmask[c] is set when entry j of the
-// concatenated incidence lists of c's bodies (first body, then second) holds
-// a contact that beats c.  blocker[c] = the weakest such contact (kUncoloured:
-// none), cinfo[c] = (start, length) of the two lists.  pmask = ~0 marks a
-// contact with more than 64 entries, which compares priorities whenever it
-// is examined.
-__global__ void k_pred_masks(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
-                             const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
-                             const uint32_t* __restrict__ adj, const uint64_t* __restrict__ prio,
-                             uint64_t* __restrict__ pmask, uint32_t* __restrict__ blocker, uint4* __restrict__ cinfo)
-{
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t a = cj1[c], b = cj2[c];
-        const bool fa = finite[a], fb = b < n && finite[b];
-        const uint32_t a0 = fa ? adj_off[a] : 0, na = fa ? adj_off[a + 1] - a0 : 0;
-        const uint32_t b0 = fb ? adj_off[b] : 0, nb = fb ? adj_off[b + 1] - b0 : 0;
-        uint64_t m = 0;
-        uint32_t first = kUncoloured;
-        if (na + nb > 64) {
-            m = ~0ull;
-        } else {
-            const uint64_t pc = prio[c];
-            uint64_t pfirst = 0;
-            for (uint32_t j = 0; j < na + nb; ++j) {
-                const uint32_t d = j < na ? adj[a0 + j] : adj[b0 + j - na];
-                const uint64_t pd = prio[d];
-                if (d != (uint32_t)c && beats(pd, d, pc, (uint32_t)c, cj1, cj2)) {
-                    if (!m || beats(pfirst, first, pd, d, cj1, cj2)) {
-                        first = d;
-                        pfirst = pd;
-                    }
-                    m |= 1ull << j;
-                }
-            }
-        }
-        pmask[c] = m;
-        blocker[c] = first;
-        cinfo[c] = make_uint4(a0, na, b0, nb);
-    }
-}
+// Colouring by waiting lists.  First-fit greedy colouring in decreasing
+// priority gives each contact the smallest colour none of its predecessors
+// (neighbours that beat it) has; the colour depends only on the
+// predecessors' colours, not on when it is computed.  So a contact is
+// examined only when it may be ready: at the start if it has no
+// predecessor, later when the predecessor it waits for (its blocker) has
+// been coloured.  A contact that finds a predecessor still uncoloured puts
+// itself on that predecessor's waiting list (whead / wnext, a lock-free
+// stack); the round after a contact is coloured walks its list.  A waiter
+// always registers in a round no later than the one that colours its
+// blocker (it saw the blocker uncoloured), so the walk, one launch later,
+// sees it.  Every round needs only the contacts coloured in the previous
+// round and their waiters, not a pass over all uncoloured contacts.
+//
+// Worklists: a buffer of C entries holds the contacts coloured in a round
+// (L, from the front) and the contacts to examine directly in the next
+// round (X, from the back: contacts with more than 64 incidence entries,
+// which keep no blocker, and examinations that did not fit a block's shared
+// buffer).  The counters (|L|, |X|) rotate through three pairs: a round
+// reads one, writes the next and clears the third.
 
-// cstate[d] = (round << 8) | colour, or kUncoloured.  Within round r a
-// contact coloured in round r still counts as uncoloured, so every decision
-// of the round sees the state at its start.
-__device__ __forceinline__ bool uncoloured_now(uint32_t sd, uint32_t round)
-{
-    return sd == kUncoloured || (sd >> 8) >= round;
-}
-
-// One warp examines contact c: its lanes cover the incidence entries.  If a
-// predecessor is still uncoloured, c waits (its blocker becomes the
-// uncoloured predecessor of lowest priority); otherwise c is a local maximum and takes the smallest
-// colour none of its predecessors has (every coloured neighbour is a
-// predecessor: the others wait for c).  Returns whether c waits.
-__device__ bool jp_examine(uint32_t c, uint32_t round, int lane, const uint32_t* __restrict__ cj1,
-                           const uint32_t* __restrict__ cj2, const uint32_t* __restrict__ adj,
-                           const uint64_t* __restrict__ prio, const uint64_t* __restrict__ pmask,
-                           uint32_t* __restrict__ blocker, const uint4* __restrict__ cinfo, uint32_t* cstate,
-                           DevInfo* info)
-{
-    const uint4 ci = cinfo[c];
-    const uint32_t len = ci.y + ci.w;
-    const uint64_t pm = pmask[c];
-    const bool slow = pm == ~0ull;
-    const uint64_t pc = slow ? prio[c] : 0;
-    uint32_t used[4] = {0u, 0u, 0u, 0u};
-    for (uint32_t j0 = 0; j0 < len; j0 += 32) {
-        const uint32_t j = j0 + lane;
-        bool pred = false, unc = false;
-        uint32_t d = 0, sd = kUncoloured;
-        if (j < len) {
-            d = j < ci.y ? adj[ci.x + j] : adj[ci.z + j - ci.y];
-            pred = slow ? (d != c && beats(prio[d], d, pc, c, cj1, cj2)) : ((pm >> j) & 1ull) != 0;
-            if (pred) {
-                sd = cstate[d];
-                unc = uncoloured_now(sd, round);
-            }
-        }
-        const uint32_t wait = __ballot_sync(0xffffffffu, pred && unc);
-        if (wait) {
-            if (!slow) {
-                // wait for the weakest uncoloured predecessor: it tends to be
-                // coloured last, so c is examined again fewer times
-                const uint64_t pd = (pred && unc) ? prio[d] : ~0ull;
-                uint64_t pmin = pd;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const uint64_t y = __shfl_xor_sync(0xffffffffu, pmin, o);
-                    pmin = y < pmin ? y : pmin;
-                }
-                const uint32_t at = __ballot_sync(0xffffffffu, (pred && unc) && pd == pmin);
-                if (lane == __ffs(at) - 1) blocker[c] = d;
-            }
-            return true;
-        }
-        if (pred) {
-            const uint32_t col = sd & 0xFFu;
-#pragma unroll
-            for (int w = 0; w < 4; ++w)
-                if ((col >> 5) == (uint32_t)w) used[w] |= 1u << (col & 31u);
-        }
-    }
-    uint32_t col = kMaxColours;
-#pragma unroll
-    for (int w = 3; w >= 0; --w) {
-        const uint32_t u = __reduce_or_sync(0xffffffffu, used[w]);
-        if (~u) col = 32u * w + (__ffs(~u) - 1);
-    }
-    if (lane == 0) {
-        if (col >= kMaxColours) {
-            atomicOr(&info->err, kErrColours);
-            col = kMaxColours - 1;
-        }
-        cstate[c] = (round << 8) | col;
-    }
-    return false;
-}
-
-// Appends val to list for every lane with pred set (one shared-memory
-// counter update per warp).
-__device__ __forceinline__ void warp_push(bool pred, uint32_t val, uint32_t* list, uint32_t* count, int lane)
+// Appends val to list (from the front, or from the back of a buffer of cap
+// entries) for every lane with pred set; one counter update per warp.
+__device__ __forceinline__ void warp_push(bool pred, uint32_t val, uint32_t* list, uint32_t* count, int lane,
+                                          bool from_back = false, uint32_t cap = 0)
 {
     const uint32_t mask = __ballot_sync(0xffffffffu, pred);
     uint32_t b = 0;
     if (lane == 0 && mask) b = atomicAdd(count, (uint32_t)__popc(mask));
     b = __shfl_sync(0xffffffffu, b, 0);
-    if (pred) list[b + __popc(mask & ((1u << lane) - 1u))] = val;
+    if (pred) {
+        const uint32_t i = b + __popc(mask & ((1u << lane) - 1u));
+        list[from_back ? cap - 1u - i : i] = val;
+    }
 }
 
-// One Jones-Plassmann round over the worklist, a tile of kJpItems per thread
-// at a time.  Phase 1, a thread per contact: a contact whose remembered
-// blocker is still uncoloured waits (two loads).  Phase 2, a warp per
-// remaining contact (jp_examine).  The waiting contacts of the tile go to
-// wl_out with one global counter update.
-constexpr int kJpThreads = 256;
-constexpr int kJpItems = 4;
-
-__global__ void __launch_bounds__(kJpThreads) k_jp_round(uint32_t round, const uint32_t* __restrict__ wl_in,
-                                  const uint32_t* __restrict__ cnt_in, uint32_t* __restrict__ wl_out,
-                                  uint32_t* __restrict__ cnt_out, const uint32_t* __restrict__ cj1,
-                                  const uint32_t* __restrict__ cj2, const uint32_t* __restrict__ adj,
-                                  const uint64_t* __restrict__ prio, const uint64_t* __restrict__ pmask,
-                                  uint32_t* __restrict__ blocker, const uint4* __restrict__ cinfo,
-                                  uint32_t* cstate, DevInfo* info)
+// Incidence entry j of contact c: the lists of its first body, then of its
+// second (finite bodies only).
+__device__ __forceinline__ uint32_t incident(const uint32_t* __restrict__ adj, uint32_t a0, uint32_t na, uint32_t b0,
+                                             uint32_t j)
 {
-    __shared__ uint32_t s_exam[kJpThreads * kJpItems];
-    __shared__ uint32_t s_keep[kJpThreads * kJpItems];
-    __shared__ uint32_t s_nexam, s_nkeep, s_base;
-    const uint32_t m = *cnt_in;
+    return j < na ? adj[a0 + j] : adj[b0 + j - na];
+}
+
+__device__ __forceinline__ void incidence(uint32_t c, int64_t n, const uint32_t* __restrict__ cj1,
+                                          const uint32_t* __restrict__ cj2, const uint8_t* __restrict__ finite,
+                                          const uint32_t* __restrict__ adj_off, uint32_t& a0, uint32_t& na,
+                                          uint32_t& b0, uint32_t& nb)
+{
+    const uint32_t a = cj1[c], b = cj2[c];
+    const bool fa = finite[a], fb = b < n && finite[b];
+    a0 = fa ? adj_off[a] : 0;
+    na = fa ? adj_off[a + 1] - a0 : 0;
+    b0 = fb ? adj_off[b] : 0;
+    nb = fb ? adj_off[b + 1] - b0 : 0;
+}
+
+// Predecessors of contact c: the incident contacts that beat it.  Pass 1
+// counts them (npred) and keeps them as a bit mask over the incidence
+// entries (pmask; ~0 for more than 64 entries, where pass 2 compares
+// priorities again).
+__global__ void k_pred_count(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
+                             const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
+                             const uint32_t* __restrict__ adj, const uint64_t* __restrict__ prio,
+                             uint64_t* __restrict__ pmask, uint32_t* __restrict__ npred)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t a0, na, b0, nb;
+        incidence((uint32_t)c, n, cj1, cj2, finite, adj_off, a0, na, b0, nb);
+        const uint64_t pc = prio[c];
+        uint64_t m = 0;
+        uint32_t k = 0;
+        for (uint32_t j = 0; j < na + nb; ++j) {
+            const uint32_t d = incident(adj, a0, na, b0, j);
+            if (d != (uint32_t)c && beats(prio[d], d, pc, (uint32_t)c, cj1, cj2)) {
+                ++k;
+                if (j < 64) m |= 1ull << j;
+            }
+        }
+        pmask[c] = na + nb > 64 ? ~0ull : m;
+        npred[c] = k;
+    }
+}
+
+// Pass 2: the predecessor list of c at preds[poff[c] ..], each entry the
+// predecessor and the high half of its priority.  A contact with
+// predecessors waits on the weakest (it tends to be coloured last, so the
+// contact is examined again fewer times); the others form the first round's
+// direct list.
+__device__ __forceinline__ uint32_t prio_hi(uint64_t p) { return (uint32_t)(p >> 32); }
+
+__global__ void k_pred_lists(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
+                             const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
+                             const uint32_t* __restrict__ adj, const uint64_t* __restrict__ prio,
+                             const uint64_t* __restrict__ pmask, const uint32_t* __restrict__ poff,
+                             uint2* __restrict__ preds, uint32_t* whead, uint32_t* __restrict__ wnext,
+                             uint32_t* __restrict__ wl, uint32_t* count)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count: every lane takes part in warp_push
+    for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x; c0 < C; c0 += stride) {
+        const int64_t c = c0 + threadIdx.x;
+        bool direct = false;
+        if (c < C) {
+            uint32_t a0, na, b0, nb;
+            incidence((uint32_t)c, n, cj1, cj2, finite, adj_off, a0, na, b0, nb);
+            const uint32_t p0 = poff[c], np = poff[c + 1] - p0;
+            const uint64_t m = pmask[c];
+            const uint64_t pc = prio[c];
+            uint32_t k = 0, weakest = kUncoloured;
+            uint64_t pweak = ~0ull;
+            for (uint32_t j = 0; j < na + nb && k < np; ++j) {
+                if (m != ~0ull && !((m >> j) & 1ull)) continue;
+                const uint32_t d = incident(adj, a0, na, b0, j);
+                const uint64_t pd = prio[d];
+                if (m == ~0ull && (d == (uint32_t)c || !beats(pd, d, pc, (uint32_t)c, cj1, cj2))) continue;
+                preds[p0 + k] = make_uint2(d, prio_hi(pd));
+                if (pd < pweak) {
+                    pweak = pd;
+                    weakest = d;
+                }
+                ++k;
+            }
+            if (np == 0) direct = true;
+            else wnext[c] = atomicExch(&whead[weakest], (uint32_t)c);
+        }
+        warp_push(direct, (uint32_t)c, wl, count, lane, true, (uint32_t)C);
+    }
+}
+
+// Examination of contact c by a group of 4 lanes (lanes 4g..4g+3 of a
+// warp; every lane of the warp calls this, valid = false for a group with no
+// contact).  The lanes cover the predecessor list, 16 entries per pass, all
+// loads of a pass in flight together.  If a predecessor is still
+// uncoloured, c waits on the weakest such one.  Otherwise c takes the
+// smallest colour none of its predecessors has.  Returns whether c was
+// coloured.
+__device__ bool jp_examine(bool valid, uint32_t c, uint32_t round, int lane, const uint32_t* __restrict__ poff,
+                           const uint2* __restrict__ preds, uint32_t* cstate, uint32_t* whead,
+                           uint32_t* __restrict__ wnext, DevInfo* info)
+{
+    const int gl = lane & 3;
+    uint32_t p0 = 0, np = 0;
+    if (valid) {
+        p0 = poff[c];
+        np = poff[c + 1] - p0;
+    }
+    const uint32_t maxnp = __reduce_max_sync(0xffffffffu, np);
+    uint32_t used[4] = {0u, 0u, 0u, 0u};
+    uint32_t wph = ~0u, wd = kUncoloured;   // weakest uncoloured predecessor seen by this lane
+    for (uint32_t w0 = 0; w0 < maxnp; w0 += 16) {
+        uint2 e[4];
+        uint32_t sd[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t j = w0 + 4 * k + gl;
+            e[k] = j < np ? preds[p0 + j] : make_uint2(kUncoloured, 0u);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sd[k] = e[k].x != kUncoloured ? cstate[e[k].x] : 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (e[k].x == kUncoloured) continue;
+            if (sd[k] == kUncoloured) {
+                if (wd == kUncoloured || e[k].y < wph) {
+                    wph = e[k].y;
+                    wd = e[k].x;
+                }
+            } else {
+                const uint32_t col = sd[k] & 0xFFu;
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    if ((col >> 5) == (uint32_t)w) used[w] |= 1u << (col & 31u);
+            }
+        }
+    }
+    // group reductions (xor 1, 2 stays inside the group)
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        const uint32_t wp2 = __shfl_xor_sync(0xffffffffu, wph, o);
+        const uint32_t wd2 = __shfl_xor_sync(0xffffffffu, wd, o);
+        if (wd2 != kUncoloured && (wd == kUncoloured || wp2 < wph)) {
+            wph = wp2;
+            wd = wd2;
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) used[w] |= __shfl_xor_sync(0xffffffffu, used[w], o);
+    }
+    if (!valid) return false;
+    if (wd != kUncoloured) {
+        if (gl == 0) wnext[c] = atomicExch(&whead[wd], c);
+        return false;
+    }
+    if (gl == 0) {
+        uint32_t col = kMaxColours;
+#pragma unroll
+        for (int w = 3; w >= 0; --w)
+            if (~used[w]) col = 32u * w + (__ffs(~used[w]) - 1);
+        if (col >= kMaxColours) {
+            atomicOr(&info->err, kErrColours);
+            col = kMaxColours - 1;
+        }
+        cstate[c] = (round << 8) | col;   // the round is informational
+    }
+    return true;
+}
+
+// One round, a tile of kJpThreads input entries at a time.  Phase 1, a
+// thread per entry: an entry of L has its waiting list walked, an entry of
+// X is taken as it is; both fill the block's examination buffer (overflow
+// goes to the next round's X).  Phase 2, 4 lanes per buffered contact
+// (jp_examine); the contacts coloured go to the next L.
+constexpr int kJpThreads = 256;
+constexpr int kJpCap = 2048;
+
+__global__ void __launch_bounds__(kJpThreads) k_jp_round(uint32_t round, uint32_t C, const uint32_t* __restrict__ wl_in,
+                                  const uint32_t* __restrict__ cnt_in, uint32_t* __restrict__ wl_out,
+                                  uint32_t* __restrict__ cnt_out, uint32_t* __restrict__ cnt_clear,
+                                  const uint32_t* __restrict__ poff, const uint2* __restrict__ preds,
+                                  uint32_t* cstate, uint32_t* whead, uint32_t* __restrict__ wnext, DevInfo* info)
+{
+    __shared__ uint32_t s_exam[kJpCap];
+    __shared__ uint32_t s_done[kJpCap];
+    __shared__ uint32_t s_nexam, s_ndone, s_base;
+    const uint32_t nl = cnt_in[0], nx = cnt_in[1], m = nl + nx;
+    if (blockIdx.x == 0 && threadIdx.x < 2) cnt_clear[threadIdx.x] = 0u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr uint32_t nwarps = kJpThreads / 32, tile = kJpThreads * kJpItems;
-    for (uint32_t base = blockIdx.x * tile; base < m; base += gridDim.x * tile) {
+    constexpr uint32_t nwarps = kJpThreads / 32;
+    for (uint32_t base = blockIdx.x * kJpThreads; base < m; base += gridDim.x * kJpThreads) {
         if (threadIdx.x == 0) {
             s_nexam = 0;
-            s_nkeep = 0;
+            s_ndone = 0;
         }
         __syncthreads();
-#pragma unroll
-        for (int i = 0; i < kJpItems; ++i) {
-            const uint32_t k = base + i * kJpThreads + threadIdx.x;
-            uint32_t c = 0;
-            bool waits = false;
-            if (k < m) {
-                c = wl_in[k];
-                const uint32_t bl = blocker[c];
-                waits = bl != kUncoloured && uncoloured_now(cstate[bl], round);
+        const uint32_t k = base + threadIdx.x;
+        if (k < nl) {
+            const uint32_t c = wl_in[k];
+            uint32_t h = whead[c];
+            whead[c] = kUncoloured;
+            while (h != kUncoloured) {
+                const uint32_t i = atomicAdd(&s_nexam, 1u);
+                if (i < kJpCap) {
+                    s_exam[i] = h;
+                } else {
+                    const uint32_t g = atomicAdd(&cnt_out[1], 1u);
+                    wl_out[C - 1u - g] = h;
+                }
+                h = wnext[h];
             }
-            warp_push(waits, c, s_keep, &s_nkeep, lane);
-            warp_push(k < m && !waits, c, s_exam, &s_nexam, lane);
+        } else if (k < m) {
+            const uint32_t c = wl_in[C - 1u - (k - nl)];
+            const uint32_t i = atomicAdd(&s_nexam, 1u);
+            if (i < kJpCap) {
+                s_exam[i] = c;
+            } else {
+                const uint32_t g = atomicAdd(&cnt_out[1], 1u);
+                wl_out[C - 1u - g] = c;
+            }
         }
         __syncthreads();
-        const uint32_t ne = s_nexam;
-        for (uint32_t e = warp; e < ne; e += nwarps) {
-            const uint32_t c = s_exam[e];
-            if (jp_examine(c, round, lane, cj1, cj2, adj, prio, pmask, blocker, cinfo, cstate, info) && lane == 0)
-                s_keep[atomicAdd(&s_nkeep, 1u)] = c;
+        const uint32_t ne = s_nexam < kJpCap ? s_nexam : kJpCap;
+        for (uint32_t e0 = 8 * warp; e0 < ne; e0 += 8 * nwarps) {
+            const uint32_t e = e0 + (lane >> 2);
+            const bool valid = e < ne;
+            const uint32_t c = valid ? s_exam[e] : 0u;
+            if (jp_examine(valid, c, round, lane, poff, preds, cstate, whead, wnext, info) && (lane & 3) == 0)
+                s_done[atomicAdd(&s_ndone, 1u)] = c;
         }
         __syncthreads();
-        const uint32_t nk = s_nkeep;
-        if (threadIdx.x == 0) s_base = nk ? atomicAdd(cnt_out, nk) : 0u;
+        const uint32_t nd = s_ndone;
+        if (threadIdx.x == 0) s_base = nd ? atomicAdd(&cnt_out[0], nd) : 0u;
         __syncthreads();
-        for (uint32_t t = threadIdx.x; t < nk; t += kJpThreads) wl_out[s_base + t] = s_keep[t];
+        for (uint32_t t = threadIdx.x; t < nd; t += kJpThreads) wl_out[s_base + t] = s_done[t];
         __syncthreads();   // the shared lists are refilled by the next tile
     }
 }
@@ -376,38 +469,52 @@ nbgs_status run_colour(nbgs_scene* s)
         const int gb = grid_for(C, T, 8, s->num_sms);
         cudaMemsetAsync(s->deg, 0, (n + 1) * sizeof(uint32_t), st);
         k_colour_init<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->prm.colour_seed, scene_view(s), s->deg,
-                                        s->cprio, s->cstate, s->wl[0]);
+                                        s->cprio, s->cstate);
         nbgs_status rc = exclusive_scan_u32(s, s->deg, s->adj_off, n, nullptr);
         if (rc != NBGS_OK) return rc;
         cudaMemsetAsync(s->deg, 0, (n + 1) * sizeof(uint32_t), st);
         k_adj_fill<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->deg, s->adj);
-        k_pred_masks<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->adj, s->cprio, s->pmask,
-                                       s->blocker, s->cinfo);
-        if (s->timing) s->phase_launches[1] += 5;
-        // Jones-Plassmann rounds; the host checks the worklist every few rounds
-        const uint32_t c32 = (uint32_t)C;
-        const int gbr = grid_for((C + kJpItems - 1) / kJpItems, kJpThreads, 8, s->num_sms);
-        cudaMemcpyAsync(&s->info->wl_count[0], &c32, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+        // predecessor lists (counts, offsets, lists weakest first)
+        k_pred_count<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->adj, s->cprio, s->pmask,
+                                       s->colour_key);
+        rc = exclusive_scan_u32(s, s->colour_key, s->poff, C, nullptr);
+        if (rc != NBGS_OK) return rc;
+        uint32_t total = 0;
+        rc = cuda_check(s, cudaMemcpyAsync(&total, s->poff + C, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
+                        "colour: predecessor count");
+        if (rc == NBGS_OK) rc = cuda_check(s, cudaStreamSynchronize(st), "colour");
+        if (rc != NBGS_OK) return rc;
+        rc = grow_preds(s, total);
+        if (rc != NBGS_OK) return rc;
+        // waiting lists empty; round-1 counters (|L| = 0, |X| filled below)
+        cudaMemsetAsync(s->whead, 0xFF, C * sizeof(uint32_t), st);
+        cudaMemsetAsync(s->info->wl_count, 0, sizeof(s->info->wl_count), st);
+        k_pred_lists<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->adj, s->cprio, s->pmask,
+                                       s->poff, s->preds, s->whead, s->wnext, s->wl[0], &s->info->wl_count[1]);
+        if (s->timing) s->phase_launches[1] += 9;
+        // rounds; the host checks the lists every few rounds
+        const int gbr = grid_for(C, kJpThreads, 8, s->num_sms);
         uint32_t round = 0;
         int cur = 0;
         for (int batch = 0; batch < 64; ++batch) {
             for (int r = 0; r < 6; ++r) {
                 ++round;
-                cudaMemsetAsync(&s->info->wl_count[1 - cur], 0, sizeof(uint32_t), st);
-                k_jp_round<<<gbr, kJpThreads, 0, st>>>(round, s->wl[cur], &s->info->wl_count[cur], s->wl[1 - cur],
-                                                       &s->info->wl_count[1 - cur], s->cj1, s->cj2, s->adj, s->cprio,
-                                                       s->pmask, s->blocker, s->cinfo, s->cstate, s->info);
+                const int ci = (round - 1) % 3, co = round % 3, cc = (round + 1) % 3;
+                k_jp_round<<<gbr, kJpThreads, 0, st>>>(round, (uint32_t)C, s->wl[cur], &s->info->wl_count[2 * ci],
+                                                       s->wl[1 - cur], &s->info->wl_count[2 * co],
+                                                       &s->info->wl_count[2 * cc], s->poff, s->preds, s->cstate,
+                                                       s->whead, s->wnext, s->info);
                 cur = 1 - cur;
             }
             if (s->timing) s->phase_launches[1] += 6;
-            uint32_t left = 0;
-            rc = cuda_check(s, cudaMemcpyAsync(&left, &s->info->wl_count[cur], sizeof(uint32_t),
+            uint32_t left[2] = {0, 0};
+            rc = cuda_check(s, cudaMemcpyAsync(left, &s->info->wl_count[2 * (round % 3)], 2 * sizeof(uint32_t),
                                                cudaMemcpyDeviceToHost, st), "colour: worklist");
             if (rc != NBGS_OK) return rc;
             rc = cuda_check(s, cudaStreamSynchronize(st), "colour");
             if (rc != NBGS_OK) return rc;
-            if (left == 0) break;
-            if (batch == 63) return fail(s, NBGS_ETIMEOUT, "colour: Jones-Plassmann did not finish in 384 rounds");
+            if (left[0] + left[1] == 0) break;
+            if (batch == 63) return fail(s, NBGS_ETIMEOUT, "colour: did not finish in 384 rounds");
         }
         k_colour_keys<<<gb, T, 0, st>>>(C, s->cstate, s->colour_key, s->perm_in, s->col_count, s->info);
         k_colour_offsets<<<1, 32, 0, st>>>(s->col_count, s->col_off);

@@ -100,7 +100,7 @@ struct DevInfo {
     uint32_t err;
     uint32_t cand_need;              // largest candidate count seen
     uint32_t sweeps_done;
-    uint32_t wl_count[3];            // colouring worklist sizes (rotating)
+    uint32_t wl_count[6];            // colouring list sizes (|L|, |X|), three rotating pairs
     uint32_t barrier_count;          // grid barrier arrival counter
     uint32_t barrier_gen;            // grid barrier generation
     uint32_t rounds;                 // colouring rounds used
@@ -276,11 +276,14 @@ struct nbgs_scene {
     uint32_t* deg = nullptr;       // n + 1
     uint32_t* adj_off = nullptr;   // n + 1
     uint32_t* adj = nullptr;       // 2 ccap
-    uint32_t* cstate = nullptr;    // (round << 8) | colour
+    uint32_t* cstate = nullptr;    // (round << 8) | colour, kUncoloured before
     uint64_t* cprio = nullptr;
     uint64_t* pmask = nullptr;     // colouring: predecessor bits over the incidence entries
-    uint32_t* blocker = nullptr;   // colouring: the predecessor a contact waits for
-    uint4* cinfo = nullptr;        // colouring: incidence list starts and lengths
+    uint32_t* whead = nullptr;     // colouring: head of a contact's waiting list
+    uint32_t* wnext = nullptr;     // colouring: next contact on the same waiting list
+    uint32_t* poff = nullptr;      // colouring: predecessor list offsets (C + 1)
+    uint2* preds = nullptr;        // colouring: predecessor lists (contact, high half of its priority)
+    int64_t preds_cap = 0;
     uint32_t* wl[2] = {nullptr, nullptr};
     uint32_t* colour_key = nullptr;   // colour per contact (sort key)
     uint32_t* colour_key2 = nullptr;
@@ -346,6 +349,7 @@ nbgs_status exclusive_scan_u32(nbgs_scene* s, const uint32_t* in, uint32_t* out,
 nbgs_status radix_sort_pairs(nbgs_scene* s, uint32_t*& keys, uint32_t*& vals, uint32_t*& keys_alt,
                              uint32_t*& vals_alt, int64_t n, int bits);
 int grid_for(int64_t work, int threads, int max_blocks_per_sm, int num_sms);
+nbgs_status grow_preds(nbgs_scene* s, int64_t need);
 SceneView scene_view(const nbgs_scene* s);
 
 }  // namespace nbgs
