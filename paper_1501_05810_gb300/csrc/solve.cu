@@ -89,17 +89,71 @@ template <class R> struct Bodies {
     R4<R> va, wa, vb, wb;
 };
 
+// 256-bit global accesses: a body's (v, 1/m) and (w, 1/I) pair and an FP32
+// sweep record each move as one request instead of two (FP64: two instead
+// of four).  The body accesses keep their order with every other memory
+// access of the thread.
+__device__ __forceinline__ void ld_body(const float4* p, float4& v, float4& w)
+{
+    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w), "=f"(w.x), "=f"(w.y), "=f"(w.z), "=f"(w.w)
+                 : "l"(p)
+                 : "memory");
+}
+__device__ __forceinline__ void ld_body(const double4_32a* p, double4_32a& v, double4_32a& w)
+{
+    asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];"
+                 : "=d"(v.x), "=d"(v.y), "=d"(v.z), "=d"(v.w)
+                 : "l"(p)
+                 : "memory");
+    asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];"
+                 : "=d"(w.x), "=d"(w.y), "=d"(w.z), "=d"(w.w)
+                 : "l"(p + 1)
+                 : "memory");
+}
+__device__ __forceinline__ void st_body(float4* p, const float4& v, const float4& w)
+{
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w), "f"(w.x), "f"(w.y), "f"(w.z), "f"(w.w)
+                 : "memory");
+}
+__device__ __forceinline__ void st_body(double4_32a* p, const double4_32a& v, const double4_32a& w)
+{
+    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(v.x), "d"(v.y), "d"(v.z), "d"(v.w)
+                 : "memory");
+    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p + 1), "d"(w.x), "d"(w.y), "d"(w.z), "d"(w.w)
+                 : "memory");
+}
+// Sweep records do not change during a solve.
+__device__ __forceinline__ SweepRec<float> ld_rec(const SweepRec<float>* p)
+{
+    SweepRec<float> r;
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(r.a.x), "=f"(r.a.y), "=f"(r.a.z), "=f"(r.a.w), "=f"(r.b.x), "=f"(r.b.y), "=f"(r.b.z), "=f"(r.b.w)
+        : "l"(p));
+    return r;
+}
+__device__ __forceinline__ SweepRec<double> ld_rec(const SweepRec<double>* p)
+{
+    SweepRec<double> r;
+    asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+        : "=d"(r.ids_bias.x), "=d"(r.ids_bias.y), "=d"(r.lev.x), "=d"(r.lev.y)
+        : "l"(p));
+    asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+        : "=d"(r.nxy.x), "=d"(r.nxy.y), "=d"(r.nz_.x), "=d"(r.nz_.y)
+        : "l"(reinterpret_cast<const char*>(p) + 32));
+    return r;
+}
+
 template <class R>
 __device__ __forceinline__ void gather(const SolveArgs<R>& A, const SweepRec<R>& rr, Bodies<R>& B)
 {
     uint32_t ia, ib;
     R la, lb, nx, ny, nz, bias;
     decode<R>(rr, ia, ib, la, lb, nx, ny, nz, bias);
-    B.va = A.vel[2 * (int64_t)ia];
-    B.wa = A.vel[2 * (int64_t)ia + 1];
+    ld_body(A.vel + 2 * (int64_t)ia, B.va, B.wa);
     if (ib < (uint32_t)A.n) {
-        B.vb = A.vel[2 * (int64_t)ib];
-        B.wb = A.vel[2 * (int64_t)ib + 1];
+        ld_body(A.vel + 2 * (int64_t)ib, B.vb, B.wb);
     } else {
         B.vb.x = B.vb.y = B.vb.z = B.vb.w = R(0);
         B.wb = B.vb;
@@ -195,8 +249,7 @@ __device__ __forceinline__ R relax_gathered(const SolveArgs<R>& A, int64_t s, co
         wa.x -= ka * qx;
         wa.y -= ka * qy;
         wa.z -= ka * qz;
-        A.vel[2 * (int64_t)ia] = va;
-        A.vel[2 * (int64_t)ia + 1] = wa;
+        st_body(A.vel + 2 * (int64_t)ia, va, wa);
     }
     if (dyn_b && (imb > R(0) || iIb > R(0))) {
         vb.x -= imb * Px;
@@ -206,8 +259,7 @@ __device__ __forceinline__ R relax_gathered(const SolveArgs<R>& A, int64_t s, co
         wb.x -= kb * qx;
         wb.y -= kb * qy;
         wb.z -= kb * qz;
-        A.vel[2 * (int64_t)ib] = vb;
-        A.vel[2 * (int64_t)ib + 1] = wb;
+        st_body(A.vel + 2 * (int64_t)ib, vb, wb);
     }
     const R r1 = wn * dn, r2 = wt * dt_, r3 = wt * do_;
     const R r = sqrt(r1 * r1 + r2 * r2 + r3 * r3);
@@ -225,7 +277,7 @@ __device__ __forceinline__ R relax_gathered(const SolveArgs<R>& A, int64_t s, co
 template <class R, bool apply_only, bool Batch = false>
 __device__ __forceinline__ R relax(const SolveArgs<R>& A, int64_t s, int sweep)
 {
-    const SweepRec<R> rr = A.rec[s];
+    const SweepRec<R> rr = ld_rec(A.rec + s);
     const R4<R> pp = A.p[s];
     Bodies<R> B;
     gather<R>(A, rr, B);
@@ -556,10 +608,10 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
                 }
                 parity ^= 1u;
             }
+            const int cn = c + 1 < ncol ? c + 1 : 0;
             const R r = process_colour<R, false, Batch>(A, c, m, srec, sp, k);
             rmax = r > rmax ? r : rmax;
             if (c == ncol - 1) block_max_to<R>(rmax, &A.info->rk_bits[rk_slot(k)]);
-            const int cn = c + 1 < ncol ? c + 1 : 0;
             if (local) {
                 publish(A.prog, g);   // its __syncthreads also ends every read of the stage
                 m = stage ? stage_issue<R>(A, cn, srec, sp, &bar) : 0;
