@@ -460,6 +460,26 @@ __device__ __forceinline__ R process_colour(const SolveArgs<R>& A, int c, int m,
     return rmax;
 }
 
+// L2 prefetch of the records and impulses of this block's chunk of colour c:
+// a hint issued one colour ahead, so that the lines stream in from HBM while
+// the current colour is relaxed (the bodies stay in L2 anyway).
+template <class R>
+__device__ __forceinline__ void prefetch_chunk(const SolveArgs<R>& A, int c)
+{
+    int64_t b0, b1;
+    colour_chunk(A.cstart, c, b0, b1);
+    if (b1 <= b0) return;
+    const char* r0 = reinterpret_cast<const char*>(A.rec + b0);
+    const char* r1 = reinterpret_cast<const char*>(A.rec + b1);
+    const char* p0 = reinterpret_cast<const char*>(A.p + b0);
+    const char* p1 = reinterpret_cast<const char*>(A.p + b1);
+    const int64_t nr = (r1 - r0 + 127) / 128, np = (p1 - p0 + 127) / 128;
+    for (int64_t i = threadIdx.x; i < nr + np; i += blockDim.x) {
+        const char* a = i < nr ? r0 + 128 * i : p0 + 128 * (i - nr);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    }
+}
+
 // Split grid barrier: arrive (after this block's stores), do independent
 // work, then wait.  The wait gives up after ~2^31 SM clocks (about a
 // second), sets the timeout bit and returns false.
@@ -609,6 +629,7 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
                 parity ^= 1u;
             }
             const int cn = c + 1 < ncol ? c + 1 : 0;
+            prefetch_chunk<R>(A, c + 1 < ncol ? c + 1 : 0);
             const R r = process_colour<R, false, Batch>(A, c, m, srec, sp, k);
             rmax = r > rmax ? r : rmax;
             if (c == ncol - 1) block_max_to<R>(rmax, &A.info->rk_bits[rk_slot(k)]);
