@@ -280,6 +280,27 @@ nbgs_status nbgs_get_contacts(nbgs_scene* scene, int64_t cap,
                               uint32_t* j1, uint32_t* j2, int32_t* colour,
                               double* normal, double* xi, double* impulse, int64_t* n_out);
 
+/* Checkpoint and resume.  The paper runs long simulations but says nothing
+ * about saving them; these calls cover what a time step reads (Alg. 2):
+ * the body state as the device holds it (FP64 positions and radii,
+ * quaternions, velocities with 1/m and 1/I in the sweep precision,
+ * finite-mass flags), the parameters, the shared walls, and the previous
+ * step's contacts with their world-frame impulses, which the warm start of
+ * Sect. 5 matches by key; plus the warm-start network if one is loaded.
+ *
+ * nbgs_save_state writes them to the file at path (a binary file in host
+ * byte order, overwritten).  Synchronises.  Plain scenes only: a batched
+ * scene returns NBGS_EINVAL.  A file error returns NBGS_EINVAL.
+ *
+ * nbgs_load_state restores such a file into a scene created with the same
+ * body count, box, periodic axes and sweep precision (else NBGS_EINVAL,
+ * before anything is copied); the steps that follow are bit-identical to
+ * those of the scene that saved it.  The parameters stored in the file
+ * replace the scene's.  Synchronises.  Every error sticks in the scene, as
+ * for the other calls. */
+nbgs_status nbgs_save_state(nbgs_scene* scene, const char* path);
+nbgs_status nbgs_load_state(nbgs_scene* scene, const char* path);
+
 /* R_k of every sweep of the last solve.  Synchronises. */
 nbgs_status nbgs_residual_history(nbgs_scene* scene, double* out, int32_t cap, int32_t* n_out);
 

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnbgs.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["api.cu", "detect.cu", "colour.cu", "solve.cu", "integrate.cu", "mlp.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "detect.cu", "colour.cu", "solve.cu", "integrate.cu", "mlp.cu", "noalloc.cu", "checkpoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -76,6 +76,8 @@ _SIG = {
     "nbgs_step": [_vp, C.c_int32, C.c_double, _P(nbgs_step_stats)],
     "nbgs_get_contacts": [_vp, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _i64p],
     "nbgs_residual_history": [_vp, _dp, C.c_int32, _i32p],
+    "nbgs_save_state": [_vp, C.c_char_p],
+    "nbgs_load_state": [_vp, C.c_char_p],
     "nbgs_final_residuals": [_vp, _P(nbgs_residuals)],
     "nbgs_sync": [_vp],
     "nbgs_enable_timing": [_vp, C.c_int32],
@@ -298,6 +300,14 @@ class Scene:
         _call(self.h, "nbgs_get_contacts", m, *[_ptr(out[k]) for k in ("j1", "j2", "colour", "normal", "xi",
                                                                         "impulse")], C.byref(n))
         return out
+
+    def save_state(self, path: str) -> None:
+        """Checkpoint of everything the next step reads (nbgs_save_state)."""
+        _call(self.h, "nbgs_save_state", os.fsencode(path))
+
+    def load_state(self, path: str) -> None:
+        """Restore a checkpoint written by save_state (nbgs_load_state)."""
+        _call(self.h, "nbgs_load_state", os.fsencode(path))
 
     def residual_history(self) -> np.ndarray:
         n = C.c_int32()
