@@ -85,7 +85,8 @@ static bool alloc_sort_temps(nbgs_scene* s)
     const int64_t big = std::max<int64_t>(std::max<int64_t>(s->n, s->ccap), 1);
     const int64_t nb = (big + 4095) / 4096;
     s->radix_hist_len = 256 * nb;
-    const int64_t scan_len = std::max<int64_t>(std::max<int64_t>(s->radix_hist_len, s->n + 1), s->ccap + 1);
+    const int64_t scan_len =
+        std::max<int64_t>(std::max<int64_t>(s->radix_hist_len, s->n + 1), std::max<int64_t>(s->ccap, s->max_cells) + 1);
     s->scan_tmp_len = (scan_len + 4095) / 4096 + 1;
     return take(s, s->radix_hist, (size_t)s->radix_hist_len + 1) && take(s, s->scan_tmp, (size_t)s->scan_tmp_len);
 }
@@ -284,8 +285,8 @@ static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_des
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
 
     bool ok = take(s, s->pos_r, nn) && take(s, s->quat, nn) && take(s, s->hull, nn) && take(s, s->p32, nn) &&
-              take(s, s->finite, nn) &&
-              take(s, s->stage, 13 * nn) && take(s, s->cell_start, (size_t)s->max_cells) &&
+              take(s, s->p32s, nn) && take(s, s->finite, nn) &&
+              take(s, s->stage, 13 * nn) && take(s, s->cell_start, (size_t)s->max_cells + 1) &&
               take(s, s->cell_end, (size_t)s->max_cells) && take(s, s->keys[0], nn) && take(s, s->keys[1], nn) &&
               take(s, s->vals[0], nn) && take(s, s->vals[1], nn) && take(s, s->cand, nn * kCandCap) &&
               take(s, s->sph_cnt, nn) && take(s, s->row_cnt, nn) && take(s, s->row_off, nn + 1) &&
@@ -319,15 +320,18 @@ static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_des
         cudaStreamSynchronize(s->stream);   // stream-ordered allocations before the blocking copies
         const size_t S = (size_t)s->n_scenes;
         bool okb = take(s, s->scene_of, nn) && take(s, s->scene_off, S + 1) && take(s, s->scene_box, 6 * S) &&
+                   take(s, s->scene_box32, 6 * S) &&
                    take(s, s->scene_mu, S) && take(s, s->scene_vmax, S) && take(s, s->scene_vref, S) &&
                    take(s, s->scene_rk, 3 * S) && take(s, s->scene_done, S) && take(s, s->scene_res, S);
         uint32_t* h_of = okb ? (uint32_t*)malloc(nn * sizeof(uint32_t)) : nullptr;
         uint32_t* h_off = okb ? (uint32_t*)malloc((S + 1) * sizeof(uint32_t)) : nullptr;
         double* h_box = okb ? (double*)malloc(6 * S * sizeof(double)) : nullptr;
-        if (!h_of || !h_off || !h_box) {
+        float* h_box32 = okb ? (float*)malloc(6 * S * sizeof(float)) : nullptr;
+        if (!h_of || !h_off || !h_box || !h_box32) {
             free(h_of);
             free(h_off);
             free(h_box);
+            free(h_box32);
             nbgs_destroy_scene(s);
             return NBGS_ENOMEM;
         }
@@ -337,6 +341,8 @@ static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_des
             for (int a = 0; a < 3; ++a) {
                 h_box[6 * k + a] = batch->box_lo[3 * k + a];
                 h_box[6 * k + 3 + a] = batch->box_hi[3 * k + a];
+                h_box32[6 * k + a] = (float)(batch->box_lo[3 * k + a] - params->box_lo[a]);
+                h_box32[6 * k + 3 + a] = (float)(batch->box_hi[3 * k + a] - params->box_lo[a]);
             }
         }
         h_off[S] = (uint32_t)n;
@@ -349,11 +355,15 @@ static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_des
             rc = cuda_check(s, cudaMemcpy(s->scene_box, h_box, 6 * S * sizeof(double), cudaMemcpyHostToDevice),
                             "batch: boxes");
         if (rc == NBGS_OK)
+            rc = cuda_check(s, cudaMemcpy(s->scene_box32, h_box32, 6 * S * sizeof(float), cudaMemcpyHostToDevice),
+                            "batch: boxes");
+        if (rc == NBGS_OK)
             rc = cuda_check(s, cudaMemcpy(s->scene_mu, batch->mu, S * sizeof(double), cudaMemcpyHostToDevice),
                             "batch: mu");
         free(h_of);
         free(h_off);
         free(h_box);
+        free(h_box32);
         if (rc != NBGS_OK) {
             nbgs_destroy_scene(s);
             return rc;
@@ -400,11 +410,12 @@ void nbgs_destroy_scene(nbgs_scene* s)
 {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
-    void* ps[] = {s->pos_r, s->quat, s->vel, s->hull, s->p32, s->finite, s->stage, s->cell_start, s->cell_end, s->keys[0],
-                  s->keys[1], s->vals[0], s->vals[1], s->radix_hist, s->scan_tmp, s->cand, s->sph_cnt, s->row_cnt,
-                  s->row_off, s->prev_row_off, s->deg, s->adj_off, s->col_count, s->col_off, s->info, s->dep,
-                  s->prog, s->cstart, s->scene_of, s->scene_off, s->scene_box, s->scene_mu, s->scene_vmax,
-                  s->scene_vref, s->scene_rk, s->scene_done, s->scene_res, s->mlp_theta, s->preds};
+    void* ps[] = {s->pos_r, s->quat, s->vel, s->hull, s->p32, s->p32s, s->finite, s->stage, s->cell_start,
+                  s->cell_end, s->keys[0], s->keys[1], s->vals[0], s->vals[1], s->radix_hist, s->scan_tmp,
+                  s->cand, s->sph_cnt, s->row_cnt, s->row_off, s->prev_row_off, s->deg, s->adj_off,
+                  s->col_count, s->col_off, s->info, s->dep, s->prog, s->cstart, s->scene_of, s->scene_off,
+                  s->scene_box, s->scene_box32, s->scene_mu, s->scene_vmax, s->scene_vref, s->scene_rk,
+                  s->scene_done, s->scene_res, s->mlp_theta, s->preds};
     for (void* p : ps) dev_free(s, p);
     free_contact_arrays(s);
     cudaStreamSynchronize(s->stream);
@@ -445,6 +456,7 @@ nbgs_status nbgs_set_bodies(nbgs_scene* s, const double* pos, const double* quat
 {
     NBGS_GUARD(s);
     s->have_prev = false;
+    s->keep_prev = false;
     s->solved = false;
     return run_set_bodies(s, pos, quat, vel, angvel);
 }

@@ -6,7 +6,8 @@
 //   k_grid_setup    cell width >= 2 (r_max + h_max), dims per axis
 //   k_cell_keys     linear cell index of every body
 //   radix sort      (cell, body) pairs, LSD, 8-bit digits, stable
-//   k_cell_ranges   [start, end) of every occupied cell
+//   scan            first sorted slot of every cell, from the cell counts
+//   k_gather_sorted FP32 positions in cell order
 //   k_narrow        per body i: bodies j > i in the 27 neighbour cells whose
 //                   hulls intersect, sorted by j; wall hull tests
 //   scan            contacts per body -> CSR offsets by j1
@@ -261,6 +262,11 @@ struct GridArgs {
     float Lf[3];         // box extents in FP32
     float margin;        // FP32 pre-filter margin: 1e-4 + 1e-6 max(L)
     double pos_err;      // bound on the error of an FP32 relative position (2^-22 max(L))
+    // FP32 wall pre-filter: plane k as n . (x - lo) + pc[k] (= n . x - c),
+    // margin 1e-4 + 4e-6 (max(L) + max |pc|)
+    float pn[kMaxPlanes][3];
+    float pc[kMaxPlanes];
+    float tauf, wmargin;
 };
 
 __device__ __forceinline__ double norm_exact(double x, double y, double z)
@@ -340,42 +346,35 @@ __global__ void k_grid_setup(GridArgs g, DevInfo* info)
     info->ncells = ncells;
 }
 
-__global__ void k_clear_cells(uint32_t* __restrict__ cs, uint32_t* __restrict__ ce, const DevInfo* info)
-{
-    const uint32_t nc = info->ncells;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
-        cs[i] = 0;
-        ce[i] = 0;
-    }
-}
-
 __device__ __forceinline__ int cell_coord(float x, float inv_w, int d)
 {
     const float f = floorf(x * inv_w);
     return f < 0.f ? 0 : (f > (float)(d - 1) ? d - 1 : (int)f);
 }
 
+// Cell key of every body, and the body count of every cell.
 __global__ void k_cell_keys(int64_t n, const float4* __restrict__ p32, const DevInfo* __restrict__ info,
-                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
+                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t* __restrict__ cnt)
 {
     const int d0 = info->dims[0], d1 = info->dims[1], d2 = info->dims[2];
     const float i0 = info->inv_wf[0], i1 = info->inv_wf[1], i2 = info->inv_wf[2];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float4 p = p32[i];
         const int cx = cell_coord(p.x, i0, d0), cy = cell_coord(p.y, i1, d1), cz = cell_coord(p.z, i2, d2);
-        keys[i] = ((uint32_t)cz * (uint32_t)d1 + (uint32_t)cy) * (uint32_t)d0 + (uint32_t)cx;
+        const uint32_t k = ((uint32_t)cz * (uint32_t)d1 + (uint32_t)cy) * (uint32_t)d0 + (uint32_t)cx;
+        keys[i] = k;
         vals[i] = (uint32_t)i;
+        atomicAdd(&cnt[k], 1u);
     }
 }
 
-__global__ void k_cell_ranges(int64_t n, const uint32_t* __restrict__ keys, uint32_t* __restrict__ cs,
-                              uint32_t* __restrict__ ce)
+// The FP32 positions gathered into cell order, so that the narrow phase
+// reads each cell's candidates contiguously.
+__global__ void k_gather_sorted(int64_t n, const uint32_t* __restrict__ vals, const float4* __restrict__ p32,
+                                float4* __restrict__ p32s)
 {
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t k = keys[s];
-        if (s == 0 || keys[s - 1] != k) cs[k] = (uint32_t)s;
-        if (s == n - 1 || keys[s + 1] != k) ce[k] = (uint32_t)(s + 1);
-    }
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        p32s[s] = p32[vals[s]];
 }
 
 // Minimum-image difference a - b along one axis (periodic: |d| <= L/2).
@@ -399,15 +398,83 @@ __device__ __forceinline__ bool wall_kept(const double nrm[3], double c, double4
 
 // Per body i (visited in cell order for locality): hull-intersecting
 // partners j > i from the 27 neighbour cells, sorted ascending; wall count.
+// cs[c] is the first sorted slot of cell c for every cell (cs[ncells] = n),
+// so the three cells x - 1 .. x + 1 of a (y, z) row are one contiguous
+// range; a periodic image adds one constant shift to a whole range.
+struct NarrowPair {
+    uint32_t list[kCandCap];
+    int cnt;
+};
+
+__device__ __forceinline__ void narrow_range(uint32_t t0, uint32_t t1, float sx, float sy, float sz, uint32_t i,
+                                             uint32_t si, const float4& qi, const double4_32a& pi, double hi_,
+                                             const uint32_t* __restrict__ svals, const float4* __restrict__ p32s,
+                                             const double4_32a* __restrict__ pos_r, const double* __restrict__ hull,
+                                             const GridArgs& g, const SceneView& V, double L0, double L1, double L2,
+                                             NarrowPair& P)
+{
+    for (uint32_t t = t0; t < t1; ++t) {
+        const uint32_t j = svals[t];
+        if (j <= i) continue;
+        if (V.batch && V.scene_of[j] != si) continue;   // scenes never touch
+        // Conservative FP32 pre-filter (FP64 throughput is scarce on this GPU).
+        // R = r_a + h_a + r_b + h_b bounds d for every kept pair.  The FP32
+        // relative positions are off by at most pos_err per coordinate, the
+        // periodic shift adds an ulp of L, so the FP32 distance is within
+        // 1e-6 max(L) of d; the FP32 square and reach add relative errors
+        // below 4e-7 and 1.2e-7, covered by the extra 1e-4 while R < ~385.
+        // So (fl(R) + margin)^2 >= fl(d^2) for every kept pair; only the
+        // pairs that pass take the exact FP64 test.
+        const float4 qj = p32s[t];
+        const float fx = (qi.x - qj.x) + sx, fy = (qi.y - qj.y) + sy, fz = (qi.z - qj.z) + sz;
+        const float rr = qi.w + qj.w + g.margin;
+        if (fx * fx + fy * fy + fz * fz > rr * rr) continue;
+        const double4_32a pj = pos_r[j];
+        const double dx3 = min_image(xsub(pi.x, pj.x), g.periodic[0], L0);
+        const double dy3 = min_image(xsub(pi.y, pj.y), g.periodic[1], L1);
+        const double dz3 = min_image(xsub(pi.z, pj.z), g.periodic[2], L2);
+        const double d = norm_exact(dx3, dy3, dz3);
+        // Sect. 4: keep the pair iff the hulls intersect
+        if (xsub(xsub(d, pi.w), pj.w) <= xadd(hi_, hull[j])) {
+            if (P.cnt < kCandCap) {
+                // insertion keeps the list sorted by j
+                int k = P.cnt;
+                while (k > 0 && P.list[k - 1] > j) {
+                    P.list[k] = P.list[k - 1];
+                    --k;
+                }
+                P.list[k] = j;
+            }
+            ++P.cnt;
+        }
+    }
+}
+
+// Neighbour index along one axis: the cell and the shift of the periodic
+// image (the image of cell d - 1 left of cell 0 sits at -L); false when the
+// cell lies outside a bounded axis.
+__device__ __forceinline__ bool axis_cell(int c, int d, int periodic, float Lf, int& out, float& shift)
+{
+    shift = 0.f;
+    if (c >= 0 && c < d) {
+        out = c;
+        return true;
+    }
+    if (!periodic || d < 3) return false;
+    out = c < 0 ? c + d : c - d;
+    shift = c < 0 ? Lf : -Lf;
+    return true;
+}
+
 __global__ void __launch_bounds__(128)
 k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ svals,
-         const double4_32a* __restrict__ pos_r, const double* __restrict__ hull, const float4* __restrict__ p32,
-         const uint32_t* __restrict__ cs,
-         const uint32_t* __restrict__ ce, GridArgs g, Planes planes, SceneView V, DevInfo* info,
+         const double4_32a* __restrict__ pos_r, const double* __restrict__ hull, const float4* __restrict__ p32s,
+         const uint32_t* __restrict__ cs, GridArgs g, Planes planes, SceneView V, DevInfo* info,
          uint32_t* __restrict__ cand, uint32_t* __restrict__ sph_cnt, uint32_t* __restrict__ row_cnt)
 {
     const int d0 = info->dims[0], d1 = info->dims[1], d2 = info->dims[2];
     const double L0 = g.hi[0] - g.lo[0], L1 = g.hi[1] - g.lo[1], L2 = g.hi[2] - g.lo[2];
+    const bool wrap_x = g.periodic[0] && d0 >= 3;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t i = svals[s];
         const uint32_t key = skeys[s];
@@ -416,73 +483,32 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
         const int cz = (int)(key / ((uint32_t)d0 * (uint32_t)d1));
         const double4_32a pi = pos_r[i];
         const double hi_ = hull[i];
-        const float4 qi = p32[i];
+        const float4 qi = p32s[s];
         const uint32_t si = V.batch ? V.scene_of[i] : 0u;
-        uint32_t list[kCandCap];
-        int cnt = 0;
+        NarrowPair P;
+        P.cnt = 0;
+        const int xlo = cx > 0 ? cx - 1 : 0, xhi = cx + 1 < d0 ? cx + 1 : d0 - 1;
         for (int dz = -1; dz <= 1; ++dz) {
-            int z = cz + dz;
-            if (z < 0 || z >= d2) {
-                if (!g.periodic[2] || d2 < 3) continue;
-                z = (z + d2) % d2;
-            }
+            int z;
+            float sz;
+            if (!axis_cell(cz + dz, d2, g.periodic[2], g.Lf[2], z, sz)) continue;
             for (int dy = -1; dy <= 1; ++dy) {
-                int y = cy + dy;
-                if (y < 0 || y >= d1) {
-                    if (!g.periodic[1] || d1 < 3) continue;
-                    y = (y + d1) % d1;
-                }
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int x = cx + dx;
-                    if (x < 0 || x >= d0) {
-                        if (!g.periodic[0] || d0 < 3) continue;
-                        x = (x + d0) % d0;
-                    }
-                    const uint32_t c = ((uint32_t)z * (uint32_t)d1 + (uint32_t)y) * (uint32_t)d0 + (uint32_t)x;
-                    const uint32_t e = ce[c];
-                    for (uint32_t t = cs[c]; t < e; ++t) {
-                        const uint32_t j = svals[t];
-                        if (j <= i) continue;
-                        if (V.batch && V.scene_of[j] != si) continue;   // scenes never touch
-                        // Conservative FP32 pre-filter (FP64 throughput is scarce on this
-                        // GPU).  R = r_a + h_a + r_b + h_b bounds d for every kept pair.
-                        // The FP32 relative positions are off by at most pos_err per
-                        // coordinate, the minimum image adds an ulp of L, so the FP32
-                        // distance is within 1e-6 max(L) of d; the FP32 square and reach
-                        // add relative errors below 4e-7 and 1.2e-7, covered by the extra
-                        // 1e-4 while R < ~385.  So (fl(R) + margin)^2 >= fl(d^2) for every
-                        // kept pair; only the pairs that pass take the exact FP64 test.
-                        {
-                            const float4 qj = p32[j];
-                            float fx = qi.x - qj.x, fy = qi.y - qj.y, fz = qi.z - qj.z;
-                            if (g.periodic[0]) fx = fx > 0.5f * g.Lf[0] ? fx - g.Lf[0] : (fx < -0.5f * g.Lf[0] ? fx + g.Lf[0] : fx);
-                            if (g.periodic[1]) fy = fy > 0.5f * g.Lf[1] ? fy - g.Lf[1] : (fy < -0.5f * g.Lf[1] ? fy + g.Lf[1] : fy);
-                            if (g.periodic[2]) fz = fz > 0.5f * g.Lf[2] ? fz - g.Lf[2] : (fz < -0.5f * g.Lf[2] ? fz + g.Lf[2] : fz);
-                            const float rr = qi.w + qj.w + g.margin;
-                            if (fx * fx + fy * fy + fz * fz > rr * rr) continue;
-                        }
-                        const double4_32a pj = pos_r[j];
-                        const double dx3 = min_image(xsub(pi.x, pj.x), g.periodic[0], L0);
-                        const double dy3 = min_image(xsub(pi.y, pj.y), g.periodic[1], L1);
-                        const double dz3 = min_image(xsub(pi.z, pj.z), g.periodic[2], L2);
-                        const double d = norm_exact(dx3, dy3, dz3);
-                        // Sect. 4: keep the pair iff the hulls intersect
-                        if (xsub(xsub(d, pi.w), pj.w) <= xadd(hi_, hull[j])) {
-                            if (cnt < kCandCap) {
-                                // insertion keeps the list sorted by j
-                                int k = cnt;
-                                while (k > 0 && list[k - 1] > j) {
-                                    list[k] = list[k - 1];
-                                    --k;
-                                }
-                                list[k] = j;
-                            }
-                            ++cnt;
-                        }
-                    }
-                }
+                int y;
+                float sy;
+                if (!axis_cell(cy + dy, d1, g.periodic[1], g.Lf[1], y, sy)) continue;
+                const uint32_t row = ((uint32_t)z * (uint32_t)d1 + (uint32_t)y) * (uint32_t)d0;
+                narrow_range(cs[row + xlo], cs[row + xhi + 1], 0.f, sy, sz, i, si, qi, pi, hi_, svals, p32s, pos_r,
+                             hull, g, V, L0, L1, L2, P);
+                if (wrap_x && cx == 0)
+                    narrow_range(cs[row + d0 - 1], cs[row + d0], g.Lf[0], sy, sz, i, si, qi, pi, hi_, svals, p32s,
+                                 pos_r, hull, g, V, L0, L1, L2, P);
+                if (wrap_x && cx == d0 - 1)
+                    narrow_range(cs[row], cs[row + 1], -g.Lf[0], sy, sz, i, si, qi, pi, hi_, svals, p32s, pos_r,
+                                 hull, g, V, L0, L1, L2, P);
             }
         }
+        int cnt = P.cnt;
+        uint32_t* list = P.list;
         if (cnt > kCandCap) {
             atomicOr(&info->err, kErrCand);
             atomicMax(&info->cand_need, (uint32_t)cnt);
@@ -490,16 +516,29 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
         }
         uint32_t* out = cand + (int64_t)i * kCandCap;
         for (int k = 0; k < cnt; ++k) out[k] = list[k];
-        int wcnt = 0;
+        // walls: a conservative FP32 test of the signed distance (errors as
+        // for the pairs, within wmargin), the exact FP64 test for the rest
+        uint32_t wmask = 0;
         const int nwall = planes.count + (V.batch ? 6 : 0);
+        const float reach = qi.w + g.tauf + g.wmargin;
         for (int k = 0; k < nwall; ++k) {
+            float sdf;
+            if (k < planes.count) {
+                sdf = g.pn[k][0] * qi.x + g.pn[k][1] * qi.y + g.pn[k][2] * qi.z + g.pc[k];
+            } else {
+                const int f = k - planes.count, axis = f >> 1;
+                const float q = axis == 0 ? qi.x : (axis == 1 ? qi.y : qi.z);
+                const float* b = V.box32 + 6 * (int64_t)si;
+                sdf = (f & 1) == 0 ? q - b[axis] : b[3 + axis] - q;
+            }
+            if (sdf > reach) continue;
             double nrm[3], c, sd, xi;
             uint32_t widx;
             wall_plane(planes, V, si, k, nrm, c, widx);
-            if (wall_kept(nrm, c, pi, hi_, g.tau, sd, xi)) ++wcnt;
+            if (wall_kept(nrm, c, pi, hi_, g.tau, sd, xi)) wmask |= 1u << k;
         }
-        sph_cnt[i] = (uint32_t)cnt;
-        row_cnt[i] = (uint32_t)(cnt + wcnt);
+        sph_cnt[i] = (uint32_t)cnt | (wmask << 8);
+        row_cnt[i] = (uint32_t)(cnt + __popc(wmask));
     }
 }
 
@@ -515,9 +554,11 @@ __global__ void k_write_contacts(int64_t n, int64_t ccap, const uint32_t* __rest
     const double L0 = g.hi[0] - g.lo[0], L1 = g.hi[1] - g.lo[1], L2 = g.hi[2] - g.lo[2];
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t i = svals[s];
+        const uint32_t packed = sph_cnt[i];
+        if (packed == 0) continue;   // no contact in this row
+        const uint32_t ns = packed & 0xFFu, wm = packed >> 8;
         const double4_32a pi = pos_r[i];
         int64_t idx = row_off[i];
-        const uint32_t ns = sph_cnt[i];
         const uint32_t* lst = cand + (int64_t)i * kCandCap;
         for (uint32_t k = 0; k < ns; ++k, ++idx) {
             const uint32_t j = lst[k];
@@ -545,14 +586,15 @@ __global__ void k_write_contacts(int64_t n, int64_t ccap, const uint32_t* __rest
             cgeo[idx] = geo;
             clev[idx] = make_double2(xsub(d, pj.w), pj.w);
         }
+        if (wm == 0) continue;
         const double hi_ = hull[i];
         const uint32_t si = V.batch ? V.scene_of[i] : 0u;
-        const int nwall = planes.count + (V.batch ? 6 : 0);
-        for (int k = 0; k < nwall; ++k) {
+        for (uint32_t m = wm; m; m &= m - 1) {   // the walls k_narrow kept, in wall order
+            const int k = __ffs(m) - 1;
             double nrm[3], c, sd, xi;
             uint32_t widx;
             wall_plane(planes, V, si, k, nrm, c, widx);
-            if (!wall_kept(nrm, c, pi, hi_, g.tau, sd, xi)) continue;
+            wall_kept(nrm, c, pi, hi_, g.tau, sd, xi);
             if (idx < ccap) {
                 cj1[idx] = i;
                 cj2[idx] = widx;
@@ -573,6 +615,7 @@ SceneView scene_view(const nbgs_scene* s)
     v.scene_of = s->scene_of;
     v.scene_off = s->scene_off;
     v.box = s->scene_box;
+    v.box32 = s->scene_box32;
     v.mu = s->scene_mu;
     v.vref = s->scene_vref;
     return v;
@@ -597,6 +640,18 @@ static GridArgs grid_args(const nbgs_scene* s)
     }
     g.margin = (float)(1e-4 + 1e-6 * lmax);
     g.pos_err = std::ldexp(lmax, -22);
+    double cmax = 0.0;
+    for (int k = 0; k < s->planes.count; ++k) {
+        double off = -s->planes.c[k];
+        for (int a = 0; a < 3; ++a) {
+            g.pn[k][a] = (float)s->planes.n[k][a];
+            off += s->planes.n[k][a] * g.lo[a];
+        }
+        g.pc[k] = (float)off;
+        cmax = std::max(cmax, std::fabs(off));
+    }
+    g.tauf = (float)g.tau;
+    g.wmargin = (float)(1e-4 + 4e-6 * (lmax + cmax));
     return g;
 }
 
@@ -614,9 +669,10 @@ nbgs_status run_detect(nbgs_scene* s)
         std::swap(s->cworld, s->prev_P);
         s->prev_count = s->n_contacts;
         s->have_prev = true;
-    } else {
+    } else if (!s->keep_prev) {   // a restored checkpoint already filled the previous-step arrays
         s->have_prev = false;
     }
+    s->keep_prev = false;
     s->detected = s->coloured = s->solved = false;
     s->n_contacts = 0;
     cudaMemsetAsync(s->info, 0, offsetof(DevInfo, cell_w), st);   // hmax, vmax
@@ -637,14 +693,17 @@ nbgs_status run_detect(nbgs_scene* s)
         k_hull<double><<<gb, T, 0, st>>>(n, (const double4_32a*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hull,
                                          s->p32, g, s->info, s->scene_of, s->scene_vmax);
     k_grid_setup<<<1, 1, 0, st>>>(g, s->info);
-    k_clear_cells<<<grid_for(s->max_cells, T, 8, s->num_sms), T, 0, st>>>(s->cell_start, s->cell_end, s->info);
-    k_cell_keys<<<gb, T, 0, st>>>(n, s->p32, s->info, s->keys[0], s->vals[0]);
+    cudaMemsetAsync(s->cell_end, 0, (size_t)s->max_cells * sizeof(uint32_t), st);   // cell counts
+    k_cell_keys<<<gb, T, 0, st>>>(n, s->p32, s->info, s->keys[0], s->vals[0], s->cell_end);
     if (s->timing) s->phase_launches[0] += 4;
     nbgs_status rc = radix_sort_pairs(s, s->keys[0], s->vals[0], s->keys[1], s->vals[1], n, s->key_bits);
     if (rc != NBGS_OK) return rc;
-    k_cell_ranges<<<gb, T, 0, st>>>(n, s->keys[0], s->cell_start, s->cell_end);
+    // first sorted slot of every cell (empty ones included); cell_start[max_cells] = n
+    rc = exclusive_scan_u32(s, s->cell_end, s->cell_start, s->max_cells, nullptr);
+    if (rc != NBGS_OK) return rc;
+    k_gather_sorted<<<gb, T, 0, st>>>(n, s->vals[0], s->p32, s->p32s);
     k_narrow<<<grid_for(n, 128, 16, s->num_sms), 128, 0, st>>>(n, s->keys[0], s->vals[0], s->pos_r, s->hull,
-                                                                 s->p32, s->cell_start, s->cell_end, g, s->planes,
+                                                                 s->p32s, s->cell_start, g, s->planes,
                                                                  scene_view(s), s->info, s->cand, s->sph_cnt,
                                                                  s->row_cnt);
     rc = exclusive_scan_u32(s, s->row_cnt, s->row_off, n, &s->info->n_contacts);

@@ -57,6 +57,7 @@ struct SceneView {
     const uint32_t* scene_of;     // n
     const uint32_t* scene_off;    // S + 1
     const double* box;            // S x 6
+    const float* box32;           // S x 6: box - global box lo, FP32 (the wall pre-filter)
     const double* mu;             // S
     const double* vref;           // S
 };
@@ -225,6 +226,7 @@ struct nbgs_scene {
     uint32_t* scene_of = nullptr;       // n: scene of each body
     uint32_t* scene_off = nullptr;      // S + 1: first body of each scene
     double* scene_box = nullptr;        // S x 6: lo xyz, hi xyz
+    float* scene_box32 = nullptr;       // S x 6: the same minus the global box lo, FP32
     double* scene_mu = nullptr;         // S
     unsigned long long* scene_vmax = nullptr;  // S: max |v| at step start (bits)
     double* scene_vref = nullptr;       // S
@@ -239,14 +241,15 @@ struct nbgs_scene {
     void* vel = nullptr;          // R4[2n]
     double* hull = nullptr;
     float4* p32 = nullptr;        // (x - lo, y - lo, z - lo, r + h) in FP32: cell keys and the narrow-phase pre-filter
+    float4* p32s = nullptr;       // p32 in cell order (the narrow phase's candidate reads)
     uint8_t* finite = nullptr;    // body takes impulses (1/m > 0 or 1/I > 0)
     double* stage = nullptr;      // 13 n doubles for state transfer
     // grid
     int dims_max[3] = {1, 1, 1};
     int64_t max_cells = 1;
     int key_bits = 1;
-    uint32_t* cell_start = nullptr;
-    uint32_t* cell_end = nullptr;
+    uint32_t* cell_start = nullptr;   // max_cells + 1: first sorted slot of every cell
+    uint32_t* cell_end = nullptr;     // max_cells: bodies per cell
     uint32_t* keys[2] = {nullptr, nullptr};
     uint32_t* vals[2] = {nullptr, nullptr};
     uint32_t* radix_hist = nullptr;
@@ -255,7 +258,7 @@ struct nbgs_scene {
     int64_t scan_tmp_len = 0;
     // candidates
     uint32_t* cand = nullptr;      // n * kCandCap
-    uint32_t* sph_cnt = nullptr;   // sphere contacts per body
+    uint32_t* sph_cnt = nullptr;   // sphere contacts per body (bits 0-7), kept-wall mask (bits 8-31)
     uint32_t* row_cnt = nullptr;   // contacts per body (sphere + wall)
     uint32_t* row_off = nullptr;   // n + 1
     // contacts (canonical)
@@ -272,6 +275,7 @@ struct nbgs_scene {
     double4_32a* prev_P = nullptr;     // world-frame impulse
     int64_t prev_count = 0;
     bool have_prev = false;
+    bool keep_prev = false;            // the previous-step arrays come from a checkpoint
     // colouring
     uint32_t* deg = nullptr;       // n + 1
     uint32_t* adj_off = nullptr;   // n + 1
