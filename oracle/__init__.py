@@ -92,6 +92,8 @@ def lib():
         L.oracle_destroy_scene.argtypes = [C.c_void_p]
         L.oracle_destroy_scene.restype = None
         L.oracle_add_plane.argtypes = [C.c_void_p, dp, C.c_double]
+        L.oracle_add_cone.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_double, C.c_double]
+        L.oracle_cone_distance.argtypes = [C.c_void_p, C.c_int32, dp, dp, dp]
         L.oracle_set_mass_properties.argtypes = [C.c_void_p, dp, dp]
         L.oracle_set_bodies.argtypes = [C.c_void_p, dp, dp, dp, dp]
         L.oracle_get_bodies.argtypes = [C.c_void_p, dp, dp, dp, dp]
@@ -170,6 +172,19 @@ class OracleScene:
             nn = _f64(n_)
             _check(L.oracle_add_plane(self._h, _dp(nn), float(c_)), "add_plane")
             self.n_planes += 1
+        self.n_cones = 0
+        for cn in scene.get("cones", []):
+            _check(L.oracle_add_cone(self._h, _dp(_f64(cn["apex"])), _dp(_f64(cn["axis"])), float(cn["half_angle"]),
+                                     float(cn["r_orifice"]), float(cn["r_top"])), "add_cone")
+            self.n_cones += 1
+
+    def cone_distance(self, k: int, x):
+        """(case, signed distance, unit normal) of point x against cone k:
+        case 0 above the frustum, 1 face, 2 orifice rim."""
+        x = _f64(x)
+        sd, nrm = C.c_double(), np.empty(3)
+        case = lib().oracle_cone_distance(self._h, int(k), _dp(x), C.byref(sd), _dp(nrm))
+        return int(case), float(sd.value), nrm
 
     def close(self):
         if getattr(self, "_h", None):

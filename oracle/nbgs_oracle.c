@@ -20,6 +20,12 @@ struct oracle_scene {
     int32_t nplanes;
     double plane_n[ORACLE_MAX_PLANES][3];
     double plane_c[ORACLE_MAX_PLANES];
+    int32_t ncones;
+    struct {
+        double apex[3], axis[3];
+        double sa, ca;           /* sin, cos of the half-angle */
+        double s_o, s_t;         /* orifice and top along a generatrix, from the apex */
+    } cone[ORACLE_MAX_CONES];
 
     /* contacts of the current step, canonical order */
     int64_t nc, cap;
@@ -181,6 +187,67 @@ int oracle_create_scene(const oracle_params* prm, int64_t n,
     return 0;
 }
 
+int oracle_add_cone(oracle_scene* s, const double apex[3], const double axis[3], double half_angle,
+                    double r_orifice, double r_top)
+{
+    if (!s || !apex || !axis || s->ncones >= ORACLE_MAX_CONES) return 1;
+    if (!(half_angle > 0.0 && half_angle < 1.5707963267948966) || !(r_orifice >= 0.0) || !(r_top > r_orifice))
+        return 1;
+    double len = sqrt((axis[0] * axis[0] + axis[1] * axis[1]) + axis[2] * axis[2]);
+    if (!(len > 0.0)) return 1;
+    int k = s->ncones++;
+    for (int d = 0; d < 3; ++d) {
+        s->cone[k].apex[d] = apex[d];
+        s->cone[k].axis[d] = axis[d] / len;
+    }
+    s->cone[k].sa = sin(half_angle);
+    s->cone[k].ca = cos(half_angle);
+    s->cone[k].s_o = r_orifice / s->cone[k].sa;
+    s->cone[k].s_t = r_top / s->cone[k].sa;
+    return 0;
+}
+
+/* Distance from x to the frustum, worked in the half-plane through the axis
+ * and x: zeta = height of x above the apex along the axis, rho = distance
+ * from the axis, e = unit radial direction.  A generatrix runs along
+ * g = (sin a, cos a) in (rho, zeta); the face is the segment s in [s_o, s_t]
+ * of it, the solid lies on the outer side, and the inward unit normal of the
+ * face is (-cos a, sin a).  Position along the generatrix of the foot of x:
+ * s = rho sin a + zeta cos a.  Face (s_o <= s <= s_t): signed distance
+ * zeta sin a - rho cos a, normal -cos a e + sin a axis.  Below the face
+ * (s < s_o) the nearest point of the solid is on the orifice rim, the circle
+ * (rho_o, zeta_o) = s_o (sin a, cos a): distance |(rho - rho_o, zeta - zeta_o)|,
+ * normal along that difference.  On the axis (rho = 0) e is undefined: the
+ * face distance is kept and the normal is the axis. */
+int oracle_cone_distance(const oracle_scene* s, int32_t k, const double x[3], double* sd, double n[3])
+{
+    const double* A = s->cone[k].apex;
+    const double* ax = s->cone[k].axis;
+    const double sa = s->cone[k].sa, ca = s->cone[k].ca;
+    double d[3], e[3];
+    for (int i = 0; i < 3; ++i) d[i] = x[i] - A[i];
+    double zeta = (d[0] * ax[0] + d[1] * ax[1]) + d[2] * ax[2];
+    for (int i = 0; i < 3; ++i) e[i] = d[i] - zeta * ax[i];
+    double rho = sqrt((e[0] * e[0] + e[1] * e[1]) + e[2] * e[2]);
+    double s_gen = rho * sa + zeta * ca;
+    if (s_gen > s->cone[k].s_t) return 0;
+    if (rho > 0.0)
+        for (int i = 0; i < 3; ++i) e[i] = e[i] / rho;
+    if (s_gen >= s->cone[k].s_o) {
+        *sd = zeta * sa - rho * ca;
+        for (int i = 0; i < 3; ++i) n[i] = rho > 0.0 ? sa * ax[i] - ca * e[i] : ax[i];
+        return 1;
+    }
+    double drho = rho - s->cone[k].s_o * sa, dzeta = zeta - s->cone[k].s_o * ca;
+    double dist = sqrt(drho * drho + dzeta * dzeta);
+    *sd = dist;
+    for (int i = 0; i < 3; ++i) {
+        if (dist > 0.0 && rho > 0.0) n[i] = (drho * e[i] + dzeta * ax[i]) / dist;
+        else n[i] = ax[i];
+    }
+    return 2;
+}
+
 int oracle_add_plane(oracle_scene* s, const double n[3], double c)
 {
     if (!s || !n || s->nplanes >= ORACLE_MAX_PLANES) return 1;
@@ -327,6 +394,18 @@ int oracle_detect_contacts(oracle_scene* s, int64_t* n_contacts)
             double xi = sd - s->r[a];
             if (xi <= (s->h[a] + P->tau)) {
                 if (push_contact(s, (uint32_t)a, (uint32_t)(s->n + k), nk, xi, sd, 0.0)) return 2;
+            }
+        }
+        /* Sphere-cone pairs (a, cone k): j2 = n + nplanes + k.  The point of
+         * the solid closest to x_a is x_a - sd n (oracle_cone_distance), so
+         * the contact has the form of a wall contact: xi = sd - r_a,
+         * l_a = -sd n, and the cone's hull radius is tau. */
+        for (int32_t k = 0; k < s->ncones; ++k) {
+            double sd, nk[3];
+            if (!oracle_cone_distance(s, k, &s->x[3 * a], &sd, nk)) continue;
+            double xi = sd - s->r[a];
+            if (xi <= (s->h[a] + P->tau)) {
+                if (push_contact(s, (uint32_t)a, (uint32_t)(s->n + s->nplanes + k), nk, xi, sd, 0.0)) return 2;
             }
         }
     }

@@ -37,6 +37,7 @@ extern "C" {
 #endif
 
 #define ORACLE_MAX_PLANES 16
+#define ORACLE_MAX_CONES 4
 
 enum { ORACLE_WARM_NONE = 0, ORACLE_WARM_PREV = 1 };
 
@@ -79,6 +80,19 @@ void oracle_destroy_scene(oracle_scene* s);
 /* Half-space wall {y : n . y <= c}; n must be a unit vector pointing out of
  * the wall solid.  Walls are bodies of infinite mass with index n_bodies + k. */
 int  oracle_add_plane(oracle_scene* s, const double n[3], double c);
+/* Conical hopper wall: the frustum of the cone with apex `apex`, axis
+ * `axis` (normalised here; the cone opens along it) and half-angle
+ * half_angle (radians, in (0, pi/2)) between the orifice circle of radius
+ * r_orifice and the top circle of radius r_top.  The solid lies outside the
+ * cone; spheres inside touch its face or, below the face, the orifice rim.
+ * sin and cos of the half-angle are taken with the C library.  Cones are
+ * walls with index n_bodies + n_planes + k (planes are added first). */
+int  oracle_add_cone(oracle_scene* s, const double apex[3], const double axis[3], double half_angle,
+                     double r_orifice, double r_top);
+/* Signed distance of x from cone k and the unit normal pointing from the
+ * surface to x; returns 0 when x lies above the frustum (no contact), 1 on
+ * the face, 2 at the rim.  Exported for the known-answer tests. */
+int  oracle_cone_distance(const oracle_scene* s, int32_t k, const double x[3], double* sd, double n[3]);
 /* Override inverse mass / inverse inertia (e.g. 0 = locked rotation). */
 int  oracle_set_mass_properties(oracle_scene* s, const double* invm, const double* invI);
 int  oracle_set_bodies(oracle_scene* s, const double* pos, const double* quat,

@@ -13,10 +13,12 @@ A scene is a dict::
                 warm_start, colour_seed, precision},
      "pos": (n, 3) f64, "vel": (n, 3) f64, "angvel": (n, 3) f64,
      "radius": (n,) f64, "density": (n,) f64,
-     "planes": [((nx, ny, nz), c), ...]}   # wall solid {y : n . y <= c}
+     "planes": [((nx, ny, nz), c), ...],   # wall solid {y : n . y <= c}
+     "cones": [{apex, axis, half_angle, r_orifice, r_top}, ...]}   # hopper walls
 
 Workload shapes follow the paper's setups (granular gas, Sect. 7.2.1;
-hexagonal close packing, Sect. 7.2.2) scaled to one GPU.
+hexagonal close packing, Sect. 7.2.2) scaled to one GPU, plus a conical
+hopper discharge.
 """
 from __future__ import annotations
 
@@ -58,7 +60,7 @@ def box_walls(lo, hi, axes=(0, 1, 2)) -> list:
     return planes
 
 
-def _scene(name, params, pos, vel, angvel, radius, density, planes):
+def _scene(name, params, pos, vel, angvel, radius, density, planes, cones=()):
     n = len(radius)
     return {
         "name": name,
@@ -69,7 +71,15 @@ def _scene(name, params, pos, vel, angvel, radius, density, planes):
         "radius": np.ascontiguousarray(radius, dtype=np.float64).reshape(n),
         "density": np.ascontiguousarray(density, dtype=np.float64).reshape(n),
         "planes": list(planes),
+        "cones": [dict(c) for c in cones],
     }
+
+
+def cone(apex, axis, half_angle_deg: float, r_orifice: float, r_top: float) -> dict:
+    """A conical hopper wall (frustum of the cone with the given apex, axis
+    and half-angle between the orifice radius and the top radius)."""
+    return {"apex": tuple(float(a) for a in apex), "axis": tuple(float(a) for a in axis),
+            "half_angle": math.radians(half_angle_deg), "r_orifice": float(r_orifice), "r_top": float(r_top)}
 
 
 # ---------------------------------------------------------------------------
@@ -214,6 +224,75 @@ def sphere_on_plane(radius: float = 0.5, density: float = 1.0, gap: float = 0.0,
     pos = np.array([[0.0, 0.0, radius + gap]])
     return _scene("sphere_on_plane", prm, pos, np.zeros((1, 3)), np.zeros((1, 3)), [radius], [density],
                   [((0.0, 0.0, 1.0), 0.0)])
+
+
+def sphere_in_cone(radius: float = 0.5, half_angle_deg: float = 30.0, height: float = None,
+                   **params) -> dict:
+    """One sphere on the axis of an upward-opening cone (apex at the origin,
+    orifice radius 0.2 r so that the sphere cannot pass); at rest it touches
+    the cone along a circle with its centre r / sin(a) above the apex."""
+    a = math.radians(half_angle_deg)
+    z = radius / math.sin(a) if height is None else height
+    prm = default_params(box_lo=(-5, -5, -5), box_hi=(5, 5, 10), **params)
+    pos = np.array([[0.0, 0.0, z]])
+    return _scene("sphere_in_cone", prm, pos, np.zeros((1, 3)), np.zeros((1, 3)), [radius], [1.0], [],
+                  [cone((0, 0, 0), (0, 0, 1), half_angle_deg, 0.2 * radius, 4.0)])
+
+
+def hopper(n: int = 2_000_000, seed: int = 0, half_angle_deg: float = 30.0, r_lo: float = 0.4, r_hi: float = 0.6,
+           orifice_diameter: float = None, spacing: float = None, jitter: float = 0.02, **params) -> dict:
+    """Conical hopper discharge: n spheres r ~ U(r_lo, r_hi) on a jittered
+    cubic lattice filling an upward-opening cone of the given half-angle
+    from just above its orifice (diameter 8 r_mean unless given), falling
+    under gravity through the orifice onto a floor 20 r_mean below it.
+    mu = 0.5, dt = 5e-4."""
+    rng = np.random.default_rng(seed)
+    a = math.radians(half_angle_deg)
+    r_mean = 0.5 * (r_lo + r_hi)
+    d_o = 8.0 * r_mean if orifice_diameter is None else orifice_diameter
+    r_o = 0.5 * d_o
+    sp = 2.0 * r_hi * 1.05 if spacing is None else spacing
+    ta = math.tan(a)
+    z_o = r_o / ta   # orifice height above the apex
+    # cone volume above the orifice level that holds n lattice sites
+    def sites(z_top):
+        zs = np.arange(z_o + r_hi + 0.05, z_top, sp)
+        tot = 0
+        for z in zs:
+            rad = z * ta - (r_hi + 0.01) / math.cos(a)
+            if rad <= 0:
+                continue
+            m = int(rad // sp)
+            tot += int(np.count_nonzero((np.add.outer(np.arange(-m, m + 1) ** 2, np.arange(-m, m + 1) ** 2)) * sp * sp
+                                        <= rad * rad))
+        return tot
+    z_top = z_o + 4.0 * sp
+    while sites(z_top) < n:
+        z_top *= 1.15
+    pts = []
+    for z in np.arange(z_o + r_hi + 0.05, z_top, sp):
+        rad = z * ta - (r_hi + 0.01) / math.cos(a)
+        if rad <= 0:
+            continue
+        m = int(rad // sp)
+        g = np.arange(-m, m + 1) * sp
+        gx, gy = np.meshgrid(g, g, indexing="ij")
+        keep = gx * gx + gy * gy <= rad * rad
+        pts.append(np.stack([gx[keep], gy[keep], np.full(int(keep.sum()), z)], -1))
+        if sum(len(q) for q in pts) >= n:
+            break
+    pos = np.concatenate(pts)[:n]
+    pos = pos + rng.uniform(-jitter, jitter, pos.shape)
+    radius = rng.uniform(r_lo, r_hi, n)
+    r_top = (pos[:, 2].max() + sp) * ta + 2.0 * r_hi
+    floor = -20.0 * r_mean
+    half = r_top + 2.0
+    kw = dict(dt=5e-4, mu=0.5, tau=0.01 * r_lo)
+    kw.update(params)
+    prm = default_params(box_lo=(-half, -half, floor - 1.0), box_hi=(half, half, r_top / ta + 2.0), **kw)
+    planes = [((0.0, 0.0, 1.0), floor)]
+    return _scene(f"hopper_{n}", prm, pos, np.zeros((n, 3)), np.zeros((n, 3)), radius, np.ones(n), planes,
+                  [cone((0, 0, 0), (0, 0, 1), half_angle_deg, r_o, r_top)])
 
 
 def head_on(ra: float = 0.5, rb: float = 0.4, rho_a: float = 1.0, rho_b: float = 2.0, gap: float = 0.01,

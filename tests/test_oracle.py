@@ -453,3 +453,132 @@ def test_batch_layout_and_sizes():
         for j in range(i):
             lo2, hi2 = boxes[j]
             assert np.any(hi <= lo2) or np.any(hi2 <= lo)   # disjoint boxes
+
+
+# ---------------------------------------------------------------------------
+# conical hopper walls
+# ---------------------------------------------------------------------------
+
+def _cone_scene(oracle_mod, apex=(0.0, 0.0, 0.0), axis=(0.0, 0.0, 1.0), deg=30.0, r_o=2.0, r_t=12.0):
+    sc = scenes.sphere_on_plane(gap=50.0)
+    sc["planes"] = []
+    sc["cones"] = [scenes.cone(apex, axis, deg, r_o, r_t)]
+    return oracle_mod.OracleScene(sc)
+
+
+def _frustum_samples(apex, axis, deg, s_lo, s_hi, ns=600, nphi=720):
+    """Points of the cone surface at generatrix distances [s_lo, s_hi] from
+    the apex, built from the cone's definition (apex, axis, half-angle)."""
+    axis = np.asarray(axis, float) / np.linalg.norm(axis)
+    helper = np.array([1.0, 0.0, 0.0]) if abs(axis[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    u = np.cross(axis, helper)
+    u /= np.linalg.norm(u)
+    w = np.cross(axis, u)
+    a = math.radians(deg)
+    s = np.linspace(s_lo, s_hi, ns)[:, None]
+    phi = np.linspace(0.0, 2.0 * math.pi, nphi, endpoint=False)[None, :]
+    radial = np.cos(phi)[..., None] * u + np.sin(phi)[..., None] * w
+    pts = np.asarray(apex)[None, None, :] + (s * math.sin(a))[..., None] * radial + (s * math.cos(a))[..., None] * axis
+    return pts.reshape(-1, 3)
+
+
+def test_cone_face_distance_against_sampled_surface(oracle_mod):
+    o = _cone_scene(oracle_mod)
+    a = math.radians(30.0)
+    surf = _frustum_samples((0, 0, 0), (0, 0, 1), 30.0, 2.0 / math.sin(a), 12.0 / math.sin(a), 1000, 1440)
+    rng = np.random.default_rng(3)
+    for _ in range(25):
+        z = rng.uniform(5.0, 15.0)
+        rad = z * math.tan(a) * rng.uniform(0.3, 0.95)
+        phi = rng.uniform(0, 2 * math.pi)
+        x = np.array([rad * math.cos(phi), rad * math.sin(phi), z])
+        case, sd, n = o.cone_distance(0, x)
+        assert case == 1
+        dmin = np.min(np.linalg.norm(surf - x, axis=1))
+        assert abs(sd - dmin) < 2e-3 * max(1.0, dmin)
+        assert abs(np.linalg.norm(n) - 1.0) < 1e-12
+        # the foot point x - sd n lies on the surface and the normal points inward
+        foot = x - sd * n
+        assert np.min(np.linalg.norm(surf - foot, axis=1)) < 2e-2
+        assert np.dot(n, np.array([-math.cos(phi), -math.sin(phi), 0.0])) > 0.0
+
+
+def test_cone_points_on_surface_have_zero_distance(oracle_mod):
+    o = _cone_scene(oracle_mod, apex=(1.0, -2.0, 0.5), axis=(0.3, 0.1, 2.0), deg=25.0, r_o=1.5, r_t=9.0)
+    a = math.radians(25.0)
+    pts = _frustum_samples((1.0, -2.0, 0.5), (0.3, 0.1, 2.0), 25.0, 1.5 / math.sin(a) + 1e-6, 9.0 / math.sin(a) - 1e-6,
+                           7, 9)
+    for x in pts:
+        case, sd, _ = o.cone_distance(0, x)
+        assert case == 1 and abs(sd) < 1e-11
+
+
+def test_cone_rim_distance_against_sampled_circle(oracle_mod):
+    o = _cone_scene(oracle_mod)
+    a = math.radians(30.0)
+    rim = _frustum_samples((0, 0, 0), (0, 0, 1), 30.0, 2.0 / math.sin(a), 2.0 / math.sin(a), 1, 200000)
+    rng = np.random.default_rng(5)
+    for _ in range(30):
+        # under the orifice plane and inside its radius: the rim is nearest
+        z = 2.0 / math.tan(a) - rng.uniform(0.1, 1.0)
+        rad = rng.uniform(0.0, 1.99)
+        phi = rng.uniform(0, 2 * math.pi)
+        x = np.array([rad * math.cos(phi), rad * math.sin(phi), z])
+        case, sd, n = o.cone_distance(0, x)
+        assert case == 2
+        assert abs(sd - np.min(np.linalg.norm(rim - x, axis=1))) < 1e-6
+        assert abs(np.linalg.norm(n) - 1.0) < 1e-12
+
+
+def test_cone_above_top_and_rotation_invariance(oracle_mod):
+    o = _cone_scene(oracle_mod)
+    assert o.cone_distance(0, np.array([0.0, 1.0, 30.0]))[0] == 0
+    # the same configuration rotated and shifted: same distances, rotated normals
+    rng = np.random.default_rng(7)
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    shift = np.array([3.0, -1.0, 2.0])
+    o2 = _cone_scene(oracle_mod, apex=tuple(shift), axis=tuple(q @ np.array([0.0, 0.0, 1.0])))
+    for x in ([1.0, 0.5, 8.0], [0.2, -0.3, 2.5], [4.0, 1.0, 10.0]):
+        x = np.array(x)
+        c1, s1, n1 = o.cone_distance(0, x)
+        c2, s2, n2 = o2.cone_distance(0, q @ x + shift)
+        assert c1 == c2 and abs(s1 - s2) < 1e-12 * max(1.0, abs(s1))
+        assert np.abs(q @ n1 - n2).max() < 1e-12
+
+
+def test_sphere_rests_in_cone_at_r_over_sin(oracle_mod):
+    """A sphere on the axis of a cone touches it along a circle; the single
+    contact takes the axis as its normal, so at rest the sphere carries its
+    weight with p_n = m g dt and stays r / sin(a) above the apex."""
+    sc = scenes.sphere_in_cone(radius=0.5, half_angle_deg=30.0)
+    o = oracle_mod.OracleScene(sc)
+    z0 = sc["pos"][0, 2]
+    m = 4.0 / 3.0 * math.pi * 0.5 ** 3
+    for _ in range(100):
+        o.step(20)
+    c = o.get_contacts()
+    assert len(c["j1"]) == 1 and c["j2"][0] == 1   # wall index n_bodies + n_planes + 0
+    assert abs(c["impulse"][0, 0] - m * 9.81 * sc["params"]["dt"]) < 1e-12
+    assert abs(o.get_bodies()["pos"][0, 2] - z0) < 1e-12
+    assert abs(z0 - 0.5 / math.sin(math.radians(30.0))) < 1e-15
+
+
+def test_hopper_contacts_have_cone_walls(oracle_mod):
+    sc = scenes.hopper(1500, seed=2, dt=2e-3)
+    o = oracle_mod.OracleScene(sc)
+    for _ in range(80):   # 0.16 s: the outer spheres fall onto the inclined face
+        o.step(20)
+    c = o.get_contacts()
+    n = len(sc["radius"])
+    assert np.any(c["j2"] == n + 1)          # the cone comes after the floor plane
+    # spheres resting on the inclined face: unit normals at 30 degrees to the
+    # horizontal, pointing up and towards the axis, and a positive push
+    rows = np.nonzero(c["j2"] == n + 1)[0]
+    nrm = c["normal"][rows]
+    assert np.all(np.abs(np.linalg.norm(nrm, axis=1) - 1.0) < 1e-12)
+    assert np.all(np.abs(nrm[:, 2] - 0.5) < 1e-12)
+    p = o.get_bodies()["pos"][c["j1"][rows]]
+    assert np.all(np.sum(nrm[:, :2] * p[:, :2], axis=1) < 0.0)
+    assert np.all(c["impulse"][rows, 0] >= 0.0) and np.any(c["impulse"][rows, 0] > 0.0)
