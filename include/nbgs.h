@@ -131,6 +131,21 @@ const char* nbgs_last_error(const nbgs_scene* scene);
  * Wall k gets body index n_bodies + k.  At most 16 walls. */
 nbgs_status nbgs_add_plane(nbgs_scene* scene, const double n[3], double c);
 
+/* Add a conical hopper wall (configuration 5 of the experiments built on
+ * Sect. 7): the frustum of the cone with apex `apex`, axis `axis` (any
+ * length; normalised here; the cone opens along it) and half-angle
+ * half_angle (radians, 0 < half_angle < pi/2), between the orifice circle of
+ * radius r_orifice and the top circle of radius r_top > r_orifice.  The
+ * solid lies outside the cone.  A sphere inside touches its face; below the
+ * face it touches the orifice rim; above the top circle it touches nothing.
+ * The contact is a wall contact (infinite mass, Sect. 6.4) at the point of
+ * the solid nearest the sphere's centre, whose normal is the direction from
+ * that point to the centre (the cone's axis for a centre on the axis).
+ * Cone k gets body index n_bodies + n_planes + k.  At most 4 cones; plain
+ * scenes only (a batched scene returns NBGS_EINVAL). */
+nbgs_status nbgs_add_cone(nbgs_scene* scene, const double apex[3], const double axis[3], double half_angle,
+                          double r_orifice, double r_top);
+
 /* Replace 1/m and/or 1/I of every sphere (n doubles each, NULL = keep).
  * 0 makes the quantity infinite (e.g. invI = 0 locks the rotation). */
 nbgs_status nbgs_set_mass_properties(nbgs_scene* scene, const double* invm, const double* invI);

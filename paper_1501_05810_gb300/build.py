@@ -19,7 +19,9 @@ LIB = os.path.join(PKG, "libnbgs.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["api.cu", "detect.cu", "colour.cu", "solve.cu", "integrate.cu", "mlp.cu", "noalloc.cu", "checkpoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
+# host code without FMA contraction: wall geometry computed on the host must
+# round exactly as written (GCC contracts by default on some targets)
+FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE]
 
 
 def nvcc() -> str:

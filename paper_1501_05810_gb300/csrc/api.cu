@@ -445,6 +445,31 @@ nbgs_status nbgs_add_plane(nbgs_scene* s, const double n[3], double c)
     return NBGS_OK;
 }
 
+nbgs_status nbgs_add_cone(nbgs_scene* s, const double apex[3], const double axis[3], double half_angle,
+                          double r_orifice, double r_top)
+{
+    NBGS_GUARD(s);
+    if (s->batch) return fail(s, NBGS_EINVAL, "add_cone: batched scenes take no cones");
+    if (!apex || !axis || s->planes.ncones >= kMaxCones) return fail(s, NBGS_EINVAL, "add_cone: bad cone or too many");
+    if (!(half_angle > 0.0 && half_angle < 1.5707963267948966) || !(r_orifice >= 0.0) || !(r_top > r_orifice))
+        return fail(s, NBGS_EINVAL, "add_cone: need 0 < half_angle < pi/2 and 0 <= r_orifice < r_top");
+    // the same operations as the oracle's (host code is built without FMA
+    // contraction), so that both sides hold the same cone
+    const double len = std::sqrt((axis[0] * axis[0] + axis[1] * axis[1]) + axis[2] * axis[2]);
+    if (!(len > 0.0)) return fail(s, NBGS_EINVAL, "add_cone: zero axis");
+    Cone& C = s->planes.cone[s->planes.ncones++];
+    for (int e = 0; e < 3; ++e) {
+        C.apex[e] = apex[e];
+        C.axis[e] = axis[e] / len;
+    }
+    C.sa = std::sin(half_angle);
+    C.ca = std::cos(half_angle);
+    C.s_o = r_orifice / C.sa;
+    C.s_t = r_top / C.sa;
+    s->detected = s->coloured = false;
+    return NBGS_OK;
+}
+
 nbgs_status nbgs_set_mass_properties(nbgs_scene* s, const double* invm, const double* invI)
 {
     NBGS_GUARD(s);

@@ -24,7 +24,7 @@ namespace nbgs {
 namespace {
 
 constexpr char kMagic[8] = {'N', 'B', 'G', 'S', 'C', 'K', 'P', '1'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 constexpr int64_t kMlpParams = 9347;
 
 struct CkptHeader {

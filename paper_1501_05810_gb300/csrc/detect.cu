@@ -267,6 +267,10 @@ struct GridArgs {
     float pn[kMaxPlanes][3];
     float pc[kMaxPlanes];
     float tauf, wmargin;
+    // FP32 cone pre-filter: apex relative to lo, axis, sin, cos, s_o, s_t;
+    // margin 1e-4 + 1e-5 (max(L) + max |apex - lo|)
+    float ca_apex[kMaxCones][3], ca_axis[kMaxCones][3], ca_sc[kMaxCones][4];
+    float cmargin;
 };
 
 __device__ __forceinline__ double norm_exact(double x, double y, double z)
@@ -386,6 +390,79 @@ __device__ __forceinline__ double min_image(double d, int periodic, double L)
         else if (d < -half) d = xadd(d, L);
     }
     return d;
+}
+
+// Distance from x to cone C, worked in the half-plane through the axis and
+// x: zeta = height above the apex along the axis, rho = distance from the
+// axis, e = unit radial direction.  A generatrix runs along (sin a, cos a)
+// in (rho, zeta); the face is its segment s in [s_o, s_t], the solid lies
+// outside, and the face's inward unit normal is (-cos a, sin a).  The foot
+// of x on the generatrix is at s = rho sin a + zeta cos a.  Face:
+// sd = zeta sin a - rho cos a, n = sin a axis - cos a e.  Below the face
+// (s < s_o) the orifice rim (rho_o, zeta_o) = s_o (sin a, cos a) is
+// nearest: sd = |(rho - rho_o, zeta - zeta_o)|, n along that difference.
+// On the axis (rho = 0) the normal is the axis.  Returns 0 above the
+// frustum (no contact), 1 on the face, 2 at the rim.  Every operation is
+// rounded to nearest, in this order, so that the contact sets are exact.
+__device__ __forceinline__ int cone_distance(const Cone& C, const double4_32a& x, double& sd, double n[3])
+{
+    const double d0 = xsub(x.x, C.apex[0]), d1 = xsub(x.y, C.apex[1]), d2 = xsub(x.z, C.apex[2]);
+    const double zeta = xadd(xadd(xmul(d0, C.axis[0]), xmul(d1, C.axis[1])), xmul(d2, C.axis[2]));
+    double e0 = xsub(d0, xmul(zeta, C.axis[0])), e1 = xsub(d1, xmul(zeta, C.axis[1])),
+           e2 = xsub(d2, xmul(zeta, C.axis[2]));
+    const double rho = xsqrt(xadd(xadd(xmul(e0, e0), xmul(e1, e1)), xmul(e2, e2)));
+    const double sg = xadd(xmul(rho, C.sa), xmul(zeta, C.ca));
+    if (sg > C.s_t) return 0;
+    if (rho > 0.0) {
+        e0 = xdiv(e0, rho);
+        e1 = xdiv(e1, rho);
+        e2 = xdiv(e2, rho);
+    }
+    if (sg >= C.s_o) {
+        sd = xsub(xmul(zeta, C.sa), xmul(rho, C.ca));
+        if (rho > 0.0) {
+            n[0] = xsub(xmul(C.sa, C.axis[0]), xmul(C.ca, e0));
+            n[1] = xsub(xmul(C.sa, C.axis[1]), xmul(C.ca, e1));
+            n[2] = xsub(xmul(C.sa, C.axis[2]), xmul(C.ca, e2));
+        } else {
+            n[0] = C.axis[0];
+            n[1] = C.axis[1];
+            n[2] = C.axis[2];
+        }
+        return 1;
+    }
+    const double drho = xsub(rho, xmul(C.s_o, C.sa)), dzeta = xsub(zeta, xmul(C.s_o, C.ca));
+    const double dist = xsqrt(xadd(xmul(drho, drho), xmul(dzeta, dzeta)));
+    sd = dist;
+    if (dist > 0.0 && rho > 0.0) {
+        n[0] = xdiv(xadd(xmul(drho, e0), xmul(dzeta, C.axis[0])), dist);
+        n[1] = xdiv(xadd(xmul(drho, e1), xmul(dzeta, C.axis[1])), dist);
+        n[2] = xdiv(xadd(xmul(drho, e2), xmul(dzeta, C.axis[2])), dist);
+    } else {
+        n[0] = C.axis[0];
+        n[1] = C.axis[1];
+        n[2] = C.axis[2];
+    }
+    return 2;
+}
+
+// The same distance in FP32 from the relative position q (the pre-filter;
+// the distance is continuous across the face/rim boundary, so a case taken
+// differently under rounding changes it little).  Returns a huge value
+// above the frustum.
+__device__ __forceinline__ float cone_distance_f(const GridArgs& g, int k, const float4& q)
+{
+    const float d0 = q.x - g.ca_apex[k][0], d1 = q.y - g.ca_apex[k][1], d2 = q.z - g.ca_apex[k][2];
+    const float* ax = g.ca_axis[k];
+    const float sa = g.ca_sc[k][0], ca = g.ca_sc[k][1], so = g.ca_sc[k][2], st = g.ca_sc[k][3];
+    const float zeta = d0 * ax[0] + d1 * ax[1] + d2 * ax[2];
+    const float e0 = d0 - zeta * ax[0], e1 = d1 - zeta * ax[1], e2 = d2 - zeta * ax[2];
+    const float rho = sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
+    const float sg = rho * sa + zeta * ca;
+    if (sg > st + g.cmargin) return 3.0e38f;
+    if (sg >= so) return zeta * sa - rho * ca;
+    const float dr = rho - so * sa, dz = zeta - so * ca;
+    return sqrtf(dr * dr + dz * dz);
 }
 
 __device__ __forceinline__ bool wall_kept(const double nrm[3], double c, double4_32a p, double h, double tau, double& sd,
@@ -519,9 +596,17 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
         // walls: a conservative FP32 test of the signed distance (errors as
         // for the pairs, within wmargin), the exact FP64 test for the rest
         uint32_t wmask = 0;
-        const int nwall = planes.count + (V.batch ? 6 : 0);
+        const int nwall = planes.count + planes.ncones + (V.batch ? 6 : 0);
         const float reach = qi.w + g.tauf + g.wmargin;
         for (int k = 0; k < nwall; ++k) {
+            const int kc = k - planes.count;
+            if (kc >= 0 && kc < planes.ncones) {   // cone (plain scenes only)
+                if (cone_distance_f(g, kc, qi) > qi.w + g.tauf + g.cmargin) continue;
+                double nrm[3], sd;
+                if (cone_distance(planes.cone[kc], pi, sd, nrm) && xsub(sd, pi.w) <= xadd(hi_, g.tau))
+                    wmask |= 1u << k;
+                continue;
+            }
             float sdf;
             if (k < planes.count) {
                 sdf = g.pn[k][0] * qi.x + g.pn[k][1] * qi.y + g.pn[k][2] * qi.z + g.pc[k];
@@ -593,8 +678,17 @@ __global__ void k_write_contacts(int64_t n, int64_t ccap, const uint32_t* __rest
             const int k = __ffs(m) - 1;
             double nrm[3], c, sd, xi;
             uint32_t widx;
-            wall_plane(planes, V, si, k, nrm, c, widx);
-            wall_kept(nrm, c, pi, hi_, g.tau, sd, xi);
+            const int kc = k - planes.count;
+            if (kc >= 0 && kc < planes.ncones) {
+                // the point of the cone's solid nearest to x_i is x_i - sd n:
+                // a wall contact with xi = sd - r_i and l_i = -sd n
+                cone_distance(planes.cone[kc], pi, sd, nrm);
+                xi = xsub(sd, pi.w);
+                widx = (uint32_t)(V.n + k);
+            } else {
+                wall_plane(planes, V, si, k, nrm, c, widx);
+                wall_kept(nrm, c, pi, hi_, g.tau, sd, xi);
+            }
             if (idx < ccap) {
                 cj1[idx] = i;
                 cj2[idx] = widx;
@@ -652,6 +746,20 @@ static GridArgs grid_args(const nbgs_scene* s)
     }
     g.tauf = (float)g.tau;
     g.wmargin = (float)(1e-4 + 4e-6 * (lmax + cmax));
+    double amax = 0.0;
+    for (int k = 0; k < s->planes.ncones; ++k) {
+        const Cone& C = s->planes.cone[k];
+        for (int a = 0; a < 3; ++a) {
+            g.ca_apex[k][a] = (float)(C.apex[a] - g.lo[a]);
+            g.ca_axis[k][a] = (float)C.axis[a];
+            amax = std::max(amax, std::fabs(C.apex[a] - g.lo[a]));
+        }
+        g.ca_sc[k][0] = (float)C.sa;
+        g.ca_sc[k][1] = (float)C.ca;
+        g.ca_sc[k][2] = (float)C.s_o;
+        g.ca_sc[k][3] = (float)C.s_t;
+    }
+    g.cmargin = (float)(1e-4 + 1e-5 * (lmax + amax));
     return g;
 }
 

@@ -43,10 +43,24 @@ enum : uint32_t {
     kErrGrid = 32u        // periodic axis with fewer than 3 cells
 };
 
+constexpr int kMaxCones = 4;
+
+// Conical hopper wall (frustum between the orifice and the top circle);
+// sin and cos of the half-angle come from the host's C library.
+struct Cone {
+    double apex[3], axis[3];   // axis unit, the cone opens along it
+    double sa, ca;             // sin, cos of the half-angle
+    double s_o, s_t;           // orifice and top along a generatrix, from the apex
+};
+
+// Shared walls: half-spaces, then cones (wall index n + k, k < count, then
+// n + count + k for cone k).
 struct Planes {
     int count;
     double n[kMaxPlanes][3];
     double c[kMaxPlanes];
+    int ncones;
+    Cone cone[kMaxCones];
 };
 
 // Batched scenes as the kernels see them (batch == 0: one plain scene).

@@ -66,6 +66,7 @@ _SIG = {
     "nbgs_destroy_scene": [_vp],
     "nbgs_last_error": [_vp],
     "nbgs_add_plane": [_vp, _dp, C.c_double],
+    "nbgs_add_cone": [_vp, _dp, _dp, C.c_double, C.c_double, C.c_double],
     "nbgs_set_mass_properties": [_vp, _vp, _vp],
     "nbgs_set_bodies": [_vp, _vp, _vp, _vp, _vp],
     "nbgs_get_bodies": [_vp, _vp, _vp, _vp, _vp],
@@ -223,6 +224,9 @@ class Scene:
         for n_, c_ in scene.get("planes", []):
             nn = (C.c_double * 3)(*n_)
             _call(self.h, "nbgs_add_plane", nn, float(c_))
+        for cn in scene.get("cones", []):
+            _call(self.h, "nbgs_add_cone", (C.c_double * 3)(*cn["apex"]), (C.c_double * 3)(*cn["axis"]),
+                  float(cn["half_angle"]), float(cn["r_orifice"]), float(cn["r_top"]))
 
     # -- lifecycle
     def close(self):

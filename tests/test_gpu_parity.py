@@ -264,3 +264,63 @@ def test_solver_modes_agree(nb):
     _rel_close(out[0][0]["vel"], out[1][0]["vel"], 1e-12)
     _rel_close(out[0][1]["impulse"], out[1][1]["impulse"], 1e-12)
     assert np.array_equal(out[0][1]["colour"], out[1][1]["colour"])
+
+
+# ---------------------------------------------------------------------------
+# conical hopper walls
+# ---------------------------------------------------------------------------
+
+def test_hopper_cone_contacts_match_oracle(nb, oracle_mod):
+    """Oracle steps a small hopper until spheres rest on the cone face and
+    fall through the orifice; from that state (oracle output as input) one
+    step on each side: contact sets, cone normals and gaps bit-exact,
+    colours exact, impulses and velocities within 1e-10."""
+    sc = scenes.hopper(2500, seed=3, dt=2e-3)
+    o = oracle_mod.OracleScene(sc)
+    for _ in range(220):   # 0.44 s: ~200 cone and ~100 sphere-sphere contacts
+        o.step(20)
+    b = o.get_bodies()
+    g = nb.Scene(sc)
+    g.set_bodies(b["pos"], b["quat"], b["vel"], b["angvel"])
+    sg, so, _ = _step_and_compare(g, o, 30)
+    c = g.get_contacts()
+    n = len(sc["radius"])
+    cone_rows = c["j2"] == n + 1
+    assert cone_rows.sum() > 100 and sg["n_contacts"] > cone_rows.sum() + 50
+
+
+def test_hopper_rim_contacts_match_oracle(nb, oracle_mod):
+    """Spheres placed under the orifice, pressed against the rim from below
+    by an upward gravity: rim contacts (orifice circle) on both sides."""
+    sc = scenes.hopper(400, seed=4, dt=2e-3)
+    a = math.radians(30.0)
+    z_o = 2.0 / math.tan(a)
+    rng = np.random.default_rng(11)
+    k = 12
+    phi = np.linspace(0.0, 2.0 * math.pi, k, endpoint=False)
+    ring = np.stack([1.9 * np.cos(phi), 1.9 * np.sin(phi), np.full(k, z_o - 0.45)], -1) + rng.uniform(-0.01, 0.01, (k, 3))
+    sc["pos"] = np.concatenate([ring, sc["pos"][k:]])
+    sc["params"]["gravity"] = (0.0, 0.0, 9.81)
+    g, o = _pair(nb, oracle_mod, sc)
+    for _ in range(3):   # each step from the oracle's state
+        _, _, bo = _step_and_compare(g, o, 30)
+        g.set_bodies(bo["pos"], bo["quat"], bo["vel"], bo["angvel"])
+    c = o.get_contacts()
+    n = len(sc["radius"])
+    rim = (c["j2"] == n + 1) & (c["j1"] < k)
+    assert rim.sum() >= k // 2
+    # a rim contact's normal points from the orifice circle towards the centre
+    assert np.all(c["normal"][rim][:, 2] < 0.0)
+
+
+def test_sphere_rests_in_cone_on_gpu(nb):
+    sc = scenes.sphere_in_cone(radius=0.5, half_angle_deg=30.0, dt=1e-3)
+    g = nb.Scene(sc)
+    z0 = sc["pos"][0, 2]
+    for _ in range(200):
+        g.step(10, stats=False)
+    b = g.get_bodies()
+    assert abs(b["pos"][0, 2] - z0) <= 1e-12 and np.abs(b["vel"]).max() <= 1e-15
+    c = g.get_contacts()
+    m = 4.0 / 3.0 * math.pi * 0.5 ** 3
+    assert len(c["j1"]) == 1 and abs(c["impulse"][0, 0] - m * 9.81 * 1e-3) < 1e-15
