@@ -151,7 +151,8 @@ nbgs_status nbgs_add_cone(nbgs_scene* scene, const double apex[3], const double 
 nbgs_status nbgs_set_mass_properties(nbgs_scene* scene, const double* invm, const double* invI);
 
 /* Overwrite / read the body state; NULL arrays are skipped.
- * nbgs_get_bodies synchronises. */
+ * nbgs_set_bodies starts a new history: the next solve has no previous-step
+ * impulses to warm start from.  nbgs_get_bodies synchronises. */
 nbgs_status nbgs_set_bodies(nbgs_scene* scene, const double* pos, const double* quat,
                             const double* vel, const double* angvel);
 nbgs_status nbgs_get_bodies(nbgs_scene* scene, double* pos, double* quat,
@@ -159,10 +160,13 @@ nbgs_status nbgs_get_bodies(nbgs_scene* scene, double* pos, double* quat,
 
 /* Sect. 4: hull radii h_i = dt(|v_i| + |w_i| r_i) + tau from the current
  * velocities, uniform cell grid sorted by radix sort, narrow phase
- * (sphere-sphere, sphere-wall).  A pair is kept iff
+ * (sphere-sphere, sphere-wall, sphere-cone).  A pair is kept iff
  * (d - r_a) - r_b <= h_a + h_b (walls: h = tau).  Contacts are stored in
- * canonical order of (j1 << 32) | j2, j1 < j2.  Synchronises once to read the
- * contact count (grows the buffers and retries on overflow). */
+ * canonical order of (j1 << 32) | j2, j1 < j2.  With a warm start, the
+ * contacts and impulses of the last solved step become the previous-step
+ * contacts here (detecting again without a solve keeps them).  Synchronises
+ * once to read the contact count (grows the buffers and retries on
+ * overflow). */
 nbgs_status nbgs_detect_contacts(nbgs_scene* scene, int64_t* n_contacts /* nullable */);
 
 /* Jones-Plassmann colouring of the conflict graph (contacts sharing a body

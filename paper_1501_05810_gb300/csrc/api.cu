@@ -481,7 +481,6 @@ nbgs_status nbgs_set_bodies(nbgs_scene* s, const double* pos, const double* quat
 {
     NBGS_GUARD(s);
     s->have_prev = false;
-    s->keep_prev = false;
     s->solved = false;
     return run_set_bodies(s, pos, quat, vel, angvel);
 }

@@ -74,7 +74,7 @@ nbgs_status run_save_state(nbgs_scene* s, const char* path)
     // (still in the current arrays), or those of a checkpoint not yet stepped
     const bool warm = s->prm.warm_start != NBGS_WARM_NONE;
     const bool cur = warm && s->solved;
-    const bool kept = warm && !cur && s->keep_prev && s->have_prev;
+    const bool kept = warm && !cur && s->have_prev;
     CkptHeader h{};
     std::memcpy(h.magic, kMagic, sizeof(kMagic));
     h.version = kVersion;
@@ -164,7 +164,6 @@ nbgs_status run_load_state(nbgs_scene* s, const char* path)
 
     // the warm-start arrays must hold prev_count contacts
     s->have_prev = false;
-    s->keep_prev = false;
     if (h.prev_count > s->ccap) {
         nbgs_status rc = grow_contacts(s, h.prev_count);
         if (rc != NBGS_OK) return rc;
@@ -194,7 +193,6 @@ nbgs_status run_load_state(nbgs_scene* s, const char* path)
     s->detected = s->coloured = s->solved = false;
     s->n_contacts = 0;
     s->have_prev = h.has_prev != 0;
-    s->keep_prev = s->have_prev;
     s->prev_count = h.has_prev ? h.prev_count : 0;
     return NBGS_OK;
 }

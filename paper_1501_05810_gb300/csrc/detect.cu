@@ -777,10 +777,10 @@ nbgs_status run_detect(nbgs_scene* s)
         std::swap(s->cworld, s->prev_P);
         s->prev_count = s->n_contacts;
         s->have_prev = true;
-    } else if (!s->keep_prev) {   // a restored checkpoint already filled the previous-step arrays
-        s->have_prev = false;
     }
-    s->keep_prev = false;
+    // otherwise the previous-step arrays keep what they hold: the contacts of
+    // the last solved step, or of a restored checkpoint (nbgs_set_bodies
+    // starts a new history)
     s->detected = s->coloured = s->solved = false;
     s->n_contacts = 0;
     cudaMemsetAsync(s->info, 0, offsetof(DevInfo, cell_w), st);   // hmax, vmax

@@ -289,7 +289,6 @@ struct nbgs_scene {
     double4_32a* prev_P = nullptr;     // world-frame impulse
     int64_t prev_count = 0;
     bool have_prev = false;
-    bool keep_prev = false;            // the previous-step arrays come from a checkpoint
     // colouring
     uint32_t* deg = nullptr;       // n + 1
     uint32_t* adj_off = nullptr;   // n + 1

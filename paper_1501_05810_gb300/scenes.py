@@ -240,18 +240,18 @@ def sphere_in_cone(radius: float = 0.5, half_angle_deg: float = 30.0, height: fl
 
 
 def hopper(n: int = 2_000_000, seed: int = 0, half_angle_deg: float = 30.0, r_lo: float = 0.4, r_hi: float = 0.6,
-           orifice_diameter: float = None, spacing: float = None, jitter: float = 0.02, **params) -> dict:
+           orifice_diameter: float = None, spacing: float = None, jitter: float = 0.004, **params) -> dict:
     """Conical hopper discharge: n spheres r ~ U(r_lo, r_hi) on a jittered
-    cubic lattice filling an upward-opening cone of the given half-angle
-    from just above its orifice (diameter 8 r_mean unless given), falling
-    under gravity through the orifice onto a floor 20 r_mean below it.
-    mu = 0.5, dt = 5e-4."""
+    cubic lattice (gaps of 0.02 between the largest spheres) filling an
+    upward-opening cone of the given half-angle from just above its orifice
+    (diameter 8 r_mean unless given), falling under gravity through the
+    orifice onto a floor 20 r_mean below it.  mu = 0.5, dt = 5e-4."""
     rng = np.random.default_rng(seed)
     a = math.radians(half_angle_deg)
     r_mean = 0.5 * (r_lo + r_hi)
     d_o = 8.0 * r_mean if orifice_diameter is None else orifice_diameter
     r_o = 0.5 * d_o
-    sp = 2.0 * r_hi * 1.05 if spacing is None else spacing
+    sp = 2.0 * r_hi + 0.02 if spacing is None else spacing
     ta = math.tan(a)
     z_o = r_o / ta   # orifice height above the apex
     # cone volume above the orifice level that holds n lattice sites

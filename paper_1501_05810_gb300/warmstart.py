@@ -151,3 +151,113 @@ def _set_warm(g, code):
     rc = nbgs.library().nbgs_set_warm_start(g.h, int(code))
     if rc != nbgs.NBGS_OK:
         raise nbgs.NBGSError(rc, "nbgs_set_warm_start", nbgs.library().nbgs_last_error(g.h).decode())
+
+
+def settling_training_data(seeds=range(8), steps: int = 250, tol_data: float = 1e-7, device="cuda:0", log=None):
+    """(features, converged impulse) pairs of the contacts that appear while
+    1,000-sphere lattice boxes (the FP64 workload's setup, dt = 2e-3) settle
+    under gravity: every contact without a previous-step impulse, at every
+    step."""
+    from . import scenes
+    X, T = [], []
+    for s in seeds:
+        sc = scenes.lattice_box(seed=int(s), per_side=10, dt=2e-3, mu=0.5, tau=0.005, vel_sigma=0.1 + 0.05 * (s % 4))
+        x, t = collect([sc], steps=steps, tol_data=tol_data, max_sweeps=5000, new_only=True, device=device)
+        X.append(x)
+        T.append(t)
+        if log:
+            log(f"settling run {s}: {len(x)} new-contact samples")
+    return np.concatenate(X), np.concatenate(T)
+
+
+def hopper_evaluation(n: int = 2_000_000, settle_steps: int = 600, settle_sweeps: int = 30, eval_steps: int = 4,
+                      tol: float = 1e-6, max_sweeps: int = 4000, theta=None, train_epochs: int = 30, seed: int = 0,
+                      checkpoint: str = "/tmp/nbgs_hopper_eval.ckpt", device="cuda:0", log=None) -> dict:
+    """Hopper discharge (conical hopper, 30 degree half-angle, orifice 8 r,
+    mu = 0.5): sweeps and device time per step to residual tol with cold,
+    previous-step and network warm starts, from the same state.
+
+    The hopper runs settle_steps FP32 steps (previous-step warm start,
+    settle_sweeps sweeps) until it discharges through the orifice; its state
+    moves into an FP64 scene, which steps once with the previous-step warm
+    start (the contact history every mode starts from) and is checkpointed.
+    Each mode then restores the checkpoint and runs eval_steps steps with FP64
+    sweeps to tol (FP32 sweeps stall above 1e-6 on dense packings).  The
+    network is trained first on settling runs unless theta is given."""
+    import time
+    import torch
+    from . import scenes
+    say = log or (lambda *_: None)
+    out = {"n": n, "tol": tol, "eval_steps": eval_steps, "settle_steps": settle_steps}
+    if theta is None:
+        t0 = time.perf_counter()
+        X, T = settling_training_data(device=device, log=say)
+        theta, losses = train(X, T, epochs=train_epochs, batch=4096, lr=1e-3, seed=seed, device=device)
+        out["training"] = {"samples": int(len(X)), "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+                           "seconds": time.perf_counter() - t0}
+        say(f"trained on {len(X)} samples: loss {losses[0]:.4g} -> {losses[-1]:.4g}")
+    sc = scenes.hopper(n, seed=seed)
+    sc32 = dict(sc, params=dict(sc["params"], precision="fp32", warm_start="prev"))
+    g = nbgs.Scene(sc32, device=device)
+    t0 = time.perf_counter()
+    for _ in range(settle_steps):
+        st = g.step(settle_sweeps, 0.0, stats=False)
+    torch.cuda.synchronize()
+    b = g.get_bodies()
+    nc = g.step(settle_sweeps, 0.0)["n_contacts"]
+    g.close()
+    cn = sc["cones"][0]
+    z_o = cn["r_orifice"] / np.tan(cn["half_angle"])   # orifice height above the apex (apex at the origin)
+    out["settle"] = {"seconds": time.perf_counter() - t0, "contacts": int(nc),
+                     "below_orifice": int(np.count_nonzero(b["pos"][:, 2] < z_o))}
+    say(f"settled: {nc} contacts, {out['settle']['below_orifice']} spheres discharged")
+    sc64 = dict(sc, params=dict(sc["params"], precision="fp64", warm_start="prev"))
+    h = nbgs.Scene(sc64, device=device)
+    h.set_bodies(b["pos"], b["quat"], b["vel"], b["angvel"])
+    h.mlp_load(theta)
+    h.step(max_sweeps, tol)
+    h.save_state(checkpoint)
+    h.close()
+    modes = {}
+    for mode in ("none", "prev", "mlp"):
+        s = nbgs.Scene(sc64, device=device)
+        s.load_state(checkpoint)
+        _set_warm(s, {"none": nbgs.NBGS_WARM_NONE, "prev": nbgs.NBGS_WARM_PREV, "mlp": nbgs.NBGS_WARM_MLP}[mode])
+        sweeps, ms, res, ncon, nnew = [], [], [], [], []
+        for _ in range(eval_steps):
+            s.detect_contacts()
+            s.colour_contacts()
+            f = s.mlp_features()   # columns 3..5: previous impulse (0: new, or no push last step)
+            nnew.append(int(np.count_nonzero(np.all(f[:, 3:6] == 0.0, axis=1))) if len(f) else 0)
+            ncon.append(int(len(f)))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
+            k, r = s.solve_nbgs(max_sweeps, tol)
+            e1.record(s.stream)
+            s.integrate()
+            torch.cuda.synchronize()
+            sweeps.append(int(k))
+            res.append(float(r))
+            ms.append(e0.elapsed_time(e1))
+        modes[mode] = {"sweeps": sweeps, "solve_ms": ms, "residual": res, "contacts": ncon, "zero_prev_impulse": nnew,
+                       "total_solve_ms": float(sum(ms))}
+        say(f"{mode}: sweeps {sweeps}, solve ms {[round(x, 1) for x in ms]}, R {['%.2g' % x for x in res]}, "
+            f"zero previous impulse {nnew} of {ncon}")
+        s.close()
+    out["modes"] = modes
+    return out
+
+
+if __name__ == "__main__":  # pragma: no cover
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="warm-start evaluation on the hopper discharge")
+    ap.add_argument("--n", type=int, default=2_000_000)
+    ap.add_argument("--settle-steps", type=int, default=600)
+    ap.add_argument("--eval-steps", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--max-sweeps", type=int, default=4000)
+    a = ap.parse_args()
+    r = hopper_evaluation(n=a.n, settle_steps=a.settle_steps, eval_steps=a.eval_steps, train_epochs=a.epochs,
+                          max_sweeps=a.max_sweeps, log=lambda m: print(m, flush=True))
+    print(json.dumps(r))
