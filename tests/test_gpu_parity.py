@@ -324,3 +324,19 @@ def test_sphere_rests_in_cone_on_gpu(nb):
     c = g.get_contacts()
     m = 4.0 / 3.0 * math.pi * 0.5 ** 3
     assert len(c["j1"]) == 1 and abs(c["impulse"][0, 0] - m * 9.81 * 1e-3) < 1e-15
+
+
+def test_colouring_buffers_grow_between_steps(nb, oracle_mod):
+    """A step with few contacts sizes the colouring's predecessor lists;
+    the next step has many more contacts (large hulls), so the lists
+    outgrow the buffer on the device and the colouring is redone with a
+    larger one: the result still equals the oracle's."""
+    sc = scenes.config1(0)
+    g, o = _pair(nb, oracle_mod, sc)
+    sg, so, bo = _step_and_compare(g, o, 20)
+    few = sg["n_contacts"]
+    vel = np.random.default_rng(21).normal(0.0, 40.0, bo["vel"].shape)
+    for obj in (g, o):
+        obj.set_bodies(bo["pos"], bo["quat"], vel, bo["angvel"])
+    sg, so, _ = _step_and_compare(g, o, 20)
+    assert sg["n_contacts"] > 20 * max(few, 1)
