@@ -69,8 +69,10 @@ enum {                                           /* scheduling of the colour swe
 enum {                                           /* nbgs_params.sweep_flags bits (persistent solver) */
     NBGS_SWEEP_GLOBAL_SYNC = 1,  /* grid barrier after every colour instead of waiting only for the
                                     blocks whose contacts share bodies with this block's contacts      */
-    NBGS_SWEEP_TMA_STAGE = 2     /* stage each block's chunk of the next colour (records, impulses)
+    NBGS_SWEEP_TMA_STAGE = 2,    /* stage each block's chunk of the next colour (records, impulses)
                                     in shared memory with bulk copies while it waits                   */
+    NBGS_SWEEP_WARP_SYNC = 4     /* every warp has its own chunk, window and progress word, so the
+                                    warps of a block do not wait for one another (no TMA staging)      */
 };
 
 typedef struct nbgs_allocator {

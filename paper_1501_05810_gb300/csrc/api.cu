@@ -370,8 +370,10 @@ static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_des
         }
     }
     if (s->coop_blocks > 0) {
-        if (!take(s, s->dep, (size_t)kMaxColours * s->coop_blocks) || !take(s, s->prog, (size_t)s->coop_blocks) ||
-            !take(s, s->cstart, (size_t)kMaxColours * (s->coop_blocks + 1))) {
+        // scheduling units: up to one per warp (NBGS_SWEEP_WARP_SYNC)
+        const size_t units = (size_t)s->coop_blocks * (size_t)(s->coop_threads / 32);
+        if (!take(s, s->dep, (size_t)kMaxColours * units) || !take(s, s->prog, units) ||
+            !take(s, s->cstart, (size_t)kMaxColours * (units + 1))) {
             nbgs_destroy_scene(s);
             return NBGS_ENOMEM;
         }
@@ -632,11 +634,11 @@ nbgs_status nbgs_autotune(nbgs_scene* s, int32_t max_sweeps, double tol, int32_t
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int max_bps = std::max(1, s->max_coop_blocks / std::max(1, s->num_sms));
-    const int flags_list[4] = {0, NBGS_SWEEP_GLOBAL_SYNC, NBGS_SWEEP_TMA_STAGE,
-                               NBGS_SWEEP_GLOBAL_SYNC | NBGS_SWEEP_TMA_STAGE};
+    const int flags_list[5] = {0, NBGS_SWEEP_GLOBAL_SYNC, NBGS_SWEEP_TMA_STAGE,
+                               NBGS_SWEEP_GLOBAL_SYNC | NBGS_SWEEP_TMA_STAGE, NBGS_SWEEP_WARP_SYNC};
     float best = 3.4e38f;
     int best_flags = s->prm.sweep_flags, best_bps = max_bps;
-    for (int fi = 0; fi < 4 && rc == NBGS_OK; ++fi) {
+    for (int fi = 0; fi < 5 && rc == NBGS_OK; ++fi) {
         for (int bps = 1; bps <= max_bps && rc == NBGS_OK; ++bps) {
             s->prm.sweep_flags = flags_list[fi];
             s->coop_blocks = bps * s->num_sms;

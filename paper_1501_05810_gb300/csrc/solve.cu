@@ -16,6 +16,7 @@
 //
 // Contacts of one colour touch disjoint finite bodies, so a colour is one
 // data-parallel pass with plain loads and stores.
+#include <algorithm>
 #include <cstring>
 
 #include "nbgs_internal.cuh"
@@ -575,7 +576,81 @@ __device__ __forceinline__ void publish(int* prog, int g)
     }
 }
 
-template <class R, bool Batch>
+// --- warp-level scheduling (NBGS_SWEEP_WARP_SYNC) ---------------------------
+// Every warp is a scheduling unit of its own ("virtual block" vb = 8 b + w of
+// V = 8 B): its own chunk of each colour, its own window and progress word,
+// so that warps of a block never wait for one another inside a sweep.
+__device__ __forceinline__ void warp_chunk(const uint32_t* cstart, int c, int nv, int vb, int64_t& b0, int64_t& b1)
+{
+    const uint32_t* row = cstart + (int64_t)c * (nv + 1);
+    b0 = row[vb];
+    b1 = row[vb + 1];
+}
+
+// The lanes of the warp poll the progress words of its window (bounded like
+// every other wait); returns the same value on every lane.
+__device__ __forceinline__ bool wait_deps_warp(const int* prog, int2 win, int g, DevInfo* info, int nv, int self)
+{
+    const int lane = threadIdx.x & 31;
+    int ok = 1;
+    for (int off = win.x + lane; off <= win.y && ok; off += 32) {
+        if (off == 0) continue;
+        const int b = ((self + off) % nv + nv) % nv;
+        volatile const int* pb = prog + b;
+        const long long t0 = clock64();
+        while (*pb < g - 1) {
+            if (((volatile uint32_t*)&info->err)[0] & kErrTimeout) {
+                ok = 0;
+                break;
+            }
+            if (clock64() - t0 > (1LL << 31)) {
+                atomicOr(&info->err, kErrTimeout);
+                ok = 0;
+                break;
+            }
+        }
+    }
+    __threadfence();
+    return __all_sync(0xffffffffu, ok) != 0;
+}
+
+// Publish that this warp finished phase g (after all its lanes' stores).
+__device__ __forceinline__ void publish_warp(int* prog, int vb, int g)
+{
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence();
+        atomicExch(prog + vb, g);
+    }
+}
+
+template <class R, bool apply_only, bool Batch>
+__device__ __forceinline__ R process_chunk_warp(const SolveArgs<R>& A, int64_t b0, int64_t b1, int sweep)
+{
+    R rmax = R(0);
+    for (int64_t s = b0 + (threadIdx.x & 31); s < b1; s += 32) {
+        const R r = relax<R, apply_only, Batch>(A, s, sweep);
+        rmax = r > rmax ? r : rmax;
+    }
+    return rmax;
+}
+
+template <class R>
+__device__ __forceinline__ void prefetch_range(const SolveArgs<R>& A, int64_t b0, int64_t b1, int lane, int width)
+{
+    if (b1 <= b0) return;
+    const char* r0 = reinterpret_cast<const char*>(A.rec + b0);
+    const char* r1 = reinterpret_cast<const char*>(A.rec + b1);
+    const char* p0 = reinterpret_cast<const char*>(A.p + b0);
+    const char* p1 = reinterpret_cast<const char*>(A.p + b1);
+    const int64_t nr = (r1 - r0 + 127) / 128, np = (p1 - p0 + 127) / 128;
+    for (int64_t i = lane; i < nr + np; i += width) {
+        const char* a = i < nr ? r0 + 128 * i : p0 + 128 * (i - nr);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    }
+}
+
+template <class R, bool Batch, bool Warp>
 __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::value) k_solve_persistent(SolveArgs<R> A)
 {
     extern __shared__ __align__(128) unsigned char stage_mem[];
@@ -590,14 +665,21 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
     const int ncol = (int)A.info->n_colours;
     const double vref = v_ref_of(A.info, A.gdt_norm);
     const double vnorm = Batch ? 1.0 : vref;   // batched residuals arrive already divided by v_ref_s
-    const bool stage = (A.flags & NBGS_SWEEP_TMA_STAGE) != 0;
+    const bool stage = !Warp && (A.flags & NBGS_SWEEP_TMA_STAGE) != 0;
     const bool local = (A.flags & NBGS_SWEEP_GLOBAL_SYNC) == 0;
     if (threadIdx.x == 0) mbar_init(&bar);
     gravity_pass<R>(A, gtid, gstride);
     if (!grid_barrier(A.info, nb)) return;
+    const int nv = (int)nb * (kPersistThreads / 32), vb = (int)blockIdx.x * (kPersistThreads / 32) + (threadIdx.x >> 5);
     if (A.warm) {
         for (int c = 0; c < ncol; ++c) {
-            process_colour<R, true, Batch>(A, c, 0, srec, sp, 0);
+            if (Warp) {
+                int64_t w0, w1;
+                warp_chunk(A.cstart, c, nv, vb, w0, w1);
+                process_chunk_warp<R, true, Batch>(A, w0, w1, 0);
+            } else {
+                process_colour<R, true, Batch>(A, c, 0, srec, sp, 0);
+            }
             if (!grid_barrier(A.info, nb)) return;
         }
     }
@@ -611,7 +693,32 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
         if (Batch)   // the slot of sweep k + 1 is neither read nor written during sweep k
             for (int64_t sc = gtid; sc < A.nscene; sc += gstride) A.scene_rk[scene_slot(k + 1) * A.nscene + sc] = 0ull;
         R rmax = R(0);
-        for (int c = 0; c < ncol; ++c) {
+        if (Warp) {
+            // each warp on its own; a warp whose wait gave up skips the rest
+            // of the sweep (the timeout bit makes every other wait return)
+            bool wok = true;
+            for (int c = 0; c < ncol; ++c) {
+                const int g = k * ncol + c;
+                int64_t w0, w1;
+                warp_chunk(A.cstart, c, nv, vb, w0, w1);
+                if (wok && w1 > w0 && !wait_deps_warp(A.prog, A.dep[(int64_t)c * nv + vb], g, A.info, nv, vb))
+                    wok = false;
+                if (wok) {
+                    int64_t n0, n1;
+                    warp_chunk(A.cstart, c + 1 < ncol ? c + 1 : 0, nv, vb, n0, n1);
+                    prefetch_range<R>(A, n0, n1, threadIdx.x & 31, 32);
+                    const R r = process_chunk_warp<R, false, Batch>(A, w0, w1, k);
+                    rmax = r > rmax ? r : rmax;
+                    publish_warp(A.prog, vb, g);
+                }
+            }
+            block_max_to<R>(rmax, &A.info->rk_bits[rk_slot(k)]);
+            if (!__syncthreads_and(wok)) {
+                ok = false;
+                break;
+            }
+        }
+        for (int c = 0; c < (Warp ? 0 : ncol); ++c) {
             const int g = k * ncol + c;
             int64_t cb0, cb1;
             colour_chunk(A.cstart, c, cb0, cb1);
@@ -931,8 +1038,10 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
         if (rc != NBGS_OK) return rc;
     }
     if (s->prm.solver == NBGS_SOLVER_PERSISTENT) {
+        // scheduling units: blocks, or warps with NBGS_SWEEP_WARP_SYNC
+        const bool warp = (s->prm.sweep_flags & NBGS_SWEEP_WARP_SYNC) && !(s->prm.sweep_flags & NBGS_SWEEP_GLOBAL_SYNC);
         if (A.C > 0) {
-            const int T = 256, B = s->coop_blocks;
+            const int T = 256, B = s->coop_blocks * (warp ? kPersistThreads / 32 : 1);
             k_chunk_starts<<<grid_for((int64_t)kMaxColours * (B + 1), T, 8, s->num_sms), T, 0, st>>>(
                 A.C, B, s->col_off, s->perm, s->info, s->cstart);
             if (s->timing) s->phase_launches[2] += 1;
@@ -951,7 +1060,10 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
         }
         void* args[] = {&A};
         if (s->timing) cudaEventRecord(s->ev[8], st);
-        const void* fn = s->batch ? (const void*)k_solve_persistent<R, true> : (const void*)k_solve_persistent<R, false>;
+        const void* fn = s->batch ? (warp ? (const void*)k_solve_persistent<R, true, true>
+                                          : (const void*)k_solve_persistent<R, true, false>)
+                                  : (warp ? (const void*)k_solve_persistent<R, false, true>
+                                          : (const void*)k_solve_persistent<R, false, false>);
         cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(s->coop_blocks),
                                                     dim3(s->coop_threads), args,
                                                     (s->prm.sweep_flags & NBGS_SWEEP_TMA_STAGE) ? Stage<R>::BYTES : 0,
@@ -1127,23 +1239,42 @@ int persistent_blocks(nbgs_scene* s)
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
     int occ_b = 0;
     if (s->fp32) {
-        cudaFuncSetAttribute(k_solve_persistent<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Stage<float>::BYTES);
-        cudaFuncSetAttribute(k_solve_persistent<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Stage<float>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent<float, false>, s->coop_threads,
+        for (const void* f : {(const void*)k_solve_persistent<float, false, false>,
+                              (const void*)k_solve_persistent<float, false, true>,
+                              (const void*)k_solve_persistent<float, true, false>,
+                              (const void*)k_solve_persistent<float, true, true>})
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<float>::BYTES);
+        // the warp-scheduled variants have the same launch bounds; the
+        // smallest occupancy of the pair is what a cooperative launch of
+        // either can rely on
+        int o1 = 0, o2 = 0, o3 = 0, o4 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_solve_persistent<float, false, false>, s->coop_threads,
                                                       Stage<float>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_solve_persistent<float, true>, s->coop_threads,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_solve_persistent<float, false, true>, s->coop_threads,
                                                       Stage<float>::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o3, k_solve_persistent<float, true, false>, s->coop_threads,
+                                                      Stage<float>::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o4, k_solve_persistent<float, true, true>, s->coop_threads,
+                                                      Stage<float>::BYTES);
+        occ = std::min(o1, o2);
+        occ_b = std::min(o3, o4);
     } else {
-        cudaFuncSetAttribute(k_solve_persistent<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Stage<double>::BYTES);
-        cudaFuncSetAttribute(k_solve_persistent<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             Stage<double>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_solve_persistent<double, false>, s->coop_threads,
+        for (const void* f : {(const void*)k_solve_persistent<double, false, false>,
+                              (const void*)k_solve_persistent<double, false, true>,
+                              (const void*)k_solve_persistent<double, true, false>,
+                              (const void*)k_solve_persistent<double, true, true>})
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<double>::BYTES);
+        int o1 = 0, o2 = 0, o3 = 0, o4 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_solve_persistent<double, false, false>, s->coop_threads,
                                                       Stage<double>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, k_solve_persistent<double, true>, s->coop_threads,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_solve_persistent<double, false, true>, s->coop_threads,
                                                       Stage<double>::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o3, k_solve_persistent<double, true, false>, s->coop_threads,
+                                                      Stage<double>::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o4, k_solve_persistent<double, true, true>, s->coop_threads,
+                                                      Stage<double>::BYTES);
+        occ = std::min(o1, o2);
+        occ_b = std::min(o3, o4);
     }
     if (s->batch) occ = occ_b;
     cudaGetLastError();

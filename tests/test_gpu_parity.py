@@ -340,3 +340,34 @@ def test_colouring_buffers_grow_between_steps(nb, oracle_mod):
         obj.set_bodies(bo["pos"], bo["quat"], vel, bo["angvel"])
     sg, so, _ = _step_and_compare(g, o, 20)
     assert sg["n_contacts"] > 20 * max(few, 1)
+
+
+def test_warp_scheduling_matches_oracle(nb, oracle_mod):
+    """NBGS_SWEEP_WARP_SYNC (every warp waits only for the warps whose
+    contacts share its bodies) relaxes the same colours in the same order:
+    parity with the oracle as for the block-level scheduling."""
+    sc = scenes.config1(1)
+    sc["vel"][:, 2] -= 3.0
+    sc["params"]["dt"] = 2e-2
+    sc["params"]["sweep_flags"] = 4
+    g, o = _pair(nb, oracle_mod, sc)
+    sg, _, _ = _step_and_compare(g, o, 50)
+    assert sg["n_contacts"] > 2000
+
+
+def test_warp_and_block_scheduling_agree(nb):
+    sc = scenes.loose_pour(seed=6, n=20000)
+    sc["vel"] = np.random.default_rng(12).normal(0.0, 2.0, sc["vel"].shape)
+    sc["params"]["dt"] = 0.05
+    sc["params"]["precision"] = "fp32"
+    sc["params"]["warm_start"] = "prev"
+    out = []
+    for flags in (0, 4):
+        sc["params"]["sweep_flags"] = flags
+        g = nb.Scene(sc)
+        for _ in range(3):
+            g.step(30)
+        out.append((g.get_bodies(), g.get_contacts()))
+    assert np.array_equal(out[0][1]["colour"], out[1][1]["colour"])
+    _rel_close(out[0][0]["vel"], out[1][0]["vel"], 1e-5)
+    _rel_close(out[0][1]["impulse"], out[1][1]["impulse"], 1e-5)
