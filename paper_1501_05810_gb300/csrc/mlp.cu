@@ -1,7 +1,8 @@
 // mlp.cu -- learned warm start: a 12 -> 64 -> 64 -> 64 -> 3 MLP (SiLU) that
 // predicts a contact's converged impulse from local features, evaluated on
-// tensor cores (BF16 operands, FP32 accumulation) before the sweeps, and its
-// training kernels (FP32 forward/backward, Adam).
+// the 5th-generation tensor cores (tcgen05: BF16 operands in shared memory,
+// FP32 accumulators in TMEM) before the sweeps, and its training kernels
+// (FP32 forward/backward, Adam).
 //
 // Parameter layout (shared with every user of the network): for each layer
 // the weight matrix W (out x in, row-major) then the bias b (out); 9,347
@@ -35,157 +36,259 @@ constexpr int kIn = 12, kHid = 64, kOutN = 3;
 constexpr int kOffW1 = 0, kOffB1 = 768, kOffW2 = 832, kOffB2 = 4928, kOffW3 = 4992, kOffB3 = 9088, kOffW4 = 9152,
               kOffB4 = 9344, kNParams = 9347;
 
-// Shared-memory image of the network for the tensor-core forward: BF16
-// weights with padded rows (conflict-free fragment loads), FP32 biases.
-constexpr int kS1 = 24;   // layer 1 row stride (12 inputs padded to 16, + 8)
-constexpr int kS2 = 72;   // 64-wide rows + 8
-struct MlpSmem {
-    __nv_bfloat16 w1[kHid * kS1];
-    __nv_bfloat16 w2[kHid * kS2];
-    __nv_bfloat16 w3[kHid * kS2];
-    __nv_bfloat16 w4[8 * kS2];      // 3 outputs padded to 8
-    float b1[kHid], b2[kHid], b3[kHid], b4[8];
-};
-
-__device__ void load_mlp_smem(const float* __restrict__ th, MlpSmem& S)
-{
-    for (int k = threadIdx.x; k < kHid * kS1; k += blockDim.x) {
-        const int o = k / kS1, i = k % kS1;
-        S.w1[k] = __float2bfloat16_rn(i < kIn ? th[kOffW1 + o * kIn + i] : 0.f);
-    }
-    for (int k = threadIdx.x; k < kHid * kS2; k += blockDim.x) {
-        const int o = k / kS2, i = k % kS2;
-        S.w2[k] = __float2bfloat16_rn(i < kHid ? th[kOffW2 + o * kHid + i] : 0.f);
-        S.w3[k] = __float2bfloat16_rn(i < kHid ? th[kOffW3 + o * kHid + i] : 0.f);
-    }
-    for (int k = threadIdx.x; k < 8 * kS2; k += blockDim.x) {
-        const int o = k / kS2, i = k % kS2;
-        S.w4[k] = __float2bfloat16_rn(o < kOutN && i < kHid ? th[kOffW4 + o * kHid + i] : 0.f);
-    }
-    for (int k = threadIdx.x; k < kHid; k += blockDim.x) {
-        S.b1[k] = th[kOffB1 + k];
-        S.b2[k] = th[kOffB2 + k];
-        S.b3[k] = th[kOffB3 + k];
-    }
-    if (threadIdx.x < 8) S.b4[threadIdx.x] = threadIdx.x < kOutN ? th[kOffB4 + threadIdx.x] : 0.f;
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x (low half) = lo
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-__device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 __device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
 
-// One warp evaluates the network on 16 rows.  feat: 16 x 16 FP32 (inputs in
-// columns 0..11, zeros after); out: 16 x 8 FP32 (outputs in columns 0..2).
-// Fragment layouts of mma.m16n8k16 (g = lane / 4, t = lane % 4):
-//   A: {row g, cols 2t,2t+1}, {row g+8, 2t,2t+1}, {row g, 2t+8,2t+9}, {row g+8, 2t+8,2t+9}
-//   B: {k 2t,2t+1; col g}, {k 2t+8,2t+9; col g}
-//   C: {row g, col 2t}, {row g, 2t+1}, {row g+8, 2t}, {row g+8, 2t+1}
-// The accumulators of column tiles 2k and 2k+1 are exactly the A fragment of
-// k-block k of the next layer, so activations stay in registers.
-__device__ void mlp_warp(const MlpSmem& S, const float (*feat)[16], float (*out)[8])
+// --- the network on the 5th-generation tensor cores (tcgen05) ---------------
+// A CTA of 128 threads evaluates 128 rows at a time, thread r owning row r.
+// Operands live in shared memory in the K-major layout without swizzle:
+// core matrices of 8 rows x 16 bytes (8 BF16), K-adjacent core matrices 128
+// bytes apart (LBO), 8-row groups K/8 * 128 bytes apart (SBO).  One thread
+// issues tcgen05.mma (M = 128, N = 64 or 16, K = 16 per instruction) into a
+// 64-column TMEM accumulator and commits it to an mbarrier; each warp reads
+// its 32 TMEM lanes (rows) back with tcgen05.ld, adds the bias, applies SiLU
+// and writes the next layer's operand.  Every wait is bounded; TMEM is freed
+// on every exit path.
+constexpr int kTcRows = 128;
+constexpr int kTcCols = 64;      // TMEM columns allocated per CTA
+
+__device__ __forceinline__ uint32_t kmaj_off(int r, int k, int K)
 {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    uint32_t A[4][4];
-    {
-        const uint32_t a0 = pack_bf16(feat[g][2 * t], feat[g][2 * t + 1]);
-        const uint32_t a1 = pack_bf16(feat[g + 8][2 * t], feat[g + 8][2 * t + 1]);
-        const uint32_t a2 = pack_bf16(feat[g][2 * t + 8], feat[g][2 * t + 9]);
-        const uint32_t a3 = pack_bf16(feat[g + 8][2 * t + 8], feat[g + 8][2 * t + 9]);
-        float acc[8][4];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            acc[j][0] = acc[j][2] = S.b1[8 * j + 2 * t];
-            acc[j][1] = acc[j][3] = S.b1[8 * j + 2 * t + 1];
-            const __nv_bfloat16* w = S.w1 + (8 * j + g) * kS1 + 2 * t;
-            mma_bf16(acc[j], a0, a1, a2, a3, ld_u32(w), ld_u32(w + 8));
-        }
-#pragma unroll
-        for (int kb = 0; kb < 4; ++kb) {
-            A[kb][0] = pack_bf16(silu_f(acc[2 * kb][0]), silu_f(acc[2 * kb][1]));
-            A[kb][1] = pack_bf16(silu_f(acc[2 * kb][2]), silu_f(acc[2 * kb][3]));
-            A[kb][2] = pack_bf16(silu_f(acc[2 * kb + 1][0]), silu_f(acc[2 * kb + 1][1]));
-            A[kb][3] = pack_bf16(silu_f(acc[2 * kb + 1][2]), silu_f(acc[2 * kb + 1][3]));
-        }
-    }
-#pragma unroll
-    for (int layer = 0; layer < 2; ++layer) {
-        const __nv_bfloat16* W = layer == 0 ? S.w2 : S.w3;
-        const float* b = layer == 0 ? S.b2 : S.b3;
-        float acc[8][4];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            acc[j][0] = acc[j][2] = b[8 * j + 2 * t];
-            acc[j][1] = acc[j][3] = b[8 * j + 2 * t + 1];
-        }
-#pragma unroll
-        for (int kb = 0; kb < 4; ++kb)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const __nv_bfloat16* w = W + (8 * j + g) * kS2 + 16 * kb + 2 * t;
-                mma_bf16(acc[j], A[kb][0], A[kb][1], A[kb][2], A[kb][3], ld_u32(w), ld_u32(w + 8));
-            }
-#pragma unroll
-        for (int kb = 0; kb < 4; ++kb) {
-            A[kb][0] = pack_bf16(silu_f(acc[2 * kb][0]), silu_f(acc[2 * kb][1]));
-            A[kb][1] = pack_bf16(silu_f(acc[2 * kb][2]), silu_f(acc[2 * kb][3]));
-            A[kb][2] = pack_bf16(silu_f(acc[2 * kb + 1][0]), silu_f(acc[2 * kb + 1][1]));
-            A[kb][3] = pack_bf16(silu_f(acc[2 * kb + 1][2]), silu_f(acc[2 * kb + 1][3]));
-        }
-    }
-    float acc[4];
-    acc[0] = acc[2] = S.b4[2 * t];
-    acc[1] = acc[3] = S.b4[2 * t + 1];
-#pragma unroll
-    for (int kb = 0; kb < 4; ++kb) {
-        const __nv_bfloat16* w = S.w4 + g * kS2 + 16 * kb + 2 * t;
-        mma_bf16(acc, A[kb][0], A[kb][1], A[kb][2], A[kb][3], ld_u32(w), ld_u32(w + 8));
-    }
-    out[g][2 * t] = acc[0];
-    out[g][2 * t + 1] = acc[1];
-    out[g + 8][2 * t] = acc[2];
-    out[g + 8][2 * t + 1] = acc[3];
+    return (uint32_t)((r >> 3) * (K / 8) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
-// --- plain inference on given rows (tests, evaluation) ------------------------
-constexpr int kMlpWarps = 8;
+struct TcMlpSmem {
+    alignas(128) __nv_bfloat16 x[kTcRows * 16];    // layer-1 operand (12 inputs + 4 zeros)
+    alignas(128) __nv_bfloat16 h[kTcRows * kHid];  // hidden operand
+    alignas(128) __nv_bfloat16 w1[kHid * 16];
+    alignas(128) __nv_bfloat16 w2[kHid * kHid];
+    alignas(128) __nv_bfloat16 w3[kHid * kHid];
+    alignas(128) __nv_bfloat16 w4[16 * kHid];      // 3 outputs padded to N = 16
+    float b1[kHid], b2[kHid], b3[kHid], b4[16];
+    alignas(8) uint64_t bar;
+    uint32_t tmem;
+    int ok;
+};
 
-__global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_infer(const float* __restrict__ theta, const float* __restrict__ X,
-                                                              float* __restrict__ Y, int64_t n)
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start >> 4, LBO >> 4, SBO >> 4, the fixed
+// version bits (46..48 = 0b001), no base offset, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
-    __shared__ MlpSmem S;
-    __shared__ float feat[kMlpWarps][16][16];
-    __shared__ float out[kMlpWarps][16][8];
-    load_mlp_smem(theta, S);
-    __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int64_t base = ((int64_t)blockIdx.x * kMlpWarps + w) * 16; base < n; base += (int64_t)gridDim.x * kMlpWarps * 16) {
-        if (lane < 16) {
-            const int64_t r = base + lane;
-            for (int k = 0; k < 16; ++k) feat[w][lane][k] = (r < n && k < kIn) ? X[r * kIn + k] : 0.f;
-        }
-        __syncwarp();
-        mlp_warp(S, feat[w], out[w]);
-        __syncwarp();
-        if (lane < 16 && base + lane < n)   // skip connection: + previous impulse (inputs 3..5), in FP32
-            for (int k = 0; k < kOutN; ++k) Y[(base + lane) * kOutN + k] = out[w][lane][k] + feat[w][lane][3 + k];
-        __syncwarp();
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, int accumulate)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Waits for the mbarrier phase with the given parity; false after ~2^31
+// SM clocks (about a second).
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done = 0;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1LL << 31)) return false;
     }
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes (one row per thread).
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// Weights into the operand layouts, biases, mbarrier, TMEM (warp 0).  All
+// 128 threads; returns with the TMEM base in S.tmem.
+__device__ void tc_setup(const float* __restrict__ th, TcMlpSmem& S)
+{
+    for (int e = threadIdx.x; e < kHid * 16; e += blockDim.x) {
+        const int n = e / 16, k = e % 16;
+        S.w1[kmaj_off(n, k, 16) / 2] = __float2bfloat16_rn(k < kIn ? th[kOffW1 + n * kIn + k] : 0.f);
+    }
+    for (int e = threadIdx.x; e < kHid * kHid; e += blockDim.x) {
+        const int n = e / kHid, k = e % kHid;
+        S.w2[kmaj_off(n, k, kHid) / 2] = __float2bfloat16_rn(th[kOffW2 + n * kHid + k]);
+        S.w3[kmaj_off(n, k, kHid) / 2] = __float2bfloat16_rn(th[kOffW3 + n * kHid + k]);
+    }
+    for (int e = threadIdx.x; e < 16 * kHid; e += blockDim.x) {
+        const int n = e / kHid, k = e % kHid;
+        S.w4[kmaj_off(n, k, kHid) / 2] = __float2bfloat16_rn(n < kOutN ? th[kOffW4 + n * kHid + k] : 0.f);
+    }
+    for (int k = threadIdx.x; k < kHid; k += blockDim.x) {
+        S.b1[k] = th[kOffB1 + k];
+        S.b2[k] = th[kOffB2 + k];
+        S.b3[k] = th[kOffB3 + k];
+    }
+    if (threadIdx.x < 16) S.b4[threadIdx.x] = threadIdx.x < kOutN ? th[kOffB4 + threadIdx.x] : 0.f;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.bar)) : "memory");
+        S.ok = 1;
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&S.tmem)),
+                     "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // weights: generic stores -> MMA reads
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ void tc_teardown(TcMlpSmem& S)
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem), "r"(kTcCols) : "memory");
+    }
+}
+
+// One layer: MMAs over K (kk slices of 16) from operand a (K columns) and
+// weights b (N rows), committed and waited for.  All threads; thread 0 issues.
+__device__ __forceinline__ bool tc_layer(TcMlpSmem& S, const __nv_bfloat16* a, const __nv_bfloat16* b, int K, int N,
+                                         uint32_t& phase)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // operand rows written by every thread
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t sa = smem_addr(a), sb = smem_addr(b);
+        const uint32_t idesc = tc_idesc(kTcRows, N);
+        for (int kk = 0; kk < K / 16; ++kk)
+            tc_mma(S.tmem, tc_desc(sa + 256u * kk, 128u, (uint32_t)(K / 8) * 128u),
+                   tc_desc(sb + 256u * kk, 128u, (uint32_t)(K / 8) * 128u), idesc, kk > 0);
+        tc_commit(&S.bar);
+    }
+    const bool ok = tc_wait(&S.bar, phase & 1u);
+    phase += 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return __syncthreads_and(ok) != 0;   // the same answer on every thread
+}
+
+// Epilogue of a hidden layer: row r's 64 accumulators + bias, SiLU, BF16
+// into the hidden operand.
+__device__ __forceinline__ void tc_hidden_out(TcMlpSmem& S, const float* bias)
+{
+    const int r = threadIdx.x, w = threadIdx.x >> 5;
+    const uint32_t lane_base = S.tmem + ((uint32_t)(32 * w) << 16);
+    for (int c0 = 0; c0 < kHid; c0 += 16) {
+        float v[16];
+        tc_ld16(lane_base + (uint32_t)c0, v);
+        uint32_t pk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            pk[j] = pack_bf16(silu_f(v[2 * j] + bias[c0 + 2 * j]), silu_f(v[2 * j + 1] + bias[c0 + 2 * j + 1]));
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.h) + kmaj_off(r, c0, kHid)) =
+            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.h) + kmaj_off(r, c0 + 8, kHid)) =
+            make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    }
+}
+
+// The network on this CTA's 128 rows: in = the thread's 12 inputs (zeros
+// for an empty row), out = the 3 outputs before the skip connection.
+// Returns false if a wait gave up (outputs undefined).
+__device__ bool tc_forward(TcMlpSmem& S, const float (&in)[kIn], float (&out)[kOutN], uint32_t& phase)
+{
+    const int r = threadIdx.x;
+    {
+        uint32_t pk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float lo = 2 * j < kIn ? in[2 * j] : 0.f, hi = 2 * j + 1 < kIn ? in[2 * j + 1] : 0.f;
+            pk[j] = pack_bf16(lo, hi);
+        }
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.x) + kmaj_off(r, 0, 16)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.x) + kmaj_off(r, 8, 16)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    }
+    bool ok = tc_layer(S, S.x, S.w1, 16, kHid, phase);
+    if (ok) tc_hidden_out(S, S.b1);
+    // the next MMA reads S.h and overwrites the accumulator: every thread has
+    // finished its tcgen05.ld (waited) and its stores before the barrier in tc_layer
+    ok = ok && tc_layer(S, S.h, S.w2, kHid, kHid, phase);
+    if (ok) tc_hidden_out(S, S.b2);
+    ok = ok && tc_layer(S, S.h, S.w3, kHid, kHid, phase);
+    if (ok) tc_hidden_out(S, S.b3);
+    ok = ok && tc_layer(S, S.h, S.w4, kHid, 16, phase);
+    if (ok) {
+        float v[16];
+        tc_ld16(S.tmem + ((uint32_t)(32 * (threadIdx.x >> 5)) << 16), v);
+#pragma unroll
+        for (int k = 0; k < kOutN; ++k) out[k] = v[k] + S.b4[k];
+    }
+    return ok;
+}
+
+__device__ unsigned g_mlp_status;   // nbgs_mlp_infer: a tensor-core wait gave up
+
+// --- plain inference on given rows (tests, evaluation) ------------------------
+__global__ void __launch_bounds__(kTcRows) k_mlp_infer_tc(const float* __restrict__ theta, const float* __restrict__ X,
+                                                          float* __restrict__ Y, int64_t n)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    TcMlpSmem& S = *reinterpret_cast<TcMlpSmem*>(tc_smem);
+    tc_setup(theta, S);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int64_t base = (int64_t)blockIdx.x * kTcRows; base < n; base += (int64_t)gridDim.x * kTcRows) {
+        const int64_t row = base + threadIdx.x;
+        float in[kIn], out[kOutN];
+#pragma unroll
+        for (int k = 0; k < kIn; ++k) in[k] = row < n ? X[row * kIn + k] : 0.f;
+        if (ok && !tc_forward(S, in, out, phase)) {   // a wait gave up (uniform): NaN from here on
+            ok = false;
+            if (threadIdx.x == 0) atomicOr(&g_mlp_status, 1u);
+        }
+        if (row < n)   // skip connection: + previous impulse (inputs 3..5), in FP32
+            for (int k = 0; k < kOutN; ++k) Y[row * kOutN + k] = ok ? out[k] + in[3 + k] : __int_as_float(0x7FC00000);
+    }
+    tc_teardown(S);
 }
 
 // --- training: FP32 forward + backward on CUDA cores --------------------------
@@ -324,121 +427,146 @@ template <class R> struct WarmArgs {
     double dt;
     double mu;
     SceneView V;
-    const DevInfo* info;
+    DevInfo* info;
+};
+
+// Features of sweep slot s (see the top of this file) and what applying the
+// network's output needs: the frame angle (cth, sth), w_n, v_ref, mu and the
+// previous-step impulse (p0.w != 0: the contact existed in the last step).
+template <class R> struct ContactFeatures {
+    float f[kIn];
+    double cth, sth, wn, vr, mu;
+    R4<R> p0;
 };
 
 template <class R>
-__global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_warmstart(WarmArgs<R> A)
+__device__ void contact_features(const WarmArgs<R>& A, int64_t s, double vr_all, ContactFeatures<R>& F)
 {
-    __shared__ MlpSmem S;
-    __shared__ float feat[kMlpWarps][16][16];
-    __shared__ float out[kMlpWarps][16][8];
-    if (A.apply) load_mlp_smem(A.theta, S);
-    __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double nx, ny, nz, tx, ty, tz, ox, oy, oz;
+    const SweepRec<R> rr = A.rec[s];
+    uint32_t ia, ib;
+    double la, lb;
+    if constexpr (sizeof(R) == 4) {
+        ia = __float_as_uint(rr.a.x);
+        ib = __float_as_uint(rr.a.y);
+        la = rr.a.z;
+        lb = rr.a.w;
+        nx = rr.b.x;
+        ny = rr.b.y;
+        nz = rr.b.z;
+    } else {
+        const uint64_t ids = (uint64_t)__double_as_longlong(rr.ids_bias.x);
+        ia = (uint32_t)(ids & 0xFFFFFFFFu);
+        ib = (uint32_t)(ids >> 32);
+        la = rr.lev.x;
+        lb = rr.lev.y;
+        nx = rr.nxy.x;
+        ny = rr.nxy.y;
+        nz = rr.nz_.x;
+    }
+    F.p0 = A.p[s];
+    const bool dyn_b = ib < (uint64_t)A.n;
+    const R4<R> va = A.vel[2 * (int64_t)ia], wa = A.vel[2 * (int64_t)ia + 1];
+    R4<R> vb, wb;
+    vb.x = vb.y = vb.z = vb.w = R(0);
+    wb = vb;
+    if (dyn_b) {
+        vb = A.vel[2 * (int64_t)ib];
+        wb = A.vel[2 * (int64_t)ib + 1];
+    }
+    F.mu = A.mu;
+    if (A.V.batch) {
+        const uint32_t sc = A.V.scene_of[ia];
+        F.vr = A.V.vref[sc];
+        F.mu = A.V.mu[sc];
+    } else {
+        F.vr = vr_all;
+    }
+    const double vr = F.vr;
+    const double ka = va.w > R(0) ? 1.0 : 0.0, kb = vb.w > R(0) ? 1.0 : 0.0;   // gravity kick of finite masses
+    const double vax = va.x + ka * A.gdt[0], vay = va.y + ka * A.gdt[1], vaz = va.z + ka * A.gdt[2];
+    const double vbx = vb.x + kb * A.gdt[0], vby = vb.y + kb * A.gdt[1], vbz = vb.z + kb * A.gdt[2];
+    const double cax = wa.y * nz - wa.z * ny, cay = wa.z * nx - wa.x * nz, caz = wa.x * ny - wa.y * nx;
+    const double cbx = wb.y * nz - wb.z * ny, cby = wb.z * nx - wb.x * nz, cbz = wb.x * ny - wb.y * nx;
+    const double ux = (vax - la * cax) - (vbx + lb * cbx);
+    const double uy = (vay - la * cay) - (vby + lb * cby);
+    const double uz = (vaz - la * caz) - (vbz + lb * cbz);
+    tangent_basis<double>(nx, ny, nz, tx, ty, tz, ox, oy, oz);
+    const double un = nx * ux + ny * uy + nz * uz;
+    const double ut = tx * ux + ty * uy + tz * uz, uo = ox * ux + oy * uy + oz * uz;
+    const double utl = sqrt(ut * ut + uo * uo);
+    F.cth = 1.0;
+    F.sth = 0.0;
+    if (utl > 1e-12 * vr) {   // e2 = -u_t / |u_t| = cos t + sin o
+        F.cth = -ut / utl;
+        F.sth = -uo / utl;
+    }
+    const double wn = (double)va.w + (double)vb.w;
+    F.wn = wn;
+    const double wt = wn + (double)wa.w * la * la + (double)wb.w * lb * lb;
+    // previous impulse in (n, e2, e3): e3 = -sin t + cos o
+    const double q2 = F.p0.y * F.cth + F.p0.z * F.sth, q3 = -F.p0.y * F.sth + F.p0.z * F.cth;
+    const double sc = wn / vr;
+    const double ra = A.pos_r[ia].w, rb = dyn_b ? A.pos_r[ib].w : 0.0;
+    const uint32_t da = A.finite[ia] ? A.adj_off[ia + 1] - A.adj_off[ia] : 0;
+    const uint32_t db = (dyn_b && A.finite[ib]) ? A.adj_off[ib + 1] - A.adj_off[ib] : 0;
+    const uint32_t cidx = A.perm[s];
+    const double xi_dt = A.cgeo[cidx].w / A.dt;   // the geometric gap, not the beta-scaled term
+    const double f[kIn] = {un / vr,   utl / vr,      xi_dt / vr,      F.p0.x * sc, q2 * sc, q3 * sc,
+                           log(fmax(wn, 1e-300)),    wt / wn, ra,     rb,          F.mu,    (double)(da + db) / 12.0};
+#pragma unroll
+    for (int k = 0; k < kIn; ++k) F.f[k] = (float)f[k];
+    if (A.feat_out) {
+        float* o = A.feat_out + (int64_t)cidx * 16;
+        for (int k = 0; k < kIn; ++k) o[k] = F.f[k];
+        o[12] = (float)F.cth;
+        o[13] = (float)F.sth;
+        o[14] = (float)wn;
+        o[15] = (float)vr;
+    }
+}
+
+// One CTA: 128 contacts per tile, thread r the contact of row r.  With
+// apply, the network runs on the tensor cores and a contact without a
+// previous-step impulse takes its prediction (previous impulse + network
+// correction, in the frame and scale of the features, projected onto the
+// friction cone); the others keep theirs, as does a non-finite output.
+template <class R>
+__global__ void __launch_bounds__(kTcRows) k_mlp_warmstart(WarmArgs<R> A)
+{
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    TcMlpSmem& S = *reinterpret_cast<TcMlpSmem*>(tc_smem);
+    if (A.apply) tc_setup(A.theta, S);
     const double vr_all = fmax(fmax(__longlong_as_double((long long)A.info->vmax_bits), A.gdt_norm), 1e-12);
-    for (int64_t base = ((int64_t)blockIdx.x * kMlpWarps + w) * 16; base < A.C;
-         base += (int64_t)gridDim.x * kMlpWarps * 16) {
-        const int64_t s = base + lane;
-        const bool live = lane < 16 && s < A.C;
-        double nx = 0, ny = 0, nz = 0, tx = 0, ty = 0, tz = 0, ox = 0, oy = 0, oz = 0, cth = 1, sth = 0, wn = 1, vr = 1,
-               mu = A.mu;
-        R4<R> p0;
-        p0.x = p0.y = p0.z = p0.w = R(0);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int64_t base = (int64_t)blockIdx.x * kTcRows; base < A.C; base += (int64_t)gridDim.x * kTcRows) {
+        const int64_t s = base + threadIdx.x;
+        const bool live = s < A.C;
+        ContactFeatures<R> F;
         if (live) {
-            const SweepRec<R> rr = A.rec[s];
-            uint32_t ia, ib;
-            double la, lb, bias;
-            if constexpr (sizeof(R) == 4) {
-                ia = __float_as_uint(rr.a.x);
-                ib = __float_as_uint(rr.a.y);
-                la = rr.a.z;
-                lb = rr.a.w;
-                nx = rr.b.x;
-                ny = rr.b.y;
-                nz = rr.b.z;
-            } else {
-                const uint64_t ids = (uint64_t)__double_as_longlong(rr.ids_bias.x);
-                ia = (uint32_t)(ids & 0xFFFFFFFFu);
-                ib = (uint32_t)(ids >> 32);
-                la = rr.lev.x;
-                lb = rr.lev.y;
-                nx = rr.nxy.x;
-                ny = rr.nxy.y;
-                nz = rr.nz_.x;
-            }
-            (void)bias;
-            p0 = A.p[s];
-            const bool dyn_b = ib < (uint64_t)A.n;
-            const R4<R> va = A.vel[2 * (int64_t)ia], wa = A.vel[2 * (int64_t)ia + 1];
-            R4<R> vb, wb;
-            vb.x = vb.y = vb.z = vb.w = R(0);
-            wb = vb;
-            if (dyn_b) {
-                vb = A.vel[2 * (int64_t)ib];
-                wb = A.vel[2 * (int64_t)ib + 1];
-            }
-            if (A.V.batch) {
-                const uint32_t sc = A.V.scene_of[ia];
-                vr = A.V.vref[sc];
-                mu = A.V.mu[sc];
-            } else {
-                vr = vr_all;
-            }
-            const double ka = va.w > R(0) ? 1.0 : 0.0, kb = vb.w > R(0) ? 1.0 : 0.0;   // gravity kick of finite masses
-            const double vax = va.x + ka * A.gdt[0], vay = va.y + ka * A.gdt[1], vaz = va.z + ka * A.gdt[2];
-            const double vbx = vb.x + kb * A.gdt[0], vby = vb.y + kb * A.gdt[1], vbz = vb.z + kb * A.gdt[2];
-            const double cax = wa.y * nz - wa.z * ny, cay = wa.z * nx - wa.x * nz, caz = wa.x * ny - wa.y * nx;
-            const double cbx = wb.y * nz - wb.z * ny, cby = wb.z * nx - wb.x * nz, cbz = wb.x * ny - wb.y * nx;
-            const double ux = (vax - la * cax) - (vbx + lb * cbx);
-            const double uy = (vay - la * cay) - (vby + lb * cby);
-            const double uz = (vaz - la * caz) - (vbz + lb * cbz);
-            tangent_basis<double>(nx, ny, nz, tx, ty, tz, ox, oy, oz);
-            const double un = nx * ux + ny * uy + nz * uz;
-            const double ut = tx * ux + ty * uy + tz * uz, uo = ox * ux + oy * uy + oz * uz;
-            const double utl = sqrt(ut * ut + uo * uo);
-            if (utl > 1e-12 * vr) {   // e2 = -u_t / |u_t| = cos t + sin o
-                cth = -ut / utl;
-                sth = -uo / utl;
-            }
-            wn = (double)va.w + (double)vb.w;
-            const double wt = wn + (double)wa.w * la * la + (double)wb.w * lb * lb;
-            // previous impulse in (n, e2, e3): e3 = -sin t + cos o
-            const double q2 = p0.y * cth + p0.z * sth, q3 = -p0.y * sth + p0.z * cth;
-            const double sc = wn / vr;
-            const double ra = A.pos_r[ia].w, rb = dyn_b ? A.pos_r[ib].w : 0.0;
-            const uint32_t da = A.finite[ia] ? A.adj_off[ia + 1] - A.adj_off[ia] : 0;
-            const uint32_t db = (dyn_b && A.finite[ib]) ? A.adj_off[ib + 1] - A.adj_off[ib] : 0;
-            const uint32_t cidx = A.perm[s];
-            const double xi_dt = A.cgeo[cidx].w / A.dt;   // the geometric gap, not the beta-scaled term
-            const double f[14] = {un / vr,       utl / vr,      xi_dt / vr,     p0.x * sc,  q2 * sc,
-                                  q3 * sc,       log(fmax(wn, 1e-300)), wt / wn, ra,       rb,
-                                  mu,            (double)(da + db) / 12.0, cth, sth};
-            for (int k = 0; k < 16; ++k) feat[w][lane][k] = k < kIn ? (float)f[k] : 0.f;
-            if (A.feat_out) {
-                float* o = A.feat_out + (int64_t)cidx * 16;
-                for (int k = 0; k < 14; ++k) o[k] = (float)f[k];
-                o[14] = (float)wn;
-                o[15] = (float)vr;
-            }
-        } else if (lane < 16) {
-            for (int k = 0; k < 16; ++k) feat[w][lane][k] = 0.f;
+            contact_features<R>(A, s, vr_all, F);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kIn; ++k) F.f[k] = 0.f;
+            F.p0.w = R(1);
         }
-        if (!A.apply) continue;
-        __syncwarp();
-        mlp_warp(S, feat[w], out[w]);
-        __syncwarp();
-        // a contact with a previous-step impulse keeps it; the network
-        // predicts the impulses of contacts that had none
-        if (live && p0.w == R(0)) {
-            const double k = vr / wn;   // skip connection: previous impulse + network correction
-            const double y1 = ((double)out[w][lane][0] + feat[w][lane][3]) * k;
-            const double y2 = ((double)out[w][lane][1] + feat[w][lane][4]) * k;
-            const double y3 = ((double)out[w][lane][2] + feat[w][lane][5]) * k;
-            double pn = y1, pt = y2 * cth - y3 * sth, po = y2 * sth + y3 * cth;
+        if (!A.apply || !ok) continue;   // both uniform over the CTA
+        float out[kOutN];
+        if (!tc_forward(S, F.f, out, phase)) {
+            ok = false;
+            if (threadIdx.x == 0) atomicOr(&A.info->err, kErrTimeout);
+            continue;
+        }
+        if (live && F.p0.w == R(0)) {
+            const double k = F.vr / F.wn;   // skip connection: previous impulse + network correction
+            const double y1 = ((double)out[0] + F.f[3]) * k;
+            const double y2 = ((double)out[1] + F.f[4]) * k;
+            const double y3 = ((double)out[2] + F.f[5]) * k;
+            double pn = y1, pt = y2 * F.cth - y3 * F.sth, po = y2 * F.sth + y3 * F.cth;
             if (isfinite(pn) && isfinite(pt) && isfinite(po)) {   // otherwise keep the previous-step impulse
                 pn = pn > 0.0 ? pn : 0.0;
-                const double lim = mu * pn, len = sqrt(pt * pt + po * po);
+                const double lim = F.mu * pn, len = sqrt(pt * pt + po * po);
                 if (len > lim) {
                     const double f = len > 0.0 ? lim / len : 0.0;
                     pt *= f;
@@ -452,8 +580,8 @@ __global__ void __launch_bounds__(32 * kMlpWarps) k_mlp_warmstart(WarmArgs<R> A)
                 A.p[s] = q;
             }
         }
-        __syncwarp();
     }
+    if (A.apply) tc_teardown(S);
 }
 
 template <class R>
@@ -490,11 +618,10 @@ nbgs_status run_mlp_prologue(nbgs_scene* s, int apply, float* feat_out)
     const int64_t C = s->n_contacts;
     if (C <= 0) return NBGS_OK;
     if (apply && !s->mlp_theta) return fail(s, NBGS_EINVAL, "MLP warm start: no network loaded (nbgs_mlp_load)");
-    const int T = 32 * kMlpWarps;
-    const int64_t groups = (C + 15) / 16;
-    const int gb = grid_for(groups * 32, T, 4, s->num_sms);
-    if (s->fp32) k_mlp_warmstart<float><<<gb, T, 0, s->stream>>>(warm_args<float>(s, apply, feat_out));
-    else k_mlp_warmstart<double><<<gb, T, 0, s->stream>>>(warm_args<double>(s, apply, feat_out));
+    const int gb = grid_for(C, kTcRows, 4, s->num_sms);
+    const size_t smem = apply ? sizeof(TcMlpSmem) : 0;
+    if (s->fp32) k_mlp_warmstart<float><<<gb, kTcRows, smem, s->stream>>>(warm_args<float>(s, apply, feat_out));
+    else k_mlp_warmstart<double><<<gb, kTcRows, smem, s->stream>>>(warm_args<double>(s, apply, feat_out));
     if (s->timing) s->phase_launches[2] += 1;
     return cuda_check(s, cudaGetLastError(), "MLP prologue");
 }
@@ -512,9 +639,9 @@ nbgs_status nbgs_mlp_infer(const float* theta, const float* X, float* Y, int64_t
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t groups = (n + 15) / 16;
-    k_mlp_infer<<<grid_for(groups * 32, 32 * kMlpWarps, 4, sms), 32 * kMlpWarps, 0, (cudaStream_t)stream>>>(theta, X, Y,
-                                                                                                         n);
+    const int64_t tiles = (n + kTcRows - 1) / kTcRows;
+    k_mlp_infer_tc<<<grid_for(tiles * kTcRows, kTcRows, 4, sms), kTcRows, sizeof(TcMlpSmem), (cudaStream_t)stream>>>(
+        theta, X, Y, n);
     return cudaGetLastError() == cudaSuccess ? NBGS_OK : NBGS_ECUDA;
 }
 

@@ -1,5 +1,5 @@
 """Learned warm start on the GPU against the FP64 references in oracle/:
-tensor-core inference (BF16 operands, FP32 accumulation), FP32 training
+tensor-core inference (tcgen05, BF16 operands, FP32 accumulation), FP32 training
 gradients and Adam, and the per-contact feature map."""
 import math
 
@@ -38,7 +38,7 @@ def test_tensor_core_inference_matches_reference(env):
     torch, nb, ws = env
     rng = np.random.default_rng(0)
     theta = ws.init_params(3) + rng.normal(0, 0.02, ws.N_PARAMS).astype(np.float32)
-    for n in (1, 16, 17, 1000, 4099):          # partial warps and blocks
+    for n in (1, 16, 17, 127, 128, 129, 1000, 4099):   # partial and full 128-row tiles
         X = rng.normal(0, 1.0, (n, 12)).astype(np.float32)
         Y = ws.infer(theta, X)
         ref = _forward_bf16(theta.astype(np.float64), X.astype(np.float64))
