@@ -277,7 +277,8 @@ nbgs_status nbgs_mlp_load(nbgs_scene* scene, const float* theta, int64_t count /
  * Synchronises. */
 nbgs_status nbgs_mlp_features(nbgs_scene* scene, float* out, int64_t cap, int64_t* n_out);
 
-/* Network on n rows of X (n x 12, device) -> Y (n x 3, device): evaluation
+/* Network on n rows of X (n x 12, device, 16-byte aligned, else
+ * NBGS_EINVAL) -> Y (n x 3, device): evaluation
  * on the 5th-generation tensor cores (tcgen05, 128 rows per CTA, TMEM
  * accumulators), BF16 operands and FP32 accumulation.  theta: device
  * pointer.  Asynchronous on stream; rows of a tile whose tensor-core wait

@@ -43,6 +43,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 }
 
 __device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
+// the inference epilogue's SiLU (its result is rounded to BF16 anyway)
+__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.f + __expf(-z)); }
 
 // --- the network on the 5th-generation tensor cores (tcgen05) ---------------
 // A CTA of 128 threads evaluates 128 rows at a time, thread r owning row r.
@@ -223,7 +225,7 @@ __device__ __forceinline__ void tc_hidden_out(TcMlpSmem& S, const float* bias)
         uint32_t pk[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-            pk[j] = pack_bf16(silu_f(v[2 * j] + bias[c0 + 2 * j]), silu_f(v[2 * j + 1] + bias[c0 + 2 * j + 1]));
+            pk[j] = pack_bf16(silu_fast(v[2 * j] + bias[c0 + 2 * j]), silu_fast(v[2 * j + 1] + bias[c0 + 2 * j + 1]));
         *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.h) + kmaj_off(r, c0, kHid)) =
             make_uint4(pk[0], pk[1], pk[2], pk[3]);
         *reinterpret_cast<uint4*>(reinterpret_cast<char*>(S.h) + kmaj_off(r, c0 + 8, kHid)) =
@@ -279,8 +281,20 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_infer_tc(const float* __restric
     for (int64_t base = (int64_t)blockIdx.x * kTcRows; base < n; base += (int64_t)gridDim.x * kTcRows) {
         const int64_t row = base + threadIdx.x;
         float in[kIn], out[kOutN];
+        if (row < n) {   // a row is 48 bytes: three 16-byte loads (X is 16-byte aligned)
+            const float4* xr = reinterpret_cast<const float4*>(X + row * kIn);
 #pragma unroll
-        for (int k = 0; k < kIn; ++k) in[k] = row < n ? X[row * kIn + k] : 0.f;
+            for (int q = 0; q < 3; ++q) {
+                const float4 v = xr[q];
+                in[4 * q] = v.x;
+                in[4 * q + 1] = v.y;
+                in[4 * q + 2] = v.z;
+                in[4 * q + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kIn; ++k) in[k] = 0.f;
+        }
         if (ok && !tc_forward(S, in, out, phase)) {   // a wait gave up (uniform): NaN from here on
             ok = false;
             if (threadIdx.x == 0) atomicOr(&g_mlp_status, 1u);
@@ -634,7 +648,7 @@ extern "C" {
 
 nbgs_status nbgs_mlp_infer(const float* theta, const float* X, float* Y, int64_t n, void* stream)
 {
-    if (!theta || n < 0 || (n > 0 && (!X || !Y))) return NBGS_EINVAL;
+    if (!theta || n < 0 || (n > 0 && (!X || !Y)) || ((uintptr_t)X & 15u)) return NBGS_EINVAL;
     if (n == 0) return NBGS_OK;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
