@@ -286,8 +286,9 @@ __global__ void k_hull(int64_t n, const R4<R>* __restrict__ vel, const double4_3
     double hmax = 0.0, vmax = 0.0;
     bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const R4<R> v = vel[2 * i], w = vel[2 * i + 1];
-        const double4_32a x = pos_r[i];
+        R4<R> v, w;
+        ld_body(vel + 2 * i, v, w);
+        const double4_32a x = ld_d4(pos_r + i);
         const double r = x.w;
         const double nv = norm_exact((double)v.x, (double)v.y, (double)v.z);
         const double nw = norm_exact((double)w.x, (double)w.y, (double)w.z);

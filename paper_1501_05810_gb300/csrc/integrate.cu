@@ -15,12 +15,13 @@ __global__ void k_integrate(int64_t n, double4_32a* __restrict__ pos_r, double4_
 {
     bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const R4<R> v = vel[2 * i], w = vel[2 * i + 1];
-        double4_32a x = pos_r[i];
+        R4<R> v, w;
+        ld_body(vel + 2 * i, v, w);
+        double4_32a x = ld_d4(pos_r + i);
         x.x += dt * (double)v.x;
         x.y += dt * (double)v.y;
         x.z += dt * (double)v.z;
-        double4_32a q = quat[i];
+        double4_32a q = ld_d4(quat + i);
         {
             // quaternion update in the sweep precision (FP64 is scarce on this
             // GPU; orientations of spheres never feed back into the dynamics)
@@ -55,8 +56,8 @@ __global__ void k_integrate(int64_t n, double4_32a* __restrict__ pos_r, double4_
             x.z = lo.z + s;
         }
         if (!(fabs(x.x) + fabs(x.y) + fabs(x.z) <= 1e300)) bad = true;
-        pos_r[i] = x;
-        quat[i] = q;
+        st_d4(pos_r + i, x);
+        st_d4(quat + i, q);
     }
     if (bad) atomicOr(&info->err, kErrNaN);
 }

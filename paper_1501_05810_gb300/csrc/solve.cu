@@ -90,41 +90,6 @@ template <class R> struct Bodies {
     R4<R> va, wa, vb, wb;
 };
 
-// 256-bit global accesses: a body's (v, 1/m) and (w, 1/I) pair and an FP32
-// sweep record each move as one request instead of two (FP64: two instead
-// of four).  The body accesses keep their order with every other memory
-// access of the thread.
-__device__ __forceinline__ void ld_body(const float4* p, float4& v, float4& w)
-{
-    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w), "=f"(w.x), "=f"(w.y), "=f"(w.z), "=f"(w.w)
-                 : "l"(p)
-                 : "memory");
-}
-__device__ __forceinline__ void ld_body(const double4_32a* p, double4_32a& v, double4_32a& w)
-{
-    asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];"
-                 : "=d"(v.x), "=d"(v.y), "=d"(v.z), "=d"(v.w)
-                 : "l"(p)
-                 : "memory");
-    asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];"
-                 : "=d"(w.x), "=d"(w.y), "=d"(w.z), "=d"(w.w)
-                 : "l"(p + 1)
-                 : "memory");
-}
-__device__ __forceinline__ void st_body(float4* p, const float4& v, const float4& w)
-{
-    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
-                 "f"(v.w), "f"(w.x), "f"(w.y), "f"(w.z), "f"(w.w)
-                 : "memory");
-}
-__device__ __forceinline__ void st_body(double4_32a* p, const double4_32a& v, const double4_32a& w)
-{
-    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(v.x), "d"(v.y), "d"(v.z), "d"(v.w)
-                 : "memory");
-    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p + 1), "d"(w.x), "d"(w.y), "d"(w.z), "d"(w.w)
-                 : "memory");
-}
 // Sweep records do not change during a solve.
 __device__ __forceinline__ SweepRec<float> ld_rec(const SweepRec<float>* p)
 {
