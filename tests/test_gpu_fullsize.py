@@ -1,0 +1,124 @@
+"""The benchmark workloads at their full sizes, in the launch configuration the
+benchmark times, checked where the oracle cannot follow them whole:
+properties that hold at any size, and outputs recomputed one by one.
+
+- Dense 1M packing (HCP 100^3, FP32 sweeps, 100 sweeps): the contact count
+  is n_x n_y (6 n_z - 1); no colour holds two contacts of one body; every
+  impulse lies in its friction cone with p_n >= 0; the gap and normal of
+  sampled contacts equal their FP64 definition recomputed here (same
+  operation order, so bit for bit).
+- 4,096-scene batch: no contact joins two scenes; every scene's bodies stay
+  in its box.
+- 30M-sphere gas: the contacts found obey the keep rule of Sect. 4,
+  recomputed for a sample, and the contact set of a step is unique."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1501_05810_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1501_05810_gb300 import build
+    build.build()
+    from paper_1501_05810_gb300 import nbgs
+    return nbgs
+
+
+def _check_colouring(c, n):
+    col = c["colour"]
+    assert col.min() >= 0
+    for k in np.unique(col):
+        rows = col == k
+        b = np.concatenate([c["j1"][rows], c["j2"][rows][c["j2"][rows] < n]])
+        assert len(np.unique(b)) == len(b), f"colour {k} touches a body twice"
+
+
+def _check_cone(c, mu, rel=1e-5):
+    p = c["impulse"]
+    scale = max(float(np.abs(p[:, 0]).max()), 1e-300)
+    assert p[:, 0].min() >= -rel * scale
+    assert np.all(np.hypot(p[:, 1], p[:, 2]) <= mu * p[:, 0] + rel * scale)
+
+
+def test_dense_packing_full_size(nb):
+    sc = scenes.dense_packing(1_000_000, seed=0, precision="fp32")
+    g = nb.Scene(sc)
+    b0 = g.get_bodies()
+    st = g.step(100, 1e-6)
+    assert st["n_contacts"] == 100 * 100 * (6 * 100 - 1)
+    c = g.get_contacts()
+    n = len(sc["radius"])
+    _check_colouring(c, n)
+    _check_cone(c, sc["params"]["mu"])
+    # sampled sphere-sphere contacts: the geometry from the start-of-step positions
+    rng = np.random.default_rng(1)
+    ss = np.nonzero(c["j2"] < n)[0]
+    pick = rng.choice(ss, 2000, replace=False)
+    a, b = c["j1"][pick].astype(np.int64), c["j2"][pick].astype(np.int64)
+    lo, hi = np.array(sc["params"]["box_lo"]), np.array(sc["params"]["box_hi"])
+    L = hi - lo
+    d3 = b0["pos"][a] - b0["pos"][b]
+    for k in range(3):
+        if sc["params"]["periodic"][k]:
+            d3[:, k] = np.where(d3[:, k] > 0.5 * L[k], d3[:, k] - L[k],
+                                np.where(d3[:, k] < -0.5 * L[k], d3[:, k] + L[k], d3[:, k]))
+    d = np.sqrt((d3[:, 0] * d3[:, 0] + d3[:, 1] * d3[:, 1]) + d3[:, 2] * d3[:, 2])
+    r = sc["radius"]
+    assert np.array_equal(c["xi"][pick], (d - r[a]) - r[b])
+    assert np.array_equal(c["normal"][pick], d3 / d[:, None])
+
+
+def test_batch_full_size(nb):
+    bs = scenes.batch_scenes(4096, seed=0, precision="fp32", contacts_per_body=4)
+    g = nb.BatchScene(bs)
+    for _ in range(3):
+        g.step(100, 1e-6)
+    c = g.get_contacts()
+    off = g.offsets
+    scene_of = np.repeat(np.arange(len(bs)), np.diff(off))
+    n = int(off[-1])
+    ss = c["j2"] < n
+    assert np.array_equal(scene_of[c["j1"][ss]], scene_of[c["j2"][ss]])
+    pos = g.get_bodies()["pos"]
+    lo = np.repeat(np.array([s["params"]["box_lo"] for s in bs]), np.diff(off), axis=0)
+    hi = np.repeat(np.array([s["params"]["box_hi"] for s in bs]), np.diff(off), axis=0)
+    assert np.all(pos >= lo - 0.1) and np.all(pos <= hi + 0.1)
+    _check_colouring(c, n)
+
+
+def test_gas_full_size_keep_rule(nb):
+    sc = scenes.granular_gas(cells=196, seed=0, precision="fp32", contacts_per_body=2)
+    g = nb.Scene(sc)
+    n = len(sc["radius"])
+    dt, tau = sc["params"]["dt"], sc["params"]["tau"]
+    for _ in range(200):   # the gas starts without contacts; its first collisions by then
+        g.step(50, 0.0, stats=False)
+    b0 = g.get_bodies()
+    nc = g.detect_contacts()
+    assert nc > 0
+    c = g.get_contacts()
+    key = (c["j1"].astype(np.int64) << 32) | c["j2"].astype(np.int64)
+    assert np.all(np.diff(key) > 0)                      # canonical order, no duplicates
+    # the velocities are FP32 in the scene: the hull of Sect. 4 from them
+    v = b0["vel"].astype(np.float32).astype(np.float64)
+    w = b0["angvel"].astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(2)
+    pick = rng.choice(len(key), min(5000, len(key)), replace=False)
+    a, b = c["j1"][pick].astype(np.int64), c["j2"][pick].astype(np.int64)
+    r = sc["radius"]
+    h = lambda i: dt * (np.sqrt((v[i, 0] ** 2 + v[i, 1] ** 2) + v[i, 2] ** 2)
+                        + np.sqrt((w[i, 0] ** 2 + w[i, 1] ** 2) + w[i, 2] ** 2) * r[i]) + tau
+    L = np.array(sc["params"]["box_hi"]) - np.array(sc["params"]["box_lo"])
+    d3 = b0["pos"][a] - b0["pos"][b]
+    d3 = np.where(d3 > 0.5 * L, d3 - L, np.where(d3 < -0.5 * L, d3 + L, d3))
+    d = np.sqrt((d3[:, 0] ** 2 + d3[:, 1] ** 2) + d3[:, 2] ** 2)
+    slack = 1e-12 * np.max(L)
+    assert np.all((d - r[a]) - r[b] <= h(a) + h(b) + slack)
