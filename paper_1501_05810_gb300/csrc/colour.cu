@@ -421,37 +421,41 @@ __global__ void k_build_sweep(int64_t C, int64_t n, const uint32_t* __restrict__
             r.nz_ = make_double2(g.z, 0.0);
         }
         rec[s] = r;
-        double pn = 0.0, pt = 0.0, po = 0.0, found = 0.0;
+        // the previous world impulse in the new contact frame, projected onto
+        // the friction cone; in the sweep precision (FP64 arithmetic is scarce
+        // on this GPU, and an FP32 sweep starts from an FP32 impulse anyway)
+        R pn = R(0), pt = R(0), po = R(0), found = R(0);
         if (warm) {
             const uint32_t e = prev_row_off[a + 1];
             for (uint32_t t = prev_row_off[a]; t < e; ++t) {
                 if (prev_j2[t] != b) continue;
                 const double4_32a P = prev_P[t];
-                const double mu = V.batch ? V.mu[V.scene_of[a]] : mu_all;
-                found = 1.0;
-                double tx, ty, tz, ox, oy, oz;
-                tangent_basis<double>(g.x, g.y, g.z, tx, ty, tz, ox, oy, oz);
-                pn = g.x * P.x + g.y * P.y + g.z * P.z;
-                if (!(pn > 0.0)) pn = 0.0;
-                pt = tx * P.x + ty * P.y + tz * P.z;
-                po = ox * P.x + oy * P.y + oz * P.z;
-                const double lim = mu * pn, len = sqrt(pt * pt + po * po);
+                const R mu = (R)(V.batch ? V.mu[V.scene_of[a]] : mu_all);
+                const R nx = (R)g.x, ny = (R)g.y, nz = (R)g.z, Px = (R)P.x, Py = (R)P.y, Pz = (R)P.z;
+                found = R(1);
+                R tx, ty, tz, ox, oy, oz;
+                tangent_basis<R>(nx, ny, nz, tx, ty, tz, ox, oy, oz);
+                pn = nx * Px + ny * Py + nz * Pz;
+                if (!(pn > R(0))) pn = R(0);
+                pt = tx * Px + ty * Py + tz * Pz;
+                po = ox * Px + oy * Py + oz * Pz;
+                const R lim = mu * pn, len = sqrt(pt * pt + po * po);
                 if (len > lim) {
-                    if (len > 0.0) {
+                    if (len > R(0)) {
                         pt *= lim / len;
                         po *= lim / len;
                     } else {
-                        pt = po = 0.0;
+                        pt = po = R(0);
                     }
                 }
                 break;
             }
         }
         R4<R> q;
-        q.x = (R)pn;
-        q.y = (R)pt;
-        q.z = (R)po;
-        q.w = (R)found;   // 1: the contact existed in the previous step (read by the network warm start)
+        q.x = pn;
+        q.y = pt;
+        q.z = po;
+        q.w = found;   // 1: the contact existed in the previous step (read by the network warm start)
         p[s] = q;
     }
 }
