@@ -58,10 +58,11 @@ def workload(name: str):
                     "30 deg, mu=0.85, v0=0.1 downhill, omega=0.75, dt=1e-5, 100 sweeps, previous-step warm start, "
                     "FP32 sweeps")
     if name == "batch":
-        bs = scenes.batch_scenes(4096, seed=0, precision="fp32", contacts_per_body=4)
+        bs = scenes.batch_scenes(4096, seed=0, precision="fp32", contacts_per_body=4, warm_start="prev")
         return bs, (f"4,096 walled-box scenes, {sum(len(b['radius']) for b in bs):,} spheres in total, sizes "
                     "log-uniform in [200, 20000], r~U(0.4,0.6), mu~U(0.2,0.8), settling under gravity, dt=5e-4, "
-                    "residual 1e-6 per scene (max 100 sweeps), one persistent sweep launch for all scenes")
+                    "residual 1e-6 per scene (max 100 sweeps), previous-step warm start, one persistent sweep launch "
+                    "for all scenes")
     if name == "hopper":
         sc = scenes.hopper(2_000_000, seed=0, precision="fp32", warm_start="prev")
         return sc, ("conical hopper discharge: 2,000,000 spheres r~U(0.4,0.6), 30 deg half-angle, orifice 8 r_mean, "
