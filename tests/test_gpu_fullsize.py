@@ -10,7 +10,9 @@ properties that hold at any size, and outputs recomputed one by one.
 - 4,096-scene batch: no contact joins two scenes; every scene's bodies stay
   in its box.
 - 30M-sphere gas: the contacts found obey the keep rule of Sect. 4,
-  recomputed for a sample, and the contact set of a step is unique."""
+  recomputed for a sample, and the contact set of a step is unique.
+- Dense packing and settled 2M hopper: FP32 sweeps against FP64 sweeps from
+  the same state, impulses and velocities within 1e-2 of the largest."""
 import math
 
 import numpy as np
@@ -122,3 +124,47 @@ def test_gas_full_size_keep_rule(nb):
     d = np.sqrt((d3[:, 0] ** 2 + d3[:, 1] ** 2) + d3[:, 2] ** 2)
     slack = 1e-12 * np.max(L)
     assert np.all((d - r[a]) - r[b] <= h(a) + h(b) + slack)
+
+
+@pytest.mark.parametrize("workload", ["dense", "hopper"])
+def test_fp32_sweeps_against_fp64_at_full_size(nb, workload):
+    """The error of FP32 sweeps (FP64 positions) against FP64 sweeps on the
+    same state at full size (the hopper after its 2,000 settling steps of 30
+    sweeps), after one step of 100 sweeps: FP64 sweeps match the oracle to
+    1e-10 at every size the oracle can run, so this is the FP32 error
+    against the FP64 reference for the configuration."""
+    if workload == "dense":
+        sc = scenes.dense_packing(1_000_000, seed=0)
+        pre = 0
+    else:
+        sc = scenes.hopper(2_000_000, seed=0, warm_start="prev")
+        pre = 2000   # the settled state the hopper discharge is measured on
+    out = {}
+    state = None
+    for prec in ("fp64", "fp32"):
+        s = dict(sc, params=dict(sc["params"], precision=prec))
+        g = nb.Scene(s)
+        if state is None:
+            for _ in range(pre):   # bring the hopper into contact (FP64 once, then shared)
+                g.step(30, 0.0, stats=False)
+            state = g.get_bodies()
+        else:
+            g.set_bodies(state["pos"], state["quat"], state["vel"], state["angvel"])
+        if pre:
+            g.set_bodies(state["pos"], state["quat"], state["vel"], state["angvel"])
+        g.step(100, 0.0)
+        out[prec] = (g.get_bodies(), g.get_contacts())
+        g.close()
+    (b64, c64), (b32, c32) = out["fp64"], out["fp32"]
+    # the FP32 scene holds FP32 velocities, so its hulls differ in the last
+    # bits: compare the contacts both found (a borderline pair may differ)
+    k64 = (c64["j1"].astype(np.int64) << 32) | c64["j2"]
+    k32 = (c32["j1"].astype(np.int64) << 32) | c32["j2"]
+    common, i64, i32 = np.intersect1d(k64, k32, assume_unique=True, return_indices=True)
+    assert len(k64) > (300_000 if pre else 5_000_000)   # the hopper: ~478k contacts after 1 s
+    assert len(common) >= (1.0 - 1e-5) * max(len(k64), len(k32))
+    ep = np.abs(c32["impulse"][i32] - c64["impulse"][i64]).max() / np.abs(c64["impulse"]).max()
+    ev = np.abs(b32["vel"] - b64["vel"]).max() / max(np.abs(b64["vel"]).max(), 1e-300)
+    print(f"{workload}: {len(c64['j1'])} contacts, FP32 vs FP64 after 100 sweeps: impulses {ep:.2e}, "
+          f"velocities {ev:.2e} (relative to the largest)")
+    assert ep < 1e-2 and ev < 1e-2
