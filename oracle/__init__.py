@@ -27,6 +27,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 WARM_NONE = 0
 WARM_PREV = 1
+SUB_NONE, SUB_GRID, SUB_JACOBI = 0, 1, 2
 
 
 class OracleParams(C.Structure):
@@ -42,6 +43,8 @@ class OracleParams(C.Structure):
         ("periodic", C.c_int32 * 3),
         ("warm_start", C.c_int32),
         ("colour_seed", C.c_uint64),
+        ("subdomain_mode", C.c_int32),
+        ("subdomains", C.c_int32 * 3),
     ]
 
 
@@ -105,6 +108,7 @@ def lib():
         L.oracle_get_contacts.argtypes = [C.c_void_p, C.c_int64, P(C.c_uint32), P(C.c_uint32),
                                           P(C.c_int32), dp, dp, dp, P(C.c_int64)]
         L.oracle_set_impulses.argtypes = [C.c_void_p, dp]
+        L.oracle_contact_subdomains.argtypes = [C.c_void_p, P(C.c_int64)]
         L.oracle_residual_history.argtypes = [C.c_void_p, dp, C.c_int32, P(C.c_int32)]
         L.oracle_final_residuals.argtypes = [C.c_void_p, P(OracleResiduals)]
         L.oracle_contact_frame.argtypes = [dp, dp, dp]
@@ -148,6 +152,14 @@ def make_params(p: dict) -> OracleParams:
     o.periodic[:] = [int(b) for b in p.get("periodic", (0, 0, 0))]
     o.warm_start = WARM_PREV if p.get("warm_start", "none") == "prev" else WARM_NONE
     o.colour_seed = int(p.get("colour_seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    sub = p.get("subdomains")
+    if sub is None:
+        o.subdomain_mode = SUB_NONE
+    elif isinstance(sub, str) and sub == "jacobi":
+        o.subdomain_mode = SUB_JACOBI
+    else:
+        o.subdomain_mode = SUB_GRID
+        o.subdomains[:] = [int(g) for g in sub]
     return o
 
 
@@ -255,6 +267,14 @@ class OracleScene:
                                      col.ctypes.data_as(C.POINTER(C.c_int32)), _dp(nrm), _dp(xi),
                                      _dp(imp), C.byref(n)), "get_contacts")
         return {"j1": j1, "j2": j2, "colour": col, "normal": nrm, "xi": xi, "impulse": imp}
+
+    def contact_subdomains(self) -> np.ndarray:
+        """Subdomain s_c(j) of every contact (canonical order)."""
+        m = len(self.get_contacts()["j1"])
+        out = np.zeros(m, np.int64)
+        _check(lib().oracle_contact_subdomains(self._h, out.ctypes.data_as(C.POINTER(C.c_int64))),
+               "contact_subdomains")
+        return out
 
     def set_impulses(self, imp):
         a = _f64(imp)

@@ -146,6 +146,10 @@ int oracle_create_scene(const oracle_params* prm, int64_t n,
 {
     if (!prm || !out || n < 0 || (n > 0 && (!pos || !vel || !angvel || !radius || !density))) return 1;
     if (!(prm->dt > 0.0)) return 1;
+    if (prm->subdomain_mode < ORACLE_SUB_NONE || prm->subdomain_mode > ORACLE_SUB_JACOBI) return 1;
+    if (prm->subdomain_mode == ORACLE_SUB_GRID)
+        for (int a = 0; a < 3; ++a)
+            if (prm->subdomains[a] < 1 || !(prm->box_hi[a] > prm->box_lo[a])) return 1;
     oracle_scene* s = (oracle_scene*)calloc(1, sizeof(oracle_scene));
     if (!s) return 2;
     s->prm = *prm;
@@ -439,6 +443,16 @@ int oracle_colour_contacts(oracle_scene* s, int32_t* n_colours)
 {
     if (!s) return 1;
     const int64_t nc = s->nc, n = s->n;
+    if (s->prm.subdomain_mode == ORACLE_SUB_JACOBI) {
+        /* Non-linear block Jacobi: every contact is a subdomain of its own,
+         * so within a sweep each one sees only the previous sweep's
+         * reactions and the order cannot matter: a single colour. */
+        for (int64_t c = 0; c < nc; ++c) s->colour[c] = 0;
+        s->ncolours = nc > 0 ? 1 : 0;
+        s->coloured = 1;
+        if (n_colours) *n_colours = s->ncolours;
+        return 0;
+    }
     int64_t* deg = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
     prio_item* items = (prio_item*)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(prio_item));
     if (!deg || !items) { free(deg); free(items); return 2; }
@@ -595,6 +609,80 @@ static int64_t find_prev(const oracle_scene* s, uint64_t key)
     return (lo < s->nprev && s->prev_key[lo] == key) ? lo : -1;
 }
 
+/* Subdomain s_c(j) of contact c (Alg. 1).  Sect. 6.2 lets any rule that
+ * partitions the contact set decide which process treats a contact and
+ * recommends favouring the particles' parent processes: with a regular grid
+ * of g0 x g1 x g2 subdomains over the box, contact c belongs to the
+ * subdomain holding the centre of its body j1 (cell k_a = floor((x_a - lo_a)
+ * g_a / L_a), clamped to [0, g_a - 1]; id = (k_2 g_1 + k_1) g_0 + k_0).
+ * Non-linear block Jacobi: every contact its own subdomain. */
+static int64_t contact_subdomain(const oracle_scene* s, int64_t c)
+{
+    if (s->prm.subdomain_mode == ORACLE_SUB_JACOBI) return c;
+    if (s->prm.subdomain_mode != ORACLE_SUB_GRID) return 0;
+    const double* x = &s->x[3 * (int64_t)s->j1[c]];
+    int64_t id = 0;
+    for (int a = 2; a >= 0; --a) {
+        const int32_t g = s->prm.subdomains[a];
+        const double L = s->prm.box_hi[a] - s->prm.box_lo[a];
+        double k = floor(((x[a] - s->prm.box_lo[a]) * (double)g) / L);
+        if (!(k >= 0.0)) k = 0.0;
+        if (k > (double)(g - 1)) k = (double)(g - 1);
+        id = id * g + (int64_t)k;
+    }
+    return id;
+}
+
+int oracle_contact_subdomains(const oracle_scene* s, int64_t* out)
+{
+    if (!s || (s->nc > 0 && !out)) return 1;
+    for (int64_t c = 0; c < s->nc; ++c) out[c] = contact_subdomain(s, c);
+    return 0;
+}
+
+/* Correction variables of Sect. 6.3 in the velocity form: one slot per pair
+ * (finite body i, subdomain p) that some contact of p touches, holding
+ * (delta v_i^[p], delta w_i^[p]).  Slots of one body are consecutive, in
+ * increasing subdomain order. */
+typedef struct { int64_t body, sub, end; } slot_item;
+
+static int cmp_slot(const void* pa, const void* pb)
+{
+    const slot_item* a = (const slot_item*)pa;
+    const slot_item* b = (const slot_item*)pb;
+    if (a->body != b->body) return a->body < b->body ? -1 : 1;
+    if (a->sub != b->sub) return a->sub < b->sub ? -1 : 1;
+    return a->end < b->end ? -1 : (a->end > b->end ? 1 : 0);
+}
+
+/* slot_of[2 c + e] = correction slot of end e (0: j1, 1: j2) of contact c,
+ * -1 for an end without a finite body; slot_body[k] = body of slot k. */
+static int build_slots(const oracle_scene* s, const contact_k* K, int64_t* slot_of, int64_t** slot_body,
+                       int64_t* nslot)
+{
+    const int64_t nc = s->nc;
+    slot_item* it = (slot_item*)malloc((size_t)(2 * nc > 0 ? 2 * nc : 1) * sizeof(slot_item));
+    int64_t* sb = (int64_t*)malloc((size_t)(2 * nc > 0 ? 2 * nc : 1) * sizeof(int64_t));
+    if (!it || !sb) { free(it); free(sb); return 2; }
+    int64_t m = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+        const int64_t sub = contact_subdomain(s, c);
+        slot_of[2 * c] = slot_of[2 * c + 1] = -1;
+        if (K[c].fa) { it[m].body = K[c].a; it[m].sub = sub; it[m].end = 2 * c; ++m; }
+        if (K[c].fb) { it[m].body = K[c].b; it[m].sub = sub; it[m].end = 2 * c + 1; ++m; }
+    }
+    qsort(it, (size_t)m, sizeof(slot_item), cmp_slot);
+    int64_t k = -1;
+    for (int64_t i = 0; i < m; ++i) {
+        if (i == 0 || it[i].body != it[i - 1].body || it[i].sub != it[i - 1].sub) sb[++k] = it[i].body;
+        slot_of[it[i].end] = k;
+    }
+    free(it);
+    *slot_body = sb;
+    *nslot = k + 1;
+    return 0;
+}
+
 int oracle_solve_nbgs(oracle_scene* s, int32_t max_sweeps, double tol,
                       int32_t* sweeps_done, double* residual)
 {
@@ -661,10 +749,112 @@ int oracle_solve_nbgs(oracle_scene* s, int32_t max_sweeps, double tol,
         apply_impulse(s, k, Pw);
     }
 
+    /* Subdomains (Alg. 1 in general): the velocity of body i seen by a
+     * contact of subdomain p is the accumulator v_i (all reactions of the
+     * previous sweep) plus the correction delta v_i^[p] of the contacts of p
+     * already relaxed in this sweep (Sect. 6.3).  After the sweep every
+     * accumulator takes the sum of its corrections. */
+    const int sub = P->subdomain_mode != ORACLE_SUB_NONE;
+    int64_t* slot_of = NULL;
+    int64_t* slot_body = NULL;
+    int64_t nslot = 0;
+    double *dv = NULL, *dw = NULL;
+    if (sub) {
+        slot_of = (int64_t*)malloc((size_t)(2 * nc > 0 ? 2 * nc : 1) * sizeof(int64_t));
+        int rc = slot_of ? build_slots(s, K, slot_of, &slot_body, &nslot) : 2;
+        if (rc == 0) {
+            dv = (double*)calloc(3 * (size_t)(nslot > 0 ? nslot : 1), sizeof(double));
+            dw = (double*)calloc(3 * (size_t)(nslot > 0 ? nslot : 1), sizeof(double));
+        }
+        if (rc != 0 || !dv || !dw) {
+            free(slot_of); free(slot_body); free(dv); free(dw); free(K); free(ord);
+            return 2;
+        }
+    }
+
     s->nhist = 0;
     int32_t k_done = 0;
     double Rk = 0.0;
-    for (int32_t sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int32_t sweep = 0; sweep < max_sweeps && sub; ++sweep) {
+        double rmax = 0.0;
+        for (int64_t i = 0; i < 3 * nslot; ++i) dv[i] = dw[i] = 0.0;
+        for (int64_t it = 0; it < nc; ++it) {
+            int64_t c = ord[it].idx;
+            const contact_k* k = &K[c];
+            if (!(k->w_n > 0.0)) continue;
+            double* p = &s->p[3 * c];
+            const int64_t sa = slot_of[2 * c], sb = slot_of[2 * c + 1];
+            /* velocities seen by this contact: accumulator + its subdomain's correction */
+            double va[3] = { 0, 0, 0 }, wa[3] = { 0, 0, 0 }, vb[3] = { 0, 0, 0 }, wb[3] = { 0, 0, 0 };
+            for (int e = 0; e < 3; ++e) {
+                if (sa >= 0) {
+                    va[e] = s->v[3 * k->a + e] + dv[3 * sa + e];
+                    wa[e] = s->w[3 * k->a + e] + dw[3 * sa + e];
+                }
+                if (sb >= 0) {
+                    vb[e] = s->v[3 * k->b + e] + dv[3 * sb + e];
+                    wb[e] = s->w[3 * k->b + e] + dw[3 * sb + e];
+                }
+            }
+            double la3[3] = { -k->la * k->n[0], -k->la * k->n[1], -k->la * k->n[2] };
+            double lb3[3] = { k->lb * k->n[0], k->lb * k->n[1], k->lb * k->n[2] };
+            double ca[3], cb[3], u[3];
+            cross3(wa, la3, ca);
+            cross3(wb, lb3, cb);
+            for (int e = 0; e < 3; ++e) u[e] = (va[e] + ca[e]) - (vb[e] + cb[e]);
+            double b[3];
+            b[0] = (dot3(k->n, u) - k->w_n * p[0]) + k->bias;
+            b[1] = dot3(k->t, u) - k->w_t * p[1];
+            b[2] = dot3(k->o, u) - k->w_t * p[2];
+            double y[3];
+            oracle_one_contact(k->w_n, k->w_t, P->mu, b, y);
+            double pnew[3], dp[3];
+            for (int e = 0; e < 3; ++e) {
+                pnew[e] = P->omega * y[e] + (1.0 - P->omega) * p[e];
+                dp[e] = pnew[e] - p[e];
+            }
+            double Pw[3];
+            for (int e = 0; e < 3; ++e) Pw[e] = dp[0] * k->n[e] + dp[1] * k->t[e] + dp[2] * k->o[e];
+            /* Sect. 6.3: the corrections of subdomain s_c(j) take the change
+             * of reaction j (+ on j1, - on j2) */
+            double ta[3], tb[3];
+            cross3(la3, Pw, ta);
+            cross3(lb3, Pw, tb);
+            for (int e = 0; e < 3; ++e) {
+                if (sa >= 0) {
+                    dv[3 * sa + e] += s->invm[k->a] * Pw[e];
+                    dw[3 * sa + e] += s->invI[k->a] * ta[e];
+                }
+                if (sb >= 0) {
+                    dv[3 * sb + e] -= s->invm[k->b] * Pw[e];
+                    dw[3 * sb + e] -= s->invI[k->b] * tb[e];
+                }
+            }
+            for (int e = 0; e < 3; ++e) p[e] = pnew[e];
+            double r1 = k->w_n * dp[0], r2 = k->w_t * dp[1], r3 = k->w_t * dp[2];
+            double rj = sqrt((r1 * r1 + r2 * r2) + r3 * r3);
+            if (rj > rmax) rmax = rj;
+        }
+        /* end of the sweep: accumulators += corrections, in increasing
+         * subdomain order per body; the corrections restart from zero */
+        for (int64_t q = 0; q < nslot; ++q)
+            for (int e = 0; e < 3; ++e) {
+                s->v[3 * slot_body[q] + e] += dv[3 * q + e];
+                s->w[3 * slot_body[q] + e] += dw[3 * q + e];
+            }
+        Rk = rmax / s->v_ref;
+        if (s->nhist == s->cap_hist) {
+            double* hh = (double*)realloc(s->hist, 2 * (size_t)s->cap_hist * sizeof(double));
+            if (!hh) { free(slot_of); free(slot_body); free(dv); free(dw); free(K); free(ord); return 2; }
+            s->hist = hh;
+            s->cap_hist *= 2;
+        }
+        s->hist[s->nhist++] = Rk;
+        k_done = sweep + 1;
+        if (tol > 0.0 && Rk <= tol) break;
+    }
+    free(slot_of); free(slot_body); free(dv); free(dw);
+    for (int32_t sweep = 0; sweep < max_sweeps && !sub; ++sweep) {
         double rmax = 0.0;
         for (int64_t it = 0; it < nc; ++it) {
             int64_t c = ord[it].idx;

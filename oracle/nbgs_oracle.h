@@ -10,8 +10,10 @@
  *
  * Everything is double precision, single-threaded and written for
  * readability: O(N^2) brute-force contact detection, a sequential greedy
- * colouring, and the nonlinear block Gauss-Seidel (NBGS) of Alg. 1 with a
- * single subdomain, run contact by contact in colour order.
+ * colouring, and the nonlinear block Gauss-Seidel (NBGS) of Alg. 1, run
+ * contact by contact in colour order: with a single subdomain (classic
+ * NBGS), with subdomains on a grid, or with one subdomain per contact
+ * (non-linear block Jacobi).
  *
  * Passages followed (section / equation / algorithm of the paper):
  *   Sect. 2, eq. (wrench) and the Q(phi) block  - wrench and quaternion rate
@@ -20,7 +22,9 @@
  *   Sect. 3, eq. (nonpenetration), eq. (coulomb)- one-contact constraints
  *   Sect. 4, eq. (expansionradius)              - intersection hulls
  *   Sect. 5, Alg. 1                             - subdomain NBGS, relaxation
- *   Sect. 6.3 (velocity accumulators)           - in-place velocity updates
+ *   Sect. 6.2 (contact treatment rule)          - subdomain of a contact
+ *   Sect. 6.3 (velocity accumulators and        - in-place velocity updates;
+ *              corrections)                       per-subdomain corrections
  *   Sect. 6.6, Alg. 2                           - order of one time step
  *
  * Return codes: 0 = ok, 1 = invalid argument, 2 = out of memory.
@@ -40,6 +44,10 @@ extern "C" {
 #define ORACLE_MAX_CONES 4
 
 enum { ORACLE_WARM_NONE = 0, ORACLE_WARM_PREV = 1 };
+/* Subdomains s_c(j) of Alg. 1: none (one subdomain: classic NBGS), a regular
+ * grid over the box (a contact belongs to the subdomain holding the centre
+ * of its body j1), or one subdomain per contact (non-linear block Jacobi). */
+enum { ORACLE_SUB_NONE = 0, ORACLE_SUB_GRID = 1, ORACLE_SUB_JACOBI = 2 };
 
 typedef struct oracle_params {
     double dt;          /* time step */
@@ -53,6 +61,8 @@ typedef struct oracle_params {
     int32_t periodic[3];
     int32_t warm_start; /* ORACLE_WARM_NONE or ORACLE_WARM_PREV */
     uint64_t colour_seed;
+    int32_t subdomain_mode; /* ORACLE_SUB_* */
+    int32_t subdomains[3];  /* grid of ORACLE_SUB_GRID, each >= 1 */
 } oracle_params;
 
 typedef struct oracle_step_stats {
@@ -106,6 +116,11 @@ int  oracle_solve_nbgs(oracle_scene* s, int32_t max_sweeps, double tol,
                        int32_t* sweeps_done, double* residual);
 int  oracle_integrate(oracle_scene* s);
 int  oracle_step(oracle_scene* s, int32_t max_sweeps, double tol, oracle_step_stats* st);
+
+/* Subdomain s_c(j) of every contact (canonical order) under the scene's
+ * subdomain mode, from the current positions; 0 for every contact when
+ * there are no subdomains. */
+int  oracle_contact_subdomains(const oracle_scene* s, int64_t* out);
 
 /* Contacts in canonical order (ascending (j1 << 32) | j2).  Any output
  * pointer may be NULL.  impulse = (p_n, p_t, p_o) in the contact frame. */

@@ -582,3 +582,177 @@ def test_hopper_contacts_have_cone_walls(oracle_mod):
     p = o.get_bodies()["pos"][c["j1"][rows]]
     assert np.all(np.sum(nrm[:, :2] * p[:, :2], axis=1) < 0.0)
     assert np.all(c["impulse"][rows, 0] >= 0.0) and np.any(c["impulse"][rows, 0] > 0.0)
+
+
+# ---------------------------------------------------------------------------
+# subdomain NBGS and non-linear block Jacobi (Alg. 1 with s_c(j), Sect. 6.3)
+# ---------------------------------------------------------------------------
+def _grid_subdomain(pos, lo, hi, g):
+    """Subdomain of a point on a regular g0 x g1 x g2 grid over [lo, hi]."""
+    k = np.floor((pos - lo) * np.asarray(g, float) / (hi - lo))
+    k = np.clip(k, 0, np.asarray(g) - 1).astype(np.int64)
+    return (k[:, 2] * g[1] + k[:, 1]) * g[0] + k[:, 0]
+
+
+def _alg1_literal(oracle_mod, sc, sub, omega, sweeps):
+    """Alg. 1 as printed, by brute force: before relaxing contact j, rebuild
+    every body velocity from scratch out of the approximations lambda~(k,j)
+    -- the new reaction of an earlier contact of the same subdomain, the
+    previous one of every other contact -- leaving out contact j itself
+    (F_j^{-1}(0, lambda~ of the others)).  Cold start, contact order:
+    colours ascending, canonical inside.  Returns the impulses and the body
+    velocities after `sweeps` sweeps."""
+    o = oracle_mod.OracleScene(sc)
+    o.detect_contacts()
+    o.colour_contacts()
+    c = o.get_contacts()
+    b0 = o.get_bodies()
+    n = len(sc["radius"])
+    prm = sc["params"]
+    m, I = _mass(sc)
+    invm, invI = 1.0 / m, 1.0 / I
+    dt, mu = prm["dt"], prm["mu"]
+    v0 = b0["vel"] + dt * np.asarray(prm["gravity"])   # eq. integrationscheme, no reactions yet
+    w0 = b0["angvel"]
+    j1, j2 = c["j1"].astype(np.int64), c["j2"].astype(np.int64)
+    C = len(j1)
+    nrm = c["normal"]
+    frames = [oracle_mod.contact_frame(nrm[j]) for j in range(C)]
+    T = np.array([[nrm[j], frames[j][0], frames[j][1]] for j in range(C)])   # rows n, t, o
+    r = sc["radius"]
+    la = c["xi"] + r[j1]                                   # l_a = -la n
+    lb = np.where(j2 < n, r[np.minimum(j2, n - 1)], 0.0)   # l_b = lb n
+    dyn_b = j2 < n
+    xi = c["xi"]
+    bias = np.where(xi >= 0, xi, prm.get("beta", 1.0) * xi) / dt
+    wn = invm[j1] + np.where(dyn_b, invm[np.minimum(j2, n - 1)], 0.0)
+    wt = wn + invI[j1] * la ** 2 + np.where(dyn_b, invI[np.minimum(j2, n - 1)] * lb ** 2, 0.0)
+    order = np.lexsort((np.arange(C), c["colour"]))
+    rank = np.empty(C, np.int64)
+    rank[order] = np.arange(C)
+
+    def velocities(pc, skip=-1):
+        P = np.einsum("ck,ckd->cd", pc, T)                 # world impulses
+        if skip >= 0:
+            P[skip] = 0.0
+        v, w = v0.copy(), w0.copy()
+        np.add.at(v, j1, invm[j1, None] * P)
+        np.add.at(w, j1, invI[j1, None] * np.cross(-la[:, None] * nrm, P))
+        jb = j2[dyn_b]
+        np.add.at(v, jb, -invm[jb, None] * P[dyn_b])
+        np.add.at(w, jb, -invI[jb, None] * np.cross(lb[dyn_b, None] * nrm[dyn_b], P[dyn_b]))
+        return v, w
+
+    p_k = np.zeros((C, 3))
+    for _ in range(sweeps):
+        p_next = p_k.copy()
+        for j in order:
+            new = (sub == sub[j]) & (rank < rank[j])
+            approx = np.where(new[:, None], p_next, p_k)
+            v, w = velocities(approx, skip=j)
+            a, bb = j1[j], j2[j]
+            u = v[a] + np.cross(w[a], -la[j] * nrm[j])
+            if dyn_b[j]:
+                u = u - (v[bb] + np.cross(w[bb], lb[j] * nrm[j]))
+            bvec = T[j] @ u + np.array([bias[j], 0.0, 0.0])
+            y = oracle_mod.one_contact(wn[j], wt[j], mu, bvec)
+            p_next[j] = omega * np.asarray(y) + (1.0 - omega) * p_k[j]
+        p_k = p_next
+    v, w = velocities(p_k)
+    return p_k, v, w
+
+
+@pytest.mark.parametrize("sub,omega", [((2, 2, 1), 1.0), ((1, 2, 2), 0.75), ("jacobi", 0.5), ("jacobi", 1.0)])
+def test_subdomain_nbgs_matches_alg1_literal(oracle_mod, sub, omega):
+    sc = scenes.hcp_packing(4, 4, 3, dt=1e-3, tau=1e-3, mu=0.4, tilt_deg=30.0, v0=0.1, omega=omega,
+                            subdomains=sub)
+    o = oracle_mod.OracleScene(sc)
+    o.detect_contacts()
+    o.colour_contacts()
+    ids = o.contact_subdomains()
+    c = o.get_contacts()
+    prm = sc["params"]
+    if sub == "jacobi":
+        assert np.array_equal(ids, np.arange(len(ids)))
+        assert np.all(c["colour"] == 0)
+    else:
+        pos = o.get_bodies()["pos"]
+        want = _grid_subdomain(pos[c["j1"].astype(np.int64)], np.array(prm["box_lo"]), np.array(prm["box_hi"]), sub)
+        assert np.array_equal(ids, want)
+        assert len(np.unique(ids)) == int(np.prod(sub))
+    sweeps = 4
+    o.solve_nbgs(sweeps)
+    p_ref, v_ref, w_ref = _alg1_literal(oracle_mod, sc, ids, omega, sweeps)
+    p = o.get_contacts()["impulse"]
+    b = o.get_bodies()
+    assert np.abs(p - p_ref).max() <= 1e-12 * np.abs(p_ref).max()
+    assert np.abs(b["vel"] - v_ref).max() <= 1e-12 * np.abs(v_ref).max()
+    assert np.abs(b["angvel"] - w_ref).max() <= 1e-12 * max(np.abs(w_ref).max(), 1e-300)
+
+
+def test_alg1_literal_reproduces_classic_nbgs(oracle_mod):
+    # the brute force itself, with one subdomain, against the classic sweep
+    sc = scenes.hcp_packing(4, 4, 3, dt=1e-3, tau=1e-3, mu=0.4, tilt_deg=30.0, v0=0.1)
+    o = oracle_mod.OracleScene(sc)
+    o.detect_contacts()
+    o.colour_contacts()
+    o.solve_nbgs(3)
+    p_ref, v_ref, _ = _alg1_literal(oracle_mod, sc, np.zeros(len(o.get_contacts()["j1"]), np.int64), 1.0, 3)
+    assert np.abs(o.get_contacts()["impulse"] - p_ref).max() <= 1e-12 * np.abs(p_ref).max()
+    assert np.abs(o.get_bodies()["vel"] - v_ref).max() <= 1e-12 * np.abs(v_ref).max()
+
+
+def test_one_subdomain_is_classic_nbgs(oracle_mod):
+    base = scenes.hcp_packing(4, 4, 3, dt=1e-3, tau=1e-3, mu=0.4, tilt_deg=30.0, v0=0.1, warm_start="prev")
+    one = dict(base, params=dict(base["params"], subdomains=(1, 1, 1)))
+    oa, _ = _run(oracle_mod, base, 5, 30)
+    ob, _ = _run(oracle_mod, one, 5, 30)
+    ca, cb = oa.get_contacts(), ob.get_contacts()
+    assert np.array_equal(ca["colour"], cb["colour"])
+    assert np.abs(ca["impulse"] - cb["impulse"]).max() <= 1e-12 * np.abs(ca["impulse"]).max()
+    va, vb = oa.get_bodies()["vel"], ob.get_bodies()["vel"]
+    assert np.abs(va - vb).max() <= 1e-12 * np.abs(va).max()
+
+
+def test_jacobi_column_converges_to_weights(oracle_mod):
+    # T6 under non-linear block Jacobi: the solution is unique, so damped
+    # Jacobi reaches the same weights as Gauss-Seidel
+    kcol, dt, g = 6, 1e-3, 9.81
+    sc = scenes.column(kcol, dt=dt, subdomains="jacobi", omega=0.5)
+    m = _mass(sc)[0][0]
+    o = oracle_mod.OracleScene(sc)
+    o.detect_contacts()
+    assert o.colour_contacts() == 1
+    k, R = o.solve_nbgs(200000, 1e-13)
+    assert R <= 1e-13
+    c = o.get_contacts()
+    for j1, j2, p in zip(c["j1"], c["j2"], c["impulse"][:, 0]):
+        above = kcol - j1 if j2 == kcol else kcol - j2
+        assert abs(p - above * m * g * dt) < 1e-9 * kcol * m * g * dt
+    # Jacobi needs more sweeps than Gauss-Seidel on the same column
+    gs = oracle_mod.OracleScene(scenes.column(kcol, dt=dt))
+    gs.detect_contacts()
+    k_gs, _ = gs.solve_nbgs(200000, 1e-13)
+    assert k > k_gs
+
+
+@pytest.mark.parametrize("sub", [(2, 2, 2), "jacobi"])
+def test_subdomain_momentum_conserved_without_gravity(oracle_mod, sub):
+    sc = scenes.periodic_cloud(seed=5, per_side=5, periodic=(0, 0, 0), dt=2e-2, subdomains=sub, omega=0.7)
+    o = oracle_mod.OracleScene(sc)
+    P0, L0 = _momenta(sc, o.get_bodies())
+    scaleP = (_mass(sc)[0][:, None] * np.abs(sc["vel"])).sum()
+    total = 0
+    for _ in range(10):
+        st = o.step(20)
+        total += st["n_contacts"]
+        P1, L1 = _momenta(sc, o.get_bodies())
+        assert np.abs(P1 - P0).max() <= 1e-13 * scaleP
+        assert np.abs(L1 - L0).max() <= 1e-12 * scaleP * 10
+    assert total > 100
+
+
+def test_subdomain_parameters_are_checked(oracle_mod):
+    sc = scenes.column(3, subdomains=(2, 0, 1))
+    with pytest.raises(RuntimeError):
+        oracle_mod.OracleScene(sc)
