@@ -75,6 +75,17 @@ enum {                                           /* nbgs_params.sweep_flags bits
                                     warps of a block do not wait for one another (no TMA staging)      */
 };
 
+enum {                                           /* nbgs_params.subdomain_mode: s_c(j) of Alg. 1 */
+    NBGS_SUB_NONE = 0,    /* one subdomain: classic NBGS in colour order                             */
+    NBGS_SUB_GRID = 1,    /* a regular subdomains[0] x [1] x [2] grid over the box; a contact belongs
+                             to the cell holding the centre of its body j1 (Sect. 6.2 lets any rule
+                             that partitions the contacts decide, favouring the particles' parents):
+                             k_a = floor((x_a - lo_a) g_a / (hi_a - lo_a)) clamped to [0, g_a - 1],
+                             id = (k_2 g_1 + k_1) g_0 + k_0                                          */
+    NBGS_SUB_JACOBI = 2   /* every contact its own subdomain: non-linear block Jacobi; the contacts
+                             are not coloured (one colour)                                           */
+};
+
 typedef struct nbgs_allocator {
     void* ctx;
     void* (*alloc)(void* ctx, size_t bytes, void* stream); /* returns NULL on failure */
@@ -97,6 +108,12 @@ typedef struct nbgs_params {
     uint64_t colour_seed; /* priorities of the colouring: splitmix64(key ^ seed)    */
     int32_t contacts_per_body; /* contact buffer capacity per body, 0 = default 8   */
     int32_t sweep_flags;  /* NBGS_SWEEP_*: scheduling details of the persistent solver */
+    int32_t subdomain_mode;  /* NBGS_SUB_*.  With subdomains a contact sees, within a sweep,
+                                the new reactions of the earlier contacts of its own subdomain
+                                only and the previous sweep's of all others (Alg. 1; the
+                                velocity accumulators and corrections of Sect. 6.3).  Single
+                                scenes only (not nbgs_create_batch).                            */
+    int32_t subdomains[3];   /* grid of NBGS_SUB_GRID, each >= 1, product < 2^31                 */
 } nbgs_params;
 
 typedef struct nbgs_step_stats {
@@ -173,14 +190,18 @@ nbgs_status nbgs_detect_contacts(nbgs_scene* scene, int64_t* n_contacts /* nulla
 
 /* Jones-Plassmann colouring of the conflict graph (contacts sharing a body
  * of finite mass) with priorities splitmix64(key ^ colour_seed); equal to
- * sequential first-fit in decreasing priority.  Asynchronous unless
- * n_colours is non-NULL. */
+ * sequential first-fit in decreasing priority.  With NBGS_SUB_JACOBI every
+ * contact takes colour 0.  With subdomains it also assigns s_c(j) and the
+ * velocity instances of the sweep.  Asynchronous unless n_colours is
+ * non-NULL. */
 nbgs_status nbgs_colour_contacts(nbgs_scene* scene, int32_t* n_colours /* nullable */);
 
 /* One NBGS solve (Alg. 1): v += dt g, apply the initial impulses, then up to
  * max_sweeps sweeps over the colours; stop early once R_k <= tol (tol = 0:
- * exactly max_sweeps).  Colours the contacts first if needed.  Asynchronous
- * unless sweeps_done or residual is non-NULL.  Call once per step. */
+ * exactly max_sweeps).  With subdomains each sweep ends by adding every
+ * subdomain's velocity corrections to the bodies (Sect. 6.3).  Colours the
+ * contacts first if needed.  Asynchronous unless sweeps_done or residual is
+ * non-NULL.  Call once per step. */
 nbgs_status nbgs_solve_nbgs(nbgs_scene* scene, int32_t max_sweeps, double tol,
                             int32_t* sweeps_done /* nullable */, double* residual /* nullable */);
 
@@ -303,6 +324,18 @@ nbgs_status nbgs_mlp_adam(float* theta, const float* grad, float* m, float* v, i
 nbgs_status nbgs_get_contacts(nbgs_scene* scene, int64_t cap,
                               uint32_t* j1, uint32_t* j2, int32_t* colour,
                               double* normal, double* xi, double* impulse, int64_t* n_out);
+
+/* Change the subdomains of later solves (NBGS_SUB_*; grid: three counts for
+ * NBGS_SUB_GRID, may be NULL otherwise).  The contacts are coloured again
+ * before the next solve.  NBGS_EINVAL for a bad mode or grid, or for any
+ * subdomains on a batch. */
+nbgs_status nbgs_set_subdomains(nbgs_scene* scene, int32_t mode, const int32_t* grid);
+
+/* Subdomain s_c(j) of every contact of the last colouring, canonical order
+ * (NBGS_SUB_GRID: the grid cell id; NBGS_SUB_JACOBI: the contact's index;
+ * NBGS_SUB_NONE: 0).  out may be NULL; at most cap values are written;
+ * *n_out receives the contact count.  Synchronises. */
+nbgs_status nbgs_get_subdomains(nbgs_scene* scene, int64_t cap, uint32_t* out, int64_t* n_out);
 
 /* Checkpoint and resume.  The paper runs long simulations but says nothing
  * about saving them; these calls cover what a time step reads (Alg. 2):

@@ -43,6 +43,8 @@ struct oracle_scene {
     uint64_t *prev_key;
     double *prev_P;
 
+    int64_t* sub;                  /* s_c(j) the last solve used (NULL: none since the detection) */
+
     double vmax_start;             /* max_i |v_i| at the start of the step */
     double v_ref;
     double *hist;                  /* R_k per sweep */
@@ -136,6 +138,7 @@ void oracle_destroy_scene(oracle_scene* s)
     free(s->colour); free(s->p);
     free(s->prev_key); free(s->prev_P);
     free(s->hist);
+    free(s->sub);
     free(s);
 }
 
@@ -342,6 +345,8 @@ int oracle_detect_contacts(oracle_scene* s, int64_t* n_contacts)
     if (!s) return 1;
     const oracle_params* P = &s->prm;
     const double dt = P->dt;
+    free(s->sub);   /* new contacts: no subdomains assigned yet */
+    s->sub = NULL;
 
     /* eq. (expansionradius): h_i = dt (|v_i| + |omega_i| r_i) + tau, with the
      * velocities at the start of the step; a sphere's bounding radius is r. */
@@ -636,7 +641,9 @@ static int64_t contact_subdomain(const oracle_scene* s, int64_t c)
 int oracle_contact_subdomains(const oracle_scene* s, int64_t* out)
 {
     if (!s || (s->nc > 0 && !out)) return 1;
-    for (int64_t c = 0; c < s->nc; ++c) out[c] = contact_subdomain(s, c);
+    /* after a solve: the subdomains it used (positions at the start of the
+     * step); before: from the current positions */
+    for (int64_t c = 0; c < s->nc; ++c) out[c] = s->sub ? s->sub[c] : contact_subdomain(s, c);
     return 0;
 }
 
@@ -761,7 +768,11 @@ int oracle_solve_nbgs(oracle_scene* s, int32_t max_sweeps, double tol,
     double *dv = NULL, *dw = NULL;
     if (sub) {
         slot_of = (int64_t*)malloc((size_t)(2 * nc > 0 ? 2 * nc : 1) * sizeof(int64_t));
-        int rc = slot_of ? build_slots(s, K, slot_of, &slot_body, &nslot) : 2;
+        free(s->sub);
+        s->sub = (int64_t*)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(int64_t));
+        if (s->sub)
+            for (int64_t c = 0; c < nc; ++c) s->sub[c] = contact_subdomain(s, c);
+        int rc = (slot_of && s->sub) ? build_slots(s, K, slot_of, &slot_body, &nslot) : 2;
         if (rc == 0) {
             dv = (double*)calloc(3 * (size_t)(nslot > 0 ? nslot : 1), sizeof(double));
             dw = (double*)calloc(3 * (size_t)(nslot > 0 ? nslot : 1), sizeof(double));

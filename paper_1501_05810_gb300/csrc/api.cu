@@ -167,6 +167,20 @@ static nbgs_status check_device_errors(nbgs_scene* s)
     return NBGS_OK;
 }
 
+// Subdomain mode and grid (NBGS_SUB_GRID: every count >= 1, ids below 2^31).
+bool subdomains_valid(int32_t mode, const int32_t g[3])
+{
+    if (mode < NBGS_SUB_NONE || mode > NBGS_SUB_JACOBI) return false;
+    if (mode != NBGS_SUB_GRID) return true;
+    int64_t cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (g[a] < 1) return false;
+        cells *= g[a];
+        if (cells >= ((int64_t)1 << 31)) return false;
+    }
+    return true;
+}
+
 }  // namespace nbgs
 
 using namespace nbgs;
@@ -221,6 +235,9 @@ static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_des
     if (params->warm_start < NBGS_WARM_NONE || params->warm_start > NBGS_WARM_MLP) return NBGS_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (!(params->box_hi[a] > params->box_lo[a])) return NBGS_EINVAL;
+    if (!subdomains_valid(params->subdomain_mode, params->subdomains) ||
+        (batch && params->subdomain_mode != NBGS_SUB_NONE))
+        return NBGS_EINVAL;
     *out = nullptr;
     nbgs_scene* s = new (std::nothrow) nbgs_scene();
     if (!s) return NBGS_ENOMEM;
@@ -420,6 +437,7 @@ void nbgs_destroy_scene(nbgs_scene* s)
                   s->scene_done, s->scene_res, s->mlp_theta, s->preds};
     for (void* p : ps) dev_free(s, p);
     free_contact_arrays(s);
+    free_subdomain_buffers(s);
     cudaStreamSynchronize(s->stream);
     if (s->hinfo) cudaFreeHost(s->hinfo);
     for (int k = 0; k < 10; ++k)
@@ -573,6 +591,20 @@ nbgs_status nbgs_set_warm_start(nbgs_scene* s, int32_t warm_start)
     NBGS_GUARD(s);
     if (warm_start < NBGS_WARM_NONE || warm_start > NBGS_WARM_MLP) return fail(s, NBGS_EINVAL, "set_warm_start: mode");
     s->prm.warm_start = warm_start;
+    return NBGS_OK;
+}
+
+nbgs_status nbgs_set_subdomains(nbgs_scene* s, int32_t mode, const int32_t grid[3])
+{
+    NBGS_GUARD(s);
+    const int32_t one[3] = {1, 1, 1};
+    const int32_t* g = grid ? grid : one;
+    if (!subdomains_valid(mode, g) || (mode == NBGS_SUB_GRID && !grid))
+        return fail(s, NBGS_EINVAL, "set_subdomains: bad mode or grid");
+    if (s->batch && mode != NBGS_SUB_NONE) return fail(s, NBGS_EINVAL, "set_subdomains: batched scenes have none");
+    s->prm.subdomain_mode = mode;
+    for (int a = 0; a < 3; ++a) s->prm.subdomains[a] = g[a];
+    s->coloured = false;   // s_c(j), the colours and the sweep records follow the mode
     return NBGS_OK;
 }
 

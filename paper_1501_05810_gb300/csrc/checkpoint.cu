@@ -24,7 +24,7 @@ namespace nbgs {
 namespace {
 
 constexpr char kMagic[8] = {'N', 'B', 'G', 'S', 'C', 'K', 'P', '1'};
-constexpr uint32_t kVersion = 2;
+constexpr uint32_t kVersion = 3;
 constexpr int64_t kMlpParams = 9347;
 
 struct CkptHeader {
@@ -139,7 +139,8 @@ nbgs_status run_load_state(nbgs_scene* s, const char* path)
             (h.prm.periodic[a] != 0) != (s->prm.periodic[a] != 0))
             return fail(s, NBGS_EINVAL, "load_state: the scene has another box");
     if (h.planes.count < 0 || h.planes.count > kMaxPlanes || h.prev_count < 0 || h.prev_count > 0xFFFFFFF0LL ||
-        (h.has_prev && h.prm.warm_start == NBGS_WARM_NONE))
+        (h.has_prev && h.prm.warm_start == NBGS_WARM_NONE) ||
+        !subdomains_valid(h.prm.subdomain_mode, h.prm.subdomains))
         return fail(s, NBGS_EINVAL, "load_state: corrupt header");
     const int64_t n = s->n;
     const size_t vbytes = s->fp32 ? 16 : 32;

@@ -395,7 +395,8 @@ __global__ void k_colour_offsets(const uint32_t* __restrict__ col_count, uint32_
 // or zero.
 template <class R>
 __global__ void k_build_sweep(int64_t C, int64_t n, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cj1,
-                              const uint32_t* __restrict__ cj2, const double4_32a* __restrict__ cgeo,
+                              const uint32_t* __restrict__ cj2, const uint32_t* __restrict__ inst,
+                              const double4_32a* __restrict__ cgeo,
                               const double2* __restrict__ clev, double dt, double beta, double mu_all, SceneView V,
                               int warm,
                               const uint32_t* __restrict__ prev_row_off, const uint32_t* __restrict__ prev_j2,
@@ -405,6 +406,9 @@ __global__ void k_build_sweep(int64_t C, int64_t n, const uint32_t* __restrict__
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < C; s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = perm[s];
         const uint32_t a = cj1[c], b = cj2[c];
+        // the velocity records the sweep reads: the bodies, or with subdomains
+        // their instances for the contact's subdomain
+        const uint32_t ra = inst ? inst[2 * (int64_t)c] : a, rb = inst ? inst[2 * (int64_t)c + 1] : b;
         const double4_32a g = cgeo[c];
         const double2 l = clev[c];
         // eq. (nonpenetration): gap term xi/dt, scaled by beta when xi < 0
@@ -412,10 +416,10 @@ __global__ void k_build_sweep(int64_t C, int64_t n, const uint32_t* __restrict__
         const double bias = xs / dt;
         SweepRec<R> r;
         if constexpr (sizeof(R) == 4) {
-            r.a = make_float4(__uint_as_float(a), __uint_as_float(b), (float)l.x, (float)l.y);
+            r.a = make_float4(__uint_as_float(ra), __uint_as_float(rb), (float)l.x, (float)l.y);
             r.b = make_float4((float)g.x, (float)g.y, (float)g.z, (float)bias);
         } else {
-            r.ids_bias = make_double2(__longlong_as_double((long long)(((uint64_t)b << 32) | a)), bias);
+            r.ids_bias = make_double2(__longlong_as_double((long long)(((uint64_t)rb << 32) | ra)), bias);
             r.lev = make_double2(l.x, l.y);
             r.nxy = make_double2(g.x, g.y);
             r.nz_ = make_double2(g.z, 0.0);
@@ -468,6 +472,9 @@ nbgs_status run_colour(nbgs_scene* s)
     if (s->timing) cudaEventRecord(s->ev[2], st);
     cudaMemsetAsync(s->col_count, 0, (kMaxColours + 1) * sizeof(uint32_t), st);
     cudaMemsetAsync(&s->info->n_colours, 0, sizeof(uint32_t), st);
+    cudaMemsetAsync(&s->info->n_shared, 0, 2 * sizeof(uint32_t), st);   // no shared bodies until assigned
+    const bool sub = s->prm.subdomain_mode != NBGS_SUB_NONE;
+    const bool jacobi = s->prm.subdomain_mode == NBGS_SUB_JACOBI;
     if (C > 0) {
         const int T = 256;
         const int gb = grid_for(C, T, 8, s->num_sms);
@@ -478,47 +485,58 @@ nbgs_status run_colour(nbgs_scene* s)
         if (rc != NBGS_OK) return rc;
         cudaMemsetAsync(s->deg, 0, (n + 1) * sizeof(uint32_t), st);
         k_adj_fill<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->deg, s->adj);
-        // predecessor lists (counts, offsets, lists weakest first)
-        k_pred_count<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->adj, s->cprio, s->pmask,
-                                       s->colour_key);
-        rc = exclusive_scan_u32(s, s->colour_key, s->poff, C, nullptr);
-        if (rc != NBGS_OK) return rc;
-        uint32_t total = 0;
-        rc = cuda_check(s, cudaMemcpyAsync(&total, s->poff + C, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
-                        "colour: predecessor count");
-        if (rc == NBGS_OK) rc = cuda_check(s, cudaStreamSynchronize(st), "colour");
-        if (rc != NBGS_OK) return rc;
-        rc = grow_preds(s, total);
-        if (rc != NBGS_OK) return rc;
-        // waiting lists empty; round-1 counters (|L| = 0, |X| filled below)
-        cudaMemsetAsync(s->whead, 0xFF, C * sizeof(uint32_t), st);
-        cudaMemsetAsync(s->info->wl_count, 0, sizeof(s->info->wl_count), st);
-        k_pred_lists<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->adj, s->cprio, s->pmask,
-                                       s->poff, s->preds, s->whead, s->wnext, s->wl[0], &s->info->wl_count[1]);
-        if (s->timing) s->phase_launches[1] += 9;
-        // rounds; the host checks the lists every few rounds
-        const int gbr = grid_for(C, kJpThreads, 8, s->num_sms);
-        uint32_t round = 0;
-        int cur = 0;
-        for (int batch = 0; batch < 64; ++batch) {
-            for (int r = 0; r < 6; ++r) {
-                ++round;
-                const int ci = (round - 1) % 3, co = round % 3, cc = (round + 1) % 3;
-                k_jp_round<<<gbr, kJpThreads, 0, st>>>(round, (uint32_t)C, s->wl[cur], &s->info->wl_count[2 * ci],
-                                                       s->wl[1 - cur], &s->info->wl_count[2 * co],
-                                                       &s->info->wl_count[2 * cc], s->poff, s->preds, s->cstate,
-                                                       s->whead, s->wnext, s->info);
-                cur = 1 - cur;
+        if (sub) {
+            rc = run_subdomains(s);
+            if (rc != NBGS_OK) return rc;
+        }
+        s->sub_count = sub ? C : -1;
+        if (jacobi) {
+            // non-linear block Jacobi: no contact sees another's reaction of
+            // the same sweep, so a single colour
+            cudaMemsetAsync(s->cstate, 0, C * sizeof(uint32_t), st);
+        } else {
+            // predecessor lists (counts, offsets, lists weakest first)
+            k_pred_count<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->adj, s->cprio, s->pmask,
+                                           s->colour_key);
+            rc = exclusive_scan_u32(s, s->colour_key, s->poff, C, nullptr);
+            if (rc != NBGS_OK) return rc;
+            uint32_t total = 0;
+            rc = cuda_check(s, cudaMemcpyAsync(&total, s->poff + C, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
+                            "colour: predecessor count");
+            if (rc == NBGS_OK) rc = cuda_check(s, cudaStreamSynchronize(st), "colour");
+            if (rc != NBGS_OK) return rc;
+            rc = grow_preds(s, total);
+            if (rc != NBGS_OK) return rc;
+            // waiting lists empty; round-1 counters (|L| = 0, |X| filled below)
+            cudaMemsetAsync(s->whead, 0xFF, C * sizeof(uint32_t), st);
+            cudaMemsetAsync(s->info->wl_count, 0, sizeof(s->info->wl_count), st);
+            k_pred_lists<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->adj, s->cprio, s->pmask,
+                                           s->poff, s->preds, s->whead, s->wnext, s->wl[0], &s->info->wl_count[1]);
+            if (s->timing) s->phase_launches[1] += 9;
+            // rounds; the host checks the lists every few rounds
+            const int gbr = grid_for(C, kJpThreads, 8, s->num_sms);
+            uint32_t round = 0;
+            int cur = 0;
+            for (int batch = 0; batch < 64; ++batch) {
+                for (int r = 0; r < 6; ++r) {
+                    ++round;
+                    const int ci = (round - 1) % 3, co = round % 3, cc = (round + 1) % 3;
+                    k_jp_round<<<gbr, kJpThreads, 0, st>>>(round, (uint32_t)C, s->wl[cur], &s->info->wl_count[2 * ci],
+                                                           s->wl[1 - cur], &s->info->wl_count[2 * co],
+                                                           &s->info->wl_count[2 * cc], s->poff, s->preds, s->cstate,
+                                                           s->whead, s->wnext, s->info);
+                    cur = 1 - cur;
+                }
+                if (s->timing) s->phase_launches[1] += 6;
+                uint32_t left[2] = {0, 0};
+                rc = cuda_check(s, cudaMemcpyAsync(left, &s->info->wl_count[2 * (round % 3)], 2 * sizeof(uint32_t),
+                                                   cudaMemcpyDeviceToHost, st), "colour: worklist");
+                if (rc != NBGS_OK) return rc;
+                rc = cuda_check(s, cudaStreamSynchronize(st), "colour");
+                if (rc != NBGS_OK) return rc;
+                if (left[0] + left[1] == 0) break;
+                if (batch == 63) return fail(s, NBGS_ETIMEOUT, "colour: did not finish in 384 rounds");
             }
-            if (s->timing) s->phase_launches[1] += 6;
-            uint32_t left[2] = {0, 0};
-            rc = cuda_check(s, cudaMemcpyAsync(left, &s->info->wl_count[2 * (round % 3)], 2 * sizeof(uint32_t),
-                                               cudaMemcpyDeviceToHost, st), "colour: worklist");
-            if (rc != NBGS_OK) return rc;
-            rc = cuda_check(s, cudaStreamSynchronize(st), "colour");
-            if (rc != NBGS_OK) return rc;
-            if (left[0] + left[1] == 0) break;
-            if (batch == 63) return fail(s, NBGS_ETIMEOUT, "colour: did not finish in 384 rounds");
         }
         k_colour_keys<<<gb, T, 0, st>>>(C, s->cstate, s->colour_key, s->perm_in, s->col_count, s->info);
         k_colour_offsets<<<1, 32, 0, st>>>(s->col_count, s->col_off);
@@ -533,12 +551,14 @@ nbgs_status run_colour(nbgs_scene* s)
         s->colour_sorted = k0;
         const int warm = (s->prm.warm_start != NBGS_WARM_NONE && s->have_prev) ? 1 : 0;
         if (s->fp32)
-            k_build_sweep<float><<<gb, T, 0, st>>>(C, n, s->perm, s->cj1, s->cj2, s->cgeo, s->clev, s->prm.dt,
+            k_build_sweep<float><<<gb, T, 0, st>>>(C, n, s->perm, s->cj1, s->cj2, sub ? s->inst : nullptr, s->cgeo,
+                                                   s->clev, s->prm.dt,
                                                    s->prm.beta, s->prm.mu, scene_view(s), warm, s->prev_row_off,
                                                    s->prev_j2,
                                                    s->prev_P, (SweepRec<float>*)s->srec, (float4*)s->sp);
         else
-            k_build_sweep<double><<<gb, T, 0, st>>>(C, n, s->perm, s->cj1, s->cj2, s->cgeo, s->clev, s->prm.dt,
+            k_build_sweep<double><<<gb, T, 0, st>>>(C, n, s->perm, s->cj1, s->cj2, sub ? s->inst : nullptr, s->cgeo,
+                                                    s->clev, s->prm.dt,
                                                     s->prm.beta, s->prm.mu, scene_view(s), warm, s->prev_row_off,
                                                     s->prev_j2,
                                                     s->prev_P, (SweepRec<double>*)s->srec, (double4_32a*)s->sp);

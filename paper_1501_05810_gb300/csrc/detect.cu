@@ -784,6 +784,7 @@ nbgs_status run_detect(nbgs_scene* s)
     // starts a new history)
     s->detected = s->coloured = s->solved = false;
     s->n_contacts = 0;
+    s->sub_count = -1;
     cudaMemsetAsync(s->info, 0, offsetof(DevInfo, cell_w), st);   // hmax, vmax
     cudaMemsetAsync(&s->info->n_contacts, 0, sizeof(uint32_t), st);
     if (n == 0) {

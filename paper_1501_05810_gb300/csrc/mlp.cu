@@ -433,6 +433,7 @@ template <class R> struct WarmArgs {
     const uint8_t* finite;
     const float* theta;
     const uint32_t* perm;
+    const uint32_t *cj1, *cj2;   // canonical bodies (j2 >= n: a wall)
     const double4_32a* cgeo;     // canonical (n, xi)
     float* feat_out;             // optional: canonical order, 16 per contact (12 features, cos, sin, w_n, v_ref)
     int apply;                   // 0: features only
@@ -458,20 +459,18 @@ __device__ void contact_features(const WarmArgs<R>& A, int64_t s, double vr_all,
 {
     double nx, ny, nz, tx, ty, tz, ox, oy, oz;
     const SweepRec<R> rr = A.rec[s];
-    uint32_t ia, ib;
+    // the bodies themselves (the record may name subdomain instances, which
+    // all hold the body's velocity before the sweeps)
+    const uint32_t c = A.perm[s];
+    const uint32_t ia = A.cj1[c], ib = A.cj2[c];
     double la, lb;
     if constexpr (sizeof(R) == 4) {
-        ia = __float_as_uint(rr.a.x);
-        ib = __float_as_uint(rr.a.y);
         la = rr.a.z;
         lb = rr.a.w;
         nx = rr.b.x;
         ny = rr.b.y;
         nz = rr.b.z;
     } else {
-        const uint64_t ids = (uint64_t)__double_as_longlong(rr.ids_bias.x);
-        ia = (uint32_t)(ids & 0xFFFFFFFFu);
-        ib = (uint32_t)(ids >> 32);
         la = rr.lev.x;
         lb = rr.lev.y;
         nx = rr.nxy.x;
@@ -612,6 +611,8 @@ static WarmArgs<R> warm_args(nbgs_scene* s, int apply, float* feat_out)
     A.finite = s->finite;
     A.theta = s->mlp_theta;
     A.perm = s->perm;
+    A.cj1 = s->cj1;
+    A.cj2 = s->cj2;
     A.cgeo = s->cgeo;
     A.feat_out = feat_out;
     A.apply = apply;

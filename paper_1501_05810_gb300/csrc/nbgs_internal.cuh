@@ -119,6 +119,8 @@ struct DevInfo {
     uint32_t barrier_count;          // grid barrier arrival counter
     uint32_t barrier_gen;            // grid barrier generation
     uint32_t rounds;                 // colouring rounds used
+    uint32_t n_shared;               // subdomains: bodies with more than one velocity instance
+    uint32_t n_extra;                // subdomains: velocity instances after the n bodies
     double residual;                 // R of the last sweep
     double v_ref;
     unsigned long long rk_bits[kMaxSweepsHist];  // max_j r_j of sweep k (bits)
@@ -302,7 +304,7 @@ struct nbgs_scene {
     // bodies
     double4_32a* pos_r = nullptr;
     double4_32a* quat = nullptr;
-    void* vel = nullptr;          // R4[2n]
+    void* vel = nullptr;          // R4[2 (n + icap)]: (v, 1/m), (w, 1/I) per body, then extra instances
     double* hull = nullptr;
     float4* p32 = nullptr;        // (x - lo, y - lo, z - lo, r + h) in FP32: cell keys and the narrow-phase pre-filter
     float4* p32s = nullptr;       // p32 in cell order (the narrow phase's candidate reads)
@@ -362,6 +364,17 @@ struct nbgs_scene {
     int2* dep = nullptr;           // kMaxColours x coop_blocks block windows [lo, hi] of each chunk
     int* prog = nullptr;           // coop_blocks: last sweep phase each block completed
     uint32_t* cstart = nullptr;    // kMaxColours x (coop_blocks + 1) chunk boundaries
+    // subdomains (Alg. 1 with s_c(j)): one velocity instance per (finite body,
+    // subdomain) pair; the body's own record serves its lowest subdomain, the
+    // others sit after the n bodies in vel
+    uint32_t* csub = nullptr;      // sub_ccap: subdomain of each contact (canonical order)
+    uint32_t* inst = nullptr;      // 2 sub_ccap: velocity record of end j1 / j2 of each contact
+    uint32_t* ext_off = nullptr;   // n + 1: extra instances per body, then their exclusive scan
+    uint32_t* shared = nullptr;    // n: bodies with extra instances (n_shared of them)
+    void* vacc = nullptr;          // R4[2n]: accumulated velocity at the start of the sweep (shared bodies)
+    int64_t sub_ccap = 0;          // contacts the subdomain arrays hold
+    int64_t sub_count = -1;        // contacts csub describes (-1: none since the last detection)
+    int64_t icap = 0;              // extra instance records allocated after the n bodies in vel
     // learned warm start
     float* mlp_theta = nullptr;    // 9,347 FP32 parameters
     // sweep
@@ -402,6 +415,11 @@ nbgs_status run_solve(nbgs_scene* s, int max_sweeps, double tol);
 nbgs_status run_integrate(nbgs_scene* s);
 nbgs_status run_final_residuals(nbgs_scene* s, nbgs_residuals* out);
 nbgs_status run_mlp_prologue(nbgs_scene* s, int apply, float* feat_out);
+nbgs_status run_subdomains(nbgs_scene* s);            // subdomain.cu: s_c(j), instances (after the adjacency)
+nbgs_status ensure_subdomain_buffers(nbgs_scene* s);  // subdomain.cu
+void free_subdomain_buffers(nbgs_scene* s);          // subdomain.cu
+nbgs_status run_get_subdomains(nbgs_scene* s, int64_t cap, uint32_t* out);
+bool subdomains_valid(int32_t mode, const int32_t g[3]);   // api.cu
 nbgs_status run_set_bodies(nbgs_scene* s, const double* pos, const double* quat, const double* vel,
                            const double* angvel);
 nbgs_status run_get_bodies(nbgs_scene* s, double* pos, double* quat, double* vel, double* angvel);

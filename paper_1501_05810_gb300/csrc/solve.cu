@@ -25,6 +25,7 @@ namespace nbgs {
 
 template <class R> struct SolveArgs {
     int64_t n;
+    int64_t nslot;       // velocity records: n, or n + extra instances with subdomains (walls beyond)
     int64_t C;
     R4<R>* vel;
     const SweepRec<R>* rec;
@@ -46,6 +47,10 @@ template <class R> struct SolveArgs {
     unsigned long long* scene_rk;   // 3 x S rotating slots of max r_j / v_ref_s
     uint32_t* scene_done;
     double* scene_res;
+    int sub;                   // subdomains: instances reduced after every sweep
+    const uint32_t* shared;    // bodies with extra instances (info->n_shared)
+    const uint32_t* ext_off;   // n + 1: their extra instances, records n + ext_off[i] ...
+    R4<R>* vacc;               // 2 n: accumulated velocity at the start of the sweep
 };
 
 // Rotating per-scene residual slot of sweep k (three, so that clearing the
@@ -118,7 +123,7 @@ __device__ __forceinline__ void gather(const SolveArgs<R>& A, const SweepRec<R>&
     R la, lb, nx, ny, nz, bias;
     decode<R>(rr, ia, ib, la, lb, nx, ny, nz, bias);
     ld_body(A.vel + 2 * (int64_t)ia, B.va, B.wa);
-    if (ib < (uint32_t)A.n) {
+    if (ib < (uint64_t)A.nslot) {
         ld_body(A.vel + 2 * (int64_t)ib, B.vb, B.wb);
     } else {
         B.vb.x = B.vb.y = B.vb.z = B.vb.w = R(0);
@@ -151,7 +156,7 @@ __device__ __forceinline__ R relax_gathered(const SolveArgs<R>& A, int64_t s, co
         vref_s = A.V.vref[scene];
     }
     R4<R> va = B.va, wa = B.wa, vb = B.vb, wb = B.wb;
-    const bool dyn_b = ib < (uint32_t)A.n;
+    const bool dyn_b = ib < (uint64_t)A.nslot;
     const R ima = va.w, iIa = wa.w, imb = vb.w, iIb = wb.w;
     R tx, ty, tz, ox, oy, oz;
     tangent_basis<R>(nx, ny, nz, tx, ty, tz, ox, oy, oz);
@@ -285,6 +290,58 @@ __device__ __forceinline__ void gravity_pass(const SolveArgs<R>& A, int64_t gtid
             v.z += A.gdt[2];
             A.vel[2 * i] = v;
         }
+    }
+}
+
+// Subdomains (Sect. 6.3): every instance of a shared body starts a sweep
+// from the accumulated velocity.
+template <class R>
+__device__ __forceinline__ void inst_init_pass(const SolveArgs<R>& A, int64_t gtid, int64_t gstride)
+{
+    const uint32_t ns = A.info->n_shared;
+    for (int64_t t = gtid; t < ns; t += gstride) {
+        const int64_t i = A.shared[t];
+        R4<R> v, w;
+        ld_body(A.vel + 2 * i, v, w);
+        st_body(A.vacc + 2 * i, v, w);
+        for (uint32_t e = A.ext_off[i]; e < A.ext_off[i + 1]; ++e) st_body(A.vel + 2 * (A.n + e), v, w);
+    }
+}
+
+// End of a sweep with subdomains: v <- v_acc + sum_p (instance_p - v_acc)
+// over the instances in increasing subdomain (the body's own record first),
+// then every instance and the accumulator restart from v.
+template <class R>
+__device__ __forceinline__ void inst_reduce_pass(const SolveArgs<R>& A, int64_t gtid, int64_t gstride)
+{
+    const uint32_t ns = A.info->n_shared;
+    for (int64_t t = gtid; t < ns; t += gstride) {
+        const int64_t i = A.shared[t];
+        R4<R> v0, w0, v, w;
+        ld_body(A.vacc + 2 * i, v0, w0);
+        ld_body(A.vel + 2 * i, v, w);
+        R4<R> av = v0, aw = w0;
+        av.x += v.x - v0.x;
+        av.y += v.y - v0.y;
+        av.z += v.z - v0.z;
+        aw.x += w.x - w0.x;
+        aw.y += w.y - w0.y;
+        aw.z += w.z - w0.z;
+        const uint32_t e0 = A.ext_off[i], e1 = A.ext_off[i + 1];
+        for (uint32_t e = e0; e < e1; ++e) {
+            ld_body(A.vel + 2 * (A.n + e), v, w);
+            av.x += v.x - v0.x;
+            av.y += v.y - v0.y;
+            av.z += v.z - v0.z;
+            aw.x += w.x - w0.x;
+            aw.y += w.y - w0.y;
+            aw.z += w.z - w0.z;
+        }
+        av.w = v0.w;   // 1/m and 1/I ride along unchanged
+        aw.w = w0.w;
+        st_body(A.vel + 2 * i, av, aw);
+        st_body(A.vacc + 2 * i, av, aw);
+        for (uint32_t e = e0; e < e1; ++e) st_body(A.vel + 2 * (A.n + e), av, aw);
     }
 }
 
@@ -615,7 +672,7 @@ __device__ __forceinline__ void prefetch_range(const SolveArgs<R>& A, int64_t b0
     }
 }
 
-template <class R, bool Batch, bool Warp>
+template <class R, bool Batch, bool Warp, bool Sub>
 __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::value) k_solve_persistent(SolveArgs<R> A)
 {
     extern __shared__ __align__(128) unsigned char stage_mem[];
@@ -635,6 +692,10 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
     if (threadIdx.x == 0) mbar_init(&bar);
     gravity_pass<R>(A, gtid, gstride);
     if (!grid_barrier(A.info, nb)) return;
+    if (Sub) {
+        inst_init_pass<R>(A, gtid, gstride);
+        if (!grid_barrier(A.info, nb)) return;
+    }
     const int nv = (int)nb * (kPersistThreads / 32), vb = (int)blockIdx.x * (kPersistThreads / 32) + (threadIdx.x >> 5);
     if (A.warm) {
         for (int c = 0; c < ncol; ++c) {
@@ -645,6 +706,10 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
             } else {
                 process_colour<R, true, Batch>(A, c, 0, srec, sp, 0);
             }
+            if (!grid_barrier(A.info, nb)) return;
+        }
+        if (Sub) {   // the initial impulses land in the accumulators
+            inst_reduce_pass<R>(A, gtid, gstride);
             if (!grid_barrier(A.info, nb)) return;
         }
     }
@@ -719,9 +784,23 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
         }
         if (!ok) break;
         synced = !local;
+        if (Sub && ncol > 0) {
+            // subdomains: every contact of the sweep is done before the
+            // corrections are summed, and the sum before the next sweep
+            if (!grid_barrier(A.info, nb)) {
+                ok = false;
+                break;
+            }
+            inst_reduce_pass<R>(A, gtid, gstride);
+            if (!grid_barrier(A.info, nb)) {
+                ok = false;
+                break;
+            }
+            synced = true;
+        }
         // R_k needs every block's contribution: a grid barrier per sweep when
         // the tolerance is tested (and near the rotating residual slots)
-        if (local && ncol > 0 && (A.tol > 0.0 || Batch || k + 2 >= kHistKept)) {
+        if (!synced && local && ncol > 0 && (A.tol > 0.0 || Batch || k + 2 >= kHistKept)) {
             if (!grid_barrier(A.info, nb)) {
                 ok = false;
                 break;
@@ -913,6 +992,20 @@ __global__ void __launch_bounds__(256) k_relax_colour(SolveArgs<R> A, int colour
 }
 
 template <class R>
+__global__ void k_inst_init(SolveArgs<R> A)
+{
+    inst_init_pass<R>(A, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
+// after_sweep: skip once an earlier sweep met the tolerance (nothing moved)
+template <class R>
+__global__ void k_inst_reduce(SolveArgs<R> A, int after_sweep)
+{
+    if (after_sweep && A.info->sweeps_done != 0xFFFFFFFFu) return;
+    inst_reduce_pass<R>(A, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
+template <class R>
 __global__ void k_sweep_done(SolveArgs<R> A, int sweep)
 {
     if (threadIdx.x != 0 || A.info->sweeps_done != 0xFFFFFFFFu) return;
@@ -978,6 +1071,11 @@ static SolveArgs<R> make_args(nbgs_scene* s, int max_sweeps, double tol)
     A.scene_rk = s->scene_rk;
     A.scene_done = s->scene_done;
     A.scene_res = s->scene_res;
+    A.sub = (s->prm.subdomain_mode != NBGS_SUB_NONE && !s->batch) ? 1 : 0;
+    A.nslot = A.sub ? s->n + s->icap : s->n;
+    A.shared = s->shared;
+    A.ext_off = s->ext_off;
+    A.vacc = (R4<R>*)s->vacc;
     return A;
 }
 
@@ -1025,10 +1123,12 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
         }
         void* args[] = {&A};
         if (s->timing) cudaEventRecord(s->ev[8], st);
-        const void* fn = s->batch ? (warp ? (const void*)k_solve_persistent<R, true, true>
-                                          : (const void*)k_solve_persistent<R, true, false>)
-                                  : (warp ? (const void*)k_solve_persistent<R, false, true>
-                                          : (const void*)k_solve_persistent<R, false, false>);
+        const void* fn = s->batch ? (warp ? (const void*)k_solve_persistent<R, true, true, false>
+                                          : (const void*)k_solve_persistent<R, true, false, false>)
+                         : A.sub  ? (warp ? (const void*)k_solve_persistent<R, false, true, true>
+                                          : (const void*)k_solve_persistent<R, false, false, true>)
+                                  : (warp ? (const void*)k_solve_persistent<R, false, true, false>
+                                          : (const void*)k_solve_persistent<R, false, false, false>);
         cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(s->coop_blocks),
                                                     dim3(s->coop_threads), args,
                                                     (s->prm.sweep_flags & NBGS_SWEEP_TMA_STAGE) ? Stage<R>::BYTES : 0,
@@ -1049,18 +1149,24 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
     if (rc != NBGS_OK) return rc;
     const int T = 256;
     if (s->timing) cudaEventRecord(s->ev[8], st);
+    const int gi = grid_for(std::max<int64_t>(s->n, 1), T, 8, s->num_sms);   // shared bodies <= n
     k_gravity<R><<<grid_for(s->n, T, 8, s->num_sms), T, 0, st>>>(A);
-    if (A.warm)
+    if (A.sub) k_inst_init<R><<<gi, T, 0, st>>>(A);
+    if (A.warm) {
         for (uint32_t c = 0; c < ncol; ++c)
             k_relax_colour<R, true><<<grid_for(A.C, T, 8, s->num_sms), T, 0, st>>>(A, (int)c, 0);
+        if (A.sub) k_inst_reduce<R><<<gi, T, 0, st>>>(A, 0);
+    }
     for (int k = 0; k < max_sweeps; ++k) {
         for (uint32_t c = 0; c < ncol; ++c)
             k_relax_colour<R, false><<<grid_for(A.C, T, 8, s->num_sms), T, 0, st>>>(A, (int)c, k);
+        if (A.sub) k_inst_reduce<R><<<gi, T, 0, st>>>(A, 1);
         k_sweep_done<R><<<1, 32, 0, st>>>(A, k);
     }
     if (s->timing) {
         cudaEventRecord(s->ev[9], st);
-        const int64_t l = 1 + (A.warm ? ncol : 0) + (int64_t)max_sweeps * (ncol + 1);
+        const int64_t l = 1 + (A.warm ? ncol : 0) + (int64_t)max_sweeps * (ncol + 1) +
+                          (A.sub ? 1 + (A.warm ? 1 : 0) + max_sweeps : 0);
         s->phase_launches[2] += l;
         s->sweep_launches += l;
     }
@@ -1198,49 +1304,39 @@ namespace nbgs {
 // Resident blocks of the persistent solve kernel (cooperative launches need
 // every block resident).  0 and a switch to per-colour launches when the
 // device cannot launch cooperatively.
+// Smallest occupancy over the variants a scene may launch (the single-scene
+// ones: block or warp scheduling, with or without subdomains; the batched
+// ones), with the shared-memory stage allowed.
+template <class R>
+static void persist_occupancy(int threads, int& occ, int& occ_b)
+{
+    const void* single[] = {(const void*)k_solve_persistent<R, false, false, false>,
+                            (const void*)k_solve_persistent<R, false, true, false>,
+                            (const void*)k_solve_persistent<R, false, false, true>,
+                            (const void*)k_solve_persistent<R, false, true, true>};
+    const void* batched[] = {(const void*)k_solve_persistent<R, true, false, false>,
+                             (const void*)k_solve_persistent<R, true, true, false>};
+    occ = occ_b = 1 << 30;
+    for (const void* f : single) {
+        int o = 0;
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<R>::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f, threads, Stage<R>::BYTES);
+        occ = std::min(occ, o);
+    }
+    for (const void* f : batched) {
+        int o = 0;
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<R>::BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f, threads, Stage<R>::BYTES);
+        occ_b = std::min(occ_b, o);
+    }
+}
+
 int persistent_blocks(nbgs_scene* s)
 {
-    int coop = 0, occ = 0;
+    int coop = 0, occ = 0, occ_b = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
-    int occ_b = 0;
-    if (s->fp32) {
-        for (const void* f : {(const void*)k_solve_persistent<float, false, false>,
-                              (const void*)k_solve_persistent<float, false, true>,
-                              (const void*)k_solve_persistent<float, true, false>,
-                              (const void*)k_solve_persistent<float, true, true>})
-            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<float>::BYTES);
-        // the warp-scheduled variants have the same launch bounds; the
-        // smallest occupancy of the pair is what a cooperative launch of
-        // either can rely on
-        int o1 = 0, o2 = 0, o3 = 0, o4 = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_solve_persistent<float, false, false>, s->coop_threads,
-                                                      Stage<float>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_solve_persistent<float, false, true>, s->coop_threads,
-                                                      Stage<float>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o3, k_solve_persistent<float, true, false>, s->coop_threads,
-                                                      Stage<float>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o4, k_solve_persistent<float, true, true>, s->coop_threads,
-                                                      Stage<float>::BYTES);
-        occ = std::min(o1, o2);
-        occ_b = std::min(o3, o4);
-    } else {
-        for (const void* f : {(const void*)k_solve_persistent<double, false, false>,
-                              (const void*)k_solve_persistent<double, false, true>,
-                              (const void*)k_solve_persistent<double, true, false>,
-                              (const void*)k_solve_persistent<double, true, true>})
-            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<double>::BYTES);
-        int o1 = 0, o2 = 0, o3 = 0, o4 = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_solve_persistent<double, false, false>, s->coop_threads,
-                                                      Stage<double>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_solve_persistent<double, false, true>, s->coop_threads,
-                                                      Stage<double>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o3, k_solve_persistent<double, true, false>, s->coop_threads,
-                                                      Stage<double>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o4, k_solve_persistent<double, true, true>, s->coop_threads,
-                                                      Stage<double>::BYTES);
-        occ = std::min(o1, o2);
-        occ_b = std::min(o3, o4);
-    }
+    if (s->fp32) persist_occupancy<float>(s->coop_threads, occ, occ_b);
+    else persist_occupancy<double>(s->coop_threads, occ, occ_b);
     if (s->batch) occ = occ_b;
     cudaGetLastError();
     if (!coop || occ < 1) {

@@ -27,7 +27,8 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ECAPACITY", "ENOTCONV", "ENA
 NBGS_FP64, NBGS_FP32 = 0, 1
 NBGS_WARM_NONE, NBGS_WARM_PREV, NBGS_WARM_MLP = 0, 1, 2
 NBGS_SOLVER_PERSISTENT, NBGS_SOLVER_PER_COLOUR = 0, 1
-NBGS_SWEEP_GLOBAL_SYNC, NBGS_SWEEP_TMA_STAGE = 1, 2
+NBGS_SWEEP_GLOBAL_SYNC, NBGS_SWEEP_TMA_STAGE, NBGS_SWEEP_WARP_SYNC = 1, 2, 4
+NBGS_SUB_NONE, NBGS_SUB_GRID, NBGS_SUB_JACOBI = 0, 1, 2
 
 
 class nbgs_allocator(C.Structure):
@@ -41,7 +42,7 @@ class nbgs_params(C.Structure):
                 ("tau", C.c_double), ("beta", C.c_double), ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3),
                 ("periodic", C.c_int32 * 3), ("precision", C.c_int32), ("warm_start", C.c_int32),
                 ("solver", C.c_int32), ("colour_seed", C.c_uint64), ("contacts_per_body", C.c_int32),
-                ("sweep_flags", C.c_int32)]
+                ("sweep_flags", C.c_int32), ("subdomain_mode", C.c_int32), ("subdomains", C.c_int32 * 3)]
 
 
 class nbgs_batch_desc(C.Structure):
@@ -90,6 +91,8 @@ _SIG = {
     "nbgs_autotune": [_vp, C.c_int32, C.c_double, _i32p, _i32p],
     "nbgs_mlp_load": [_vp, _vp, C.c_int64],
     "nbgs_set_warm_start": [_vp, C.c_int32],
+    "nbgs_set_subdomains": [_vp, C.c_int32, _i32p],
+    "nbgs_get_subdomains": [_vp, C.c_int64, _u32p, _i64p],
     "nbgs_mlp_features": [_vp, _vp, C.c_int64, _i64p],
     "nbgs_mlp_infer": [_vp, _vp, _vp, C.c_int64, _vp],
     "nbgs_mlp_grad": [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp],
@@ -171,7 +174,21 @@ def make_params(p: dict, solver: str = "persistent") -> nbgs_params:
     o.colour_seed = int(p.get("colour_seed", 0)) & 0xFFFFFFFFFFFFFFFF
     o.contacts_per_body = int(p.get("contacts_per_body", 0))
     o.sweep_flags = int(p.get("sweep_flags", 0))
+    o.subdomain_mode, grid = _subdomains(p.get("subdomains"))
+    o.subdomains[:] = grid
     return o
+
+
+def _subdomains(sub):
+    """(mode, grid) of a scene's "subdomains" entry: None (classic NBGS),
+    "jacobi" (one subdomain per contact) or a grid (g0, g1, g2)."""
+    if sub is None:
+        return NBGS_SUB_NONE, [1, 1, 1]
+    if isinstance(sub, str):
+        if sub != "jacobi":
+            raise ValueError(f"unknown subdomains {sub!r}")
+        return NBGS_SUB_JACOBI, [1, 1, 1]
+    return NBGS_SUB_GRID, [int(g) for g in sub]
 
 
 class TorchAllocator:
@@ -303,6 +320,20 @@ class Scene:
                "normal": np.empty((m, 3)), "xi": np.empty(m), "impulse": np.empty((m, 3))}
         _call(self.h, "nbgs_get_contacts", m, *[_ptr(out[k]) for k in ("j1", "j2", "colour", "normal", "xi",
                                                                         "impulse")], C.byref(n))
+        return out
+
+    def set_subdomains(self, sub) -> None:
+        """Subdomains of later solves: None, "jacobi" or a grid (g0, g1, g2)."""
+        mode, grid = _subdomains(sub)
+        g = (C.c_int32 * 3)(*grid)
+        _call(self.h, "nbgs_set_subdomains", mode, g)
+
+    def get_subdomains(self) -> np.ndarray:
+        """s_c(j) of every contact of the last colouring (canonical order)."""
+        n = C.c_int64()
+        _call(self.h, "nbgs_get_subdomains", 0, None, C.byref(n))
+        out = np.zeros(n.value, np.uint32)
+        _call(self.h, "nbgs_get_subdomains", n.value, out.ctypes.data_as(_u32p), C.byref(n))
         return out
 
     def save_state(self, path: str) -> None:
