@@ -182,6 +182,21 @@ def count_contact_kinds(g, n):
     return len(c["j2"]) - walls, walls, sizes
 
 
+def count_instances(g, n):
+    """Subdomains: (bodies with more than one velocity instance, extra
+    instances) of the last colouring -- every distinct (body, subdomain)
+    pair among the contact ends beyond the first per body."""
+    c = g.get_contacts()
+    sub = g.get_subdomains().astype(np.int64)
+    ends = np.concatenate([c["j1"].astype(np.int64), c["j2"].astype(np.int64)])
+    subs = np.concatenate([sub, sub])
+    keep = ends < n
+    pairs = np.unique(ends[keep] * (int(sub.max()) + 1 if len(sub) else 1) + subs[keep])
+    bodies = pairs // (int(sub.max()) + 1 if len(sub) else 1)
+    per = np.bincount(bodies, minlength=n)
+    return int(np.count_nonzero(per > 1)), int(np.maximum(per - 1, 0).sum())
+
+
 def cpu_baseline(steps_budget_s: float = 15.0):
     """The oracle, as it stands, on a bounded sample of the same workload:
     a 24 x 24 x 10 cut of the dense packing (5,760 spheres), whole steps
@@ -231,6 +246,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--sweep-flags", type=int, default=None, help="nbgs_params.sweep_flags override")
     ap.add_argument("--warm", default=None, choices=["none", "prev"], help="warm start of the solves")
+    ap.add_argument("--subdomains", default=None,
+                    help="subdomains of Alg. 1: 'jacobi' (one per contact) or a grid 'g0,g1,g2'")
+    ap.add_argument("--omega", type=float, default=None, help="relaxation parameter of Alg. 1")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -257,6 +275,16 @@ def main():
         for x in (sc if batch else [sc]):
             x["params"]["warm_start"] = args.warm
         desc += f", warm start {args.warm}"
+    if args.subdomains is not None:
+        sub = "jacobi" if args.subdomains == "jacobi" else tuple(int(v) for v in args.subdomains.split(","))
+        for x in (sc if batch else [sc]):
+            x["params"]["subdomains"] = sub
+        desc += (", non-linear block Jacobi (one subdomain per contact)" if sub == "jacobi"
+                 else f", subdomain NBGS on a {sub[0]}x{sub[1]}x{sub[2]} grid")
+    if args.omega is not None:
+        for x in (sc if batch else [sc]):
+            x["params"]["omega"] = args.omega
+        desc += f", omega={args.omega}"
     prec = first["params"].get("precision", "fp64")
     stream = torch.cuda.Stream(device=local)
     with torch.cuda.stream(stream):
@@ -273,6 +301,7 @@ def main():
         for _ in range(max(args.warmup, 0)):
             g.step(sweeps, tol)
         n_ss, n_sw, colour_sizes = count_contact_kinds(g, n)
+        n_shared, n_extra = count_instances(g, n) if args.subdomains is not None else (0, 0)
         g.enable_timing(True)
         clocks = ClockSampler(local)
         clocks.start()
@@ -331,9 +360,16 @@ def main():
     b_ss, b_sw = BYTES[prec]
     # dominant kernel: the persistent sweep kernel, one launch per solve
     alg_bytes_per_launch = (n_ss * b_ss + n_sw * b_sw) * statistics.mean(sweeps_done)
+    # subdomains: per sweep, each shared body's accumulator and own record
+    # read and written, each extra instance read and written; once, the
+    # instances and accumulators set from the bodies
+    rec = 32 if prec == "fp32" else 64
+    alg_bytes_per_launch += ((4 * rec * n_shared + 2 * rec * n_extra) * statistics.mean(sweeps_done)
+                             + 2 * rec * n_shared + rec * n_extra)
     per_launch_ms = phase_ms["sweep_kernel"] / max(1, launches["sweep_kernel"])
     peak, peak_src = read_peaks()
-    traffic = measured_traffic(prec, n_ss + n_sw, statistics.mean(sweeps_done))
+    traffic = (measured_traffic(prec, n_ss + n_sw, statistics.mean(sweeps_done)) if args.subdomains is None
+               else None)
     achieved = alg_bytes_per_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -342,6 +378,8 @@ def main():
         "config": {"workload": desc, "spheres": n, "contacts": contacts[-1], "colours": stats[-1]["n_colours"], "colour_sizes": colour_sizes,
                    "sweeps_per_step": sweeps,
                    "tol": tol, "l2": "inputs larger than L2 (no flush)",
+                   **({"subdomains": args.subdomains, "shared_bodies": n_shared, "extra_instances": n_extra}
+                      if args.subdomains is not None else {}),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "steps_per_s": args.steps / (t_max / 1e3),
         "sweep_updates_per_s": sweep_rate,

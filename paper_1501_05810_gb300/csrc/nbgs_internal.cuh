@@ -372,6 +372,10 @@ struct nbgs_scene {
     uint32_t* ext_off = nullptr;   // n + 1: extra instances per body, then their exclusive scan
     uint32_t* shared = nullptr;    // n: bodies with extra instances (n_shared of them)
     void* vacc = nullptr;          // R4[2n]: accumulated velocity at the start of the sweep (shared bodies)
+    uint32_t* rlist = nullptr;     // n: shared bodies grouped by the block that reduces them
+    uint32_t* rstart = nullptr;    // units + 1: each block's range of rlist
+    uint32_t* rcount = nullptr;    // units + 1: scratch counts
+    int2* dep_r = nullptr;         // units: window of each block's reduction phase
     int64_t sub_ccap = 0;          // contacts the subdomain arrays hold
     int64_t sub_count = -1;        // contacts csub describes (-1: none since the last detection)
     int64_t icap = 0;              // extra instance records allocated after the n bodies in vel

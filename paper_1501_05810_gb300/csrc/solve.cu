@@ -51,6 +51,9 @@ template <class R> struct SolveArgs {
     const uint32_t* shared;    // bodies with extra instances (info->n_shared)
     const uint32_t* ext_off;   // n + 1: their extra instances, records n + ext_off[i] ...
     R4<R>* vacc;               // 2 n: accumulated velocity at the start of the sweep
+    const uint32_t* rlist;     // shared bodies grouped by the block that reduces them (local scheduling)
+    const uint32_t* rstart;    // B + 1: each block's range of rlist
+    const int2* dep_r;         // B: window of each block's reduction phase
 };
 
 // Rotating per-scene residual slot of sweep k (three, so that clearing the
@@ -312,37 +315,40 @@ __device__ __forceinline__ void inst_init_pass(const SolveArgs<R>& A, int64_t gt
 // over the instances in increasing subdomain (the body's own record first),
 // then every instance and the accumulator restart from v.
 template <class R>
-__device__ __forceinline__ void inst_reduce_pass(const SolveArgs<R>& A, int64_t gtid, int64_t gstride)
+__device__ __forceinline__ void inst_reduce_body(const SolveArgs<R>& A, int64_t i)
 {
-    const uint32_t ns = A.info->n_shared;
-    for (int64_t t = gtid; t < ns; t += gstride) {
-        const int64_t i = A.shared[t];
-        R4<R> v0, w0, v, w;
-        ld_body(A.vacc + 2 * i, v0, w0);
-        ld_body(A.vel + 2 * i, v, w);
-        R4<R> av = v0, aw = w0;
+    R4<R> v0, w0, v, w;
+    ld_body(A.vacc + 2 * i, v0, w0);
+    ld_body(A.vel + 2 * i, v, w);
+    R4<R> av = v0, aw = w0;
+    av.x += v.x - v0.x;
+    av.y += v.y - v0.y;
+    av.z += v.z - v0.z;
+    aw.x += w.x - w0.x;
+    aw.y += w.y - w0.y;
+    aw.z += w.z - w0.z;
+    const uint32_t e0 = A.ext_off[i], e1 = A.ext_off[i + 1];
+    for (uint32_t e = e0; e < e1; ++e) {
+        ld_body(A.vel + 2 * (A.n + e), v, w);
         av.x += v.x - v0.x;
         av.y += v.y - v0.y;
         av.z += v.z - v0.z;
         aw.x += w.x - w0.x;
         aw.y += w.y - w0.y;
         aw.z += w.z - w0.z;
-        const uint32_t e0 = A.ext_off[i], e1 = A.ext_off[i + 1];
-        for (uint32_t e = e0; e < e1; ++e) {
-            ld_body(A.vel + 2 * (A.n + e), v, w);
-            av.x += v.x - v0.x;
-            av.y += v.y - v0.y;
-            av.z += v.z - v0.z;
-            aw.x += w.x - w0.x;
-            aw.y += w.y - w0.y;
-            aw.z += w.z - w0.z;
-        }
-        av.w = v0.w;   // 1/m and 1/I ride along unchanged
-        aw.w = w0.w;
-        st_body(A.vel + 2 * i, av, aw);
-        st_body(A.vacc + 2 * i, av, aw);
-        for (uint32_t e = e0; e < e1; ++e) st_body(A.vel + 2 * (A.n + e), av, aw);
     }
+    av.w = v0.w;   // 1/m and 1/I ride along unchanged
+    aw.w = w0.w;
+    st_body(A.vel + 2 * i, av, aw);
+    st_body(A.vacc + 2 * i, av, aw);
+    for (uint32_t e = e0; e < e1; ++e) st_body(A.vel + 2 * (A.n + e), av, aw);
+}
+
+template <class R>
+__device__ __forceinline__ void inst_reduce_pass(const SolveArgs<R>& A, int64_t gtid, int64_t gstride)
+{
+    const uint32_t ns = A.info->n_shared;
+    for (int64_t t = gtid; t < ns; t += gstride) inst_reduce_body<R>(A, A.shared[t]);
 }
 
 template <class R>
@@ -713,6 +719,11 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
             if (!grid_barrier(A.info, nb)) return;
         }
     }
+    // subdomains under local scheduling: the reduction is one more phase of
+    // every sweep, each block summing the shared bodies assigned to it after
+    // the blocks that touch them have finished the sweep
+    const bool wred = Sub && local && !Warp;
+    const int P = wred ? ncol + 1 : ncol;   // phases per sweep
     uint32_t parity = 0;
     int m = (stage && ncol > 0) ? stage_issue<R>(A, 0, srec, sp, &bar) : 0;   // a copy is in flight iff m > 0
     int k = 0;
@@ -749,7 +760,7 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
             }
         }
         for (int c = 0; c < (Warp ? 0 : ncol); ++c) {
-            const int g = k * ncol + c;
+            const int g = k * P + c;
             int64_t cb0, cb1;
             colour_chunk(A.cstart, c, cb0, cb1);
             // an empty chunk touches no body: nothing to wait for (this block's
@@ -784,7 +795,16 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
         }
         if (!ok) break;
         synced = !local;
-        if (Sub && ncol > 0) {
+        if (wred && ncol > 0) {
+            const int g = k * P + ncol;
+            const uint32_t r0 = A.rstart[blockIdx.x], r1 = A.rstart[blockIdx.x + 1];
+            if (r1 > r0 && !wait_deps(A.prog, A.dep_r[blockIdx.x], g, A.info, &s_ok)) {
+                ok = false;
+                break;
+            }
+            for (uint32_t t = r0 + threadIdx.x; t < r1; t += blockDim.x) inst_reduce_body<R>(A, A.rlist[t]);
+            publish(A.prog, g);
+        } else if (Sub && ncol > 0) {
             // subdomains: every contact of the sweep is done before the
             // corrections are summed, and the sum before the next sweep
             if (!grid_barrier(A.info, nb)) {
@@ -866,6 +886,38 @@ __device__ __forceinline__ int block_of(int64_t k, int64_t C, int nblk)
 {
     const int64_t b = (k * nblk) / C;
     return (int)(b < nblk ? b : nblk - 1);
+}
+
+// Subdomains under local scheduling: shared body i is reduced by the first
+// block on the ring whose chunks hold a contact of it (home block + dmin);
+// every block touching i lies within dmax - dmin blocks after it, so that
+// block's reduction window is [0, largest span of its bodies], and every
+// chunk touching i has the reducing block in its own window.
+__global__ void k_reduce_count(int64_t C, int nblk, const uint32_t* __restrict__ shared,
+                               const DevInfo* __restrict__ info, const uint32_t* __restrict__ row_off,
+                               const int* __restrict__ dmin, const int* __restrict__ dmax,
+                               uint32_t* __restrict__ rcount, int2* __restrict__ dep_r)
+{
+    const uint32_t ns = info->n_shared;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ns; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = shared[t];
+        const int r = ((block_of(row_off[i], C, nblk) + dmin[i]) % nblk + nblk) % nblk;
+        atomicAdd(&rcount[r], 1u);
+        atomicMax(&dep_r[r].y, dmax[i] - dmin[i]);
+    }
+}
+
+__global__ void k_reduce_fill(int64_t C, int nblk, const uint32_t* __restrict__ shared,
+                              const DevInfo* __restrict__ info, const uint32_t* __restrict__ row_off,
+                              const int* __restrict__ dmin, const uint32_t* __restrict__ rstart,
+                              uint32_t* __restrict__ rfill, uint32_t* __restrict__ rlist)
+{
+    const uint32_t ns = info->n_shared;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ns; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = shared[t];
+        const int r = ((block_of(row_off[i], C, nblk) + dmin[i]) % nblk + nblk) % nblk;
+        rlist[rstart[r] + atomicAdd(&rfill[r], 1u)] = i;
+    }
 }
 
 // Chunk boundaries: cstart[c][b] = first slot of colour c whose canonical
@@ -1076,6 +1128,9 @@ static SolveArgs<R> make_args(nbgs_scene* s, int max_sweeps, double tol)
     A.shared = s->shared;
     A.ext_off = s->ext_off;
     A.vacc = (R4<R>*)s->vacc;
+    A.rlist = s->rlist;
+    A.rstart = s->rstart;
+    A.dep_r = s->dep_r;
     return A;
 }
 
@@ -1119,6 +1174,19 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
                                                   s->finite, dmin, dmax, s->info, s->dep);
                 cudaMemsetAsync(s->prog, 0xFF, B * sizeof(int), st);
                 if (s->timing) s->phase_launches[2] += 2;
+                if (A.sub && !warp) {
+                    const int gs = grid_for(std::max<int64_t>(s->n, 1), T, 8, s->num_sms);
+                    cudaMemsetAsync(s->rcount, 0, (B + 1) * sizeof(uint32_t), st);
+                    cudaMemsetAsync(s->dep_r, 0, B * sizeof(int2), st);
+                    k_reduce_count<<<gs, T, 0, st>>>(A.C, B, s->shared, s->info, s->row_off, dmin, dmax, s->rcount,
+                                                     s->dep_r);
+                    nbgs_status rc = exclusive_scan_u32(s, s->rcount, s->rstart, B, nullptr);
+                    if (rc != NBGS_OK) return rc;
+                    cudaMemsetAsync(s->rcount, 0, (B + 1) * sizeof(uint32_t), st);
+                    k_reduce_fill<<<gs, T, 0, st>>>(A.C, B, s->shared, s->info, s->row_off, dmin, s->rstart,
+                                                    s->rcount, s->rlist);
+                    if (s->timing) s->phase_launches[2] += 5;
+                }
             }
         }
         void* args[] = {&A};

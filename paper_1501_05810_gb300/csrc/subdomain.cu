@@ -36,29 +36,33 @@ struct SubGrid {
     double lo[3], L[3];
 };
 
+// Grid cell of every body centre (the subdomain of the contacts it is j1 of).
+__global__ void k_body_sub(int64_t n, const double4_32a* __restrict__ pos_r, SubGrid G, uint32_t* __restrict__ bsub)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double4_32a x = pos_r[i];
+        uint32_t id = 0;
+        for (int ax = 2; ax >= 0; --ax) {
+            const double xa = ax == 0 ? x.x : (ax == 1 ? x.y : x.z);
+            double k = floor(xdiv(xmul(xsub(xa, G.lo[ax]), (double)G.g[ax]), G.L[ax]));
+            if (!(k >= 0.0)) k = 0.0;
+            if (k > (double)(G.g[ax] - 1)) k = (double)(G.g[ax] - 1);
+            id = id * (uint32_t)G.g[ax] + (uint32_t)k;
+        }
+        bsub[i] = id;
+    }
+}
+
 // Subdomain of every contact; every contact end names its own body until
 // k_inst_assign gives the finite ones their instances (walls: 0xFFFFFFFF,
 // beyond every velocity record).
 __global__ void k_sub_assign(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
-                             const double4_32a* __restrict__ pos_r, SubGrid G, uint32_t* __restrict__ csub,
+                             const uint32_t* __restrict__ bsub, int jacobi, uint32_t* __restrict__ csub,
                              uint32_t* __restrict__ inst)
 {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t a = cj1[c], b = cj2[c];
-        uint32_t id = 0;
-        if (G.mode == NBGS_SUB_JACOBI) {
-            id = (uint32_t)c;
-        } else {
-            const double4_32a x = pos_r[a];
-            for (int ax = 2; ax >= 0; --ax) {
-                const double xa = ax == 0 ? x.x : (ax == 1 ? x.y : x.z);
-                double k = floor(xdiv(xmul(xsub(xa, G.lo[ax]), (double)G.g[ax]), G.L[ax]));
-                if (!(k >= 0.0)) k = 0.0;
-                if (k > (double)(G.g[ax] - 1)) k = (double)(G.g[ax] - 1);
-                id = id * (uint32_t)G.g[ax] + (uint32_t)k;
-            }
-        }
-        csub[c] = id;
+        csub[c] = jacobi ? (uint32_t)c : bsub[a];
         inst[2 * c] = a;
         inst[2 * c + 1] = b < (uint64_t)n ? b : 0xFFFFFFFFu;
     }
@@ -89,8 +93,17 @@ __global__ void k_inst_count(int64_t n, const uint32_t* __restrict__ adj_off, co
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t e0 = adj_off[i], e1 = adj_off[i + 1];
         uint32_t distinct = 0;
+        uint32_t lo = 0xFFFFFFFFu, hi = 0;
+        if (!jacobi)
+            for (uint32_t e = e0; e < e1; ++e) {
+                const uint32_t q = csub[adj[e]];
+                lo = q < lo ? q : lo;
+                hi = q > hi ? q : hi;
+            }
         if (jacobi) {
             distinct = e1 - e0;   // one subdomain per contact
+        } else if (lo == hi) {
+            distinct = e1 > e0 ? 1u : 0u;   // inside one subdomain: the common case
         } else {
             for (uint32_t e = e0; e < e1; ++e) {
                 const uint32_t q = csub[adj[e]];
@@ -109,14 +122,19 @@ __global__ void k_inst_count(int64_t n, const uint32_t* __restrict__ adj_off, co
 // record, rank r > 0 -> record n + ext_off[i] + r - 1.
 __global__ void k_inst_assign(int64_t n, const uint32_t* __restrict__ adj_off, const uint32_t* __restrict__ adj,
                               const uint32_t* __restrict__ csub, const uint32_t* __restrict__ cj1,
-                              const uint32_t* __restrict__ ext_off, uint32_t* __restrict__ inst)
+                              const uint32_t* __restrict__ ext_off, int jacobi, uint32_t* __restrict__ inst)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t e0 = adj_off[i], e1 = adj_off[i + 1];
         if (ext_off[i + 1] == ext_off[i]) continue;   // one instance: the body's own record (already set)
         for (uint32_t e = e0; e < e1; ++e) {
             const uint32_t c = adj[e];
-            const uint32_t r = sub_rank(adj, csub, e0, e1, csub[c]);
+            uint32_t r = 0;
+            if (jacobi) {   // s_c(j) = j: all distinct, the rank counts the lower contacts
+                for (uint32_t f = e0; f < e1; ++f) r += adj[f] < c ? 1u : 0u;
+            } else {
+                r = sub_rank(adj, csub, e0, e1, csub[c]);
+            }
             const uint32_t slot = r == 0 ? (uint32_t)i : (uint32_t)n + ext_off[i] + r - 1u;
             inst[2 * (int64_t)c + (cj1[c] == (uint32_t)i ? 0 : 1)] = slot;
         }
@@ -127,10 +145,11 @@ __global__ void k_inst_assign(int64_t n, const uint32_t* __restrict__ adj_off, c
 
 void free_subdomain_buffers(nbgs_scene* s)
 {
-    void* ps[] = {s->csub, s->inst, s->ext_off, s->shared, s->vacc};
+    void* ps[] = {s->csub, s->inst, s->ext_off, s->shared, s->vacc, s->rlist, s->rstart, s->rcount, s->dep_r};
     for (void* p : ps) dev_free(s, p);
-    s->csub = s->inst = s->ext_off = s->shared = nullptr;
+    s->csub = s->inst = s->ext_off = s->shared = s->rlist = s->rstart = s->rcount = nullptr;
     s->vacc = nullptr;
+    s->dep_r = nullptr;
     s->sub_ccap = 0;
 }
 
@@ -163,10 +182,16 @@ nbgs_status ensure_subdomain_buffers(nbgs_scene* s)
     }
     if (!s->ext_off) {
         const size_t nn = (size_t)(n > 0 ? n : 1);
+        const size_t units = (size_t)std::max(s->max_coop_blocks, 1) * (size_t)(s->coop_threads / 32);
         s->ext_off = (uint32_t*)dev_alloc(s, (nn + 1) * sizeof(uint32_t));
         s->shared = (uint32_t*)dev_alloc(s, nn * sizeof(uint32_t));
         s->vacc = dev_alloc(s, 2 * nn * v4);
-        if (!s->ext_off || !s->shared || !s->vacc) return fail(s, NBGS_ENOMEM, "subdomains: allocation failed");
+        s->rlist = (uint32_t*)dev_alloc(s, nn * sizeof(uint32_t));
+        s->rstart = (uint32_t*)dev_alloc(s, (units + 1) * sizeof(uint32_t));
+        s->rcount = (uint32_t*)dev_alloc(s, (units + 1) * sizeof(uint32_t));
+        s->dep_r = (int2*)dev_alloc(s, units * sizeof(int2));
+        if (!s->ext_off || !s->shared || !s->vacc || !s->rlist || !s->rstart || !s->rcount || !s->dep_r)
+            return fail(s, NBGS_ENOMEM, "subdomains: allocation failed");
     }
     return cuda_check(s, cudaGetLastError(), "subdomains: buffers");
 }
@@ -189,18 +214,21 @@ nbgs_status run_subdomains(nbgs_scene* s)
     }
     const int T = 256;
     cudaMemsetAsync(&s->info->n_shared, 0, 2 * sizeof(uint32_t), st);   // n_shared, n_extra
-    k_sub_assign<<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(C, n, s->cj1, s->cj2, s->pos_r, G, s->csub, s->inst);
+    const int jacobi = G.mode == NBGS_SUB_JACOBI ? 1 : 0;
+    if (!jacobi && n > 0)   // body cells in ext_off (free until the scan below)
+        k_body_sub<<<grid_for(n, T, 8, s->num_sms), T, 0, st>>>(n, s->pos_r, G, s->ext_off);
+    k_sub_assign<<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(C, n, s->cj1, s->cj2, s->ext_off, jacobi, s->csub,
+                                                              s->inst);
     if (n > 0) {
         // per-body counts in deg (free once the incidence lists are filled)
         k_inst_count<<<grid_for(n, T, 8, s->num_sms), T, 0, st>>>(n, s->adj_off, s->adj, s->csub,
-                                                                   G.mode == NBGS_SUB_JACOBI ? 1 : 0, s->deg,
-                                                                   s->shared, s->info);
+                                                                   jacobi, s->deg, s->shared, s->info);
         rc = exclusive_scan_u32(s, s->deg, s->ext_off, n, &s->info->n_extra);
         if (rc != NBGS_OK) return rc;
         k_inst_assign<<<grid_for(n, T, 8, s->num_sms), T, 0, st>>>(n, s->adj_off, s->adj, s->csub, s->cj1,
-                                                                    s->ext_off, s->inst);
+                                                                    s->ext_off, jacobi, s->inst);
     }
-    if (s->timing) s->phase_launches[1] += n > 0 ? 4 : 1;
+    if (s->timing) s->phase_launches[1] += n > 0 ? (jacobi ? 6 : 7) : 1;
     return cuda_check(s, cudaGetLastError(), "subdomains");
 }
 

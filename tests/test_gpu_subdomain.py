@@ -106,13 +106,21 @@ def test_periodic_jacobi_with_warm_start_and_tolerance(nb, oracle_mod):
     assert 0 < sg["sweeps_done"] < 400
 
 
-def test_warp_scheduling_with_subdomains(nb, oracle_mod):
-    from paper_1501_05810_gb300.nbgs import NBGS_SWEEP_WARP_SYNC
+@pytest.mark.parametrize("flags", ["warp", "global", "tma"])
+@pytest.mark.parametrize("sub", [(2, 3, 2), "jacobi"])
+def test_sweep_schedules_with_subdomains(nb, oracle_mod, flags, sub):
+    """Every schedule of the persistent solver: warps with per-sweep grid
+    barriers around the reduction, a grid barrier after every colour, and the
+    default block windows (here with the shared-memory stage), where the
+    reduction is a windowed phase of its own."""
+    f = {"warp": nb.NBGS_SWEEP_WARP_SYNC, "global": nb.NBGS_SWEEP_GLOBAL_SYNC, "tma": nb.NBGS_SWEEP_TMA_STAGE}[flags]
     sc = scenes.config1(1)
     sc["vel"][:, 2] -= 3.0
-    sc = _with(sc, dt=2e-2, subdomains=(2, 3, 2), omega=0.8, sweep_flags=NBGS_SWEEP_WARP_SYNC)
+    sc = _with(sc, dt=2e-2, subdomains=sub, omega=0.6, sweep_flags=f)
     g, o = nb.Scene(sc), oracle_mod.OracleScene(sc)
-    _step_and_compare(g, o, 50)
+    for _ in range(2):
+        sg, so, bo = _step_and_compare(g, o, 50)
+        g.set_bodies(bo["pos"], bo["quat"], bo["vel"], bo["angvel"])
 
 
 def test_fp32_subdomain_sweeps_against_fp64_oracle(nb, oracle_mod):
