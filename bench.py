@@ -156,7 +156,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
-def measured_traffic(prec, contacts, sweeps):
+def measured_traffic(prec, contacts, sweeps, variant=""):
     """DRAM bytes per launch of the sweep kernel from the committed ncu
     capture (profiles/traffic.json), scaled by the contact updates of one
     launch; None when the kernel source changed since the capture."""
@@ -164,7 +164,7 @@ def measured_traffic(prec, contacts, sweeps):
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    key = f"k_solve_persistent<{'float' if prec == 'fp32' else 'double'}>"
+    key = f"k_solve_persistent<{'float' if prec == 'fp32' else 'double'}>" + variant
     d = json.load(open(p)).get(key)
     if not d:
         return None
@@ -368,8 +368,10 @@ def main():
                              + 2 * rec * n_shared + rec * n_extra)
     per_launch_ms = phase_ms["sweep_kernel"] / max(1, launches["sweep_kernel"])
     peak, peak_src = read_peaks()
-    traffic = (measured_traffic(prec, n_ss + n_sw, statistics.mean(sweeps_done)) if args.subdomains is None
-               else None)
+    # with subdomains the traffic depends on the grid: a capture of the same
+    # workload and grid only
+    traffic = measured_traffic(prec, n_ss + n_sw, statistics.mean(sweeps_done),
+                               "" if args.subdomains is None else f" {args.workload} subdomains {args.subdomains}")
     achieved = alg_bytes_per_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -127,11 +127,33 @@ __global__ void k_inst_assign(int64_t n, const uint32_t* __restrict__ adj_off, c
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t e0 = adj_off[i], e1 = adj_off[i + 1];
         if (ext_off[i + 1] == ext_off[i]) continue;   // one instance: the body's own record (already set)
+        // grid: the body's distinct subdomains in increasing order (few: the
+        // cells around one point), or the quadratic rank beyond kFew of them
+        constexpr int kFew = 16;
+        uint32_t few[kFew];
+        int nfew = 0;
+        bool listed = !jacobi;
+        for (uint32_t e = e0; e < e1 && listed; ++e) {
+            const uint32_t q = csub[adj[e]];
+            int pos = 0;
+            while (pos < nfew && few[pos] < q) ++pos;
+            if (pos < nfew && few[pos] == q) continue;
+            if (nfew == kFew) {
+                listed = false;
+                break;
+            }
+            for (int t = nfew; t > pos; --t) few[t] = few[t - 1];
+            few[pos] = q;
+            ++nfew;
+        }
         for (uint32_t e = e0; e < e1; ++e) {
             const uint32_t c = adj[e];
             uint32_t r = 0;
             if (jacobi) {   // s_c(j) = j: all distinct, the rank counts the lower contacts
                 for (uint32_t f = e0; f < e1; ++f) r += adj[f] < c ? 1u : 0u;
+            } else if (listed) {
+                const uint32_t q = csub[c];
+                while (few[r] != q) ++r;
             } else {
                 r = sub_rank(adj, csub, e0, e1, csub[c]);
             }
