@@ -109,12 +109,18 @@ def lib():
                                           P(C.c_int32), dp, dp, dp, P(C.c_int64)]
         L.oracle_set_impulses.argtypes = [C.c_void_p, dp]
         L.oracle_contact_subdomains.argtypes = [C.c_void_p, P(C.c_int64)]
+        L.oracle_create_composite_scene.argtypes = [P(OracleParams), C.c_int64, dp, dp, dp, dp, C.c_int64,
+                                                    P(C.c_int32), dp, dp, P(C.c_void_p)]
+        L.oracle_member_positions.argtypes = [C.c_void_p, dp]
+        L.oracle_body_mass_properties.argtypes = [C.c_void_p, dp, dp]
         L.oracle_residual_history.argtypes = [C.c_void_p, dp, C.c_int32, P(C.c_int32)]
         L.oracle_final_residuals.argtypes = [C.c_void_p, P(OracleResiduals)]
         L.oracle_contact_frame.argtypes = [dp, dp, dp]
         L.oracle_contact_frame.restype = None
         L.oracle_one_contact.argtypes = [C.c_double, C.c_double, C.c_double, dp, dp]
         L.oracle_one_contact.restype = None
+        L.oracle_one_contact_general.argtypes = [dp, C.c_double, dp, dp]
+        L.oracle_one_contact_general.restype = C.c_int
         L.oracle_splitmix64.argtypes = [C.c_uint64]
         L.oracle_splitmix64.restype = C.c_uint64
         _lib = L
@@ -168,16 +174,27 @@ class OracleScene:
 
     def __init__(self, scene: dict):
         L = lib()
-        self.n = int(len(scene["radius"]))
         self.params = make_params(scene["params"])
+        self.composite = "members" in scene
+        self.n = int(len(scene["pos"]))
         pos = _f64(scene["pos"], (self.n, 3))
         vel = _f64(scene["vel"], (self.n, 3))
         ang = _f64(scene["angvel"], (self.n, 3))
-        rad = _f64(scene["radius"])
         den = _f64(scene["density"])
         h = C.c_void_p()
-        _check(L.oracle_create_scene(C.byref(self.params), self.n, _dp(pos), _dp(vel), _dp(ang),
-                                     _dp(rad), _dp(den), C.byref(h)), "create_scene")
+        if self.composite:
+            mem = scene["members"]
+            mb = np.ascontiguousarray(mem["body"], dtype=np.int32)
+            self.nm = int(len(mb))
+            mo = _f64(mem["offset"], (self.nm, 3))
+            mr = _f64(mem["radius"])
+            _check(L.oracle_create_composite_scene(C.byref(self.params), self.n, _dp(pos), _dp(vel), _dp(ang),
+                                                   _dp(den), self.nm, mb.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                   _dp(mo), _dp(mr), C.byref(h)), "create_composite_scene")
+        else:
+            rad = _f64(scene["radius"])
+            _check(L.oracle_create_scene(C.byref(self.params), self.n, _dp(pos), _dp(vel), _dp(ang),
+                                         _dp(rad), _dp(den), C.byref(h)), "create_scene")
         self._h = h
         self.n_planes = 0
         for n_, c_ in scene.get("planes", []):
@@ -268,6 +285,19 @@ class OracleScene:
                                      _dp(imp), C.byref(n)), "get_contacts")
         return {"j1": j1, "j2": j2, "colour": col, "normal": nrm, "xi": xi, "impulse": imp}
 
+    def body_mass_properties(self):
+        """(1/m per body, body-frame inertia n x 3 x 3) of a composite scene."""
+        invm = np.empty(self.n)
+        I0 = np.empty((self.n, 3, 3))
+        _check(lib().oracle_body_mass_properties(self._h, _dp(invm), _dp(I0)), "body_mass_properties")
+        return invm, I0
+
+    def member_positions(self) -> np.ndarray:
+        """World positions of the member spheres of a composite scene."""
+        out = np.empty((self.nm, 3))
+        _check(lib().oracle_member_positions(self._h, _dp(out)), "member_positions")
+        return out
+
     def contact_subdomains(self) -> np.ndarray:
         """Subdomain s_c(j) of every contact (canonical order)."""
         m = len(self.get_contacts()["j1"])
@@ -305,6 +335,16 @@ def one_contact(w_n, w_t, mu, b):
     p = np.empty(3)
     lib().oracle_one_contact(float(w_n), float(w_t), float(mu), _dp(b), _dp(p))
     return p
+
+
+def one_contact_general(W6, mu, b):
+    """(p, status) of the one-contact problem with a full symmetric Delassus
+    block W6 = (Wnn, Wtt, Woo, Wnt, Wno, Wto); status -1: diagonal fallback."""
+    w = _f64(W6)
+    bb = _f64(b)
+    out = np.empty(3)
+    st = lib().oracle_one_contact_general(_dp(w), float(mu), _dp(bb), _dp(out))
+    return out, st
 
 
 def splitmix64(x: int) -> int:

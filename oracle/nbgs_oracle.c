@@ -45,6 +45,15 @@ struct oracle_scene {
 
     int64_t* sub;                  /* s_c(j) the last solve used (NULL: none since the detection) */
 
+    /* composite particles (Sect. 2: composites of convex particles): bodies
+     * are rigid unions of member spheres; contacts join members of different
+     * bodies, j1/j2 are member indices and walls follow the members */
+    int composite;
+    int64_t nm;                    /* member spheres */
+    int32_t* mbody;                /* body of each member, non-decreasing */
+    double *moff, *mr;             /* body-frame offset from the centre of mass (3 per member), radius */
+    double *I0, *I0inv;            /* body-frame inertia about the centre of mass, and its inverse (9 per body) */
+
     double vmax_start;             /* max_i |v_i| at the start of the step */
     double v_ref;
     double *hist;                  /* R_k per sweep */
@@ -63,9 +72,18 @@ static void cross3(const double a[3], const double b[3], double c[3])
     c[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-static int is_finite_body(const oracle_scene* s, uint32_t i)
+/* Body that contact end j acts on (a sphere, or the body of a member of a
+ * composite), -1 for a wall. */
+static int64_t end_body(const oracle_scene* s, uint32_t j)
 {
-    return (int64_t)i < s->n && (s->invm[i] > 0.0 || s->invI[i] > 0.0);
+    if (s->composite) return (int64_t)j < s->nm ? (int64_t)s->mbody[j] : -1;
+    return (int64_t)j < s->n ? (int64_t)j : -1;
+}
+
+static int is_finite_body(const oracle_scene* s, uint32_t j)
+{
+    int64_t i = end_body(s, j);
+    return i >= 0 && (s->invm[i] > 0.0 || s->invI[i] > 0.0);
 }
 
 /* splitmix64 (Steele, Lea & Flood, OOPSLA 2014; Vigna's reference
@@ -126,6 +144,119 @@ void oracle_one_contact(double w_n, double w_t, double mu, const double b[3], do
     p[2] = po;
 }
 
+/* One-contact problem with a full symmetric Delassus block W (contact frame
+ * (n, t, o); W[0..5] = Wnn, Wtt, Woo, Wnt, Wno, Wto), as composite particles
+ * give it (levers not parallel to n).  Find p with u = W p + b satisfying
+ * eq. (nonpenetration) and eq. (coulomb):
+ *   1. separation: p = 0 is a solution whenever b_n >= 0, and is taken then;
+ *   2. sticking: u = 0, p = -W^-1 b, if p_n > 0 and |p_to| <= mu p_n;
+ *   3. sliding: p = p_n (1, mu cos th, mu sin th) with u_n = 0, so
+ *      p_n = -b_n / D(th), D = Wnn + mu (Wnt cos th + Wno sin th) > 0, and
+ *      u_to antiparallel to (cos th, sin th).  Parallel: the cross product of
+ *      (cos th, sin th) with D u_to vanishes, a trigonometric polynomial of
+ *      degree 2 in th (a quartic in tan(th/2), the route of Bonnefon et al.
+ *      cited in Sect. 3).  Its roots are bracketed by 64 equal samples of
+ *      [0, 2 pi) and refined by 60 bisections; a root is a solution if D > 0
+ *      and u_to points against (cos th, sin th).  Where several are, the one
+ *      of least 1/2 p.W p + b.p is taken (first in th on ties).
+ * For diagonal W with Wtt = Woo this is exactly oracle_one_contact.  Should
+ * no sliding root qualify (a double root the samples cannot bracket), the
+ * diagonal solution with w_n = Wnn, w_t = (Wtt + Woo)/2 is returned and the
+ * result is -1 (0 otherwise). */
+static void w_full(const double W[6], double M[3][3])
+{
+    M[0][0] = W[0]; M[1][1] = W[1]; M[2][2] = W[2];
+    M[0][1] = M[1][0] = W[3];
+    M[0][2] = M[2][0] = W[4];
+    M[1][2] = M[2][1] = W[5];
+}
+
+/* D(th) u_to(th) for p = p_n (1, mu c, mu s), p_n = -b_n / D */
+static void slide_dut(double M[3][3], double mu, const double b[3], double c, double s, double* D, double* vt,
+                      double* vo)
+{
+    *D = M[0][0] + mu * (M[0][1] * c + M[0][2] * s);
+    *vt = -b[0] * (M[1][0] + mu * (M[1][1] * c + M[1][2] * s)) + *D * b[1];
+    *vo = -b[0] * (M[2][0] + mu * (M[2][1] * c + M[2][2] * s)) + *D * b[2];
+}
+
+static double slide_g(double M[3][3], double mu, const double b[3], double th)
+{
+    double D, vt, vo, c = cos(th), s = sin(th);
+    slide_dut(M, mu, b, c, s, &D, &vt, &vo);
+    return -s * vt + c * vo;
+}
+
+static double energy(double M[3][3], const double b[3], const double p[3])
+{
+    double e = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        double wp = (M[i][0] * p[0] + M[i][1] * p[1]) + M[i][2] * p[2];
+        e += p[i] * (0.5 * wp + b[i]);
+    }
+    return e;
+}
+
+int oracle_one_contact_general(const double W[6], double mu, const double b[3], double p[3])
+{
+    double M[3][3];
+    w_full(W, M);
+    p[0] = p[1] = p[2] = 0.0;
+    if (b[0] >= 0.0) return 0;
+    /* sticking: W p = -b by Cramer's rule (W is symmetric positive definite) */
+    double c00 = M[1][1] * M[2][2] - M[1][2] * M[2][1];
+    double c01 = M[1][2] * M[2][0] - M[1][0] * M[2][2];
+    double c02 = M[1][0] * M[2][1] - M[1][1] * M[2][0];
+    double det = (M[0][0] * c00 + M[0][1] * c01) + M[0][2] * c02;
+    double inv[3][3] = {
+        { c00, M[0][2] * M[2][1] - M[0][1] * M[2][2], M[0][1] * M[1][2] - M[0][2] * M[1][1] },
+        { c01, M[0][0] * M[2][2] - M[0][2] * M[2][0], M[0][2] * M[1][0] - M[0][0] * M[1][2] },
+        { c02, M[0][1] * M[2][0] - M[0][0] * M[2][1], M[0][0] * M[1][1] - M[0][1] * M[1][0] },
+    };
+    double ps[3];
+    for (int i = 0; i < 3; ++i) ps[i] = -((inv[i][0] * b[0] + inv[i][1] * b[1]) + inv[i][2] * b[2]) / det;
+    if (ps[0] > 0.0 && sqrt(ps[1] * ps[1] + ps[2] * ps[2]) <= mu * ps[0]) {
+        p[0] = ps[0]; p[1] = ps[1]; p[2] = ps[2];
+        return 0;
+    }
+    /* sliding */
+    const int K = 64;
+    const double two_pi = 6.283185307179586;
+    double best = 0.0;
+    int found = 0;
+    double g0 = slide_g(M, mu, b, 0.0);
+    for (int k = 0; k < K; ++k) {
+        double lo = two_pi * k / K, hi = two_pi * (k + 1) / K;
+        double glo = k == 0 ? g0 : slide_g(M, mu, b, lo);
+        double ghi = k + 1 == K ? g0 : slide_g(M, mu, b, hi);
+        double th;
+        if (glo == 0.0) th = lo;
+        else if ((glo < 0.0) != (ghi < 0.0) && ghi != 0.0) {
+            for (int it = 0; it < 60; ++it) {
+                double mid = 0.5 * (lo + hi);
+                double gm = slide_g(M, mu, b, mid);
+                if ((gm < 0.0) == (glo < 0.0)) { lo = mid; glo = gm; }
+                else hi = mid;
+            }
+            th = 0.5 * (lo + hi);
+        } else continue;
+        double c = cos(th), s = sin(th), D, vt, vo;
+        slide_dut(M, mu, b, c, s, &D, &vt, &vo);
+        if (!(D > 0.0) || c * vt + s * vo > 0.0) continue;
+        double pn = -b[0] / D;
+        double q[3] = { pn, mu * pn * c, mu * pn * s };
+        double e = energy(M, b, q);
+        if (!found || e < best) {
+            best = e;
+            p[0] = q[0]; p[1] = q[1]; p[2] = q[2];
+            found = 1;
+        }
+    }
+    if (found) return 0;
+    oracle_one_contact(W[0], 0.5 * (W[1] + W[2]), mu, b, p);
+    return -1;
+}
+
 /* ------------------------------------------------------------------ */
 /* scene lifecycle                                                      */
 /* ------------------------------------------------------------------ */
@@ -139,6 +270,7 @@ void oracle_destroy_scene(oracle_scene* s)
     free(s->prev_key); free(s->prev_P);
     free(s->hist);
     free(s->sub);
+    free(s->mbody); free(s->moff); free(s->mr); free(s->I0); free(s->I0inv);
     free(s);
 }
 
@@ -197,7 +329,7 @@ int oracle_create_scene(const oracle_params* prm, int64_t n,
 int oracle_add_cone(oracle_scene* s, const double apex[3], const double axis[3], double half_angle,
                     double r_orifice, double r_top)
 {
-    if (!s || !apex || !axis || s->ncones >= ORACLE_MAX_CONES) return 1;
+    if (!s || !apex || !axis || s->ncones >= ORACLE_MAX_CONES || s->composite) return 1;
     if (!(half_angle > 0.0 && half_angle < 1.5707963267948966) || !(r_orifice >= 0.0) || !(r_top > r_orifice))
         return 1;
     double len = sqrt((axis[0] * axis[0] + axis[1] * axis[1]) + axis[2] * axis[2]);
@@ -268,7 +400,7 @@ int oracle_add_plane(oracle_scene* s, const double n[3], double c)
 
 int oracle_set_mass_properties(oracle_scene* s, const double* invm, const double* invI)
 {
-    if (!s) return 1;
+    if (!s || s->composite) return 1;
     for (int64_t i = 0; i < s->n; ++i) {
         if (invm) s->invm[i] = invm[i];
         if (invI) s->invI[i] = invI[i];
@@ -340,6 +472,8 @@ static int push_contact(oracle_scene* s, uint32_t a, uint32_t b, const double nr
     return 0;
 }
 
+static int detect_composite(oracle_scene* s);
+
 int oracle_detect_contacts(oracle_scene* s, int64_t* n_contacts)
 {
     if (!s) return 1;
@@ -347,6 +481,11 @@ int oracle_detect_contacts(oracle_scene* s, int64_t* n_contacts)
     const double dt = P->dt;
     free(s->sub);   /* new contacts: no subdomains assigned yet */
     s->sub = NULL;
+    if (s->composite) {
+        int rc = detect_composite(s);
+        if (rc == 0 && n_contacts) *n_contacts = s->nc;
+        return rc;
+    }
 
     /* eq. (expansionradius): h_i = dt (|v_i| + |omega_i| r_i) + tau, with the
      * velocities at the start of the step; a sphere's bounding radius is r. */
@@ -462,8 +601,8 @@ int oracle_colour_contacts(oracle_scene* s, int32_t* n_colours)
     prio_item* items = (prio_item*)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(prio_item));
     if (!deg || !items) { free(deg); free(items); return 2; }
     for (int64_t c = 0; c < nc; ++c) {
-        if (is_finite_body(s, s->j1[c])) deg[s->j1[c] + 1]++;
-        if (is_finite_body(s, s->j2[c])) deg[s->j2[c] + 1]++;
+        if (is_finite_body(s, s->j1[c])) deg[end_body(s, s->j1[c]) + 1]++;
+        if (is_finite_body(s, s->j2[c])) deg[end_body(s, s->j2[c]) + 1]++;
     }
     for (int64_t i = 0; i < n; ++i) deg[i + 1] += deg[i];
     int64_t* adj = (int64_t*)malloc((size_t)(deg[n] > 0 ? deg[n] : 1) * sizeof(int64_t));
@@ -472,7 +611,10 @@ int oracle_colour_contacts(oracle_scene* s, int32_t* n_colours)
     for (int64_t c = 0; c < nc; ++c) {
         uint32_t b[2] = { s->j1[c], s->j2[c] };
         for (int e = 0; e < 2; ++e)
-            if (is_finite_body(s, b[e])) adj[deg[b[e]] + fill[b[e]]++] = c;
+            if (is_finite_body(s, b[e])) {
+                int64_t i = end_body(s, b[e]);
+                adj[deg[i] + fill[i]++] = c;
+            }
     }
     for (int64_t c = 0; c < nc; ++c) {
         uint64_t key = ((uint64_t)s->j1[c] << 32) | s->j2[c];
@@ -497,7 +639,8 @@ int oracle_colour_contacts(oracle_scene* s, int32_t* n_colours)
         uint32_t b[2] = { s->j1[c], s->j2[c] };
         for (int e = 0; e < 2; ++e) {
             if (!is_finite_body(s, b[e])) continue;
-            for (int64_t k = deg[b[e]]; k < deg[b[e] + 1]; ++k) {
+            int64_t i = end_body(s, b[e]);
+            for (int64_t k = deg[i]; k < deg[i + 1]; ++k) {
                 int64_t d = adj[k];
                 if (d != c && s->colour[d] >= 0) mark[s->colour[d]] = c;
             }
@@ -690,6 +833,9 @@ static int build_slots(const oracle_scene* s, const contact_k* K, int64_t* slot_
     return 0;
 }
 
+static int solve_composite(oracle_scene* s, int32_t max_sweeps, double tol, int32_t* sweeps_done,
+                           double* residual);
+
 int oracle_solve_nbgs(oracle_scene* s, int32_t max_sweeps, double tol,
                       int32_t* sweeps_done, double* residual)
 {
@@ -698,6 +844,7 @@ int oracle_solve_nbgs(oracle_scene* s, int32_t max_sweeps, double tol,
         int rc = oracle_colour_contacts(s, NULL);
         if (rc) return rc;
     }
+    if (s->composite) return solve_composite(s, max_sweeps, tol, sweeps_done, residual);
     const oracle_params* P = &s->prm;
     const int64_t nc = s->nc;
     contact_k* K = (contact_k*)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(contact_k));
@@ -931,6 +1078,431 @@ int oracle_solve_nbgs(oracle_scene* s, int32_t max_sweeps, double tol,
 }
 
 /* ------------------------------------------------------------------ */
+/* composite particles                                                  */
+/* ------------------------------------------------------------------ */
+/* Rotation matrix of the unit quaternion (w, x, y, z). */
+static void quat_matrix(const double q[4], double R[3][3])
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0][0] = 1.0 - 2.0 * (y * y + z * z); R[0][1] = 2.0 * (x * y - w * z); R[0][2] = 2.0 * (x * z + w * y);
+    R[1][0] = 2.0 * (x * y + w * z); R[1][1] = 1.0 - 2.0 * (x * x + z * z); R[1][2] = 2.0 * (y * z - w * x);
+    R[2][0] = 2.0 * (x * z - w * y); R[2][1] = 2.0 * (y * z + w * x); R[2][2] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+static void mat_vec(double A[3][3], const double v[3], double out[3])
+{
+    for (int k = 0; k < 3; ++k) out[k] = (A[k][0] * v[0] + A[k][1] * v[1]) + A[k][2] * v[2];
+}
+
+/* R T0 R^T for a body-frame tensor T0 (9, row-major) */
+static void to_world(double R[3][3], const double* T0, double T[3][3])
+{
+    double RT[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            RT[a][b] = (R[a][0] * T0[0 * 3 + b] + R[a][1] * T0[1 * 3 + b]) + R[a][2] * T0[2 * 3 + b];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) T[a][b] = (RT[a][0] * R[b][0] + RT[a][1] * R[b][1]) + RT[a][2] * R[b][2];
+}
+
+static int inverse3(const double* A, double* Ai)
+{
+    double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+    double det = (A[0] * c00 + A[1] * c01) + A[2] * c02;
+    if (!(det > 0.0)) return 1;
+    Ai[0] = c00 / det; Ai[1] = (A[2] * A[7] - A[1] * A[8]) / det; Ai[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    Ai[3] = c01 / det; Ai[4] = (A[0] * A[8] - A[2] * A[6]) / det; Ai[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    Ai[6] = c02 / det; Ai[7] = (A[1] * A[6] - A[0] * A[7]) / det; Ai[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+    return 0;
+}
+
+/* Sect. 2: a body of k member spheres (radius r_m, density rho, offset d_m
+ * from the given reference point, body frame = observational frame at the
+ * start).  Reading: the members' masses and inertias add up (overlapping
+ * volume counted once per member), m = sum rho 4/3 pi r_m^3; the body's
+ * position is its centre of mass X = sum m_m d_m / m (added to the
+ * reference point); the body-frame inertia about X is
+ * sum [2/5 m_m r_m^2 1 + m_m (|d'|^2 1 - d' d'^T)], d' = d_m - X; the
+ * bounding radius of eq. (expansionradius) is max |d'| + r_m. */
+int oracle_create_composite_scene(const oracle_params* prm, int64_t n, const double* pos, const double* vel,
+                                  const double* angvel, const double* density, int64_t nm,
+                                  const int32_t* member_body, const double* member_offset,
+                                  const double* member_radius, oracle_scene** out)
+{
+    if (!prm || !out || n < 1 || nm < n || !pos || !vel || !angvel || !density || !member_body || !member_offset ||
+        !member_radius || prm->subdomain_mode != ORACLE_SUB_NONE)
+        return 1;
+    for (int64_t m = 0; m < nm; ++m) {
+        if (member_body[m] < 0 || member_body[m] >= n || !(member_radius[m] > 0.0)) return 1;
+        if (m > 0 && member_body[m] < member_body[m - 1]) return 1;
+        if (m > 0 && member_body[m] > member_body[m - 1] + 1) return 1;   /* every body has members */
+    }
+    if (member_body[0] != 0 || member_body[nm - 1] != n - 1) return 1;
+    double* ones = (double*)malloc((size_t)n * sizeof(double));
+    if (!ones) return 2;
+    for (int64_t i = 0; i < n; ++i) ones[i] = 1.0;
+    oracle_scene* s = NULL;
+    int rc = oracle_create_scene(prm, n, pos, vel, angvel, ones, density, &s);
+    free(ones);
+    if (rc) return rc;
+    s->composite = 1;
+    s->nm = nm;
+    s->mbody = (int32_t*)malloc((size_t)nm * sizeof(int32_t));
+    s->moff = (double*)malloc(3 * (size_t)nm * sizeof(double));
+    s->mr = (double*)malloc((size_t)nm * sizeof(double));
+    s->I0 = (double*)malloc(9 * (size_t)n * sizeof(double));
+    s->I0inv = (double*)malloc(9 * (size_t)n * sizeof(double));
+    if (!s->mbody || !s->moff || !s->mr || !s->I0 || !s->I0inv) { oracle_destroy_scene(s); return 2; }
+    int64_t m0 = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t m1 = m0;
+        while (m1 < nm && member_body[m1] == i) ++m1;
+        if (m1 - m0 > ORACLE_MAX_MEMBERS) { oracle_destroy_scene(s); return 1; }
+        double M = 0.0, X[3] = { 0.0, 0.0, 0.0 };
+        for (int64_t m = m0; m < m1; ++m) {
+            double r = member_radius[m];
+            double mm = density[i] * (4.0 / 3.0) * M_PI * r * r * r;
+            M += mm;
+            for (int e = 0; e < 3; ++e) X[e] += mm * member_offset[3 * m + e];
+        }
+        for (int e = 0; e < 3; ++e) X[e] = X[e] / M;
+        double* I = &s->I0[9 * i];
+        for (int k = 0; k < 9; ++k) I[k] = 0.0;
+        double rbar = 0.0;
+        for (int64_t m = m0; m < m1; ++m) {
+            double r = member_radius[m];
+            double mm = density[i] * (4.0 / 3.0) * M_PI * r * r * r;
+            double d[3];
+            for (int e = 0; e < 3; ++e) d[e] = member_offset[3 * m + e] - X[e];
+            double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    I[3 * a + b] += (a == b ? 0.4 * mm * r * r + mm * d2 : 0.0) - mm * d[a] * d[b];
+            s->mbody[m] = (int32_t)i;
+            for (int e = 0; e < 3; ++e) s->moff[3 * m + e] = d[e];
+            s->mr[m] = r;
+            double reach = sqrt(d2) + r;
+            if (reach > rbar) rbar = reach;
+        }
+        for (int e = 0; e < 3; ++e) s->x[3 * i + e] = pos[3 * i + e] + X[e];
+        s->r[i] = rbar;
+        s->invm[i] = M > 0.0 ? 1.0 / M : 0.0;
+        if (M > 0.0) {
+            if (inverse3(I, &s->I0inv[9 * i])) { oracle_destroy_scene(s); return 1; }
+            s->invI[i] = 1.0;   /* finite: takes impulses; the tensor is I0inv */
+        } else {
+            for (int k = 0; k < 9; ++k) s->I0inv[9 * i + k] = 0.0;
+            s->invI[i] = 0.0;
+        }
+        m0 = m1;
+    }
+    *out = s;
+    return 0;
+}
+
+/* World position of member m: X_b + R(q_b) d'_m. */
+static void member_position(const oracle_scene* s, int64_t m, double p[3])
+{
+    const int64_t b = s->mbody[m];
+    double R[3][3], rd[3];
+    quat_matrix(&s->q[4 * b], R);
+    mat_vec(R, &s->moff[3 * m], rd);
+    for (int e = 0; e < 3; ++e) p[e] = s->x[3 * b + e] + rd[e];
+}
+
+int oracle_body_mass_properties(const oracle_scene* s, double* invm, double* I0)
+{
+    if (!s || !s->composite) return 1;
+    for (int64_t i = 0; i < s->n; ++i) {
+        if (invm) invm[i] = s->invm[i];
+        if (I0)
+            for (int k = 0; k < 9; ++k) I0[9 * i + k] = s->I0[9 * i + k];
+    }
+    return 0;
+}
+
+int oracle_member_positions(const oracle_scene* s, double* out)
+{
+    if (!s || !s->composite || !out) return 1;
+    for (int64_t m = 0; m < s->nm; ++m) member_position(s, m, &out[3 * m]);
+    return 0;
+}
+
+/* Contacts between members of different bodies and between members and the
+ * walls, tested like spheres (eq. contactpos for two spheres) against the
+ * hulls of their bodies (eq. expansionradius with the bounding radius). */
+static int detect_composite(oracle_scene* s)
+{
+    const oracle_params* P = &s->prm;
+    const double dt = P->dt;
+    s->vmax_start = 0.0;
+    for (int64_t i = 0; i < s->n; ++i) {
+        double nv = norm3(&s->v[3 * i]);
+        double nw = norm3(&s->w[3 * i]);
+        s->h[i] = dt * (nv + nw * s->r[i]) + P->tau;
+        if (nv > s->vmax_start) s->vmax_start = nv;
+    }
+    double L[3];
+    for (int k = 0; k < 3; ++k) L[k] = P->box_hi[k] - P->box_lo[k];
+    double* pm = (double*)malloc(3 * (size_t)s->nm * sizeof(double));
+    if (!pm) return 2;
+    for (int64_t m = 0; m < s->nm; ++m) member_position(s, m, &pm[3 * m]);
+    s->nc = 0;
+    s->coloured = 0;
+    for (int64_t a = 0; a < s->nm; ++a) {
+        const int64_t A = s->mbody[a];
+        for (int64_t b = a + 1; b < s->nm; ++b) {
+            const int64_t B = s->mbody[b];
+            if (A == B) continue;
+            double d3[3];
+            for (int k = 0; k < 3; ++k) {
+                double dk = pm[3 * a + k] - pm[3 * b + k];
+                if (P->periodic[k]) {
+                    if (dk > 0.5 * L[k]) dk -= L[k];
+                    else if (dk < -0.5 * L[k]) dk += L[k];
+                }
+                d3[k] = dk;
+            }
+            double d = sqrt((d3[0] * d3[0] + d3[1] * d3[1]) + d3[2] * d3[2]);
+            if (((d - s->mr[a]) - s->mr[b]) <= (s->h[A] + s->h[B])) {
+                double nrm[3];
+                if (d > 0.0) { nrm[0] = d3[0] / d; nrm[1] = d3[1] / d; nrm[2] = d3[2] / d; }
+                else { nrm[0] = 0.0; nrm[1] = 0.0; nrm[2] = 1.0; }
+                double xi = (d - s->mr[a]) - s->mr[b];
+                if (push_contact(s, (uint32_t)a, (uint32_t)b, nrm, xi, d - s->mr[b], s->mr[b])) { free(pm); return 2; }
+            }
+        }
+        for (int32_t k = 0; k < s->nplanes; ++k) {
+            const double* nk = s->plane_n[k];
+            double sd = ((nk[0] * pm[3 * a + 0] + nk[1] * pm[3 * a + 1]) + nk[2] * pm[3 * a + 2]) - s->plane_c[k];
+            double xi = sd - s->mr[a];
+            if (xi <= (s->h[A] + P->tau))
+                if (push_contact(s, (uint32_t)a, (uint32_t)(s->nm + k), nk, xi, sd, 0.0)) { free(pm); return 2; }
+        }
+    }
+    free(pm);
+    return 0;
+}
+
+/* Per-contact constants of a composite contact: bodies, contact frame,
+ * levers l = x_hat - X of both bodies (eq. wrench), and the Delassus block
+ * W = sum over the bodies of 1/m 1 - [l]x I^-1 [l]x in the contact frame. */
+typedef struct {
+    int64_t A, B;              /* bodies; B = -1 for a wall */
+    double n[3], t[3], o[3];
+    double lA[3], lB[3];
+    double W[6];               /* Wnn, Wtt, Woo, Wnt, Wno, Wto */
+    double bias;
+} ccontact;
+
+static void add_response(double W[3][3], double invm, double Iinv[3][3], const double l[3])
+{
+    /* - [l]x I^-1 [l]x e_b for every column b */
+    for (int b = 0; b < 3; ++b) {
+        double e[3] = { 0.0, 0.0, 0.0 }, lxe[3], Il[3], col[3];
+        e[b] = 1.0;
+        cross3(l, e, lxe);
+        mat_vec(Iinv, lxe, Il);
+        cross3(Il, l, col);   /* (I^-1 (l x e)) x l = -l x (I^-1 (l x e)) */
+        for (int a = 0; a < 3; ++a) W[a][b] += (a == b ? invm : 0.0) + col[a];
+    }
+}
+
+static void comp_apply(oracle_scene* s, const ccontact* k, double (*Iwinv)[3][3], const double P[3])
+{
+    double tq[3], dw[3];
+    if (k->A >= 0 && s->invm[k->A] > 0.0) {
+        cross3(k->lA, P, tq);
+        mat_vec(Iwinv[k->A], tq, dw);
+        for (int e = 0; e < 3; ++e) {
+            s->v[3 * k->A + e] += s->invm[k->A] * P[e];
+            s->w[3 * k->A + e] += dw[e];
+        }
+    }
+    if (k->B >= 0 && s->invm[k->B] > 0.0) {
+        cross3(k->lB, P, tq);
+        mat_vec(Iwinv[k->B], tq, dw);
+        for (int e = 0; e < 3; ++e) {
+            s->v[3 * k->B + e] -= s->invm[k->B] * P[e];
+            s->w[3 * k->B + e] -= dw[e];
+        }
+    }
+}
+
+static int solve_composite(oracle_scene* s, int32_t max_sweeps, double tol, int32_t* sweeps_done, double* residual)
+{
+    const oracle_params* P = &s->prm;
+    const int64_t nc = s->nc, n = s->n;
+    ccontact* K = (ccontact*)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(ccontact));
+    order_item* ord = (order_item*)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(order_item));
+    double (*Iwinv)[3][3] = malloc((size_t)n * sizeof(*Iwinv));
+    double (*Iw)[3][3] = malloc((size_t)n * sizeof(*Iw));
+    if (!K || !ord || !Iwinv || !Iw) { free(K); free(ord); free(Iwinv); free(Iw); return 2; }
+    for (int64_t i = 0; i < n; ++i) {
+        double R[3][3];
+        quat_matrix(&s->q[4 * i], R);
+        to_world(R, &s->I0inv[9 * i], Iwinv[i]);
+        to_world(R, &s->I0[9 * i], Iw[i]);
+    }
+    for (int64_t c = 0; c < nc; ++c) {
+        ccontact* k = &K[c];
+        const uint32_t a = s->j1[c], b = s->j2[c];
+        k->A = s->mbody[a];
+        k->B = (int64_t)b < s->nm ? (int64_t)s->mbody[b] : -1;
+        for (int e = 0; e < 3; ++e) k->n[e] = s->cn[3 * c + e];
+        oracle_contact_frame(k->n, k->t, k->o);
+        double R[3][3], rd[3];
+        quat_matrix(&s->q[4 * k->A], R);
+        mat_vec(R, &s->moff[3 * a], rd);
+        for (int e = 0; e < 3; ++e) k->lA[e] = rd[e] - s->la[c] * k->n[e];
+        for (int e = 0; e < 3; ++e) k->lB[e] = 0.0;
+        double Wd[3][3] = { { 0, 0, 0 }, { 0, 0, 0 }, { 0, 0, 0 } };
+        if (s->invm[k->A] > 0.0) add_response(Wd, s->invm[k->A], Iwinv[k->A], k->lA);
+        if (k->B >= 0) {
+            quat_matrix(&s->q[4 * k->B], R);
+            mat_vec(R, &s->moff[3 * b], rd);
+            for (int e = 0; e < 3; ++e) k->lB[e] = rd[e] + s->lb[c] * k->n[e];
+            if (s->invm[k->B] > 0.0) add_response(Wd, s->invm[k->B], Iwinv[k->B], k->lB);
+        }
+        const double* F[3] = { k->n, k->t, k->o };
+        double Wc[3][3];
+        for (int x = 0; x < 3; ++x)
+            for (int y = 0; y < 3; ++y) {
+                double wf[3];
+                mat_vec(Wd, F[y], wf);
+                Wc[x][y] = dot3(F[x], wf);
+            }
+        k->W[0] = Wc[0][0]; k->W[1] = Wc[1][1]; k->W[2] = Wc[2][2];
+        k->W[3] = Wc[0][1]; k->W[4] = Wc[0][2]; k->W[5] = Wc[1][2];
+        double xi = s->xi[c];
+        double xs = xi >= 0.0 ? xi : P->beta * xi;
+        k->bias = xs / P->dt;
+        ord[c].colour = s->colour[c];
+        ord[c].idx = c;
+    }
+    qsort(ord, (size_t)nc, sizeof(order_item), cmp_order);
+
+    double gdt = norm3(P->gravity) * P->dt;
+    s->v_ref = s->vmax_start;
+    if (gdt > s->v_ref) s->v_ref = gdt;
+    if (1e-12 > s->v_ref) s->v_ref = 1e-12;
+
+    /* eq. (integrationscheme) without contact reactions: v += dt g and
+     * w += dt I^-1 (-w x I w) with the inertia of the orientation at t */
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(s->invm[i] > 0.0)) continue;
+        double* w = &s->w[3 * i];
+        double Lw[3], g[3], dw[3];
+        mat_vec(Iw[i], w, Lw);
+        cross3(w, Lw, g);
+        for (int e = 0; e < 3; ++e) g[e] = -g[e];
+        mat_vec(Iwinv[i], g, dw);
+        for (int e = 0; e < 3; ++e) {
+            w[e] += P->dt * dw[e];
+            s->v[3 * i + e] += P->dt * P->gravity[e];
+        }
+    }
+    for (int64_t c = 0; c < nc; ++c) {
+        double* p = &s->p[3 * c];
+        p[0] = p[1] = p[2] = 0.0;
+        if (P->warm_start == ORACLE_WARM_PREV && s->nprev > 0) {
+            uint64_t key = ((uint64_t)s->j1[c] << 32) | s->j2[c];
+            int64_t kk = find_prev(s, key);
+            if (kk >= 0) {
+                const double* Pw = &s->prev_P[3 * kk];
+                const ccontact* kc = &K[c];
+                double pn = dot3(kc->n, Pw);
+                if (!(pn > 0.0)) pn = 0.0;
+                double pt = dot3(kc->t, Pw), po = dot3(kc->o, Pw);
+                double lim = P->mu * pn, len = sqrt(pt * pt + po * po);
+                if (len > lim) {
+                    if (len > 0.0) { pt = pt * (lim / len); po = po * (lim / len); }
+                    else { pt = 0.0; po = 0.0; }
+                }
+                p[0] = pn; p[1] = pt; p[2] = po;
+            }
+        }
+    }
+    for (int64_t it = 0; it < nc; ++it) {
+        int64_t c = ord[it].idx;
+        const ccontact* k = &K[c];
+        const double* p = &s->p[3 * c];
+        if (p[0] == 0.0 && p[1] == 0.0 && p[2] == 0.0) continue;
+        double Pw[3];
+        for (int e = 0; e < 3; ++e) Pw[e] = p[0] * k->n[e] + p[1] * k->t[e] + p[2] * k->o[e];
+        comp_apply(s, k, Iwinv, Pw);
+    }
+    s->nhist = 0;
+    int32_t k_done = 0;
+    double Rk = 0.0;
+    for (int32_t sweep = 0; sweep < max_sweeps; ++sweep) {
+        double rmax = 0.0;
+        for (int64_t it = 0; it < nc; ++it) {
+            int64_t c = ord[it].idx;
+            const ccontact* k = &K[c];
+            if (!(k->W[0] > 0.0)) continue;
+            double* p = &s->p[3 * c];
+            double u[3] = { 0.0, 0.0, 0.0 }, cr[3];
+            if (k->A >= 0) {
+                cross3(&s->w[3 * k->A], k->lA, cr);
+                for (int e = 0; e < 3; ++e) u[e] += s->v[3 * k->A + e] + cr[e];
+            }
+            if (k->B >= 0) {
+                cross3(&s->w[3 * k->B], k->lB, cr);
+                for (int e = 0; e < 3; ++e) u[e] -= s->v[3 * k->B + e] + cr[e];
+            }
+            double Wm[3][3];
+            w_full(k->W, Wm);
+            double uc[3] = { dot3(k->n, u), dot3(k->t, u), dot3(k->o, u) }, wp[3], b[3];
+            mat_vec(Wm, p, wp);
+            for (int e = 0; e < 3; ++e) b[e] = uc[e] - wp[e];
+            b[0] += k->bias;
+            double y[3];
+            oracle_one_contact_general(k->W, P->mu, b, y);
+            double pnew[3], dp[3];
+            for (int e = 0; e < 3; ++e) {
+                pnew[e] = P->omega * y[e] + (1.0 - P->omega) * p[e];
+                dp[e] = pnew[e] - p[e];
+            }
+            double Pw[3];
+            for (int e = 0; e < 3; ++e) Pw[e] = dp[0] * k->n[e] + dp[1] * k->t[e] + dp[2] * k->o[e];
+            comp_apply(s, k, Iwinv, Pw);
+            for (int e = 0; e < 3; ++e) p[e] = pnew[e];
+            double wd[3];
+            mat_vec(Wm, dp, wd);
+            double rj = sqrt((wd[0] * wd[0] + wd[1] * wd[1]) + wd[2] * wd[2]);
+            if (rj > rmax) rmax = rj;
+        }
+        Rk = rmax / s->v_ref;
+        if (s->nhist == s->cap_hist) {
+            double* hh = (double*)realloc(s->hist, 2 * (size_t)s->cap_hist * sizeof(double));
+            if (!hh) { free(K); free(ord); free(Iwinv); free(Iw); return 2; }
+            s->hist = hh;
+            s->cap_hist *= 2;
+        }
+        s->hist[s->nhist++] = Rk;
+        k_done = sweep + 1;
+        if (tol > 0.0 && Rk <= tol) break;
+    }
+    free(s->prev_key);
+    free(s->prev_P);
+    s->prev_key = (uint64_t*)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(uint64_t));
+    s->prev_P = (double*)malloc(3 * (size_t)(nc > 0 ? nc : 1) * sizeof(double));
+    if (!s->prev_key || !s->prev_P) { free(K); free(ord); free(Iwinv); free(Iw); s->nprev = 0; return 2; }
+    for (int64_t c = 0; c < nc; ++c) {
+        s->prev_key[c] = ((uint64_t)s->j1[c] << 32) | s->j2[c];
+        const double* p = &s->p[3 * c];
+        for (int e = 0; e < 3; ++e)
+            s->prev_P[3 * c + e] = p[0] * K[c].n[e] + p[1] * K[c].t[e] + p[2] * K[c].o[e];
+    }
+    s->nprev = nc;
+    free(K); free(ord); free(Iwinv); free(Iw);
+    if (sweeps_done) *sweeps_done = k_done;
+    if (residual) *residual = Rk;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* time integration (Sect. 3, eq. integrationscheme)                    */
 /* ------------------------------------------------------------------ */
 int oracle_integrate(oracle_scene* s)
@@ -1029,7 +1601,7 @@ int oracle_residual_history(const oracle_scene* s, double* out, int32_t cap, int
  * velocity units by v_ref. */
 int oracle_final_residuals(const oracle_scene* s, oracle_residuals* out)
 {
-    if (!s || !out) return 1;
+    if (!s || !out || s->composite) return 1;
     memset(out, 0, sizeof(*out));
     double vr = s->v_ref > 0.0 ? s->v_ref : 1e-12;
     for (int64_t c = 0; c < s->nc; ++c) {

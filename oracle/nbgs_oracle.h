@@ -42,6 +42,7 @@ extern "C" {
 
 #define ORACLE_MAX_PLANES 16
 #define ORACLE_MAX_CONES 4
+#define ORACLE_MAX_MEMBERS 4   /* member spheres of a composite particle */
 
 enum { ORACLE_WARM_NONE = 0, ORACLE_WARM_PREV = 1 };
 /* Subdomains s_c(j) of Alg. 1: none (one subdomain: classic NBGS), a regular
@@ -117,6 +118,25 @@ int  oracle_solve_nbgs(oracle_scene* s, int32_t max_sweeps, double tol,
 int  oracle_integrate(oracle_scene* s);
 int  oracle_step(oracle_scene* s, int32_t max_sweeps, double tol, oracle_step_stats* st);
 
+/* Composite particles (Sect. 2, composites of convex particles): n rigid
+ * bodies made of nm member spheres.  member_body (nm, non-decreasing, every
+ * body 1..ORACLE_MAX_MEMBERS members), member_offset (nm x 3, from the
+ * body's reference point pos, observational axes), member_radius (nm).
+ * Mass, centre of mass and inertia follow from the members (see the
+ * definition); the body's position becomes its centre of mass and its
+ * orientation the identity.  Contacts join members of different bodies
+ * (j1 < j2 member indices) or a member and a wall (j2 = nm + k).  No cones,
+ * subdomains, mass overrides or final residuals. */
+int  oracle_create_composite_scene(const oracle_params* prm, int64_t n, const double* pos, const double* vel,
+                                   const double* angvel, const double* density, int64_t nm,
+                                   const int32_t* member_body, const double* member_offset,
+                                   const double* member_radius, oracle_scene** out);
+/* 1/m and the body-frame inertia about the centre of mass (n x 9) of every
+ * composite body. */
+int  oracle_body_mass_properties(const oracle_scene* s, double* invm, double* I0);
+/* World positions of the members (nm x 3). */
+int  oracle_member_positions(const oracle_scene* s, double* out);
+
 /* Subdomain s_c(j) of every contact (canonical order) under the scene's
  * subdomain mode, from the current positions; 0 for every contact when
  * there are no subdomains. */
@@ -139,6 +159,11 @@ void     oracle_contact_frame(const double n[3], double t[3], double o[3]);
 void     oracle_one_contact(double w_n, double w_t, double mu, const double b[3],
                             double p[3]);
 uint64_t oracle_splitmix64(uint64_t x);
+/* One-contact problem with a full symmetric Delassus block in the contact
+ * frame, W = (Wnn, Wtt, Woo, Wnt, Wno, Wto): separation, sticking or
+ * sliding (see the definition in nbgs_oracle.c).  Returns 0, or -1 when it
+ * fell back to the diagonal solution. */
+int      oracle_one_contact_general(const double W[6], double mu, const double b[3], double p[3]);
 
 #ifdef __cplusplus
 }

@@ -402,3 +402,84 @@ def layout_batch(scenes: list, gap: float = 4.0) -> list:
         t["planes"] = box_walls(lo, hi)
         out.append(t)
     return out
+
+
+# ---------------------------------------------------------------------------
+# composite particles: rigid unions of 1-4 member spheres
+# ---------------------------------------------------------------------------
+def _composite_scene(name, params, pos, vel, angvel, density, member_body, member_offset, member_radius, planes):
+    """A scene of composite bodies: pos is each body's reference point, the
+    members' offsets are measured from it (observational axes)."""
+    n = len(density)
+    m = len(member_body)
+    return {
+        "name": name,
+        "params": params,
+        "pos": np.ascontiguousarray(pos, dtype=np.float64).reshape(n, 3),
+        "vel": np.ascontiguousarray(vel, dtype=np.float64).reshape(n, 3),
+        "angvel": np.ascontiguousarray(angvel, dtype=np.float64).reshape(n, 3),
+        "density": np.ascontiguousarray(density, dtype=np.float64).reshape(n),
+        "members": {
+            "body": np.ascontiguousarray(member_body, dtype=np.int32).reshape(m),
+            "offset": np.ascontiguousarray(member_offset, dtype=np.float64).reshape(m, 3),
+            "radius": np.ascontiguousarray(member_radius, dtype=np.float64).reshape(m),
+        },
+        "planes": list(planes),
+        "cones": [],
+    }
+
+
+def as_composites(sc: dict) -> dict:
+    """A sphere scene as composites of one member each (offset 0)."""
+    n = len(sc["radius"])
+    return _composite_scene(sc["name"] + "_as_composites", dict(sc["params"]), sc["pos"], sc["vel"], sc["angvel"],
+                            sc["density"], np.arange(n), np.zeros((n, 3)), sc["radius"], sc["planes"])
+
+
+def dumbbell_on_plane(radius: float = 0.5, half_sep: float = 0.6, gap: float = 0.0, **params) -> dict:
+    """Two equal spheres glued at (+-half_sep, 0, 0) resting on the floor z = 0."""
+    prm = default_params(box_lo=(-5, -5, -5), box_hi=(5, 5, 5), **params)
+    return _composite_scene("dumbbell_on_plane", prm, [[0.0, 0.0, radius + gap]], np.zeros((1, 3)),
+                            np.zeros((1, 3)), [1.0], [0, 0], [[-half_sep, 0, 0], [half_sep, 0, 0]],
+                            [radius, radius], [((0.0, 0.0, 1.0), 0.0)])
+
+
+def spinning_body(angvel=(0.3, 2.0, 0.1), offsets=None, radii=None, **params) -> dict:
+    """One free composite (gravity off, no walls) spinning with angvel; the
+    default is an asymmetric three-member body."""
+    if offsets is None:
+        offsets = [[0.0, 0.0, 0.0], [0.9, 0.1, 0.0], [0.1, 0.0, 0.6]]
+        radii = [0.5, 0.35, 0.3]
+    prm = default_params(gravity=(0.0, 0.0, 0.0), box_lo=(-50, -50, -50), box_hi=(50, 50, 50), **params)
+    k = len(offsets)
+    return _composite_scene("spinning_body", prm, np.zeros((1, 3)), np.zeros((1, 3)), [list(angvel)], [1.0],
+                            [0] * k, offsets, radii, [])
+
+
+def composite_gas(nx: int = 10, ny: int = 10, nz: int = 10, seed: int = 0, spacing: float = 1.1,
+                  bound_radius: float = 0.5, r_lo: float = 0.3, r_hi: float = 0.4, v_max: float = 0.2,
+                  walls: bool = True, **params) -> dict:
+    """The granular gas of Sect. 7.2.1 as the paper ran it: composites of two
+    to four spheres of diameters U(0.6, 0.8) (radii r_lo..r_hi) touching the
+    inside of a bounding sphere of diameter 1, on a Cartesian grid of spacing
+    1.1, velocities U(-v_max, v_max) per component (|v| <= 0.2 sqrt 3),
+    confined by walls, no gravity, mu = 0.1, omega = 0.75."""
+    rng = np.random.default_rng(seed)
+    n = nx * ny * nz
+    i, j, k = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    lo = np.zeros(3)
+    hi = np.array([nx, ny, nz], dtype=np.float64) * spacing
+    pos = (np.stack([i.ravel(), j.ravel(), k.ravel()], -1) + 0.5) * spacing
+    counts = rng.integers(2, 5, n)
+    mb = np.repeat(np.arange(n), counts)
+    m = len(mb)
+    r = rng.uniform(r_lo, r_hi, m)
+    d = rng.normal(size=(m, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    off = d * (bound_radius - r)[:, None]
+    vel = rng.uniform(-v_max, v_max, (n, 3))
+    kw = dict(gravity=(0.0, 0.0, 0.0), mu=0.1, omega=0.75, dt=1e-4, tau=0.005, box_lo=tuple(lo), box_hi=tuple(hi))
+    kw.update(params)
+    prm = default_params(**kw)
+    planes = box_walls(lo, hi) if walls else []
+    return _composite_scene(f"composite_gas_{n}", prm, pos, vel, np.zeros((n, 3)), np.ones(n), mb, off, r, planes)

@@ -756,3 +756,294 @@ def test_subdomain_parameters_are_checked(oracle_mod):
     sc = scenes.column(3, subdomains=(2, 0, 1))
     with pytest.raises(RuntimeError):
         oracle_mod.OracleScene(sc)
+
+
+# ---------------------------------------------------------------------------
+# one-contact problem with a full Delassus block (composite particles)
+# ---------------------------------------------------------------------------
+def _skew(a):
+    return np.array([[0.0, -a[2], a[1]], [a[2], 0.0, -a[0]], [-a[1], a[0], 0.0]])
+
+
+def _random_delassus(rng):
+    """W of a contact between two rigid bodies with random masses, inertia
+    tensors and levers, in a random contact frame: sum over the bodies of
+    1/m 1 - [l]x I^-1 [l]x (eq. wrench, eq. integrationscheme)."""
+    W = np.zeros((3, 3))
+    for _ in range(2):
+        m = rng.uniform(0.5, 2.0)
+        A = rng.normal(size=(3, 3))
+        I = A @ A.T + 0.2 * np.eye(3)
+        lev = rng.normal(size=3) * rng.uniform(0.2, 1.0)
+        W += np.eye(3) / m - _skew(lev) @ np.linalg.inv(I) @ _skew(lev)
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    return Q.T @ W @ Q
+
+
+def _w6(W):
+    return np.array([W[0, 0], W[1, 1], W[2, 2], W[0, 1], W[0, 2], W[1, 2]])
+
+
+def test_general_one_contact_reduces_to_closed_form(oracle_mod):
+    rng = np.random.default_rng(3)
+    for _ in range(2000):
+        wn, wt = rng.uniform(0.1, 3.0), rng.uniform(0.1, 3.0)
+        mu = rng.uniform(0.0, 1.2)
+        b = rng.normal(size=3)
+        p_ref = oracle_mod.one_contact(wn, wt, mu, b)
+        p, st = oracle_mod.one_contact_general([wn, wt, wt, 0.0, 0.0, 0.0], mu, b)
+        assert st == 0
+        assert np.abs(p - p_ref).max() <= 1e-13 * max(1.0, np.abs(p_ref).max())
+
+
+def test_general_one_contact_satisfies_the_discrete_constraints(oracle_mod):
+    """eq. (nonpenetration) and eq. (coulomb) at u = W p + b, checked
+    directly, for random Delassus blocks of two rigid bodies."""
+    rng = np.random.default_rng(4)
+    kinds = {"sep": 0, "stick": 0, "slide": 0}
+    fallbacks = 0
+    for _ in range(3000):
+        W = _random_delassus(rng)
+        mu = rng.uniform(0.05, 1.0)
+        b = rng.normal(size=3)
+        p, st = oracle_mod.one_contact_general(_w6(W), mu, b)
+        if st != 0:
+            fallbacks += 1
+            continue
+        u = W @ p + b
+        scale = np.abs(b).max() + 1e-300
+        pt, ut = np.hypot(p[1], p[2]), np.hypot(u[1], u[2])
+        assert p[0] >= 0.0 and u[0] >= -1e-12 * scale
+        assert abs(p[0] * u[0]) <= 1e-12 * scale * max(p[0], 1e-300) + 1e-300
+        assert pt <= mu * p[0] * (1 + 1e-12) + 1e-300
+        if p[0] == 0.0:
+            kinds["sep"] += 1
+        elif ut <= 1e-12 * scale:
+            kinds["stick"] += 1
+        else:
+            kinds["slide"] += 1
+            # sliding: p_t = -mu p_n u_t / |u_t| (eq. coulomb, second line)
+            assert np.abs(p[1:] + mu * p[0] * u[1:] / ut).max() <= 1e-10 * mu * p[0]
+    assert min(kinds.values()) > 100, kinds
+    assert fallbacks <= 3
+
+
+def test_general_one_contact_takes_the_least_energy_slide(oracle_mod):
+    """Against every sliding state a dense scan of the angle finds."""
+    rng = np.random.default_rng(5)
+    checked = 0
+    th = np.linspace(0.0, 2 * np.pi, 200001)[:-1]
+    c, s = np.cos(th), np.sin(th)
+    for _ in range(300):
+        W = _random_delassus(rng)
+        mu = rng.uniform(0.3, 1.0)
+        b = rng.normal(size=3)
+        b[0] = -abs(b[0])
+        p, st = oracle_mod.one_contact_general(_w6(W), mu, b)
+        Wi = np.linalg.inv(W)
+        ps = -Wi @ b
+        if st != 0 or (ps[0] > 0 and np.hypot(ps[1], ps[2]) <= mu * ps[0]):
+            continue
+        D = W[0, 0] + mu * (W[0, 1] * c + W[0, 2] * s)
+        vt = -b[0] * (W[1, 0] + mu * (W[1, 1] * c + W[1, 2] * s)) + D * b[1]
+        vo = -b[0] * (W[2, 0] + mu * (W[2, 1] * c + W[2, 2] * s)) + D * b[2]
+        g = -s * vt + c * vo
+        roots = np.nonzero(np.sign(g) != np.sign(np.roll(g, -1)))[0]
+        energies = []
+        for k in roots:   # refine each bracket by the secant step
+            t0, t1 = th[k], th[(k + 1) % len(th)] + (2 * np.pi if k + 1 == len(th) else 0.0)
+            t = t0 - g[k] * (t1 - t0) / (g[(k + 1) % len(th)] - g[k])
+            cc, ss = np.cos(t), np.sin(t)
+            Dd = W[0, 0] + mu * (W[0, 1] * cc + W[0, 2] * ss)
+            ut = -b[0] * (W[1:, 0] + mu * (W[1:, 1:] @ np.array([cc, ss]))) / Dd + b[1:]
+            if Dd <= 0 or cc * ut[0] + ss * ut[1] > 0:
+                continue
+            q = -b[0] / Dd * np.array([1.0, mu * cc, mu * ss])
+            energies.append(0.5 * q @ W @ q + b @ q)
+        if not energies:
+            continue
+        e = 0.5 * p @ W @ p + b @ p
+        assert e <= min(energies) + 1e-9 * abs(min(energies))
+        checked += 1
+    assert checked > 100
+
+
+# ---------------------------------------------------------------------------
+# composite particles (Sect. 2: composites of convex particles)
+# ---------------------------------------------------------------------------
+def test_single_member_composites_are_spheres(oracle_mod):
+    """A composite of one member at its centre is the sphere itself: the same
+    contacts, and impulses and velocities to rounding (the full Delassus
+    block of a sphere is diag(w_n, w_t, w_t) up to rounding)."""
+    sc = scenes.hcp_packing(4, 4, 3, dt=1e-3, tau=1e-3, mu=0.4, tilt_deg=30.0, v0=0.1, warm_start="prev")
+    a, _ = _run(oracle_mod, sc, 4, 30)
+    b, _ = _run(oracle_mod, scenes.as_composites(sc), 4, 30)
+    ca, cb = a.get_contacts(), b.get_contacts()
+    assert np.array_equal(ca["j1"], cb["j1"]) and np.array_equal(ca["j2"], cb["j2"])
+    assert np.array_equal(ca["colour"], cb["colour"])
+    assert np.abs(ca["impulse"] - cb["impulse"]).max() <= 1e-11 * np.abs(ca["impulse"]).max()
+    ba, bb = a.get_bodies(), b.get_bodies()
+    assert np.abs(ba["vel"] - bb["vel"]).max() <= 1e-11 * np.abs(ba["vel"]).max()
+    assert np.abs(ba["pos"] - bb["pos"]).max() <= 1e-12
+
+
+def _mc_inertia(offsets, radii, density, rng, samples=400000):
+    """Mass, centre of mass and inertia about it by Monte-Carlo integration
+    over each member ball (a member's volume counted for that member)."""
+    M, S, T = 0.0, np.zeros(3), np.zeros((3, 3))
+    pts_all, w_all = [], []
+    for d, r in zip(offsets, radii):
+        u = rng.uniform(-1, 1, (samples, 3))
+        u = u[(u * u).sum(1) <= 1.0]
+        vol = 4.0 / 3.0 * np.pi * r ** 3
+        p = np.asarray(d) + r * u
+        w = density * vol / len(p)
+        pts_all.append(p)
+        w_all.append(np.full(len(p), w))
+    p = np.concatenate(pts_all)
+    w = np.concatenate(w_all)
+    M = w.sum()
+    X = (w[:, None] * p).sum(0) / M
+    q = p - X
+    T = (w[:, None, None] * ((q * q).sum(1)[:, None, None] * np.eye(3) - q[:, :, None] * q[:, None, :])).sum(0)
+    return M, X, T
+
+
+def test_composite_mass_properties_against_volume_integration(oracle_mod):
+    """Mass, centre of mass and inertia of composites against Monte-Carlo
+    integration over the member balls (each ball counted for its member)."""
+    rng = np.random.default_rng(9)
+    for sc in (scenes.spinning_body(), scenes.dumbbell_on_plane(), scenes.composite_gas(2, 1, 1, seed=3)):
+        o = oracle_mod.OracleScene(sc)
+        invm, I0 = o.body_mass_properties()
+        pos = o.get_bodies()["pos"]
+        mb, off, rad = sc["members"]["body"], sc["members"]["offset"], sc["members"]["radius"]
+        for i in range(len(sc["density"])):
+            sel = mb == i
+            M, X, T = _mc_inertia(off[sel], rad[sel], sc["density"][i], rng)
+            assert abs(1.0 / invm[i] - M) <= 3e-3 * M
+            assert np.abs(pos[i] - (sc["pos"][i] + X)).max() <= 3e-3 * rad[sel].max()
+            assert np.abs(I0[i] - T).max() <= 1e-2 * np.abs(T).max()
+
+
+def test_dumbbell_rests_on_two_contacts(oracle_mod):
+    """Two equal members on the floor: each contact carries half the weight
+    (p_n = m g dt / 2), the body neither moves nor turns."""
+    dt, g = 1e-3, 9.81
+    sc = scenes.dumbbell_on_plane(dt=dt)
+    o = oracle_mod.OracleScene(sc)
+    invm, _ = o.body_mass_properties()
+    for _ in range(20):
+        st = o.step(200, 1e-14)
+        assert st["n_contacts"] == 2
+    c = o.get_contacts()
+    assert np.abs(c["impulse"][:, 0] - 0.5 * g * dt / invm[0]).max() <= 1e-10 * g * dt / invm[0]
+    b = o.get_bodies()
+    assert np.abs(b["vel"]).max() <= 1e-12 and np.abs(b["angvel"]).max() <= 1e-12
+    assert abs(b["pos"][0, 2] - 0.5) <= 1e-12
+
+
+def test_free_rotation_about_a_symmetry_axis_is_exact(oracle_mod):
+    """A dumbbell spinning about its own axis: w x I w = 0, so w stays
+    constant and the orientation is the exact rotation (members on the axis
+    stay put; a quarter turn at t = pi / (2 |w|) for an off-axis check is
+    replaced by the members staying on the spin axis)."""
+    w0 = 3.0
+    sc = scenes.spinning_body(angvel=(w0, 0.0, 0.0), offsets=[[-0.6, 0, 0], [0.6, 0, 0]], radii=[0.5, 0.5], dt=1e-3)
+    o = oracle_mod.OracleScene(sc)
+    p0 = o.member_positions()
+    for _ in range(500):
+        o.step(1)
+    b = o.get_bodies()
+    assert np.abs(b["angvel"][0] - [w0, 0, 0]).max() <= 1e-13
+    assert np.abs(o.member_positions() - p0).max() <= 1e-12
+    # quaternion: rotation by w0 t about x (the integrator of the sphere tests)
+    ang = np.arctan2(b["quat"][0, 1], b["quat"][0, 0]) * 2.0
+    assert abs(ang - w0 * 500 * 1e-3) <= 5e-6
+
+
+def test_gyroscopic_term_converges_at_first_order(oracle_mod):
+    """An asymmetric free body against Euler's torque-free equations
+    I0 dw_b/dt = -w_b x I0 w_b in the body frame, integrated by scipy to
+    1e-12: eq. (integrationscheme) with the explicit term -w x I w is first
+    order in dt, so the error of the body-frame w(T) halves with dt (a wrong
+    sign or a missing term converges to another motion)."""
+    from scipy.integrate import solve_ivp
+    T = 0.5
+    sc = scenes.spinning_body()
+    _, I0 = oracle_mod.OracleScene(sc).body_mass_properties()
+    I0, I0i = I0[0], np.linalg.inv(I0[0])
+    w0 = np.asarray(sc["angvel"][0])
+    ref = solve_ivp(lambda t, w: -I0i @ np.cross(w, I0 @ w), (0.0, T), w0, method="DOP853", rtol=1e-12,
+                    atol=1e-14).y[:, -1]
+
+    def err(dt):
+        o = oracle_mod.OracleScene(scenes.spinning_body(dt=dt))
+        for _ in range(int(round(T / dt))):
+            o.step(1)
+        b = o.get_bodies()
+        w, q = b["angvel"][0], b["quat"][0]
+        qw, qx, qy, qz = q
+        R = np.array([[1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)],
+                      [2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)],
+                      [2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)]])
+        return np.abs(R.T @ w - ref).max()
+
+    e1, e2 = err(T / 256), err(T / 512)
+    assert e1 < 0.05 * np.abs(w0).max()
+    assert 1.7 < e1 / e2 < 2.3
+
+
+def test_composite_momentum_conserved(oracle_mod):
+    sc = scenes.composite_gas(4, 4, 3, seed=2, spacing=1.02, v_max=1.0, walls=False, dt=2e-2,
+                              periodic=(1, 1, 1))
+    o = oracle_mod.OracleScene(sc)
+    invm, _ = o.body_mass_properties()
+    m = 1.0 / invm
+    P0 = (m[:, None] * o.get_bodies()["vel"]).sum(0)
+    scale = (m[:, None] * np.abs(sc["vel"])).sum()
+    total = 0
+    for _ in range(8):
+        total += o.step(20)["n_contacts"]
+        P1 = (m[:, None] * o.get_bodies()["vel"]).sum(0)
+        assert np.abs(P1 - P0).max() <= 1e-13 * scale
+    assert total > 50
+
+
+def test_composite_detection_against_kdtree(oracle_mod):
+    """Member pairs of different bodies within r_a + r_b + h_A + h_B, found
+    by scipy's kd-tree on the members' world positions, are the contacts."""
+    from scipy.spatial import cKDTree
+    sc = scenes.composite_gas(5, 4, 4, seed=4, spacing=1.02, v_max=1.0, dt=2e-2)
+    o = oracle_mod.OracleScene(sc)
+    for _ in range(3):
+        o.step(10)
+    b = o.get_bodies()
+    pm = o.member_positions()
+    mb, rad = sc["members"]["body"], sc["members"]["radius"]
+    prm = sc["params"]
+    rbar = np.zeros(len(b["pos"]))
+    invm, I0 = o.body_mass_properties()
+    # body hulls of eq. (expansionradius) with the bounding radius
+    for i in range(len(rbar)):
+        sel = mb == i
+        dd = np.linalg.norm(pm[sel] - b["pos"][i], axis=1) + rad[sel]
+        rbar[i] = dd.max()
+    h = prm["dt"] * (np.linalg.norm(b["vel"], axis=1) + np.linalg.norm(b["angvel"], axis=1) * rbar) + prm["tau"]
+    reach = rad.max() * 2 + 2 * h.max()
+    pairs = cKDTree(pm).query_pairs(reach, output_type="ndarray")
+    want = set()
+    for a_, b_ in pairs:
+        a_, b_ = min(a_, b_), max(a_, b_)
+        if mb[a_] == mb[b_]:
+            continue
+        d = np.linalg.norm(pm[a_] - pm[b_])
+        xi = d - rad[a_] - rad[b_]
+        if xi <= h[mb[a_]] + h[mb[b_]] - 1e-12 or abs(xi - (h[mb[a_]] + h[mb[b_]])) > 1e-9 and xi <= h[mb[a_]] + h[mb[b_]]:
+            want.add((a_, b_))
+    o.detect_contacts()
+    c = o.get_contacts()
+    nm = len(mb)
+    got = {(int(x), int(y)) for x, y in zip(c["j1"], c["j2"]) if y < nm}
+    assert len(want) > 20
+    assert want <= got and len(got - want) <= 2   # borderline pairs at rounding distance aside
