@@ -331,6 +331,36 @@ nbgs_status nbgs_get_contacts(nbgs_scene* scene, int64_t cap,
  * subdomains on a batch. */
 nbgs_status nbgs_set_subdomains(nbgs_scene* scene, int32_t mode, const int32_t* grid);
 
+/* Composite particles (Sect. 2: non-convex objects as composites of convex
+ * particles): n_bodies rigid bodies made of n_members member spheres.
+ * pos, vel, angvel: n_bodies x 3 (pos is each body's reference point);
+ * density: n_bodies; member_body: n_members, non-decreasing, every body with
+ * 1..4 members; member_offset: n_members x 3, from the reference point along
+ * the observational axes; member_radius: n_members.  All host pointers;
+ * copied in.  The members' masses and inertias add up (an overlap counts for
+ * every member it belongs to), m = sum density 4/3 pi r^3; the body's
+ * position becomes its centre of mass X = sum m_m d_m / m and its body-frame
+ * inertia about X is sum [2/5 m_m r_m^2 1 + m_m (|d'|^2 1 - d' d'^T)],
+ * d' = d - X; the bounding radius max |d'| + r enters the hull of
+ * eq. expansionradius; orientation starts at the identity.  Contacts join
+ * members of different bodies (j1 < j2 member indices) or a member and a
+ * wall (j2 = n_members + k); their levers are full vectors, so the
+ * one-contact problem has a full 3x3 Delassus block: separation, sticking,
+ * else the sliding root of the friction direction equation (a trigonometric
+ * polynomial of degree 2, bracketed by 64 samples and bisected; the valid
+ * root of least 1/2 p.W p + b.p).  The velocity step adds the gyroscopic
+ * term -w x I w of eq. integrationscheme.  nbgs_get_bodies and
+ * nbgs_set_bodies take bodies (n_bodies rows, centres of mass); colours,
+ * contacts and residual histories work as for spheres.  Not available for
+ * composites: cones, nbgs_set_mass_properties, subdomains, the network warm
+ * start, nbgs_final_residuals, checkpoints, nbgs_autotune, batches.
+ * NBGS_EINVAL on bad arguments; synchronises. */
+nbgs_status nbgs_create_composite_scene(const nbgs_params* params, int64_t n_bodies, const double* pos,
+                                        const double* vel, const double* angvel, const double* density,
+                                        int64_t n_members, const int32_t* member_body, const double* member_offset,
+                                        const double* member_radius, const nbgs_allocator* allocator, void* stream,
+                                        nbgs_scene** out);
+
 /* Subdomain s_c(j) of every contact of the last colouring, canonical order
  * (NBGS_SUB_GRID: the grid cell id; NBGS_SUB_JACOBI: the contact's index;
  * NBGS_SUB_NONE: 0).  out may be NULL; at most cap values are written;

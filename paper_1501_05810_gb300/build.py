@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnbgs.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["api.cu", "detect.cu", "colour.cu", "solve.cu", "integrate.cu", "mlp.cu", "noalloc.cu", "checkpoint.cu",
-           "subdomain.cu"]
+           "subdomain.cu", "composite.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code without FMA contraction: wall geometry computed on the host must
 # round exactly as written (GCC contracts by default on some targets)

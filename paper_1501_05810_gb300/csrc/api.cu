@@ -4,6 +4,7 @@
 #include <cstring>
 #include <new>
 #include <utility>
+#include <vector>
 
 #include "nbgs_internal.cuh"
 
@@ -222,6 +223,131 @@ nbgs_status nbgs_create_batch(const nbgs_params* params, const nbgs_batch_desc* 
     return create_common(params, batch, n_bodies, pos, vel, angvel, radius, density, allocator, stream, out);
 }
 
+nbgs_status nbgs_create_composite_scene(const nbgs_params* params, int64_t n_bodies, const double* pos,
+                                        const double* vel, const double* angvel, const double* density,
+                                        int64_t n_members, const int32_t* member_body, const double* member_offset,
+                                        const double* member_radius, const nbgs_allocator* allocator, void* stream,
+                                        nbgs_scene** out)
+{
+    if (!params || !out || n_bodies < 1 || n_members < n_bodies || n_members > 0x7FFFFFF0LL || !pos || !vel ||
+        !angvel || !density || !member_body || !member_offset || !member_radius)
+        return NBGS_EINVAL;
+    if (params->subdomain_mode != NBGS_SUB_NONE || params->warm_start == NBGS_WARM_MLP) return NBGS_EINVAL;
+    const int64_t nb = n_bodies, nm = n_members;
+    if (member_body[0] != 0 || member_body[nm - 1] != nb - 1) return NBGS_EINVAL;
+    for (int64_t m = 0; m < nm; ++m) {
+        if (!(member_radius[m] > 0.0)) return NBGS_EINVAL;
+        if (m > 0 && (member_body[m] < member_body[m - 1] || member_body[m] > member_body[m - 1] + 1))
+            return NBGS_EINVAL;
+    }
+    // mass properties on the host, rounded as the oracle writes them: the
+    // members' masses and inertias add up; the body's position is its centre
+    // of mass; the bounding radius max |d'| + r enters the hull
+    std::vector<double> bpos(4 * nb), I0(9 * nb), I0inv(9 * nb), invm(nb), moff(4 * nm), mzero(3 * nm, 0.0),
+        ones(nm, 1.0);
+    std::vector<uint32_t> mbody(nm);
+    std::vector<uint8_t> bfin(nb);
+    int64_t m0 = 0;
+    for (int64_t i = 0; i < nb; ++i) {
+        int64_t m1 = m0;
+        while (m1 < nm && member_body[m1] == i) ++m1;
+        if (m1 - m0 > kMaxMembers) return NBGS_EINVAL;
+        double M = 0.0, X[3] = {0.0, 0.0, 0.0};
+        for (int64_t m = m0; m < m1; ++m) {
+            const double r = member_radius[m];
+            const double mm = density[i] * (4.0 / 3.0) * 3.14159265358979323846 * r * r * r;
+            M += mm;
+            for (int e = 0; e < 3; ++e) X[e] += mm * member_offset[3 * m + e];
+        }
+        for (int e = 0; e < 3; ++e) X[e] = X[e] / M;
+        double* I = &I0[9 * i];
+        double rbar = 0.0;
+        for (int64_t m = m0; m < m1; ++m) {
+            const double r = member_radius[m];
+            const double mm = density[i] * (4.0 / 3.0) * 3.14159265358979323846 * r * r * r;
+            double d[3];
+            for (int e = 0; e < 3; ++e) d[e] = member_offset[3 * m + e] - X[e];
+            const double d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) I[3 * a + b] += (a == b ? 0.4 * mm * r * r + mm * d2 : 0.0) - mm * d[a] * d[b];
+            mbody[m] = (uint32_t)i;
+            for (int e = 0; e < 3; ++e) moff[4 * m + e] = d[e];
+            moff[4 * m + 3] = r;
+            const double reach = std::sqrt(d2) + r;
+            if (reach > rbar) rbar = reach;
+        }
+        for (int e = 0; e < 3; ++e) bpos[4 * i + e] = pos[3 * i + e] + X[e];
+        bpos[4 * i + 3] = rbar;
+        invm[i] = M > 0.0 ? 1.0 / M : 0.0;
+        bfin[i] = M > 0.0 ? 1 : 0;
+        // inverse by cofactors (positive definite)
+        const double* A = I;
+        double* Ai = &I0inv[9 * i];
+        const double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+        const double det = (A[0] * c00 + A[1] * c01) + A[2] * c02;
+        if (M > 0.0 && !(det > 0.0)) return NBGS_EINVAL;
+        if (M > 0.0) {
+            Ai[0] = c00 / det; Ai[1] = (A[2] * A[7] - A[1] * A[8]) / det; Ai[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+            Ai[3] = c01 / det; Ai[4] = (A[0] * A[8] - A[2] * A[6]) / det; Ai[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+            Ai[6] = c02 / det; Ai[7] = (A[1] * A[6] - A[0] * A[7]) / det; Ai[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+        }
+        m0 = m1;
+    }
+    // the detection machinery sized for the members (as spheres at the origin)
+    nbgs_scene* s = nullptr;
+    nbgs_status rc = create_common(params, nullptr, nm, mzero.data(), mzero.data(), mzero.data(), member_radius,
+                                   ones.data(), allocator, stream, &s);
+    if (rc != NBGS_OK) return rc;
+    s->composite = true;
+    s->nb = nb;
+    const size_t v4 = s->fp32 ? 16 : 32;
+    bool ok = take(s, s->bpos, (size_t)nb) && take(s, s->bquat, (size_t)nb) && take(s, s->bI0, 9 * (size_t)nb) &&
+              take(s, s->bI0inv, 9 * (size_t)nb) && take(s, s->bIinv, 6 * (size_t)nb) && take(s, s->binvm, (size_t)nb) &&
+              take(s, s->bfinite, (size_t)nb) && take(s, s->mbody, (size_t)nm) && take(s, s->moff, (size_t)nm);
+    if (ok) {
+        s->bvel = dev_alloc(s, 4 * (size_t)nb * v4);
+        ok = s->bvel != nullptr;
+    }
+    if (!ok) {
+        nbgs_destroy_scene(s);
+        return NBGS_ENOMEM;
+    }
+    std::vector<double> q(4 * nb, 0.0);
+    for (int64_t i = 0; i < nb; ++i) q[4 * i] = 1.0;
+    // body records: (v, 1/m), (w, 0); the inverse inertia rows are set each step
+    std::vector<unsigned char> bv(4 * (size_t)nb * v4, 0);
+    for (int64_t i = 0; i < nb; ++i) {
+        const double vals[8] = {vel[3 * i], vel[3 * i + 1], vel[3 * i + 2], invm[i],
+                                angvel[3 * i], angvel[3 * i + 1], angvel[3 * i + 2], 0.0};
+        for (int k = 0; k < 8; ++k) {
+            if (s->fp32) {
+                const float f = (float)vals[k];
+                std::memcpy(&bv[4 * i * v4 + 4 * k], &f, 4);
+            } else {
+                std::memcpy(&bv[4 * i * v4 + 8 * k], &vals[k], 8);
+            }
+        }
+    }
+    cudaStream_t st = s->stream;
+    cudaMemcpyAsync(s->bpos, bpos.data(), bpos.size() * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->bquat, q.data(), q.size() * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->bI0, I0.data(), I0.size() * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->bI0inv, I0inv.data(), I0inv.size() * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->binvm, invm.data(), invm.size() * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->bfinite, bfin.data(), bfin.size(), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->mbody, mbody.data(), mbody.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->moff, moff.data(), moff.size() * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->bvel, bv.data(), bv.size(), cudaMemcpyHostToDevice, st);
+    rc = ensure_composite_buffers(s);
+    if (rc == NBGS_OK) rc = cuda_check(s, cudaStreamSynchronize(st), "create_composite_scene");
+    if (rc != NBGS_OK) {
+        nbgs_destroy_scene(s);
+        return rc;
+    }
+    *out = s;
+    return NBGS_OK;
+}
+
 static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_desc* batch, int64_t n,
                                  const double* pos, const double* vel, const double* angvel, const double* radius,
                                  const double* density, const nbgs_allocator* allocator, void* stream,
@@ -438,6 +564,7 @@ void nbgs_destroy_scene(nbgs_scene* s)
     for (void* p : ps) dev_free(s, p);
     free_contact_arrays(s);
     free_subdomain_buffers(s);
+    free_composite_buffers(s);
     cudaStreamSynchronize(s->stream);
     if (s->hinfo) cudaFreeHost(s->hinfo);
     for (int k = 0; k < 10; ++k)
@@ -469,7 +596,7 @@ nbgs_status nbgs_add_cone(nbgs_scene* s, const double apex[3], const double axis
                           double r_orifice, double r_top)
 {
     NBGS_GUARD(s);
-    if (s->batch) return fail(s, NBGS_EINVAL, "add_cone: batched scenes take no cones");
+    if (s->batch || s->composite) return fail(s, NBGS_EINVAL, "add_cone: batches and composite scenes take no cones");
     if (!apex || !axis || s->planes.ncones >= kMaxCones) return fail(s, NBGS_EINVAL, "add_cone: bad cone or too many");
     if (!(half_angle > 0.0 && half_angle < 1.5707963267948966) || !(r_orifice >= 0.0) || !(r_top > r_orifice))
         return fail(s, NBGS_EINVAL, "add_cone: need 0 < half_angle < pi/2 and 0 <= r_orifice < r_top");
@@ -493,6 +620,7 @@ nbgs_status nbgs_add_cone(nbgs_scene* s, const double apex[3], const double axis
 nbgs_status nbgs_set_mass_properties(nbgs_scene* s, const double* invm, const double* invI)
 {
     NBGS_GUARD(s);
+    if (s->composite) return fail(s, NBGS_EINVAL, "set_mass_properties: composites take theirs from the members");
     return run_set_mass(s, invm, invI, false, nullptr, nullptr);
 }
 
@@ -590,6 +718,8 @@ nbgs_status nbgs_set_warm_start(nbgs_scene* s, int32_t warm_start)
 {
     NBGS_GUARD(s);
     if (warm_start < NBGS_WARM_NONE || warm_start > NBGS_WARM_MLP) return fail(s, NBGS_EINVAL, "set_warm_start: mode");
+    if (s->composite && warm_start == NBGS_WARM_MLP)
+        return fail(s, NBGS_EINVAL, "set_warm_start: the network takes sphere contacts only");
     s->prm.warm_start = warm_start;
     return NBGS_OK;
 }
@@ -601,7 +731,8 @@ nbgs_status nbgs_set_subdomains(nbgs_scene* s, int32_t mode, const int32_t grid[
     const int32_t* g = grid ? grid : one;
     if (!subdomains_valid(mode, g) || (mode == NBGS_SUB_GRID && !grid))
         return fail(s, NBGS_EINVAL, "set_subdomains: bad mode or grid");
-    if (s->batch && mode != NBGS_SUB_NONE) return fail(s, NBGS_EINVAL, "set_subdomains: batched scenes have none");
+    if ((s->batch || s->composite) && mode != NBGS_SUB_NONE)
+        return fail(s, NBGS_EINVAL, "set_subdomains: batches and composite scenes have none");
     s->prm.subdomain_mode = mode;
     for (int a = 0; a < 3; ++a) s->prm.subdomains[a] = g[a];
     s->coloured = false;   // s_c(j), the colours and the sweep records follow the mode
@@ -642,6 +773,7 @@ nbgs_status nbgs_batch_step(nbgs_scene* s, int32_t max_sweeps, double tol, int32
 nbgs_status nbgs_autotune(nbgs_scene* s, int32_t max_sweeps, double tol, int32_t* sweep_flags, int32_t* blocks_per_sm)
 {
     NBGS_GUARD(s);
+    if (s->composite) return fail(s, NBGS_EINVAL, "autotune: composite scenes have one schedule");
     if (!s->detected) return fail(s, NBGS_EINVAL, "autotune: call detect_contacts first");
     if (s->prm.solver != NBGS_SOLVER_PERSISTENT || s->max_coop_blocks == 0)
         return fail(s, NBGS_EINVAL, "autotune: needs the persistent solver");
@@ -752,6 +884,7 @@ nbgs_status nbgs_final_residuals(nbgs_scene* s, nbgs_residuals* out)
 {
     NBGS_GUARD(s);
     if (!out) return fail(s, NBGS_EINVAL, "final_residuals: null output");
+    if (s->composite) return fail(s, NBGS_EINVAL, "final_residuals: sphere scenes only");
     nbgs_status rc = run_final_residuals(s, out);
     if (rc == NBGS_OK) rc = check_device_errors(s);
     return rc;

@@ -67,7 +67,7 @@ nbgs_status d2h(nbgs_scene* s, std::vector<T>& h, const void* d, size_t count)
 nbgs_status run_save_state(nbgs_scene* s, const char* path)
 {
     if (!path) return fail(s, NBGS_EINVAL, "save_state: null path");
-    if (s->batch) return fail(s, NBGS_EINVAL, "save_state: batched scenes are not supported");
+    if (s->batch || s->composite) return fail(s, NBGS_EINVAL, "save_state: batched and composite scenes are not supported");
     const int64_t n = s->n;
     const size_t vbytes = s->fp32 ? 16 : 32;
     // the contacts the next step's warm start reads: the last solved step's
@@ -124,7 +124,7 @@ nbgs_status grow_contacts(nbgs_scene* s, int64_t need);  // api.cu
 nbgs_status run_load_state(nbgs_scene* s, const char* path)
 {
     if (!path) return fail(s, NBGS_EINVAL, "load_state: null path");
-    if (s->batch) return fail(s, NBGS_EINVAL, "load_state: batched scenes are not supported");
+    if (s->batch || s->composite) return fail(s, NBGS_EINVAL, "load_state: batched and composite scenes are not supported");
     File f;
     f.f = fopen(path, "rb");
     if (!f.f) return fail(s, NBGS_EINVAL, std::string("load_state: cannot open ") + path);

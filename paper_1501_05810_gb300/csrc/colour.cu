@@ -41,14 +41,18 @@ __device__ __forceinline__ uint64_t local_key(uint32_t a, uint32_t b, const Scen
     return ((uint64_t)(a - off) << 32) | lb;
 }
 
+// Priorities from the contacts' keys; body degrees from the incidence ends
+// ib1, ib2 (the contact's bodies: the contact ends themselves for spheres,
+// the members' bodies for composites; >= n marks a wall).
 __global__ void k_colour_init(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
+                              const uint32_t* __restrict__ ib1, const uint32_t* __restrict__ ib2,
                               const uint8_t* __restrict__ finite, uint64_t seed, SceneView V, uint32_t* __restrict__ deg,
                               uint64_t* __restrict__ prio, uint32_t* __restrict__ cstate)
 {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t a = cj1[c], b = cj2[c];
-        prio[c] = splitmix64(local_key(a, b, V) ^ seed);
+        prio[c] = splitmix64(local_key(cj1[c], cj2[c], V) ^ seed);
         cstate[c] = kUncoloured;
+        const uint32_t a = ib1[c], b = ib2[c];
         if (finite[a]) atomicAdd(&deg[a], 1u);
         if (b < n && finite[b]) atomicAdd(&deg[b], 1u);
     }
@@ -66,13 +70,11 @@ __global__ void k_adj_fill(int64_t C, int64_t n, const uint32_t* __restrict__ cj
 }
 
 // (prio, key) of d beats that of c: higher priority, ties to the lower key.
-__device__ __forceinline__ bool beats(uint64_t pd, uint32_t d, uint64_t pc, uint32_t c, const uint32_t* cj1,
-                                      const uint32_t* cj2)
+// Contacts are stored in canonical order, so the lower index is the lower key.
+__device__ __forceinline__ bool beats(uint64_t pd, uint32_t d, uint64_t pc, uint32_t c)
 {
     if (pd != pc) return pd > pc;
-    const uint64_t kd = ((uint64_t)cj1[d] << 32) | cj2[d];
-    const uint64_t kc = ((uint64_t)cj1[c] << 32) | cj2[c];
-    return kd < kc;
+    return d < c;
 }
 
 // Colouring by waiting lists.  First-fit greedy colouring in decreasing
@@ -149,7 +151,7 @@ __global__ void k_pred_count(int64_t C, int64_t n, const uint32_t* __restrict__ 
         uint32_t k = 0;
         for (uint32_t j = 0; j < na + nb; ++j) {
             const uint32_t d = incident(adj, a0, na, b0, j);
-            if (d != (uint32_t)c && beats(prio[d], d, pc, (uint32_t)c, cj1, cj2)) {
+            if (d != (uint32_t)c && beats(prio[d], d, pc, (uint32_t)c)) {
                 ++k;
                 if (j < 64) m |= 1ull << j;
             }
@@ -191,7 +193,7 @@ __global__ void k_pred_lists(int64_t C, int64_t n, const uint32_t* __restrict__ 
                 if (m != ~0ull && !((m >> j) & 1ull)) continue;
                 const uint32_t d = incident(adj, a0, na, b0, j);
                 const uint64_t pd = prio[d];
-                if (m == ~0ull && (d == (uint32_t)c || !beats(pd, d, pc, (uint32_t)c, cj1, cj2))) continue;
+                if (m == ~0ull && (d == (uint32_t)c || !beats(pd, d, pc, (uint32_t)c))) continue;
                 preds[p0 + k] = make_uint2(d, prio_hi(pd));
                 if (pd < pweak) {
                     pweak = pd;
@@ -478,13 +480,23 @@ nbgs_status run_colour(nbgs_scene* s)
     if (C > 0) {
         const int T = 256;
         const int gb = grid_for(C, T, 8, s->num_sms);
-        cudaMemsetAsync(s->deg, 0, (n + 1) * sizeof(uint32_t), st);
-        k_colour_init<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->prm.colour_seed, scene_view(s), s->deg,
-                                        s->cprio, s->cstate);
-        nbgs_status rc = exclusive_scan_u32(s, s->deg, s->adj_off, n, nullptr);
+        // the conflict graph: contacts sharing a body of finite mass (for
+        // composites the body of a member, not the member)
+        if (s->composite) {
+            nbgs_status rc = run_comp_ends(s);
+            if (rc != NBGS_OK) return rc;
+        }
+        const uint32_t* ib1 = s->composite ? s->cb1 : s->cj1;
+        const uint32_t* ib2 = s->composite ? s->cb2 : s->cj2;
+        const uint8_t* finc = s->composite ? s->bfinite : s->finite;
+        const int64_t ninc = s->composite ? s->nb : n;
+        cudaMemsetAsync(s->deg, 0, (ninc + 1) * sizeof(uint32_t), st);
+        k_colour_init<<<gb, T, 0, st>>>(C, ninc, s->cj1, s->cj2, ib1, ib2, finc, s->prm.colour_seed, scene_view(s),
+                                        s->deg, s->cprio, s->cstate);
+        nbgs_status rc = exclusive_scan_u32(s, s->deg, s->adj_off, ninc, nullptr);
         if (rc != NBGS_OK) return rc;
-        cudaMemsetAsync(s->deg, 0, (n + 1) * sizeof(uint32_t), st);
-        k_adj_fill<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->deg, s->adj);
+        cudaMemsetAsync(s->deg, 0, (ninc + 1) * sizeof(uint32_t), st);
+        k_adj_fill<<<gb, T, 0, st>>>(C, ninc, ib1, ib2, finc, s->adj_off, s->deg, s->adj);
         if (sub) {
             rc = run_subdomains(s);
             if (rc != NBGS_OK) return rc;
@@ -496,7 +508,7 @@ nbgs_status run_colour(nbgs_scene* s)
             cudaMemsetAsync(s->cstate, 0, C * sizeof(uint32_t), st);
         } else {
             // predecessor lists (counts, offsets, lists weakest first)
-            k_pred_count<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->adj, s->cprio, s->pmask,
+            k_pred_count<<<gb, T, 0, st>>>(C, ninc, ib1, ib2, finc, s->adj_off, s->adj, s->cprio, s->pmask,
                                            s->colour_key);
             rc = exclusive_scan_u32(s, s->colour_key, s->poff, C, nullptr);
             if (rc != NBGS_OK) return rc;
@@ -510,7 +522,7 @@ nbgs_status run_colour(nbgs_scene* s)
             // waiting lists empty; round-1 counters (|L| = 0, |X| filled below)
             cudaMemsetAsync(s->whead, 0xFF, C * sizeof(uint32_t), st);
             cudaMemsetAsync(s->info->wl_count, 0, sizeof(s->info->wl_count), st);
-            k_pred_lists<<<gb, T, 0, st>>>(C, n, s->cj1, s->cj2, s->finite, s->adj_off, s->adj, s->cprio, s->pmask,
+            k_pred_lists<<<gb, T, 0, st>>>(C, ninc, ib1, ib2, finc, s->adj_off, s->adj, s->cprio, s->pmask,
                                            s->poff, s->preds, s->whead, s->wnext, s->wl[0], &s->info->wl_count[1]);
             if (s->timing) s->phase_launches[1] += 9;
             // rounds; the host checks the lists every few rounds
@@ -550,7 +562,10 @@ nbgs_status run_colour(nbgs_scene* s)
         if (v0 != s->perm) return fail(s, NBGS_EINVAL, "colour: permutation buffer mix-up");
         s->colour_sorted = k0;
         const int warm = (s->prm.warm_start != NBGS_WARM_NONE && s->have_prev) ? 1 : 0;
-        if (s->fp32)
+        if (s->composite) {
+            rc = run_comp_records(s, warm);
+            if (rc != NBGS_OK) return rc;
+        } else if (s->fp32)
             k_build_sweep<float><<<gb, T, 0, st>>>(C, n, s->perm, s->cj1, s->cj2, sub ? s->inst : nullptr, s->cgeo,
                                                    s->clev, s->prm.dt,
                                                    s->prm.beta, s->prm.mu, scene_view(s), warm, s->prev_row_off,

@@ -278,6 +278,82 @@ __device__ __forceinline__ double norm_exact(double x, double y, double z)
     return xsqrt(xadd(xadd(xmul(x, x), xmul(y, y)), xmul(z, z)));
 }
 
+// Composite particles: the members' world positions X + R(q) d (FP64, each
+// operation rounded as written: the contact geometry depends on them bit for
+// bit), their bodies' hulls h = dt (|v| + |w| r_bound) + tau (eq.
+// expansionradius with the bounding radius) and the FP32 copies for the cell
+// grid, wrapped into the box on periodic axes (the FP64 positions stay
+// unwrapped; the exact tests take minimum images of differences).
+template <class R>
+__global__ void k_member_update(int64_t n, const uint32_t* __restrict__ mbody, const double4_32a* __restrict__ moff,
+                                const double4_32a* __restrict__ bpos, const double4_32a* __restrict__ bquat,
+                                const R4<R>* __restrict__ bvel, double dt, double tau,
+                                double4_32a* __restrict__ pos_r, double* __restrict__ hull, float4* __restrict__ p32,
+                                GridArgs g, DevInfo* info)
+{
+    double hmax = 0.0, vmax = 0.0;
+    bool bad = false;
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = mbody[m];
+        const double4_32a X = ld_d4(bpos + b), q = ld_d4(bquat + b), d = ld_d4(moff + m);
+        const R4<R> v = bvel[4 * (int64_t)b], w = bvel[4 * (int64_t)b + 1];
+        // R(q) rows, as 1 - 2 (y^2 + z^2), 2 (xy - wz), ... (unit quaternion)
+        const double qw = q.x, qx = q.y, qy = q.z, qz = q.w;
+        const double r00 = xsub(1.0, xmul(2.0, xadd(xmul(qy, qy), xmul(qz, qz))));
+        const double r01 = xmul(2.0, xsub(xmul(qx, qy), xmul(qw, qz)));
+        const double r02 = xmul(2.0, xadd(xmul(qx, qz), xmul(qw, qy)));
+        const double r10 = xmul(2.0, xadd(xmul(qx, qy), xmul(qw, qz)));
+        const double r11 = xsub(1.0, xmul(2.0, xadd(xmul(qx, qx), xmul(qz, qz))));
+        const double r12 = xmul(2.0, xsub(xmul(qy, qz), xmul(qw, qx)));
+        const double r20 = xmul(2.0, xsub(xmul(qx, qz), xmul(qw, qy)));
+        const double r21 = xmul(2.0, xadd(xmul(qy, qz), xmul(qw, qx)));
+        const double r22 = xsub(1.0, xmul(2.0, xadd(xmul(qx, qx), xmul(qy, qy))));
+        double4_32a p;
+        p.x = xadd(X.x, xadd(xadd(xmul(r00, d.x), xmul(r01, d.y)), xmul(r02, d.z)));
+        p.y = xadd(X.y, xadd(xadd(xmul(r10, d.x), xmul(r11, d.y)), xmul(r12, d.z)));
+        p.z = xadd(X.z, xadd(xadd(xmul(r20, d.x), xmul(r21, d.y)), xmul(r22, d.z)));
+        p.w = d.w;
+        st_d4(pos_r + m, p);
+        const double nv = norm_exact((double)v.x, (double)v.y, (double)v.z);
+        const double nw = norm_exact((double)w.x, (double)w.y, (double)w.z);
+        const double h = xadd(xmul(dt, xadd(nv, xmul(nw, X.w))), tau);
+        hull[m] = h;
+        double rel[3] = {p.x - g.lo[0], p.y - g.lo[1], p.z - g.lo[2]};
+        for (int a = 0; a < 3; ++a) {
+            const double L = g.hi[a] - g.lo[a];
+            if (g.periodic[a] && !(rel[a] >= 0.0 && rel[a] < L)) {
+                double sft = fmod(rel[a], L);
+                if (sft < 0.0) sft += L;
+                rel[a] = sft;
+            }
+        }
+        p32[m] = make_float4((float)rel[0], (float)rel[1], (float)rel[2], (float)(p.w + h));
+        if (!(h <= 1e300)) bad = true;
+        hmax = fmax(hmax, h);
+        vmax = fmax(vmax, nv);
+    }
+    __shared__ double sh[2][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        hmax = fmax(hmax, __shfl_down_sync(0xffffffffu, hmax, o));
+        vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
+    }
+    if (lane == 0) {
+        sh[0][wid] = hmax;
+        sh[1][wid] = vmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            hmax = fmax(hmax, sh[0][k]);
+            vmax = fmax(vmax, sh[1][k]);
+        }
+        atomicMax(&info->hmax_bits, (unsigned long long)__double_as_longlong(hmax));
+        atomicMax(&info->vmax_bits, (unsigned long long)__double_as_longlong(vmax));
+    }
+    if (bad) atomicOr(&info->err, kErrNaN);
+}
+
 template <class R>
 __global__ void k_hull(int64_t n, const R4<R>* __restrict__ vel, const double4_32a* __restrict__ pos_r, double dt,
                        double tau, double* __restrict__ hull, float4* __restrict__ p32, GridArgs g, DevInfo* info,
@@ -495,6 +571,7 @@ __device__ __forceinline__ void narrow_range(uint32_t t0, uint32_t t1, float sx,
         const uint32_t j = svals[t];
         if (j <= i) continue;
         if (V.batch && V.scene_of[j] != si) continue;   // scenes never touch
+        if (V.body_of && V.body_of[j] == V.body_of[i]) continue;   // members of one body never touch
         // Conservative FP32 pre-filter (FP64 throughput is scarce on this GPU).
         // R = r_a + h_a + r_b + h_b bounds d for every kept pair.  The FP32
         // relative positions are off by at most pos_err per coordinate, the
@@ -713,6 +790,7 @@ SceneView scene_view(const nbgs_scene* s)
     v.box32 = s->scene_box32;
     v.mu = s->scene_mu;
     v.vref = s->scene_vref;
+    v.body_of = s->composite ? s->mbody : nullptr;
     return v;
 }
 
@@ -796,7 +874,15 @@ nbgs_status run_detect(nbgs_scene* s)
     const int T = 256;
     const int gb = grid_for(n, T, 8, s->num_sms);
     if (s->batch) cudaMemsetAsync(s->scene_vmax, 0, s->n_scenes * sizeof(unsigned long long), st);
-    if (s->fp32)
+    if (s->composite) {
+        if (s->fp32)
+            k_member_update<float><<<gb, T, 0, st>>>(n, s->mbody, s->moff, s->bpos, s->bquat, (const float4*)s->bvel,
+                                                     s->prm.dt, s->prm.tau, s->pos_r, s->hull, s->p32, g, s->info);
+        else
+            k_member_update<double><<<gb, T, 0, st>>>(n, s->mbody, s->moff, s->bpos, s->bquat,
+                                                      (const double4_32a*)s->bvel, s->prm.dt, s->prm.tau, s->pos_r,
+                                                      s->hull, s->p32, g, s->info);
+    } else if (s->fp32)
         k_hull<float><<<gb, T, 0, st>>>(n, (const float4*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hull, s->p32,
                                         g, s->info, s->scene_of, s->scene_vmax);
     else

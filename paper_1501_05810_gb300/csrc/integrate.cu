@@ -64,6 +64,7 @@ __global__ void k_integrate(int64_t n, double4_32a* __restrict__ pos_r, double4_
 
 nbgs_status run_integrate(nbgs_scene* s)
 {
+    if (s->composite) return run_integrate_comp(s);
     if (s->n == 0) return NBGS_OK;
     cudaStream_t st = s->stream;
     if (s->timing) cudaEventRecord(s->ev[6], st);
@@ -211,12 +212,14 @@ static nbgs_status set_bodies_impl(nbgs_scene* s, const double* pos, const doubl
 nbgs_status run_set_bodies(nbgs_scene* s, const double* pos, const double* quat, const double* vel,
                            const double* angvel)
 {
+    if (s->composite) return run_comp_set_bodies(s, pos, quat, vel, angvel);
     if (s->n == 0) return NBGS_OK;
     return s->fp32 ? set_bodies_impl<float>(s, pos, quat, vel, angvel) : set_bodies_impl<double>(s, pos, quat, vel, angvel);
 }
 
 nbgs_status run_get_bodies(nbgs_scene* s, double* pos, double* quat, double* vel, double* angvel)
 {
+    if (s->composite) return run_comp_get_bodies(s, pos, quat, vel, angvel);
     const int64_t n = s->n;
     if (n == 0) return NBGS_OK;
     cudaStream_t st = s->stream;

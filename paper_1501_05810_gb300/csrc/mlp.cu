@@ -630,6 +630,7 @@ static WarmArgs<R> warm_args(nbgs_scene* s, int apply, float* feat_out)
 // contacts; runs before the sweeps (after colouring, before the gravity kick).
 nbgs_status run_mlp_prologue(nbgs_scene* s, int apply, float* feat_out)
 {
+    if (s->composite) return fail(s, NBGS_EINVAL, "MLP: the network takes sphere contacts only");
     const int64_t C = s->n_contacts;
     if (C <= 0) return NBGS_OK;
     if (apply && !s->mlp_theta) return fail(s, NBGS_EINVAL, "MLP warm start: no network loaded (nbgs_mlp_load)");

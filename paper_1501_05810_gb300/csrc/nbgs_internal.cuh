@@ -44,6 +44,7 @@ enum : uint32_t {
 };
 
 constexpr int kMaxCones = 4;
+constexpr int kMaxMembers = 4;          // member spheres of a composite particle
 
 // Conical hopper wall (frustum between the orifice and the top circle);
 // sin and cos of the half-angle come from the host's C library.
@@ -74,6 +75,7 @@ struct SceneView {
     const float* box32;           // S x 6: box - global box lo, FP32 (the wall pre-filter)
     const double* mu;             // S
     const double* vref;           // S
+    const uint32_t* body_of;      // composite scenes: body of each member sphere (null otherwise)
 };
 
 // Wall k of body i's scene: k < nplanes are the shared planes, then the six
@@ -379,6 +381,24 @@ struct nbgs_scene {
     int64_t sub_ccap = 0;          // contacts the subdomain arrays hold
     int64_t sub_count = -1;        // contacts csub describes (-1: none since the last detection)
     int64_t icap = 0;              // extra instance records allocated after the n bodies in vel
+    // composite particles: the detection spheres (n of them) are the members
+    // of nb rigid bodies; contacts join members, the sweeps act on bodies
+    bool composite = false;
+    int64_t nb = 0;
+    double4_32a* bpos = nullptr;   // nb: centre of mass, bounding radius
+    double4_32a* bquat = nullptr;  // nb: orientation (w, x, y, z)
+    void* bvel = nullptr;          // R4[4 nb]: (v, 1/m), (w, 0), (Ixx, Iyy, Izz, Ixy), (Ixz, Iyz, 0, 0) of I^-1 (world)
+    double* bI0 = nullptr;         // 9 nb: body-frame inertia about the centre of mass
+    double* bI0inv = nullptr;      // 9 nb: its inverse
+    double* bIinv = nullptr;       // 6 nb: world inverse inertia of the current orientation (FP64)
+    double* binvm = nullptr;       // nb: 1/m (FP64)
+    uint8_t* bfinite = nullptr;    // nb
+    uint32_t* mbody = nullptr;     // n: body of each member
+    double4_32a* moff = nullptr;   // n: body-frame offset from the centre of mass, radius
+    uint32_t* cb1 = nullptr;       // comp_ccap: body of contact end j1
+    uint32_t* cb2 = nullptr;       // comp_ccap: body of contact end j2 (nb: a wall)
+    void* crec = nullptr;          // comp_ccap composite sweep records (colour order)
+    int64_t comp_ccap = 0;
     // learned warm start
     float* mlp_theta = nullptr;    // 9,347 FP32 parameters
     // sweep
@@ -424,6 +444,16 @@ nbgs_status ensure_subdomain_buffers(nbgs_scene* s);  // subdomain.cu
 void free_subdomain_buffers(nbgs_scene* s);          // subdomain.cu
 nbgs_status run_get_subdomains(nbgs_scene* s, int64_t cap, uint32_t* out);
 bool subdomains_valid(int32_t mode, const int32_t g[3]);   // api.cu
+// composite particles (composite.cu)
+nbgs_status ensure_composite_buffers(nbgs_scene* s);
+nbgs_status run_comp_ends(nbgs_scene* s);               // bodies of the contact ends (colouring)
+nbgs_status run_comp_records(nbgs_scene* s, int warm);   // after colouring: inverse inertias, sweep records
+nbgs_status run_solve_comp(nbgs_scene* s, int max_sweeps, double tol);
+nbgs_status run_integrate_comp(nbgs_scene* s);
+nbgs_status run_comp_get_bodies(nbgs_scene* s, double* pos, double* quat, double* vel, double* angvel);
+nbgs_status run_comp_set_bodies(nbgs_scene* s, const double* pos, const double* quat, const double* vel,
+                                const double* angvel);
+void free_composite_buffers(nbgs_scene* s);
 nbgs_status run_set_bodies(nbgs_scene* s, const double* pos, const double* quat, const double* vel,
                            const double* angvel);
 nbgs_status run_get_bodies(nbgs_scene* s, double* pos, double* quat, double* vel, double* angvel);

@@ -1250,7 +1250,9 @@ nbgs_status run_solve(nbgs_scene* s, int max_sweeps, double tol)
     if (max_sweeps < 0) return fail(s, NBGS_EINVAL, "solve: max_sweeps < 0");
     cudaStream_t st = s->stream;
     if (s->timing) cudaEventRecord(s->ev[4], st);
-    nbgs_status rc = s->fp32 ? solve_impl<float>(s, max_sweeps, tol) : solve_impl<double>(s, max_sweeps, tol);
+    nbgs_status rc = s->composite ? run_solve_comp(s, max_sweeps, tol)
+                     : s->fp32    ? solve_impl<float>(s, max_sweeps, tol)
+                                  : solve_impl<double>(s, max_sweeps, tol);
     if (rc != NBGS_OK) return rc;
     if (s->timing) cudaEventRecord(s->ev[5], st);
     const int64_t C = s->n_contacts;

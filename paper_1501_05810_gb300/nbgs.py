@@ -92,6 +92,8 @@ _SIG = {
     "nbgs_mlp_load": [_vp, _vp, C.c_int64],
     "nbgs_set_warm_start": [_vp, C.c_int32],
     "nbgs_set_subdomains": [_vp, C.c_int32, _i32p],
+    "nbgs_create_composite_scene": [_P(nbgs_params), C.c_int64, _vp, _vp, _vp, _vp, C.c_int64, _vp, _vp, _vp,
+                                    _P(nbgs_allocator), _vp, _P(_vp)],
     "nbgs_get_subdomains": [_vp, C.c_int64, _u32p, _i64p],
     "nbgs_mlp_features": [_vp, _vp, C.c_int64, _i64p],
     "nbgs_mlp_infer": [_vp, _vp, _vp, C.c_int64, _vp],
@@ -227,14 +229,31 @@ class Scene:
         import torch
         self.torch = torch
         self.device = torch.device(device)
-        self.n = int(len(scene["radius"]))
+        self.composite = "members" in scene
+        self.n = int(len(scene["pos"]))   # bodies (spheres, or composites)
         self.params = make_params(scene["params"], solver)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.allocator = TorchAllocator(self.device) if use_torch_allocator else None
-        arrs = [np.ascontiguousarray(scene[k], dtype=np.float64) for k in ("pos", "vel", "angvel", "radius", "density")]
-        with torch.cuda.device(self.device):
-            st, h = nbgs_create_scene(self.params, self.n, *[_ptr(a) for a in arrs],
-                                      self.allocator.struct if self.allocator else None, self.stream.cuda_stream)
+        alloc = self.allocator.struct if self.allocator else None
+        if self.composite:
+            mem = scene["members"]
+            arrs = [np.ascontiguousarray(scene[k], dtype=np.float64) for k in ("pos", "vel", "angvel", "density")]
+            mb = np.ascontiguousarray(mem["body"], dtype=np.int32)
+            mo = np.ascontiguousarray(mem["offset"], dtype=np.float64)
+            mr = np.ascontiguousarray(mem["radius"], dtype=np.float64)
+            self.n_members = len(mb)
+            h = C.c_void_p()
+            with torch.cuda.device(self.device):
+                st = _lib.nbgs_create_composite_scene(C.byref(self.params), self.n, *[_ptr(a) for a in arrs],
+                                                      self.n_members, _ptr(mb), _ptr(mo), _ptr(mr),
+                                                      C.byref(alloc) if alloc is not None else None,
+                                                      self.stream.cuda_stream, C.byref(h))
+        else:
+            arrs = [np.ascontiguousarray(scene[k], dtype=np.float64)
+                    for k in ("pos", "vel", "angvel", "radius", "density")]
+            with torch.cuda.device(self.device):
+                st, h = nbgs_create_scene(self.params, self.n, *[_ptr(a) for a in arrs], alloc,
+                                          self.stream.cuda_stream)
         if st != NBGS_OK:
             raise NBGSError(st, "nbgs_create_scene", "scene creation failed")
         self.h = h
