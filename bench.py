@@ -34,6 +34,9 @@ SWEEPS, TOL = 100, 1e-6
 # algorithmic bytes per contact update of the sweep kernel (read + write of
 # what must move once): sphere-sphere and sphere-wall, FP32 / FP64
 BYTES = {"fp32": (168, 112), "fp64": (328, 216)}
+# composites: record 80 / 160 B, impulse read + write, per body 4 records
+# read (v, w, inverse inertia) and 2 written
+BYTES_COMP = {"fp32": (80 + 32 + 2 * 96, 80 + 32 + 96), "fp64": (160 + 64 + 2 * 192, 160 + 64 + 192)}
 
 
 def workload(name: str):
@@ -68,12 +71,27 @@ def workload(name: str):
         return sc, ("conical hopper discharge: 2,000,000 spheres r~U(0.4,0.6), 30 deg half-angle, orifice 8 r_mean, "
                     "mu=0.5, dt=5e-4, previous-step warm start, measured after 2,000 settling steps (30 sweeps), "
                     "100 sweeps or residual 1e-6, FP32 sweeps, FP64 positions")
+    if name == "compgas":
+        sc = scenes.composite_gas(160, 160, 160, seed=0, precision="fp32", contacts_per_body=2)
+        return sc, (f"granular gas of composite particles (Sect. 7.2.1 as run): {len(sc['pos']):,} bodies of 2-4 "
+                    f"spheres ({len(sc['members']['body']):,} members, diameters U(0.6, 0.8) inside a bounding "
+                    "sphere of diameter 1), Cartesian grid of spacing 1.1, velocities U(-0.2, 0.2) per component, "
+                    "walls, no gravity, mu=0.1, omega=0.75, dt=1e-4, 10 sweeps, FP32 sweeps, FP64 positions")
+    if name == "comppile":
+        sc = scenes.composite_gas(100, 100, 100, seed=0, spacing=1.02, v_max=0.5, dt=2e-2, mu=0.4, omega=1.0,
+                                  gravity=(0.0, 0.0, -9.81), precision="fp32", contacts_per_body=8,
+                                  warm_start="prev")
+        sc["vel"][:, 2] -= 3.0
+        return sc, (f"pile of composite particles: {len(sc['pos']):,} bodies of 2-4 spheres "
+                    f"({len(sc['members']['body']):,} members) on a grid of spacing 1.02 thrown down at 3 m/s into a "
+                    "walled box under gravity, mu=0.4, dt=2e-2, 50 sweeps, previous-step warm start, FP32 sweeps, "
+                    "FP64 positions")
     raise SystemExit(f"unknown workload {name}")
 
 
 # sweeps and tolerance per workload: (max_sweeps, tol)
 SOLVE = {"dense1m": (100, 1e-6), "config1": (50, 0.0), "gas": (50, 0.0), "ramp": (100, 0.0), "batch": (100, 1e-6),
-         "hopper": (100, 1e-6)}
+         "hopper": (100, 1e-6), "compgas": (10, 0.0), "comppile": (50, 0.0)}
 # untimed steps (sweeps, count) that bring a workload into its regime first
 SETTLE = {"hopper": (30, 2000)}
 
@@ -156,7 +174,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
-def measured_traffic(prec, contacts, sweeps, variant=""):
+def measured_traffic(prec, contacts, sweeps, variant="", kernel="k_solve_persistent"):
     """DRAM bytes per launch of the sweep kernel from the committed ncu
     capture (profiles/traffic.json), scaled by the contact updates of one
     launch; None when the kernel source changed since the capture."""
@@ -164,7 +182,7 @@ def measured_traffic(prec, contacts, sweeps, variant=""):
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    key = f"k_solve_persistent<{'float' if prec == 'fp32' else 'double'}>" + variant
+    key = f"{kernel}<{'float' if prec == 'fp32' else 'double'}>" + variant
     d = json.load(open(p)).get(key)
     if not d:
         return None
@@ -177,7 +195,7 @@ def measured_traffic(prec, contacts, sweeps, variant=""):
 
 def count_contact_kinds(g, n):
     c = g.get_contacts()
-    walls = int(np.count_nonzero(c["j2"] >= n))
+    walls = int(np.count_nonzero(c["j2"] >= getattr(g, "n_members", n)))   # walls follow the members
     sizes = np.bincount(c["colour"][c["colour"] >= 0]).tolist() if len(c["colour"]) else []
     return len(c["j2"]) - walls, walls, sizes
 
@@ -357,7 +375,8 @@ def main():
     contacts = [s["n_contacts"] for s in stats]
     solve_ms = phase_ms["solve"]
     sweep_rate = updates / (phase_ms["sweep_kernel"] / 1e3) if phase_ms["sweep_kernel"] > 0 else None
-    b_ss, b_sw = BYTES[prec]
+    comp = "members" in first
+    b_ss, b_sw = (BYTES_COMP if comp else BYTES)[prec]
     # dominant kernel: the persistent sweep kernel, one launch per solve
     alg_bytes_per_launch = (n_ss * b_ss + n_sw * b_sw) * statistics.mean(sweeps_done)
     # subdomains: per sweep, each shared body's accumulator and own record
@@ -371,13 +390,15 @@ def main():
     # with subdomains the traffic depends on the grid: a capture of the same
     # workload and grid only
     traffic = measured_traffic(prec, n_ss + n_sw, statistics.mean(sweeps_done),
-                               "" if args.subdomains is None else f" {args.workload} subdomains {args.subdomains}")
+                               "" if args.subdomains is None else f" {args.workload} subdomains {args.subdomains}",
+                               "k_solve_comp" if comp else "k_solve_persistent")
     achieved = alg_bytes_per_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": desc, "spheres": n, "contacts": contacts[-1], "colours": stats[-1]["n_colours"], "colour_sizes": colour_sizes,
+        "config": {"workload": desc, **({"bodies": n, "members": int(g.n_members)} if comp else {"spheres": n}),
+                   "contacts": contacts[-1], "colours": stats[-1]["n_colours"], "colour_sizes": colour_sizes,
                    "sweeps_per_step": sweeps,
                    "tol": tol, "l2": "inputs larger than L2 (no flush)",
                    **({"subdomains": args.subdomains, "shared_bodies": n_shared, "extra_instances": n_extra}
@@ -390,7 +411,7 @@ def main():
         "gpu_launches": int(sum(v for k, v in launches.items() if k != "sweep_kernel")),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": f"k_solve_persistent<{'float' if prec == 'fp32' else 'double'}>",
+                     "kernel": f"{'k_solve_comp' if comp else 'k_solve_persistent'}<{'float' if prec == 'fp32' else 'double'}>",
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                      "alg_bytes_per_launch": alg_bytes_per_launch, "launch_ms": per_launch_ms},
         "clocks": ck,

@@ -81,7 +81,8 @@ __device__ __forceinline__ void sym_mul(const T I[6], const T v[3], T out[3])
 // must point against (cos th, sin th): the cross product of the two
 // vanishes, a trigonometric polynomial of degree 2 in th (a quartic in
 // tan(th/2), the route of Bonnefon et al. cited in Sect. 3).  Its roots
-// are bracketed by 64 equal samples of [0, 2 pi) and refined by bisection;
+// are bracketed by 64 equal samples of [0, 2 pi) and refined inside the
+// bracket (safeguarded Newton on the polynomial expanded in cos, sin);
 // a root qualifies if D > 0 and u_to . (cos th, sin th) <= 0; the one of
 // least 1/2 p.W p + b.p is taken (the first in th on ties).  Without a
 // qualifying root (a double root the samples miss), the diagonal solution
@@ -95,16 +96,6 @@ __device__ __forceinline__ void slide_dut(const Sym3<R>& W, R mu, const R b[3], 
 }
 
 template <class R>
-__device__ __forceinline__ R slide_g(const Sym3<R>& W, R mu, const R b[3], R th)
-{
-    R s, c, D, vt, vo;
-    if constexpr (sizeof(R) == 4) sincosf(th, &s, &c);
-    else sincos(th, &s, &c);
-    slide_dut(W, mu, b, c, s, D, vt, vo);
-    return -s * vt + c * vo;
-}
-
-template <class R>
 __device__ __forceinline__ R energy(const Sym3<R>& W, const R b[3], const R p[3])
 {
     const R w0 = W.nn * p[0] + W.nt * p[1] + W.no * p[2];
@@ -112,6 +103,17 @@ __device__ __forceinline__ R energy(const Sym3<R>& W, const R b[3], const R p[3]
     const R w2 = W.no * p[0] + W.to * p[1] + W.oo * p[2];
     return p[0] * (R(0.5) * w0 + b[0]) + p[1] * (R(0.5) * w1 + b[1]) + p[2] * (R(0.5) * w2 + b[2]);
 }
+
+// cos and sin of the 64 sample angles 2 pi k / 64 (set from the host's libm)
+__constant__ double c_cos64[64], c_sin64[64];
+__constant__ float c_cos32[64], c_sin32[64];
+
+template <class R> __device__ __forceinline__ R tab_cos(int k);
+template <class R> __device__ __forceinline__ R tab_sin(int k);
+template <> __device__ __forceinline__ float tab_cos<float>(int k) { return c_cos32[k]; }
+template <> __device__ __forceinline__ float tab_sin<float>(int k) { return c_sin32[k]; }
+template <> __device__ __forceinline__ double tab_cos<double>(int k) { return c_cos64[k]; }
+template <> __device__ __forceinline__ double tab_sin<double>(int k) { return c_sin64[k]; }
 
 template <class R>
 __device__ void one_contact_general(const Sym3<R>& W, R mu, const R b[3], R p[3])
@@ -135,41 +137,68 @@ __device__ void one_contact_general(const Sym3<R>& W, R mu, const R b[3], R p[3]
         p[2] = ps2;
         return;
     }
+    // sliding: the condition (cos th, sin th) x D u_to = 0 expanded in
+    // c = cos th, s = sin th: g = P1 s + Q1 c + Rsc s c + S2 s^2 + C2 c^2
+    const R P1 = b[0] * W.nt - b[1] * W.nn;
+    const R Q1 = b[2] * W.nn - b[0] * W.no;
+    const R Rsc = mu * (b[0] * (W.tt - W.oo) - b[1] * W.nt + b[2] * W.no);
+    const R S2 = mu * (b[0] * W.to - b[1] * W.no);
+    const R C2 = mu * (b[2] * W.nt - b[0] * W.to);
     constexpr int K = 64;
-    constexpr int kBisect = sizeof(R) == 4 ? 30 : 60;
+    constexpr int kIter = sizeof(R) == 4 ? 12 : 24;
     const R two_pi = (R)6.283185307179586;
+    const R dth = two_pi / (R)K;
     bool found = false;
     R best = R(0);
-    const R g0 = slide_g(W, mu, b, R(0));
+    R ghi_prev = R(0);
     for (int k = 0; k < K; ++k) {
-        R lo = two_pi * (R)k / (R)K, hi = two_pi * (R)(k + 1) / (R)K;
-        R glo = k == 0 ? g0 : slide_g(W, mu, b, lo);
-        const R ghi = k + 1 == K ? g0 : slide_g(W, mu, b, hi);
+        const int k1 = k + 1 == K ? 0 : k + 1;
+        R c = tab_cos<R>(k), s = tab_sin<R>(k);
+        const R glo = k == 0 ? P1 * s + Q1 * c + Rsc * s * c + S2 * s * s + C2 * c * c : ghi_prev;
+        c = tab_cos<R>(k1);
+        s = tab_sin<R>(k1);
+        const R ghi = P1 * s + Q1 * c + Rsc * s * c + S2 * s * s + C2 * c * c;
+        ghi_prev = ghi;
         R th;
         if (glo == R(0)) {
-            th = lo;
+            th = dth * (R)k;
         } else if ((glo < R(0)) != (ghi < R(0)) && ghi != R(0)) {
-            for (int it = 0; it < kBisect; ++it) {
-                const R mid = R(0.5) * (lo + hi);
-                const R gm = slide_g(W, mu, b, mid);
-                if ((gm < R(0)) == (glo < R(0))) {
-                    lo = mid;
-                    glo = gm;
+            // the root in [lo, hi]: Newton steps kept inside the bracket
+            // (bisection where a step would leave it)
+            R lo = dth * (R)k, hi = dth * (R)(k + 1);
+            R gl = glo;
+            th = lo + (hi - lo) * (glo / (glo - ghi));
+            for (int it = 0; it < kIter; ++it) {
+                R sn, cs;
+                if constexpr (sizeof(R) == 4) sincosf(th, &sn, &cs);
+                else sincos(th, &sn, &cs);
+                const R g = P1 * sn + Q1 * cs + Rsc * sn * cs + S2 * sn * sn + C2 * cs * cs;
+                if (g == R(0)) break;
+                if ((g < R(0)) == (gl < R(0))) {
+                    lo = th;
+                    gl = g;
                 } else {
-                    hi = mid;
+                    hi = th;
                 }
+                const R dg = P1 * cs - Q1 * sn + Rsc * (cs * cs - sn * sn) + R(2) * (S2 - C2) * sn * cs;
+                const R step = g / dg;
+                // a step below the resolution of th: converged (checked before
+                // the bracket, which has shrunk onto th)
+                if (fabs(step) <= (R)(sizeof(R) == 4 ? 1e-7 : 1e-15) * (R(1) + fabs(th))) break;
+                R nt = th - step;
+                if (!(nt > lo && nt < hi)) nt = R(0.5) * (lo + hi);
+                th = nt;
             }
-            th = R(0.5) * (lo + hi);
         } else {
             continue;
         }
-        R s, c, D, vt, vo;
-        if constexpr (sizeof(R) == 4) sincosf(th, &s, &c);
-        else sincos(th, &s, &c);
-        slide_dut(W, mu, b, c, s, D, vt, vo);
-        if (!(D > R(0)) || c * vt + s * vo > R(0)) continue;
+        R sn, cs, D, vt, vo;
+        if constexpr (sizeof(R) == 4) sincosf(th, &sn, &cs);
+        else sincos(th, &sn, &cs);
+        slide_dut(W, mu, b, cs, sn, D, vt, vo);
+        if (!(D > R(0)) || cs * vt + sn * vo > R(0)) continue;
         const R pn = -b[0] / D;
-        const R q[3] = {pn, mu * pn * c, mu * pn * s};
+        const R q[3] = {pn, mu * pn * cs, mu * pn * sn};
         const R e = energy(W, b, q);
         if (!found || e < best) {
             best = e;
@@ -716,7 +745,25 @@ void free_composite_buffers(nbgs_scene* s)
 // Contact-sized composite arrays for the current capacity.
 nbgs_status ensure_composite_buffers(nbgs_scene* s)
 {
-    if (!s->composite || s->comp_ccap >= s->ccap) return NBGS_OK;
+    if (!s->composite) return NBGS_OK;
+    if (s->comp_ccap == 0) {   // the sample angles of the one-contact solve
+        double c64[64], s64[64];
+        float c32[64], s32[64];
+        for (int k = 0; k < 64; ++k) {
+            const double th = 6.283185307179586 * k / 64;
+            c64[k] = std::cos(th);
+            s64[k] = std::sin(th);
+            c32[k] = (float)c64[k];
+            s32[k] = (float)s64[k];
+        }
+        cudaMemcpyToSymbolAsync(c_cos64, c64, sizeof(c64), 0, cudaMemcpyHostToDevice, s->stream);
+        cudaMemcpyToSymbolAsync(c_sin64, s64, sizeof(s64), 0, cudaMemcpyHostToDevice, s->stream);
+        cudaMemcpyToSymbolAsync(c_cos32, c32, sizeof(c32), 0, cudaMemcpyHostToDevice, s->stream);
+        cudaMemcpyToSymbolAsync(c_sin32, s32, sizeof(s32), 0, cudaMemcpyHostToDevice, s->stream);
+        nbgs_status rc = cuda_check(s, cudaStreamSynchronize(s->stream), "composite: sample table");
+        if (rc != NBGS_OK) return rc;
+    }
+    if (s->comp_ccap >= s->ccap) return NBGS_OK;
     dev_free(s, s->cb1);
     dev_free(s, s->cb2);
     dev_free(s, s->crec);

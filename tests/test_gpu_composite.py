@@ -3,8 +3,9 @@
 Bit-exact from one state: member contact keys, gaps, normals (the member
 positions X + R(q) d are rounded as written on both sides) and colours.
 Impulses and velocities after a step with FP64 sweeps: 1e-10 relative to the
-largest (the one-contact solve brackets the same sliding roots; the device's
-sine and cosine differ from the host's in the last bits)."""
+largest, positions and orientations likewise (the one-contact solve brackets
+the same sliding roots and refines them differently: bisection on the host,
+Newton steps inside the bracket on the device)."""
 import numpy as np
 import pytest
 
@@ -51,8 +52,10 @@ def _step_and_compare(g, o, sweeps, tol=0.0, rel=REL, exact=True):
     bg, bo = g.get_bodies(), o.get_bodies()
     _rel_close(bg["vel"], bo["vel"], rel)
     _rel_close(bg["angvel"], bo["angvel"], rel)
-    assert np.abs(bg["pos"] - bo["pos"]).max() <= 1e-12 * max(1.0, np.abs(bo["pos"]).max())
-    assert np.abs(bg["quat"] - bo["quat"]).max() <= 1e-12
+    # positions and orientations move by dt v' and dt Q w' / 2: they inherit
+    # the velocities' tolerance
+    assert np.abs(bg["pos"] - bo["pos"]).max() <= rel * max(1.0, np.abs(bo["pos"]).max())
+    assert np.abs(bg["quat"] - bo["quat"]).max() <= rel
     return sg, so, bo
 
 
