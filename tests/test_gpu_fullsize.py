@@ -12,7 +12,11 @@ properties that hold at any size, and outputs recomputed one by one.
 - 30M-sphere gas: the contacts found obey the keep rule of Sect. 4,
   recomputed for a sample, and the contact set of a step is unique.
 - Dense packing and settled 2M hopper: FP32 sweeps against FP64 sweeps from
-  the same state, impulses and velocities within 1e-2 of the largest."""
+  the same state, impulses and velocities within 1e-2 of the largest.
+- 1M-body composite pile: no contact inside a body, colours valid over bodies,
+  cones, sampled member-pair geometry from the body state bit for bit.
+- 1M ramp on a 16 x 16 x 1 subdomain grid: sampled s_c(j) bit for bit, every
+  cell used, colours valid."""
 import math
 
 import numpy as np
@@ -168,3 +172,97 @@ def test_fp32_sweeps_against_fp64_at_full_size(nb, workload):
     print(f"{workload}: {len(c64['j1'])} contacts, FP32 vs FP64 after 100 sweeps: impulses {ep:.2e}, "
           f"velocities {ev:.2e} (relative to the largest)")
     assert ep < 1e-2 and ev < 1e-2
+
+
+def test_composite_pile_full_size(nb):
+    """The 1M-body composite pile of the benchmark: no contact joins two
+    members of one body, the colouring is valid over bodies, impulses lie in
+    their cones, and sampled member-pair gaps and normals equal their FP64
+    definition from the bodies' state (members at X + R(q) d, bit for bit)."""
+    sc = scenes.composite_gas(100, 100, 100, seed=0, spacing=1.02, v_max=0.5, dt=2e-2, mu=0.4, omega=1.0,
+                              gravity=(0.0, 0.0, -9.81), precision="fp32", contacts_per_body=8, warm_start="prev")
+    sc["vel"][:, 2] -= 3.0
+    g = nb.Scene(sc)
+    for _ in range(3):
+        g.step(50, 0.0, stats=False)
+    b0 = g.get_bodies()
+    st = g.step(50, 0.0)
+    assert st["n_contacts"] > 1_000_000
+    c = g.get_contacts()
+    mb = sc["members"]["body"]
+    nm = len(mb)
+    mem = c["j2"] < nm
+    a, bm = c["j1"].astype(np.int64), c["j2"].astype(np.int64)
+    assert np.all(mb[a[mem]] != mb[bm[mem]])
+    # colours over bodies
+    body1 = mb[a]
+    body2 = np.where(mem, mb[np.minimum(bm, nm - 1)], -1)
+    for k in np.unique(c["colour"]):
+        rows = c["colour"] == k
+        bb = np.concatenate([body1[rows], body2[rows][body2[rows] >= 0]])
+        assert len(np.unique(bb)) == len(bb), f"colour {k} touches a body twice"
+    _check_cone(c, sc["params"]["mu"], rel=1e-4)
+    # geometry of sampled member pairs from the start-of-step body state
+    rng = np.random.default_rng(3)
+    pick = rng.choice(np.nonzero(mem)[0], 2000, replace=False)
+
+    def member_pos(m):
+        i = mb[m]
+        q = b0["quat"][i]
+        w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+        R = np.empty((len(m), 3, 3))
+        R[:, 0, 0] = 1.0 - 2.0 * (y * y + z * z); R[:, 0, 1] = 2.0 * (x * y - w * z); R[:, 0, 2] = 2.0 * (x * z + w * y)
+        R[:, 1, 0] = 2.0 * (x * y + w * z); R[:, 1, 1] = 1.0 - 2.0 * (x * x + z * z); R[:, 1, 2] = 2.0 * (y * z - w * x)
+        R[:, 2, 0] = 2.0 * (x * z - w * y); R[:, 2, 1] = 2.0 * (y * z + w * x); R[:, 2, 2] = 1.0 - 2.0 * (x * x + y * y)
+        d = _member_offsets(sc)[m]
+        rd = (R[:, :, 0] * d[:, 0:1] + R[:, :, 1] * d[:, 1:2]) + R[:, :, 2] * d[:, 2:3]
+        return b0["pos"][i] + rd
+
+    pa, pb = member_pos(a[pick]), member_pos(bm[pick])
+    d3 = pa - pb
+    d = np.sqrt((d3[:, 0] * d3[:, 0] + d3[:, 1] * d3[:, 1]) + d3[:, 2] * d3[:, 2])
+    r = sc["members"]["radius"]
+    assert np.array_equal(c["xi"][pick], (d - r[a[pick]]) - r[bm[pick]])
+    assert np.array_equal(c["normal"][pick], d3 / d[:, None])
+
+
+def _member_offsets(sc):
+    """Members' offsets from their body's centre of mass (the masses of the
+    members add up; the body's centre of mass is their weighted mean)."""
+    mb, off, r = sc["members"]["body"], sc["members"]["offset"], sc["members"]["radius"]
+    rho = sc["density"][mb]
+    mm = rho * (4.0 / 3.0) * np.pi * r * r * r
+    n = len(sc["density"])
+    M = np.zeros(n)
+    X = np.zeros((n, 3))
+    # sequential sums in member order, as the definition writes them
+    for m in range(len(mb)):
+        M[mb[m]] += mm[m]
+        X[mb[m]] += mm[m] * off[m]
+    X /= M[:, None]
+    return off - X[mb]
+
+
+def test_subdomain_ramp_full_size(nb):
+    """The 1M ramp on the 16 x 16 x 1 grid of the benchmark: sampled s_c(j)
+    equal the cell of body j1's centre recomputed here, every cell of the
+    grid holds contacts, and the colouring is valid."""
+    sc = scenes.hcp_packing(100, 100, 100, dt=1e-5, tau=0.005, mu=0.85, tilt_deg=30.0, v0=0.1, omega=0.5,
+                            precision="fp32", warm_start="prev", subdomains=(16, 16, 1))
+    g = nb.Scene(sc)
+    b0 = g.get_bodies()
+    st = g.step(100, 0.0)
+    assert st["n_contacts"] == 100 * 100 * (6 * 100 - 1)
+    c = g.get_contacts()
+    sub = g.get_subdomains()
+    n = len(sc["radius"])
+    _check_colouring(c, n)
+    lo, hi = np.array(sc["params"]["box_lo"]), np.array(sc["params"]["box_hi"])
+    gd = np.array([16, 16, 1])
+    rng = np.random.default_rng(4)
+    pick = rng.choice(len(sub), 20000, replace=False)
+    x = b0["pos"][c["j1"][pick].astype(np.int64)]
+    k = np.clip(np.floor(((x - lo) * gd) / (hi - lo)), 0, gd - 1).astype(np.int64)
+    want = (k[:, 2] * gd[1] + k[:, 1]) * gd[0] + k[:, 0]
+    assert np.array_equal(sub[pick].astype(np.int64), want)
+    assert len(np.unique(sub)) == 256
