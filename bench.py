@@ -50,6 +50,10 @@ def workload(name: str):
     if name == "config1":
         sc = scenes.config1(0)
         return sc, "1,000 spheres in a 10.5^3 walled box, FP64, mu=0.5, dt=1e-3, 50 sweeps"
+    if name == "config1_1e6":
+        sc = scenes.config1(0)
+        return sc, ("1,000 spheres in a 10.5^3 walled box, FP64, mu=0.5, dt=1e-3, time steps to residual 1e-6 "
+                    "(at most 1,000 sweeps), cold start")
     if name == "gas":
         sc = scenes.granular_gas(cells=196, seed=0, precision="fp32", contacts_per_body=2)
         return sc, (f"dense granular gas, {len(sc['radius']):,} spheres r~U(0.45,0.55), FCC start at phi=0.5, "
@@ -91,9 +95,9 @@ def workload(name: str):
 
 # sweeps and tolerance per workload: (max_sweeps, tol)
 SOLVE = {"dense1m": (100, 1e-6), "config1": (50, 0.0), "gas": (50, 0.0), "ramp": (100, 0.0), "batch": (100, 1e-6),
-         "hopper": (100, 1e-6), "compgas": (10, 0.0), "comppile": (50, 0.0)}
+         "hopper": (100, 1e-6), "compgas": (10, 0.0), "comppile": (50, 0.0), "config1_1e6": (1000, 1e-6)}
 # untimed steps (sweeps, count) that bring a workload into its regime first
-SETTLE = {"hopper": (30, 2000)}
+SETTLE = {"hopper": (30, 2000), "config1_1e6": (50, 150)}
 
 
 def read_peaks():
@@ -267,6 +271,8 @@ def main():
     ap.add_argument("--subdomains", default=None,
                     help="subdomains of Alg. 1: 'jacobi' (one per contact) or a grid 'g0,g1,g2'")
     ap.add_argument("--omega", type=float, default=None, help="relaxation parameter of Alg. 1")
+    ap.add_argument("--autotune", action="store_true",
+                    help="after the warm-up, let nbgs_autotune pick the sweep schedule and blocks per SM (untimed)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -318,6 +324,12 @@ def main():
                 g.step(s_sweeps, 0.0, stats=False)
         for _ in range(max(args.warmup, 0)):
             g.step(sweeps, tol)
+        tuned = None
+        if args.autotune:
+            g.detect_contacts()   # the tuner times solves on the current contacts
+            f_, b_ = nbgs.autotune(g, sweeps, tol)
+            tuned = {"sweep_flags": int(f_), "blocks_per_sm": int(b_)}
+            desc += f", autotuned schedule (sweep flags {f_}, {b_} blocks per SM)"
         n_ss, n_sw, colour_sizes = count_contact_kinds(g, n)
         n_shared, n_extra = count_instances(g, n) if args.subdomains is not None else (0, 0)
         g.enable_timing(True)
@@ -401,6 +413,7 @@ def main():
                    "contacts": contacts[-1], "colours": stats[-1]["n_colours"], "colour_sizes": colour_sizes,
                    "sweeps_per_step": sweeps,
                    "tol": tol, "l2": "inputs larger than L2 (no flush)",
+                   **({"autotuned": tuned} if tuned else {}),
                    **({"subdomains": args.subdomains, "shared_bodies": n_shared, "extra_instances": n_extra}
                       if args.subdomains is not None else {}),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
