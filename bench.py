@@ -242,6 +242,20 @@ def cpu_baseline(steps_budget_s: float = 15.0):
                       f"1 thread, host nproc={os.cpu_count()}"}
 
 
+def reduce_over_ranks(dist, ms_total, updates, device):
+    """Replicas: the job's time is the slowest rank's, its work the sum of
+    all ranks' (no data-path collective; this reduction runs once, after the
+    timed region)."""
+    if dist is None:
+        return float(ms_total), float(updates)
+    import torch
+    t = torch.tensor([float(ms_total)], device=device, dtype=torch.float64)
+    u = torch.tensor([float(updates)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -372,15 +386,7 @@ def main():
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
 
-    t_max = ms_total
-    if dist:
-        t = torch.tensor([ms_total, float(updates)], device=f"cuda:{local}", dtype=torch.float64)
-        tt = t.clone()
-        dist.all_reduce(tt[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
-        t_max, updates_all = float(tt[0]), float(tt[1])
-    else:
-        updates_all = float(updates)
+    t_max, updates_all = reduce_over_ranks(dist, ms_total, updates, f"cuda:{local}")
     value = updates_all / (t_max / 1e3)
     sweeps_done = [s["sweeps_done"] for s in stats]
     residuals = [float(s["residual"]) for s in stats]
