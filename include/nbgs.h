@@ -334,7 +334,7 @@ nbgs_status nbgs_set_subdomains(nbgs_scene* scene, int32_t mode, const int32_t* 
 /* Composite particles (Sect. 2: non-convex objects as composites of convex
  * particles): n_bodies rigid bodies made of n_members member spheres.
  * pos, vel, angvel: n_bodies x 3 (pos is each body's reference point);
- * density: n_bodies; member_body: n_members, non-decreasing, every body with
+ * density: n_bodies, > 0; member_body: n_members, non-decreasing, every body with
  * 1..4 members; member_offset: n_members x 3, from the reference point along
  * the observational axes; member_radius: n_members.  All host pointers;
  * copied in.  The members' masses and inertias add up (an overlap counts for

@@ -1138,6 +1138,8 @@ int oracle_create_composite_scene(const oracle_params* prm, int64_t n, const dou
         if (m > 0 && member_body[m] > member_body[m - 1] + 1) return 1;   /* every body has members */
     }
     if (member_body[0] != 0 || member_body[nm - 1] != n - 1) return 1;
+    for (int64_t i = 0; i < n; ++i)
+        if (!(density[i] > 0.0)) return 1;   /* the centre of mass needs a mass */
     double* ones = (double*)malloc((size_t)n * sizeof(double));
     if (!ones) return 2;
     for (int64_t i = 0; i < n; ++i) ones[i] = 1.0;

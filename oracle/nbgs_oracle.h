@@ -121,8 +121,8 @@ int  oracle_step(oracle_scene* s, int32_t max_sweeps, double tol, oracle_step_st
 /* Composite particles (Sect. 2, composites of convex particles): n rigid
  * bodies made of nm member spheres.  member_body (nm, non-decreasing, every
  * body 1..ORACLE_MAX_MEMBERS members), member_offset (nm x 3, from the
- * body's reference point pos, observational axes), member_radius (nm).
- * Mass, centre of mass and inertia follow from the members (see the
+ * body's reference point pos, observational axes), member_radius (nm);
+ * density > 0 (walls are the bodies of infinite mass).  Mass, centre of mass and inertia follow from the members (see the
  * definition); the body's position becomes its centre of mass and its
  * orientation the identity.  Contacts join members of different bodies
  * (j1 < j2 member indices) or a member and a wall (j2 = nm + k).  No cones,

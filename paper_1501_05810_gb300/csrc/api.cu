@@ -235,6 +235,8 @@ nbgs_status nbgs_create_composite_scene(const nbgs_params* params, int64_t n_bod
     if (params->subdomain_mode != NBGS_SUB_NONE || params->warm_start == NBGS_WARM_MLP) return NBGS_EINVAL;
     const int64_t nb = n_bodies, nm = n_members;
     if (member_body[0] != 0 || member_body[nm - 1] != nb - 1) return NBGS_EINVAL;
+    for (int64_t i = 0; i < nb; ++i)
+        if (!(density[i] > 0.0)) return NBGS_EINVAL;   // the centre of mass needs a mass
     for (int64_t m = 0; m < nm; ++m) {
         if (!(member_radius[m] > 0.0)) return NBGS_EINVAL;
         if (m > 0 && (member_body[m] < member_body[m - 1] || member_body[m] > member_body[m - 1] + 1))

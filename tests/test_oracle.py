@@ -1047,3 +1047,15 @@ def test_composite_detection_against_kdtree(oracle_mod):
     got = {(int(x), int(y)) for x, y in zip(c["j1"], c["j2"]) if y < nm}
     assert len(want) > 20
     assert want <= got and len(got - want) <= 2   # borderline pairs at rounding distance aside
+
+
+def test_composite_arguments_are_checked(oracle_mod):
+    good = scenes.dumbbell_on_plane()
+    oracle_mod.OracleScene(good)
+    bad = [dict(good, density=np.array([0.0])),
+           dict(good, members=dict(good["members"], body=np.array([0, 1], np.int32))),
+           dict(good, members=dict(good["members"], radius=np.array([0.5, -0.1]))),
+           dict(good, params=dict(good["params"], subdomains="jacobi"))]
+    for sc in bad:
+        with pytest.raises(RuntimeError):
+            oracle_mod.OracleScene(sc)
