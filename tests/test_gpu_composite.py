@@ -159,3 +159,15 @@ def test_composite_rejections(nb, tmp_path):
         with pytest.raises(nb.NBGSError) as e:
             call(s)
         assert e.value.status == nb.NBGS_EINVAL
+
+
+def test_composite_creation_checks_its_arguments(nb):
+    good = scenes.dumbbell_on_plane()
+    nb.Scene(good).close()
+    bad = [dict(good, density=np.array([0.0])),
+           dict(good, members=dict(good["members"], body=np.array([0, 1], np.int32))),
+           dict(good, members=dict(good["members"], radius=np.array([0.5, -0.1]))),
+           dict(good, params=dict(good["params"], subdomains="jacobi"))]
+    for sc in bad:
+        with pytest.raises(nb.NBGSError):
+            nb.Scene(sc)
