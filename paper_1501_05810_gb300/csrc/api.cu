@@ -247,13 +247,14 @@ nbgs_status nbgs_create_composite_scene(const nbgs_params* params, int64_t n_bod
     // of mass; the bounding radius max |d'| + r enters the hull
     std::vector<double> bpos(4 * nb), I0(9 * nb), I0inv(9 * nb), invm(nb), moff(4 * nm), mzero(3 * nm, 0.0),
         ones(nm, 1.0);
-    std::vector<uint32_t> mbody(nm);
+    std::vector<uint32_t> mbody(nm), bfirst(nb);
     std::vector<uint8_t> bfin(nb);
     int64_t m0 = 0;
     for (int64_t i = 0; i < nb; ++i) {
         int64_t m1 = m0;
         while (m1 < nm && member_body[m1] == i) ++m1;
         if (m1 - m0 > kMaxMembers) return NBGS_EINVAL;
+        bfirst[i] = (uint32_t)m0;
         double M = 0.0, X[3] = {0.0, 0.0, 0.0};
         for (int64_t m = m0; m < m1; ++m) {
             const double r = member_radius[m];
@@ -305,7 +306,8 @@ nbgs_status nbgs_create_composite_scene(const nbgs_params* params, int64_t n_bod
     const size_t v4 = s->fp32 ? 16 : 32;
     bool ok = take(s, s->bpos, (size_t)nb) && take(s, s->bquat, (size_t)nb) && take(s, s->bI0, 9 * (size_t)nb) &&
               take(s, s->bI0inv, 9 * (size_t)nb) && take(s, s->bIinv, 6 * (size_t)nb) && take(s, s->binvm, (size_t)nb) &&
-              take(s, s->bfinite, (size_t)nb) && take(s, s->mbody, (size_t)nm) && take(s, s->moff, (size_t)nm);
+              take(s, s->bfinite, (size_t)nb) && take(s, s->mbody, (size_t)nm) && take(s, s->moff, (size_t)nm) &&
+              take(s, s->bfirst, (size_t)nb) && take(s, s->banchor, (size_t)nb);
     if (ok) {
         s->bvel = dev_alloc(s, 4 * (size_t)nb * v4);
         ok = s->bvel != nullptr;
@@ -338,6 +340,7 @@ nbgs_status nbgs_create_composite_scene(const nbgs_params* params, int64_t n_bod
     cudaMemcpyAsync(s->binvm, invm.data(), invm.size() * 8, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(s->bfinite, bfin.data(), bfin.size(), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(s->mbody, mbody.data(), mbody.size() * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(s->bfirst, bfirst.data(), bfirst.size() * 4, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(s->moff, moff.data(), moff.size() * 8, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(s->bvel, bv.data(), bv.size(), cudaMemcpyHostToDevice, st);
     rc = ensure_composite_buffers(s);

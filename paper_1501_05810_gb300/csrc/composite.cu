@@ -266,6 +266,15 @@ __global__ void k_comp_iinv(int64_t nb, const double4_32a* __restrict__ bquat, c
     }
 }
 
+// A canonical contact position per body for the dependency windows: the
+// first contact of its first member (any fixed position serves).
+__global__ void k_comp_anchor(int64_t nb, const uint32_t* __restrict__ bfirst, const uint32_t* __restrict__ row_off,
+                              uint32_t* __restrict__ anchor)
+{
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x)
+        anchor[b] = row_off[bfirst[b]];
+}
+
 // Sweep record of slot s (contact perm[s]) and its initial impulse.
 template <class R>
 __global__ void k_comp_records(int64_t C, int64_t nm, const uint32_t* __restrict__ perm,
@@ -414,6 +423,10 @@ __global__ void k_comp_velinit(int64_t nb, const double4_32a* __restrict__ bquat
 }
 
 template <class R> struct CompArgs {
+    int local;                 // dependency windows (else a grid barrier after every colour)
+    int* prog;                 // per block: last sweep phase completed
+    const int2* dep;           // per (colour, block): ring window of blocks sharing bodies with the chunk
+    const uint32_t* cstart;    // per colour, B + 1 chunk boundaries
     int64_t C, nb;
     const CompRec<R>* rec;
     R4<R>* p;
@@ -565,24 +578,54 @@ __global__ void __launch_bounds__(kCompThreads) k_solve_comp(CompArgs<R> A)
             if (!grid_barrier(A.info, nb)) return;
         }
     }
+    __shared__ int s_ok;
     int k = 0;
     double Rk = 0.0;
+    bool synced = true;
     for (; k < A.max_sweeps; ++k) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && k + 1 >= kHistKept) A.info->rk_bits[rk_slot(k + 1)] = 0ull;
         R rmax = R(0);
         for (int c = 0; c < ncol; ++c) {
-            for (int64_t s = A.col_off[c] + gtid; s < A.col_off[c + 1]; s += gstride) {
-                const R r = relax_comp<R, false>(A, s);
-                rmax = r > rmax ? r : rmax;
+            if (A.local) {
+                // this block's chunk of the colour, after the blocks sharing
+                // its bodies have finished the phase before
+                const int g = k * ncol + c;
+                int64_t b0, b1;
+                colour_chunk(A.cstart, c, b0, b1);
+                if (b1 > b0 && !wait_deps(A.prog, A.dep[c * (int)nb + blockIdx.x], g, A.info, &s_ok)) return;
+                for (int64_t s = b0 + threadIdx.x; s < b1; s += blockDim.x) {
+                    const R r = relax_comp<R, false>(A, s);
+                    rmax = r > rmax ? r : rmax;
+                }
+                if (c == ncol - 1) block_max_atomic((double)rmax, &A.info->rk_bits[rk_slot(k)]);
+                publish(A.prog, g);
+            } else {
+                for (int64_t s = A.col_off[c] + gtid; s < A.col_off[c + 1]; s += gstride) {
+                    const R r = relax_comp<R, false>(A, s);
+                    rmax = r > rmax ? r : rmax;
+                }
+                if (c == ncol - 1) block_max_atomic((double)rmax, &A.info->rk_bits[rk_slot(k)]);
+                if (!grid_barrier(A.info, nb)) return;
             }
-            if (c == ncol - 1) block_max_atomic((double)rmax, &A.info->rk_bits[rk_slot(k)]);
+        }
+        synced = !A.local;
+        // R_k needs every block: a grid barrier per sweep when the tolerance
+        // is tested (and near the rotating residual slots)
+        if (A.local && ncol > 0 && (A.tol > 0.0 || k + 2 >= kHistKept)) {
             if (!grid_barrier(A.info, nb)) return;
+            synced = true;
         }
-        Rk = __longlong_as_double((long long)((volatile unsigned long long*)A.info->rk_bits)[rk_slot(k)]) / vref;
-        if (A.tol > 0.0 && ncol > 0 && Rk <= A.tol) {
-            ++k;
-            break;
+        if (synced) {
+            Rk = __longlong_as_double((long long)((volatile unsigned long long*)A.info->rk_bits)[rk_slot(k)]) / vref;
+            if (A.tol > 0.0 && ncol > 0 && Rk <= A.tol) {
+                ++k;
+                break;
+            }
         }
+    }
+    if (!synced && k > 0) {
+        if (!grid_barrier(A.info, nb)) return;
+        Rk = __longlong_as_double((long long)((volatile unsigned long long*)A.info->rk_bits)[rk_slot(k - 1)]) / vref;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.info->sweeps_done = (uint32_t)k;
@@ -720,8 +763,18 @@ nbgs_status solve_comp_impl(nbgs_scene* s, int max_sweeps, double tol)
     A.max_sweeps = max_sweeps;
     A.tol = tol;
     A.warm = (s->prm.warm_start == NBGS_WARM_PREV && s->have_prev) ? 1 : 0;
-    const int blocks = comp_blocks<R>(s);
+    const int blocks = std::min(comp_blocks<R>(s), s->max_coop_blocks);
     if (blocks < 1) return fail(s, NBGS_EINVAL, "composite solve: the device cannot launch it cooperatively");
+    // local synchronisation unless a grid barrier per colour is asked for
+    A.local = (A.C > 0 && !(s->prm.sweep_flags & NBGS_SWEEP_GLOBAL_SYNC)) ? 1 : 0;
+    A.prog = s->prog;
+    A.dep = s->dep;
+    A.cstart = s->cstart;
+    if (A.local) {
+        k_comp_anchor<<<grid_for(s->nb, T, 8, s->num_sms), T, 0, st>>>(s->nb, s->bfirst, s->row_off, s->banchor);
+        nbgs_status rc = build_windows(s, blocks, s->nb, s->cb1, s->cb2, s->banchor, s->bfinite);
+        if (rc != NBGS_OK) return rc;
+    }
     void* args[] = {&A};
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_solve_comp<R>, dim3(blocks), dim3(kCompThreads), args, 0,
                                                 st);
@@ -738,7 +791,7 @@ nbgs_status solve_comp_impl(nbgs_scene* s, int max_sweeps, double tol)
 void free_composite_buffers(nbgs_scene* s)
 {
     void* ps[] = {s->bpos, s->bquat, s->bvel, s->bI0, s->bI0inv, s->bIinv, s->binvm, s->bfinite, s->mbody,
-                  s->moff, s->cb1, s->cb2, s->crec};
+                  s->moff, s->cb1, s->cb2, s->crec, s->bfirst, s->banchor};
     for (void* p : ps) dev_free(s, p);
 }
 

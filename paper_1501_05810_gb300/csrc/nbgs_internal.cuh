@@ -269,6 +269,65 @@ __device__ __forceinline__ bool grid_barrier(DevInfo* info, unsigned nblocks)
     return ok != 0;
 }
 
+// ---------------------------------------------------------------------------
+// Local synchronisation of the colour sweeps (dependency windows): block b
+// of a cooperative launch owns the slots [cstart[c][b], cstart[c][b + 1]) of
+// colour c, chunks balanced by contact count and local in body index.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void colour_chunk(const uint32_t* cstart, int c, int64_t& b0, int64_t& b1)
+{
+    const uint32_t* row = cstart + (int64_t)c * (gridDim.x + 1);
+    b0 = row[blockIdx.x];
+    b1 = row[blockIdx.x + 1];
+}
+
+
+// Wait until every block in this chunk's window has completed sweep phase
+// g - 1 (it and all earlier phases): then every contact of another colour
+// that shares a body with this chunk is settled.  Warp 0 polls the progress
+// words; bounded like every other wait.
+__device__ __forceinline__ bool wait_deps(const int* prog, int2 win, int g, DevInfo* info, int* s_ok)
+{
+    if (threadIdx.x < 32) {
+        int ok = 1;
+        const int nblk = (int)gridDim.x, self = (int)blockIdx.x;
+        for (int off = win.x + (int)threadIdx.x; off <= win.y && ok; off += 32) {
+            if (off == 0) continue;
+            const int b = ((self + off) % nblk + nblk) % nblk;
+            volatile const int* pb = prog + b;
+            const long long t0 = clock64();
+            while (*pb < g - 1) {
+                if (((volatile uint32_t*)&info->err)[0] & kErrTimeout) {
+                    ok = 0;
+                    break;
+                }
+                if (clock64() - t0 > (1LL << 31)) {
+                    atomicOr(&info->err, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok = __all_sync(0xffffffffu, ok);
+        if (threadIdx.x == 0) *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Publish that this block finished sweep phase g (after all its stores).
+__device__ __forceinline__ void publish(int* prog, int g)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(prog + blockIdx.x, g);
+    }
+}
+
+
+
 }  // namespace nbgs
 
 // ---------------------------------------------------------------------------
@@ -394,6 +453,8 @@ struct nbgs_scene {
     double* binvm = nullptr;       // nb: 1/m (FP64)
     uint8_t* bfinite = nullptr;    // nb
     uint32_t* mbody = nullptr;     // n: body of each member
+    uint32_t* bfirst = nullptr;    // nb: first member of each body
+    uint32_t* banchor = nullptr;   // nb: a canonical contact position per body (dependency windows)
     double4_32a* moff = nullptr;   // n: body-frame offset from the centre of mass, radius
     uint32_t* cb1 = nullptr;       // comp_ccap: body of contact end j1
     uint32_t* cb2 = nullptr;       // comp_ccap: body of contact end j2 (nb: a wall)
@@ -447,6 +508,8 @@ bool subdomains_valid(int32_t mode, const int32_t g[3]);   // api.cu
 // composite particles (composite.cu)
 nbgs_status ensure_composite_buffers(nbgs_scene* s);
 nbgs_status run_comp_ends(nbgs_scene* s);               // bodies of the contact ends (colouring)
+nbgs_status build_windows(nbgs_scene* s, int B, int64_t ninc, const uint32_t* ib1, const uint32_t* ib2,
+                          const uint32_t* anchor, const uint8_t* finc);   // solve.cu
 nbgs_status run_comp_records(nbgs_scene* s, int warm);   // after colouring: inverse inertias, sweep records
 nbgs_status run_solve_comp(nbgs_scene* s, int max_sweeps, double tol);
 nbgs_status run_integrate_comp(nbgs_scene* s);

@@ -395,13 +395,6 @@ template <class R> struct Stage {
 // [ceil(b C / B), ceil((b + 1) C / B)): a contiguous range of the colour
 // (the colour sort is stable), balanced by contact count and local in body
 // index, so that a chunk's bodies are touched only by nearby blocks.
-__device__ __forceinline__ void colour_chunk(const uint32_t* cstart, int c, int64_t& b0, int64_t& b1)
-{
-    const uint32_t* row = cstart + (int64_t)c * (gridDim.x + 1);
-    b0 = row[blockIdx.x];
-    b1 = row[blockIdx.x + 1];
-}
-
 // --- TMA bulk copies (global -> shared) completed on an mbarrier -----------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -559,50 +552,6 @@ template <class R, bool Batch> struct PersistMinBlocks {
     // FP64 and the per-scene bookkeeping of batches need more registers per thread
     static constexpr int value = sizeof(R) == 4 ? (Batch ? 3 : 4) : 2;
 };
-
-// Wait until every block in this chunk's window has completed sweep phase
-// g - 1 (it and all earlier phases): then every contact of another colour
-// that shares a body with this chunk is settled.  Warp 0 polls the progress
-// words; bounded like every other wait.
-__device__ __forceinline__ bool wait_deps(const int* prog, int2 win, int g, DevInfo* info, int* s_ok)
-{
-    if (threadIdx.x < 32) {
-        int ok = 1;
-        const int nblk = (int)gridDim.x, self = (int)blockIdx.x;
-        for (int off = win.x + (int)threadIdx.x; off <= win.y && ok; off += 32) {
-            if (off == 0) continue;
-            const int b = ((self + off) % nblk + nblk) % nblk;
-            volatile const int* pb = prog + b;
-            const long long t0 = clock64();
-            while (*pb < g - 1) {
-                if (((volatile uint32_t*)&info->err)[0] & kErrTimeout) {
-                    ok = 0;
-                    break;
-                }
-                if (clock64() - t0 > (1LL << 31)) {
-                    atomicOr(&info->err, kErrTimeout);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-        ok = __all_sync(0xffffffffu, ok);
-        if (threadIdx.x == 0) *s_ok = ok;
-    }
-    __syncthreads();
-    return *s_ok != 0;
-}
-
-// Publish that this block finished sweep phase g (after all its stores).
-__device__ __forceinline__ void publish(int* prog, int g)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicExch(prog + blockIdx.x, g);
-    }
-}
 
 // --- warp-level scheduling (NBGS_SWEEP_WARP_SYNC) ---------------------------
 // Every warp is a scheduling unit of its own ("virtual block" vb = 8 b + w of
@@ -1016,6 +965,33 @@ __global__ void k_chunk_windows(int64_t C, int64_t n, const uint32_t* __restrict
         }
         __syncthreads();
     }
+}
+
+// Chunk starts and dependency windows of a cooperative sweep over B blocks,
+// for contacts whose ends act on the bodies ib1, ib2 (>= ninc: a wall) of
+// finiteness finc, body x anchored at the canonical contact position
+// anchor[x] (any fixed position: the windows are offsets from it); the
+// progress words start at -1.  The body degree arrays of the colouring serve
+// as scratch.
+nbgs_status build_windows(nbgs_scene* s, int B, int64_t ninc, const uint32_t* ib1, const uint32_t* ib2,
+                          const uint32_t* anchor, const uint8_t* finc)
+{
+    const int T = 256;
+    const int64_t C = s->n_contacts;
+    cudaStream_t st = s->stream;
+    k_chunk_starts<<<grid_for((int64_t)kMaxColours * (B + 1), T, 8, s->num_sms), T, 0, st>>>(C, B, s->col_off,
+                                                                                          s->perm, s->info, s->cstart);
+    int* dmin = (int*)s->deg;
+    int* dmax = (int*)s->adj_off;
+    cudaMemsetAsync(dmin, 0x7F, (size_t)std::max<int64_t>(ninc, 1) * sizeof(int), st);
+    cudaMemsetAsync(dmax, 0x80, (size_t)std::max<int64_t>(ninc, 1) * sizeof(int), st);
+    k_body_blocks<<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(C, ninc, B, s->perm, ib1, ib2, anchor, finc, dmin,
+                                                                dmax);
+    k_chunk_windows<<<B, T, 0, st>>>(C, ninc, s->cstart, s->perm, ib1, ib2, anchor, finc, dmin, dmax, s->info,
+                                      s->dep);
+    cudaMemsetAsync(s->prog, 0xFF, (size_t)B * sizeof(int), st);
+    if (s->timing) s->phase_launches[2] += 3;
+    return cuda_check(s, cudaGetLastError(), "solve: dependency windows");
 }
 
 // --- one launch per colour ------------------------------------------------

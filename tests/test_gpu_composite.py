@@ -67,9 +67,13 @@ def _pile(seed=1, **kw):
     return sc
 
 
+@pytest.mark.parametrize("schedule", ["windows", "global"])
 @pytest.mark.parametrize("mu", [0.4, 0.05])
-def test_composite_pile_matches_oracle(nb, oracle_mod, mu):
-    sc = _with(_pile(), mu=mu)
+def test_composite_pile_matches_oracle(nb, oracle_mod, mu, schedule):
+    """Both schedules of the composite sweep: dependency windows between
+    blocks, or a grid barrier after every colour."""
+    flags = nb.NBGS_SWEEP_GLOBAL_SYNC if schedule == "global" else 0
+    sc = _with(_pile(), mu=mu, sweep_flags=flags)
     g, o = nb.Scene(sc), oracle_mod.OracleScene(sc)
     for _ in range(4):
         sg, so, bo = _step_and_compare(g, o, 40)
