@@ -347,8 +347,8 @@ nbgs_status nbgs_set_subdomains(nbgs_scene* scene, int32_t mode, const int32_t* 
  * wall (j2 = n_members + k); their levers are full vectors, so the
  * one-contact problem has a full 3x3 Delassus block: separation, sticking,
  * else the sliding root of the friction direction equation (a trigonometric
- * polynomial of degree 2, bracketed by 64 samples and bisected; the valid
- * root of least 1/2 p.W p + b.p).  The velocity step adds the gyroscopic
+ * polynomial of degree 2, bracketed by 64 samples and refined by Newton
+ * steps kept inside the bracket; the valid root of least 1/2 p.W p + b.p).  The velocity step adds the gyroscopic
  * term -w x I w of eq. integrationscheme.  nbgs_get_bodies and
  * nbgs_set_bodies take bodies (n_bodies rows, centres of mass); colours,
  * contacts and residual histories work as for spheres.  Not available for
