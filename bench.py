@@ -181,7 +181,8 @@ class ClockSampler:
 def measured_traffic(prec, contacts, sweeps, variant="", kernel="k_solve_persistent"):
     """DRAM bytes per launch of the sweep kernel from the committed ncu
     capture (profiles/traffic.json), scaled by the contact updates of one
-    launch; None when the kernel source changed since the capture."""
+    launch; None when the kernel's sources (the entry's "sources", else
+    solve.cu and nbgs_internal.cuh) changed since the capture."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
@@ -191,7 +192,7 @@ def measured_traffic(prec, contacts, sweeps, variant="", kernel="k_solve_persist
     if not d:
         return None
     src = b"".join(open(os.path.join(ROOT, "paper_1501_05810_gb300", "csrc", f), "rb").read()
-                   for f in ("solve.cu", "nbgs_internal.cuh"))
+                   for f in d.get("sources", ("solve.cu", "nbgs_internal.cuh")))
     if hashlib.sha256(src).hexdigest()[:16] != d["source_sha256_16"]:
         return None
     return d["dram_bytes_per_update"] * contacts * sweeps
