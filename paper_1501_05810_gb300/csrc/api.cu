@@ -182,6 +182,18 @@ bool subdomains_valid(int32_t mode, const int32_t g[3])
     return true;
 }
 
+// The parameters every scene needs, checked where a scene is created and
+// where a checkpoint replaces them.
+bool params_valid(const nbgs_params* p)
+{
+    if (!(p->dt > 0.0) || !(p->tau > 0.0) || !(p->omega > 0.0) || !(p->mu >= 0.0)) return false;
+    if (p->precision != NBGS_FP64 && p->precision != NBGS_FP32) return false;
+    if (p->warm_start < NBGS_WARM_NONE || p->warm_start > NBGS_WARM_MLP) return false;
+    for (int a = 0; a < 3; ++a)
+        if (!(p->box_hi[a] > p->box_lo[a])) return false;
+    return subdomains_valid(p->subdomain_mode, p->subdomains);
+}
+
 }  // namespace nbgs
 
 using namespace nbgs;
@@ -360,15 +372,7 @@ static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_des
 {
     if (!params || !out || n < 0 || n > 0x7FFFFFF0LL) return NBGS_EINVAL;
     if (n > 0 && (!pos || !vel || !angvel || !radius || !density)) return NBGS_EINVAL;
-    if (!(params->dt > 0.0) || !(params->tau > 0.0) || !(params->omega > 0.0) || !(params->mu >= 0.0))
-        return NBGS_EINVAL;
-    if (params->precision != NBGS_FP64 && params->precision != NBGS_FP32) return NBGS_EINVAL;
-    if (params->warm_start < NBGS_WARM_NONE || params->warm_start > NBGS_WARM_MLP) return NBGS_EINVAL;
-    for (int a = 0; a < 3; ++a)
-        if (!(params->box_hi[a] > params->box_lo[a])) return NBGS_EINVAL;
-    if (!subdomains_valid(params->subdomain_mode, params->subdomains) ||
-        (batch && params->subdomain_mode != NBGS_SUB_NONE))
-        return NBGS_EINVAL;
+    if (!params_valid(params) || (batch && params->subdomain_mode != NBGS_SUB_NONE)) return NBGS_EINVAL;
     *out = nullptr;
     nbgs_scene* s = new (std::nothrow) nbgs_scene();
     if (!s) return NBGS_ENOMEM;

@@ -13,6 +13,7 @@
 // (n x 32 B), vel (2n x 16 B FP32 / 32 B FP64), finite (n B), then, if
 // has_prev: row offsets by j1 (n + 1 u32), j2 (prev_count u32), world
 // impulses (prev_count x 32 B), then, if has_mlp: 9,347 FP32 parameters.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -120,6 +121,7 @@ nbgs_status run_save_state(nbgs_scene* s, const char* path)
 }
 
 nbgs_status grow_contacts(nbgs_scene* s, int64_t need);  // api.cu
+bool params_valid(const nbgs_params* p);                  // api.cu
 
 nbgs_status run_load_state(nbgs_scene* s, const char* path)
 {
@@ -138,9 +140,12 @@ nbgs_status run_load_state(nbgs_scene* s, const char* path)
         if (h.prm.box_lo[a] != s->prm.box_lo[a] || h.prm.box_hi[a] != s->prm.box_hi[a] ||
             (h.prm.periodic[a] != 0) != (s->prm.periodic[a] != 0))
             return fail(s, NBGS_EINVAL, "load_state: the scene has another box");
-    if (h.planes.count < 0 || h.planes.count > kMaxPlanes || h.prev_count < 0 || h.prev_count > 0xFFFFFFF0LL ||
-        (h.has_prev && h.prm.warm_start == NBGS_WARM_NONE) ||
-        !subdomains_valid(h.prm.subdomain_mode, h.prm.subdomains))
+    // everything below indexes device arrays or sizes the cell grid: the
+    // header must hold what a scene of this library can hold
+    if (h.planes.count < 0 || h.planes.count > kMaxPlanes || h.planes.ncones < 0 || h.planes.ncones > kMaxCones ||
+        h.prev_count < 0 || h.prev_count > 0xFFFFFFF0LL || (h.has_prev && h.prm.warm_start == NBGS_WARM_NONE) ||
+        !params_valid(&h.prm) || (h.prm.precision == NBGS_FP32) != s->fp32 || !std::isfinite(h.r_max) ||
+        !(h.r_max >= 0.0))
         return fail(s, NBGS_EINVAL, "load_state: corrupt header");
     const int64_t n = s->n;
     const size_t vbytes = s->fp32 ? 16 : 32;
@@ -156,6 +161,14 @@ nbgs_status run_load_state(nbgs_scene* s, const char* path)
         P.resize((size_t)h.prev_count * 32);
         ok = get(f.f, off.data(), off.size() * 4) && get(f.f, j2.data(), j2.size() * 4) && get(f.f, P.data(), P.size());
         if (ok) ok = off[0] == 0 && (int64_t)off[n] == h.prev_count;
+        for (int64_t i = 0; ok && i < n; ++i) ok = off[i] <= off[i + 1];   // rows inside [0, prev_count]
+    }
+    // radii (the fourth word of every position record) within the largest
+    // radius the cell grid is sized for
+    for (int64_t i = 0; ok && i < n; ++i) {
+        double r;
+        std::memcpy(&r, &pos[(size_t)i * 32 + 24], sizeof(r));
+        ok = r >= 0.0 && r <= h.r_max;
     }
     if (ok && h.has_mlp) {
         theta.resize((size_t)kMlpParams);

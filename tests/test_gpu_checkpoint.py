@@ -106,3 +106,57 @@ def test_mismatched_scene_and_damaged_file_are_refused(nb, tmp_path):
     fresh2 = nb.Scene(scenes.column(4, dt=1e-3, warm_start="prev"))
     with pytest.raises(nb.NBGSError, match="cannot open"):
         fresh2.load_state(str(tmp_path / "missing.nbgs"))
+
+
+def test_corrupt_header_and_rows_are_refused(nb, tmp_path):
+    """A damaged checkpoint is refused before anything reaches the device:
+    cone and plane counts beyond the arrays, parameters a scene could not be
+    created with, a precision other than the scene's, a non-finite largest
+    radius, warm-start rows that leave [0, prev_count], a radius beyond the
+    largest one.  The header layout (host byte order, natural alignment) is
+    checked against known values first."""
+    import struct
+    sc = scenes.column(4, dt=1e-3, warm_start="prev")
+    a = nb.Scene(sc)
+    a.step(3)
+    path = str(tmp_path / "ok.nbgs")
+    a.save_state(path)
+    data = bytearray(open(path, "rb").read())
+    hb, n = struct.unpack_from("<I", data, 12)[0], struct.unpack_from("<q", data, 16)[0]
+    prev_count = struct.unpack_from("<q", data, 32)[0]
+    assert n == 4 and prev_count > 0 and struct.unpack_from("<i", data, 28)[0] == 1
+    R_MAX, PRM, PLANES = 48, 56, 224
+    assert struct.unpack_from("<d", data, R_MAX)[0] == 0.5
+    assert struct.unpack_from("<d", data, PRM)[0] == 1e-3                       # prm.dt
+    assert struct.unpack_from("<i", data, PRM + 124)[0] == nb.NBGS_FP64          # prm.precision
+    assert struct.unpack_from("<i", data, PLANES)[0] == 1                       # planes.count
+    NCONES = PLANES + 8 + 16 * 24 + 16 * 8
+    assert struct.unpack_from("<i", data, NCONES)[0] == 0
+    vbytes = 32                                                                   # FP64 velocity records
+    OFF = hb + n * 32 + n * 32 + n * 2 * vbytes + n
+    assert struct.unpack_from("<I", data, OFF)[0] == 0
+    assert struct.unpack_from("<I", data, OFF + 4 * n)[0] == prev_count
+
+    def damaged(fmt, at, value):
+        d = bytearray(data)
+        struct.pack_into(fmt, d, at, value)
+        return d
+
+    cases = [("corrupt header", damaged("<i", NCONES, 1000)),
+             ("corrupt header", damaged("<i", PLANES, 17)),
+             ("corrupt header", damaged("<d", PRM, -1.0)),
+             ("corrupt header", damaged("<i", PRM + 124, nb.NBGS_FP32)),
+             ("corrupt header", damaged("<d", R_MAX, float("nan"))),
+             ("inconsistent", damaged("<I", OFF + 4, prev_count + 5)),
+             ("inconsistent", damaged("<d", hb + 32 * 2 + 24, 0.75))]   # radius of body 2 above r_max
+    for k, (msg, d) in enumerate(cases):
+        bad = str(tmp_path / f"bad{k}.nbgs")
+        open(bad, "wb").write(bytes(d))
+        fresh = nb.Scene(sc)
+        with pytest.raises(nb.NBGSError, match=msg) as e:
+            fresh.load_state(bad)
+        assert e.value.status == nb.NBGS_EINVAL
+    # the undamaged file still loads and steps
+    b = nb.Scene(sc)
+    b.load_state(path)
+    b.step(3)
