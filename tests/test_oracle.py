@@ -121,15 +121,21 @@ def test_one_contact_matches_brute_force_minimiser(oracle_mod):
 # contact detection (Sect. 4)
 # ---------------------------------------------------------------------------
 
-def _two_spheres(gap, ra=0.5, rb=0.3, va=(0, 0, 0), periodic=False, dt=1e-3, tau=0.01):
-    prm = scenes.default_params(dt=dt, tau=tau, gravity=(0, 0, 0), box_lo=(0, 0, 0), box_hi=(10, 10, 10),
+def _two_spheres(gap, ra=0.5, rb=0.3, va=(0, 0, 0), periodic=False, dt=1e-3, tau=0.01, origin=(0.0, 0.0, 0.0)):
+    """Two spheres in the box origin + [0, 10]^3 (the origin tests the wrap
+    and minimum image away from 0)."""
+    lo = np.asarray(origin, float)
+    prm = scenes.default_params(dt=dt, tau=tau, gravity=(0, 0, 0), box_lo=tuple(lo), box_hi=tuple(lo + 10.0),
                                 periodic=(1, 1, 1) if periodic else (0, 0, 0))
     if periodic:
         pos = [[0.2, 5.0, 5.0], [10.0 + 0.2 - (ra + rb + gap), 5.0, 5.0]]
     else:
         pos = [[5.0, 5.0, 5.0], [5.0 + ra + rb + gap, 5.0, 5.0]]
-    return scenes._scene("pair", prm, np.array(pos), np.array([va, (0, 0, 0)], float), np.zeros((2, 3)),
+    return scenes._scene("pair", prm, np.array(pos) + lo, np.array([va, (0, 0, 0)], float), np.zeros((2, 3)),
                          [ra, rb], [1.0, 1.0], [])
+
+
+ORIGINS = [(0.0, 0.0, 0.0), (-7.5, 3.25, -2.0)]
 
 
 def test_pair_geometry_and_hull_threshold(oracle_mod):
@@ -147,8 +153,9 @@ def test_pair_geometry_and_hull_threshold(oracle_mod):
         assert o.detect_contacts() == keep, gap
 
 
-def test_periodic_minimum_image(oracle_mod):
-    o = oracle_mod.OracleScene(_two_spheres(0.001, periodic=True))
+@pytest.mark.parametrize("origin", ORIGINS)
+def test_periodic_minimum_image(oracle_mod, origin):
+    o = oracle_mod.OracleScene(_two_spheres(0.001, periodic=True, origin=origin))
     assert o.detect_contacts() == 1
     c = o.get_contacts()
     # body 0 sits just right of x = 0, body 1 just left of x = 10: the normal
@@ -419,14 +426,17 @@ def test_free_flight_and_quaternion_rotation(oracle_mod):
     assert min(np.abs(q - qe).max(), np.abs(q + qe).max()) < 5 * dt
 
 
-def test_periodic_wrap(oracle_mod):
-    sc = _two_spheres(1.0, periodic=True)
+@pytest.mark.parametrize("origin", ORIGINS)
+def test_periodic_wrap(oracle_mod, origin):
+    """A sphere leaving through x = lo re-enters at hi: x' = lo + ((x + v dt - lo) mod L)."""
+    sc = _two_spheres(1.0, periodic=True, origin=origin)
     sc["vel"] = np.array([[-30.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
     sc["params"]["dt"] = 0.01
     o = oracle_mod.OracleScene(sc)
     o.step(1)
     x = o.get_bodies()["pos"][0, 0]
-    assert abs(x - (10.0 + 0.2 - 0.3)) < 1e-12 and 0.0 <= x < 10.0
+    lo = origin[0]
+    assert abs(x - (lo + 10.0 + 0.2 - 0.3)) < 1e-12 and lo <= x < lo + 10.0
 
 
 def test_config1_runs_clean(oracle_mod):
@@ -601,7 +611,10 @@ def _alg1_literal(oracle_mod, sc, sub, omega, sweeps):
     previous one of every other contact -- leaving out contact j itself
     (F_j^{-1}(0, lambda~ of the others)).  Cold start, contact order:
     colours ascending, canonical inside.  Returns the impulses and the body
-    velocities after `sweeps` sweeps."""
+    velocities after `sweeps` sweeps; the residual of every sweep, the largest
+    velocity change diag(w_n, w_t, w_t) (p_next - p) of a contact over
+    v_ref = max(largest speed at the step's start, |g| dt, 1e-12) (the
+    convergence criterion of Sect. 5), is left in _alg1_literal.history."""
     o = oracle_mod.OracleScene(sc)
     o.detect_contacts()
     o.colour_contacts()
@@ -643,6 +656,8 @@ def _alg1_literal(oracle_mod, sc, sub, omega, sweeps):
         np.add.at(w, jb, -invI[jb, None] * np.cross(lb[dyn_b, None] * nrm[dyn_b], P[dyn_b]))
         return v, w
 
+    v_ref = max(np.linalg.norm(b0["vel"], axis=1).max(), np.linalg.norm(prm["gravity"]) * dt, 1e-12)
+    _alg1_literal.history = []
     p_k = np.zeros((C, 3))
     for _ in range(sweeps):
         p_next = p_k.copy()
@@ -657,6 +672,8 @@ def _alg1_literal(oracle_mod, sc, sub, omega, sweeps):
             bvec = T[j] @ u + np.array([bias[j], 0.0, 0.0])
             y = oracle_mod.one_contact(wn[j], wt[j], mu, bvec)
             p_next[j] = omega * np.asarray(y) + (1.0 - omega) * p_k[j]
+        dw = (p_next - p_k) * np.stack([wn, wt, wt], -1)
+        _alg1_literal.history.append(np.linalg.norm(dw, axis=1).max() / v_ref)
         p_k = p_next
     v, w = velocities(p_k)
     return p_k, v, w
@@ -688,6 +705,8 @@ def test_subdomain_nbgs_matches_alg1_literal(oracle_mod, sub, omega):
     assert np.abs(p - p_ref).max() <= 1e-12 * np.abs(p_ref).max()
     assert np.abs(b["vel"] - v_ref).max() <= 1e-12 * np.abs(v_ref).max()
     assert np.abs(b["angvel"] - w_ref).max() <= 1e-12 * max(np.abs(w_ref).max(), 1e-300)
+    hist = np.asarray(o.residual_history())
+    assert len(hist) == sweeps and np.abs(hist - _alg1_literal.history).max() <= 1e-10 * max(hist)
 
 
 def test_alg1_literal_reproduces_classic_nbgs(oracle_mod):
@@ -700,6 +719,8 @@ def test_alg1_literal_reproduces_classic_nbgs(oracle_mod):
     p_ref, v_ref, _ = _alg1_literal(oracle_mod, sc, np.zeros(len(o.get_contacts()["j1"]), np.int64), 1.0, 3)
     assert np.abs(o.get_contacts()["impulse"] - p_ref).max() <= 1e-12 * np.abs(p_ref).max()
     assert np.abs(o.get_bodies()["vel"] - v_ref).max() <= 1e-12 * np.abs(v_ref).max()
+    hist = np.asarray(o.residual_history())
+    assert len(hist) == 3 and np.abs(hist - _alg1_literal.history).max() <= 1e-10 * max(hist)
 
 
 def test_one_subdomain_is_classic_nbgs(oracle_mod):
@@ -868,6 +889,71 @@ def test_general_one_contact_takes_the_least_energy_slide(oracle_mod):
     assert checked > 100
 
 
+def _coupled_case(rng):
+    """A strongly coupled one-contact problem: one or two bodies with long
+    levers and small, anisotropic inertia tensors, mu up to 3, approaching."""
+    W = np.zeros((3, 3))
+    for _ in range(rng.integers(1, 3)):
+        m = rng.uniform(0.5, 2.0)
+        A = rng.normal(size=(3, 3))
+        I = A @ A.T * rng.uniform(0.01, 1.0) + 0.01 * np.eye(3)
+        lev = rng.normal(size=3) * rng.uniform(0.5, 3.0)
+        W += np.eye(3) / m - _skew(lev) @ np.linalg.inv(I) @ _skew(lev)
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    W = Q.T @ W @ Q
+    mu = rng.uniform(0.5, 3.0)
+    b = rng.normal(size=3)
+    b[0] = -abs(b[0])
+    return W, mu, b
+
+
+def _slide_energies(W, mu, b, n=400000):
+    """Energies 1/2 p.W p + b.p of every valid sliding state (D > 0, u_t
+    against the friction direction) found by a dense scan of the angle with a
+    secant step inside each sign change."""
+    th = np.linspace(0.0, 2 * np.pi, n + 1)[:-1]
+    c, s = np.cos(th), np.sin(th)
+    D = W[0, 0] + mu * (W[0, 1] * c + W[0, 2] * s)
+    vt = -b[0] * (W[1, 0] + mu * (W[1, 1] * c + W[1, 2] * s)) + D * b[1]
+    vo = -b[0] * (W[2, 0] + mu * (W[2, 1] * c + W[2, 2] * s)) + D * b[2]
+    g = -s * vt + c * vo
+    out = []
+    for k in np.nonzero(np.sign(g) != np.sign(np.roll(g, -1)))[0]:
+        t0, k1 = th[k], (k + 1) % n
+        t1 = th[k1] + (2 * np.pi if k1 == 0 else 0.0)
+        t = t0 - g[k] * (t1 - t0) / (g[k1] - g[k])
+        cc, ss = np.cos(t), np.sin(t)
+        Dd = W[0, 0] + mu * (W[0, 1] * cc + W[0, 2] * ss)
+        ut = -b[0] * (W[1:, 0] + mu * (W[1:, 1:] @ np.array([cc, ss]))) / Dd + b[1:]
+        if Dd <= 0 or cc * ut[0] + ss * ut[1] > 0:
+            continue
+        q = -b[0] / Dd * np.array([1.0, mu * cc, mu * ss])
+        out.append(0.5 * q @ W @ q + b @ q)
+    return out
+
+
+def test_general_one_contact_chooses_among_several_slides(oracle_mod):
+    """Where the friction-direction equation has several valid sliding roots
+    (rare: four cases in 40,000 of a strongly coupled family, at fixed
+    places of its seeded stream, each with three), the solver returns the one
+    of least energy, not merely a valid one."""
+    rng = np.random.default_rng(5)
+    picks = {3864, 23274, 31903, 37769}
+    seen = 0
+    for it in range(max(picks) + 1):
+        W, mu, b = _coupled_case(rng)
+        if it not in picks:
+            continue
+        e = _slide_energies(W, mu, b)
+        assert len(e) >= 2 and max(e) - min(e) > 1e-6 * abs(min(e)), (it, e)
+        p, st = oracle_mod.one_contact_general(_w6(W), mu, b)
+        assert st == 0
+        ep = 0.5 * p @ W @ p + b @ p
+        assert abs(ep - min(e)) <= 1e-8 * abs(min(e)), (it, ep, e)
+        seen += 1
+    assert seen == len(picks)
+
+
 # ---------------------------------------------------------------------------
 # composite particles (Sect. 2: composites of convex particles)
 # ---------------------------------------------------------------------------
@@ -885,6 +971,9 @@ def test_single_member_composites_are_spheres(oracle_mod):
     ba, bb = a.get_bodies(), b.get_bodies()
     assert np.abs(ba["vel"] - bb["vel"]).max() <= 1e-11 * np.abs(ba["vel"]).max()
     assert np.abs(ba["pos"] - bb["pos"]).max() <= 1e-12
+    # the residual |W dp| of the full block reduces to |diag(w_n, w_t, w_t) dp|
+    ha, hb = np.asarray(a.residual_history()), np.asarray(b.residual_history())
+    assert len(ha) == len(hb) == 30 and np.abs(ha - hb).max() <= 1e-9 * ha.max()
 
 
 def _mc_inertia(offsets, radii, density, rng, samples=400000):
@@ -1055,7 +1144,90 @@ def test_composite_arguments_are_checked(oracle_mod):
     bad = [dict(good, density=np.array([0.0])),
            dict(good, members=dict(good["members"], body=np.array([0, 1], np.int32))),
            dict(good, members=dict(good["members"], radius=np.array([0.5, -0.1]))),
+           dict(good, members=dict(good["members"], radius=np.array([0.5, 0.0]))),   # a member has volume
            dict(good, params=dict(good["params"], subdomains="jacobi"))]
     for sc in bad:
         with pytest.raises(RuntimeError):
             oracle_mod.OracleScene(sc)
+
+
+def test_plane_capacity(oracle_mod):
+    """Sixteen walls fit; a seventeenth is refused."""
+    sc = scenes.column(2, dt=1e-3)
+    far = [((0.0, 0.0, 1.0), -10.0 - k) for k in range(16)]
+    o = oracle_mod.OracleScene(dict(sc, planes=far))
+    assert o.detect_contacts() == 1   # the pair only: every wall is far below
+    with pytest.raises(RuntimeError):
+        oracle_mod.OracleScene(dict(sc, planes=far + [((0.0, 0.0, 1.0), 0.0)]))
+
+
+def test_subdomain_of_a_body_on_the_upper_faces(oracle_mod):
+    """A centre exactly on box_hi lies in the last cell of every axis (the
+    clamp to g - 1 of the grid rule), one on box_lo in the first."""
+    g = (3, 2, 4)
+    prm = scenes.default_params(dt=1e-3, gravity=(0, 0, 0), box_lo=(-1.0, 0.0, 2.0), box_hi=(5.0, 4.0, 10.0),
+                                subdomains=g, tau=0.01)
+    pos = np.array([[5.0, 4.0, 10.0], [5.0, 4.0, 9.0], [-1.0, 0.0, 2.0], [-1.0, 1.0, 2.0]])
+    sc = scenes._scene("faces", prm, pos, np.zeros((4, 3)), np.zeros((4, 3)), np.full(4, 0.5), np.ones(4), [])
+    o = oracle_mod.OracleScene(sc)
+    o.detect_contacts()
+    o.colour_contacts()
+    c = o.get_contacts()
+    ids = o.contact_subdomains()
+    assert len(ids) == 2
+    want = {0: (g[2] - 1) * g[1] * g[0] + (g[1] - 1) * g[0] + (g[0] - 1), 2: 0}
+    for j1, sid in zip(c["j1"], ids):
+        assert sid == want[int(j1)], (j1, sid)
+
+
+def test_set_bodies_round_trip_and_free_flight(oracle_mod):
+    """Bodies set are the bodies read back, bit for bit; one contact-free step
+    without gravity then moves every sphere by dt v and keeps its angular
+    velocity (no torque, no gyroscopic term for a sphere)."""
+    rng = np.random.default_rng(21)
+    n = 5
+    prm = scenes.default_params(dt=0.01, gravity=(0.0, 0.0, 0.0), box_lo=(-20, -20, -20), box_hi=(20, 20, 20))
+    pos0 = np.stack([np.arange(n) * 3.0 - 6.0, np.zeros(n), np.zeros(n)], -1)
+    sc = scenes._scene("spaced", prm, pos0, np.zeros((n, 3)), np.zeros((n, 3)), np.full(n, 0.5), np.ones(n), [])
+    o = oracle_mod.OracleScene(sc)
+    pos = pos0 + rng.uniform(-0.2, 0.2, (n, 3))
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    vel, ang = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    o.set_bodies(pos, q, vel, ang)
+    b = o.get_bodies()
+    for k, want in (("pos", pos), ("quat", q), ("vel", vel), ("angvel", ang)):
+        assert np.array_equal(b[k], want), k
+    assert o.step(5)["n_contacts"] == 0
+    b = o.get_bodies()
+    assert np.abs(b["pos"] - (pos + 0.01 * vel)).max() <= 1e-15 * 10
+    assert np.array_equal(b["vel"], vel) and np.array_equal(b["angvel"], ang)
+
+
+def test_composite_member_wall_gaps_under_a_tilted_plane(oracle_mod):
+    """Member-wall contacts of a rotated asymmetric composite against a plane
+    with a general normal: every member is a contact with gap
+    n . (X + R(q) d') - c - r and normal n (the large margin keeps all of
+    them), with X the centre of mass and d' the offsets from it, R(q)
+    from scipy's rotation of the quaternion."""
+    from scipy.spatial.transform import Rotation
+    nrm = np.array([0.48, 0.6, 0.64])
+    sc = scenes.spinning_body(angvel=(0.0, 0.0, 0.0), tau=1.0)
+    d = np.asarray(sc["members"]["offset"], float)
+    r = np.asarray(sc["members"]["radius"], float)
+    m = 4.0 / 3.0 * math.pi * r ** 3
+    dprime = d - (m[:, None] * d).sum(0) / m.sum()
+    rng = np.random.default_rng(8)
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    X = np.array([1.5, -2.0, 0.75])
+    pm = X + Rotation.from_quat([q[1], q[2], q[3], q[0]]).apply(dprime)
+    c = (pm @ nrm - r).min() - 0.3
+    sc["planes"] = [(tuple(nrm), float(c))]
+    o = oracle_mod.OracleScene(sc)
+    o.set_bodies(X[None], q[None], np.zeros((1, 3)), np.zeros((1, 3)))
+    assert o.detect_contacts() == len(r)
+    ct = o.get_contacts()
+    assert np.array_equal(ct["j1"], np.arange(len(r))) and np.all(ct["j2"] == len(r))
+    assert np.abs(ct["xi"] - (pm @ nrm - c - r)).max() <= 1e-12
+    assert np.abs(ct["normal"] - nrm).max() <= 1e-15
