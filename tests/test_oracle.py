@@ -1231,3 +1231,87 @@ def test_composite_member_wall_gaps_under_a_tilted_plane(oracle_mod):
     assert np.array_equal(ct["j1"], np.arange(len(r))) and np.all(ct["j2"] == len(r))
     assert np.abs(ct["xi"] - (pm @ nrm - c - r)).max() <= 1e-12
     assert np.abs(ct["normal"] - nrm).max() <= 1e-15
+
+
+def test_composite_solve_conserves_angular_momentum(oracle_mod):
+    """Without gravity and spin, one solve changes every body's momentum by
+    the contact impulses only; each impulse acts on both bodies at the same
+    contact point with opposite signs, so sum X x m v + I w (orientations
+    still the identity, positions not yet moved) is conserved to rounding.
+    A lever aimed at another member, or one body's torque about the wrong
+    point, breaks it."""
+    sc = scenes.composite_gas(4, 4, 3, seed=2, spacing=0.97, v_max=1.0, walls=False, dt=2e-2,
+                              gravity=(0.0, 0.0, 0.0))
+    o = oracle_mod.OracleScene(sc)
+    b0 = o.get_bodies()
+    invm, I0 = o.body_mass_properties()
+    m = 1.0 / invm
+
+    def L(b):
+        return (np.cross(b["pos"], m[:, None] * b["vel"]) + np.einsum("nij,nj->ni", I0, b["angvel"])).sum(0)
+
+    assert np.all(b0["angvel"] == 0.0) and np.all(b0["quat"] == [1.0, 0.0, 0.0, 0.0])
+    nc = o.detect_contacts()
+    o.colour_contacts()
+    o.solve_nbgs(20)
+    b1 = o.get_bodies()
+    assert nc > 10 and np.abs(b1["angvel"]).max() > 1e-3     # the contacts did spin bodies up
+    assert np.array_equal(b1["pos"], b0["pos"])
+    scale = (np.linalg.norm(b0["pos"], axis=1) * m * np.linalg.norm(b0["vel"], axis=1)).sum()
+    assert np.abs(L(b1) - L(b0)).max() <= 1e-13 * scale
+
+
+def test_sphere_plane_gaps_under_a_tilted_plane(oracle_mod):
+    """Sphere-wall contacts against a plane of general normal n, solid
+    {y : n.y <= c}: gap n.x - c - r, normal n, for spheres at random points."""
+    rng = np.random.default_rng(31)
+    n = 6
+    nrm = np.array([0.48, -0.6, 0.64])
+    pos = rng.uniform(-3.0, 3.0, (n, 3))
+    r = rng.uniform(0.3, 0.6, n)
+    prm = scenes.default_params(dt=1e-3, gravity=(0, 0, 0), tau=2.0, box_lo=(-20, -20, -20), box_hi=(20, 20, 20))
+    pos[:, 0] += np.arange(n) * 10.0 - 25.0    # far apart: wall contacts only
+    pos[:, 0] = np.clip(pos[:, 0], -19.0, 19.0)
+    c = float((pos @ nrm - r).min() - 0.2)
+    sc = scenes._scene("tilted", prm, pos, np.zeros((n, 3)), np.zeros((n, 3)), r, np.ones(n), [(tuple(nrm), c)])
+    o = oracle_mod.OracleScene(sc)
+    o.detect_contacts()
+    ct = o.get_contacts()
+    walls = ct["j2"] == n
+    gaps = pos @ nrm - c - r
+    keep = gaps <= 2.0 * 2.0                   # hull tau + tau, no motion
+    assert np.array_equal(np.sort(ct["j1"][walls]), np.nonzero(keep)[0]) and keep.sum() >= 2
+    assert np.abs(ct["xi"][walls] - gaps[ct["j1"][walls].astype(int)]).max() <= 1e-12
+    assert np.abs(ct["normal"][walls] - nrm).max() <= 1e-15
+
+
+@pytest.mark.parametrize("composite", [False, True])
+def test_coincident_centres_take_the_z_normal(oracle_mod, composite):
+    """Two spheres (or one-member composites) at the same point: the closest
+    points are degenerate; the contact takes n = +z and xi = -(r_a + r_b)."""
+    prm = scenes.default_params(dt=1e-3, gravity=(0, 0, 0), box_lo=(-5, -5, -5), box_hi=(5, 5, 5))
+    sc = scenes._scene("same", prm, np.array([[0.5, -1.0, 2.0]] * 2), np.zeros((2, 3)), np.zeros((2, 3)),
+                       [0.5, 0.3], [1.0, 1.0], [])
+    o = oracle_mod.OracleScene(scenes.as_composites(sc) if composite else sc)
+    assert o.detect_contacts() == 1
+    ct = o.get_contacts()
+    assert np.array_equal(ct["normal"][0], [0.0, 0.0, 1.0]) and abs(ct["xi"][0] + 0.8) < 1e-15
+
+
+def test_composite_cold_steps_keep_no_impulse(oracle_mod):
+    """Without a warm start every step starts from zero impulses: a second
+    step equals the first step of a scene set to the state after the first."""
+    sc = scenes.composite_gas(4, 3, 3, seed=7, spacing=1.02, v_max=1.0, walls=False, dt=2e-2,
+                              gravity=(0.0, 0.0, 0.0))
+    a = oracle_mod.OracleScene(sc)
+    a.step(15)
+    mid = a.get_bodies()
+    a.step(15)
+    b = oracle_mod.OracleScene(sc)
+    b.set_bodies(mid["pos"], mid["quat"], mid["vel"], mid["angvel"])
+    b.step(15)
+    ca, cb = a.get_contacts(), b.get_contacts()
+    assert len(ca["j1"]) > 5
+    assert np.array_equal(ca["impulse"], cb["impulse"])
+    for k in ("pos", "quat", "vel", "angvel"):
+        assert np.array_equal(a.get_bodies()[k], b.get_bodies()[k]), k
