@@ -1315,3 +1315,18 @@ def test_composite_cold_steps_keep_no_impulse(oracle_mod):
     assert np.array_equal(ca["impulse"], cb["impulse"])
     for k in ("pos", "quat", "vel", "angvel"):
         assert np.array_equal(a.get_bodies()[k], b.get_bodies()[k]), k
+
+
+def test_zero_sweeps_apply_no_reaction(oracle_mod):
+    """max_sweeps = 0 is a valid solve: the contacts keep their (cold) zero
+    impulses and the step is eq. (integrationscheme) without reactions,
+    v' = v + dt g, x' = x + dt v'."""
+    sc = scenes.column(3, dt=1e-3)
+    o = oracle_mod.OracleScene(sc)
+    st = o.step(0)
+    assert st["n_contacts"] == 3 and st["sweeps_done"] == 0
+    assert np.all(o.get_contacts()["impulse"] == 0.0)
+    b = o.get_bodies()
+    v = sc["vel"] + 1e-3 * np.asarray(sc["params"]["gravity"])
+    assert np.array_equal(b["vel"], v)
+    assert np.abs(b["pos"] - (sc["pos"] + 1e-3 * v)).max() <= 1e-15 * 10
