@@ -536,8 +536,12 @@ def test_cone_rim_distance_against_sampled_circle(oracle_mod):
         x = np.array([rad * math.cos(phi), rad * math.sin(phi), z])
         case, sd, n = o.cone_distance(0, x)
         assert case == 2
-        assert abs(sd - np.min(np.linalg.norm(rim - x, axis=1))) < 1e-6
+        dist = np.linalg.norm(rim - x, axis=1)
+        k = np.argmin(dist)
+        assert abs(sd - dist[k]) < 1e-6
         assert abs(np.linalg.norm(n) - 1.0) < 1e-12
+        # the normal points from the nearest rim point to x
+        assert np.abs(n - (x - rim[k]) / dist[k]).max() < 2e-3
 
 
 def test_cone_above_top_and_rotation_invariance(oracle_mod):
@@ -1330,3 +1334,18 @@ def test_zero_sweeps_apply_no_reaction(oracle_mod):
     v = sc["vel"] + 1e-3 * np.asarray(sc["params"]["gravity"])
     assert np.array_equal(b["vel"], v)
     assert np.abs(b["pos"] - (sc["pos"] + 1e-3 * v)).max() <= 1e-15 * 10
+
+
+def test_cone_capacity_and_pointed_cones(oracle_mod):
+    """Four cones fit and a fifth is refused; an orifice of radius 0 (a
+    pointed cone) is a cone: its face distance is zeta sin a - rho cos a."""
+    sc = scenes.column(2, dt=1e-3)
+    cones = [scenes.cone((0.0, 0.0, -20.0 - 5 * k), (0.0, 0.0, 1.0), 30.0, 1.0, 3.0) for k in range(4)]
+    oracle_mod.OracleScene(dict(sc, cones=cones))
+    with pytest.raises(RuntimeError):
+        oracle_mod.OracleScene(dict(sc, cones=cones + [scenes.cone((0.0, 0.0, -50.0), (0.0, 0.0, 1.0), 30.0, 1.0, 3.0)]))
+    o = oracle_mod.OracleScene(dict(sc, cones=[scenes.cone((0.0, 0.0, -20.0), (0.0, 0.0, 1.0), 30.0, 0.0, 3.0)]))
+    a = math.radians(30.0)
+    x = np.array([0.3, 0.4, -20.0 + 2.0])
+    case, sd, n = o.cone_distance(0, x)
+    assert case == 1 and abs(sd - (2.0 * math.sin(a) - 0.5 * math.cos(a))) < 1e-14
