@@ -1528,9 +1528,12 @@ int oracle_integrate(oracle_scene* s)
         qw += dt * dw; qx += dt * dx; qy += dt * dy; qz += dt * dz;
         double qn = sqrt(((qw * qw + qx * qx) + qy * qy) + qz * qz);
         q[0] = qw / qn; q[1] = qx / qn; q[2] = qy / qn; q[3] = qz / qn;
+        /* periodic axes: a centre that left [lo, hi) re-enters at the
+         * opposite face; one inside stays exactly where it is */
         for (int e = 0; e < 3; ++e) {
             if (!P->periodic[e]) continue;
             double L = P->box_hi[e] - P->box_lo[e];
+            if (x[e] >= P->box_lo[e] && x[e] < P->box_lo[e] + L) continue;
             double sft = fmod(x[e] - P->box_lo[e], L);
             if (sft < 0.0) sft += L;
             x[e] = P->box_lo[e] + sft;

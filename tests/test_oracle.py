@@ -434,9 +434,17 @@ def test_periodic_wrap(oracle_mod, origin):
     sc["params"]["dt"] = 0.01
     o = oracle_mod.OracleScene(sc)
     o.step(1)
-    x = o.get_bodies()["pos"][0, 0]
+    b = o.get_bodies()
+    x = b["pos"][0, 0]
     lo = origin[0]
     assert abs(x - (lo + 10.0 + 0.2 - 0.3)) < 1e-12 and lo <= x < lo + 10.0
+    # a body that stays inside is not moved by the wrap, not even by rounding
+    assert np.array_equal(b["pos"][1], sc["pos"][1])
+    # nor is one that moves inside: x + dt v exactly
+    sc["vel"] = np.array([[0.0, 0.0, 0.0], [0.37, -0.11, 0.23]])
+    o = oracle_mod.OracleScene(sc)
+    o.step(1)
+    assert np.array_equal(o.get_bodies()["pos"][1], sc["pos"][1] + 0.01 * sc["vel"][1])
 
 
 def test_config1_runs_clean(oracle_mod):
