@@ -1357,3 +1357,94 @@ def test_cone_capacity_and_pointed_cones(oracle_mod):
     x = np.array([0.3, 0.4, -20.0 + 2.0])
     case, sd, n = o.cone_distance(0, x)
     assert case == 1 and abs(sd - (2.0 * math.sin(a) - 0.5 * math.cos(a))) < 1e-14
+
+
+def _one_floor_contact(oracle_mod, xi=0.01, mu=0.4, dt=0.01, v_ref=1.0):
+    """A sphere (r 0.5, set to 1/m = 0.5, 1/I = 5) xi above the floor z = 0,
+    no gravity, starting at speed v_ref (the reference speed of the step);
+    detected, coloured and solved with zero sweeps, ready for velocities and
+    impulses to be set."""
+    prm = scenes.default_params(dt=dt, mu=mu, gravity=(0.0, 0.0, 0.0), tau=0.05, box_lo=(-5, -5, -1),
+                                box_hi=(5, 5, 5))
+    sc = scenes._scene("one", prm, np.array([[0.0, 0.0, 0.5 + xi]]), np.array([[0.0, 0.0, -v_ref]]),
+                       np.zeros((1, 3)), [0.5], [1.0], [((0.0, 0.0, 1.0), 0.0)])
+    o = oracle_mod.OracleScene(sc)
+    o.set_mass_properties(np.array([0.5]), np.array([5.0]))
+    assert o.detect_contacts() == 1
+    o.colour_contacts()
+    o.solve_nbgs(0)
+
+    def residuals(v, w, p):
+        o.set_bodies(sc["pos"], np.array([[1.0, 0.0, 0.0, 0.0]]), np.array([v], float), np.array([w], float))
+        o.set_impulses(np.array([p], float))
+        return o.final_residuals()
+    return residuals
+
+
+def test_final_residuals_vanish_exactly_where_the_constraints_hold(oracle_mod):
+    """Frame of the floor contact: n = z, t = x, o = y; the contact point is
+    0.51 below the centre (l_a = r + xi), so u = v + w x (-0.51 z); the gap
+    term is xi / dt = 1; w_n = 0.5, w_t = 0.5 + 5 (0.51)^2."""
+    res = _one_floor_contact(oracle_mod)
+    wt = 0.5 + 5.0 * 0.51 ** 2
+    # separating, no reaction: every residual 0
+    r = res((0.0, 0.0, 2.0), (0.0, 0.0, 0.0), (0.0, 0.0, 0.0))
+    assert all(v == 0.0 for v in r.values()), r
+    # approaching faster than the gap closes (u_n + xi/dt = -0.5) with no reaction
+    r = res((0.0, 0.0, -1.5), (0.0, 0.0, 0.0), (0.0, 0.0, 0.0))
+    assert abs(r["non_penetration"] - 0.5) < 1e-15 and abs(r["complementarity"] - 0.5) < 1e-15
+    assert r["cone"] == 0.0 and r["dissipation"] == 0.0
+    # closing exactly (u_n = -1), pressing (p_n = 0.8), sliding along -x with
+    # friction on the cone's edge against the sliding: everything holds
+    r = res((-1.0, 0.0, -1.0), (0.0, 0.0, 0.0), (0.8, 0.32, 0.0))
+    assert max(r.values()) <= 1e-15, r
+    # the same slide in a general direction, with spin: u_t = (0.3 - 1.02, -0.4 + 0.51)
+    ut = np.array([0.3 - 1.02, -0.4 + 0.51])
+    pt = -0.4 * 0.8 * ut / np.linalg.norm(ut)
+    r = res((0.3, -0.4, -1.0), (1.0, 2.0, 3.0), (0.8, pt[0], pt[1]))
+    assert max(r.values()) <= 1e-15, r
+    # sticking (u_t = 0: v_t cancels the spin at the contact) inside the cone
+    r = res((1.02, -0.51, -1.0), (1.0, 2.0, 0.0), (0.8, 0.1, -0.2))
+    assert max(r.values()) <= 1e-15, r
+
+
+def test_final_residuals_measure_each_violation(oracle_mod):
+    res = _one_floor_contact(oracle_mod)
+    wt = 0.5 + 5.0 * 0.51 ** 2
+    # friction beyond the cone by 0.18 (|p_t| = 0.5 against mu p_n = 0.32), sticking
+    r = res((1.02, -0.51, -1.0), (1.0, 2.0, 0.0), (0.8, 0.3, -0.4))
+    assert abs(r["cone"] - 0.18 * wt) < 1e-14 and r["non_penetration"] == 0.0
+    assert r["dissipation"] == 0.0 and r["complementarity"] <= 1e-14   # xi = 0.51 - 0.5 rounds
+    # a reaction while separating: u_n + xi/dt = 0.5 > 0 with p_n = 2 (w_n p_n = 1)
+    r = res((0.0, 0.0, -0.5), (0.0, 0.0, 0.0), (2.0, 0.0, 0.0))
+    assert abs(r["complementarity"] - 0.5) < 1e-15 and r["non_penetration"] == 0.0
+    # friction on the cone's edge but along the sliding instead of against it:
+    # | |u_t| p_t + mu p_n u_t | w_t = 2 mu p_n |u_t| w_t (v_ref = 1)
+    r = res((-1.0, 0.0, -1.0), (0.0, 0.0, 0.0), (0.8, -0.32, 0.0))
+    assert abs(r["dissipation"] - 2 * 0.32 * 1.0 * wt) < 1e-14 and r["cone"] == 0.0
+    # ... and perpendicular to it: |(|u_t| p_t + mu p_n u_t)| = sqrt(2) mu p_n |u_t|
+    r = res((-1.0, 0.0, -1.0), (0.0, 0.0, 0.0), (0.8, 0.0, 0.32))
+    assert abs(r["dissipation"] - math.sqrt(2.0) * 0.32 * wt) < 1e-14
+
+
+def test_final_residuals_scale_with_the_reference_speed(oracle_mod):
+    """Velocity residuals are divided by v_ref, the dissipation residual (a
+    velocity times w_t times an impulse) by v_ref^2."""
+    state = ((-1.0, 0.3, -1.5), (0.5, 0.0, 0.0), (0.8, -0.6, 0.2))
+    r1 = _one_floor_contact(oracle_mod, v_ref=1.0)(*state)
+    r2 = _one_floor_contact(oracle_mod, v_ref=2.0)(*state)
+    assert min(r1.values()) > 0.0, r1
+    for k in ("non_penetration", "cone", "complementarity"):
+        assert abs(r2[k] - r1[k] / 2.0) <= 1e-15 * r1[k], k
+    assert abs(r2["dissipation"] - r1["dissipation"] / 4.0) <= 1e-15 * r1["dissipation"]
+
+
+def test_periodic_wrap_of_a_centre_landing_on_the_upper_face(oracle_mod):
+    """x = hi exactly is outside [lo, hi): it wraps to lo, not to hi."""
+    sc = _two_spheres(5.0, periodic=True)
+    sc["pos"] = np.array([[9.5, 5.0, 5.0], [3.0, 5.0, 5.0]])
+    sc["vel"] = np.array([[50.0, 0.0, 0.0], [0.0, 0.0, 0.0]])
+    sc["params"]["dt"] = 0.01
+    o = oracle_mod.OracleScene(sc)
+    o.step(1)
+    assert 9.5 + 0.01 * 50.0 == 10.0 and o.get_bodies()["pos"][0, 0] == 0.0
