@@ -348,8 +348,9 @@ nbgs_status nbgs_set_subdomains(nbgs_scene* scene, int32_t mode, const int32_t* 
  * one-contact problem has a full 3x3 Delassus block: separation, sticking,
  * else the sliding root of the friction direction equation (a trigonometric
  * polynomial of degree 2, bracketed by 64 samples and refined by Newton
- * steps kept inside the bracket; the valid root of least 1/2 p.W p + b.p).  The velocity step adds the gyroscopic
- * term -w x I w of eq. integrationscheme.  nbgs_get_bodies and
+ * steps kept inside the bracket; the valid root of least 1/2 p.W p + b.p).
+ * The velocity step adds the gyroscopic term -w x I w of
+ * eq. integrationscheme.  nbgs_get_bodies and
  * nbgs_set_bodies take bodies (n_bodies rows, centres of mass); colours,
  * contacts and residual histories work as for spheres.  Not available for
  * composites: cones, nbgs_set_mass_properties, subdomains, the network warm
@@ -382,7 +383,10 @@ nbgs_status nbgs_get_subdomains(nbgs_scene* scene, int64_t cap, uint32_t* out, i
  * nbgs_load_state restores such a file into a scene created with the same
  * body count, box, periodic axes and sweep precision (else NBGS_EINVAL,
  * before anything is copied); the steps that follow are bit-identical to
- * those of the scene that saved it.  The parameters stored in the file
+ * those of the scene that saved it.  A damaged file is refused the same way:
+ * plane or cone counts beyond their arrays, parameters a scene could not be
+ * created with, a non-finite largest radius or a radius beyond it, and
+ * previous-step rows that do not rise from 0 to the stored contact count.  The parameters stored in the file
  * replace the scene's.  Synchronises.  Every error sticks in the scene, as
  * for the other calls. */
 nbgs_status nbgs_save_state(nbgs_scene* scene, const char* path);
