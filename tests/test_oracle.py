@@ -1448,3 +1448,24 @@ def test_periodic_wrap_of_a_centre_landing_on_the_upper_face(oracle_mod):
     o = oracle_mod.OracleScene(sc)
     o.step(1)
     assert 9.5 + 0.01 * 50.0 == 10.0 and o.get_bodies()["pos"][0, 0] == 0.0
+
+
+def test_scene_parameters_are_checked(oracle_mod):
+    """A time step must be positive; a subdomain grid needs at least one cell
+    per axis."""
+    sc = scenes.column(2, dt=1e-3)
+    oracle_mod.OracleScene(sc)
+    for bad in ({"dt": 0.0}, {"dt": -1e-3}, {"subdomains": (2, 0, 1)}):
+        with pytest.raises(RuntimeError):
+            oracle_mod.OracleScene(dict(sc, params=dict(sc["params"], **bad)))
+
+
+@pytest.mark.parametrize("composite", [False, True])
+def test_sweep_counts_and_histories(oracle_mod, composite):
+    """With tol = 0 a solve runs exactly max_sweeps sweeps and records one
+    residual per sweep, the last being the one it reports."""
+    sc = scenes.hcp_packing(3, 2, 2, dt=1e-3, tau=1e-3, mu=0.4, tilt_deg=30.0, v0=0.1)
+    o = oracle_mod.OracleScene(scenes.as_composites(sc) if composite else sc)
+    st = o.step(7)
+    h = o.residual_history()
+    assert st["sweeps_done"] == 7 and len(h) == 7 and h[-1] == st["residual"] and st["n_contacts"] > 0
