@@ -1342,6 +1342,10 @@ def test_zero_sweeps_apply_no_reaction(oracle_mod):
     v = sc["vel"] + 1e-3 * np.asarray(sc["params"]["gravity"])
     assert np.array_equal(b["vel"], v)
     assert np.abs(b["pos"] - (sc["pos"] + 1e-3 * v)).max() <= 1e-15 * 10
+    # impulses set on every contact are the impulses read back
+    imp = np.arange(9, dtype=float).reshape(3, 3) + 0.5
+    o.set_impulses(imp)
+    assert np.array_equal(o.get_contacts()["impulse"], imp)
 
 
 def test_cone_capacity_and_pointed_cones(oracle_mod):
