@@ -1473,3 +1473,24 @@ def test_sweep_counts_and_histories(oracle_mod, composite):
     st = o.step(7)
     h = o.residual_history()
     assert st["sweeps_done"] == 7 and len(h) == 7 and h[-1] == st["residual"] and st["n_contacts"] > 0
+
+
+@pytest.mark.parametrize("factor,kept", [(1.9, True), (2.1, False)])
+def test_cone_contact_keep_rule(oracle_mod, factor, kept):
+    """A sphere at rest (hull radius tau) inside a cone (half-angle 30 deg,
+    apex 0, axis z) at gap xi from the face is a contact iff xi <= tau + tau
+    (the wall's hull is tau alone)."""
+    tau, r, a = 0.05, 0.5, math.radians(30.0)
+    s_gen = 8.0                                              # on the face: s_o = 4 < s < s_t = 24
+    d = r + factor * tau                                     # centre to face along the inward normal
+    rho, zeta = s_gen * math.sin(a) - d * math.cos(a), s_gen * math.cos(a) + d * math.sin(a)
+    prm = scenes.default_params(dt=1e-3, tau=tau, gravity=(0.0, 0.0, 0.0), box_lo=(-20, -20, -5),
+                                box_hi=(20, 20, 30))
+    sc = scenes._scene("in_cone", prm, np.array([[rho, 0.0, zeta]]), np.zeros((1, 3)), np.zeros((1, 3)),
+                       [r], [1.0], [])
+    sc["cones"] = [scenes.cone((0.0, 0.0, 0.0), (0.0, 0.0, 1.0), 30.0, 2.0, 12.0)]
+    o = oracle_mod.OracleScene(sc)
+    assert o.detect_contacts() == (1 if kept else 0)
+    if kept:
+        c = o.get_contacts()
+        assert c["j2"][0] == 1 and abs(c["xi"][0] - factor * tau) < 1e-12
