@@ -73,3 +73,42 @@ def test_invalid_parameters_rejected_before_any_device_work(nb):
 def test_library_built_for_sm_103a_only(nb):
     from paper_1501_05810_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _c_layout(tmp_path, include_dir, header, structs):
+    """sizeof and every field offset of C structs, from gcc."""
+    lines = []
+    for cname, fields in structs:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        lines += [f'printf("%zu\\n", offsetof({cname}, {f}));' for f in fields]
+    src = tmp_path / "all_layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include <stdint.h>\n"
+                   f'#include "{header}"\nint main(void) {{\n' + "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "all_layout"
+    subprocess.run(["gcc", "-I", include_dir, str(src), "-o", str(exe)], check=True)
+    return [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+
+
+def _py_layout(pairs):
+    out = []
+    for _, cls in pairs:
+        out.append(C.sizeof(cls))
+        out += [getattr(cls, f).offset for f, _ in cls._fields_]
+    return out
+
+
+def test_every_field_of_the_binding_structs_matches_the_header(nb, tmp_path):
+    pairs = [("nbgs_params", nb.nbgs_params), ("nbgs_step_stats", nb.nbgs_step_stats),
+             ("nbgs_residuals", nb.nbgs_residuals), ("nbgs_batch_desc", nb.nbgs_batch_desc)]
+    got = _c_layout(tmp_path, os.path.join(ROOT, "include"), "nbgs.h",
+                    [(c, [f for f, _ in cls._fields_]) for c, cls in pairs])
+    assert got == _py_layout(pairs)
+
+
+def test_every_field_of_the_oracle_structs_matches_its_header(tmp_path):
+    import oracle
+    pairs = [("oracle_params", oracle.OracleParams), ("oracle_step_stats", oracle.OracleStepStats),
+             ("oracle_residuals", oracle.OracleResiduals)]
+    got = _c_layout(tmp_path, os.path.join(ROOT, "oracle"), "nbgs_oracle.h",
+                    [(c, [f for f, _ in cls._fields_]) for c, cls in pairs])
+    assert got == _py_layout(pairs)
