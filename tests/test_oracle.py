@@ -1349,13 +1349,16 @@ def test_zero_sweeps_apply_no_reaction(oracle_mod):
 
 
 def test_cone_capacity_and_pointed_cones(oracle_mod):
-    """Four cones fit and a fifth is refused; an orifice of radius 0 (a
-    pointed cone) is a cone: its face distance is zeta sin a - rho cos a."""
+    """Four cones fit and a fifth is refused, as is a zero axis; an orifice
+    of radius 0 (a pointed cone) is a cone: its face distance is
+    zeta sin a - rho cos a."""
     sc = scenes.column(2, dt=1e-3)
     cones = [scenes.cone((0.0, 0.0, -20.0 - 5 * k), (0.0, 0.0, 1.0), 30.0, 1.0, 3.0) for k in range(4)]
     oracle_mod.OracleScene(dict(sc, cones=cones))
     with pytest.raises(RuntimeError):
         oracle_mod.OracleScene(dict(sc, cones=cones + [scenes.cone((0.0, 0.0, -50.0), (0.0, 0.0, 1.0), 30.0, 1.0, 3.0)]))
+    with pytest.raises(RuntimeError):   # an axis needs a direction
+        oracle_mod.OracleScene(dict(sc, cones=[scenes.cone((0.0, 0.0, -20.0), (0.0, 0.0, 0.0), 30.0, 1.0, 3.0)]))
     o = oracle_mod.OracleScene(dict(sc, cones=[scenes.cone((0.0, 0.0, -20.0), (0.0, 0.0, 1.0), 30.0, 0.0, 3.0)]))
     a = math.radians(30.0)
     x = np.array([0.3, 0.4, -20.0 + 2.0])
