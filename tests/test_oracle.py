@@ -1497,3 +1497,34 @@ def test_cone_contact_keep_rule(oracle_mod, factor, kept):
     if kept:
         c = o.get_contacts()
         assert c["j2"][0] == 1 and abs(c["xi"][0] - factor * tau) < 1e-12
+
+
+def test_general_one_contact_falls_back_to_the_diagonal_form(oracle_mod):
+    """Where the 64 equal samples bracket no qualifying root (two seeded
+    cases of the strongly coupled family: in each, two roots fall inside one
+    sample interval, so g keeps its sign at both ends and the pair is
+    missed), the solver reports it and returns the diagonal closed form with
+    w_t the mean of the two tangential diagonal entries."""
+    rng = np.random.default_rng(5)
+    picks = {8251, 13987}
+    seen = 0
+    th = np.linspace(0.0, 2 * np.pi, 400001)[:-1]
+    for it in range(max(picks) + 1):
+        W, mu, b = _coupled_case(rng)
+        if it not in picks:
+            continue
+        D = W[0, 0] + mu * (W[0, 1] * np.cos(th) + W[0, 2] * np.sin(th))
+        vt = -b[0] * (W[1, 0] + mu * (W[1, 1] * np.cos(th) + W[1, 2] * np.sin(th))) + D * b[1]
+        vo = -b[0] * (W[2, 0] + mu * (W[2, 1] * np.cos(th) + W[2, 2] * np.sin(th))) + D * b[2]
+        g = -np.sin(th) * vt + np.cos(th) * vo
+        roots = th[np.nonzero(np.sign(g) != np.sign(np.roll(g, -1)))[0]]
+        bins = np.floor(roots / (2 * np.pi / 64)).astype(int)
+        assert len(bins) > len(set(bins.tolist())), (it, roots)      # a close pair in one interval
+        ps = -np.linalg.solve(W, b)
+        assert not (ps[0] > 0 and np.hypot(ps[1], ps[2]) <= mu * ps[0]) and b[0] < 0   # not sticking
+        p, st = oracle_mod.one_contact_general(_w6(W), mu, b)
+        assert st == -1
+        want = oracle_mod.one_contact(W[0, 0], 0.5 * (W[1, 1] + W[2, 2]), mu, b)
+        assert np.array_equal(p, want)
+        seen += 1
+    assert seen == len(picks)
