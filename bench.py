@@ -1,11 +1,14 @@
 """Benchmark of the NBGS granular time step on GB300.
 
 A step is one nbgs_step(): contact detection, colouring, NBGS sweeps
-(100 or residual 1e-6) and integration.  The default workload is the dense
-1M-sphere packing (hexagonal close packing 100 x 100 x 100, r = 0.5,
-mu = 0.5, dt = 5e-4, FP32 sweeps, FP64 positions): the sweep-dominated
-regime of the settled 1M-sphere packing.  Its working set (~1 GB) is larger
-than L2, so no flush is needed between steps.
+(100 or residual 1e-6) and integration.  The default workload is the settled
+1M-sphere pour: 1,000,000 polydisperse spheres (r ~ U(0.4, 0.6), density 1)
+poured from a loose lattice at volume fraction 0.3 into a walled
+100 x 100 x 200 box and settled under gravity (untimed, on the GPU: 3,000
+steps of 2e-3 with 30 sweeps), then measured at mu = 0.5, dt = 5e-4, 100
+sweeps or residual 1e-6, previous-step warm start, FP32 sweeps, FP64
+positions.  Its working set (~0.8 GB) is larger than L2, so no flush is
+needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -41,6 +44,13 @@ BYTES_COMP = {"fp32": (80 + 32 + 2 * 96, 80 + 32 + 96), "fp64": (160 + 64 + 2 * 
 
 def workload(name: str):
     from paper_1501_05810_gb300 import scenes
+    if name == "pour1m":
+        sc = scenes.loose_pour(seed=0, n=1_000_000, precision="fp32", warm_start="prev")
+        dt_s, sw_s, n_s = PRE_SETTLE["pour1m"]
+        desc = ("settled pour of 1,000,000 spheres r~U(0.4,0.6) (loose lattice at phi=0.3 in a walled 100x100x200 "
+                f"box, settled under gravity for {n_s} untimed steps of dt={dt_s:g} with {sw_s} sweeps), mu=0.5, "
+                "dt=5e-4, 100 sweeps or residual 1e-6, previous-step warm start, FP32 sweeps, FP64 positions")
+        return sc, desc
     if name == "dense1m":
         sc = scenes.dense_packing(1_000_000, seed=0, precision="fp32", warm_start="prev")
         desc = ("dense packing of 1,000,000 spheres (HCP 100x100x100, r=0.5, periodic x,y, walls z), "
@@ -94,10 +104,13 @@ def workload(name: str):
 
 
 # sweeps and tolerance per workload: (max_sweeps, tol)
-SOLVE = {"dense1m": (100, 1e-6), "config1": (50, 0.0), "gas": (50, 0.0), "ramp": (100, 0.0), "batch": (100, 1e-6),
+SOLVE = {"pour1m": (100, 1e-6), "dense1m": (100, 1e-6), "config1": (50, 0.0), "gas": (50, 0.0), "ramp": (100, 0.0), "batch": (100, 1e-6),
          "hopper": (100, 1e-6), "compgas": (10, 0.0), "comppile": (50, 0.0), "config1_1e6": (1000, 1e-6)}
 # untimed steps (sweeps, count) that bring a workload into its regime first
 SETTLE = {"hopper": (30, 2000), "config1_1e6": (50, 150)}
+# settled first in a scene of its own with a larger time step: (dt, sweeps,
+# steps); the measured scene starts from the settled state
+PRE_SETTLE = {"pour1m": (2e-3, 30, 3000)}   # the schedule of workloads.POUR_SETTLE
 
 
 def read_peaks():
@@ -220,14 +233,35 @@ def count_instances(g, n):
     return int(np.count_nonzero(per > 1)), int(np.maximum(per - 1, 0).sum())
 
 
-def cpu_baseline(steps_budget_s: float = 15.0):
-    """The oracle, as it stands, on a bounded sample of the same workload:
-    a 24 x 24 x 10 cut of the dense packing (5,760 spheres), whole steps
-    (O(N^2) detection + 100 sweeps) for about steps_budget_s seconds."""
+# the oracle's sample of the pour: a 2,000-sphere pour of the same recipe
+# (its box scaled with n^(1/3)), settled by the oracle itself (untimed)
+CPU_POUR_N, CPU_POUR_SETTLE = 2000, (2e-3, 30, 1500)
+
+
+def cpu_sample(name: str):
+    """(oracle scene, description) of the bounded CPU sample of a workload."""
     import oracle
     from paper_1501_05810_gb300 import scenes
+    if name == "pour1m":
+        sc = scenes.loose_pour(seed=1, n=CPU_POUR_N, warm_start="prev")
+        dt_s, sw_s, n_s = CPU_POUR_SETTLE
+        o = oracle.OracleScene(dict(sc, params=dict(sc["params"], dt=dt_s)))
+        for _ in range(n_s):
+            o.step(sw_s)
+        b = o.get_bodies()
+        o.close()
+        sc = dict(sc, pos=b["pos"], vel=b["vel"], angvel=b["angvel"])
+        return oracle.OracleScene(sc), (f"a {CPU_POUR_N:,}-sphere pour of the same recipe settled by the oracle "
+                                        f"({n_s} untimed steps of dt={dt_s:g}, {sw_s} sweeps)")
     sc = scenes.hcp_packing(24, 24, 10, radius=0.5, dt=5e-4, mu=0.5, tau=0.005)
-    o = oracle.OracleScene(sc)
+    return oracle.OracleScene(sc), "a 5,760-sphere 24x24x10 cut of the dense packing"
+
+
+def cpu_baseline(name: str = "pour1m", steps_budget_s: float = 15.0):
+    """The oracle, as it stands, on a bounded sample of the same workload
+    (cpu_sample), whole steps (O(N^2) detection + 100 sweeps or residual
+    1e-6) for about steps_budget_s seconds."""
+    o, what = cpu_sample(name)
     t0 = time.perf_counter()
     updates, steps = 0, 0
     while True:
@@ -238,9 +272,8 @@ def cpu_baseline(steps_budget_s: float = 15.0):
             break
     dt = time.perf_counter() - t0
     return {"value": updates / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} whole oracle steps (brute-force detection + {SWEEPS} sweeps / tol {TOL}) of a "
-                      f"5,760-sphere 24x24x10 cut of the dense packing, {updates:,} contact updates in {dt:.1f} s, "
-                      f"1 thread, host nproc={os.cpu_count()}"}
+            "sample": f"{steps} whole oracle steps (brute-force detection + {SWEEPS} sweeps / tol {TOL}) of {what}, "
+                      f"{updates:,} contact updates in {dt:.1f} s, 1 thread, host nproc={os.cpu_count()}"}, what
 
 
 def steps_to_residual(nbgs, torch, local, steps=30):
@@ -289,12 +322,13 @@ def reduce_over_ranks(dist, ms_total, updates, device):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    cb = cpu_baseline(min(20.0, 5.0 + 2.0 * args.steps))
+    name = args.workload if args.workload in ("pour1m", "dense1m") else "pour1m"
+    cb, what = cpu_baseline(name, min(20.0, 5.0 + 2.0 * args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "oracle on a 5,760-sphere cut of the dense 1M-sphere packing (the full "
-                                   "size needs O(N^2) detection)", "l2": "inputs smaller than L2 (CPU run)"},
+            "config": {"workload": f"oracle on {what} (the full size needs O(N^2) detection)",
+                       "l2": "inputs smaller than L2 (CPU run)"},
             "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -307,7 +341,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="dense1m")
+    ap.add_argument("--workload", default="pour1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--sweep-flags", type=int, default=None, help="nbgs_params.sweep_flags override")
@@ -356,6 +390,10 @@ def main():
     prec = first["params"].get("precision", "fp64")
     stream = torch.cuda.Stream(device=local)
     with torch.cuda.stream(stream):
+        if args.workload in PRE_SETTLE:
+            from paper_1501_05810_gb300 import workloads
+            dt_s, sw_s, n_s = PRE_SETTLE[args.workload]
+            sc = workloads.settle(sc, dt_s, sw_s, n_s, device=f"cuda:{local}", stream=stream)
         if batch:
             g = nbgs.BatchScene(sc, device=f"cuda:{local}", stream=stream)
         else:
@@ -470,8 +508,8 @@ def main():
     }
     if args.workload == "dense1m":
         line["steps_to_residual"] = steps_to_residual(nbgs, torch, local)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "dense1m":
-        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("pour1m", "dense1m"):
+        line["cpu_baseline"] = cpu_baseline(args.workload)[0]
     if rank == 0:
         print(json.dumps(line), flush=True)
     g.close()

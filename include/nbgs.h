@@ -71,8 +71,11 @@ enum {                                           /* nbgs_params.sweep_flags bits
                                     blocks whose contacts share bodies with this block's contacts      */
     NBGS_SWEEP_TMA_STAGE = 2,    /* stage each block's chunk of the next colour (records, impulses)
                                     in shared memory with bulk copies while it waits                   */
-    NBGS_SWEEP_WARP_SYNC = 4     /* every warp has its own chunk, window and progress word, so the
+    NBGS_SWEEP_WARP_SYNC = 4,    /* every warp has its own chunk, window and progress word, so the
                                     warps of a block do not wait for one another (no TMA staging)      */
+    NBGS_SWEEP_GATHER2 = 8       /* a thread loads records, impulses and body states of two of its
+                                    contacts of a colour before relaxing either (block scheduling, no
+                                    TMA staging; three resident blocks per SM instead of four)         */
 };
 
 enum {                                           /* nbgs_params.subdomain_mode: s_c(j) of Alg. 1 */
@@ -253,8 +256,9 @@ nbgs_status nbgs_get_scene_stats(nbgs_scene* scene, int32_t* sweeps_done, double
 
 /* Autotuner: times the solve of the current contacts (state saved and
  * restored) under every sweep schedule (point-to-point or grid-barrier
- * synchronisation, with or without shared-memory staging) and 1 to the
- * maximum resident blocks per SM, keeps the fastest, and returns its
+ * synchronisation, with or without shared-memory staging, warp-level units,
+ * two contacts gathered per thread) and 1 to the maximum resident blocks
+ * per SM, keeps the fastest, and returns its
  * sweep_flags and blocks per SM.  Call after nbgs_detect_contacts and
  * nbgs_colour_contacts.  Synchronises. */
 nbgs_status nbgs_autotune(nbgs_scene* scene, int32_t max_sweeps, double tol, int32_t* sweep_flags,
@@ -399,6 +403,17 @@ nbgs_status nbgs_residual_history(nbgs_scene* scene, double* out, int32_t cap, i
  * velocities and impulses.  Synchronises. */
 nbgs_status nbgs_final_residuals(nbgs_scene* scene, nbgs_residuals* out);
 
+/* Replace the impulses of the current contacts (Sect. 5: Alg. 1 may start
+ * from any reactions; Sect. 3: p = dt lambda).  impulse: n_contacts x 3
+ * doubles, host or device memory, in the canonical contact order of
+ * nbgs_get_contacts() and in the contact frame (n, t, o); n_contacts is the
+ * count of the last nbgs_detect_contacts().  The values are copied: they
+ * become what nbgs_get_contacts() and nbgs_final_residuals() read and the
+ * previous-step impulses the next step's warm start matches.  Sphere scenes
+ * (and batches) after a solve of the current contacts, else NBGS_EINVAL;
+ * NBGS_ENOMEM if the staging buffer cannot be allocated.  Synchronises. */
+nbgs_status nbgs_set_impulses(nbgs_scene* scene, const double* impulse);
+
 /* Allocation-free variant of nbgs_final_residuals() for callers that cannot
  * allocate device memory (fixed arenas, plugins handed only buffers,
  * processes whose allocator belongs to someone else).  The paper has no
@@ -408,7 +423,11 @@ nbgs_status nbgs_final_residuals(nbgs_scene* scene, nbgs_residuals* out);
  * nbgs_get_bodies() produce: j1, j2 (n_contacts; j2 >= n_bodies marks a
  * wall), normal (n_contacts x 3), xi (n_contacts), impulse (n_contacts x 3,
  * contact frame), vel and angvel (n_bodies x 3), radius, invm, invI
- * (n_bodies).  dt, beta, mu and v_ref as in the scene and its step stats.
+ * (n_bodies).  dt, beta, mu and v_ref as in the scene and its step stats:
+ * one mu and one v_ref for all contacts, so the contacts of one sphere scene
+ * (not of a batch, whose scenes have their own mu and v_ref; composites are
+ * refused by nbgs_final_residuals as well).  Maxima above 1e300 and NaN are
+ * reported as +inf, as nbgs_final_residuals() does.
  * out: device pointer to 4 doubles, written in nbgs_residuals order.
  * Enqueued on `stream` (a cudaStream_t, NULL = legacy default stream).
  *
@@ -417,6 +436,8 @@ nbgs_status nbgs_final_residuals(nbgs_scene* scene, nbgs_residuals* out);
  * n_contacts may not exceed 2,097,152 (NBGS_ECAPACITY otherwise).  The
  * first call on a device looks up the array's address (cudaGetSymbolAddress)
  * with that device current: make that first call before any stream capture.
+ * Every later call on a stream that is not capturing looks it up again (so a
+ * device reset that reloads the library's module is followed).
  * All calls share the array, so calls that overlap on the GPU (different
  * streams, or different host threads on one device) race and may return
  * wrong maxima; serialise them.  Returns NBGS_EINVAL on bad arguments and

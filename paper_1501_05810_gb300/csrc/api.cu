@@ -807,11 +807,12 @@ nbgs_status nbgs_autotune(nbgs_scene* s, int32_t max_sweeps, double tol, int32_t
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int max_bps = std::max(1, s->max_coop_blocks / std::max(1, s->num_sms));
-    const int flags_list[5] = {0, NBGS_SWEEP_GLOBAL_SYNC, NBGS_SWEEP_TMA_STAGE,
-                               NBGS_SWEEP_GLOBAL_SYNC | NBGS_SWEEP_TMA_STAGE, NBGS_SWEEP_WARP_SYNC};
+    const int flags_list[6] = {0, NBGS_SWEEP_GLOBAL_SYNC, NBGS_SWEEP_TMA_STAGE,
+                               NBGS_SWEEP_GLOBAL_SYNC | NBGS_SWEEP_TMA_STAGE, NBGS_SWEEP_WARP_SYNC,
+                               NBGS_SWEEP_GATHER2};
     float best = 3.4e38f;
     int best_flags = s->prm.sweep_flags, best_bps = max_bps;
-    for (int fi = 0; fi < 5 && rc == NBGS_OK; ++fi) {
+    for (int fi = 0; fi < 6 && rc == NBGS_OK; ++fi) {
         for (int bps = 1; bps <= max_bps && rc == NBGS_OK; ++bps) {
             s->prm.sweep_flags = flags_list[fi];
             s->coop_blocks = bps * s->num_sms;
@@ -886,6 +887,17 @@ nbgs_status nbgs_residual_history(nbgs_scene* s, double* out, int32_t cap, int32
         }
         free(tmp);
     }
+    return rc;
+}
+
+nbgs_status nbgs_set_impulses(nbgs_scene* s, const double* impulse)
+{
+    NBGS_GUARD(s);
+    if (!impulse) return fail(s, NBGS_EINVAL, "set_impulses: null impulses");
+    if (s->composite) return fail(s, NBGS_EINVAL, "set_impulses: sphere scenes only");
+    if (!s->solved) return fail(s, NBGS_EINVAL, "set_impulses: solve the current contacts first");
+    nbgs_status rc = run_set_impulses(s, impulse);
+    if (rc == NBGS_OK) rc = check_device_errors(s);
     return rc;
 }
 

@@ -317,13 +317,16 @@ __device__ __forceinline__ bool wait_deps(const int* prog, int2 win, int g, DevI
 }
 
 // Publish that this block finished sweep phase g (after all its stores).
+// Phases are numbered 0, 1, 2, ... and a block publishes every one of them
+// in order, its word starting at -1, so advancing the word by one sets it to
+// g.  The increment is a release reduction: it orders the block's stores
+// (before the barrier) ahead of the new value without waiting for a reply.
 __device__ __forceinline__ void publish(int* prog, int g)
 {
+    (void)g;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicExch(prog + blockIdx.x, g);
-    }
+    if (threadIdx.x == 0)
+        asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(prog + blockIdx.x) : "memory");
 }
 
 
@@ -499,6 +502,7 @@ nbgs_status run_colour(nbgs_scene* s);
 nbgs_status run_solve(nbgs_scene* s, int max_sweeps, double tol);
 nbgs_status run_integrate(nbgs_scene* s);
 nbgs_status run_final_residuals(nbgs_scene* s, nbgs_residuals* out);
+nbgs_status run_set_impulses(nbgs_scene* s, const double* impulse);
 nbgs_status run_mlp_prologue(nbgs_scene* s, int apply, float* feat_out);
 nbgs_status run_subdomains(nbgs_scene* s);            // subdomain.cu: s_c(j), instances (after the adjacency)
 nbgs_status ensure_subdomain_buffers(nbgs_scene* s);  // subdomain.cu

@@ -26,8 +26,8 @@ constexpr int64_t kNaMaxContacts = (int64_t)kNaTile * kNaMaxBlocks;   // 2,097,1
 // Shared by every call on a device; the last call's partial maxima stay here.
 static __device__ __align__(256) double g_na_partial[4 * kNaMaxBlocks];
 
-// Device address of g_na_partial per device, taken once with that device
-// current (the host-side name is only a stand-in for the device symbol).
+// Device address of g_na_partial per device, taken with that device current
+// (the host-side name is only a stand-in for the device symbol).
 constexpr int kNaMaxDevices = 64;
 static double* g_na_addr[kNaMaxDevices] = {};
 static std::mutex g_na_mutex;
@@ -104,21 +104,30 @@ __global__ void k_na_final(int nblocks, const double* __restrict__ partial, doub
     if (threadIdx.x < 4) {
         double x = 0.0;
         for (int b = 0; b < nblocks; ++b) x = fmax(x, partial[4 * b + threadIdx.x]);
-        out[threadIdx.x] = x;
+        // as the scene entry point reports them: NaN and anything above 1e300 as +inf
+        out[threadIdx.x] = x <= 1e300 ? x : __longlong_as_double(0x7FF0000000000000LL);
     }
 }
 
-// Address of the static scratch on the current device; looked up once per
-// device with cudaGetSymbolAddress.
-nbgs_status na_scratch(double** out)
+// Address of the static scratch on the current device, looked up with
+// cudaGetSymbolAddress with that device current.  It is looked up again on
+// every call whose stream is not being captured (a device reset can reload
+// the module elsewhere); a capturing call uses the address cached by an
+// earlier call on the device.
+nbgs_status na_scratch(cudaStream_t st, double** out)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) {
         cudaGetLastError();
         return NBGS_ECUDA;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return NBGS_ECUDA;
+    }
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_addr[dev]) {
+    if (!g_na_addr[dev] || cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_na_partial);
         if (e != cudaSuccess || !p) {
@@ -146,10 +155,10 @@ extern "C" nbgs_status nbgs_final_residuals_noalloc(int64_t n_bodies, int64_t n_
     if (n_contacts > kNaMaxContacts) return NBGS_ECAPACITY;
     if (n_contacts > 0 && (!j1 || !j2 || !normal || !xi || !impulse || !vel || !angvel || !radius || !invm || !invI))
         return NBGS_EINVAL;
-    double* partial = nullptr;
-    nbgs_status rc = na_scratch(&partial);
-    if (rc != NBGS_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    double* partial = nullptr;
+    nbgs_status rc = na_scratch(st, &partial);
+    if (rc != NBGS_OK) return rc;
     const int nblocks = n_contacts > 0 ? (int)((n_contacts + kNaTile - 1) / kNaTile) : 1;
     const double vr = v_ref > 0.0 ? v_ref : 1e-12;
     k_na_partial<<<nblocks, kNaThreads, 0, st>>>(n_contacts, n_bodies, j1, j2, normal, xi, impulse, vel, angvel,

@@ -18,6 +18,9 @@
 // data-parallel pass with plain loads and stores.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "nbgs_internal.cuh"
 
@@ -548,9 +551,10 @@ __device__ __forceinline__ bool barrier_wait(DevInfo* info, const uint32_t* s_ge
     return *s_ok != 0;
 }
 
-template <class R, bool Batch> struct PersistMinBlocks {
-    // FP64 and the per-scene bookkeeping of batches need more registers per thread
-    static constexpr int value = sizeof(R) == 4 ? (Batch ? 3 : 4) : 2;
+template <class R, bool Batch, int K = 1> struct PersistMinBlocks {
+    // FP64 and the per-scene bookkeeping of batches need more registers per
+    // thread, and so does a second contact whose state a thread holds
+    static constexpr int value = sizeof(R) == 4 ? (K == 1 ? (Batch ? 3 : 4) : (Batch ? 2 : 3)) : (K == 1 ? 2 : 1);
 };
 
 // --- warp-level scheduling (NBGS_SWEEP_WARP_SYNC) ---------------------------
@@ -627,8 +631,54 @@ __device__ __forceinline__ void prefetch_range(const SolveArgs<R>& A, int64_t b0
     }
 }
 
-template <class R, bool Batch, bool Warp, bool Sub>
-__global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::value) k_solve_persistent(SolveArgs<R> A)
+// Gathered processing of a chunk: a thread loads the records and impulses
+// of up to K of its contacts, then the state of all their bodies, and only
+// then relaxes them one after the other.  Contacts of one colour share no
+// finite body, so the loads of contact k + 1 may precede the stores of
+// contact k; the K dependent chains (record -> bodies -> stores) overlap
+// instead of running back to back.  The first K records and impulses of a
+// colour are loaded before the wait for the neighbouring blocks (they do not
+// depend on it: records are read-only and a slot's impulse is written by
+// the same thread only).
+template <class R, int K>
+__device__ __forceinline__ void preload(const SolveArgs<R>& A, int64_t base, int64_t b1, SweepRec<R> (&pr)[K],
+                                        R4<R> (&pq)[K])
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t s = base + (int64_t)k * blockDim.x;
+        if (s < b1) {
+            pr[k] = ld_rec(A.rec + s);
+            pq[k] = A.p[s];
+        }
+    }
+}
+
+template <class R, bool Batch, int K>
+__device__ __forceinline__ R process_gathered(const SolveArgs<R>& A, int64_t b0, int64_t b1, SweepRec<R> (&pr)[K],
+                                              R4<R> (&pq)[K], int sweep)
+{
+    R rmax = R(0);
+    const int64_t T = blockDim.x;
+    for (int64_t base = b0 + threadIdx.x; base < b1; base += K * T) {
+        if (base != b0 + threadIdx.x) preload<R, K>(A, base, b1, pr, pq);
+        Bodies<R> B[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (base + k * T < b1) gather<R>(A, pr[k], B[k]);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (base + k * T < b1) {
+                const R r = relax_gathered<R, false, Batch>(A, base + k * T, pr[k], pq[k], B[k], sweep);
+                rmax = r > rmax ? r : rmax;
+            }
+        }
+    }
+    return rmax;
+}
+
+template <class R, bool Batch, bool Warp, bool Sub, int K = 1>
+__global__ void __launch_bounds__(kPersistThreads, (PersistMinBlocks<R, Batch, K>::value)) k_solve_persistent(SolveArgs<R> A)
 {
     extern __shared__ __align__(128) unsigned char stage_mem[];
     SweepRec<R>* srec = reinterpret_cast<SweepRec<R>*>(stage_mem);
@@ -642,7 +692,7 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
     const int ncol = (int)A.info->n_colours;
     const double vref = v_ref_of(A.info, A.gdt_norm);
     const double vnorm = Batch ? 1.0 : vref;   // batched residuals arrive already divided by v_ref_s
-    const bool stage = !Warp && (A.flags & NBGS_SWEEP_TMA_STAGE) != 0;
+    const bool stage = K == 1 && !Warp && (A.flags & NBGS_SWEEP_TMA_STAGE) != 0;
     const bool local = (A.flags & NBGS_SWEEP_GLOBAL_SYNC) == 0;
     if (threadIdx.x == 0) mbar_init(&bar);
     gravity_pass<R>(A, gtid, gstride);
@@ -712,6 +762,9 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
             const int g = k * P + c;
             int64_t cb0, cb1;
             colour_chunk(A.cstart, c, cb0, cb1);
+            SweepRec<R> pr[K];
+            R4<R> pq[K];
+            if (!stage) preload<R, K>(A, cb0 + threadIdx.x, cb1, pr, pq);
             // an empty chunk touches no body: nothing to wait for (this block's
             // own earlier phases are complete, which is all a neighbour needs)
             if (local && cb1 > cb0 && !wait_deps(A.prog, A.dep[c * (int)nb + blockIdx.x], g, A.info, &s_ok)) {
@@ -727,7 +780,8 @@ __global__ void __launch_bounds__(kPersistThreads, PersistMinBlocks<R, Batch>::v
             }
             const int cn = c + 1 < ncol ? c + 1 : 0;
             prefetch_chunk<R>(A, c + 1 < ncol ? c + 1 : 0);
-            const R r = process_colour<R, false, Batch>(A, c, m, srec, sp, k);
+            const R r = !stage ? process_gathered<R, Batch, K>(A, cb0, cb1, pr, pq, k)
+                               : process_colour<R, false, Batch>(A, c, m, srec, sp, k);
             rmax = r > rmax ? r : rmax;
             if (c == ncol - 1) block_max_to<R>(rmax, &A.info->rk_bits[rk_slot(k)]);
             if (local) {
@@ -1071,6 +1125,41 @@ __global__ void k_finish(int64_t C, const uint32_t* __restrict__ perm, const R4<
     }
 }
 
+// Impulses given in canonical order and in the contact frame (n, t, o)
+// become the contacts' current impulses: the ones the residuals evaluate
+// and the next step's warm start reads (as world vectors, like k_finish).
+__global__ void k_set_impulses(int64_t C, const double* __restrict__ p3, const double4_32a* __restrict__ cgeo,
+                               double4_32a* __restrict__ cimp, double4_32a* __restrict__ cworld)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        const double pn = p3[3 * c], pt = p3[3 * c + 1], po = p3[3 * c + 2];
+        const double4_32a g = cgeo[c];
+        double tx, ty, tz, ox, oy, oz;
+        tangent_basis<double>(g.x, g.y, g.z, tx, ty, tz, ox, oy, oz);
+        cimp[c] = make_double4_32a(pn, pt, po, 0.0);
+        cworld[c] = make_double4_32a(pn * g.x + pt * tx + po * ox, pn * g.y + pt * ty + po * oy,
+                                     pn * g.z + pt * tz + po * oz, 0.0);
+    }
+}
+
+nbgs_status run_set_impulses(nbgs_scene* s, const double* impulse)
+{
+    const int64_t C = s->n_contacts;
+    if (C == 0) return NBGS_OK;
+    cudaStream_t st = s->stream;
+    double* tmp = (double*)dev_alloc(s, (size_t)C * 3 * sizeof(double));
+    if (!tmp) return fail(s, NBGS_ENOMEM, "set_impulses: staging buffer");
+    nbgs_status rc = cuda_check(s, cudaMemcpyAsync(tmp, impulse, (size_t)C * 3 * sizeof(double), cudaMemcpyDefault, st),
+                                "set_impulses: copy");
+    if (rc == NBGS_OK) {
+        k_set_impulses<<<grid_for(C, 256, 8, s->num_sms), 256, 0, st>>>(C, tmp, s->cgeo, s->cimp, s->cworld);
+        rc = cuda_check(s, cudaGetLastError(), "set_impulses");
+    }
+    if (rc == NBGS_OK) rc = cuda_check(s, cudaStreamSynchronize(st), "set_impulses");
+    dev_free(s, tmp);
+    return rc;
+}
+
 template <class R>
 static SolveArgs<R> make_args(nbgs_scene* s, int max_sweeps, double tol)
 {
@@ -1110,6 +1199,27 @@ static SolveArgs<R> make_args(nbgs_scene* s, int max_sweeps, double tol)
     return A;
 }
 
+// Contacts a thread gathers at once in the persistent sweep (sweep flags).
+static int gather_k(int flags) { return (flags & NBGS_SWEEP_GATHER2) ? 2 : 1; }
+
+// Resident blocks per SM of one persistent sweep variant (with the shared
+// memory of the TMA stage reserved), looked up once per variant.
+template <class R>
+static int persist_occ(const void* fn)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, int>> known;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto& kv : known)
+        if (kv.first == fn) return kv.second;
+    int o = 0;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<R>::BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, kPersistThreads, Stage<R>::BYTES);
+    cudaGetLastError();
+    known.emplace_back(fn, o);
+    return o;
+}
+
 template <class R>
 static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
 {
@@ -1134,8 +1244,21 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
     if (s->prm.solver == NBGS_SOLVER_PERSISTENT) {
         // scheduling units: blocks, or warps with NBGS_SWEEP_WARP_SYNC
         const bool warp = (s->prm.sweep_flags & NBGS_SWEEP_WARP_SYNC) && !(s->prm.sweep_flags & NBGS_SWEEP_GLOBAL_SYNC);
+        const int gk = gather_k(s->prm.sweep_flags);
+        const void* fn = s->batch ? (warp      ? (const void*)k_solve_persistent<R, true, true, false>
+                                     : gk == 2 ? (const void*)k_solve_persistent<R, true, false, false, 2>
+                                               : (const void*)k_solve_persistent<R, true, false, false>)
+                         : A.sub  ? (warp ? (const void*)k_solve_persistent<R, false, true, true>
+                                          : (const void*)k_solve_persistent<R, false, false, true>)
+                                  : (warp      ? (const void*)k_solve_persistent<R, false, true, false>
+                                     : gk == 2 ? (const void*)k_solve_persistent<R, false, false, false, 2>
+                                               : (const void*)k_solve_persistent<R, false, false, false>);
+        // every block of a cooperative launch must be resident: variants that
+        // hold more contacts per thread fit fewer blocks per SM
+        const int nblocks = std::min(s->coop_blocks, persist_occ<R>(fn) * s->num_sms);
+        if (nblocks < 1) return fail(s, NBGS_ECUDA, "solve: persistent kernel does not fit");
         if (A.C > 0) {
-            const int T = 256, B = s->coop_blocks * (warp ? kPersistThreads / 32 : 1);
+            const int T = 256, B = nblocks * (warp ? kPersistThreads / 32 : 1);
             k_chunk_starts<<<grid_for((int64_t)kMaxColours * (B + 1), T, 8, s->num_sms), T, 0, st>>>(
                 A.C, B, s->col_off, s->perm, s->info, s->cstart);
             if (s->timing) s->phase_launches[2] += 1;
@@ -1167,13 +1290,7 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
         }
         void* args[] = {&A};
         if (s->timing) cudaEventRecord(s->ev[8], st);
-        const void* fn = s->batch ? (warp ? (const void*)k_solve_persistent<R, true, true, false>
-                                          : (const void*)k_solve_persistent<R, true, false, false>)
-                         : A.sub  ? (warp ? (const void*)k_solve_persistent<R, false, true, true>
-                                          : (const void*)k_solve_persistent<R, false, false, true>)
-                                  : (warp ? (const void*)k_solve_persistent<R, false, true, false>
-                                          : (const void*)k_solve_persistent<R, false, false, false>);
-        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(s->coop_blocks),
+        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nblocks),
                                                     dim3(s->coop_threads), args,
                                                     (s->prm.sweep_flags & NBGS_SWEEP_TMA_STAGE) ? Stage<R>::BYTES : 0,
                                                     st);

@@ -27,7 +27,7 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ECAPACITY", "ENOTCONV", "ENA
 NBGS_FP64, NBGS_FP32 = 0, 1
 NBGS_WARM_NONE, NBGS_WARM_PREV, NBGS_WARM_MLP = 0, 1, 2
 NBGS_SOLVER_PERSISTENT, NBGS_SOLVER_PER_COLOUR = 0, 1
-NBGS_SWEEP_GLOBAL_SYNC, NBGS_SWEEP_TMA_STAGE, NBGS_SWEEP_WARP_SYNC = 1, 2, 4
+NBGS_SWEEP_GLOBAL_SYNC, NBGS_SWEEP_TMA_STAGE, NBGS_SWEEP_WARP_SYNC, NBGS_SWEEP_GATHER2 = 1, 2, 4, 8
 NBGS_SUB_NONE, NBGS_SUB_GRID, NBGS_SUB_JACOBI = 0, 1, 2
 
 
@@ -81,6 +81,7 @@ _SIG = {
     "nbgs_save_state": [_vp, C.c_char_p],
     "nbgs_load_state": [_vp, C.c_char_p],
     "nbgs_final_residuals": [_vp, _P(nbgs_residuals)],
+    "nbgs_set_impulses": [_vp, _vp],
     "nbgs_sync": [_vp],
     "nbgs_enable_timing": [_vp, C.c_int32],
     "nbgs_get_timings": [_vp, _dp, _i64p],
@@ -369,6 +370,12 @@ class Scene:
         out = np.empty(n.value)
         _call(self.h, "nbgs_residual_history", out.ctypes.data_as(_dp), n.value, C.byref(n))
         return out
+
+    def set_impulses(self, imp) -> None:
+        """Impulses of the current contacts (n_contacts x 3, canonical order,
+        contact frame)."""
+        a = np.ascontiguousarray(imp, dtype=np.float64).reshape(-1, 3)
+        _call(self.h, "nbgs_set_impulses", _ptr(a))
 
     def final_residuals(self) -> dict:
         r = nbgs_residuals()

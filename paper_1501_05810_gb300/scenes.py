@@ -135,7 +135,7 @@ def loose_pour(seed: int = 0, n: int = 1_000_000, r_lo: float = 0.4, r_hi: float
     pos = pos + rng.uniform(-j, j, pos.shape)
     height = max(height, (nz + 1) * s)
     lo, hi = (0.0, 0.0, 0.0), (nx * s, nx * s, height)
-    prm = default_params(dt=5e-4, mu=0.5, tau=0.01 * r_lo, box_lo=lo, box_hi=hi, **params)
+    prm = default_params(**{**dict(dt=5e-4, mu=0.5, tau=0.01 * r_lo, box_lo=lo, box_hi=hi), **params})
     return _scene(f"loose_pour_{n}", prm, pos, np.zeros((n, 3)), np.zeros((n, 3)), radius,
                   np.ones(n), box_walls(lo, hi))
 
