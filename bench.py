@@ -77,9 +77,9 @@ def workload(name: str):
     if name == "batch":
         bs = scenes.batch_scenes(4096, seed=0, precision="fp32", contacts_per_body=4, warm_start="prev")
         return bs, (f"4,096 walled-box scenes, {sum(len(b['radius']) for b in bs):,} spheres in total, sizes "
-                    "log-uniform in [200, 20000], r~U(0.4,0.6), mu~U(0.2,0.8), settling under gravity, dt=5e-4, "
-                    "residual 1e-6 per scene (max 100 sweeps), previous-step warm start, one persistent sweep launch "
-                    "for all scenes")
+                    "log-uniform in [200, 20000], r~U(0.4,0.6), mu~U(0.2,0.8), settling under gravity from a loose "
+                    "lattice, dt=5e-4, residual 1e-6 per scene (max 1,000 sweeps), previous-step warm start, one "
+                    "persistent sweep launch for all scenes per step, steps replayed from captured CUDA graphs")
     if name == "hopper":
         sc = scenes.hopper(2_000_000, seed=0, precision="fp32", warm_start="prev")
         return sc, ("conical hopper discharge: 2,000,000 spheres r~U(0.4,0.6), 30 deg half-angle, orifice 8 r_mean, "
@@ -104,10 +104,16 @@ def workload(name: str):
 
 
 # sweeps and tolerance per workload: (max_sweeps, tol)
-SOLVE = {"pour1m": (100, 1e-6), "dense1m": (100, 1e-6), "config1": (50, 0.0), "gas": (50, 0.0), "ramp": (100, 0.0), "batch": (100, 1e-6),
+SOLVE = {"pour1m": (100, 1e-6), "dense1m": (100, 1e-6), "config1": (50, 0.0), "gas": (50, 0.0), "ramp": (100, 0.0),
+         "batch": (1000, 1e-6),
          "hopper": (100, 1e-6), "compgas": (10, 0.0), "comppile": (50, 0.0), "config1_1e6": (1000, 1e-6)}
 # untimed steps (sweeps, count) that bring a workload into its regime first
 SETTLE = {"hopper": (30, 2000), "config1_1e6": (50, 150)}
+# timed steps per workload when --steps is not given (the batch: the 500
+# steps of its configuration)
+DEFAULT_STEPS = {"batch": 500}
+# workloads timed as replayed CUDA graphs by default
+GRAPH_DEFAULT = ("batch",)
 # settled first in a scene of its own with a larger time step: (dt, sweeps,
 # steps); the measured scene starts from the settled state
 PRE_SETTLE = {"pour1m": (2e-3, 30, 3000)}   # the schedule of workloads.POUR_SETTLE
@@ -305,6 +311,55 @@ def steps_to_residual(nbgs, torch, local, steps=30):
             "residual_max": max(float(x["residual"]) for x in st), "contacts": st[-1]["n_contacts"]}
 
 
+def compare_one_by_one(nbgs, torch, g, scene_list, sweeps, tol, stream, local, sample=64, steps=5):
+    """The batched form against the same scenes solved one by one by plain
+    cold-start NBGS on the same GPU, from the batch's current state: the
+    batch's next `steps` steps as replayed graphs (previous-step warm start),
+    and for a sample of the scenes (evenly spaced in order of size) `steps`
+    ordinary steps each in a scene of its own with no warm start, after one
+    untimed step that sizes its buffers.  The sample's time is scaled by the
+    scene count."""
+    b = g.get_bodies()
+    off = g.offsets
+    S = len(scene_list)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g.get_updates()
+    e0.record(stream)
+    g.graph_step(sweeps, tol, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1)
+    u_batch = g.get_updates()
+    sizes = np.diff(off)
+    pick = np.argsort(sizes, kind="stable")[np.linspace(0, S - 1, min(sample, S)).astype(int)]
+    t_one, u_one = 0.0, 0
+    for i in pick:
+        sl = slice(int(off[i]), int(off[i + 1]))
+        d = dict(scene_list[i], pos=b["pos"][sl], vel=b["vel"][sl], angvel=b["angvel"][sl])
+        d["params"] = dict(d["params"], warm_start="none")
+        one = nbgs.Scene(d, device=f"cuda:{local}", stream=stream)
+        one.step(sweeps, tol, stats=False)
+        one.set_bodies(b["pos"][sl], b["quat"][sl], b["vel"][sl], b["angvel"][sl])
+        one.get_updates()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            one.step(sweeps, tol, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_one += e0.elapsed_time(e1)
+        u_one += one.get_updates()
+        one.close()
+    est = t_one * S / len(pick)
+    return {"scenes": S, "sample_scenes": int(len(pick)), "steps": steps, "sweeps_max": sweeps, "tol": tol,
+            "batched_ms_per_step": t_batch / steps, "batched_contact_updates": int(u_batch),
+            "one_by_one_ms_per_step_est": est / steps, "one_by_one_sample_contact_updates": int(u_one),
+            "speedup_batched_over_one_by_one": est / t_batch if t_batch > 0 else None,
+            "one_by_one": "each sampled scene alone, nbgs_step with no warm start (plain cold-start NBGS), "
+                          "time scaled by scenes / sample"}
+
+
 def reduce_over_ranks(dist, ms_total, updates, device):
     """Replicas: the job's time is the slowest rank's, its work the sum of
     all ranks' (no data-path collective; this reduction runs once, after the
@@ -338,7 +393,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: 500 for batch, else 30)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="pour1m")
@@ -349,10 +404,14 @@ def main():
     ap.add_argument("--subdomains", default=None,
                     help="subdomains of Alg. 1: 'jacobi' (one per contact) or a grid 'g0,g1,g2'")
     ap.add_argument("--omega", type=float, default=None, help="relaxation parameter of Alg. 1")
+    ap.add_argument("--graph", default="auto", choices=["auto", "on", "off"],
+                    help="time replayed CUDA graphs of the step (auto: for the batch)")
     ap.add_argument("--autotune", action="store_true",
                     help="after the warm-up, let nbgs_autotune pick the sweep schedule and blocks per SM (untimed)")
     args = ap.parse_args()
 
+    steps = args.steps if args.steps is not None else DEFAULT_STEPS.get(args.workload, 30)
+    args.steps = steps
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -412,22 +471,27 @@ def main():
             f_, b_ = nbgs.autotune(g, sweeps, tol)
             tuned = {"sweep_flags": int(f_), "blocks_per_sm": int(b_)}
             desc += f", autotuned schedule (sweep flags {f_}, {b_} blocks per SM)"
+        use_graph = args.graph == "on" or (args.graph == "auto" and args.workload in GRAPH_DEFAULT)
+        if use_graph:
+            g.graph_step(sweeps, tol, 1)   # captures the step (untimed), then replays it once
+            g.sync()
         n_ss, n_sw, colour_sizes = count_contact_kinds(g, n)
         n_shared, n_extra = count_instances(g, n) if args.subdomains is not None else (0, 0)
-        g.enable_timing(True)
         clocks = ClockSampler(local)
         clocks.start()
+        g.get_updates()   # counted on the device; read (and reset) after the timed region
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         clocks.mark_start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        updates, stats = 0, []
-        for _ in range(args.steps):
-            st = g.step(sweeps, tol)
-            stats.append(st)
-            updates += st["n_contacts"] * st["sweeps_done"]
+        stats = []
+        if use_graph:
+            g.graph_step(sweeps, tol, steps)   # no host synchronisation inside
+        else:
+            for _ in range(steps):
+                g.step(sweeps, tol, stats=False)
         e1.record(stream)
         torch.cuda.synchronize()
         clocks.mark_end()
@@ -435,7 +499,24 @@ def main():
             dist.barrier()
         ck = clocks.stop()
         ms_total = e0.elapsed_time(e1)
+        updates = g.get_updates()
+        batch_stats = None
+        if batch:
+            ks, rs = g.scene_stats()
+            batch_stats = {"scenes": int(len(ks)), "scenes_at_tol_last_step": int(np.count_nonzero(rs <= tol)),
+                           "sweeps_last_step": {"median": float(np.median(ks)), "max": int(ks.max()),
+                                                "min": int(ks.min())},
+                           "residual_last_step_max": float(rs.max())}
+        # phase breakdown and the sweep kernel's launch time: a few ordinary
+        # steps with the library's CUDA-event timing, right after the timed ones
+        g.enable_timing(True)
+        n_phase = min(5, steps)
+        for _ in range(n_phase):
+            stats.append(g.step(sweeps, tol))
         phase_ms, launches = g.get_timings()
+        g.enable_timing(False)
+        phase_updates = g.get_updates()
+        one_by_one = compare_one_by_one(nbgs, torch, g, sc, sweeps, tol, stream, local) if batch else None
         # end to end through the public API with host buffers: upload the
         # state from pinned memory, step, read the state back
         host = {k: torch.empty((n, d), dtype=torch.float64, pin_memory=True)
@@ -444,58 +525,66 @@ def main():
         for k in host:
             host[k].copy_(torch.from_numpy(b[k]))
         torch.cuda.synchronize()
+        g.get_updates()
         t0 = time.perf_counter()
-        e2e_updates = 0
         for _ in range(args.e2e_steps):
             g.set_bodies(host["pos"], host["quat"], host["vel"], host["angvel"])
-            st = g.step(sweeps, tol)
-            e2e_updates += st["n_contacts"] * st["sweeps_done"]
+            g.step(sweeps, tol, stats=False)
             nbgs._call(g.h, "nbgs_get_bodies", *[host[k].data_ptr() for k in ("pos", "quat", "vel", "angvel")])
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
+        e2e_updates = g.get_updates()
 
     t_max, updates_all = reduce_over_ranks(dist, ms_total, updates, f"cuda:{local}")
     value = updates_all / (t_max / 1e3)
     sweeps_done = [s["sweeps_done"] for s in stats]
     residuals = [float(s["residual"]) for s in stats]
     contacts = [s["n_contacts"] for s in stats]
-    solve_ms = phase_ms["solve"]
-    sweep_rate = updates / (phase_ms["sweep_kernel"] / 1e3) if phase_ms["sweep_kernel"] > 0 else None
     comp = "members" in first
     b_ss, b_sw = (BYTES_COMP if comp else BYTES)[prec]
-    # dominant kernel: the persistent sweep kernel, one launch per solve
-    alg_bytes_per_launch = (n_ss * b_ss + n_sw * b_sw) * statistics.mean(sweeps_done)
+    # dominant kernel: the persistent sweep kernel, one launch per solve; its
+    # contact updates per launch from the device count of the timing steps
+    n_launch = max(1, launches["sweep_kernel"])
+    upd_launch = phase_updates / n_launch
+    per_update = (n_ss * b_ss + n_sw * b_sw) / max(1, n_ss + n_sw)
+    sweeps_launch = upd_launch / max(1, n_ss + n_sw)
+    alg_bytes_per_launch = upd_launch * per_update
     # subdomains: per sweep, each shared body's accumulator and own record
     # read and written, each extra instance read and written; once, the
     # instances and accumulators set from the bodies
     rec = 32 if prec == "fp32" else 64
-    alg_bytes_per_launch += ((4 * rec * n_shared + 2 * rec * n_extra) * statistics.mean(sweeps_done)
+    alg_bytes_per_launch += ((4 * rec * n_shared + 2 * rec * n_extra) * sweeps_launch
                              + 2 * rec * n_shared + rec * n_extra)
-    per_launch_ms = phase_ms["sweep_kernel"] / max(1, launches["sweep_kernel"])
+    per_launch_ms = phase_ms["sweep_kernel"] / n_launch
+    sweep_rate = phase_updates / (phase_ms["sweep_kernel"] / 1e3) if phase_ms["sweep_kernel"] > 0 else None
     peak, peak_src = read_peaks()
     # with subdomains the traffic depends on the grid: a capture of the same
     # workload and grid only
-    traffic = measured_traffic(prec, n_ss + n_sw, statistics.mean(sweeps_done),
+    traffic = measured_traffic(prec, n_ss + n_sw, sweeps_launch,
                                "" if args.subdomains is None else f" {args.workload} subdomains {args.subdomains}",
                                "k_solve_comp" if comp else "k_solve_persistent")
     achieved = alg_bytes_per_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": t_max / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": desc, **({"bodies": n, "members": int(g.n_members)} if comp else {"spheres": n}),
                    "contacts": contacts[-1], "colours": stats[-1]["n_colours"], "colour_sizes": colour_sizes,
                    "sweeps_per_step": sweeps,
                    "tol": tol, "l2": "inputs larger than L2 (no flush)",
+                   "timed_steps": "replayed CUDA graphs (nbgs_graph_step), no host synchronisation"
+                                  if use_graph else "nbgs_step calls",
                    **({"autotuned": tuned} if tuned else {}),
                    **({"subdomains": args.subdomains, "shared_bodies": n_shared, "extra_instances": n_extra}
                       if args.subdomains is not None else {}),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "steps_per_s": args.steps / (t_max / 1e3),
+        "steps_per_s": steps / (t_max / 1e3),
+        "contact_updates": updates,
         "sweep_updates_per_s": sweep_rate,
         "sweeps_done": sweeps_done, "residual_reached_max": max(residuals) if residuals else None,
-        "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
-        "gpu_launches": int(sum(v for k, v in launches.items() if k != "sweep_kernel")),
+        "phase_ms_per_step": {k: v / n_phase for k, v in phase_ms.items()},
+        "phase_timing": f"{n_phase} nbgs_step calls with CUDA-event timing after the timed steps",
+        "gpu_launches": int(round(sum(v for k, v in launches.items() if k != "sweep_kernel") * steps / n_phase)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "kernel": f"{'k_solve_comp' if comp else 'k_solve_persistent'}<{'float' if prec == 'fp32' else 'double'}>",
@@ -506,6 +595,10 @@ def main():
                 "h2d_bytes_per_step": int(13 * 8 * n), "d2h_bytes_per_step": int(13 * 8 * n),
                 "steps": args.e2e_steps},
     }
+    if batch_stats:
+        line["batch"] = batch_stats
+    if one_by_one:
+        line["one_by_one"] = one_by_one
     if args.workload == "dense1m":
         line["steps_to_residual"] = steps_to_residual(nbgs, torch, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("pour1m", "dense1m"):

@@ -251,6 +251,27 @@ nbgs_status nbgs_create_batch(const nbgs_params* params, const nbgs_batch_desc* 
 nbgs_status nbgs_batch_step(nbgs_scene* scene, int32_t max_sweeps, double tol, int32_t* sweeps_done,
                             double* residual);
 
+/* n_steps time steps captured as CUDA graphs and replayed on the scene
+ * stream, with no host synchronisation inside or between the steps (the
+ * batched extension: thousands of scenes in one persistent sweep launch
+ * under a captured graph).  Every step does what nbgs_step(max_sweeps, tol)
+ * does, with device-sized launches: the contact count stays on the device,
+ * the colouring rounds run in one cooperative launch, and the buffers keep
+ * the capacities they had at capture (contacts: the capacity the last
+ * nbgs_step left, at least contacts_per_body per body; predecessor lists of
+ * the colouring: six per contact).  A step that needs more sets an error
+ * bit and the next synchronising call returns NBGS_ECAPACITY (take ordinary
+ * nbgs_step calls then, which grow the buffers).  The first call, and any
+ * call with other max_sweeps or tol or after the buffers grew, captures the
+ * step first (two graphs, one for each parity of the warm-start buffers).
+ * Needs one ordinary nbgs_step before (it sizes the buffers and starts the
+ * warm-start history); sphere scenes or batches, the persistent solver, no
+ * subdomains, no network warm start, timing off (else NBGS_EINVAL).  Results
+ * equal those of nbgs_step.  Asynchronous: statistics, contacts and bodies
+ * are read afterwards with the usual calls (nbgs_get_scene_stats,
+ * nbgs_sync, ...), which synchronise and report device-side errors. */
+nbgs_status nbgs_graph_step(nbgs_scene* scene, int32_t max_sweeps, double tol, int32_t n_steps);
+
 /* Per-scene results of the last solve (see nbgs_batch_step).  Synchronises. */
 nbgs_status nbgs_get_scene_stats(nbgs_scene* scene, int32_t* sweeps_done, double* residual);
 
@@ -448,6 +469,12 @@ nbgs_status nbgs_final_residuals_noalloc(int64_t n_bodies, int64_t n_contacts, c
                                          const double* radius, const double* invm, const double* invI,
                                          double dt, double beta, double mu, double v_ref, double* out,
                                          void* stream);
+
+/* Contact updates since the scene was created or this call last read
+ * them: every contact relaxed once per sweep its scene ran (a scene of a
+ * batch stops at its own tolerance), counted on the device, so that graph
+ * steps need no host read per step.  Reads and resets.  Synchronises. */
+nbgs_status nbgs_get_updates(nbgs_scene* scene, int64_t* updates);
 
 /* Wait for the scene's stream and report device-side errors. */
 nbgs_status nbgs_sync(nbgs_scene* scene);

@@ -164,7 +164,26 @@ static nbgs_status check_device_errors(nbgs_scene* s)
     const uint32_t e = s->hinfo->err;
     if (e & kErrTimeout) return fail(s, NBGS_ETIMEOUT, "a grid barrier wait timed out");
     if (e & kErrNaN) return fail(s, NBGS_ENAN, "NaN or Inf in the body state");
+    if (e & kErrContacts) return fail(s, NBGS_ECAPACITY, "a graph step found more contacts than its buffers hold");
+    if (e & kErrPreds) return fail(s, NBGS_ECAPACITY, "a graph step's colouring outgrew its predecessor lists");
     if (e & kErrColours) return fail(s, NBGS_ECAPACITY, "more than 128 colours needed");
+    return NBGS_OK;
+}
+
+// After graph steps the host does not know the contact counts: read them
+// (and the device's error bits) before anything else uses them.
+static nbgs_status refresh_after_graphs(nbgs_scene* s)
+{
+    if (!s->counts_stale) return NBGS_OK;
+    s->counts_stale = false;
+    nbgs_status rc = check_device_errors(s);
+    if (rc != NBGS_OK) return rc;
+    s->n_contacts = s->hinfo->n_contacts;
+    s->prev_count = s->hinfo->prev_contacts;
+    s->have_prev = s->prm.warm_start != NBGS_WARM_NONE;
+    s->solved = true;
+    s->detected = s->coloured = false;
+    s->n_colours = -1;
     return NBGS_OK;
 }
 
@@ -198,10 +217,14 @@ bool params_valid(const nbgs_params* p)
 
 using namespace nbgs;
 
-#define NBGS_GUARD(s)                              \
-    do {                                           \
-        if (!(s)) return NBGS_EINVAL;              \
-        if ((s)->status != NBGS_OK) return (s)->status; \
+#define NBGS_GUARD(s)                                         \
+    do {                                                      \
+        if (!(s)) return NBGS_EINVAL;                         \
+        if ((s)->status != NBGS_OK) return (s)->status;       \
+        if ((s)->counts_stale) {                              \
+            const nbgs_status guard_rc_ = refresh_after_graphs(s); \
+            if (guard_rc_ != NBGS_OK) return guard_rc_;       \
+        }                                                     \
     } while (0)
 
 extern "C" {
@@ -560,10 +583,13 @@ static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_des
     return NBGS_OK;
 }
 
+static void drop_graphs(nbgs_scene* s);
+
 void nbgs_destroy_scene(nbgs_scene* s)
 {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
+    drop_graphs(s);
     void* ps[] = {s->pos_r, s->quat, s->vel, s->hull, s->p32, s->p32s, s->finite, s->stage, s->cell_start,
                   s->cell_end, s->keys[0], s->keys[1], s->vals[0], s->vals[1], s->radix_hist, s->scan_tmp,
                   s->cand, s->sph_cnt, s->row_cnt, s->row_off, s->prev_row_off, s->deg, s->adj_off,
@@ -779,6 +805,101 @@ nbgs_status nbgs_batch_step(nbgs_scene* s, int32_t max_sweeps, double tol, int32
     return rc;
 }
 
+// The host-side half of the warm-start swap run_detect performs (the
+// device-side arrays a graph step reads and writes follow these pointers).
+static void swap_warm_buffers(nbgs_scene* s)
+{
+    std::swap(s->row_off, s->prev_row_off);
+    std::swap(s->cj2, s->prev_j2);
+    std::swap(s->cworld, s->prev_P);
+}
+
+static void drop_graphs(nbgs_scene* s)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (s->gexec[k]) cudaGraphExecDestroy(s->gexec[k]);
+        s->gexec[k] = nullptr;
+    }
+    s->g_sweeps = -1;
+}
+
+// One step (detect, colour, solve, integrate) recorded without any host
+// synchronisation.  The recording runs on a private stream (the scene's
+// stream may be the legacy default stream, which cannot be captured); the
+// graph is later launched on the scene's stream, which orders it.
+static nbgs_status capture_step(nbgs_scene* s, int32_t max_sweeps, double tol, cudaGraphExec_t* out)
+{
+    cudaStream_t cap = nullptr;
+    nbgs_status rc = cuda_check(s, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "graph_step: stream");
+    if (rc != NBGS_OK) return rc;
+    cudaStream_t scene_stream = s->stream;
+    s->stream = cap;
+    rc = cuda_check(s, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "graph_step: begin capture");
+    if (rc == NBGS_OK) {
+        rc = run_detect(s);
+        if (rc == NBGS_OK) rc = run_colour(s);
+        if (rc == NBGS_OK) rc = run_solve(s, max_sweeps, tol);
+        if (rc == NBGS_OK) rc = run_integrate(s);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cap, &g);
+        if (rc == NBGS_OK) rc = cuda_check(s, e, "graph_step: end capture");
+        if (rc == NBGS_OK) rc = cuda_check(s, cudaGraphInstantiate(out, g, 0), "graph_step: instantiate");
+        if (g) cudaGraphDestroy(g);
+    }
+    s->stream = scene_stream;
+    cudaStreamDestroy(cap);
+    return rc;
+}
+
+nbgs_status nbgs_graph_step(nbgs_scene* s, int32_t max_sweeps, double tol, int32_t n_steps)
+{
+    if (!s) return NBGS_EINVAL;
+    if (s->status != NBGS_OK) return s->status;
+    if (n_steps < 0 || max_sweeps < 0 || !(tol >= 0.0)) return fail(s, NBGS_EINVAL, "graph_step: bad arguments");
+    if (s->composite || s->prm.subdomain_mode != NBGS_SUB_NONE || s->prm.warm_start == NBGS_WARM_MLP ||
+        s->prm.solver != NBGS_SOLVER_PERSISTENT || s->coop_blocks == 0)
+        return fail(s, NBGS_EINVAL, "graph_step: sphere scenes or batches with the persistent solver, no subdomains, "
+                                    "no network warm start");
+    if (s->timing) return fail(s, NBGS_EINVAL, "graph_step: disable timing first");
+    if (n_steps == 0) return NBGS_OK;
+    const bool fresh = s->gexec[0] && max_sweeps == s->g_sweeps && tol == s->g_tol && s->ccap == s->g_ccap &&
+                       s->preds_cap == s->g_pcap;
+    if (!fresh) {
+        nbgs_status rc = refresh_after_graphs(s);
+        if (rc != NBGS_OK) return rc;
+        if (!s->solved || s->n == 0)
+            return fail(s, NBGS_EINVAL, "graph_step: take one nbgs_step first (it sizes the buffers)");
+        drop_graphs(s);
+        // predecessor lists for a colouring of a full contact buffer (about
+        // six entries per contact in dense packings)
+        rc = grow_preds(s, 6 * s->ccap + 4096);
+        if (rc != NBGS_OK) return rc;
+        s->device_sized = true;
+        rc = capture_step(s, max_sweeps, tol, &s->gexec[0]);
+        if (rc == NBGS_OK) rc = capture_step(s, max_sweeps, tol, &s->gexec[1]);
+        s->device_sized = false;
+        if (rc != NBGS_OK) {
+            drop_graphs(s);
+            return rc;
+        }
+        // each capture swapped the warm-start pointers once: back where they were
+        s->g_sweeps = max_sweeps;
+        s->g_tol = tol;
+        s->g_ccap = s->ccap;
+        s->g_pcap = s->preds_cap;
+        s->g_next = 0;
+        s->last_sweeps = max_sweeps;
+    }
+    for (int32_t k = 0; k < n_steps; ++k) {
+        nbgs_status rc = cuda_check(s, cudaGraphLaunch(s->gexec[s->g_next], s->stream), "graph_step: launch");
+        if (rc != NBGS_OK) return rc;
+        swap_warm_buffers(s);
+        s->g_next ^= 1;
+    }
+    s->counts_stale = true;
+    return NBGS_OK;
+}
+
 nbgs_status nbgs_autotune(nbgs_scene* s, int32_t max_sweeps, double tol, int32_t* sweep_flags, int32_t* blocks_per_sm)
 {
     NBGS_GUARD(s);
@@ -908,6 +1029,19 @@ nbgs_status nbgs_final_residuals(nbgs_scene* s, nbgs_residuals* out)
     if (s->composite) return fail(s, NBGS_EINVAL, "final_residuals: sphere scenes only");
     nbgs_status rc = run_final_residuals(s, out);
     if (rc == NBGS_OK) rc = check_device_errors(s);
+    return rc;
+}
+
+nbgs_status nbgs_get_updates(nbgs_scene* s, int64_t* updates)
+{
+    NBGS_GUARD(s);
+    if (!updates) return fail(s, NBGS_EINVAL, "get_updates: null output");
+    unsigned long long u = 0;
+    nbgs_status rc = cuda_check(s, cudaMemcpyAsync(&u, &s->info->updates, sizeof(u), cudaMemcpyDeviceToHost, s->stream),
+                                "get_updates");
+    if (rc == NBGS_OK) rc = cuda_check(s, cudaMemsetAsync(&s->info->updates, 0, sizeof(u), s->stream), "get_updates");
+    if (rc == NBGS_OK) rc = check_device_errors(s);
+    if (rc == NBGS_OK) *updates = (int64_t)u;
     return rc;
 }
 

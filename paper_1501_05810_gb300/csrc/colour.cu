@@ -13,10 +13,12 @@
 //   k_jp_round      a contact whose predecessors are all coloured takes the
 //                   smallest colour none of them has: first-fit greedy in
 //                   decreasing priority, as Jones-Plassmann rounds give it,
-//                   driven by waiting lists
+//                   driven by waiting lists (k_jp_persistent: every round
+//                   in one cooperative launch, for device-sized steps)
 //   k_colour_keys   colour histogram
 //   radix pass      stable counting sort by colour -> permutation
 //   k_build_sweep   sweep records in colour order, initial impulses
+#include <algorithm>
 #include <utility>
 
 #include "nbgs_internal.cuh"
@@ -44,11 +46,12 @@ __device__ __forceinline__ uint64_t local_key(uint32_t a, uint32_t b, const Scen
 // Priorities from the contacts' keys; body degrees from the incidence ends
 // ib1, ib2 (the contact's bodies: the contact ends themselves for spheres,
 // the members' bodies for composites; >= n marks a wall).
-__global__ void k_colour_init(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
+__global__ void k_colour_init(DCount Cc, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
                               const uint32_t* __restrict__ ib1, const uint32_t* __restrict__ ib2,
                               const uint8_t* __restrict__ finite, uint64_t seed, SceneView V, uint32_t* __restrict__ deg,
                               uint64_t* __restrict__ prio, uint32_t* __restrict__ cstate)
 {
+    const int64_t C = Cc.get();
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
         prio[c] = splitmix64(local_key(cj1[c], cj2[c], V) ^ seed);
         cstate[c] = kUncoloured;
@@ -58,10 +61,11 @@ __global__ void k_colour_init(int64_t C, int64_t n, const uint32_t* __restrict__
     }
 }
 
-__global__ void k_adj_fill(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
+__global__ void k_adj_fill(DCount Cc, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
                            const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
                            uint32_t* __restrict__ fill, uint32_t* __restrict__ adj)
 {
+    const int64_t C = Cc.get();
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t a = cj1[c], b = cj2[c];
         if (finite[a]) adj[adj_off[a] + atomicAdd(&fill[a], 1u)] = (uint32_t)c;
@@ -138,11 +142,12 @@ __device__ __forceinline__ void incidence(uint32_t c, int64_t n, const uint32_t*
 // counts them (npred) and keeps them as a bit mask over the incidence
 // entries (pmask; ~0 for more than 64 entries, where pass 2 compares
 // priorities again).
-__global__ void k_pred_count(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
+__global__ void k_pred_count(DCount Cc, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
                              const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
                              const uint32_t* __restrict__ adj, const uint64_t* __restrict__ prio,
                              uint64_t* __restrict__ pmask, uint32_t* __restrict__ npred)
 {
+    const int64_t C = Cc.get();
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
         uint32_t a0, na, b0, nb;
         incidence((uint32_t)c, n, cj1, cj2, finite, adj_off, a0, na, b0, nb);
@@ -168,13 +173,14 @@ __global__ void k_pred_count(int64_t C, int64_t n, const uint32_t* __restrict__ 
 // direct list.
 __device__ __forceinline__ uint32_t prio_hi(uint64_t p) { return (uint32_t)(p >> 32); }
 
-__global__ void k_pred_lists(int64_t C, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
+__global__ void k_pred_lists(DCount Cc, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
                              const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
                              const uint32_t* __restrict__ adj, const uint64_t* __restrict__ prio,
                              const uint64_t* __restrict__ pmask, const uint32_t* __restrict__ poff,
-                             uint2* __restrict__ preds, uint32_t* whead, uint32_t* __restrict__ wnext,
+                             uint2* __restrict__ preds, int64_t pcap, uint32_t* whead, uint32_t* __restrict__ wnext,
                              uint32_t* __restrict__ wl, uint32_t* count)
 {
+    const int64_t C = Cc.get();
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // warp-uniform trip count: every lane takes part in warp_push
@@ -194,7 +200,7 @@ __global__ void k_pred_lists(int64_t C, int64_t n, const uint32_t* __restrict__ 
                 const uint32_t d = incident(adj, a0, na, b0, j);
                 const uint64_t pd = prio[d];
                 if (m == ~0ull && (d == (uint32_t)c || !beats(pd, d, pc, (uint32_t)c))) continue;
-                preds[p0 + k] = make_uint2(d, prio_hi(pd));
+                if (p0 + k < pcap) preds[p0 + k] = make_uint2(d, prio_hi(pd));   // beyond: the error bit is set
                 if (pd < pweak) {
                     pweak = pd;
                     weakest = d;
@@ -293,16 +299,20 @@ __device__ bool jp_examine(bool valid, uint32_t c, uint32_t round, int lane, con
 constexpr int kJpThreads = 256;
 constexpr int kJpCap = 2048;
 
-__global__ void __launch_bounds__(kJpThreads) k_jp_round(uint32_t round, uint32_t C, const uint32_t* __restrict__ wl_in,
-                                  const uint32_t* __restrict__ cnt_in, uint32_t* __restrict__ wl_out,
-                                  uint32_t* __restrict__ cnt_out, uint32_t* __restrict__ cnt_clear,
-                                  const uint32_t* __restrict__ poff, const uint2* __restrict__ preds,
-                                  uint32_t* cstate, uint32_t* whead, uint32_t* __restrict__ wnext, DevInfo* info)
+// Round `round` over the input lists (tiles of kJpThreads entries, grid-
+// stride).  What other blocks wrote in earlier rounds (lists, counters,
+// states, waiting lists) is visible after the grid barrier between rounds
+// (its acquire fence); the counters are read through L2.
+__device__ __forceinline__ void jp_round(uint32_t round, uint32_t C, const uint32_t* __restrict__ wl_in,
+                                         const uint32_t* cnt_in, uint32_t* __restrict__ wl_out, uint32_t* cnt_out,
+                                         uint32_t* cnt_clear, const uint32_t* __restrict__ poff,
+                                         const uint2* __restrict__ preds, uint32_t* cstate, uint32_t* whead,
+                                         uint32_t* __restrict__ wnext, DevInfo* info)
 {
     __shared__ uint32_t s_exam[kJpCap];
     __shared__ uint32_t s_done[kJpCap];
     __shared__ uint32_t s_nexam, s_ndone, s_base;
-    const uint32_t nl = cnt_in[0], nx = cnt_in[1], m = nl + nx;
+    const uint32_t nl = __ldcg(cnt_in), nx = __ldcg(cnt_in + 1), m = nl + nx;
     if (blockIdx.x == 0 && threadIdx.x < 2) cnt_clear[threadIdx.x] = 0u;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr uint32_t nwarps = kJpThreads / 32;
@@ -355,9 +365,83 @@ __global__ void __launch_bounds__(kJpThreads) k_jp_round(uint32_t round, uint32_
     }
 }
 
-__global__ void k_colour_keys(int64_t C, const uint32_t* __restrict__ cstate, uint32_t* __restrict__ ckey,
+// One round per launch (the host checks the lists every few rounds).
+__global__ void __launch_bounds__(kJpThreads) k_jp_round(uint32_t round, uint32_t C, const uint32_t* __restrict__ wl_in,
+                                                         const uint32_t* cnt_in, uint32_t* __restrict__ wl_out,
+                                                         uint32_t* cnt_out, uint32_t* cnt_clear,
+                                                         const uint32_t* __restrict__ poff,
+                                                         const uint2* __restrict__ preds, uint32_t* cstate,
+                                                         uint32_t* whead, uint32_t* __restrict__ wnext, DevInfo* info)
+{
+    jp_round(round, C, wl_in, cnt_in, wl_out, cnt_out, cnt_clear, poff, preds, cstate, whead, wnext, info);
+}
+
+// All rounds in one cooperative launch (no host in the loop, so a step can
+// be captured in a CUDA graph): a grid barrier ends each round (it
+// plays the part of a launch boundary: every waiter registered and every
+// colour written before the next round walks the lists), and the round's
+// output counters, read by every block after the barrier, tell whether
+// anything is left.  A contact count of zero leaves at once; more than
+// kJpMaxRounds rounds set the colour error bit.
+constexpr int kJpMaxRounds = 1024;
+
+// Grid barrier of the colouring rounds: the arrival count and generation
+// words of the grid barrier, polled without sleeping (rounds are short);
+// bounded like every wait (~1 s of SM clocks), then the timeout bit.
+__device__ __forceinline__ bool jp_barrier(DevInfo* info)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t* vgen = &info->barrier_gen;
+        const uint32_t gen = *vgen;
+        __threadfence();
+        int good = 1;
+        if (atomicAdd(&info->barrier_count, 1u) == gridDim.x - 1) {
+            info->barrier_count = 0;
+            __threadfence();
+            atomicAdd(&info->barrier_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == gen) {
+                if (clock64() - t0 > (1LL << 31)) {
+                    atomicOr(&info->err, kErrTimeout);
+                    good = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__global__ void __launch_bounds__(kJpThreads) k_jp_persistent(DCount Cc, uint32_t* wl0,
+                                                              uint32_t* wl1, uint32_t* cnt,
+                                                              const uint32_t* __restrict__ poff,
+                                                              const uint2* __restrict__ preds, uint32_t* cstate,
+                                                              uint32_t* whead, uint32_t* __restrict__ wnext,
+                                                              DevInfo* info)
+{
+    const uint32_t C = (uint32_t)Cc.get();
+    if (C == 0 || (info->err & kErrPreds)) return;   // overflowed lists: the colours stay unset (error bit)
+    for (uint32_t round = 1; round <= (uint32_t)kJpMaxRounds; ++round) {
+        const int ci = (round - 1) % 3, co = round % 3, cc = (round + 1) % 3;
+        const bool odd = (round & 1u) != 0u;   // round 1 reads wl0 and writes wl1, round 2 the reverse, ...
+        jp_round(round, C, odd ? wl0 : wl1, cnt + 2 * ci, odd ? wl1 : wl0, cnt + 2 * co, cnt + 2 * cc, poff, preds,
+                 cstate, whead, wnext, info);
+        if (!jp_barrier(info)) return;
+        if (__ldcg(cnt + 2 * co) + __ldcg(cnt + 2 * co + 1) == 0u) return;   // nothing coloured or left to examine
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&info->err, kErrColours);
+}
+
+__global__ void k_colour_keys(DCount Cc, const uint32_t* __restrict__ cstate, uint32_t* __restrict__ ckey,
                               uint32_t* __restrict__ cval, uint32_t* __restrict__ col_count, DevInfo* info)
 {
+    const int64_t C = Cc.get();
     __shared__ uint32_t h[kMaxColours];
     for (int t = threadIdx.x; t < kMaxColours; t += blockDim.x) h[t] = 0;
     __syncthreads();
@@ -396,15 +480,16 @@ __global__ void k_colour_offsets(const uint32_t* __restrict__ col_count, uint32_
 // previous step (world frame, re-projected onto the new frame and the cone)
 // or zero.
 template <class R>
-__global__ void k_build_sweep(int64_t C, int64_t n, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cj1,
+__global__ void k_build_sweep(DCount Cc, int64_t n, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cj1,
                               const uint32_t* __restrict__ cj2, const uint32_t* __restrict__ inst,
                               const double4_32a* __restrict__ cgeo,
                               const double2* __restrict__ clev, double dt, double beta, double mu_all, SceneView V,
                               int warm,
                               const uint32_t* __restrict__ prev_row_off, const uint32_t* __restrict__ prev_j2,
-                              const double4_32a* __restrict__ prev_P, SweepRec<R>* __restrict__ rec,
+                              const double4_32a* __restrict__ prev_P, int64_t prev_cap, SweepRec<R>* __restrict__ rec,
                               R4<R>* __restrict__ p)
 {
+    const int64_t C = Cc.get();
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < C; s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = perm[s];
         const uint32_t a = cj1[c], b = cj2[c];
@@ -433,7 +518,7 @@ __global__ void k_build_sweep(int64_t C, int64_t n, const uint32_t* __restrict__
         R pn = R(0), pt = R(0), po = R(0), found = R(0);
         if (warm) {
             const uint32_t e = prev_row_off[a + 1];
-            for (uint32_t t = prev_row_off[a]; t < e; ++t) {
+            for (uint32_t t = prev_row_off[a]; t < e && t < prev_cap; ++t) {
                 if (prev_j2[t] != b) continue;
                 const double4_32a P = prev_P[t];
                 const R mu = (R)(V.batch ? V.mu[V.scene_of[a]] : mu_all);
@@ -466,11 +551,34 @@ __global__ void k_build_sweep(int64_t C, int64_t n, const uint32_t* __restrict__
     }
 }
 
+// Device-sized steps: predecessor entries beyond the buffer set an error bit.
+__global__ void k_check_preds(DevInfo* info, int64_t pcap)
+{
+    if ((int64_t)info->pred_total > pcap) atomicOr(&info->err, kErrPreds);
+}
+
+// Resident blocks of the cooperative colouring launch (every block must be
+// resident for its grid barriers), looked up once.
+static int jp_blocks(const nbgs_scene* s)
+{
+    static int occ = -1;
+    if (occ < 0) {
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, (const void*)k_jp_persistent, kJpThreads, 0);
+        cudaGetLastError();
+        occ = o > 0 ? o : 1;
+    }
+    return occ * s->num_sms;
+}
+
 nbgs_status run_colour(nbgs_scene* s)
 {
     if (!s->detected) return fail(s, NBGS_EINVAL, "colour_contacts: call detect_contacts first");
     cudaStream_t st = s->stream;
+    // C: the count, or in device-sized steps the capacity the launches are
+    // sized for (the kernels read the count, Cn, on the device)
     const int64_t C = s->n_contacts, n = s->n;
+    const DCount Cn = contact_count(s);
     if (s->timing) cudaEventRecord(s->ev[2], st);
     cudaMemsetAsync(s->col_count, 0, (kMaxColours + 1) * sizeof(uint32_t), st);
     cudaMemsetAsync(&s->info->n_colours, 0, sizeof(uint32_t), st);
@@ -491,12 +599,12 @@ nbgs_status run_colour(nbgs_scene* s)
         const uint8_t* finc = s->composite ? s->bfinite : s->finite;
         const int64_t ninc = s->composite ? s->nb : n;
         cudaMemsetAsync(s->deg, 0, (ninc + 1) * sizeof(uint32_t), st);
-        k_colour_init<<<gb, T, 0, st>>>(C, ninc, s->cj1, s->cj2, ib1, ib2, finc, s->prm.colour_seed, scene_view(s),
+        k_colour_init<<<gb, T, 0, st>>>(Cn, ninc, s->cj1, s->cj2, ib1, ib2, finc, s->prm.colour_seed, scene_view(s),
                                         s->deg, s->cprio, s->cstate);
         nbgs_status rc = exclusive_scan_u32(s, s->deg, s->adj_off, ninc, nullptr);
         if (rc != NBGS_OK) return rc;
         cudaMemsetAsync(s->deg, 0, (ninc + 1) * sizeof(uint32_t), st);
-        k_adj_fill<<<gb, T, 0, st>>>(C, ninc, ib1, ib2, finc, s->adj_off, s->deg, s->adj);
+        k_adj_fill<<<gb, T, 0, st>>>(Cn, ninc, ib1, ib2, finc, s->adj_off, s->deg, s->adj);
         if (sub) {
             rc = run_subdomains(s);
             if (rc != NBGS_OK) return rc;
@@ -508,54 +616,76 @@ nbgs_status run_colour(nbgs_scene* s)
             cudaMemsetAsync(s->cstate, 0, C * sizeof(uint32_t), st);
         } else {
             // predecessor lists (counts, offsets, lists weakest first)
-            k_pred_count<<<gb, T, 0, st>>>(C, ninc, ib1, ib2, finc, s->adj_off, s->adj, s->cprio, s->pmask,
+            k_pred_count<<<gb, T, 0, st>>>(Cn, ninc, ib1, ib2, finc, s->adj_off, s->adj, s->cprio, s->pmask,
                                            s->colour_key);
-            rc = exclusive_scan_u32(s, s->colour_key, s->poff, C, nullptr);
+            rc = exclusive_scan_u32(s, s->colour_key, s->poff, Cn, s->device_sized ? &s->info->pred_total : nullptr);
             if (rc != NBGS_OK) return rc;
-            uint32_t total = 0;
-            rc = cuda_check(s, cudaMemcpyAsync(&total, s->poff + C, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
-                            "colour: predecessor count");
-            if (rc == NBGS_OK) rc = cuda_check(s, cudaStreamSynchronize(st), "colour");
-            if (rc != NBGS_OK) return rc;
-            rc = grow_preds(s, total);
-            if (rc != NBGS_OK) return rc;
+            if (s->device_sized) {
+                // the lists keep their capacity; an overflow sets an error bit
+                k_check_preds<<<1, 1, 0, st>>>(s->info, s->preds_cap);
+            } else {
+                uint32_t total = 0;
+                rc = cuda_check(s, cudaMemcpyAsync(&total, s->poff + C, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
+                                "colour: predecessor count");
+                if (rc == NBGS_OK) rc = cuda_check(s, cudaStreamSynchronize(st), "colour");
+                if (rc != NBGS_OK) return rc;
+                rc = grow_preds(s, total);
+                if (rc != NBGS_OK) return rc;
+            }
             // waiting lists empty; round-1 counters (|L| = 0, |X| filled below)
             cudaMemsetAsync(s->whead, 0xFF, C * sizeof(uint32_t), st);
             cudaMemsetAsync(s->info->wl_count, 0, sizeof(s->info->wl_count), st);
-            k_pred_lists<<<gb, T, 0, st>>>(C, ninc, ib1, ib2, finc, s->adj_off, s->adj, s->cprio, s->pmask,
-                                           s->poff, s->preds, s->whead, s->wnext, s->wl[0], &s->info->wl_count[1]);
+            k_pred_lists<<<gb, T, 0, st>>>(Cn, ninc, ib1, ib2, finc, s->adj_off, s->adj, s->cprio, s->pmask,
+                                           s->poff, s->preds, s->preds_cap, s->whead, s->wnext, s->wl[0],
+                                           &s->info->wl_count[1]);
             if (s->timing) s->phase_launches[1] += 9;
-            // rounds; the host checks the lists every few rounds
-            const int gbr = grid_for(C, kJpThreads, 8, s->num_sms);
-            uint32_t round = 0;
-            int cur = 0;
-            for (int batch = 0; batch < 64; ++batch) {
-                for (int r = 0; r < 6; ++r) {
-                    ++round;
-                    const int ci = (round - 1) % 3, co = round % 3, cc = (round + 1) % 3;
-                    k_jp_round<<<gbr, kJpThreads, 0, st>>>(round, (uint32_t)C, s->wl[cur], &s->info->wl_count[2 * ci],
-                                                           s->wl[1 - cur], &s->info->wl_count[2 * co],
-                                                           &s->info->wl_count[2 * cc], s->poff, s->preds, s->cstate,
-                                                           s->whead, s->wnext, s->info);
-                    cur = 1 - cur;
+            if (s->device_sized) {
+                // all rounds in one cooperative launch (grid barrier between rounds)
+                cudaMemsetAsync(&s->info->barrier_count, 0, 2 * sizeof(uint32_t), st);
+                const int gbr = std::min(jp_blocks(s), grid_for(C, kJpThreads, 8, s->num_sms));
+                DCount Cd = Cn;
+                uint32_t *wl0 = s->wl[0], *wl1 = s->wl[1], *cnt = s->info->wl_count;
+                void* args[] = {(void*)&Cd, (void*)&wl0, (void*)&wl1, (void*)&cnt, (void*)&s->poff, (void*)&s->preds,
+                                (void*)&s->cstate, (void*)&s->whead, (void*)&s->wnext, (void*)&s->info};
+                rc = cuda_check(s, cudaLaunchCooperativeKernel((const void*)k_jp_persistent, dim3(gbr),
+                                                               dim3(kJpThreads), args, 0, st),
+                                "colour: rounds");
+                if (rc != NBGS_OK) return rc;
+                if (s->timing) s->phase_launches[1] += 2;
+            } else {
+                // one launch per round; the host checks the lists every few rounds
+                const int gbr = grid_for(C, kJpThreads, 8, s->num_sms);
+                uint32_t round = 0;
+                int cur = 0;
+                for (int batch = 0; batch < 64; ++batch) {
+                    for (int r = 0; r < 6; ++r) {
+                        ++round;
+                        const int ci = (round - 1) % 3, co = round % 3, cc = (round + 1) % 3;
+                        k_jp_round<<<gbr, kJpThreads, 0, st>>>(round, (uint32_t)C, s->wl[cur],
+                                                               &s->info->wl_count[2 * ci], s->wl[1 - cur],
+                                                               &s->info->wl_count[2 * co], &s->info->wl_count[2 * cc],
+                                                               s->poff, s->preds, s->cstate, s->whead, s->wnext,
+                                                               s->info);
+                        cur = 1 - cur;
+                    }
+                    if (s->timing) s->phase_launches[1] += 6;
+                    uint32_t left[2] = {0, 0};
+                    rc = cuda_check(s, cudaMemcpyAsync(left, &s->info->wl_count[2 * (round % 3)], 2 * sizeof(uint32_t),
+                                                       cudaMemcpyDeviceToHost, st), "colour: worklist");
+                    if (rc != NBGS_OK) return rc;
+                    rc = cuda_check(s, cudaStreamSynchronize(st), "colour");
+                    if (rc != NBGS_OK) return rc;
+                    if (left[0] + left[1] == 0) break;
+                    if (batch == 63) return fail(s, NBGS_ETIMEOUT, "colour: did not finish in 384 rounds");
                 }
-                if (s->timing) s->phase_launches[1] += 6;
-                uint32_t left[2] = {0, 0};
-                rc = cuda_check(s, cudaMemcpyAsync(left, &s->info->wl_count[2 * (round % 3)], 2 * sizeof(uint32_t),
-                                                   cudaMemcpyDeviceToHost, st), "colour: worklist");
-                if (rc != NBGS_OK) return rc;
-                rc = cuda_check(s, cudaStreamSynchronize(st), "colour");
-                if (rc != NBGS_OK) return rc;
-                if (left[0] + left[1] == 0) break;
-                if (batch == 63) return fail(s, NBGS_ETIMEOUT, "colour: did not finish in 384 rounds");
             }
         }
-        k_colour_keys<<<gb, T, 0, st>>>(C, s->cstate, s->colour_key, s->perm_in, s->col_count, s->info);
+        k_colour_keys<<<gb, T, 0, st>>>(Cn, s->cstate, s->colour_key, s->perm_in, s->col_count, s->info);
         k_colour_offsets<<<1, 32, 0, st>>>(s->col_count, s->col_off);
         // stable counting sort by colour (one 8-bit radix pass): contacts of a
         // colour stay in canonical order
         uint32_t *k0 = s->colour_key, *k1 = s->colour_key2, *v0 = s->perm_in, *v1 = s->perm;
-        rc = radix_sort_pairs(s, k0, v0, k1, v1, C, 8);
+        rc = radix_sort_pairs(s, k0, v0, k1, v1, Cn, 8);
         if (rc != NBGS_OK) return rc;
         // radix_sort_pairs swapped the pointers: v0 / k0 now hold the sorted values / keys
         if (v0 != s->perm) std::swap(s->perm, s->perm_in);
@@ -566,17 +696,18 @@ nbgs_status run_colour(nbgs_scene* s)
             rc = run_comp_records(s, warm);
             if (rc != NBGS_OK) return rc;
         } else if (s->fp32)
-            k_build_sweep<float><<<gb, T, 0, st>>>(C, n, s->perm, s->cj1, s->cj2, sub ? s->inst : nullptr, s->cgeo,
+            k_build_sweep<float><<<gb, T, 0, st>>>(Cn, n, s->perm, s->cj1, s->cj2, sub ? s->inst : nullptr, s->cgeo,
                                                    s->clev, s->prm.dt,
                                                    s->prm.beta, s->prm.mu, scene_view(s), warm, s->prev_row_off,
                                                    s->prev_j2,
-                                                   s->prev_P, (SweepRec<float>*)s->srec, (float4*)s->sp);
+                                                   s->prev_P, s->ccap, (SweepRec<float>*)s->srec, (float4*)s->sp);
         else
-            k_build_sweep<double><<<gb, T, 0, st>>>(C, n, s->perm, s->cj1, s->cj2, sub ? s->inst : nullptr, s->cgeo,
+            k_build_sweep<double><<<gb, T, 0, st>>>(Cn, n, s->perm, s->cj1, s->cj2, sub ? s->inst : nullptr, s->cgeo,
                                                     s->clev, s->prm.dt,
                                                     s->prm.beta, s->prm.mu, scene_view(s), warm, s->prev_row_off,
                                                     s->prev_j2,
-                                                    s->prev_P, (SweepRec<double>*)s->srec, (double4_32a*)s->sp);
+                                                    s->prev_P, s->ccap, (SweepRec<double>*)s->srec,
+                                                    (double4_32a*)s->sp);
         if (s->timing) s->phase_launches[1] += 3;
         s->n_colours = -1;  // known on the device; read lazily
     } else {

@@ -71,8 +71,9 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& excl)
     return total;
 }
 
-__global__ void k_scan_reduce(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums)
+__global__ void k_scan_reduce(const uint32_t* __restrict__ in, DCount nc, uint32_t* __restrict__ sums)
 {
+    const int64_t n = nc.get();
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     uint32_t acc = 0;
 #pragma unroll
@@ -99,10 +100,11 @@ __global__ void k_scan_top(uint32_t* sums, int64_t nb)
     }
 }
 
-__global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
+__global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, DCount nc,
                             const uint32_t* __restrict__ sums, uint32_t* __restrict__ total_dst)
 {
     __shared__ uint32_t tile[kScanTile];
+    const int64_t n = nc.get();   // tiles past n hold zeros: the last block's total is the total
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
@@ -136,15 +138,21 @@ __global__ void k_scan_down(const uint32_t* __restrict__ in, uint32_t* __restric
 }
 
 // out must hold n + 1 entries; out[n] receives the total (also *total_dst).
-nbgs_status exclusive_scan_u32(nbgs_scene* s, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dst)
+// A device-read count: the launch covers n.v entries (the capacity).
+nbgs_status exclusive_scan_u32(nbgs_scene* s, const uint32_t* in, uint32_t* out, DCount n, uint32_t* total_dst)
 {
-    int64_t nb = (n + kScanTile - 1) / kScanTile;
+    int64_t nb = (n.v + kScanTile - 1) / kScanTile;
     if (nb < 1) nb = 1;
     if (nb > s->scan_tmp_len) return fail(s, NBGS_EINVAL, "scan: block-sum buffer too small");
     k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s->stream>>>(in, n, s->scan_tmp);
     k_scan_top<<<1, 1024, 0, s->stream>>>(s->scan_tmp, nb);
     k_scan_down<<<(unsigned)nb, kScanThreads, 0, s->stream>>>(in, out, n, s->scan_tmp, total_dst);
     return cuda_check(s, cudaGetLastError(), "scan");
+}
+
+nbgs_status exclusive_scan_u32(nbgs_scene* s, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dst)
+{
+    return exclusive_scan_u32(s, in, out, DCount{n, nullptr}, total_dst);
 }
 
 // ---------------------------------------------------------------------------
@@ -157,10 +165,11 @@ constexpr int kRadixItems = 16;
 constexpr int kRadixTile = kRadixThreads * kRadixItems;   // 4096
 constexpr int kWarps = kRadixThreads / 32;
 
-__global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist,
+__global__ void k_radix_hist(const uint32_t* __restrict__ keys, DCount nc, int shift, uint32_t* __restrict__ hist,
                              int64_t nblocks)
 {
     __shared__ uint32_t h[256];
+    const int64_t n = nc.get();
     h[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kRadixTile;
@@ -175,9 +184,10 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int64_t n, int s
 
 __global__ void __launch_bounds__(kRadixThreads)
 k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
-                uint32_t* __restrict__ vout, int64_t n, int shift, const uint32_t* __restrict__ hist_scan,
+                uint32_t* __restrict__ vout, DCount nc, int shift, const uint32_t* __restrict__ hist_scan,
                 int64_t nblocks)
 {
+    const int64_t n = nc.get();
     __shared__ uint32_t cnt[kWarps][256];
     __shared__ uint32_t goff[256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -229,10 +239,10 @@ k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ v
 }
 
 nbgs_status radix_sort_pairs(nbgs_scene* s, uint32_t*& keys, uint32_t*& vals, uint32_t*& keys_alt,
-                             uint32_t*& vals_alt, int64_t n, int bits)
+                             uint32_t*& vals_alt, DCount n, int bits)
 {
-    if (n <= 1) return NBGS_OK;
-    const int64_t nb = (n + kRadixTile - 1) / kRadixTile;
+    if (!n.dev && n.v <= 1) return NBGS_OK;
+    const int64_t nb = std::max<int64_t>((n.v + kRadixTile - 1) / kRadixTile, 1);
     if (256 * nb > s->radix_hist_len) return fail(s, NBGS_EINVAL, "radix sort: histogram buffer too small");
     for (int shift = 0; shift < bits; shift += 8) {
         k_radix_hist<<<(unsigned)nb, kRadixThreads, 0, s->stream>>>(keys, n, shift, s->radix_hist, nb);
@@ -249,6 +259,12 @@ nbgs_status radix_sort_pairs(nbgs_scene* s, uint32_t*& keys, uint32_t*& vals, ui
         if (s->timing) s->phase_launches[0] += 4;
     }
     return cuda_check(s, cudaGetLastError(), "radix sort");
+}
+
+nbgs_status radix_sort_pairs(nbgs_scene* s, uint32_t*& keys, uint32_t*& vals, uint32_t*& keys_alt,
+                             uint32_t*& vals_alt, int64_t n, int bits)
+{
+    return radix_sort_pairs(s, keys, vals, keys_alt, vals_alt, DCount{n, nullptr}, bits);
 }
 
 // ---------------------------------------------------------------------------
@@ -844,6 +860,15 @@ static GridArgs grid_args(const nbgs_scene* s)
 
 nbgs_status grow_contacts(nbgs_scene* s, int64_t need);  // api.cu
 
+// Device-sized steps: the previous step's contact count, kept before the
+// detection clears it; a count beyond the buffers sets the contact error bit.
+__global__ void k_keep_count(DevInfo* info) { info->prev_contacts = info->n_contacts; }
+
+__global__ void k_check_contacts(DevInfo* info, int64_t ccap)
+{
+    if ((int64_t)info->n_contacts > ccap) atomicOr(&info->err, kErrContacts);
+}
+
 nbgs_status run_detect(nbgs_scene* s)
 {
     const int64_t n = s->n;
@@ -863,6 +888,7 @@ nbgs_status run_detect(nbgs_scene* s)
     s->detected = s->coloured = s->solved = false;
     s->n_contacts = 0;
     s->sub_count = -1;
+    if (s->device_sized) k_keep_count<<<1, 1, 0, st>>>(s->info);
     cudaMemsetAsync(s->info, 0, offsetof(DevInfo, cell_w), st);   // hmax, vmax
     cudaMemsetAsync(&s->info->n_contacts, 0, sizeof(uint32_t), st);
     if (n == 0) {
@@ -905,6 +931,22 @@ nbgs_status run_detect(nbgs_scene* s)
     rc = exclusive_scan_u32(s, s->row_cnt, s->row_off, n, &s->info->n_contacts);
     if (rc != NBGS_OK) return rc;
     if (s->timing) s->phase_launches[0] += 5;
+    if (s->device_sized) {
+        // no synchronisation: the buffers keep their capacity, an overflow
+        // sets an error bit (the writes past it are skipped), and every
+        // later kernel reads the count on the device
+        k_check_contacts<<<1, 1, 0, st>>>(s->info, s->ccap);
+        k_write_contacts<<<grid_for(n, T, 8, s->num_sms), T, 0, st>>>(n, s->ccap, s->vals[0], s->pos_r, s->hull,
+                                                                      s->cand, s->sph_cnt, s->row_off, g, s->planes,
+                                                                      scene_view(s), s->cj1, s->cj2, s->cgeo, s->clev);
+        if (s->timing) {
+            s->phase_launches[0] += 3;
+            cudaEventRecord(s->ev[1], st);
+        }
+        s->n_contacts = s->ccap;   // an upper bound; the count itself stays on the device
+        s->detected = true;
+        return cuda_check(s, cudaGetLastError(), "detect");
+    }
     // one synchronisation per step: the contact count sizes everything after
     rc = cuda_check(s, cudaMemcpyAsync(s->hinfo, s->info, offsetof(DevInfo, rk_bits), cudaMemcpyDeviceToHost, st),
                     "detect: read info");

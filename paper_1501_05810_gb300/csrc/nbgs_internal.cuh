@@ -40,7 +40,25 @@ enum : uint32_t {
     kErrColours = 4u,     // more than kMaxColours colours
     kErrTimeout = 8u,     // a grid barrier wait gave up
     kErrNaN = 16u,        // NaN / Inf in velocities or positions
-    kErrGrid = 32u        // periodic axis with fewer than 3 cells
+    kErrGrid = 32u,       // periodic axis with fewer than 3 cells
+    kErrPreds = 64u       // colouring predecessor lists beyond their buffer (device-sized steps)
+};
+
+// A count that the host either knows (dev == nullptr: v is the count) or
+// leaves to the device (v is the capacity the launch is sized for, *dev the
+// count, read by the kernel): device-sized steps read every contact count
+// on the device, so that no step waits for the host.  A device count beyond
+// the capacity (an overflow, reported by an error bit) is clamped to it, so
+// that no kernel reads or writes past the buffers.
+struct DCount {
+    int64_t v;
+    const uint32_t* dev;
+    __device__ __forceinline__ int64_t get() const
+    {
+        if (!dev) return v;
+        const int64_t c = (int64_t)*dev;
+        return c < v ? c : v;
+    }
 };
 
 constexpr int kMaxCones = 4;
@@ -123,6 +141,9 @@ struct DevInfo {
     uint32_t rounds;                 // colouring rounds used
     uint32_t n_shared;               // subdomains: bodies with more than one velocity instance
     uint32_t n_extra;                // subdomains: velocity instances after the n bodies
+    uint32_t pred_total;             // colouring: predecessor entries of the step
+    uint32_t prev_contacts;          // contacts of the previous step (device-sized steps)
+    unsigned long long updates;      // contact updates (contacts x sweeps relaxed) since the last read
     double residual;                 // R of the last sweep
     double v_ref;
     unsigned long long rk_bits[kMaxSweepsHist];  // max_j r_j of sweep k (bits)
@@ -478,6 +499,17 @@ struct nbgs_scene {
     bool coloured = false;
     bool solved = false;
     int32_t last_sweeps = 0;
+    // device-sized steps (nbgs_graph_step): no host synchronisation inside a
+    // step; contact counts are read on the device, buffers keep their
+    // capacities and overflows set error bits; the step is captured as two
+    // CUDA graphs (the two parities of the warm-start buffer swap)
+    bool device_sized = false;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int32_t g_sweeps = -1;
+    double g_tol = -1.0;
+    int g_next = 0;                // graph of the next replay
+    int64_t g_ccap = -1, g_pcap = -1;   // capacities the graphs were captured with
+    bool counts_stale = false;     // graphs ran since the host last read the counts
     // timing
     bool timing = false;
     cudaEvent_t ev[10] = {};            // start/end of detect, colour, solve, integrate, sweep kernels
@@ -534,8 +566,17 @@ nbgs_status exclusive_scan_u32(nbgs_scene* s, const uint32_t* in, uint32_t* out,
                                uint32_t* total_dst);
 nbgs_status radix_sort_pairs(nbgs_scene* s, uint32_t*& keys, uint32_t*& vals, uint32_t*& keys_alt,
                              uint32_t*& vals_alt, int64_t n, int bits);
+nbgs_status exclusive_scan_u32(nbgs_scene* s, const uint32_t* in, uint32_t* out, DCount n, uint32_t* total_dst);
+nbgs_status radix_sort_pairs(nbgs_scene* s, uint32_t*& keys, uint32_t*& vals, uint32_t*& keys_alt,
+                             uint32_t*& vals_alt, DCount n, int bits);
 int grid_for(int64_t work, int threads, int max_blocks_per_sm, int num_sms);
 nbgs_status grow_preds(nbgs_scene* s, int64_t need);
+// The contact count of the current step for kernels: host-known, or read on
+// the device (device-sized steps; launches sized for the capacity).
+inline DCount contact_count(const nbgs_scene* s)
+{
+    return s->device_sized ? DCount{s->ccap, &s->info->n_contacts} : DCount{s->n_contacts, nullptr};
+}
 SceneView scene_view(const nbgs_scene* s);
 
 }  // namespace nbgs

@@ -925,10 +925,11 @@ __global__ void k_reduce_fill(int64_t C, int nblk, const uint32_t* __restrict__ 
 
 // Chunk boundaries: cstart[c][b] = first slot of colour c whose canonical
 // index is >= ceil(b C / B) (binary search; perm is increasing in a colour).
-__global__ void k_chunk_starts(int64_t C, int nblk, const uint32_t* __restrict__ col_off,
+__global__ void k_chunk_starts(DCount Cc, int nblk, const uint32_t* __restrict__ col_off,
                                const uint32_t* __restrict__ perm, const DevInfo* __restrict__ info,
                                uint32_t* __restrict__ cstart)
 {
+    const int64_t C = Cc.get();
     const int ncol = (int)info->n_colours;
     const int64_t total = (int64_t)ncol * (nblk + 1);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -946,11 +947,12 @@ __global__ void k_chunk_starts(int64_t C, int nblk, const uint32_t* __restrict__
 
 // Pass 1: per finite body, min and max ring offset (from its home block) of
 // the blocks whose chunks hold a contact of the body.
-__global__ void k_body_blocks(int64_t C, int64_t n, int nblk, const uint32_t* __restrict__ perm,
+__global__ void k_body_blocks(DCount Cc, int64_t n, int nblk, const uint32_t* __restrict__ perm,
                               const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
                               const uint32_t* __restrict__ row_off, const uint8_t* __restrict__ finite,
                               int* __restrict__ dmin, int* __restrict__ dmax)
 {
+    const int64_t C = Cc.get();
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < C; s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = perm[s];
         const int b = block_of(k, C, nblk);
@@ -971,13 +973,14 @@ __global__ void k_body_blocks(int64_t C, int64_t n, int nblk, const uint32_t* __
 // Pass 2: block b computes, for its chunk of every colour, the ring window
 // [lo, hi] (offsets from b) covering every block that touches one of the
 // chunk's bodies.
-__global__ void k_chunk_windows(int64_t C, int64_t n, const uint32_t* __restrict__ cstart,
+__global__ void k_chunk_windows(DCount Cc, int64_t n, const uint32_t* __restrict__ cstart,
                                 const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cj1,
                                 const uint32_t* __restrict__ cj2, const uint32_t* __restrict__ row_off,
                                 const uint8_t* __restrict__ finite, const int* __restrict__ dmin,
                                 const int* __restrict__ dmax, const DevInfo* __restrict__ info,
                                 int2* __restrict__ dep)
 {
+    const int64_t C = Cc.get();
     __shared__ int slo[32], shi[32];
     const int ncol = (int)info->n_colours;
     const int nblk = gridDim.x;
@@ -1033,15 +1036,15 @@ nbgs_status build_windows(nbgs_scene* s, int B, int64_t ninc, const uint32_t* ib
     const int T = 256;
     const int64_t C = s->n_contacts;
     cudaStream_t st = s->stream;
-    k_chunk_starts<<<grid_for((int64_t)kMaxColours * (B + 1), T, 8, s->num_sms), T, 0, st>>>(C, B, s->col_off,
+    k_chunk_starts<<<grid_for((int64_t)kMaxColours * (B + 1), T, 8, s->num_sms), T, 0, st>>>(DCount{C, nullptr}, B, s->col_off,
                                                                                           s->perm, s->info, s->cstart);
     int* dmin = (int*)s->deg;
     int* dmax = (int*)s->adj_off;
     cudaMemsetAsync(dmin, 0x7F, (size_t)std::max<int64_t>(ninc, 1) * sizeof(int), st);
     cudaMemsetAsync(dmax, 0x80, (size_t)std::max<int64_t>(ninc, 1) * sizeof(int), st);
-    k_body_blocks<<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(C, ninc, B, s->perm, ib1, ib2, anchor, finc, dmin,
+    k_body_blocks<<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(DCount{C, nullptr}, ninc, B, s->perm, ib1, ib2, anchor, finc, dmin,
                                                                 dmax);
-    k_chunk_windows<<<B, T, 0, st>>>(C, ninc, s->cstart, s->perm, ib1, ib2, anchor, finc, dmin, dmax, s->info,
+    k_chunk_windows<<<B, T, 0, st>>>(DCount{C, nullptr}, ninc, s->cstart, s->perm, ib1, ib2, anchor, finc, dmin, dmax, s->info,
                                       s->dep);
     cudaMemsetAsync(s->prog, 0xFF, (size_t)B * sizeof(int), st);
     if (s->timing) s->phase_launches[2] += 3;
@@ -1109,9 +1112,10 @@ __global__ void k_scene_vref(int64_t S, const unsigned long long* __restrict__ v
 // Canonical impulses (contact frame) and world-frame impulses for the next
 // warm start.
 template <class R>
-__global__ void k_finish(int64_t C, const uint32_t* __restrict__ perm, const R4<R>* __restrict__ p,
+__global__ void k_finish(DCount Cc, const uint32_t* __restrict__ perm, const R4<R>* __restrict__ p,
                          const double4_32a* __restrict__ cgeo, double4_32a* __restrict__ cimp, double4_32a* __restrict__ cworld)
 {
+    const int64_t C = Cc.get();
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < C; s += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t c = perm[s];
         const R4<R> q = p[s];
@@ -1123,6 +1127,25 @@ __global__ void k_finish(int64_t C, const uint32_t* __restrict__ perm, const R4<
         cworld[c] = make_double4_32a(pn * g.x + pt * tx + po * ox, pn * g.y + pt * ty + po * oy,
                                  pn * g.z + pt * tz + po * oz, 0.0);
     }
+}
+
+// Contact updates of the solve just finished: every contact relaxed once
+// per sweep its scene ran (a scene of a batch stops at its own tolerance).
+__global__ void k_count_updates(DCount Cc, int max_sweeps, const uint32_t* __restrict__ perm,
+                                const uint32_t* __restrict__ cj1, SceneView V, const uint32_t* __restrict__ scene_done,
+                                DevInfo* info)
+{
+    const int64_t C = Cc.get();
+    if (max_sweeps == 0) return;
+    if (!V.batch) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&info->updates, (unsigned long long)C * info->sweeps_done);
+        return;
+    }
+    unsigned long long u = 0;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < C; s += (int64_t)gridDim.x * blockDim.x)
+        u += scene_done[V.scene_of[cj1[perm[s]]]];
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(0xffffffffu, u, o);
+    if ((threadIdx.x & 31) == 0 && u) atomicAdd(&info->updates, u);
 }
 
 // Impulses given in canonical order and in the contact frame (n, t, o)
@@ -1257,19 +1280,20 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
         // hold more contacts per thread fit fewer blocks per SM
         const int nblocks = std::min(s->coop_blocks, persist_occ<R>(fn) * s->num_sms);
         if (nblocks < 1) return fail(s, NBGS_ECUDA, "solve: persistent kernel does not fit");
+        const DCount Cn = contact_count(s);
         if (A.C > 0) {
             const int T = 256, B = nblocks * (warp ? kPersistThreads / 32 : 1);
             k_chunk_starts<<<grid_for((int64_t)kMaxColours * (B + 1), T, 8, s->num_sms), T, 0, st>>>(
-                A.C, B, s->col_off, s->perm, s->info, s->cstart);
+                Cn, B, s->col_off, s->perm, s->info, s->cstart);
             if (s->timing) s->phase_launches[2] += 1;
             if (!(s->prm.sweep_flags & NBGS_SWEEP_GLOBAL_SYNC)) {
                 int* dmin = (int*)s->deg;      // colouring scratch, free during the solve
                 int* dmax = (int*)s->adj_off;
                 cudaMemsetAsync(dmin, 0x7F, s->n * sizeof(int), st);   // large positive
                 cudaMemsetAsync(dmax, 0x80, s->n * sizeof(int), st);   // large negative
-                k_body_blocks<<<grid_for(A.C, T, 8, s->num_sms), T, 0, st>>>(A.C, s->n, B, s->perm, s->cj1, s->cj2,
+                k_body_blocks<<<grid_for(A.C, T, 8, s->num_sms), T, 0, st>>>(Cn, s->n, B, s->perm, s->cj1, s->cj2,
                                                                               s->row_off, s->finite, dmin, dmax);
-                k_chunk_windows<<<B, T, 0, st>>>(A.C, s->n, s->cstart, s->perm, s->cj1, s->cj2, s->row_off,
+                k_chunk_windows<<<B, T, 0, st>>>(Cn, s->n, s->cstart, s->perm, s->cj1, s->cj2, s->row_off,
                                                   s->finite, dmin, dmax, s->info, s->dep);
                 cudaMemsetAsync(s->prog, 0xFF, B * sizeof(int), st);
                 if (s->timing) s->phase_launches[2] += 2;
@@ -1352,12 +1376,18 @@ nbgs_status run_solve(nbgs_scene* s, int max_sweeps, double tol)
     if (C > 0) {
         const int T = 256;
         if (s->fp32)
-            k_finish<float><<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(C, s->perm, (const float4*)s->sp, s->cgeo,
+            k_finish<float><<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(contact_count(s), s->perm, (const float4*)s->sp, s->cgeo,
                                                                          s->cimp, s->cworld);
         else
-            k_finish<double><<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(C, s->perm, (const double4_32a*)s->sp, s->cgeo,
+            k_finish<double><<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(contact_count(s), s->perm, (const double4_32a*)s->sp, s->cgeo,
                                                                           s->cimp, s->cworld);
     }
+    if (C > 0 && !s->composite)
+        k_count_updates<<<s->batch ? grid_for(C, 256, 8, s->num_sms) : 1, 256, 0, st>>>(
+            contact_count(s), max_sweeps, s->perm, s->cj1, scene_view(s), s->scene_done, s->info);
+    else if (C > 0)
+        k_count_updates<<<1, 32, 0, st>>>(contact_count(s), max_sweeps, s->perm, s->cj1, scene_view(s), nullptr,
+                                          s->info);
     s->solved = true;
     s->last_sweeps = max_sweeps;
     return cuda_check(s, cudaGetLastError(), "solve");

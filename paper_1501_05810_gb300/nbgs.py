@@ -89,6 +89,8 @@ _SIG = {
                           _P(nbgs_allocator), _vp, _P(_vp)],
     "nbgs_batch_step": [_vp, C.c_int32, C.c_double, _i32p, _dp],
     "nbgs_get_scene_stats": [_vp, _i32p, _dp],
+    "nbgs_graph_step": [_vp, C.c_int32, C.c_double, C.c_int32],
+    "nbgs_get_updates": [_vp, _i64p],
     "nbgs_autotune": [_vp, C.c_int32, C.c_double, _i32p, _i32p],
     "nbgs_mlp_load": [_vp, _vp, C.c_int64],
     "nbgs_set_warm_start": [_vp, C.c_int32],
@@ -327,6 +329,17 @@ class Scene:
         st = nbgs_step_stats()
         _call(self.h, "nbgs_step", int(max_sweeps), float(tol), C.byref(st))
         return {f: getattr(st, f) for f, _ in nbgs_step_stats._fields_}
+
+    def graph_step(self, max_sweeps: int, tol: float = 0.0, n_steps: int = 1) -> None:
+        """n_steps time steps replayed from captured CUDA graphs, without host
+        synchronisation (asynchronous; read results with the usual calls)."""
+        _call(self.h, "nbgs_graph_step", int(max_sweeps), float(tol), int(n_steps))
+
+    def get_updates(self) -> int:
+        """Contact updates since the last call (read and reset)."""
+        u = C.c_int64()
+        _call(self.h, "nbgs_get_updates", C.byref(u))
+        return u.value
 
     def sync(self):
         _call(self.h, "nbgs_sync")
