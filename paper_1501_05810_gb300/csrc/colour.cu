@@ -367,13 +367,65 @@ __device__ __forceinline__ void jp_round(uint32_t round, uint32_t C, const uint3
 
 // One round per launch (the host checks the lists every few rounds).
 __global__ void __launch_bounds__(kJpThreads) k_jp_round(uint32_t round, uint32_t C, const uint32_t* __restrict__ wl_in,
-                                                         const uint32_t* cnt_in, uint32_t* __restrict__ wl_out,
-                                                         uint32_t* cnt_out, uint32_t* cnt_clear,
-                                                         const uint32_t* __restrict__ poff,
-                                                         const uint2* __restrict__ preds, uint32_t* cstate,
-                                                         uint32_t* whead, uint32_t* __restrict__ wnext, DevInfo* info)
+                                  const uint32_t* __restrict__ cnt_in, uint32_t* __restrict__ wl_out,
+                                  uint32_t* __restrict__ cnt_out, uint32_t* __restrict__ cnt_clear,
+                                  const uint32_t* __restrict__ poff, const uint2* __restrict__ preds,
+                                  uint32_t* cstate, uint32_t* whead, uint32_t* __restrict__ wnext, DevInfo* info)
 {
-    jp_round(round, C, wl_in, cnt_in, wl_out, cnt_out, cnt_clear, poff, preds, cstate, whead, wnext, info);
+    __shared__ uint32_t s_exam[kJpCap];
+    __shared__ uint32_t s_done[kJpCap];
+    __shared__ uint32_t s_nexam, s_ndone, s_base;
+    const uint32_t nl = cnt_in[0], nx = cnt_in[1], m = nl + nx;
+    if (blockIdx.x == 0 && threadIdx.x < 2) cnt_clear[threadIdx.x] = 0u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr uint32_t nwarps = kJpThreads / 32;
+    for (uint32_t base = blockIdx.x * kJpThreads; base < m; base += gridDim.x * kJpThreads) {
+        if (threadIdx.x == 0) {
+            s_nexam = 0;
+            s_ndone = 0;
+        }
+        __syncthreads();
+        const uint32_t k = base + threadIdx.x;
+        if (k < nl) {
+            const uint32_t c = wl_in[k];
+            uint32_t h = whead[c];
+            whead[c] = kUncoloured;
+            while (h != kUncoloured) {
+                const uint32_t i = atomicAdd(&s_nexam, 1u);
+                if (i < kJpCap) {
+                    s_exam[i] = h;
+                } else {
+                    const uint32_t g = atomicAdd(&cnt_out[1], 1u);
+                    wl_out[C - 1u - g] = h;
+                }
+                h = wnext[h];
+            }
+        } else if (k < m) {
+            const uint32_t c = wl_in[C - 1u - (k - nl)];
+            const uint32_t i = atomicAdd(&s_nexam, 1u);
+            if (i < kJpCap) {
+                s_exam[i] = c;
+            } else {
+                const uint32_t g = atomicAdd(&cnt_out[1], 1u);
+                wl_out[C - 1u - g] = c;
+            }
+        }
+        __syncthreads();
+        const uint32_t ne = s_nexam < kJpCap ? s_nexam : kJpCap;
+        for (uint32_t e0 = 8 * warp; e0 < ne; e0 += 8 * nwarps) {
+            const uint32_t e = e0 + (lane >> 2);
+            const bool valid = e < ne;
+            const uint32_t c = valid ? s_exam[e] : 0u;
+            if (jp_examine(valid, c, round, lane, poff, preds, cstate, whead, wnext, info) && (lane & 3) == 0)
+                s_done[atomicAdd(&s_ndone, 1u)] = c;
+        }
+        __syncthreads();
+        const uint32_t nd = s_ndone;
+        if (threadIdx.x == 0) s_base = nd ? atomicAdd(&cnt_out[0], nd) : 0u;
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < nd; t += kJpThreads) wl_out[s_base + t] = s_done[t];
+        __syncthreads();   // the shared lists are refilled by the next tile
+    }
 }
 
 // All rounds in one cooperative launch (no host in the loop, so a step can

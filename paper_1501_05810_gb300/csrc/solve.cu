@@ -22,7 +22,7 @@
 #include <utility>
 #include <vector>
 
-#include "nbgs_internal.cuh"
+#include "mlp_tc.cuh"
 
 namespace nbgs {
 
@@ -57,6 +57,8 @@ template <class R> struct SolveArgs {
     const uint32_t* rlist;     // shared bodies grouped by the block that reduces them (local scheduling)
     const uint32_t* rstart;    // B + 1: each block's range of rlist
     const int2* dep_r;         // B: window of each block's reduction phase
+    int mlp;                   // the network's warm start of new contacts runs in the kernel's prologue
+    WarmArgs<R> W;             // its arguments
 };
 
 // Rotating per-scene residual slot of sweep k (three, so that clearing the
@@ -677,7 +679,7 @@ __device__ __forceinline__ R process_gathered(const SolveArgs<R>& A, int64_t b0,
     return rmax;
 }
 
-template <class R, bool Batch, bool Warp, bool Sub, int K = 1>
+template <class R, bool Batch, bool Warp, bool Sub, int K = 1, bool Mlp = false>
 __global__ void __launch_bounds__(kPersistThreads, (PersistMinBlocks<R, Batch, K>::value)) k_solve_persistent(SolveArgs<R> A)
 {
     extern __shared__ __align__(128) unsigned char stage_mem[];
@@ -695,6 +697,13 @@ __global__ void __launch_bounds__(kPersistThreads, (PersistMinBlocks<R, Batch, K
     const bool stage = K == 1 && !Warp && (A.flags & NBGS_SWEEP_TMA_STAGE) != 0;
     const bool local = (A.flags & NBGS_SWEEP_GLOBAL_SYNC) == 0;
     if (threadIdx.x == 0) mbar_init(&bar);
+    if constexpr (Mlp) {
+        // the network's warm start (tensor cores, 128 contacts per tile, the
+        // dynamic shared memory as its operand space), every impulse written
+        // before any block applies them
+        warm_tiles<R>(A.W, reinterpret_cast<TcMlpSmem*>(stage_mem));
+        if (!grid_barrier(A.info, nb)) return;
+    }
     gravity_pass<R>(A, gtid, gstride);
     if (!grid_barrier(A.info, nb)) return;
     if (Sub) {
@@ -1219,6 +1228,7 @@ static SolveArgs<R> make_args(nbgs_scene* s, int max_sweeps, double tol)
     A.rlist = s->rlist;
     A.rstart = s->rstart;
     A.dep_r = s->dep_r;
+    A.mlp = 0;
     return A;
 }
 
@@ -1236,8 +1246,9 @@ static int persist_occ(const void* fn)
     for (const auto& kv : known)
         if (kv.first == fn) return kv.second;
     int o = 0;
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<R>::BYTES);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, kPersistThreads, Stage<R>::BYTES);
+    const int dyn = (int)std::max<size_t>(Stage<R>::BYTES, sizeof(TcMlpSmem));   // TMA stage or network operands
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, kPersistThreads, dyn);
     cudaGetLastError();
     known.emplace_back(fn, o);
     return o;
@@ -1261,14 +1272,25 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
         if (s->timing) s->phase_launches[2] += 1;
     }
     if (s->prm.warm_start == NBGS_WARM_MLP) {
-        nbgs_status rc = run_mlp_prologue(s, 1, nullptr);
-        if (rc != NBGS_OK) return rc;
+        const bool warp_sched = (s->prm.sweep_flags & NBGS_SWEEP_WARP_SYNC) && !(s->prm.sweep_flags & NBGS_SWEEP_GLOBAL_SYNC);
+        if (s->prm.solver == NBGS_SOLVER_PERSISTENT && !s->composite && s->n_contacts > 0 && !A.sub && !warp_sched) {
+            // fused into the persistent kernel's prologue
+            if (!s->mlp_theta) return fail(s, NBGS_EINVAL, "MLP warm start: no network loaded (nbgs_mlp_load)");
+            A.mlp = 1;
+            A.W = warm_args<R>(s, 1, nullptr);
+            A.W.C = s->n_contacts;
+        } else {
+            nbgs_status rc = run_mlp_prologue(s, 1, nullptr);
+            if (rc != NBGS_OK) return rc;
+        }
     }
     if (s->prm.solver == NBGS_SOLVER_PERSISTENT) {
         // scheduling units: blocks, or warps with NBGS_SWEEP_WARP_SYNC
         const bool warp = (s->prm.sweep_flags & NBGS_SWEEP_WARP_SYNC) && !(s->prm.sweep_flags & NBGS_SWEEP_GLOBAL_SYNC);
         const int gk = gather_k(s->prm.sweep_flags);
-        const void* fn = s->batch ? (warp      ? (const void*)k_solve_persistent<R, true, true, false>
+        const void* fn = A.mlp ? (s->batch ? (const void*)k_solve_persistent<R, true, false, false, 1, true>
+                                           : (const void*)k_solve_persistent<R, false, false, false, 1, true>)
+                         : s->batch ? (warp      ? (const void*)k_solve_persistent<R, true, true, false>
                                      : gk == 2 ? (const void*)k_solve_persistent<R, true, false, false, 2>
                                                : (const void*)k_solve_persistent<R, true, false, false>)
                          : A.sub  ? (warp ? (const void*)k_solve_persistent<R, false, true, true>
@@ -1287,8 +1309,11 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
                 Cn, B, s->col_off, s->perm, s->info, s->cstart);
             if (s->timing) s->phase_launches[2] += 1;
             if (!(s->prm.sweep_flags & NBGS_SWEEP_GLOBAL_SYNC)) {
-                int* dmin = (int*)s->deg;      // colouring scratch, free during the solve
-                int* dmax = (int*)s->adj_off;
+                // scratch free during the solve: the colouring's body degrees and the
+                // detection's per-body counts (the body offsets adj_off stay: the
+                // network's features read them in the kernel's prologue)
+                int* dmin = (int*)s->deg;
+                int* dmax = (int*)s->row_cnt;
                 cudaMemsetAsync(dmin, 0x7F, s->n * sizeof(int), st);   // large positive
                 cudaMemsetAsync(dmax, 0x80, s->n * sizeof(int), st);   // large negative
                 k_body_blocks<<<grid_for(A.C, T, 8, s->num_sms), T, 0, st>>>(Cn, s->n, B, s->perm, s->cj1, s->cj2,
@@ -1314,10 +1339,9 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
         }
         void* args[] = {&A};
         if (s->timing) cudaEventRecord(s->ev[8], st);
-        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nblocks),
-                                                    dim3(s->coop_threads), args,
-                                                    (s->prm.sweep_flags & NBGS_SWEEP_TMA_STAGE) ? Stage<R>::BYTES : 0,
-                                                    st);
+        size_t dyn = (s->prm.sweep_flags & NBGS_SWEEP_TMA_STAGE) ? Stage<R>::BYTES : 0;
+        if (A.mlp) dyn = std::max(dyn, sizeof(TcMlpSmem));
+        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(s->coop_threads), args, dyn, st);
         if (s->timing) {
             cudaEventRecord(s->ev[9], st);
             s->phase_launches[2] += 1;
@@ -1510,16 +1534,17 @@ static void persist_occupancy(int threads, int& occ, int& occ_b)
     const void* batched[] = {(const void*)k_solve_persistent<R, true, false, false>,
                              (const void*)k_solve_persistent<R, true, true, false>};
     occ = occ_b = 1 << 30;
+    const int dyn = (int)std::max<size_t>(Stage<R>::BYTES, sizeof(TcMlpSmem));   // TMA stage or network operands
     for (const void* f : single) {
         int o = 0;
-        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<R>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f, threads, Stage<R>::BYTES);
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f, threads, dyn);
         occ = std::min(occ, o);
     }
     for (const void* f : batched) {
         int o = 0;
-        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, Stage<R>::BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f, threads, Stage<R>::BYTES);
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f, threads, dyn);
         occ_b = std::min(occ_b, o);
     }
 }

@@ -111,3 +111,30 @@ def test_features_match_reference(env, oracle_mod):
     assert len(F) == len(ref) > 100
     scale = np.maximum(1.0, np.abs(ref).max(0))
     assert np.all(np.abs(F - ref).max(0) <= 1e-5 * scale), np.abs(F - ref).max(0) / scale
+
+
+def test_fused_prologue_equals_prologue_kernel(env):
+    """The network's warm start inside the persistent sweep kernel (256
+    threads per block, its dynamic shared memory as operand space) gives the
+    same impulses, bit for bit, as the separate prologue kernel the per-colour
+    solver launches (128 threads per block): every row of a 128-row tile is
+    computed alone.  Zero sweeps: the impulses are the warm start itself."""
+    torch, nb, ws = env
+    rng = np.random.default_rng(9)
+    theta = (ws.init_params(5) + rng.normal(0, 0.05, ws.N_PARAMS)).astype(np.float32)
+    theta[ws.N_PARAMS - 3] = 2.0   # output bias of the normal impulse: positive predictions
+    sc = scenes.periodic_cloud(seed=12, per_side=9, dt=2e-2, vel_sigma=1.0, mu=0.4)
+    sc["params"]["warm_start"] = "mlp"
+    out = []
+    for solver in ("persistent", "per_colour"):
+        g = nb.Scene(sc, solver=solver)
+        g.mlp_load(theta)
+        g.detect_contacts()
+        g.colour_contacts()
+        g.solve_nbgs(0, 0.0)
+        out.append(g.get_contacts())
+        g.close()
+    assert len(out[0]["j1"]) > 300
+    assert np.array_equal(out[0]["j1"], out[1]["j1"]) and np.array_equal(out[0]["j2"], out[1]["j2"])
+    assert np.array_equal(out[0]["impulse"], out[1]["impulse"])
+    assert np.abs(out[0]["impulse"]).max() > 0.0   # the network acted (every contact is new)
