@@ -81,6 +81,39 @@ def loss_and_grad(theta, X, T):
     return L, flatten(grads)
 
 
+def loss_and_grad_rounded(theta, X, T, rnd=None):
+    """Loss and gradient as loss_and_grad computes them, except that every
+    operand of a matrix product is first passed through `rnd`: the inputs,
+    the weights, the hidden activations and the back-propagated deltas
+    (bfloat16 operands of tensor-core products, sums exact).  The biases, the
+    skip connection, the loss and the bias gradients use the unrounded
+    values, and the activations that feed the next layer are the rounded
+    ones.  rnd = None rounds to bfloat16; the identity gives
+    loss_and_grad."""
+    rnd = bf16_round if rnd is None else rnd
+    X = np.asarray(X, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    layers = unflatten(theta)
+    ops, zs = [rnd(X)], []
+    for li, (W, b) in enumerate(layers):
+        z = ops[-1] @ rnd(W).T + b
+        zs.append(z)
+        if li < len(layers) - 1:
+            ops.append(rnd(silu(z)))
+    Y = zs[-1] + X[:, 3:6]
+    n = len(Y)
+    dz = (Y - T) / n
+    grads = [None] * len(layers)
+    for li in range(len(layers) - 1, -1, -1):
+        W, _ = layers[li]
+        dr = rnd(dz)
+        grads[li] = (dr.T @ ops[li], dz.sum(0))
+        if li > 0:
+            dz = (dr @ rnd(W)) * silu_grad(zs[li - 1])
+    L = float(np.sum((Y - T) ** 2) / (2.0 * n))
+    return L, flatten(grads)
+
+
 def adam(theta, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     """One Adam step (Kingma & Ba 2015) with bias correction; returns new
     (theta, m, v)."""

@@ -2,7 +2,7 @@
 // predicts a contact's converged impulse from local features, evaluated on
 // the 5th-generation tensor cores (tcgen05: BF16 operands in shared memory,
 // FP32 accumulators in TMEM) before the sweeps, and its training kernels
-// (FP32 forward/backward, Adam).
+// (forward and backward on the tensor cores, Adam).
 //
 // Parameter layout (shared with every user of the network): for each layer
 // the weight matrix W (out x in, row-major) then the bias b (out); 9,347
@@ -68,23 +68,107 @@ __global__ void __launch_bounds__(kTcRows) k_mlp_infer_tc(const float* __restric
     tc_teardown(S);
 }
 
-// --- training: FP32 forward + backward on CUDA cores --------------------------
-constexpr int kTile = 32;        // samples per tile
-constexpr int kTrainThreads = 256;
+// --- training: forward and backward on the tensor cores (tcgen05) -----------
+// One CTA per SM, 128 threads, 128 samples per tile, thread r sample r.  All
+// products are tcgen05.mma with BF16 operands in shared memory (K-major, no
+// swizzle) and FP32 accumulators in TMEM:
+//   forward   Z_L   = A_{L-1} W_L^T        (M 128 samples, N out, K in)
+//   backward  B_L   = D_L W_L              (M 128 samples, N in, K out)
+//             dW_L += D_L^T A_{L-1}        (M out, padded to 128, N in, K 128 samples)
+// with D_4 = (Y - T) / n, D_{L-1} = B_L * silu'(Z_{L-1} + b_{L-1}).  The
+// pre-activations stay in TMEM for the backward pass; every A_L and D_L is
+// written twice, sample-major for the products that run over features and
+// feature-major for the weight gradients, which run over samples; the weight
+// gradients accumulate in TMEM over all tiles of the CTA and are added to
+// the global gradient once.  Bias gradients and the loss: FP32 sums of the
+// unrounded deltas on the CUDA cores.
+constexpr int kTrRows = 128;
+constexpr int kTrCols = 512;                       // TMEM columns (one CTA per SM)
+constexpr uint32_t kZ1 = 0, kZ2 = 64, kZ3 = 128, kZ4 = 192, kBk = 208;   // TMEM column offsets
+constexpr uint32_t kDW1 = 272, kDW2 = 288, kDW3 = 352, kDW4 = 416;
 
-struct TrainSmem {
-    float th[kNParams];
-    float gr[kNParams];
-    float x[kTile][kIn];
-    float z[3][kTile][kHid];     // pre-activations of the hidden layers
-    float d[2][kTile][kHid];     // back-propagated deltas
-    float y[kTile][4];           // output, then dL/dY
+struct TrainTcSmem {
+    alignas(128) __nv_bfloat16 a0[kTrRows * 16];           // inputs, sample-major (K 16)
+    alignas(128) __nv_bfloat16 a[3][kTrRows * kHid];       // hidden activations, sample-major
+    alignas(128) __nv_bfloat16 a0t[16 * kTrRows];          // inputs, feature-major (K 128 samples)
+    alignas(128) __nv_bfloat16 at[3][kHid * kTrRows];      // hidden activations, feature-major
+    alignas(128) __nv_bfloat16 d[kTrRows * kHid];          // deltas, sample-major (K = layer outputs)
+    alignas(128) __nv_bfloat16 dt[kTrRows * kTrRows];      // deltas, output-major, rows >= outputs unused
+    alignas(128) __nv_bfloat16 w1[kHid * 16];              // W_L (rows = outputs, K = inputs)
+    alignas(128) __nv_bfloat16 w2[kHid * kHid];
+    alignas(128) __nv_bfloat16 w3[kHid * kHid];
+    alignas(128) __nv_bfloat16 w4[16 * kHid];
+    alignas(128) __nv_bfloat16 w2t[kHid * kHid];           // W_L^T (rows = inputs, K = outputs)
+    alignas(128) __nv_bfloat16 w3t[kHid * kHid];
+    alignas(128) __nv_bfloat16 w4t[kHid * 16];
+    float b1[kHid], b2[kHid], b3[kHid], b4[16];
+    float gb[kHid * 3 + 16];                                // bias gradients b1, b2, b3, b4
+    alignas(8) uint64_t bar;
+    uint32_t tmem;
 };
 
-__device__ __forceinline__ float act(const TrainSmem& S, int layer, int s, int i)
+__device__ __forceinline__ void st_bf16(__nv_bfloat16* base, uint32_t byte_off, float v)
 {
-    // input of layer `layer` (0 = network input)
-    return layer == 0 ? S.x[s][i] : silu_f(S.z[layer - 1][s][i]);
+    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(base) + byte_off) = __float2bfloat16_rn(v);
+}
+
+// Row r (< 128) of a sample-major operand with K columns from 2K FP32 values
+// (K a multiple of 8), eight columns per 16-byte store.
+__device__ __forceinline__ void st_row(__nv_bfloat16* base, int r, int K, const float* v)
+{
+    for (int c0 = 0; c0 < K; c0 += 8) {
+        const uint4 q = make_uint4(pack_bf16(v[c0], v[c0 + 1]), pack_bf16(v[c0 + 2], v[c0 + 3]),
+                                   pack_bf16(v[c0 + 4], v[c0 + 5]), pack_bf16(v[c0 + 6], v[c0 + 7]));
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(base) + kmaj_off(r, c0, K)) = q;
+    }
+}
+
+// Column r of a feature-major operand (rows = features, K = 128 samples).
+__device__ __forceinline__ void st_col(__nv_bfloat16* base, int r, int nfeat, const float* v)
+{
+    for (int f = 0; f < nfeat; ++f) st_bf16(base, kmaj_off(f, r, kTrRows), v[f]);
+}
+
+// 64 FP32 columns of this thread's TMEM lane (row) starting at column col.
+__device__ __forceinline__ void tm_row64(uint32_t tmem, uint32_t col, float (&v)[64])
+{
+    const uint32_t lane = (uint32_t)(32 * (threadIdx.x >> 5)) << 16;
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+        float t[16];
+        tc_ld16(tmem + lane + col + (uint32_t)c0, t);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[c0 + k] = t[k];
+    }
+}
+
+// K/16 MMAs D(+)= A B^T of an M = 128 product; acc: accumulate into D from the first slice on.
+__device__ __forceinline__ void tr_mma(uint32_t d, const void* a, const void* b, int K, int N, bool acc)
+{
+    const uint32_t sa = smem_addr(a), sb = smem_addr(b);
+    const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+    for (int kk = 0; kk < K / 16; ++kk)
+        tc_mma(d, tc_desc(sa + 256u * kk, 128u, sbo), tc_desc(sb + 256u * kk, 128u, sbo), tc_idesc(kTrRows, N),
+               (acc || kk > 0) ? 1 : 0);
+}
+
+// Operands written by every thread -> barrier -> thread 0 issues (issue())
+// and commits -> all wait.  False when the wait gave up (same on all threads).
+template <class F>
+__device__ __forceinline__ bool tr_step(TrainTcSmem& S, uint32_t& phase, F issue)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        issue();
+        tc_commit(&S.bar);
+    }
+    const bool ok = tc_wait(&S.bar, phase & 1u);
+    phase += 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return __syncthreads_and(ok) != 0;
 }
 
 __device__ __forceinline__ float silu_grad_f(float z)
@@ -93,83 +177,164 @@ __device__ __forceinline__ float silu_grad_f(float z)
     return sg * (1.f + z * (1.f - sg));
 }
 
-__global__ void __launch_bounds__(kTrainThreads) k_mlp_grad(const float* __restrict__ theta, const float* __restrict__ X,
-                                                            const float* __restrict__ T, int64_t n,
-                                                            float* __restrict__ grad, double* __restrict__ loss)
+// Sum over the CTA's 128 rows of v[0..m) into gb[0..m) (shared memory).
+__device__ __forceinline__ void bias_grad(float* gb, const float* v, int m)
 {
-    extern __shared__ __align__(16) unsigned char train_smem[];
-    TrainSmem& S = *reinterpret_cast<TrainSmem*>(train_smem);
-    for (int k = threadIdx.x; k < kNParams; k += blockDim.x) {
-        S.th[k] = theta[k];
-        S.gr[k] = 0.f;
+    for (int o = 0; o < m; ++o) {
+        float x = v[o];
+        for (int k = 16; k > 0; k >>= 1) x += __shfl_xor_sync(0xffffffffu, x, k);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&gb[o], x);
     }
-    const int offW[4] = {kOffW1, kOffW2, kOffW3, kOffW4}, offB[4] = {kOffB1, kOffB2, kOffB3, kOffB4};
-    const int nin[4] = {kIn, kHid, kHid, kHid}, nout[4] = {kHid, kHid, kHid, kOutN};
+}
+
+__global__ void __launch_bounds__(kTrRows, 1) k_mlp_grad_tc(const float* __restrict__ th, const float* __restrict__ X,
+                                                            const float* __restrict__ T, int64_t n,
+                                                            float* __restrict__ grad, double* __restrict__ loss,
+                                                            unsigned* status)
+{
+    extern __shared__ __align__(1024) unsigned char tr_smem[];
+    TrainTcSmem& S = *reinterpret_cast<TrainTcSmem*>(tr_smem);
+    const int r = threadIdx.x;
+    // weights in both layouts, biases, bias gradients, the unused delta rows
+    for (int e = r; e < kHid * 16; e += kTrRows) {
+        const int o = e / 16, i = e % 16;
+        st_bf16(S.w1, kmaj_off(o, i, 16), i < kIn ? th[kOffW1 + o * kIn + i] : 0.f);
+    }
+    for (int e = r; e < kHid * kHid; e += kTrRows) {
+        const int o = e / kHid, i = e % kHid;
+        const float w2 = th[kOffW2 + o * kHid + i], w3 = th[kOffW3 + o * kHid + i];
+        st_bf16(S.w2, kmaj_off(o, i, kHid), w2);
+        st_bf16(S.w3, kmaj_off(o, i, kHid), w3);
+        st_bf16(S.w2t, kmaj_off(i, o, kHid), w2);
+        st_bf16(S.w3t, kmaj_off(i, o, kHid), w3);
+    }
+    for (int e = r; e < 16 * kHid; e += kTrRows) {
+        const int o = e / kHid, i = e % kHid;
+        const float w = o < kOutN ? th[kOffW4 + o * kHid + i] : 0.f;
+        st_bf16(S.w4, kmaj_off(o, i, kHid), w);
+        st_bf16(S.w4t, kmaj_off(i, o, 16), w);
+    }
+    for (int k = r; k < kHid; k += kTrRows) {
+        S.b1[k] = th[kOffB1 + k];
+        S.b2[k] = th[kOffB2 + k];
+        S.b3[k] = th[kOffB3 + k];
+    }
+    if (r < 16) S.b4[r] = r < kOutN ? th[kOffB4 + r] : 0.f;
+    for (int k = r; k < kHid * 3 + 16; k += kTrRows) S.gb[k] = 0.f;
+    for (int e = r; e < kTrRows * kTrRows; e += kTrRows) S.dt[e] = __float2bfloat16_rn(0.f);
+    if (r == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.bar)) : "memory");
+    if (r < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&S.tmem)),
+                     "r"(kTrCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tm = S.tmem;
     const float inv_n = 1.f / (float)n;
     double lsum = 0.0;
-    __syncthreads();
-    for (int64_t base = (int64_t)blockIdx.x * kTile; base < n; base += (int64_t)gridDim.x * kTile) {
-        const int m = (int)(n - base < kTile ? n - base : kTile);
-        for (int k = threadIdx.x; k < kTile * kIn; k += blockDim.x) {
-            const int s = k / kIn, i = k % kIn;
-            S.x[s][i] = s < m ? X[(base + s) * kIn + i] : 0.f;
-        }
-        __syncthreads();
-        // forward: z_L = W_L a_{L-1} + b_L
-        for (int L = 0; L < 4; ++L) {
-            for (int k = threadIdx.x; k < kTile * nout[L]; k += blockDim.x) {
-                const int s = k / nout[L], o = k % nout[L];
-                float z = S.th[offB[L] + o];
-                const float* w = S.th + offW[L] + o * nin[L];
-                for (int i = 0; i < nin[L]; ++i) z += w[i] * act(S, L, s, i);
-                if (L < 3) S.z[L][s][o] = z;
-                else S.y[s][o] = z + S.x[s][3 + o];   // skip connection: + previous impulse
+    uint32_t phase = 0;
+    bool ok = true, first = true;
+    __nv_bfloat16* const A[4] = {S.a0, S.a[0], S.a[1], S.a[2]};
+    for (int64_t base = (int64_t)blockIdx.x * kTrRows; base < n && ok; base += (int64_t)gridDim.x * kTrRows) {
+        const int64_t row = base + r;
+        const bool valid = row < n;
+        float x[16], t[kOutN];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) x[k] = (valid && k < kIn) ? X[row * kIn + k] : 0.f;
+#pragma unroll
+        for (int k = 0; k < kOutN; ++k) t[k] = valid ? T[row * kOutN + k] : 0.f;
+        st_row(S.a0, r, 16, x);
+        st_col(S.a0t, r, 16, x);
+        // forward
+        const uint32_t zc[4] = {kZ1, kZ2, kZ3, kZ4};
+        const __nv_bfloat16* W[4] = {S.w1, S.w2, S.w3, S.w4};
+        const float* bias[3] = {S.b1, S.b2, S.b3};
+        for (int L = 0; L < 4 && ok; ++L) {
+            const int K = L == 0 ? 16 : kHid, N = L == 3 ? 16 : kHid;
+            ok = tr_step(S, phase, [&] { tr_mma(tm + zc[L], A[L], W[L], K, N, false); });
+            if (!ok) break;
+            if (L < 3) {
+                float z[64];
+                tm_row64(tm, zc[L], z);
+#pragma unroll
+                for (int k = 0; k < 64; ++k) z[k] = silu_fast(z[k] + bias[L][k]);
+                st_row(A[L + 1], r, kHid, z);
+                st_col(S.at[L], r, kHid, z);
             }
-            __syncthreads();
         }
-        // loss and dL/dY = (Y - T) / n (rows beyond m contribute nothing)
-        for (int k = threadIdx.x; k < kTile * kOutN; k += blockDim.x) {
-            const int s = k / kOutN, o = k % kOutN;
-            float dy = 0.f;
-            if (s < m) {
-                const float e = S.y[s][o] - T[(base + s) * kOutN + o];
+        if (!ok) break;
+        // output, loss, D_4
+        {
+            float y[16];
+            tc_ld16(tm + ((uint32_t)(32 * (r >> 5)) << 16) + kZ4, y);
+            float d4[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) d4[k] = 0.f;
+#pragma unroll
+            for (int k = 0; k < kOutN; ++k) {
+                const float e = valid ? (y[k] + S.b4[k] + x[3 + k]) - t[k] : 0.f;
                 lsum += 0.5 * (double)e * (double)e;
-                dy = e * inv_n;
+                d4[k] = e * inv_n;
             }
-            S.y[s][o] = dy;
+            st_row(S.d, r, 16, d4);
+            st_col(S.dt, r, 16, d4);
+            bias_grad(S.gb + 3 * kHid, d4, kOutN);
         }
-        __syncthreads();
-        // backward, layer 4 .. 1; delta of layer L lives in y (L = 3) or d[L % 2]
-        for (int L = 3; L >= 0; --L) {
-            const int no = nout[L], ni = nin[L];
-            auto delta = [&](int s, int o) -> float { return L == 3 ? S.y[s][o] : S.d[L & 1][s][o]; };
-            // weight and bias gradients: each thread owns whole entries
-            for (int k = threadIdx.x; k < no * ni + no; k += blockDim.x) {
-                float acc = 0.f;
-                if (k < no * ni) {
-                    const int o = k / ni, i = k % ni;
-                    for (int s = 0; s < m; ++s) acc += delta(s, o) * act(S, L, s, i);
-                    S.gr[offW[L] + k] += acc;
-                } else {
-                    const int o = k - no * ni;
-                    for (int s = 0; s < m; ++s) acc += delta(s, o);
-                    S.gr[offB[L] + o] += acc;
-                }
-            }
-            if (L > 0) {   // delta of layer L - 1: (W_L^T delta_L) * silu'(z_{L-1})
-                for (int k = threadIdx.x; k < kTile * ni; k += blockDim.x) {
-                    const int s = k / ni, i = k % ni;
-                    float acc = 0.f;
-                    for (int o = 0; o < no; ++o) acc += S.th[offW[L] + o * ni + i] * delta(s, o);
-                    S.d[(L - 1) & 1][s][i] = acc * silu_grad_f(S.z[L - 1][s][i]);
-                }
-            }
-            __syncthreads();
+        // backward: layer 4 .. 1
+        const uint32_t dwc[4] = {kDW1, kDW2, kDW3, kDW4};
+        const __nv_bfloat16* WT[4] = {nullptr, S.w2t, S.w3t, S.w4t};
+        const __nv_bfloat16* AT[4] = {S.a0t, S.at[0], S.at[1], S.at[2]};
+        for (int L = 3; L >= 0 && ok; --L) {
+            const int Kout = L == 3 ? 16 : kHid, Nin = L == 0 ? 16 : kHid;
+            const bool acc = !first;
+            ok = tr_step(S, phase, [&] {
+                tr_mma(tm + dwc[L], S.dt, AT[L], kTrRows, Nin, acc);      // dW_L (+)= D_L^T A_{L-1}
+                if (L > 0) tr_mma(tm + kBk, S.d, WT[L], Kout, kHid, false);   // B_L = D_L W_L
+            });
+            if (!ok || L == 0) break;
+            float bk[64], z[64];
+            tm_row64(tm, kBk, bk);
+            tm_row64(tm, zc[L - 1], z);
+#pragma unroll
+            for (int k = 0; k < 64; ++k) bk[k] *= silu_grad_f(z[k] + bias[L - 1][k]);
+            st_row(S.d, r, kHid, bk);
+            st_col(S.dt, r, kHid, bk);
+            bias_grad(S.gb + (L - 1) * kHid, bk, kHid);
         }
+        first = false;
     }
-    for (int k = threadIdx.x; k < kNParams; k += blockDim.x) atomicAdd(&grad[k], S.gr[k]);
-    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, lsum / (double)n);
+    if (!ok && r == 0) atomicOr(status, 1u);
+    // weight gradients: rows (outputs) of the TMEM accumulators, lanes 0..63
+    // (warps 0 and 1; the rows of warps 2 and 3 are padding)
+    if (ok && !first && r < kHid) {
+        float v[64];
+        tm_row64(tm, kDW2, v);
+        for (int i = 0; i < kHid; ++i) atomicAdd(&grad[kOffW2 + r * kHid + i], v[i]);
+        tm_row64(tm, kDW3, v);
+        for (int i = 0; i < kHid; ++i) atomicAdd(&grad[kOffW3 + r * kHid + i], v[i]);
+        tm_row64(tm, kDW4, v);
+        if (r < kOutN)
+            for (int i = 0; i < kHid; ++i) atomicAdd(&grad[kOffW4 + r * kHid + i], v[i]);
+        float w[16];
+        tc_ld16(tm + ((uint32_t)(32 * (r >> 5)) << 16) + kDW1, w);
+        for (int i = 0; i < kIn; ++i) atomicAdd(&grad[kOffW1 + r * kIn + i], w[i]);
+    }
+    __syncthreads();
+    if (ok && !first) {
+        const int boff[4] = {kOffB1, kOffB2, kOffB3, kOffB4};
+        for (int k = r; k < kHid * 3 + kOutN; k += kTrRows) atomicAdd(&grad[boff[k / kHid] + k % kHid], S.gb[k]);
+    }
+    for (int k = 16; k > 0; k >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, k);
+    if ((r & 31) == 0 && lsum != 0.0) atomicAdd(loss, lsum / (double)n);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (r < 32) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTrCols) : "memory");
+    }
 }
 
 __global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
@@ -236,15 +401,17 @@ nbgs_status nbgs_mlp_grad(const float* theta, const float* X, const float* T, in
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    static_assert(sizeof(TrainSmem) < 227 * 1024, "training tile too large");
-    if (cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem)) !=
-        cudaSuccess)
+    static_assert(sizeof(TrainTcSmem) < 227 * 1024, "training tile too large");
+    const int smem = (int)sizeof(TrainTcSmem);
+    if (cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return NBGS_ECUDA;
+    unsigned* status = nullptr;
+    if (cudaGetSymbolAddress((void**)&status, g_mlp_status) != cudaSuccess) return NBGS_ECUDA;
     cudaMemsetAsync(grad, 0, kNParams * sizeof(float), st);
     cudaMemsetAsync(loss, 0, sizeof(double), st);
-    const int64_t tiles = (n + kTile - 1) / kTile;
-    const int blocks = (int)std::min<int64_t>(tiles, (int64_t)sms);
-    k_mlp_grad<<<blocks, kTrainThreads, sizeof(TrainSmem), st>>>(theta, X, T, n, grad, loss);
+    const int64_t tiles = (n + kTrRows - 1) / kTrRows;
+    const int blocks = (int)std::min<int64_t>(tiles, (int64_t)sms);   // one CTA per SM (all of its TMEM)
+    k_mlp_grad_tc<<<blocks, kTrRows, smem, st>>>(theta, X, T, n, grad, loss, status);
     return cudaGetLastError() == cudaSuccess ? NBGS_OK : NBGS_ECUDA;
 }
 

@@ -1,6 +1,7 @@
 """Learned warm start on the GPU against the FP64 references in oracle/:
-tensor-core inference (tcgen05, BF16 operands, FP32 accumulation), FP32 training
-gradients and Adam, and the per-contact feature map."""
+tensor-core inference and training (tcgen05, BF16 operands, FP32 accumulation in
+TMEM), Adam, the per-contact feature map, and the network inside the sweep
+kernel's prologue."""
 import math
 
 import numpy as np
@@ -48,11 +49,18 @@ def test_tensor_core_inference_matches_reference(env):
         assert np.abs(Y - full).max() <= 6e-2 * scale     # BF16 versus exact
 
 
-def test_training_gradient_matches_reference(env):
+@pytest.mark.parametrize("n", [1000, 40000])
+def test_training_gradient_matches_reference(env, n):
+    """Forward and backward on the tensor cores (BF16 operands, FP32
+    accumulation in TMEM) against the FP64 reference with the same operand
+    roundings (oracle.mlp.loss_and_grad_rounded): the loss to 1e-5, the
+    gradient to 5e-4 of its largest entry, direction to 1e-8.  n = 1000: one
+    ragged 128-sample tile per CTA; n = 40,000: two or three tiles per CTA,
+    so the weight gradients accumulate in TMEM across tiles.  And within
+    BF16 precision of the exact gradient."""
     torch, nb, ws = env
     rng = np.random.default_rng(1)
-    theta = ws.init_params(4)
-    n = 1000                                             # 31 full tiles of 32 and a ragged one
+    theta = ws.init_params(4) + rng.normal(0, 0.02, ws.N_PARAMS).astype(np.float32)
     X = rng.normal(size=(n, 12)).astype(np.float32)
     T = rng.normal(size=(n, 3)).astype(np.float32)
     dev = torch.device("cuda:0")
@@ -61,11 +69,17 @@ def test_training_gradient_matches_reference(env):
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
     assert nb.library().nbgs_mlp_grad(th.data_ptr(), Xd.data_ptr(), Td.data_ptr(), n, g.data_ptr(), loss.data_ptr(),
                                       torch.cuda.current_stream().cuda_stream) == nb.NBGS_OK
-    L, G = omlp.loss_and_grad(theta.astype(np.float64), X.astype(np.float64), T.astype(np.float64))
-    assert abs(loss.item() - L) <= 1e-5 * L
-    gg = g.cpu().numpy()
-    assert np.abs(gg - G).max() <= 2e-4 * np.abs(G).max()
-    assert np.dot(gg, G) / (np.linalg.norm(gg) * np.linalg.norm(G)) > 1 - 1e-6
+    torch.cuda.synchronize()
+    th64, X64, T64 = theta.astype(np.float64), X.astype(np.float64), T.astype(np.float64)
+    L, G = omlp.loss_and_grad_rounded(th64, X64, T64)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert abs(loss.item() - L) <= 1e-5 * L, (loss.item(), L)
+    err = np.abs(gg - G).max() / np.abs(G).max()
+    cos = np.dot(gg, G) / (np.linalg.norm(gg) * np.linalg.norm(G))
+    print(f"n={n}: gradient vs rounded reference: max err {err:.2e} of the largest, 1 - cos {1 - cos:.2e}")
+    assert err <= 5e-4 and cos > 1 - 1e-8   # measured on a GB300: 4.7e-5 / 1.3e-10 (n = 1000)
+    Le, Ge = omlp.loss_and_grad(th64, X64, T64)
+    assert np.dot(gg, Ge) / (np.linalg.norm(gg) * np.linalg.norm(Ge)) > 1 - 1e-3
 
 
 def test_adam_step_matches_reference(env):

@@ -204,3 +204,31 @@ def test_features_treat_a_tiny_tangential_speed_as_none():
     for speed, want in ((1e-10, (1.0, 0.0)), (3e-9, (-1.0, 0.0))):
         F = _features(c, [[speed, 0.0, 0.0]], np.zeros((1, 3)), [0.5], [0.5], [5.0], params, 1e3)
         assert tuple(F[0, 12:14]) == want, (speed, F[0, 12:14])
+
+
+def test_rounded_gradient_reference():
+    """The reference of the tensor-core training (operands of the products
+    rounded, sums exact): with the identity as rounding it is the exact
+    gradient (so it has every term of the chain rule and no transposed
+    operand); with bfloat16 it stays within bfloat16's relative precision of
+    the exact gradient; each rounding point matters (rounding only the
+    deltas, or only the weights, moves the result)."""
+    rng = np.random.default_rng(3)
+    theta = mlp.init(2) + rng.normal(0, 0.05, mlp.N_PARAMS)
+    X = rng.normal(size=(257, 12))
+    T = rng.normal(size=(257, 3))
+    L, g = mlp.loss_and_grad(theta, X, T)
+    Li, gi = mlp.loss_and_grad_rounded(theta, X, T, rnd=lambda a: a)
+    assert abs(Li - L) <= 1e-14 * L and np.abs(gi - g).max() <= 1e-12 * np.abs(g).max()
+    Lb, gb = mlp.loss_and_grad_rounded(theta, X, T)
+    cos = np.dot(gb, g) / (np.linalg.norm(gb) * np.linalg.norm(g))
+    assert abs(Lb - L) <= 2e-2 * L and cos > 1 - 1e-3 and np.abs(gb - g).max() > 1e-6 * np.abs(g).max()
+    # a product operand that escapes the rounding changes the result
+    calls = []
+
+    def spy(a):
+        calls.append(np.shape(a))
+        return mlp.bf16_round(a)
+    mlp.loss_and_grad_rounded(theta, X, T, rnd=spy)
+    # forward: X, 4 weights, 3 activations; backward: 4 deltas, 3 weights
+    assert len(calls) == 1 + 4 + 3 + 4 + 3
