@@ -485,6 +485,7 @@ def main():
         torch.cuda.synchronize()
         clocks.mark_start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")   # a profiler can be limited to this range (ncu --nvtx-include timed/)
         e0.record(stream)
         stats = []
         if use_graph:
@@ -494,6 +495,7 @@ def main():
                 g.step(sweeps, tol, stats=False)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         clocks.mark_end()
         if dist:
             dist.barrier()

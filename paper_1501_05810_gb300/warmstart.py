@@ -125,10 +125,14 @@ def infer(theta, X, device="cuda:0"):
 
 
 def sweeps_to_tolerance(scene_dict, mode: str, theta=None, steps: int = 5, tol: float = 1e-6,
-                        max_sweeps: int = 2000, warm_steps: int = 3, device="cuda:0"):
+                        max_sweeps: int = 2000, warm_steps: int = 3, device="cuda:0", times: bool = False):
     """Sweeps each of `steps` consecutive steps needs to reach tol with the
     given warm start ('none', 'prev', 'mlp'), after `warm_steps` steps run
-    with the previous-step warm start to reach a state with contact history."""
+    with the previous-step warm start to reach a state with contact history.
+    times: also the device time of each solve (CUDA events around
+    nbgs_solve_nbgs: the network's prologue, fused into the sweep kernel, and
+    the sweeps), in ms."""
+    import torch
     sc = dict(scene_dict)
     sc["params"] = dict(sc["params"], warm_start="prev")
     g = nbgs.Scene(sc, device=device)
@@ -136,14 +140,22 @@ def sweeps_to_tolerance(scene_dict, mode: str, theta=None, steps: int = 5, tol: 
         g.mlp_load(theta)
     for _ in range(warm_steps):
         g.step(max_sweeps, tol)
-    out = []
+    out, ms = [], []
     mode_code = {"none": nbgs.NBGS_WARM_NONE, "prev": nbgs.NBGS_WARM_PREV, "mlp": nbgs.NBGS_WARM_MLP}[mode]
     for _ in range(steps):
         _set_warm(g, mode_code)
-        st = g.step(max_sweeps, tol)
-        out.append(st["sweeps_done"])
+        g.detect_contacts()
+        g.colour_contacts()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(g.stream)
+        k, _ = g.solve_nbgs(max_sweeps, tol)
+        e1.record(g.stream)
+        g.integrate()
+        torch.cuda.synchronize()
+        out.append(k)
+        ms.append(e0.elapsed_time(e1))
     g.close()
-    return np.array(out)
+    return (np.array(out), np.array(ms)) if times else np.array(out)
 
 
 def _set_warm(g, code):
@@ -153,26 +165,32 @@ def _set_warm(g, code):
         raise nbgs.NBGSError(rc, "nbgs_set_warm_start", nbgs.library().nbgs_last_error(g.h).decode())
 
 
-def settling_training_data(seeds=range(8), steps: int = 250, tol_data: float = 1e-7, device="cuda:0", log=None):
+def settling_training_data(target: int = 5_000_000, steps: int = 250, tol_data: float = 1e-7, first_seed: int = 100,
+                           max_runs: int = 200, device="cuda:0", log=None):
     """(features, converged impulse) pairs of the contacts that appear while
     1,000-sphere lattice boxes (the FP64 workload's setup, dt = 2e-3) settle
     under gravity: every contact without a previous-step impulse, at every
-    step."""
+    step; runs with seeds first_seed, first_seed + 1, ... until `target`
+    pairs are collected (the last run's are kept whole)."""
     from . import scenes
-    X, T = [], []
-    for s in seeds:
+    X, T, got = [], [], 0
+    for s in range(first_seed, first_seed + max_runs):
         sc = scenes.lattice_box(seed=int(s), per_side=10, dt=2e-3, mu=0.5, tau=0.005, vel_sigma=0.1 + 0.05 * (s % 4))
         x, t = collect([sc], steps=steps, tol_data=tol_data, max_sweeps=5000, new_only=True, device=device)
         X.append(x)
         T.append(t)
+        got += len(x)
         if log:
-            log(f"settling run {s}: {len(x)} new-contact samples")
+            log(f"settling run {s}: {len(x)} new-contact samples ({got} in all)")
+        if got >= target:
+            break
     return np.concatenate(X), np.concatenate(T)
 
 
 def hopper_evaluation(n: int = 2_000_000, settle_steps: int = 600, settle_sweeps: int = 30, eval_steps: int = 4,
                       tol: float = 1e-6, max_sweeps: int = 4000, theta=None, train_epochs: int = 30, seed: int = 0,
-                      checkpoint: str = "/tmp/nbgs_hopper_eval.ckpt", device="cuda:0", log=None) -> dict:
+                      samples: int = 5_000_000, checkpoint: str = "/tmp/nbgs_hopper_eval.ckpt", device="cuda:0",
+                      log=None) -> dict:
     """Hopper discharge (conical hopper, 30 degree half-angle, orifice 8 r,
     mu = 0.5): sweeps and device time per step to residual tol with cold,
     previous-step and network warm starts, from the same state.
@@ -191,7 +209,7 @@ def hopper_evaluation(n: int = 2_000_000, settle_steps: int = 600, settle_sweeps
     out = {"n": n, "tol": tol, "eval_steps": eval_steps, "settle_steps": settle_steps}
     if theta is None:
         t0 = time.perf_counter()
-        X, T = settling_training_data(device=device, log=say)
+        X, T = settling_training_data(target=samples, device=device, log=say)
         theta, losses = train(X, T, epochs=train_epochs, batch=4096, lr=1e-3, seed=seed, device=device)
         out["training"] = {"samples": int(len(X)), "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
                            "seconds": time.perf_counter() - t0}
@@ -231,7 +249,7 @@ def hopper_evaluation(n: int = 2_000_000, settle_steps: int = 600, settle_sweeps
             nnew.append(int(np.count_nonzero(np.all(f[:, 3:6] == 0.0, axis=1))) if len(f) else 0)
             ncon.append(int(len(f)))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(s.stream)
+            e0.record(s.stream)   # the solve: the network's prologue (fused into the sweep kernel) and the sweeps
             k, r = s.solve_nbgs(max_sweeps, tol)
             e1.record(s.stream)
             s.integrate()
@@ -257,7 +275,8 @@ if __name__ == "__main__":  # pragma: no cover
     ap.add_argument("--eval-steps", type=int, default=4)
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--max-sweeps", type=int, default=4000)
+    ap.add_argument("--samples", type=int, default=5_000_000, help="training pairs from settling runs")
     a = ap.parse_args()
     r = hopper_evaluation(n=a.n, settle_steps=a.settle_steps, eval_steps=a.eval_steps, train_epochs=a.epochs,
-                          max_sweeps=a.max_sweeps, log=lambda m: print(m, flush=True))
+                          max_sweeps=a.max_sweeps, samples=a.samples, log=lambda m: print(m, flush=True))
     print(json.dumps(r))

@@ -4,10 +4,11 @@ A network is trained on the GPU (libnbgs forward/backward/Adam kernels) on
 the contacts that appear in a dense granular gas (no previous impulse), then
 used as the warm start of held-out gases.  Checks: its predictions of the
 converged impulses of new contacts are much closer than the zero start of
-plain NBGS; the solves need no more sweeps in total than cold starts; and
-in a static packing, where every contact keeps its previous impulse, the
-network changes nothing.  (On these gases the sweep count to the max-norm
-tolerance is not reduced; the test bounds it and prints the totals.)"""
+plain NBGS; sweeps and solve time against cold and previous-step starts, as
+measured; and in a static packing, where every contact keeps its previous impulse, the
+network changes nothing.  On these gases the sweep count to the max-norm
+tolerance is not reduced by any start; the solve-time test states that
+measured outcome."""
 import numpy as np
 import pytest
 
@@ -42,17 +43,30 @@ def test_network_predicts_new_contacts(trained):
     assert err_net < 0.5 * err_zero
 
 
-def test_sweeps_against_cold_and_previous_start(trained):
+def test_solve_time_against_cold_and_previous_start(trained):
+    """What the network gains in the solve itself, measured on held-out gases:
+    sweeps to residual 1e-6 and the device time of the solve (the network's
+    prologue, fused into the sweep kernel, included) with cold,
+    previous-step and network starts.  The outcome measured on a GB300: the
+    three starts need the same sweeps to within a few percent (534, 536, 536
+    over 24 solves: the count is set by the slowest cluster of contacts under
+    the max-norm criterion, not by the new contacts the network predicts), so
+    the network's nine times better starting impulses buy no solve time; its
+    prologue costs a few percent of a solve.  The test holds that outcome:
+    sweeps within 5 % of the cold start's, solve time within 15 % of the
+    previous-step start's."""
     ws, theta = trained
     held = [scenes.periodic_cloud(seed=100 + s, per_side=8, dt=1e-2, vel_sigma=1.0, mu=0.3) for s in range(3)]
-    tot = {}
+    tot, ms = {}, {}
     for mode in ("none", "prev", "mlp"):
-        tot[mode] = int(sum(ws.sweeps_to_tolerance(sc, mode, theta, steps=8, tol=1e-6, warm_steps=3).sum()
-                            for sc in held))
-    print("total sweeps to 1e-6 over 24 solves:", tot)
-    # the sweep count is set by the slowest cluster (max-norm criterion);
-    # better starts for new contacts must at least not slow the solve down
-    assert tot["mlp"] <= 1.02 * tot["none"]
+        k, t = zip(*(ws.sweeps_to_tolerance(sc, mode, theta, steps=8, tol=1e-6, warm_steps=3, times=True)
+                     for sc in held))
+        tot[mode] = int(sum(x.sum() for x in k))
+        ms[mode] = float(sum(x.sum() for x in t))
+    print("sweeps to 1e-6 over 24 solves:", tot, "solve ms:", {m: round(v, 2) for m, v in ms.items()})
+    assert abs(tot["mlp"] - tot["none"]) <= 0.05 * tot["none"]
+    assert abs(tot["prev"] - tot["none"]) <= 0.05 * tot["none"]
+    assert ms["mlp"] <= 1.15 * ms["prev"]
 
 
 def test_static_packing_keeps_previous_impulses(trained):
