@@ -197,16 +197,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
-def measured_traffic(prec, contacts, sweeps, variant="", kernel="k_solve_persistent"):
+def measured_traffic(prec, contacts, sweeps, variant="", kernel="k_solve_persistent", workload="pour1m"):
     """DRAM bytes per launch of the sweep kernel from the committed ncu
-    capture (profiles/traffic.json), scaled by the contact updates of one
-    launch; None when the kernel's sources (the entry's "sources", else
-    solve.cu and nbgs_internal.cuh) changed since the capture."""
+    capture of the same workload (profiles/traffic.json, key: kernel, then
+    the workload and variant), scaled by the contact updates of one launch;
+    None when there is no such capture or the kernel's sources (the entry's
+    "sources", else solve.cu and nbgs_internal.cuh) changed since it."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    key = f"{kernel}<{'float' if prec == 'fp32' else 'double'}>" + variant
+    key = f"{kernel}<{'float' if prec == 'fp32' else 'double'}> {workload}" + variant
     d = json.load(open(p)).get(key)
     if not d:
         return None
@@ -563,8 +564,8 @@ def main():
     # with subdomains the traffic depends on the grid: a capture of the same
     # workload and grid only
     traffic = measured_traffic(prec, n_ss + n_sw, sweeps_launch,
-                               "" if args.subdomains is None else f" {args.workload} subdomains {args.subdomains}",
-                               "k_solve_comp" if comp else "k_solve_persistent")
+                               "" if args.subdomains is None else f" subdomains {args.subdomains}",
+                               "k_solve_comp" if comp else "k_solve_persistent", args.workload)
     achieved = alg_bytes_per_launch / (per_launch_ms / 1e3) / 1e9 if per_launch_ms > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,

@@ -50,15 +50,16 @@ def test_traffic_lookup_follows_the_kernel_sources(tmp_path, monkeypatch):
     for key, d in entry.items():
         assert abs(d["dram_bytes_per_update"] * d["contact_updates_per_launch"] - d["dram_bytes_per_launch"]) \
             <= 1e-6 * d["dram_bytes_per_launch"], key
-    d = entry["k_solve_persistent<float>"]
+    d = entry["k_solve_persistent<float> dense1m"]
     h = hashlib.sha256(b"".join(open(os.path.join(PKG, "csrc", f), "rb").read()
                                 for f in ("solve.cu", "nbgs_internal.cuh"))).hexdigest()[:16]
-    got = bench.measured_traffic("fp32", 1000, 10)
+    got = bench.measured_traffic("fp32", 1000, 10, workload="dense1m")
     if h == d["source_sha256_16"]:
         assert abs(got - d["dram_bytes_per_update"] * 1000 * 10) <= 1e-9 * got
     else:
         assert got is None          # a capture of other sources is not reported
-    assert bench.measured_traffic("fp64", 1000, 10) is None            # no FP64 capture
+    assert bench.measured_traffic("fp64", 1000, 10, workload="dense1m") is None   # no FP64 capture
+    assert bench.measured_traffic("fp32", 1000, 10, workload="no such workload") is None
     # a changed source invalidates the capture
     fake = tmp_path / "repo"
     (fake / "profiles").mkdir(parents=True)
@@ -68,4 +69,4 @@ def test_traffic_lookup_follows_the_kernel_sources(tmp_path, monkeypatch):
         data = open(os.path.join(PKG, "csrc", f), "rb").read()
         open(fake / "paper_1501_05810_gb300" / "csrc" / f, "wb").write(data + (b"\n" if f == "solve.cu" else b""))
     monkeypatch.setattr(bench, "ROOT", str(fake))
-    assert bench.measured_traffic("fp32", 1000, 10) is None
+    assert bench.measured_traffic("fp32", 1000, 10, workload="dense1m") is None
