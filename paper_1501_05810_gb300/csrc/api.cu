@@ -166,7 +166,7 @@ static nbgs_status check_device_errors(nbgs_scene* s)
     if (e & kErrNaN) return fail(s, NBGS_ENAN, "NaN or Inf in the body state");
     if (e & kErrContacts) return fail(s, NBGS_ECAPACITY, "a graph step found more contacts than its buffers hold");
     if (e & kErrPreds) return fail(s, NBGS_ECAPACITY, "a graph step's colouring outgrew its predecessor lists");
-    if (e & kErrColours) return fail(s, NBGS_ECAPACITY, "more than 128 colours needed");
+    if (e & kErrColours) return fail(s, NBGS_ECAPACITY, "more than 256 colours needed");
     return NBGS_OK;
 }
 

@@ -232,7 +232,7 @@ __device__ bool jp_examine(bool valid, uint32_t c, uint32_t round, int lane, con
         np = poff[c + 1] - p0;
     }
     const uint32_t maxnp = __reduce_max_sync(0xffffffffu, np);
-    uint32_t used[4] = {0u, 0u, 0u, 0u};
+    uint32_t used[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};   // colours taken by predecessors (kMaxColours bits)
     uint32_t wph = ~0u, wd = kUncoloured;   // weakest uncoloured predecessor seen by this lane
     for (uint32_t w0 = 0; w0 < maxnp; w0 += 16) {
         uint2 e[4];
@@ -255,7 +255,7 @@ __device__ bool jp_examine(bool valid, uint32_t c, uint32_t round, int lane, con
             } else {
                 const uint32_t col = sd[k] & 0xFFu;
 #pragma unroll
-                for (int w = 0; w < 4; ++w)
+                for (int w = 0; w < 8; ++w)
                     if ((col >> 5) == (uint32_t)w) used[w] |= 1u << (col & 31u);
             }
         }
@@ -270,7 +270,7 @@ __device__ bool jp_examine(bool valid, uint32_t c, uint32_t round, int lane, con
             wd = wd2;
         }
 #pragma unroll
-        for (int w = 0; w < 4; ++w) used[w] |= __shfl_xor_sync(0xffffffffu, used[w], o);
+        for (int w = 0; w < 8; ++w) used[w] |= __shfl_xor_sync(0xffffffffu, used[w], o);
     }
     if (!valid) return false;
     if (wd != kUncoloured) {
@@ -280,7 +280,7 @@ __device__ bool jp_examine(bool valid, uint32_t c, uint32_t round, int lane, con
     if (gl == 0) {
         uint32_t col = kMaxColours;
 #pragma unroll
-        for (int w = 3; w >= 0; --w)
+        for (int w = 7; w >= 0; --w)
             if (~used[w]) col = 32u * w + (__ffs(~used[w]) - 1);
         if (col >= kMaxColours) {
             atomicOr(&info->err, kErrColours);
@@ -499,8 +499,9 @@ __global__ void k_colour_keys(DCount Cc, const uint32_t* __restrict__ cstate, ui
     __syncthreads();
     uint32_t cmax = 0;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t col = cstate[c] & 0xFFu;
-        if (col >= (uint32_t)kMaxColours) {   // uncoloured or out of range: report, keep indices in bounds
+        const uint32_t st = cstate[c];
+        uint32_t col = st & 0xFFu;
+        if (st == kUncoloured || col >= (uint32_t)kMaxColours) {   // uncoloured or out of range: report, keep indices in bounds
             atomicOr(&info->err, kErrColours);
             col = kMaxColours - 1;
         }

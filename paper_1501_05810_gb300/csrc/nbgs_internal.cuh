@@ -22,7 +22,7 @@
 namespace nbgs {
 
 constexpr int kMaxPlanes = 16;
-constexpr int kMaxColours = 128;       // colour bitmask of two u64 words
+constexpr int kMaxColours = 256;       // a colour is 8 bits of the colouring state
 constexpr int kCandCap = 32;           // sphere candidates per body with j > i
 constexpr uint32_t kUncoloured = 0xFFFFFFFFu;
 constexpr int kMaxSweepsHist = 4096;   // residual slots: history, 3 rotating, 4 final
