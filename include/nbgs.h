@@ -417,6 +417,20 @@ nbgs_status nbgs_get_subdomains(nbgs_scene* scene, int64_t cap, uint32_t* out, i
 nbgs_status nbgs_save_state(nbgs_scene* scene, const char* path);
 nbgs_status nbgs_load_state(nbgs_scene* scene, const char* path);
 
+/* The one-contact problem of Sect. 3 (eq. nonpenetration and eq. coulomb
+ * for one contact, the others' reactions frozen) with a full symmetric
+ * Delassus block, solved on the GPU for n independent contacts by the same
+ * solver the composite sweep relaxes every contact with: separation, then
+ * sticking p = -W^-1 b if inside the friction cone, else sliding on the
+ * cone with the friction direction against the tangential velocity, the
+ * least-energy slide where several qualify.  Device pointers: W6 n x 6
+ * (W_nn, W_tt, W_oo, W_nt, W_no, W_to in the contact frame), mu n, b n x 3
+ * (the contact's velocity without its own reaction, plus the gap term), p
+ * n x 3 out (impulse in the contact frame).  Enqueued on `stream`.
+ * NBGS_EINVAL on bad arguments, NBGS_ECUDA if the launch fails. */
+nbgs_status nbgs_one_contact(int64_t n, const double* W6, const double* mu, const double* b, double* p,
+                             void* stream);
+
 /* R_k of every sweep of the last solve.  Synchronises. */
 nbgs_status nbgs_residual_history(nbgs_scene* scene, double* out, int32_t cap, int32_t* n_out);
 

@@ -970,3 +970,36 @@ nbgs_status run_comp_set_bodies(nbgs_scene* s, const double* pos, const double* 
 }
 
 }  // namespace nbgs
+
+namespace nbgs {
+
+// Independent one-contact problems with the solver of the composite sweep.
+__global__ void k_one_contact(int64_t n, const double* __restrict__ W6, const double* __restrict__ mu,
+                              const double* __restrict__ b, double* __restrict__ p)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double* w = W6 + 6 * i;
+        const Sym3<double> W{w[0], w[1], w[2], w[3], w[4], w[5]};
+        const double bb[3] = {b[3 * i], b[3 * i + 1], b[3 * i + 2]};
+        double y[3];
+        one_contact_general<double>(W, mu[i], bb, y);
+        p[3 * i] = y[0];
+        p[3 * i + 1] = y[1];
+        p[3 * i + 2] = y[2];
+    }
+}
+
+}  // namespace nbgs
+
+extern "C" nbgs_status nbgs_one_contact(int64_t n, const double* W6, const double* mu, const double* b, double* p,
+                                        void* stream)
+{
+    using namespace nbgs;
+    if (n < 0 || (n > 0 && (!W6 || !mu || !b || !p))) return NBGS_EINVAL;
+    if (n == 0) return NBGS_OK;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_one_contact<<<grid_for(n, 128, 8, sms), 128, 0, (cudaStream_t)stream>>>(n, W6, mu, b, p);
+    return cudaGetLastError() == cudaSuccess ? NBGS_OK : NBGS_ECUDA;
+}
