@@ -579,9 +579,8 @@ __device__ __forceinline__ bool wait_deps_warp(const int* prog, int2 win, int g,
     for (int off = win.x + lane; off <= win.y && ok; off += 32) {
         if (off == 0) continue;
         const int b = ((self + off) % nv + nv) % nv;
-        volatile const int* pb = prog + b;
         const long long t0 = clock64();
-        while (*pb < g - 1) {
+        while (ld_acquire(prog + b) < g - 1) {
             if (((volatile uint32_t*)&info->err)[0] & kErrTimeout) {
                 ok = 0;
                 break;
@@ -593,7 +592,6 @@ __device__ __forceinline__ bool wait_deps_warp(const int* prog, int2 win, int g,
             }
         }
     }
-    __threadfence();
     return __all_sync(0xffffffffu, ok) != 0;
 }
 
