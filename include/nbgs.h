@@ -431,6 +431,17 @@ nbgs_status nbgs_load_state(nbgs_scene* scene, const char* path);
 nbgs_status nbgs_one_contact(int64_t n, const double* W6, const double* mu, const double* b, double* p,
                              void* stream);
 
+/* Sphere contact geometry of Sect. 2 eq. (contactpos) as the detection
+ * computes it, for n centre differences x_i - x_j: the distance
+ * d = |x_i - x_j| (the square root of the squares summed in x, y, z order)
+ * and the unit normal n = (x_i - x_j) / d, every operation rounded to
+ * nearest (the quotients through one correctly rounded reciprocal of d and
+ * a fused correction step, which gives the correctly rounded quotient);
+ * coincident centres give n = (0, 0, 1).  Device pointers: dvec n x 3 in,
+ * out n x 4 (n_x, n_y, n_z, d).  Enqueued on `stream`.  NBGS_EINVAL on bad
+ * arguments, NBGS_ECUDA if the launch fails. */
+nbgs_status nbgs_pair_normals(int64_t n, const double* dvec, double* out, void* stream);
+
 /* R_k of every sweep of the last solve.  Synchronises. */
 nbgs_status nbgs_residual_history(nbgs_scene* scene, double* out, int32_t cap, int32_t* n_out);
 

@@ -294,6 +294,46 @@ __device__ __forceinline__ double norm_exact(double x, double y, double z)
     return xsqrt(xadd(xadd(xmul(x, x), xmul(y, y)), xmul(z, z)));
 }
 
+// a / b rounded to nearest, given y = 1/b rounded to nearest: the quotient
+// q = RN(a y) is within one ulp of a / b, the remainder a - b q is exact in
+// one fused multiply-add, and RN(q + (a - b q) y) is the correctly rounded
+// quotient (Markstein's theorem, IBM J. Res. Dev. 34(1), 1990; Muller et
+// al., Handbook of Floating-Point Arithmetic, the chapter on division with
+// an FMA).  The theorem excludes underflow: zeros and tiny numerators take
+// the division itself, as does the caller for a tiny or huge b.
+__device__ __forceinline__ double div_by(double a, double b, double y)
+{
+    if (fabs(a) < 0x1p-900) return xdiv(a, b);
+    const double q = __dmul_rn(a, y);
+    const double r = __fma_rn(-q, b, a);
+    return __fma_rn(r, y, q);
+}
+
+// Sphere pair geometry of eq. (contactpos) from the centre difference
+// (dx, dy, dz) = x_i - x_j: d = |x_i - x_j| and the unit normal
+// n = (x_i - x_j) / d, every operation rounded to nearest as written (the
+// three quotients share one correctly rounded reciprocal of d); coincident
+// centres take n = (0, 0, 1).
+__device__ __forceinline__ double pair_normal(double dx, double dy, double dz, double n[3])
+{
+    const double d = norm_exact(dx, dy, dz);
+    if (d > 0x1p-1000 && d < 0x1p1000) {
+        const double y = __drcp_rn(d);
+        n[0] = div_by(dx, d, y);
+        n[1] = div_by(dy, d, y);
+        n[2] = div_by(dz, d, y);
+    } else if (d > 0.0) {
+        n[0] = xdiv(dx, d);
+        n[1] = xdiv(dy, d);
+        n[2] = xdiv(dz, d);
+    } else {
+        n[0] = 0.0;
+        n[1] = 0.0;
+        n[2] = 1.0;
+    }
+    return d;
+}
+
 // Composite particles: the members' world positions X + R(q) d (FP64, each
 // operation rounded as written: the contact geometry depends on them bit for
 // bit), their bodies' hulls h = dt (|v| + |w| r_bound) + tau (eq.
@@ -588,25 +628,33 @@ __device__ __forceinline__ void narrow_range(uint32_t t0, uint32_t t1, float sx,
         if (j <= i) continue;
         if (V.batch && V.scene_of[j] != si) continue;   // scenes never touch
         if (V.body_of && V.body_of[j] == V.body_of[i]) continue;   // members of one body never touch
-        // Conservative FP32 pre-filter (FP64 throughput is scarce on this GPU).
+        // Conservative FP32 screens (FP64 throughput is scarce on this GPU).
         // R = r_a + h_a + r_b + h_b bounds d for every kept pair.  The FP32
         // relative positions are off by at most pos_err per coordinate, the
         // periodic shift adds an ulp of L, so the FP32 distance is within
         // 1e-6 max(L) of d; the FP32 square and reach add relative errors
-        // below 4e-7 and 1.2e-7, covered by the extra 1e-4 while R < ~385.
-        // So (fl(R) + margin)^2 >= fl(d^2) for every kept pair; only the
-        // pairs that pass take the exact FP64 test.
+        // below 4e-7 and 1.2e-7, covered by the extra 1e-4 while R < ~250.
+        // So (fl(R) + margin)^2 >= fl(d^2) for every kept pair, and
+        // fl(d^2) < (fl(R) - margin)^2 only for pairs with d below R by more
+        // than the FP64 keep rule's rounding: those are kept without it.
+        // Only the pairs in the band between take the exact FP64 test.
         const float4 qj = p32s[t];
         const float fx = (qi.x - qj.x) + sx, fy = (qi.y - qj.y) + sy, fz = (qi.z - qj.z) + sz;
-        const float rr = qi.w + qj.w + g.margin;
-        if (fx * fx + fy * fy + fz * fz > rr * rr) continue;
-        const double4_32a pj = pos_r[j];
-        const double dx3 = min_image(xsub(pi.x, pj.x), g.periodic[0], L0);
-        const double dy3 = min_image(xsub(pi.y, pj.y), g.periodic[1], L1);
-        const double dz3 = min_image(xsub(pi.z, pj.z), g.periodic[2], L2);
-        const double d = norm_exact(dx3, dy3, dz3);
-        // Sect. 4: keep the pair iff the hulls intersect
-        if (xsub(xsub(d, pi.w), pj.w) <= xadd(hi_, hull[j])) {
+        const float rs = qi.w + qj.w;
+        const float rr = rs + g.margin, rl = rs - g.margin;
+        const float d2f = fx * fx + fy * fy + fz * fz;
+        if (rs < 250.f && d2f > rr * rr) continue;
+        bool keep = rl > 0.f && rs < 250.f && d2f < rl * rl;
+        if (!keep) {
+            const double4_32a pj = pos_r[j];
+            const double dx3 = min_image(xsub(pi.x, pj.x), g.periodic[0], L0);
+            const double dy3 = min_image(xsub(pi.y, pj.y), g.periodic[1], L1);
+            const double dz3 = min_image(xsub(pi.z, pj.z), g.periodic[2], L2);
+            const double d = norm_exact(dx3, dy3, dz3);
+            // Sect. 4: keep the pair iff the hulls intersect
+            keep = xsub(xsub(d, pi.w), pj.w) <= xadd(hi_, hull[j]);
+        }
+        if (keep) {
             if (P.cnt < kCandCap) {
                 // insertion keeps the list sorted by j
                 int k = P.cnt;
@@ -746,19 +794,14 @@ __global__ void k_write_contacts(int64_t n, int64_t ccap, const uint32_t* __rest
             const double dx3 = min_image(xsub(pi.x, pj.x), g.periodic[0], L0);
             const double dy3 = min_image(xsub(pi.y, pj.y), g.periodic[1], L1);
             const double dz3 = min_image(xsub(pi.z, pj.z), g.periodic[2], L2);
-            const double d = norm_exact(dx3, dy3, dz3);
-            double4_32a geo;
             // eq. (contactpos) for spheres: n = (x_i - x_j)/d, the outward
             // normal of S_j at its point closest to x_i; xi = d - r_i - r_j
-            if (d > 0.0) {
-                geo.x = xdiv(dx3, d);
-                geo.y = xdiv(dy3, d);
-                geo.z = xdiv(dz3, d);
-            } else {
-                geo.x = 0.0;
-                geo.y = 0.0;
-                geo.z = 1.0;
-            }
+            double nrm[3];
+            const double d = pair_normal(dx3, dy3, dz3, nrm);
+            double4_32a geo;
+            geo.x = nrm[0];
+            geo.y = nrm[1];
+            geo.z = nrm[2];
             geo.w = xsub(xsub(d, pi.w), pj.w);
             cj1[idx] = i;
             cj2[idx] = j;
@@ -977,3 +1020,29 @@ nbgs_status run_detect(nbgs_scene* s)
 }
 
 }  // namespace nbgs
+
+namespace nbgs {
+__global__ void k_pair_normals(int64_t n, const double* __restrict__ dvec, double* __restrict__ out)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        double nrm[3];
+        const double d = pair_normal(dvec[3 * k], dvec[3 * k + 1], dvec[3 * k + 2], nrm);
+        out[4 * k] = nrm[0];
+        out[4 * k + 1] = nrm[1];
+        out[4 * k + 2] = nrm[2];
+        out[4 * k + 3] = d;
+    }
+}
+}  // namespace nbgs
+
+extern "C" nbgs_status nbgs_pair_normals(int64_t n, const double* dvec, double* out, void* stream)
+{
+    using namespace nbgs;
+    if (n < 0 || (n > 0 && (!dvec || !out))) return NBGS_EINVAL;
+    if (n == 0) return NBGS_OK;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_pair_normals<<<grid_for(n, 256, 8, sms), 256, 0, (cudaStream_t)stream>>>(n, dvec, out);
+    return cudaGetLastError() == cudaSuccess ? NBGS_OK : NBGS_ECUDA;
+}

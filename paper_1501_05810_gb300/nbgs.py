@@ -92,6 +92,7 @@ _SIG = {
     "nbgs_graph_step": [_vp, C.c_int32, C.c_double, C.c_int32],
     "nbgs_get_updates": [_vp, _i64p],
     "nbgs_one_contact": [C.c_int64, _vp, _vp, _vp, _vp, _vp],
+    "nbgs_pair_normals": [C.c_int64, _vp, _vp, _vp],
     "nbgs_autotune": [_vp, C.c_int32, C.c_double, _i32p, _i32p],
     "nbgs_mlp_load": [_vp, _vp, C.c_int64],
     "nbgs_set_warm_start": [_vp, C.c_int32],

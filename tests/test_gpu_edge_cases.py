@@ -194,3 +194,46 @@ def test_one_contact_solver_matches_oracle(nb, oracle_mod):
         assert err[i] <= 1e-9, (i, pg[i], po[i])
     print("one-contact solver, GPU against oracle: largest relative difference", float(err.max()))
     assert err.max() <= 1e-10   # measured on a GB300: 1.8e-12
+
+
+def test_pair_normals_are_correctly_rounded(nb):
+    """nbgs_pair_normals (the detection's sphere geometry): d and the three
+    quotients (x_i - x_j) / d bit for bit equal to IEEE division and square
+    root in FP64 (numpy), on 2M random differences over 80 binades, exact
+    powers of two, distances whose significand is all ones, signed zeros,
+    tiny numerators and coincident centres."""
+    import torch
+    rng = np.random.default_rng(17)
+    m = 2_000_000
+    dv = rng.normal(size=(m, 3)) * np.exp2(rng.integers(-40, 40, (m, 1)))
+    dv[:1000] = rng.uniform(0.0, 100.0, (1000, 3)) - rng.uniform(0.0, 100.0, (1000, 3))
+    k = 1000
+    for e in range(-20, 21):                    # axis-aligned: d an exact power of two
+        dv[k] = [0.0, -np.ldexp(1.0, e), 0.0]
+        dv[k + 1] = [np.ldexp(1.0, e), 0.0, -0.0]
+        k += 2
+    ones = np.nextafter(2.0, 0.0)               # significand all ones
+    for e in range(-10, 11):
+        dv[k] = [np.ldexp(ones, e), 0.0, 0.0]
+        dv[k + 1] = [np.ldexp(ones, e) * 0.6, np.ldexp(ones, e) * 0.8, 0.0]
+        k += 2
+    dv[k] = [0.0, 0.0, 0.0]                     # coincident centres
+    dv[k + 1] = [-0.0, 0.0, -0.0]
+    dv[k + 2] = [1e-300, 1.0, 0.0]              # tiny numerator
+    dv[k + 3] = [5e-324, -2.0, 3.0]             # subnormal numerator
+    dev = torch.device("cuda:0")
+    td = torch.as_tensor(dv, device=dev)
+    to = torch.empty((m, 4), dtype=torch.float64, device=dev)
+    assert nb.library().nbgs_pair_normals(m, td.data_ptr(), to.data_ptr(),
+                                          torch.cuda.current_stream().cuda_stream) == nb.NBGS_OK
+    torch.cuda.synchronize()
+    out = to.cpu().numpy()
+    x, y, z = dv[:, 0], dv[:, 1], dv[:, 2]
+    d = np.sqrt((x * x + y * y) + z * z)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ref = np.stack([x / d, y / d, z / d, d], axis=1)
+    zero = d == 0.0
+    ref[zero, :3] = [0.0, 0.0, 1.0]
+    same = out.view(np.uint64) == ref.view(np.uint64)
+    bad = np.nonzero(~same.all(1))[0]
+    assert len(bad) == 0, (len(bad), dv[bad[:5]], out[bad[:5]], ref[bad[:5]])
