@@ -147,6 +147,7 @@ struct DevInfo {
     double residual;                 // R of the last sweep
     double v_ref;
     unsigned long long rk_bits[kMaxSweepsHist];  // max_j r_j of sweep k (bits)
+    uint32_t votes[2 * kMaxSweepsHist];          // tolerance test of sweep k: (a block above tol, blocks at or below)
 };
 
 // ---------------------------------------------------------------------------

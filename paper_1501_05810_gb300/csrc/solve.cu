@@ -677,6 +677,44 @@ __device__ __forceinline__ R process_gathered(const SolveArgs<R>& A, int64_t b0,
     return rmax;
 }
 
+// The tolerance test of sweep k without a grid barrier.  R_k <= tol holds
+// exactly when every block's own maximum (divided by the same v_ref) is at
+// or below tol, so a block above it announces that and goes on at once; a
+// block at or below it counts itself and waits until either some block has
+// announced (the sweeps go on) or every block has counted itself (the solve
+// stops after sweep k).  Every block reaches the end of sweep k, so the
+// wait ends; bounded like every other.  Returns 1 to go on, 0 to stop, -1
+// when the wait ran out.
+__device__ __forceinline__ int tol_vote(DevInfo* info, int k, double rb, double vnorm, double tol, unsigned nb,
+                                        int* s_vote)
+{
+    if (threadIdx.x == 0) {
+        uint32_t* flag = info->votes + 2 * k;
+        int v = 1;
+        if (!(rb / vnorm <= tol)) {
+            atomicExch(flag, 1u);
+        } else {
+            atomicAdd(flag + 1, 1u);
+            const long long t0 = clock64();
+            for (;;) {
+                if (((volatile uint32_t*)flag)[0] != 0u) break;
+                if (((volatile uint32_t*)flag)[1] == nb) {
+                    v = 0;
+                    break;
+                }
+                if ((((volatile uint32_t*)&info->err)[0] & kErrTimeout) || clock64() - t0 > (1LL << 31)) {
+                    atomicOr(&info->err, kErrTimeout);
+                    v = -1;
+                    break;
+                }
+            }
+        }
+        *s_vote = v;
+    }
+    __syncthreads();
+    return *s_vote;
+}
+
 template <class R, bool Batch, bool Warp, bool Sub, int K = 1, bool Mlp = false>
 __global__ void __launch_bounds__(kPersistThreads, (PersistMinBlocks<R, Batch, K>::value)) k_solve_persistent(SolveArgs<R> A)
 {
@@ -686,6 +724,7 @@ __global__ void __launch_bounds__(kPersistThreads, (PersistMinBlocks<R, Batch, K
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t s_gen;
     __shared__ int s_ok;
+    __shared__ int s_vote;
     const unsigned nb = gridDim.x;
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
@@ -740,6 +779,7 @@ __global__ void __launch_bounds__(kPersistThreads, (PersistMinBlocks<R, Batch, K
         if (Batch)   // the slot of sweep k + 1 is neither read nor written during sweep k
             for (int64_t sc = gtid; sc < A.nscene; sc += gstride) A.scene_rk[scene_slot(k + 1) * A.nscene + sc] = 0ull;
         R rmax = R(0);
+        double rb = 0.0;   // this block's max_j r_j of the sweep (thread 0)
         if (Warp) {
             // each warp on its own; a warp whose wait gave up skips the rest
             // of the sweep (the timeout bit makes every other wait return)
@@ -790,7 +830,7 @@ __global__ void __launch_bounds__(kPersistThreads, (PersistMinBlocks<R, Batch, K
             const R r = !stage ? process_gathered<R, Batch, K>(A, cb0, cb1, pr, pq, k)
                                : process_colour<R, false, Batch>(A, c, m, srec, sp, k);
             rmax = r > rmax ? r : rmax;
-            if (c == ncol - 1) block_max_to<R>(rmax, &A.info->rk_bits[rk_slot(k)]);
+            if (c == ncol - 1) rb = block_max_to<R>(rmax, &A.info->rk_bits[rk_slot(k)]);
             if (local) {
                 publish(A.prog, g);   // its __syncthreads also ends every read of the stage
                 m = stage ? stage_issue<R>(A, cn, srec, sp, &bar) : 0;
@@ -827,6 +867,19 @@ __global__ void __launch_bounds__(kPersistThreads, (PersistMinBlocks<R, Batch, K
                 break;
             }
             synced = true;
+        }
+        // a single scene's tolerance test: a vote instead of a grid barrier
+        if (!synced && local && !Warp && !Batch && !Sub && ncol > 0 && A.tol > 0.0 && k + 2 < kHistKept) {
+            const int v = tol_vote(A.info, k, rb, vnorm, A.tol, nb, &s_vote);
+            if (v < 0) {
+                ok = false;
+                break;
+            }
+            if (v == 0) {
+                ++k;
+                break;
+            }
+            continue;
         }
         // R_k needs every block's contribution: a grid barrier per sweep when
         // the tolerance is tested (and near the rotating residual slots)
@@ -1259,6 +1312,7 @@ static nbgs_status solve_impl(nbgs_scene* s, int max_sweeps, double tol)
     SolveArgs<R> A = make_args<R>(s, max_sweeps, tol);
     const int nk = max_sweeps < kHistKept ? max_sweeps : kHistKept + 3;
     cudaMemsetAsync(A.info->rk_bits, 0, (size_t)(nk > 0 ? nk : 1) * sizeof(unsigned long long), st);
+    cudaMemsetAsync(A.info->votes, 0, (size_t)(nk > 0 ? 2 * nk : 2) * sizeof(uint32_t), st);
     cudaMemsetAsync(&A.info->barrier_count, 0, 2 * sizeof(uint32_t), st);
     const uint32_t not_done = 0xFFFFFFFFu;
     if (s->batch) {
