@@ -115,6 +115,73 @@ template <> __device__ __forceinline__ float tab_sin<float>(int k) { return c_si
 template <> __device__ __forceinline__ double tab_cos<double>(int k) { return c_cos64[k]; }
 template <> __device__ __forceinline__ double tab_sin<double>(int k) { return c_sin64[k]; }
 
+// g(th) of the sliding condition, expanded in c = cos th, s = sin th.
+template <class R>
+__device__ __forceinline__ R slide_g(const R co[5], R c, R s)
+{
+    return co[0] * s + co[1] * c + co[2] * s * c + co[3] * s * s + co[4] * c * c;
+}
+
+// The root of g in the bracket [k dth, (k + 1) dth] (g(lo) = glo, g(hi) =
+// ghi of opposite signs, or glo = 0: the sample itself): Newton steps from
+// the secant point, kept inside the bracket (bisection where a step would
+// leave it).
+template <class R>
+__device__ __forceinline__ R slide_root(const R co[5], int k, R glo, R ghi, R dth)
+{
+    constexpr int kIter = sizeof(R) == 4 ? 12 : 24;
+    if (glo == R(0)) return dth * (R)k;
+    R lo = dth * (R)k, hi = dth * (R)(k + 1);
+    R gl = glo;
+    R th = lo + (hi - lo) * (glo / (glo - ghi));
+    for (int it = 0; it < kIter; ++it) {
+        R sn, cs;
+        if constexpr (sizeof(R) == 4) sincosf(th, &sn, &cs);
+        else sincos(th, &sn, &cs);
+        const R g = slide_g(co, cs, sn);
+        if (g == R(0)) break;
+        if ((g < R(0)) == (gl < R(0))) {
+            lo = th;
+            gl = g;
+        } else {
+            hi = th;
+        }
+        const R dg = co[0] * cs - co[1] * sn + co[2] * (cs * cs - sn * sn) + R(2) * (co[3] - co[4]) * sn * cs;
+        const R step = g / dg;
+        // a step below the resolution of th: converged (checked before the
+        // bracket, which has shrunk onto th)
+        if (fabs(step) <= (R)(sizeof(R) == 4 ? 1e-7 : 1e-15) * (R(1) + fabs(th))) break;
+        R nt = th - step;
+        if (!(nt > lo && nt < hi)) nt = R(0.5) * (lo + hi);
+        th = nt;
+    }
+    return th;
+}
+
+// The sliding state at th, if it qualifies (D > 0, u_to against the
+// friction direction), replaces the best one so far when its energy is
+// lower (the first in th on ties).
+template <class R>
+__device__ __forceinline__ void slide_candidate(const Sym3<R>& W, R mu, const R b[3], R th, bool& found, R& best,
+                                                R p[3])
+{
+    R sn, cs, D, vt, vo;
+    if constexpr (sizeof(R) == 4) sincosf(th, &sn, &cs);
+    else sincos(th, &sn, &cs);
+    slide_dut(W, mu, b, cs, sn, D, vt, vo);
+    if (!(D > R(0)) || cs * vt + sn * vo > R(0)) return;
+    const R pn = -b[0] / D;
+    const R q[3] = {pn, mu * pn * cs, mu * pn * sn};
+    const R e = energy(W, b, q);
+    if (!found || e < best) {
+        best = e;
+        p[0] = q[0];
+        p[1] = q[1];
+        p[2] = q[2];
+        found = true;
+    }
+}
+
 template <class R>
 __device__ void one_contact_general(const Sym3<R>& W, R mu, const R b[3], R p[3])
 {
@@ -139,73 +206,66 @@ __device__ void one_contact_general(const Sym3<R>& W, R mu, const R b[3], R p[3]
     }
     // sliding: the condition (cos th, sin th) x D u_to = 0 expanded in
     // c = cos th, s = sin th: g = P1 s + Q1 c + Rsc s c + S2 s^2 + C2 c^2
-    const R P1 = b[0] * W.nt - b[1] * W.nn;
-    const R Q1 = b[2] * W.nn - b[0] * W.no;
-    const R Rsc = mu * (b[0] * (W.tt - W.oo) - b[1] * W.nt + b[2] * W.no);
-    const R S2 = mu * (b[0] * W.to - b[1] * W.no);
-    const R C2 = mu * (b[2] * W.nt - b[0] * W.to);
+    const R co[5] = {b[0] * W.nt - b[1] * W.nn, b[2] * W.nn - b[0] * W.no,
+                     mu * (b[0] * (W.tt - W.oo) - b[1] * W.nt + b[2] * W.no), mu * (b[0] * W.to - b[1] * W.no),
+                     mu * (b[2] * W.nt - b[0] * W.to)};
     constexpr int K = 64;
-    constexpr int kIter = sizeof(R) == 4 ? 12 : 24;
     const R two_pi = (R)6.283185307179586;
     const R dth = two_pi / (R)K;
     bool found = false;
     R best = R(0);
-    R ghi_prev = R(0);
+    // Pass 1 finds the brackets (at most four sign changes: g has degree 2
+    // in cos and sin), pass 2 refines them in order.  Refining inside the
+    // sampling loop would run one lane's refinement at a time (lanes meet
+    // their roots at different samples); in pass 2 the lanes of a warp
+    // refine their r-th roots together.  More than four (rounding near a
+    // double root): the sampling loop refines as it goes.
+    int nbr = 0, k0 = 0, k1 = 0, k2 = 0, k3 = 0;
+    R l0 = R(0), l1 = R(0), l2 = R(0), l3 = R(0), h0 = R(0), h1 = R(0), h2 = R(0), h3 = R(0);
+    R gprev = slide_g(co, tab_cos<R>(0), tab_sin<R>(0));
     for (int k = 0; k < K; ++k) {
-        const int k1 = k + 1 == K ? 0 : k + 1;
-        R c = tab_cos<R>(k), s = tab_sin<R>(k);
-        const R glo = k == 0 ? P1 * s + Q1 * c + Rsc * s * c + S2 * s * s + C2 * c * c : ghi_prev;
-        c = tab_cos<R>(k1);
-        s = tab_sin<R>(k1);
-        const R ghi = P1 * s + Q1 * c + Rsc * s * c + S2 * s * s + C2 * c * c;
-        ghi_prev = ghi;
-        R th;
-        if (glo == R(0)) {
-            th = dth * (R)k;
-        } else if ((glo < R(0)) != (ghi < R(0)) && ghi != R(0)) {
-            // the root in [lo, hi]: Newton steps kept inside the bracket
-            // (bisection where a step would leave it)
-            R lo = dth * (R)k, hi = dth * (R)(k + 1);
-            R gl = glo;
-            th = lo + (hi - lo) * (glo / (glo - ghi));
-            for (int it = 0; it < kIter; ++it) {
-                R sn, cs;
-                if constexpr (sizeof(R) == 4) sincosf(th, &sn, &cs);
-                else sincos(th, &sn, &cs);
-                const R g = P1 * sn + Q1 * cs + Rsc * sn * cs + S2 * sn * sn + C2 * cs * cs;
-                if (g == R(0)) break;
-                if ((g < R(0)) == (gl < R(0))) {
-                    lo = th;
-                    gl = g;
-                } else {
-                    hi = th;
-                }
-                const R dg = P1 * cs - Q1 * sn + Rsc * (cs * cs - sn * sn) + R(2) * (S2 - C2) * sn * cs;
-                const R step = g / dg;
-                // a step below the resolution of th: converged (checked before
-                // the bracket, which has shrunk onto th)
-                if (fabs(step) <= (R)(sizeof(R) == 4 ? 1e-7 : 1e-15) * (R(1) + fabs(th))) break;
-                R nt = th - step;
-                if (!(nt > lo && nt < hi)) nt = R(0.5) * (lo + hi);
-                th = nt;
-            }
-        } else {
-            continue;
+        const int kn = k + 1 == K ? 0 : k + 1;
+        const R glo = gprev;
+        const R ghi = slide_g(co, tab_cos<R>(kn), tab_sin<R>(kn));
+        gprev = ghi;
+        if (!(glo == R(0) || ((glo < R(0)) != (ghi < R(0)) && ghi != R(0)))) continue;
+        if (nbr == 0) {
+            k0 = k;
+            l0 = glo;
+            h0 = ghi;
+        } else if (nbr == 1) {
+            k1 = k;
+            l1 = glo;
+            h1 = ghi;
+        } else if (nbr == 2) {
+            k2 = k;
+            l2 = glo;
+            h2 = ghi;
+        } else if (nbr == 3) {
+            k3 = k;
+            l3 = glo;
+            h3 = ghi;
         }
-        R sn, cs, D, vt, vo;
-        if constexpr (sizeof(R) == 4) sincosf(th, &sn, &cs);
-        else sincos(th, &sn, &cs);
-        slide_dut(W, mu, b, cs, sn, D, vt, vo);
-        if (!(D > R(0)) || cs * vt + sn * vo > R(0)) continue;
-        const R pn = -b[0] / D;
-        const R q[3] = {pn, mu * pn * cs, mu * pn * sn};
-        const R e = energy(W, b, q);
-        if (!found || e < best) {
-            best = e;
-            p[0] = q[0];
-            p[1] = q[1];
-            p[2] = q[2];
-            found = true;
+        ++nbr;
+    }
+    if (nbr <= 4) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (r >= nbr) break;
+            const int k = r == 0 ? k0 : (r == 1 ? k1 : (r == 2 ? k2 : k3));
+            const R glo = r == 0 ? l0 : (r == 1 ? l1 : (r == 2 ? l2 : l3));
+            const R ghi = r == 0 ? h0 : (r == 1 ? h1 : (r == 2 ? h2 : h3));
+            slide_candidate(W, mu, b, slide_root(co, k, glo, ghi, dth), found, best, p);
+        }
+    } else {
+        gprev = slide_g(co, tab_cos<R>(0), tab_sin<R>(0));
+        for (int k = 0; k < K; ++k) {
+            const int kn = k + 1 == K ? 0 : k + 1;
+            const R glo = gprev;
+            const R ghi = slide_g(co, tab_cos<R>(kn), tab_sin<R>(kn));
+            gprev = ghi;
+            if (!(glo == R(0) || ((glo < R(0)) != (ghi < R(0)) && ghi != R(0)))) continue;
+            slide_candidate(W, mu, b, slide_root(co, k, glo, ghi, dth), found, best, p);
         }
     }
     if (found) return;
