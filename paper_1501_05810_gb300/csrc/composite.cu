@@ -500,12 +500,11 @@ template <class R> struct CompArgs {
     int warm;
 };
 
-// Relax one composite contact (apply_only: add the stored impulse).
+// Relax one composite contact (apply_only: add the stored impulse), its
+// record and impulse already loaded.
 template <class R, bool apply_only>
-__device__ __forceinline__ R relax_comp(const CompArgs<R>& A, int64_t s)
+__device__ __forceinline__ R relax_comp_loaded(const CompArgs<R>& A, int64_t s, const CompRec<R>& rr, const R4<R>& pp)
 {
-    const CompRec<R> rr = A.rec[s];
-    const R4<R> pp = A.p[s];
     uint32_t ia, ib;
     R bias;
     if constexpr (sizeof(R) == 4) {
@@ -525,16 +524,17 @@ __device__ __forceinline__ R relax_comp(const CompArgs<R>& A, int64_t s)
     const R lA[3] = {rr.c.x, rr.c.y, rr.c.z}, lB[3] = {rr.d.x, rr.d.y, rr.d.z};
     R t[3], o[3];
     tangent_basis<R>(n[0], n[1], n[2], t[0], t[1], t[2], o[0], o[1], o[2]);
-    R4<R> va = A.bv[4 * (int64_t)ia], wa = A.bv[4 * (int64_t)ia + 1];
-    const R4<R> ia1 = A.bv[4 * (int64_t)ia + 2], ia2 = A.bv[4 * (int64_t)ia + 3];
+    // a body's state is 4 vectors: v, w and the 6 entries of its world inverse
+    // inertia, read as two 256-bit accesses
+    R4<R> va, wa, ia1, ia2;
+    ld_body(A.bv + 4 * (int64_t)ia, va, wa);
+    ld_body(A.bv + 4 * (int64_t)ia + 2, ia1, ia2);
     R4<R> vb, wb, ib1, ib2;
     vb.x = vb.y = vb.z = vb.w = R(0);
     wb = ib1 = ib2 = vb;
     if (hasB) {
-        vb = A.bv[4 * (int64_t)ib];
-        wb = A.bv[4 * (int64_t)ib + 1];
-        ib1 = A.bv[4 * (int64_t)ib + 2];
-        ib2 = A.bv[4 * (int64_t)ib + 3];
+        ld_body(A.bv + 4 * (int64_t)ib, vb, wb);
+        ld_body(A.bv + 4 * (int64_t)ib + 2, ib1, ib2);
     }
     R d[3];
     if (apply_only) {
@@ -581,8 +581,7 @@ __device__ __forceinline__ R relax_comp(const CompArgs<R>& A, int64_t s)
         wa.x += dw[0];
         wa.y += dw[1];
         wa.z += dw[2];
-        A.bv[4 * (int64_t)ia] = va;
-        A.bv[4 * (int64_t)ia + 1] = wa;
+        st_body(A.bv + 4 * (int64_t)ia, va, wa);
     }
     if (hasB && vb.w > R(0)) {
         const R I6[6] = {ib1.x, ib1.y, ib1.z, ib1.w, ib2.x, ib2.y};
@@ -595,13 +594,20 @@ __device__ __forceinline__ R relax_comp(const CompArgs<R>& A, int64_t s)
         wb.x -= dw[0];
         wb.y -= dw[1];
         wb.z -= dw[2];
-        A.bv[4 * (int64_t)ib] = vb;
-        A.bv[4 * (int64_t)ib + 1] = wb;
+        st_body(A.bv + 4 * (int64_t)ib, vb, wb);
     }
     const R r0 = W.nn * d[0] + W.nt * d[1] + W.no * d[2];
     const R r1 = W.nt * d[0] + W.tt * d[1] + W.to * d[2];
     const R r2 = W.no * d[0] + W.to * d[1] + W.oo * d[2];
     return sqrt(r0 * r0 + r1 * r1 + r2 * r2);
+}
+
+template <class R, bool apply_only>
+__device__ __forceinline__ R relax_comp(const CompArgs<R>& A, int64_t s)
+{
+    const CompRec<R> rr = A.rec[s];
+    const R4<R> pp = A.p[s];
+    return relax_comp_loaded<R, apply_only>(A, s, rr, pp);
 }
 
 __device__ __forceinline__ void block_max_atomic(double x, unsigned long long* dst)
@@ -652,9 +658,22 @@ __global__ void __launch_bounds__(kCompThreads) k_solve_comp(CompArgs<R> A)
                 const int g = k * ncol + c;
                 int64_t b0, b1;
                 colour_chunk(A.cstart, c, b0, b1);
+                // the first record and impulse of this thread do not depend on
+                // the neighbours: loaded before the wait
+                const int64_t s0 = b0 + threadIdx.x;
+                CompRec<R> rr;
+                R4<R> pp;
+                if (s0 < b1) {
+                    rr = A.rec[s0];
+                    pp = A.p[s0];
+                }
                 if (b1 > b0 && !wait_deps(A.prog, A.dep[c * (int)nb + blockIdx.x], g, A.info, &s_ok)) return;
-                for (int64_t s = b0 + threadIdx.x; s < b1; s += blockDim.x) {
-                    const R r = relax_comp<R, false>(A, s);
+                for (int64_t s = s0; s < b1; s += blockDim.x) {
+                    if (s != s0) {
+                        rr = A.rec[s];
+                        pp = A.p[s];
+                    }
+                    const R r = relax_comp_loaded<R, false>(A, s, rr, pp);
                     rmax = r > rmax ? r : rmax;
                 }
                 if (c == ncol - 1) block_max_atomic((double)rmax, &A.info->rk_bits[rk_slot(k)]);
