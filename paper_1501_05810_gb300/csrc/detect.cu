@@ -770,7 +770,10 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
 }
 
 // Canonical contact records: row i of the CSR holds (i, j) for the sorted
-// partners j, then the walls in the order they were added.
+// partners j, then the walls in the order they were added.  A warp takes 32
+// bodies (in cell order) and spreads their sphere pairs over its lanes, one
+// pair per lane and pass, so that the FP64 chains of a row run side by side;
+// the walls of a body stay with its own lane.
 __global__ void k_write_contacts(int64_t n, int64_t ccap, const uint32_t* __restrict__ svals,
                                  const double4_32a* __restrict__ pos_r, const double* __restrict__ hull,
                                  const uint32_t* __restrict__ cand, const uint32_t* __restrict__ sph_cnt,
@@ -779,21 +782,57 @@ __global__ void k_write_contacts(int64_t n, int64_t ccap, const uint32_t* __rest
                                  double2* __restrict__ clev)
 {
     const double L0 = g.hi[0] - g.lo[0], L1 = g.hi[1] - g.lo[1], L2 = g.hi[2] - g.lo[2];
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t i = svals[s];
-        const uint32_t packed = sph_cnt[i];
-        if (packed == 0) continue;   // no contact in this row
-        const uint32_t ns = packed & 0xFFu, wm = packed >> 8;
-        const double4_32a pi = pos_r[i];
-        int64_t idx = row_off[i];
-        const uint32_t* lst = cand + (int64_t)i * kCandCap;
-        for (uint32_t k = 0; k < ns; ++k, ++idx) {
-            const uint32_t j = lst[k];
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count: every lane takes part in the shuffles
+    for (int64_t s0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); s0 < n; s0 += wstride) {
+        const int64_t s = s0 + lane;
+        uint32_t i = 0, packed = 0, ro = 0;
+        double4_32a pi = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+        if (s < n) {
+            i = svals[s];
+            packed = sph_cnt[i];
+            if (packed != 0) {
+                pi = pos_r[i];
+                ro = row_off[i];
+            }
+        }
+        const uint32_t ns = packed & 0xFFu;
+        uint32_t pre = ns;   // inclusive prefix of the pair counts over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += v;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, pre, 31);
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t t = base + lane;
+            // owner: the number of lanes whose pairs end at or before t
+            int own = 0;
+#pragma unroll
+            for (int b = 16; b >= 1; b >>= 1) {
+                const uint32_t v = __shfl_sync(0xffffffffu, pre, own + b - 1);
+                if (v <= t) own += b;
+            }
+            own = own < 31 ? own : 31;
+            const uint32_t i_o = __shfl_sync(0xffffffffu, i, own);
+            const uint32_t ro_o = __shfl_sync(0xffffffffu, ro, own);
+            const uint32_t end_o = __shfl_sync(0xffffffffu, pre, own);
+            const uint32_t ns_o = __shfl_sync(0xffffffffu, ns, own);
+            double4_32a po;
+            po.x = __shfl_sync(0xffffffffu, pi.x, own);
+            po.y = __shfl_sync(0xffffffffu, pi.y, own);
+            po.z = __shfl_sync(0xffffffffu, pi.z, own);
+            po.w = __shfl_sync(0xffffffffu, pi.w, own);
+            if (t >= total) continue;
+            const uint32_t k = t - (end_o - ns_o);
+            const int64_t idx = (int64_t)ro_o + k;
             if (idx >= ccap) continue;
+            const uint32_t j = cand[(int64_t)i_o * kCandCap + k];
             const double4_32a pj = pos_r[j];
-            const double dx3 = min_image(xsub(pi.x, pj.x), g.periodic[0], L0);
-            const double dy3 = min_image(xsub(pi.y, pj.y), g.periodic[1], L1);
-            const double dz3 = min_image(xsub(pi.z, pj.z), g.periodic[2], L2);
+            const double dx3 = min_image(xsub(po.x, pj.x), g.periodic[0], L0);
+            const double dy3 = min_image(xsub(po.y, pj.y), g.periodic[1], L1);
+            const double dz3 = min_image(xsub(po.z, pj.z), g.periodic[2], L2);
             // eq. (contactpos) for spheres: n = (x_i - x_j)/d, the outward
             // normal of S_j at its point closest to x_i; xi = d - r_i - r_j
             double nrm[3];
@@ -802,15 +841,17 @@ __global__ void k_write_contacts(int64_t n, int64_t ccap, const uint32_t* __rest
             geo.x = nrm[0];
             geo.y = nrm[1];
             geo.z = nrm[2];
-            geo.w = xsub(xsub(d, pi.w), pj.w);
-            cj1[idx] = i;
+            geo.w = xsub(xsub(d, po.w), pj.w);
+            cj1[idx] = i_o;
             cj2[idx] = j;
             cgeo[idx] = geo;
             clev[idx] = make_double2(xsub(d, pj.w), pj.w);
         }
+        const uint32_t wm = packed >> 8;
         if (wm == 0) continue;
         const double hi_ = hull[i];
         const uint32_t si = V.batch ? V.scene_of[i] : 0u;
+        int64_t idx = (int64_t)ro + ns;
         for (uint32_t m = wm; m; m &= m - 1) {   // the walls k_narrow kept, in wall order
             const int k = __ffs(m) - 1;
             double nrm[3], c, sd, xi;
