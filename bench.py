@@ -563,7 +563,7 @@ def main():
         g.get_updates()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            g.set_bodies(host["pos"], host["quat"], host["vel"], host["angvel"])
+            g.update_bodies(host["pos"], host["quat"], host["vel"], host["angvel"])
             g.step(sweeps, tol, stats=False)
             nbgs._call(g.h, "nbgs_get_bodies", *[host[k].data_ptr() for k in ("pos", "quat", "vel", "angvel")])
         torch.cuda.synchronize()

@@ -179,6 +179,15 @@ nbgs_status nbgs_set_bodies(nbgs_scene* scene, const double* pos, const double* 
                             const double* vel, const double* angvel);
 nbgs_status nbgs_get_bodies(nbgs_scene* scene, double* pos, double* quat,
                             double* vel, double* angvel);
+/* Overwrite the body state as nbgs_set_bodies does, but continue the
+ * history: the next solve warm starts from the impulses of the last one,
+ * matched by contact key as after an ordinary step (Sect. 5).  For a caller
+ * that reads the state back, changes it on the host (external forces, a
+ * coupled code) and writes it again between steps; writing back unchanged
+ * what nbgs_get_bodies returned leaves the next step exactly as without the
+ * round trip.  NULL arrays are skipped; errors as for nbgs_set_bodies. */
+nbgs_status nbgs_update_bodies(nbgs_scene* scene, const double* pos, const double* quat,
+                               const double* vel, const double* angvel);
 
 /* Sect. 4: hull radii h_i = dt(|v_i| + |w_i| r_i) + tau from the current
  * velocities, uniform cell grid sorted by radix sort, narrow phase

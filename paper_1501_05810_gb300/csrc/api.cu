@@ -668,6 +668,13 @@ nbgs_status nbgs_set_bodies(nbgs_scene* s, const double* pos, const double* quat
     return run_set_bodies(s, pos, quat, vel, angvel);
 }
 
+nbgs_status nbgs_update_bodies(nbgs_scene* s, const double* pos, const double* quat, const double* vel,
+                               const double* angvel)
+{
+    NBGS_GUARD(s);
+    return run_set_bodies(s, pos, quat, vel, angvel);
+}
+
 nbgs_status nbgs_get_bodies(nbgs_scene* s, double* pos, double* quat, double* vel, double* angvel)
 {
     NBGS_GUARD(s);

@@ -70,6 +70,7 @@ _SIG = {
     "nbgs_add_cone": [_vp, _dp, _dp, C.c_double, C.c_double, C.c_double],
     "nbgs_set_mass_properties": [_vp, _vp, _vp],
     "nbgs_set_bodies": [_vp, _vp, _vp, _vp, _vp],
+    "nbgs_update_bodies": [_vp, _vp, _vp, _vp, _vp],
     "nbgs_get_bodies": [_vp, _vp, _vp, _vp, _vp],
     "nbgs_detect_contacts": [_vp, _i64p],
     "nbgs_colour_contacts": [_vp, _i32p],
@@ -293,6 +294,15 @@ class Scene:
                                         else np.ascontiguousarray(a, dtype=np.float64))
                 for a in (pos, quat, vel, angvel)]
         _call(self.h, "nbgs_set_bodies", *[_ptr(a) for a in arrs])
+        self.sync()
+
+    def update_bodies(self, pos=None, quat=None, vel=None, angvel=None):
+        """Overwrite the body state and keep the warm-start history
+        (nbgs_update_bodies)."""
+        arrs = [None if a is None else (a if not isinstance(a, (np.ndarray, list, tuple))
+                                        else np.ascontiguousarray(a, dtype=np.float64))
+                for a in (pos, quat, vel, angvel)]
+        _call(self.h, "nbgs_update_bodies", *[_ptr(a) for a in arrs])
         self.sync()
 
     def get_bodies(self) -> dict:

@@ -237,3 +237,30 @@ def test_pair_normals_are_correctly_rounded(nb):
     same = out.view(np.uint64) == ref.view(np.uint64)
     bad = np.nonzero(~same.all(1))[0]
     assert len(bad) == 0, (len(bad), dv[bad[:5]], out[bad[:5]], ref[bad[:5]])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_update_bodies_round_trip_keeps_the_history(nb, precision):
+    """Reading the state back and writing it again with nbgs_update_bodies
+    between steps leaves every step as it was (the warm start still finds
+    the previous impulses), bit for bit; nbgs_set_bodies starts a new
+    history instead (cold start: different impulses after a few sweeps)."""
+    sc = scenes.loose_pour(seed=3, n=6000, precision=precision, warm_start="prev")
+    sc["vel"] = np.random.default_rng(4).normal(0.0, 2.0, sc["vel"].shape)
+    sc["params"]["dt"] = 0.02
+    a, b, c = nb.Scene(sc), nb.Scene(sc), nb.Scene(sc)
+    for g in (a, b, c):
+        g.step(20)
+    for _ in range(3):
+        for g, how in ((b, "update"), (c, "set")):
+            st = g.get_bodies()
+            getattr(g, how + "_bodies")(st["pos"], st["quat"], st["vel"], st["angvel"])
+        for g in (a, b, c):
+            g.step(5)
+    ba, bb = a.get_bodies(), b.get_bodies()
+    ca, cb, cc = a.get_contacts(), b.get_contacts(), c.get_contacts()
+    assert len(ca["j1"]) > 1000
+    for k in ("pos", "quat", "vel", "angvel"):
+        assert np.array_equal(ba[k], bb[k]), k
+    assert np.array_equal(ca["impulse"], cb["impulse"])
+    assert not np.array_equal(ca["impulse"], cc["impulse"])
