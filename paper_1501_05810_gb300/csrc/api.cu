@@ -63,9 +63,9 @@ static bool alloc_contact_arrays(nbgs_scene* s, int64_t cap)
     const size_t c = (size_t)cap;
     bool ok = take(s, s->cj1, c) && take(s, s->cj2, c) && take(s, s->cgeo, c) && take(s, s->clev, c) &&
               take(s, s->cimp, c) && take(s, s->cworld, c) && take(s, s->prev_j2, c) && take(s, s->prev_P, c) &&
-              take(s, s->adj, 2 * c) && take(s, s->cstate, c) && take(s, s->cprio, c) && take(s, s->wl[0], c) &&
-              take(s, s->wl[1], c) && take(s, s->colour_key, c) && take(s, s->colour_key2, c) &&
-              take(s, s->pmask, c) && take(s, s->whead, c) && take(s, s->wnext, c) && take(s, s->poff, c + 1) &&
+              take(s, s->adj, 2 * c) && take(s, s->cstate, c) && take(s, s->cprio, c) && take(s, s->wl[0], 2 * c) &&
+              take(s, s->wl[1], 2 * c) && take(s, s->colour_key, c) && take(s, s->colour_key2, c) &&
+              take(s, s->cpack, c) &&
               take(s, s->perm, c) && take(s, s->perm_in, c);
     if (!ok) return false;
     s->srec = dev_alloc(s, c * rec_bytes(s));
@@ -77,7 +77,7 @@ static void free_contact_arrays(nbgs_scene* s)
 {
     void* ps[] = {s->cj1, s->cj2, s->cgeo, s->clev, s->cimp, s->cworld, s->prev_j2, s->prev_P, s->adj, s->cstate,
                   s->cprio, s->wl[0], s->wl[1], s->colour_key, s->colour_key2, s->perm, s->perm_in, s->srec, s->sp,
-                  s->pmask, s->whead, s->wnext, s->poff};
+                  s->cpack};
     for (void* p : ps) dev_free(s, p);
 }
 
@@ -90,18 +90,6 @@ static bool alloc_sort_temps(nbgs_scene* s)
         std::max<int64_t>(std::max<int64_t>(s->radix_hist_len, s->n + 1), std::max<int64_t>(s->ccap, s->max_cells) + 1);
     s->scan_tmp_len = (scan_len + 4095) / 4096 + 1;
     return take(s, s->radix_hist, (size_t)s->radix_hist_len + 1) && take(s, s->scan_tmp, (size_t)s->scan_tmp_len);
-}
-
-// Grow the predecessor-list buffer of the colouring to `need` entries.
-nbgs_status grow_preds(nbgs_scene* s, int64_t need)
-{
-    if (need <= s->preds_cap) return NBGS_OK;
-    const int64_t cap = need + need / 4 + 4096;
-    dev_free(s, s->preds);
-    s->preds = (uint2*)dev_alloc(s, (size_t)cap * sizeof(uint2));
-    s->preds_cap = s->preds ? cap : 0;
-    if (!s->preds) return fail(s, NBGS_ENOMEM, "colour: predecessor lists: allocation failed");
-    return NBGS_OK;
 }
 
 // Grow every contact-sized buffer to hold `need` contacts; the previous
@@ -165,7 +153,6 @@ static nbgs_status check_device_errors(nbgs_scene* s)
     if (e & kErrTimeout) return fail(s, NBGS_ETIMEOUT, "a grid barrier wait timed out");
     if (e & kErrNaN) return fail(s, NBGS_ENAN, "NaN or Inf in the body state");
     if (e & kErrContacts) return fail(s, NBGS_ECAPACITY, "a graph step found more contacts than its buffers hold");
-    if (e & kErrPreds) return fail(s, NBGS_ECAPACITY, "a graph step's colouring outgrew its predecessor lists");
     if (e & kErrColours) return fail(s, NBGS_ECAPACITY, "more than 256 colours needed");
     return NBGS_OK;
 }
@@ -466,6 +453,7 @@ static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_des
               take(s, s->vals[0], nn) && take(s, s->vals[1], nn) && take(s, s->cand, nn * kCandCap) &&
               take(s, s->sph_cnt, nn) && take(s, s->row_cnt, nn) && take(s, s->row_off, nn + 1) &&
               take(s, s->prev_row_off, nn + 1) && take(s, s->deg, nn + 1) && take(s, s->adj_off, nn + 1) &&
+              take(s, s->cmask, 8 * (nn + 1)) &&
               take(s, s->col_count, kMaxColours + 1) && take(s, s->col_off, kMaxColours + 1) &&
               take(s, s->info, 1);
     if (ok) {
@@ -595,7 +583,7 @@ void nbgs_destroy_scene(nbgs_scene* s)
                   s->cand, s->sph_cnt, s->row_cnt, s->row_off, s->prev_row_off, s->deg, s->adj_off,
                   s->col_count, s->col_off, s->info, s->dep, s->prog, s->cstart, s->scene_of, s->scene_off,
                   s->scene_box, s->scene_box32, s->scene_mu, s->scene_vmax, s->scene_vref, s->scene_rk,
-                  s->scene_done, s->scene_res, s->mlp_theta, s->preds};
+                  s->scene_done, s->scene_res, s->mlp_theta, s->cmask};
     for (void* p : ps) dev_free(s, p);
     free_contact_arrays(s);
     free_subdomain_buffers(s);
@@ -869,18 +857,13 @@ nbgs_status nbgs_graph_step(nbgs_scene* s, int32_t max_sweeps, double tol, int32
                                     "no network warm start");
     if (s->timing) return fail(s, NBGS_EINVAL, "graph_step: disable timing first");
     if (n_steps == 0) return NBGS_OK;
-    const bool fresh = s->gexec[0] && max_sweeps == s->g_sweeps && tol == s->g_tol && s->ccap == s->g_ccap &&
-                       s->preds_cap == s->g_pcap;
+    const bool fresh = s->gexec[0] && max_sweeps == s->g_sweeps && tol == s->g_tol && s->ccap == s->g_ccap;
     if (!fresh) {
         nbgs_status rc = refresh_after_graphs(s);
         if (rc != NBGS_OK) return rc;
         if (!s->solved || s->n == 0)
             return fail(s, NBGS_EINVAL, "graph_step: take one nbgs_step first (it sizes the buffers)");
         drop_graphs(s);
-        // predecessor lists for a colouring of a full contact buffer (about
-        // six entries per contact in dense packings)
-        rc = grow_preds(s, 6 * s->ccap + 4096);
-        if (rc != NBGS_OK) return rc;
         s->device_sized = true;
         rc = capture_step(s, max_sweeps, tol, &s->gexec[0]);
         if (rc == NBGS_OK) rc = capture_step(s, max_sweeps, tol, &s->gexec[1]);
@@ -893,7 +876,6 @@ nbgs_status nbgs_graph_step(nbgs_scene* s, int32_t max_sweeps, double tol, int32
         s->g_sweeps = max_sweeps;
         s->g_tol = tol;
         s->g_ccap = s->ccap;
-        s->g_pcap = s->preds_cap;
         s->g_next = 0;
         s->last_sweeps = max_sweeps;
     }

@@ -7,14 +7,14 @@
 //
 //   k_colour_init   priority splitmix64(key ^ seed), body degrees
 //   scan + k_adj_fill  body -> contact incidence lists (finite bodies only)
-//   k_pred_count, scan, k_pred_lists
-//                   per contact: the incident contacts that beat it (its
-//                   predecessors); it waits on the weakest
-//   k_jp_round      a contact whose predecessors are all coloured takes the
-//                   smallest colour none of them has: first-fit greedy in
-//                   decreasing priority, as Jones-Plassmann rounds give it,
-//                   driven by waiting lists (k_jp_persistent: every round
-//                   in one cooperative launch, for device-sized steps)
+//   k_adj_sort_*    every incidence list in decreasing priority; each
+//                   contact's position in the lists of its bodies
+//   k_fr_round      rounds of first-fit greedy colouring in decreasing
+//                   priority, as Jones-Plassmann rounds give it: a contact
+//                   at the front of the remaining lists of all its bodies
+//                   takes the smallest colour absent from their coloured
+//                   prefixes (k_fr_persistent: every round in one
+//                   cooperative launch, for device-sized steps)
 //   k_colour_keys   colour histogram
 //   radix pass      stable counting sort by colour -> permutation
 //   k_build_sweep   sweep records in colour order, initial impulses
@@ -43,21 +43,26 @@ __device__ __forceinline__ uint64_t local_key(uint32_t a, uint32_t b, const Scen
     return ((uint64_t)(a - off) << 32) | lb;
 }
 
+constexpr uint32_t kNoList = 0xFFFFFFFFu;   // a contact end without an incidence list (wall, infinite mass)
+
 // Priorities from the contacts' keys; body degrees from the incidence ends
 // ib1, ib2 (the contact's bodies: the contact ends themselves for spheres,
 // the members' bodies for composites; >= n marks a wall).
 __global__ void k_colour_init(DCount Cc, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
                               const uint32_t* __restrict__ ib1, const uint32_t* __restrict__ ib2,
                               const uint8_t* __restrict__ finite, uint64_t seed, SceneView V, uint32_t* __restrict__ deg,
-                              uint64_t* __restrict__ prio, uint32_t* __restrict__ cstate)
+                              uint64_t* __restrict__ prio, uint32_t* __restrict__ cstate, uint4* __restrict__ cpack)
 {
     const int64_t C = Cc.get();
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
         prio[c] = splitmix64(local_key(cj1[c], cj2[c], V) ^ seed);
         cstate[c] = kUncoloured;
         const uint32_t a = ib1[c], b = ib2[c];
-        if (finite[a]) atomicAdd(&deg[a], 1u);
-        if (b < n && finite[b]) atomicAdd(&deg[b], 1u);
+        const bool fa = finite[a] != 0, fb = b < n && finite[b];
+        if (fa) atomicAdd(&deg[a], 1u);
+        if (fb) atomicAdd(&deg[b], 1u);
+        // the bodies whose incidence lists hold c (none: no list), positions later
+        cpack[c] = make_uint4(fa ? a : kNoList, fb ? b : kNoList, 0u, 0u);
     }
 }
 
@@ -81,359 +86,278 @@ __device__ __forceinline__ bool beats(uint64_t pd, uint32_t d, uint64_t pc, uint
     return d < c;
 }
 
-// Colouring by waiting lists.  First-fit greedy colouring in decreasing
-// priority gives each contact the smallest colour none of its predecessors
-// (neighbours that beat it) has; the colour depends only on the
-// predecessors' colours, not on when it is computed.  So a contact is
-// examined only when it may be ready: at the start if it has no
-// predecessor, later when the predecessor it waits for (its blocker) has
-// been coloured.  A contact that finds a predecessor still uncoloured puts
-// itself on that predecessor's waiting list (whead / wnext, a lock-free
-// stack); the round after a contact is coloured walks its list.  A waiter
-// always registers in a round no later than the one that colours its
-// blocker (it saw the blocker uncoloured), so the walk, one launch later,
-// sees it.  Every round needs only the contacts coloured in the previous
-// round and their waiters, not a pass over all uncoloured contacts.
+// Colouring by priority-ordered incidence lists.  First-fit greedy
+// colouring in decreasing priority gives each contact the smallest colour
+// none of its predecessors (incident contacts that beat it) has.  With the
+// incidence list of every body sorted by priority, the predecessors of c
+// are the entries before c in the lists of its bodies.  A body's front is
+// the length of the coloured prefix of its list, and its mask the set of
+// colours in that prefix; c can be coloured once it is at the front of the
+// lists of all its (finite) bodies, and its colour is the smallest one in
+// none of their masks.  Colouring c adds its colour to those masks,
+// advances the fronts by one and exposes the next entry of each list, which
+// the next round colours if it is at the front of its other body's list
+// too (else that body's front exposes it later).  Each round colours
+// exactly the contacts whose predecessors were all coloured before it: the
+// rounds of Jones-Plassmann, with O(1) work per contact and round.
 //
-// Worklists: a buffer of C entries holds the contacts coloured in a round
-// (L, from the front) and the contacts to examine directly in the next
-// round (X, from the back: contacts with more than 64 incidence entries,
-// which keep no blocker, and examinations that did not fit a block's shared
-// buffer).  The counters (|L|, |X|) rotate through three pairs: a round
-// reads one, writes the next and clears the third.
+// A body's front is advanced at most once per round (only its front entry
+// can be coloured), and it is tagged with the round that advanced it: a
+// contact checked in the same round sees the value the front had when the
+// round began.  So each round reads only what earlier rounds wrote (a launch
+// boundary or a grid barrier apart), and a body's mask is written only by
+// the one contact at its front.
+constexpr uint32_t kFrontBits = 20;   // position bits of a front word; the round above them
+constexpr int kJpThreads = 256;       // threads of a colouring round's blocks
+constexpr uint32_t kClaimed = 0xFFFFFFFEu;
 
-// Appends val to list (from the front, or from the back of a buffer of cap
-// entries) for every lane with pred set; one counter update per warp.
-__device__ __forceinline__ void warp_push(bool pred, uint32_t val, uint32_t* list, uint32_t* count, int lane,
-                                          bool from_back = false, uint32_t cap = 0)
+__device__ __forceinline__ uint32_t front_at(uint32_t f, uint32_t round)
 {
-    const uint32_t mask = __ballot_sync(0xffffffffu, pred);
-    uint32_t b = 0;
-    if (lane == 0 && mask) b = atomicAdd(count, (uint32_t)__popc(mask));
-    b = __shfl_sync(0xffffffffu, b, 0);
-    if (pred) {
-        const uint32_t i = b + __popc(mask & ((1u << lane) - 1u));
-        list[from_back ? cap - 1u - i : i] = val;
-    }
+    const uint32_t v = f & ((1u << kFrontBits) - 1u);
+    return (f >> kFrontBits) == round ? v - 1u : v;
 }
 
-// Incidence entry j of contact c: the lists of its first body, then of its
-// second (finite bodies only).
-__device__ __forceinline__ uint32_t incident(const uint32_t* __restrict__ adj, uint32_t a0, uint32_t na, uint32_t b0,
-                                             uint32_t j)
+// Incidence lists in decreasing priority ("beats" order), and each
+// contact's position in the lists of its bodies (cpack z for its first
+// body, w for its second).  Short lists (up to 16 contacts, every sphere
+// scene) take a bitonic network in a thread's registers; longer ones a
+// warp, lane l holding entries l, l + 32, ..., an entry's position being the
+// number of entries that beat it, counted over the others broadcast by
+// shuffles (one lane sorts lists beyond the warp's slots in place).
+constexpr uint32_t kShortList = 16;
+constexpr int kSortSlots = 8;   // entries per lane of the warp sort: lists of up to 256 contacts
+
+__device__ __forceinline__ void set_position(uint4* cpack, uint32_t c, uint32_t x, uint32_t k)
 {
-    return j < na ? adj[a0 + j] : adj[b0 + j - na];
+    uint32_t* q = reinterpret_cast<uint32_t*>(cpack + c);
+    q[q[0] == x ? 2 : 3] = k;
 }
 
-__device__ __forceinline__ void incidence(uint32_t c, int64_t n, const uint32_t* __restrict__ cj1,
-                                          const uint32_t* __restrict__ cj2, const uint8_t* __restrict__ finite,
-                                          const uint32_t* __restrict__ adj_off, uint32_t& a0, uint32_t& na,
-                                          uint32_t& b0, uint32_t& nb)
+__global__ void k_adj_sort_short(int64_t n, const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
+                                 uint32_t* __restrict__ adj, const uint64_t* __restrict__ prio,
+                                 uint4* __restrict__ cpack)
 {
-    const uint32_t a = cj1[c], b = cj2[c];
-    const bool fa = finite[a], fb = b < n && finite[b];
-    a0 = fa ? adj_off[a] : 0;
-    na = fa ? adj_off[a + 1] - a0 : 0;
-    b0 = fb ? adj_off[b] : 0;
-    nb = fb ? adj_off[b + 1] - b0 : 0;
-}
-
-// Predecessors of contact c: the incident contacts that beat it.  Pass 1
-// counts them (npred) and keeps them as a bit mask over the incidence
-// entries (pmask; ~0 for more than 64 entries, where pass 2 compares
-// priorities again).
-__global__ void k_pred_count(DCount Cc, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
-                             const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
-                             const uint32_t* __restrict__ adj, const uint64_t* __restrict__ prio,
-                             uint64_t* __restrict__ pmask, uint32_t* __restrict__ npred)
-{
-    const int64_t C = Cc.get();
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t a0, na, b0, nb;
-        incidence((uint32_t)c, n, cj1, cj2, finite, adj_off, a0, na, b0, nb);
-        const uint64_t pc = prio[c];
-        uint64_t m = 0;
-        uint32_t k = 0;
-        for (uint32_t j = 0; j < na + nb; ++j) {
-            const uint32_t d = incident(adj, a0, na, b0, j);
-            if (d != (uint32_t)c && beats(prio[d], d, pc, (uint32_t)c)) {
-                ++k;
-                if (j < 64) m |= 1ull << j;
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        if (!finite[x]) continue;
+        const uint32_t a0 = adj_off[x], m = adj_off[x + 1] - a0;
+        if (m > kShortList || m == 0) continue;
+        uint32_t id[kShortList];
+        uint64_t pr[kShortList];
+#pragma unroll
+        for (uint32_t i = 0; i < kShortList; ++i) id[i] = i < m ? adj[a0 + i] : 0xFFFFFFFFu;
+#pragma unroll
+        for (uint32_t i = 0; i < kShortList; ++i) pr[i] = i < m ? prio[id[i]] : 0ull;   // padding sorts last
+        // bitonic network: after it, entry i beats entry i + 1
+#pragma unroll
+        for (uint32_t k = 2; k <= kShortList; k <<= 1) {
+#pragma unroll
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+                for (uint32_t i = 0; i < kShortList; ++i) {
+                    const uint32_t l = i ^ j;
+                    if (l <= i) continue;
+                    const bool first = (i & k) == 0;   // this half ends with i beating l
+                    const bool swap = first ? beats(pr[l], id[l], pr[i], id[i]) : beats(pr[i], id[i], pr[l], id[l]);
+                    if (swap) {
+                        const uint32_t ti = id[i];
+                        const uint64_t tp = pr[i];
+                        id[i] = id[l];
+                        pr[i] = pr[l];
+                        id[l] = ti;
+                        pr[l] = tp;
+                    }
+                }
             }
         }
-        pmask[c] = na + nb > 64 ? ~0ull : m;
-        npred[c] = k;
+#pragma unroll
+        for (uint32_t i = 0; i < kShortList; ++i) {
+            if (i < m) {
+                adj[a0 + i] = id[i];
+                set_position(cpack, id[i], (uint32_t)x, i);
+            }
+        }
     }
 }
 
-// Pass 2: the predecessor list of c at preds[poff[c] ..], each entry the
-// predecessor and the high half of its priority.  A contact with
-// predecessors waits on the weakest (it tends to be coloured last, so the
-// contact is examined again fewer times); the others form the first round's
-// direct list.
-__device__ __forceinline__ uint32_t prio_hi(uint64_t p) { return (uint32_t)(p >> 32); }
+__global__ void k_adj_sort_long(int64_t n, const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
+                                uint32_t* __restrict__ adj, const uint64_t* __restrict__ prio, uint4* __restrict__ cpack)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += nw) {
+        if (!finite[x]) continue;   // the same for every lane of the warp
+        const uint32_t a0 = adj_off[x], m = adj_off[x + 1] - a0;
+        if (m <= kShortList) continue;
+        if (m > 32u * kSortSlots) {   // beyond the slots: insertion sort by one lane
+            if (lane == 0) {
+                for (uint32_t i = 1; i < m; ++i) {
+                    const uint32_t c = adj[a0 + i];
+                    const uint64_t pc = prio[c];
+                    uint32_t j = i;
+                    while (j > 0) {
+                        const uint32_t d = adj[a0 + j - 1];
+                        if (!beats(pc, c, prio[d], d)) break;
+                        adj[a0 + j] = d;
+                        --j;
+                    }
+                    adj[a0 + j] = c;
+                }
+                for (uint32_t k = 0; k < m; ++k) set_position(cpack, adj[a0 + k], (uint32_t)x, k);
+            }
+            continue;
+        }
+        uint32_t id[kSortSlots], rk[kSortSlots];
+        uint64_t pr[kSortSlots];
+#pragma unroll
+        for (int k = 0; k < kSortSlots; ++k) {
+            const uint32_t i = lane + 32u * k;
+            id[k] = i < m ? adj[a0 + i] : 0u;
+            rk[k] = 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < kSortSlots; ++k) pr[k] = lane + 32u * k < m ? prio[id[k]] : 0ull;
+#pragma unroll
+        for (int kc = 0; kc < kSortSlots; ++kc) {
+            if (32u * kc >= m) break;
+            const uint32_t cnt = min(32u, m - 32u * kc);
+            for (uint32_t l = 0; l < cnt; ++l) {
+                const uint32_t idj = __shfl_sync(0xffffffffu, id[kc], l);
+                const uint64_t prj = __shfl_sync(0xffffffffu, pr[kc], l);
+#pragma unroll
+                for (int k = 0; k < kSortSlots; ++k)
+                    if (lane + 32u * k < m && beats(prj, idj, pr[k], id[k])) ++rk[k];
+            }
+        }
+        __syncwarp();   // every entry read before any is overwritten
+#pragma unroll
+        for (int k = 0; k < kSortSlots; ++k) {
+            if (lane + 32u * k >= m) continue;
+            adj[a0 + rk[k]] = id[k];
+            set_position(cpack, id[k], (uint32_t)x, rk[k]);
+        }
+    }
+}
 
-__global__ void k_pred_lists(DCount Cc, int64_t n, const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
-                             const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
-                             const uint32_t* __restrict__ adj, const uint64_t* __restrict__ prio,
-                             const uint64_t* __restrict__ pmask, const uint32_t* __restrict__ poff,
-                             uint2* __restrict__ preds, int64_t pcap, uint32_t* whead, uint32_t* __restrict__ wnext,
-                             uint32_t* __restrict__ wl, uint32_t* count)
+// Block-wide append of up to two values per thread to list (cap entries):
+// one counter update per block (a counter every block of a round appends
+// to is contended).  Entries beyond cap set the colour error bit.
+__device__ __forceinline__ void block_push2(uint32_t e0, uint32_t e1, uint32_t* list, uint32_t* count, int64_t cap,
+                                            DevInfo* info)
+{
+    __shared__ uint32_t s_buf[2 * kJpThreads];
+    __shared__ uint32_t s_n, s_base;
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    if (e0 != kUncoloured) s_buf[atomicAdd(&s_n, 1u)] = e0;
+    if (e1 != kUncoloured) s_buf[atomicAdd(&s_n, 1u)] = e1;
+    __syncthreads();
+    const uint32_t k = s_n;
+    if (threadIdx.x == 0) s_base = k ? atomicAdd(count, k) : 0u;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
+        const int64_t idx = (int64_t)s_base + i;
+        if (idx < cap) list[idx] = s_buf[i];
+        else atomicOr(&info->err, kErrColours);
+    }
+    __syncthreads();   // the buffer is refilled by the next call
+}
+
+// The contacts at the front of all their lists from the start (no
+// predecessor) form the first round's list.
+__global__ void k_fr_seed(DCount Cc, const uint4* __restrict__ cpack, uint32_t* __restrict__ wl, uint32_t* count,
+                          DevInfo* info)
 {
     const int64_t C = Cc.get();
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // warp-uniform trip count: every lane takes part in warp_push
-    for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x; c0 < C; c0 += stride) {
+    // block-uniform trip count: every thread takes part in block_push2
+    for (int64_t c0 = blockIdx.x * (int64_t)blockDim.x; c0 < C; c0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = c0 + threadIdx.x;
-        bool direct = false;
+        bool ready = false;
         if (c < C) {
-            uint32_t a0, na, b0, nb;
-            incidence((uint32_t)c, n, cj1, cj2, finite, adj_off, a0, na, b0, nb);
-            const uint32_t p0 = poff[c], np = poff[c + 1] - p0;
-            const uint64_t m = pmask[c];
-            const uint64_t pc = prio[c];
-            uint32_t k = 0, weakest = kUncoloured;
-            uint64_t pweak = ~0ull;
-            for (uint32_t j = 0; j < na + nb && k < np; ++j) {
-                if (m != ~0ull && !((m >> j) & 1ull)) continue;
-                const uint32_t d = incident(adj, a0, na, b0, j);
-                const uint64_t pd = prio[d];
-                if (m == ~0ull && (d == (uint32_t)c || !beats(pd, d, pc, (uint32_t)c))) continue;
-                if (p0 + k < pcap) preds[p0 + k] = make_uint2(d, prio_hi(pd));   // beyond: the error bit is set
-                if (pd < pweak) {
-                    pweak = pd;
-                    weakest = d;
-                }
-                ++k;
-            }
-            if (np == 0) direct = true;
-            else wnext[c] = atomicExch(&whead[weakest], (uint32_t)c);
+            const uint4 q = cpack[c];
+            ready = (q.x == kNoList || q.z == 0u) && (q.y == kNoList || q.w == 0u);
         }
-        warp_push(direct, (uint32_t)c, wl, count, lane, true, (uint32_t)C);
+        block_push2(ready ? (uint32_t)c : kUncoloured, kUncoloured, wl, count, C, info);
     }
 }
 
-// Examination of contact c by a group of 4 lanes (lanes 4g..4g+3 of a
-// warp; every lane of the warp calls this, valid = false for a group with no
-// contact).  The lanes cover the predecessor list, 16 entries per pass, all
-// loads of a pass in flight together.  If a predecessor is still
-// uncoloured, c waits on the weakest such one.  Otherwise c takes the
-// smallest colour none of its predecessors has.  Returns whether c was
-// coloured.
-__device__ bool jp_examine(bool valid, uint32_t c, uint32_t round, int lane, const uint32_t* __restrict__ poff,
-                           const uint2* __restrict__ preds, uint32_t* cstate, uint32_t* whead,
-                           uint32_t* __restrict__ wnext, DevInfo* info)
+// One round over the list `in` (cnt_in entries); the contacts exposed go to
+// `out`.  cnt_clear (the counter two rounds ahead) is zeroed for reuse.
+__device__ __forceinline__ void fr_round(uint32_t round, const uint4* __restrict__ cpack,
+                                         const uint32_t* __restrict__ adj_off, const uint32_t* __restrict__ adj,
+                                         uint32_t* front, uint32_t* mask, const uint32_t* in, uint32_t m, uint32_t* out,
+                                         uint32_t* cnt_out, int64_t cap, uint32_t* cstate, DevInfo* info)
 {
-    const int gl = lane & 3;
-    uint32_t p0 = 0, np = 0;
-    if (valid) {
-        p0 = poff[c];
-        np = poff[c + 1] - p0;
-    }
-    const uint32_t maxnp = __reduce_max_sync(0xffffffffu, np);
-    uint32_t used[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};   // colours taken by predecessors (kMaxColours bits)
-    uint32_t wph = ~0u, wd = kUncoloured;   // weakest uncoloured predecessor seen by this lane
-    for (uint32_t w0 = 0; w0 < maxnp; w0 += 16) {
-        uint2 e[4];
-        uint32_t sd[4];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // block-uniform trip count: every thread takes part in block_push2
+    for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x; t0 < m; t0 += stride) {
+        const int64_t t = t0 + threadIdx.x;
+        uint32_t e0 = kUncoloured, e1 = kUncoloured;
+        if (t < m) {
+            const uint32_t c = in[t];
+            const uint4 q = cpack[c];
+            const uint32_t a = q.x, b = q.y, pa = q.z, pb = q.w;
+            const bool fa = a != kNoList, fb = b != kNoList;
+            const bool ready = (!fa || front_at(__ldcg(front + a), round) == pa) &&
+                               (!fb || front_at(__ldcg(front + b), round) == pb);
+            // an entry exposed twice, or already coloured: the claim fails
+            if (ready && atomicCAS(cstate + c, kUncoloured, kClaimed) == kUncoloured) {
+                const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+                const uint4* ma = reinterpret_cast<const uint4*>(mask + 8 * (int64_t)a);
+                const uint4* mb = reinterpret_cast<const uint4*>(mask + 8 * (int64_t)b);
+                const uint4 a_lo = fa ? __ldcg(ma) : z, a_hi = fa ? __ldcg(ma + 1) : z;
+                const uint4 b_lo = fb ? __ldcg(mb) : z, b_hi = fb ? __ldcg(mb + 1) : z;
+                const uint32_t used[8] = {a_lo.x | b_lo.x, a_lo.y | b_lo.y, a_lo.z | b_lo.z, a_lo.w | b_lo.w,
+                                          a_hi.x | b_hi.x, a_hi.y | b_hi.y, a_hi.z | b_hi.z, a_hi.w | b_hi.w};
+                uint32_t col = kMaxColours;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t j = w0 + 4 * k + gl;
-            e[k] = j < np ? preds[p0 + j] : make_uint2(kUncoloured, 0u);
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) sd[k] = e[k].x != kUncoloured ? cstate[e[k].x] : 0u;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (e[k].x == kUncoloured) continue;
-            if (sd[k] == kUncoloured) {
-                if (wd == kUncoloured || e[k].y < wph) {
-                    wph = e[k].y;
-                    wd = e[k].x;
+                for (int k = 7; k >= 0; --k)
+                    if (~used[k]) col = 32u * k + (__ffs(~used[k]) - 1);
+                if (col >= (uint32_t)kMaxColours) {
+                    atomicOr(&info->err, kErrColours);
+                    col = kMaxColours - 1;
                 }
-            } else {
-                const uint32_t col = sd[k] & 0xFFu;
-#pragma unroll
-                for (int w = 0; w < 8; ++w)
-                    if ((col >> 5) == (uint32_t)w) used[w] |= 1u << (col & 31u);
-            }
-        }
-    }
-    // group reductions (xor 1, 2 stays inside the group)
-#pragma unroll
-    for (int o = 1; o < 4; o <<= 1) {
-        const uint32_t wp2 = __shfl_xor_sync(0xffffffffu, wph, o);
-        const uint32_t wd2 = __shfl_xor_sync(0xffffffffu, wd, o);
-        if (wd2 != kUncoloured && (wd == kUncoloured || wp2 < wph)) {
-            wph = wp2;
-            wd = wd2;
-        }
-#pragma unroll
-        for (int w = 0; w < 8; ++w) used[w] |= __shfl_xor_sync(0xffffffffu, used[w], o);
-    }
-    if (!valid) return false;
-    if (wd != kUncoloured) {
-        if (gl == 0) wnext[c] = atomicExch(&whead[wd], c);
-        return false;
-    }
-    if (gl == 0) {
-        uint32_t col = kMaxColours;
-#pragma unroll
-        for (int w = 7; w >= 0; --w)
-            if (~used[w]) col = 32u * w + (__ffs(~used[w]) - 1);
-        if (col >= kMaxColours) {
-            atomicOr(&info->err, kErrColours);
-            col = kMaxColours - 1;
-        }
-        cstate[c] = (round << 8) | col;   // the round is informational
-    }
-    return true;
-}
-
-// One round, a tile of kJpThreads input entries at a time.  Phase 1, a
-// thread per entry: an entry of L has its waiting list walked, an entry of
-// X is taken as it is; both fill the block's examination buffer (overflow
-// goes to the next round's X).  Phase 2, 4 lanes per buffered contact
-// (jp_examine); the contacts coloured go to the next L.
-constexpr int kJpThreads = 256;
-constexpr int kJpCap = 2048;
-
-// Round `round` over the input lists (tiles of kJpThreads entries, grid-
-// stride).  What other blocks wrote in earlier rounds (lists, counters,
-// states, waiting lists) is visible after the grid barrier between rounds
-// (its acquire fence); the counters are read through L2.
-__device__ __forceinline__ void jp_round(uint32_t round, uint32_t C, const uint32_t* __restrict__ wl_in,
-                                         const uint32_t* cnt_in, uint32_t* __restrict__ wl_out, uint32_t* cnt_out,
-                                         uint32_t* cnt_clear, const uint32_t* __restrict__ poff,
-                                         const uint2* __restrict__ preds, uint32_t* cstate, uint32_t* whead,
-                                         uint32_t* __restrict__ wnext, DevInfo* info)
-{
-    __shared__ uint32_t s_exam[kJpCap];
-    __shared__ uint32_t s_done[kJpCap];
-    __shared__ uint32_t s_nexam, s_ndone, s_base;
-    const uint32_t nl = __ldcg(cnt_in), nx = __ldcg(cnt_in + 1), m = nl + nx;
-    if (blockIdx.x == 0 && threadIdx.x < 2) cnt_clear[threadIdx.x] = 0u;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr uint32_t nwarps = kJpThreads / 32;
-    for (uint32_t base = blockIdx.x * kJpThreads; base < m; base += gridDim.x * kJpThreads) {
-        if (threadIdx.x == 0) {
-            s_nexam = 0;
-            s_ndone = 0;
-        }
-        __syncthreads();
-        const uint32_t k = base + threadIdx.x;
-        if (k < nl) {
-            const uint32_t c = wl_in[k];
-            uint32_t h = whead[c];
-            whead[c] = kUncoloured;
-            while (h != kUncoloured) {
-                const uint32_t i = atomicAdd(&s_nexam, 1u);
-                if (i < kJpCap) {
-                    s_exam[i] = h;
-                } else {
-                    const uint32_t g = atomicAdd(&cnt_out[1], 1u);
-                    wl_out[C - 1u - g] = h;
+                cstate[c] = col;
+                const uint32_t bit = 1u << (col & 31u), wd = col >> 5;
+                // only c, the front of a and of b, writes their masks and fronts
+                if (fa) {
+                    __stcg(mask + 8 * (int64_t)a + wd, __ldcg(mask + 8 * (int64_t)a + wd) | bit);
+                    __stcg(front + a, (round << kFrontBits) | (pa + 1));
+                    const uint32_t a0 = adj_off[a];
+                    if (pa + 1 < adj_off[a + 1] - a0) e0 = adj[a0 + pa + 1];
                 }
-                h = wnext[h];
-            }
-        } else if (k < m) {
-            const uint32_t c = wl_in[C - 1u - (k - nl)];
-            const uint32_t i = atomicAdd(&s_nexam, 1u);
-            if (i < kJpCap) {
-                s_exam[i] = c;
-            } else {
-                const uint32_t g = atomicAdd(&cnt_out[1], 1u);
-                wl_out[C - 1u - g] = c;
+                if (fb) {
+                    __stcg(mask + 8 * (int64_t)b + wd, __ldcg(mask + 8 * (int64_t)b + wd) | bit);
+                    __stcg(front + b, (round << kFrontBits) | (pb + 1));
+                    const uint32_t b0 = adj_off[b];
+                    if (pb + 1 < adj_off[b + 1] - b0) e1 = adj[b0 + pb + 1];
+                }
             }
         }
-        __syncthreads();
-        const uint32_t ne = s_nexam < kJpCap ? s_nexam : kJpCap;
-        for (uint32_t e0 = 8 * warp; e0 < ne; e0 += 8 * nwarps) {
-            const uint32_t e = e0 + (lane >> 2);
-            const bool valid = e < ne;
-            const uint32_t c = valid ? s_exam[e] : 0u;
-            if (jp_examine(valid, c, round, lane, poff, preds, cstate, whead, wnext, info) && (lane & 3) == 0)
-                s_done[atomicAdd(&s_ndone, 1u)] = c;
-        }
-        __syncthreads();
-        const uint32_t nd = s_ndone;
-        if (threadIdx.x == 0) s_base = nd ? atomicAdd(&cnt_out[0], nd) : 0u;
-        __syncthreads();
-        for (uint32_t t = threadIdx.x; t < nd; t += kJpThreads) wl_out[s_base + t] = s_done[t];
-        __syncthreads();   // the shared lists are refilled by the next tile
+        block_push2(e0, e1, out, cnt_out, cap, info);
     }
 }
 
-// One round per launch (the host checks the lists every few rounds).
-__global__ void __launch_bounds__(kJpThreads) k_jp_round(uint32_t round, uint32_t C, const uint32_t* __restrict__ wl_in,
-                                  const uint32_t* __restrict__ cnt_in, uint32_t* __restrict__ wl_out,
-                                  uint32_t* __restrict__ cnt_out, uint32_t* __restrict__ cnt_clear,
-                                  const uint32_t* __restrict__ poff, const uint2* __restrict__ preds,
-                                  uint32_t* cstate, uint32_t* whead, uint32_t* __restrict__ wnext, DevInfo* info)
+// One round per launch (the host checks the list counts every few rounds).
+// The counters rotate through three slots: a round reads one, writes the
+// next and clears the third.
+__global__ void __launch_bounds__(kJpThreads) k_fr_round(uint32_t round, const uint4* __restrict__ cpack,
+                                                         const uint32_t* __restrict__ adj_off,
+                                                         const uint32_t* __restrict__ adj, uint32_t* front,
+                                                         uint32_t* mask, const uint32_t* in, const uint32_t* cnt_in,
+                                                         uint32_t* out, uint32_t* cnt_out, uint32_t* cnt_clear,
+                                                         int64_t cap, uint32_t* cstate, DevInfo* info)
 {
-    __shared__ uint32_t s_exam[kJpCap];
-    __shared__ uint32_t s_done[kJpCap];
-    __shared__ uint32_t s_nexam, s_ndone, s_base;
-    const uint32_t nl = cnt_in[0], nx = cnt_in[1], m = nl + nx;
-    if (blockIdx.x == 0 && threadIdx.x < 2) cnt_clear[threadIdx.x] = 0u;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr uint32_t nwarps = kJpThreads / 32;
-    for (uint32_t base = blockIdx.x * kJpThreads; base < m; base += gridDim.x * kJpThreads) {
-        if (threadIdx.x == 0) {
-            s_nexam = 0;
-            s_ndone = 0;
-        }
-        __syncthreads();
-        const uint32_t k = base + threadIdx.x;
-        if (k < nl) {
-            const uint32_t c = wl_in[k];
-            uint32_t h = whead[c];
-            whead[c] = kUncoloured;
-            while (h != kUncoloured) {
-                const uint32_t i = atomicAdd(&s_nexam, 1u);
-                if (i < kJpCap) {
-                    s_exam[i] = h;
-                } else {
-                    const uint32_t g = atomicAdd(&cnt_out[1], 1u);
-                    wl_out[C - 1u - g] = h;
-                }
-                h = wnext[h];
-            }
-        } else if (k < m) {
-            const uint32_t c = wl_in[C - 1u - (k - nl)];
-            const uint32_t i = atomicAdd(&s_nexam, 1u);
-            if (i < kJpCap) {
-                s_exam[i] = c;
-            } else {
-                const uint32_t g = atomicAdd(&cnt_out[1], 1u);
-                wl_out[C - 1u - g] = c;
-            }
-        }
-        __syncthreads();
-        const uint32_t ne = s_nexam < kJpCap ? s_nexam : kJpCap;
-        for (uint32_t e0 = 8 * warp; e0 < ne; e0 += 8 * nwarps) {
-            const uint32_t e = e0 + (lane >> 2);
-            const bool valid = e < ne;
-            const uint32_t c = valid ? s_exam[e] : 0u;
-            if (jp_examine(valid, c, round, lane, poff, preds, cstate, whead, wnext, info) && (lane & 3) == 0)
-                s_done[atomicAdd(&s_ndone, 1u)] = c;
-        }
-        __syncthreads();
-        const uint32_t nd = s_ndone;
-        if (threadIdx.x == 0) s_base = nd ? atomicAdd(&cnt_out[0], nd) : 0u;
-        __syncthreads();
-        for (uint32_t t = threadIdx.x; t < nd; t += kJpThreads) wl_out[s_base + t] = s_done[t];
-        __syncthreads();   // the shared lists are refilled by the next tile
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *cnt_clear = 0u;
+        if (*cnt_in > 0u) info->rounds = round;   // the last round with work
     }
+    fr_round(round, cpack, adj_off, adj, front, mask, in, *cnt_in, out, cnt_out, cap, cstate, info);
 }
 
 // All rounds in one cooperative launch (no host in the loop, so a step can
-// be captured in a CUDA graph): a grid barrier ends each round (it
-// plays the part of a launch boundary: every waiter registered and every
-// colour written before the next round walks the lists), and the round's
-// output counters, read by every block after the barrier, tell whether
-// anything is left.  A contact count of zero leaves at once; more than
+// be captured in a CUDA graph): a grid barrier ends each round (it plays
+// the part of a launch boundary), and the round's output count, read by
+// every block after the barrier, tells whether anything is left.  More than
 // kJpMaxRounds rounds set the colour error bit.
 constexpr int kJpMaxRounds = 1024;
 
@@ -470,22 +394,22 @@ __device__ __forceinline__ bool jp_barrier(DevInfo* info)
     return ok != 0;
 }
 
-__global__ void __launch_bounds__(kJpThreads) k_jp_persistent(DCount Cc, uint32_t* wl0,
-                                                              uint32_t* wl1, uint32_t* cnt,
-                                                              const uint32_t* __restrict__ poff,
-                                                              const uint2* __restrict__ preds, uint32_t* cstate,
-                                                              uint32_t* whead, uint32_t* __restrict__ wnext,
-                                                              DevInfo* info)
+__global__ void __launch_bounds__(kJpThreads) k_fr_persistent(DCount Cc, const uint4* __restrict__ cpack,
+                                                              const uint32_t* __restrict__ adj_off,
+                                                              const uint32_t* __restrict__ adj, uint32_t* front,
+                                                              uint32_t* mask, uint32_t* wl0, uint32_t* wl1,
+                                                              uint32_t* cnt, uint32_t* cstate, DevInfo* info)
 {
-    const uint32_t C = (uint32_t)Cc.get();
-    if (C == 0 || (info->err & kErrPreds)) return;   // overflowed lists: the colours stay unset (error bit)
+    const int64_t C = Cc.get();
+    if (C == 0) return;
     for (uint32_t round = 1; round <= (uint32_t)kJpMaxRounds; ++round) {
         const int ci = (round - 1) % 3, co = round % 3, cc = (round + 1) % 3;
         const bool odd = (round & 1u) != 0u;   // round 1 reads wl0 and writes wl1, round 2 the reverse, ...
-        jp_round(round, C, odd ? wl0 : wl1, cnt + 2 * ci, odd ? wl1 : wl0, cnt + 2 * co, cnt + 2 * cc, poff, preds,
-                 cstate, whead, wnext, info);
+        if (blockIdx.x == 0 && threadIdx.x == 0) cnt[cc] = 0u;
+        fr_round(round, cpack, adj_off, adj, front, mask, odd ? wl0 : wl1, __ldcg(cnt + ci), odd ? wl1 : wl0,
+                 cnt + co, 2 * C, cstate, info);
         if (!jp_barrier(info)) return;
-        if (__ldcg(cnt + 2 * co) + __ldcg(cnt + 2 * co + 1) == 0u) return;   // nothing coloured or left to examine
+        if (__ldcg(cnt + co) == 0u) return;   // nothing exposed: every contact is coloured
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&info->err, kErrColours);
 }
@@ -604,20 +528,14 @@ __global__ void k_build_sweep(DCount Cc, int64_t n, const uint32_t* __restrict__
     }
 }
 
-// Device-sized steps: predecessor entries beyond the buffer set an error bit.
-__global__ void k_check_preds(DevInfo* info, int64_t pcap)
-{
-    if ((int64_t)info->pred_total > pcap) atomicOr(&info->err, kErrPreds);
-}
-
 // Resident blocks of the cooperative colouring launch (every block must be
 // resident for its grid barriers), looked up once.
-static int jp_blocks(const nbgs_scene* s)
+static int fr_blocks(const nbgs_scene* s)
 {
     static int occ = -1;
     if (occ < 0) {
         int o = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, (const void*)k_jp_persistent, kJpThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, (const void*)k_fr_persistent, kJpThreads, 0);
         cudaGetLastError();
         occ = o > 0 ? o : 1;
     }
@@ -653,7 +571,7 @@ nbgs_status run_colour(nbgs_scene* s)
         const int64_t ninc = s->composite ? s->nb : n;
         cudaMemsetAsync(s->deg, 0, (ninc + 1) * sizeof(uint32_t), st);
         k_colour_init<<<gb, T, 0, st>>>(Cn, ninc, s->cj1, s->cj2, ib1, ib2, finc, s->prm.colour_seed, scene_view(s),
-                                        s->deg, s->cprio, s->cstate);
+                                        s->deg, s->cprio, s->cstate, s->cpack);
         nbgs_status rc = exclusive_scan_u32(s, s->deg, s->adj_off, ninc, nullptr);
         if (rc != NBGS_OK) return rc;
         cudaMemsetAsync(s->deg, 0, (ninc + 1) * sizeof(uint32_t), st);
@@ -668,68 +586,65 @@ nbgs_status run_colour(nbgs_scene* s)
             // the same sweep, so a single colour
             cudaMemsetAsync(s->cstate, 0, C * sizeof(uint32_t), st);
         } else {
-            // predecessor lists (counts, offsets, lists weakest first)
-            k_pred_count<<<gb, T, 0, st>>>(Cn, ninc, ib1, ib2, finc, s->adj_off, s->adj, s->cprio, s->pmask,
-                                           s->colour_key);
-            rc = exclusive_scan_u32(s, s->colour_key, s->poff, Cn, s->device_sized ? &s->info->pred_total : nullptr);
-            if (rc != NBGS_OK) return rc;
-            if (s->device_sized) {
-                // the lists keep their capacity; an overflow sets an error bit
-                k_check_preds<<<1, 1, 0, st>>>(s->info, s->preds_cap);
-            } else {
-                uint32_t total = 0;
-                rc = cuda_check(s, cudaMemcpyAsync(&total, s->poff + C, sizeof(uint32_t), cudaMemcpyDeviceToHost, st),
-                                "colour: predecessor count");
-                if (rc == NBGS_OK) rc = cuda_check(s, cudaStreamSynchronize(st), "colour");
-                if (rc != NBGS_OK) return rc;
-                rc = grow_preds(s, total);
-                if (rc != NBGS_OK) return rc;
-            }
-            // waiting lists empty; round-1 counters (|L| = 0, |X| filled below)
-            cudaMemsetAsync(s->whead, 0xFF, C * sizeof(uint32_t), st);
-            cudaMemsetAsync(s->info->wl_count, 0, sizeof(s->info->wl_count), st);
-            k_pred_lists<<<gb, T, 0, st>>>(Cn, ninc, ib1, ib2, finc, s->adj_off, s->adj, s->cprio, s->pmask,
-                                           s->poff, s->preds, s->preds_cap, s->whead, s->wnext, s->wl[0],
-                                           &s->info->wl_count[1]);
-            if (s->timing) s->phase_launches[1] += 9;
+            // incidence lists in priority order, fronts and masks empty, the
+            // contacts without predecessors as the first round's list
+            uint32_t* front = s->deg;   // scratch again: the degrees are adj_off's differences
+            cudaMemsetAsync(front, 0, (ninc + 1) * sizeof(uint32_t), st);
+            cudaMemsetAsync(s->cmask, 0, 8 * (size_t)(ninc + 1) * sizeof(uint32_t), st);
+            cudaMemsetAsync(s->info->wl_count, 0, 3 * sizeof(uint32_t), st);
+            k_adj_sort_short<<<grid_for(ninc, T, 8, s->num_sms), T, 0, st>>>(ninc, finc, s->adj_off, s->adj,
+                                                                              s->cprio, s->cpack);
+            k_adj_sort_long<<<grid_for(32 * ninc, T, 8, s->num_sms), T, 0, st>>>(ninc, finc, s->adj_off, s->adj,
+                                                                                  s->cprio, s->cpack);
+            k_fr_seed<<<gb, T, 0, st>>>(Cn, s->cpack, s->wl[0], &s->info->wl_count[0], s->info);
+            if (s->timing) s->phase_launches[1] += 5;
             if (s->device_sized) {
                 // all rounds in one cooperative launch (grid barrier between rounds)
                 cudaMemsetAsync(&s->info->barrier_count, 0, 2 * sizeof(uint32_t), st);
-                const int gbr = std::min(jp_blocks(s), grid_for(C, kJpThreads, 8, s->num_sms));
+                const int gbr = std::min(fr_blocks(s), grid_for(C, kJpThreads, 8, s->num_sms));
                 DCount Cd = Cn;
-                uint32_t *wl0 = s->wl[0], *wl1 = s->wl[1], *cnt = s->info->wl_count;
-                void* args[] = {(void*)&Cd, (void*)&wl0, (void*)&wl1, (void*)&cnt, (void*)&s->poff, (void*)&s->preds,
-                                (void*)&s->cstate, (void*)&s->whead, (void*)&s->wnext, (void*)&s->info};
-                rc = cuda_check(s, cudaLaunchCooperativeKernel((const void*)k_jp_persistent, dim3(gbr),
+                uint32_t *wl0 = s->wl[0], *wl1 = s->wl[1], *cnt = s->info->wl_count, *msk = s->cmask;
+                const uint4* cp = s->cpack;
+                void* args[] = {(void*)&Cd, (void*)&cp, (void*)&s->adj_off, (void*)&s->adj, (void*)&front,
+                                (void*)&msk, (void*)&wl0, (void*)&wl1, (void*)&cnt, (void*)&s->cstate, (void*)&s->info};
+                rc = cuda_check(s, cudaLaunchCooperativeKernel((const void*)k_fr_persistent, dim3(gbr),
                                                                dim3(kJpThreads), args, 0, st),
                                 "colour: rounds");
                 if (rc != NBGS_OK) return rc;
                 if (s->timing) s->phase_launches[1] += 2;
             } else {
-                // one launch per round; the host checks the lists every few rounds
+                // one launch per round; the host checks the list counts after as
+                // many rounds as the last colouring took, then every four
                 const int gbr = grid_for(C, kJpThreads, 8, s->num_sms);
                 uint32_t round = 0;
                 int cur = 0;
-                for (int batch = 0; batch < 64; ++batch) {
-                    for (int r = 0; r < 6; ++r) {
+                int batch = std::max(4, s->colour_rounds);
+                for (;;) {
+                    for (int r = 0; r < batch; ++r) {
                         ++round;
                         const int ci = (round - 1) % 3, co = round % 3, cc = (round + 1) % 3;
-                        k_jp_round<<<gbr, kJpThreads, 0, st>>>(round, (uint32_t)C, s->wl[cur],
-                                                               &s->info->wl_count[2 * ci], s->wl[1 - cur],
-                                                               &s->info->wl_count[2 * co], &s->info->wl_count[2 * cc],
-                                                               s->poff, s->preds, s->cstate, s->whead, s->wnext,
-                                                               s->info);
+                        k_fr_round<<<gbr, kJpThreads, 0, st>>>(round, s->cpack, s->adj_off, s->adj, front, s->cmask,
+                                                               s->wl[cur], &s->info->wl_count[ci], s->wl[1 - cur],
+                                                               &s->info->wl_count[co], &s->info->wl_count[cc], 2 * C,
+                                                               s->cstate, s->info);
                         cur = 1 - cur;
                     }
-                    if (s->timing) s->phase_launches[1] += 6;
-                    uint32_t left[2] = {0, 0};
-                    rc = cuda_check(s, cudaMemcpyAsync(left, &s->info->wl_count[2 * (round % 3)], 2 * sizeof(uint32_t),
-                                                       cudaMemcpyDeviceToHost, st), "colour: worklist");
+                    if (s->timing) s->phase_launches[1] += batch;
+                    uint32_t left = 0, used = 0;
+                    rc = cuda_check(s, cudaMemcpyAsync(&left, &s->info->wl_count[round % 3], sizeof(uint32_t),
+                                                       cudaMemcpyDeviceToHost, st), "colour: list count");
+                    if (rc == NBGS_OK)
+                        rc = cuda_check(s, cudaMemcpyAsync(&used, &s->info->rounds, sizeof(uint32_t),
+                                                           cudaMemcpyDeviceToHost, st), "colour: rounds");
                     if (rc != NBGS_OK) return rc;
                     rc = cuda_check(s, cudaStreamSynchronize(st), "colour");
                     if (rc != NBGS_OK) return rc;
-                    if (left[0] + left[1] == 0) break;
-                    if (batch == 63) return fail(s, NBGS_ETIMEOUT, "colour: did not finish in 384 rounds");
+                    if (left == 0) {
+                        s->colour_rounds = (int)used + 1;
+                        break;
+                    }
+                    if (round >= (uint32_t)kJpMaxRounds) return fail(s, NBGS_ETIMEOUT, "colour: did not finish in 1024 rounds");
+                    batch = 4;
                 }
             }
         }

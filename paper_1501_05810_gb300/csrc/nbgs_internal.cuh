@@ -40,8 +40,7 @@ enum : uint32_t {
     kErrColours = 4u,     // more than kMaxColours colours
     kErrTimeout = 8u,     // a grid barrier wait gave up
     kErrNaN = 16u,        // NaN / Inf in velocities or positions
-    kErrGrid = 32u,       // periodic axis with fewer than 3 cells
-    kErrPreds = 64u       // colouring predecessor lists beyond their buffer (device-sized steps)
+    kErrGrid = 32u        // periodic axis with fewer than 3 cells
 };
 
 // A count that the host either knows (dev == nullptr: v is the count) or
@@ -141,7 +140,6 @@ struct DevInfo {
     uint32_t rounds;                 // colouring rounds used
     uint32_t n_shared;               // subdomains: bodies with more than one velocity instance
     uint32_t n_extra;                // subdomains: velocity instances after the n bodies
-    uint32_t pred_total;             // colouring: predecessor entries of the step
     uint32_t prev_contacts;          // contacts of the previous step (device-sized steps)
     unsigned long long updates;      // contact updates (contacts x sweeps relaxed) since the last read
     double residual;                 // R of the last sweep
@@ -443,12 +441,9 @@ struct nbgs_scene {
     uint32_t* adj = nullptr;       // 2 ccap
     uint32_t* cstate = nullptr;    // (round << 8) | colour, kUncoloured before
     uint64_t* cprio = nullptr;
-    uint64_t* pmask = nullptr;     // colouring: predecessor bits over the incidence entries
-    uint32_t* whead = nullptr;     // colouring: head of a contact's waiting list
-    uint32_t* wnext = nullptr;     // colouring: next contact on the same waiting list
-    uint32_t* poff = nullptr;      // colouring: predecessor list offsets (C + 1)
-    uint2* preds = nullptr;        // colouring: predecessor lists (contact, high half of its priority)
-    int64_t preds_cap = 0;
+    uint4* cpack = nullptr;        // colouring: per contact (body 1, body 2 or none, its positions in their lists)
+    uint32_t* cmask = nullptr;     // colouring: 8 x 32 colour bits per body (its coloured prefix)
+    int colour_rounds = 0;         // rounds the last colouring took (the host checks after as many)
     uint32_t* wl[2] = {nullptr, nullptr};
     uint32_t* colour_key = nullptr;   // colour per contact (sort key)
     uint32_t* colour_key2 = nullptr;
@@ -519,7 +514,7 @@ struct nbgs_scene {
     int32_t g_sweeps = -1;
     double g_tol = -1.0;
     int g_next = 0;                // graph of the next replay
-    int64_t g_ccap = -1, g_pcap = -1;   // capacities the graphs were captured with
+    int64_t g_ccap = -1;   // contact capacity the graphs were captured with
     bool counts_stale = false;     // graphs ran since the host last read the counts
     // timing
     bool timing = false;
@@ -581,7 +576,6 @@ nbgs_status exclusive_scan_u32(nbgs_scene* s, const uint32_t* in, uint32_t* out,
 nbgs_status radix_sort_pairs(nbgs_scene* s, uint32_t*& keys, uint32_t*& vals, uint32_t*& keys_alt,
                              uint32_t*& vals_alt, DCount n, int bits);
 int grid_for(int64_t work, int threads, int max_blocks_per_sm, int num_sms);
-nbgs_status grow_preds(nbgs_scene* s, int64_t need);
 // The contact count of the current step for kernels: host-known, or read on
 // the device (device-sized steps; launches sized for the capacity).
 inline DCount contact_count(const nbgs_scene* s)
