@@ -267,8 +267,8 @@ nbgs_status nbgs_batch_step(nbgs_scene* scene, int32_t max_sweeps, double tol, i
  * does, with device-sized launches: the contact count stays on the device,
  * the colouring rounds run in one cooperative launch, and the buffers keep
  * the capacities they had at capture (contacts: the capacity the last
- * nbgs_step left, at least contacts_per_body per body; predecessor lists of
- * the colouring: six per contact).  A step that needs more sets an error
+ * nbgs_step left, at least contacts_per_body per body).  A step that needs
+ * more sets an error
  * bit and the next synchronising call returns NBGS_ECAPACITY (take ordinary
  * nbgs_step calls then, which grow the buffers).  The first call, and any
  * call with other max_sweeps or tol or after the buffers grew, captures the

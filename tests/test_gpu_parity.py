@@ -327,10 +327,9 @@ def test_sphere_rests_in_cone_on_gpu(nb):
 
 
 def test_colouring_buffers_grow_between_steps(nb, oracle_mod):
-    """A step with few contacts sizes the colouring's predecessor lists;
-    the next step has many more contacts (large hulls), so the lists
-    outgrow the buffer on the device and the colouring is redone with a
-    larger one: the result still equals the oracle's."""
+    """A step with few contacts sizes the contact buffers; the next step
+    has many more contacts (large hulls), so the buffers grow (the
+    colouring's lists with them): the result still equals the oracle's."""
     sc = scenes.config1(0)
     g, o = _pair(nb, oracle_mod, sc)
     sg, so, bo = _step_and_compare(g, o, 20)
