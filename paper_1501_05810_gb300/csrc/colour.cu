@@ -453,11 +453,20 @@ __global__ void k_colour_offsets(const uint32_t* __restrict__ col_count, uint32_
     }
 }
 
-// Sweep record s <- canonical contact perm[s]; initial impulse from the
+// Slot of every canonical contact in colour order: the inverse of perm.
+__global__ void k_invert(DCount Cc, const uint32_t* __restrict__ perm, uint32_t* __restrict__ inv)
+{
+    const int64_t C = Cc.get();
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < C; s += (int64_t)gridDim.x * blockDim.x)
+        inv[perm[s]] = (uint32_t)s;
+}
+
+// Sweep record inv[c] <- canonical contact c; initial impulse from the
 // previous step (world frame, re-projected onto the new frame and the cone)
-// or zero.
+// or zero.  A thread per canonical contact: the contact arrays and the
+// previous step's rows are read in order, the records written scattered.
 template <class R>
-__global__ void k_build_sweep(DCount Cc, int64_t n, const uint32_t* __restrict__ perm, const uint32_t* __restrict__ cj1,
+__global__ void k_build_sweep(DCount Cc, int64_t n, const uint32_t* __restrict__ inv, const uint32_t* __restrict__ cj1,
                               const uint32_t* __restrict__ cj2, const uint32_t* __restrict__ inst,
                               const double4_32a* __restrict__ cgeo,
                               const double2* __restrict__ clev, double dt, double beta, double mu_all, SceneView V,
@@ -467,8 +476,8 @@ __global__ void k_build_sweep(DCount Cc, int64_t n, const uint32_t* __restrict__
                               R4<R>* __restrict__ p)
 {
     const int64_t C = Cc.get();
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < C; s += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = perm[s];
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = inv[c];
         const uint32_t a = cj1[c], b = cj2[c];
         // the velocity records the sweep reads: the bodies, or with subdomains
         // their instances for the contact's subdomain
@@ -660,17 +669,21 @@ nbgs_status run_colour(nbgs_scene* s)
         if (v0 != s->perm) return fail(s, NBGS_EINVAL, "colour: permutation buffer mix-up");
         s->colour_sorted = k0;
         const int warm = (s->prm.warm_start != NBGS_WARM_NONE && s->have_prev) ? 1 : 0;
+        // the slots of the canonical contacts (perm_in is free after the sort;
+        // the records and the solve's finish read it)
+        k_invert<<<gb, T, 0, st>>>(Cn, s->perm, s->perm_in);
+        if (s->timing) s->phase_launches[1] += 1;
         if (s->composite) {
             rc = run_comp_records(s, warm);
             if (rc != NBGS_OK) return rc;
         } else if (s->fp32)
-            k_build_sweep<float><<<gb, T, 0, st>>>(Cn, n, s->perm, s->cj1, s->cj2, sub ? s->inst : nullptr, s->cgeo,
+            k_build_sweep<float><<<gb, T, 0, st>>>(Cn, n, s->perm_in, s->cj1, s->cj2, sub ? s->inst : nullptr, s->cgeo,
                                                    s->clev, s->prm.dt,
                                                    s->prm.beta, s->prm.mu, scene_view(s), warm, s->prev_row_off,
                                                    s->prev_j2,
                                                    s->prev_P, s->ccap, (SweepRec<float>*)s->srec, (float4*)s->sp);
         else
-            k_build_sweep<double><<<gb, T, 0, st>>>(Cn, n, s->perm, s->cj1, s->cj2, sub ? s->inst : nullptr, s->cgeo,
+            k_build_sweep<double><<<gb, T, 0, st>>>(Cn, n, s->perm_in, s->cj1, s->cj2, sub ? s->inst : nullptr, s->cgeo,
                                                     s->clev, s->prm.dt,
                                                     s->prm.beta, s->prm.mu, scene_view(s), warm, s->prev_row_off,
                                                     s->prev_j2,

@@ -448,7 +448,7 @@ struct nbgs_scene {
     uint32_t* colour_key = nullptr;   // colour per contact (sort key)
     uint32_t* colour_key2 = nullptr;
     uint32_t* perm = nullptr;      // sweep slot -> canonical index
-    uint32_t* perm_in = nullptr;
+    uint32_t* perm_in = nullptr;   // the sort's input, then canonical index -> sweep slot (perm inverted)
     uint32_t* col_count = nullptr; // kMaxColours + 1
     uint32_t* col_off = nullptr;   // kMaxColours + 1
     uint32_t* colour_sorted = nullptr;  // colour of each sweep slot (points into colour_key / colour_key2)

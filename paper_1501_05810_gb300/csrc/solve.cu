@@ -1172,13 +1172,13 @@ __global__ void k_scene_vref(int64_t S, const unsigned long long* __restrict__ v
 // Canonical impulses (contact frame) and world-frame impulses for the next
 // warm start.
 template <class R>
-__global__ void k_finish(DCount Cc, const uint32_t* __restrict__ perm, const R4<R>* __restrict__ p,
+__global__ void k_finish(DCount Cc, const uint32_t* __restrict__ inv, const R4<R>* __restrict__ p,
                          const double4_32a* __restrict__ cgeo, double4_32a* __restrict__ cimp, double4_32a* __restrict__ cworld)
 {
     const int64_t C = Cc.get();
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < C; s += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = perm[s];
-        const R4<R> q = p[s];
+    // a thread per canonical contact: only the impulse is read scattered
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        const R4<R> q = p[inv[c]];
         const double4_32a g = cgeo[c];
         double tx, ty, tz, ox, oy, oz;
         tangent_basis<double>(g.x, g.y, g.z, tx, ty, tz, ox, oy, oz);
@@ -1452,10 +1452,10 @@ nbgs_status run_solve(nbgs_scene* s, int max_sweeps, double tol)
     if (C > 0) {
         const int T = 256;
         if (s->fp32)
-            k_finish<float><<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(contact_count(s), s->perm, (const float4*)s->sp, s->cgeo,
+            k_finish<float><<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(contact_count(s), s->perm_in, (const float4*)s->sp, s->cgeo,
                                                                          s->cimp, s->cworld);
         else
-            k_finish<double><<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(contact_count(s), s->perm, (const double4_32a*)s->sp, s->cgeo,
+            k_finish<double><<<grid_for(C, T, 8, s->num_sms), T, 0, st>>>(contact_count(s), s->perm_in, (const double4_32a*)s->sp, s->cgeo,
                                                                           s->cimp, s->cworld);
     }
     if (C > 0 && !s->composite)
