@@ -133,14 +133,25 @@ __device__ __forceinline__ void set_position(uint4* cpack, uint32_t c, uint32_t 
     q[q[0] == x ? 2 : 3] = k;
 }
 
+// Also empties the front and colour mask of every body with a list (the
+// rounds read no other body's) and collects the bodies with long lists.
 __global__ void k_adj_sort_short(int64_t n, const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
                                  uint32_t* __restrict__ adj, const uint64_t* __restrict__ prio,
-                                 uint4* __restrict__ cpack)
+                                 uint4* __restrict__ cpack, uint32_t* __restrict__ front, uint32_t* __restrict__ mask,
+                                 uint32_t* __restrict__ longs, uint32_t* n_long)
 {
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
         if (!finite[x]) continue;
         const uint32_t a0 = adj_off[x], m = adj_off[x + 1] - a0;
-        if (m > kShortList || m == 0) continue;
+        if (m == 0) continue;
+        front[x] = 0u;
+        uint4* mk = reinterpret_cast<uint4*>(mask + 8 * x);
+        mk[0] = make_uint4(0u, 0u, 0u, 0u);
+        mk[1] = make_uint4(0u, 0u, 0u, 0u);
+        if (m > kShortList) {
+            longs[atomicAdd(n_long, 1u)] = (uint32_t)x;
+            continue;
+        }
         uint32_t id[kShortList];
         uint64_t pr[kShortList];
 #pragma unroll
@@ -179,15 +190,15 @@ __global__ void k_adj_sort_short(int64_t n, const uint8_t* __restrict__ finite, 
     }
 }
 
-__global__ void k_adj_sort_long(int64_t n, const uint8_t* __restrict__ finite, const uint32_t* __restrict__ adj_off,
-                                uint32_t* __restrict__ adj, const uint64_t* __restrict__ prio, uint4* __restrict__ cpack)
+__global__ void k_adj_sort_long(const uint32_t* __restrict__ longs, const uint32_t* __restrict__ n_long,
+                                const uint32_t* __restrict__ adj_off, uint32_t* __restrict__ adj,
+                                const uint64_t* __restrict__ prio, uint4* __restrict__ cpack)
 {
     const uint32_t lane = threadIdx.x & 31u;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += nw) {
-        if (!finite[x]) continue;   // the same for every lane of the warp
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5, nl = *n_long;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nl; k += nw) {
+        const uint32_t x = longs[k];   // the same for every lane of the warp
         const uint32_t a0 = adj_off[x], m = adj_off[x + 1] - a0;
-        if (m <= kShortList) continue;
         if (m > 32u * kSortSlots) {   // beyond the slots: insertion sort by one lane
             if (lane == 0) {
                 for (uint32_t i = 1; i < m; ++i) {
@@ -597,14 +608,14 @@ nbgs_status run_colour(nbgs_scene* s)
         } else {
             // incidence lists in priority order, fronts and masks empty, the
             // contacts without predecessors as the first round's list
-            uint32_t* front = s->deg;   // scratch again: the degrees are adj_off's differences
-            cudaMemsetAsync(front, 0, (ninc + 1) * sizeof(uint32_t), st);
-            cudaMemsetAsync(s->cmask, 0, 8 * (size_t)(ninc + 1) * sizeof(uint32_t), st);
-            cudaMemsetAsync(s->info->wl_count, 0, 3 * sizeof(uint32_t), st);
+            uint32_t* front = s->deg;   // scratch again (the degrees are adj_off's differences); emptied per body below
+            // (the bodies with long lists go to wl[1], counted in wl_count[3])
+            cudaMemsetAsync(s->info->wl_count, 0, 4 * sizeof(uint32_t), st);
             k_adj_sort_short<<<grid_for(ninc, T, 8, s->num_sms), T, 0, st>>>(ninc, finc, s->adj_off, s->adj,
-                                                                              s->cprio, s->cpack);
-            k_adj_sort_long<<<grid_for(32 * ninc, T, 8, s->num_sms), T, 0, st>>>(ninc, finc, s->adj_off, s->adj,
-                                                                                  s->cprio, s->cpack);
+                                                                              s->cprio, s->cpack, front, s->cmask,
+                                                                              s->wl[1], &s->info->wl_count[3]);
+            k_adj_sort_long<<<2 * s->num_sms, T, 0, st>>>(s->wl[1], &s->info->wl_count[3], s->adj_off, s->adj,
+                                                           s->cprio, s->cpack);
             k_fr_seed<<<gb, T, 0, st>>>(Cn, s->cpack, s->wl[0], &s->info->wl_count[0], s->info);
             if (s->timing) s->phase_launches[1] += 5;
             if (s->device_sized) {
