@@ -115,6 +115,21 @@ template <> __device__ __forceinline__ float tab_sin<float>(int k) { return c_si
 template <> __device__ __forceinline__ double tab_cos<double>(int k) { return c_cos64[k]; }
 template <> __device__ __forceinline__ double tab_sin<double>(int k) { return c_sin64[k]; }
 
+// cos and sin of an angle th in [0, 2 pi]: in FP32 the hardware
+// approximations on th moved into [-pi, pi] (their absolute error there is
+// below 2^-21, far inside what an FP32 sweep resolves; the root found is
+// the root of g to that accuracy), in FP64 the library's sincos.
+template <class R>
+__device__ __forceinline__ void slide_sincos(R th, R& sn, R& cs)
+{
+    if constexpr (sizeof(R) == 4) {
+        const float t = th > 3.14159265f ? th - 6.28318531f : th;
+        __sincosf(t, &sn, &cs);
+    } else {
+        sincos(th, &sn, &cs);
+    }
+}
+
 // g(th) of the sliding condition, expanded in c = cos th, s = sin th.
 template <class R>
 __device__ __forceinline__ R slide_g(const R co[5], R c, R s)
@@ -136,8 +151,7 @@ __device__ __forceinline__ R slide_root(const R co[5], int k, R glo, R ghi, R dt
     R th = lo + (hi - lo) * (glo / (glo - ghi));
     for (int it = 0; it < kIter; ++it) {
         R sn, cs;
-        if constexpr (sizeof(R) == 4) sincosf(th, &sn, &cs);
-        else sincos(th, &sn, &cs);
+        slide_sincos(th, sn, cs);
         const R g = slide_g(co, cs, sn);
         if (g == R(0)) break;
         if ((g < R(0)) == (gl < R(0))) {
@@ -166,8 +180,7 @@ __device__ __forceinline__ void slide_candidate(const Sym3<R>& W, R mu, const R 
                                                 R p[3])
 {
     R sn, cs, D, vt, vo;
-    if constexpr (sizeof(R) == 4) sincosf(th, &sn, &cs);
-    else sincos(th, &sn, &cs);
+    slide_sincos(th, sn, cs);
     slide_dut(W, mu, b, cs, sn, D, vt, vo);
     if (!(D > R(0)) || cs * vt + sn * vo > R(0)) return;
     const R pn = -b[0] / D;
