@@ -614,7 +614,7 @@ nbgs_status run_colour(nbgs_scene* s)
             k_adj_sort_short<<<grid_for(ninc, T, 8, s->num_sms), T, 0, st>>>(ninc, finc, s->adj_off, s->adj,
                                                                               s->cprio, s->cpack, front, s->cmask,
                                                                               s->wl[1], &s->info->wl_count[3]);
-            k_adj_sort_long<<<2 * s->num_sms, T, 0, st>>>(s->wl[1], &s->info->wl_count[3], s->adj_off, s->adj,
+            k_adj_sort_long<<<8 * s->num_sms, T, 0, st>>>(s->wl[1], &s->info->wl_count[3], s->adj_off, s->adj,
                                                            s->cprio, s->cpack);
             k_fr_seed<<<gb, T, 0, st>>>(Cn, s->cpack, s->wl[0], &s->info->wl_count[0], s->info);
             if (s->timing) s->phase_launches[1] += 5;
