@@ -349,6 +349,9 @@ __global__ void k_comp_anchor(int64_t nb, const uint32_t* __restrict__ bfirst, c
 }
 
 // Sweep record of slot s (contact perm[s]) and its initial impulse.
+// Component k of the normal of a contact's geometry record.
+__device__ __forceinline__ double g_comp(const double4_32a& g, int k) { return k == 0 ? g.x : (k == 1 ? g.y : g.z); }
+
 template <class R>
 __global__ void k_comp_records(int64_t C, int64_t nm, const uint32_t* __restrict__ perm,
                                const uint32_t* __restrict__ cj1, const uint32_t* __restrict__ cj2,
@@ -368,42 +371,48 @@ __global__ void k_comp_records(int64_t C, int64_t nm, const uint32_t* __restrict
         const uint32_t B = hasB ? mbody[mbm] : 0xFFFFFFFFu;
         const double4_32a g = cgeo[c];
         const double2 l = clev[c];
-        const double n[3] = {g.x, g.y, g.z};
-        double t[3], o[3];
-        tangent_basis<double>(n[0], n[1], n[2], t[0], t[1], t[2], o[0], o[1], o[2]);
+        // the block and the levers in the sweep's precision R (FP64 arithmetic
+        // is scarce on this GPU; an FP32 sweep reads them in FP32 anyway), in
+        // the frame the sweep builds from the normal as stored
+        const R n[3] = {(R)g.x, (R)g.y, (R)g.z};
+        R t[3], o[3];
+        tangent_basis<R>(n[0], n[1], n[2], t[0], t[1], t[2], o[0], o[1], o[2]);
         // levers from the centres of mass to x_hat: R_A d_a - l_a n, R_B d_b + l_b n
         double Rm[3][3];
         quat_rows(bquat[A], Rm);
         const double4_32a da = moff[ma];
-        double lA[3], lB[3] = {0.0, 0.0, 0.0};
-        for (int k = 0; k < 3; ++k) lA[k] = (Rm[k][0] * da.x + Rm[k][1] * da.y + Rm[k][2] * da.z) - l.x * n[k];
+        R lA[3], lB[3] = {R(0), R(0), R(0)};
+        for (int k = 0; k < 3; ++k)
+            lA[k] = (R)((Rm[k][0] * da.x + Rm[k][1] * da.y + Rm[k][2] * da.z) - l.x * g_comp(g, k));
         if (hasB) {
             quat_rows(bquat[B], Rm);
             const double4_32a db = moff[mbm];
-            for (int k = 0; k < 3; ++k) lB[k] = (Rm[k][0] * db.x + Rm[k][1] * db.y + Rm[k][2] * db.z) + l.y * n[k];
+            for (int k = 0; k < 3; ++k)
+                lB[k] = (R)((Rm[k][0] * db.x + Rm[k][1] * db.y + Rm[k][2] * db.z) + l.y * g_comp(g, k));
         }
         // W = sum 1/m 1 - [l]x I^-1 [l]x, then W_c = F^T W F, F = [n t o]
-        double Wd[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        R Wd[3][3] = {{R(0), R(0), R(0)}, {R(0), R(0), R(0)}, {R(0), R(0), R(0)}};
         for (int body = 0; body < (hasB ? 2 : 1); ++body) {
             const uint32_t id = body == 0 ? A : B;
-            const double im = binvm[id];
-            if (!(im > 0.0)) continue;
-            const double* I6 = bIinv + 6 * id;
-            const double* lv = body == 0 ? lA : lB;
+            const R im = (R)binvm[id];
+            if (!(im > R(0))) continue;
+            const double* I6d = bIinv + 6 * id;
+            const R I6[6] = {(R)I6d[0], (R)I6d[1], (R)I6d[2], (R)I6d[3], (R)I6d[4], (R)I6d[5]};
+            const R* lv = body == 0 ? lA : lB;
             for (int col = 0; col < 3; ++col) {
-                double e[3] = {0.0, 0.0, 0.0}, lxe[3], Il[3], cc[3];
-                e[col] = 1.0;
+                R e[3] = {R(0), R(0), R(0)}, lxe[3], Il[3], cc[3];
+                e[col] = R(1);
                 cross(lv, e, lxe);
                 sym_mul(I6, lxe, Il);
                 cross(Il, lv, cc);
-                for (int r = 0; r < 3; ++r) Wd[r][col] += (r == col ? im : 0.0) + cc[r];
+                for (int r = 0; r < 3; ++r) Wd[r][col] += (r == col ? im : R(0)) + cc[r];
             }
         }
-        const double* F[3] = {n, t, o};
-        double Wc[3][3];
+        const R* F[3] = {n, t, o};
+        R Wc[3][3];
         for (int x = 0; x < 3; ++x)
             for (int y = 0; y < 3; ++y) {
-                double acc = 0.0;
+                R acc = R(0);
                 for (int r = 0; r < 3; ++r) acc += F[x][r] * (Wd[r][0] * F[y][0] + Wd[r][1] * F[y][1] + Wd[r][2] * F[y][2]);
                 Wc[x][y] = acc;
             }
