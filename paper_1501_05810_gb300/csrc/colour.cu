@@ -190,6 +190,44 @@ __global__ void k_adj_sort_short(int64_t n, const uint8_t* __restrict__ finite, 
     }
 }
 
+// One list of m entries (m <= 32 K) by the warp: lane l holds entries l,
+// l + 32, ...; an entry's position is the number of entries that beat it.
+template <int K>
+__device__ __forceinline__ void warp_sort_list(uint32_t x, uint32_t a0, uint32_t m, uint32_t lane,
+                                               uint32_t* __restrict__ adj, const uint64_t* __restrict__ prio,
+                                               uint4* __restrict__ cpack)
+{
+    uint32_t id[K], rk[K];
+    uint64_t pr[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const uint32_t i = lane + 32u * k;
+        id[k] = i < m ? adj[a0 + i] : 0u;
+        rk[k] = 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) pr[k] = lane + 32u * k < m ? prio[id[k]] : 0ull;
+#pragma unroll
+    for (int kc = 0; kc < K; ++kc) {
+        if (32u * kc >= m) break;
+        const uint32_t cnt = min(32u, m - 32u * kc);
+        for (uint32_t l = 0; l < cnt; ++l) {
+            const uint32_t idj = __shfl_sync(0xffffffffu, id[kc], l);
+            const uint64_t prj = __shfl_sync(0xffffffffu, pr[kc], l);
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (lane + 32u * k < m && beats(prj, idj, pr[k], id[k])) ++rk[k];
+        }
+    }
+    __syncwarp();   // every entry read before any is overwritten
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (lane + 32u * k >= m) continue;
+        adj[a0 + rk[k]] = id[k];
+        set_position(cpack, id[k], x, rk[k]);
+    }
+}
+
 __global__ void k_adj_sort_long(const uint32_t* __restrict__ longs, const uint32_t* __restrict__ n_long,
                                 const uint32_t* __restrict__ adj_off, uint32_t* __restrict__ adj,
                                 const uint64_t* __restrict__ prio, uint4* __restrict__ cpack)
@@ -199,52 +237,24 @@ __global__ void k_adj_sort_long(const uint32_t* __restrict__ longs, const uint32
     for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nl; k += nw) {
         const uint32_t x = longs[k];   // the same for every lane of the warp
         const uint32_t a0 = adj_off[x], m = adj_off[x + 1] - a0;
-        if (m > 32u * kSortSlots) {   // beyond the slots: insertion sort by one lane
-            if (lane == 0) {
-                for (uint32_t i = 1; i < m; ++i) {
-                    const uint32_t c = adj[a0 + i];
-                    const uint64_t pc = prio[c];
-                    uint32_t j = i;
-                    while (j > 0) {
-                        const uint32_t d = adj[a0 + j - 1];
-                        if (!beats(pc, c, prio[d], d)) break;
-                        adj[a0 + j] = d;
-                        --j;
-                    }
-                    adj[a0 + j] = c;
+        if (m <= 32u) warp_sort_list<1>(x, a0, m, lane, adj, prio, cpack);
+        else if (m <= 64u) warp_sort_list<2>(x, a0, m, lane, adj, prio, cpack);
+        else if (m <= 128u) warp_sort_list<4>(x, a0, m, lane, adj, prio, cpack);
+        else if (m <= 32u * kSortSlots) warp_sort_list<kSortSlots>(x, a0, m, lane, adj, prio, cpack);
+        else if (lane == 0) {   // beyond the slots: insertion sort by one lane
+            for (uint32_t i = 1; i < m; ++i) {
+                const uint32_t c = adj[a0 + i];
+                const uint64_t pc = prio[c];
+                uint32_t j = i;
+                while (j > 0) {
+                    const uint32_t d = adj[a0 + j - 1];
+                    if (!beats(pc, c, prio[d], d)) break;
+                    adj[a0 + j] = d;
+                    --j;
                 }
-                for (uint32_t k = 0; k < m; ++k) set_position(cpack, adj[a0 + k], (uint32_t)x, k);
+                adj[a0 + j] = c;
             }
-            continue;
-        }
-        uint32_t id[kSortSlots], rk[kSortSlots];
-        uint64_t pr[kSortSlots];
-#pragma unroll
-        for (int k = 0; k < kSortSlots; ++k) {
-            const uint32_t i = lane + 32u * k;
-            id[k] = i < m ? adj[a0 + i] : 0u;
-            rk[k] = 0u;
-        }
-#pragma unroll
-        for (int k = 0; k < kSortSlots; ++k) pr[k] = lane + 32u * k < m ? prio[id[k]] : 0ull;
-#pragma unroll
-        for (int kc = 0; kc < kSortSlots; ++kc) {
-            if (32u * kc >= m) break;
-            const uint32_t cnt = min(32u, m - 32u * kc);
-            for (uint32_t l = 0; l < cnt; ++l) {
-                const uint32_t idj = __shfl_sync(0xffffffffu, id[kc], l);
-                const uint64_t prj = __shfl_sync(0xffffffffu, pr[kc], l);
-#pragma unroll
-                for (int k = 0; k < kSortSlots; ++k)
-                    if (lane + 32u * k < m && beats(prj, idj, pr[k], id[k])) ++rk[k];
-            }
-        }
-        __syncwarp();   // every entry read before any is overwritten
-#pragma unroll
-        for (int k = 0; k < kSortSlots; ++k) {
-            if (lane + 32u * k >= m) continue;
-            adj[a0 + rk[k]] = id[k];
-            set_position(cpack, id[k], (uint32_t)x, rk[k]);
+            for (uint32_t q = 0; q < m; ++q) set_position(cpack, adj[a0 + q], x, q);
         }
     }
 }
