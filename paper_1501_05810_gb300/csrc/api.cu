@@ -446,7 +446,8 @@ static nbgs_status create_common(const nbgs_params* params, const nbgs_batch_des
     s->ccap = std::max<int64_t>(1024, (int64_t)cpb * n);
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
 
-    bool ok = take(s, s->pos_r, nn) && take(s, s->quat, nn) && take(s, s->hull, nn) && take(s, s->p32, nn) &&
+    bool ok = take(s, s->pos_r, nn) && take(s, s->quat, nn) && take(s, s->hull, nn) && take(s, s->hvw, nn) &&
+              take(s, s->p32, nn) &&
               take(s, s->p32s, nn) && take(s, s->finite, nn) &&
               take(s, s->stage, 13 * nn) && take(s, s->cell_start, (size_t)s->max_cells + 1) &&
               take(s, s->cell_end, (size_t)s->max_cells) && take(s, s->keys[0], nn) && take(s, s->keys[1], nn) &&
@@ -578,7 +579,7 @@ void nbgs_destroy_scene(nbgs_scene* s)
     if (!s) return;
     cudaStreamSynchronize(s->stream);
     drop_graphs(s);
-    void* ps[] = {s->pos_r, s->quat, s->vel, s->hull, s->p32, s->p32s, s->finite, s->stage, s->cell_start,
+    void* ps[] = {s->pos_r, s->quat, s->vel, s->hull, s->hvw, s->p32, s->p32s, s->finite, s->stage, s->cell_start,
                   s->cell_end, s->keys[0], s->keys[1], s->vals[0], s->vals[1], s->radix_hist, s->scan_tmp,
                   s->cand, s->sph_cnt, s->row_cnt, s->row_off, s->prev_row_off, s->deg, s->adj_off,
                   s->col_count, s->col_off, s->info, s->dep, s->prog, s->cstart, s->scene_of, s->scene_off,

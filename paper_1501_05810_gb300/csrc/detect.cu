@@ -410,54 +410,77 @@ __global__ void k_member_update(int64_t n, const uint32_t* __restrict__ mbody, c
     if (bad) atomicOr(&info->err, kErrNaN);
 }
 
+// Hull radius of eq. (expansionradius), h = dt (|v| + |w| r) + tau, rounded
+// as the FP64 step computes it: for a sphere from the squares of |v| and |w|
+// stored by k_hull (so that only the contacts that need the exact value pay
+// for its two square roots), for a composite member from the member hulls.
+struct HullView {
+    const double* hull;   // member hulls (composites), else null
+    const double2* vw;    // |v|^2, |w|^2 per sphere
+    double dt, tau;
+};
+__device__ __forceinline__ double hull_of(const HullView& H, uint32_t x, double r)
+{
+    if (H.hull) return H.hull[x];
+    const double2 q = H.vw[x];
+    return xadd(xmul(H.dt, xadd(xsqrt(q.x), xmul(xsqrt(q.y), r))), H.tau);
+}
+
+// Per sphere: |v|^2 and |w|^2 in FP64 (the exact hull's inputs), the FP32
+// position relative to the box corner and the reach r + h with h in FP32
+// (cell keys and the narrow phase's screens run on these; the FP32 hull is
+// within 5e-7 of h relative, inside the screens' margins), an upper bound
+// of the largest hull for the grid, and max |v| (v_ref) exactly: the
+// square root of the largest |v|^2, square roots being monotone.
 template <class R>
 __global__ void k_hull(int64_t n, const R4<R>* __restrict__ vel, const double4_32a* __restrict__ pos_r, double dt,
-                       double tau, double* __restrict__ hull, float4* __restrict__ p32, GridArgs g, DevInfo* info,
+                       double tau, double2* __restrict__ vw, float4* __restrict__ p32, GridArgs g, DevInfo* info,
                        const uint32_t* __restrict__ scene_of, unsigned long long* __restrict__ scene_vmax)
 {
-    double hmax = 0.0, vmax = 0.0;
+    double hmax = 0.0, v2max = 0.0;
     bool bad = false;
+    const float dtf = (float)dt, tauf = (float)tau;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         R4<R> v, w;
         ld_body(vel + 2 * i, v, w);
         const double4_32a x = ld_d4(pos_r + i);
         const double r = x.w;
-        const double nv = norm_exact((double)v.x, (double)v.y, (double)v.z);
-        const double nw = norm_exact((double)w.x, (double)w.y, (double)w.z);
-        // eq. (expansionradius): h = dt (|v| + |w| r) + tau
-        const double h = xadd(xmul(dt, xadd(nv, xmul(nw, r))), tau);
-        hull[i] = h;
-        // FP32 relative position and reach r + h: cell keys and the narrow phase's
-        // conservative pre-filter run on these (FP64 throughput is scarce)
-        p32[i] = make_float4((float)(x.x - g.lo[0]), (float)(x.y - g.lo[1]), (float)(x.z - g.lo[2]), (float)(r + h));
-        if (!(h <= 1e300)) bad = true;
-        if (scene_of) {   // per-scene v_ref; the filter only saves atomics
+        const double vx = v.x, vy = v.y, vz = v.z, wx = w.x, wy = w.y, wz = w.z;
+        const double v2 = xadd(xadd(xmul(vx, vx), xmul(vy, vy)), xmul(vz, vz));
+        const double w2 = xadd(xadd(xmul(wx, wx), xmul(wy, wy)), xmul(wz, wz));
+        vw[i] = make_double2(v2, w2);
+        const float h32 = dtf * (sqrtf((float)v2) + sqrtf((float)w2) * (float)r) + tauf;
+        p32[i] = make_float4((float)(x.x - g.lo[0]), (float)(x.y - g.lo[1]), (float)(x.z - g.lo[2]),
+                             (float)(r + (double)h32));
+        if (!(v2 <= 1e300) || !(w2 <= 1e300)) bad = true;
+        if (scene_of) {   // per-scene max |v|^2 (v_ref); the filter only saves atomics
             unsigned long long* dst = scene_vmax + scene_of[i];
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(nv);
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(v2);
             if (bits > *(volatile unsigned long long*)dst) atomicMax(dst, bits);
         }
-        hmax = fmax(hmax, h);
-        vmax = fmax(vmax, nv);
+        hmax = fmax(hmax, (double)h32);
+        v2max = fmax(v2max, v2);
     }
     // block max, then one atomic per block (non-negative doubles order like their bits)
     __shared__ double sh[2][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int o = 16; o > 0; o >>= 1) {
         hmax = fmax(hmax, __shfl_down_sync(0xffffffffu, hmax, o));
-        vmax = fmax(vmax, __shfl_down_sync(0xffffffffu, vmax, o));
+        v2max = fmax(v2max, __shfl_down_sync(0xffffffffu, v2max, o));
     }
     if (lane == 0) {
         sh[0][wid] = hmax;
-        sh[1][wid] = vmax;
+        sh[1][wid] = v2max;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
             hmax = fmax(hmax, sh[0][k]);
-            vmax = fmax(vmax, sh[1][k]);
+            v2max = fmax(v2max, sh[1][k]);
         }
-        atomicMax(&info->hmax_bits, (unsigned long long)__double_as_longlong(hmax));
-        atomicMax(&info->vmax_bits, (unsigned long long)__double_as_longlong(vmax));
+        // the FP32 hulls are within 5e-7 of h relative: 1e-5 makes an upper bound
+        atomicMax(&info->hmax_bits, (unsigned long long)__double_as_longlong(hmax * (1.0 + 1e-5)));
+        atomicMax(&info->vmax_bits, (unsigned long long)__double_as_longlong(xsqrt(v2max)));
     }
     if (bad) atomicOr(&info->err, kErrNaN);
 }
@@ -617,9 +640,9 @@ struct NarrowPair {
 };
 
 __device__ __forceinline__ void narrow_range(uint32_t t0, uint32_t t1, float sx, float sy, float sz, uint32_t i,
-                                             uint32_t si, const float4& qi, const double4_32a& pi, double hi_,
+                                             uint32_t si, const float4& qi, const double4_32a& pi, double& hi_,
                                              const uint32_t* __restrict__ svals, const float4* __restrict__ p32s,
-                                             const double4_32a* __restrict__ pos_r, const double* __restrict__ hull,
+                                             const double4_32a* __restrict__ pos_r, const HullView& H,
                                              const GridArgs& g, const SceneView& V, double L0, double L1, double L2,
                                              NarrowPair& P)
 {
@@ -633,7 +656,8 @@ __device__ __forceinline__ void narrow_range(uint32_t t0, uint32_t t1, float sx,
         // relative positions are off by at most pos_err per coordinate, the
         // periodic shift adds an ulp of L, so the FP32 distance is within
         // 1e-6 max(L) of d; the FP32 square and reach add relative errors
-        // below 4e-7 and 1.2e-7, covered by the extra 1e-4 while R < ~250.
+        // below 4e-7 and 1.2e-7, covered by the extra 1e-4 while R < ~100 (the FP32 hull's own error
+        // included).
         // So (fl(R) + margin)^2 >= fl(d^2) for every kept pair, and
         // fl(d^2) < (fl(R) - margin)^2 only for pairs with d below R by more
         // than the FP64 keep rule's rounding: those are kept without it.
@@ -643,16 +667,18 @@ __device__ __forceinline__ void narrow_range(uint32_t t0, uint32_t t1, float sx,
         const float rs = qi.w + qj.w;
         const float rr = rs + g.margin, rl = rs - g.margin;
         const float d2f = fx * fx + fy * fy + fz * fz;
-        if (rs < 250.f && d2f > rr * rr) continue;
-        bool keep = rl > 0.f && rs < 250.f && d2f < rl * rl;
+        if (rs < 100.f && d2f > rr * rr) continue;
+        bool keep = rl > 0.f && rs < 100.f && d2f < rl * rl;
         if (!keep) {
             const double4_32a pj = pos_r[j];
             const double dx3 = min_image(xsub(pi.x, pj.x), g.periodic[0], L0);
             const double dy3 = min_image(xsub(pi.y, pj.y), g.periodic[1], L1);
             const double dz3 = min_image(xsub(pi.z, pj.z), g.periodic[2], L2);
             const double d = norm_exact(dx3, dy3, dz3);
-            // Sect. 4: keep the pair iff the hulls intersect
-            keep = xsub(xsub(d, pi.w), pj.w) <= xadd(hi_, hull[j]);
+            // Sect. 4: keep the pair iff the hulls intersect (the exact hulls,
+            // body i's computed once)
+            if (!(hi_ >= 0.0)) hi_ = hull_of(H, i, pi.w);
+            keep = xsub(xsub(d, pi.w), pj.w) <= xadd(hi_, hull_of(H, j, pj.w));
         }
         if (keep) {
             if (P.cnt < kCandCap) {
@@ -687,7 +713,7 @@ __device__ __forceinline__ bool axis_cell(int c, int d, int periodic, float Lf, 
 
 __global__ void __launch_bounds__(128)
 k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ svals,
-         const double4_32a* __restrict__ pos_r, const double* __restrict__ hull, const float4* __restrict__ p32s,
+         const double4_32a* __restrict__ pos_r, HullView H, const float4* __restrict__ p32s,
          const uint32_t* __restrict__ cs, GridArgs g, Planes planes, SceneView V, DevInfo* info,
          uint32_t* __restrict__ cand, uint32_t* __restrict__ sph_cnt, uint32_t* __restrict__ row_cnt)
 {
@@ -701,7 +727,7 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
         const int cy = (int)((key / (uint32_t)d0) % (uint32_t)d1);
         const int cz = (int)(key / ((uint32_t)d0 * (uint32_t)d1));
         const double4_32a pi = pos_r[i];
-        const double hi_ = hull[i];
+        double hi_ = -1.0;   // the exact hull of i, computed when a test needs it
         const float4 qi = p32s[s];
         const uint32_t si = V.batch ? V.scene_of[i] : 0u;
         NarrowPair P;
@@ -717,13 +743,13 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
                 if (!axis_cell(cy + dy, d1, g.periodic[1], g.Lf[1], y, sy)) continue;
                 const uint32_t row = ((uint32_t)z * (uint32_t)d1 + (uint32_t)y) * (uint32_t)d0;
                 narrow_range(cs[row + xlo], cs[row + xhi + 1], 0.f, sy, sz, i, si, qi, pi, hi_, svals, p32s, pos_r,
-                             hull, g, V, L0, L1, L2, P);
+                             H, g, V, L0, L1, L2, P);
                 if (wrap_x && cx == 0)
                     narrow_range(cs[row + d0 - 1], cs[row + d0], g.Lf[0], sy, sz, i, si, qi, pi, hi_, svals, p32s,
-                                 pos_r, hull, g, V, L0, L1, L2, P);
+                                 pos_r, H, g, V, L0, L1, L2, P);
                 if (wrap_x && cx == d0 - 1)
                     narrow_range(cs[row], cs[row + 1], -g.Lf[0], sy, sz, i, si, qi, pi, hi_, svals, p32s, pos_r,
-                                 hull, g, V, L0, L1, L2, P);
+                                 H, g, V, L0, L1, L2, P);
             }
         }
         int cnt = P.cnt;
@@ -745,6 +771,7 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
             if (kc >= 0 && kc < planes.ncones) {   // cone (plain scenes only)
                 if (cone_distance_f(g, kc, qi) > qi.w + g.tauf + g.cmargin) continue;
                 double nrm[3], sd;
+                if (!(hi_ >= 0.0)) hi_ = hull_of(H, i, pi.w);
                 if (cone_distance(planes.cone[kc], pi, sd, nrm) && xsub(sd, pi.w) <= xadd(hi_, g.tau))
                     wmask |= 1u << k;
                 continue;
@@ -762,6 +789,7 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
             double nrm[3], c, sd, xi;
             uint32_t widx;
             wall_plane(planes, V, si, k, nrm, c, widx);
+            if (!(hi_ >= 0.0)) hi_ = hull_of(H, i, pi.w);
             if (wall_kept(nrm, c, pi, hi_, g.tau, sd, xi)) wmask |= 1u << k;
         }
         sph_cnt[i] = (uint32_t)cnt | (wmask << 8);
@@ -775,7 +803,7 @@ k_narrow(int64_t n, const uint32_t* __restrict__ skeys, const uint32_t* __restri
 // pair per lane and pass, so that the FP64 chains of a row run side by side;
 // the walls of a body stay with its own lane.
 __global__ void k_write_contacts(int64_t n, int64_t ccap, const uint32_t* __restrict__ svals,
-                                 const double4_32a* __restrict__ pos_r, const double* __restrict__ hull,
+                                 const double4_32a* __restrict__ pos_r,
                                  const uint32_t* __restrict__ cand, const uint32_t* __restrict__ sph_cnt,
                                  const uint32_t* __restrict__ row_off, GridArgs g, Planes planes, SceneView V,
                                  uint32_t* __restrict__ cj1, uint32_t* __restrict__ cj2, double4_32a* __restrict__ cgeo,
@@ -849,7 +877,6 @@ __global__ void k_write_contacts(int64_t n, int64_t ccap, const uint32_t* __rest
         }
         const uint32_t wm = packed >> 8;
         if (wm == 0) continue;
-        const double hi_ = hull[i];
         const uint32_t si = V.batch ? V.scene_of[i] : 0u;
         int64_t idx = (int64_t)ro + ns;
         for (uint32_t m = wm; m; m &= m - 1) {   // the walls k_narrow kept, in wall order
@@ -865,7 +892,7 @@ __global__ void k_write_contacts(int64_t n, int64_t ccap, const uint32_t* __rest
                 widx = (uint32_t)(V.n + k);
             } else {
                 wall_plane(planes, V, si, k, nrm, c, widx);
-                wall_kept(nrm, c, pi, hi_, g.tau, sd, xi);
+                wall_kept(nrm, c, pi, 0.0, g.tau, sd, xi);   // kept already: only sd and xi are used
             }
             if (idx < ccap) {
                 cj1[idx] = i;
@@ -993,10 +1020,10 @@ nbgs_status run_detect(nbgs_scene* s)
                                                       (const double4_32a*)s->bvel, s->prm.dt, s->prm.tau, s->pos_r,
                                                       s->hull, s->p32, g, s->info);
     } else if (s->fp32)
-        k_hull<float><<<gb, T, 0, st>>>(n, (const float4*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hull, s->p32,
+        k_hull<float><<<gb, T, 0, st>>>(n, (const float4*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hvw, s->p32,
                                         g, s->info, s->scene_of, s->scene_vmax);
     else
-        k_hull<double><<<gb, T, 0, st>>>(n, (const double4_32a*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hull,
+        k_hull<double><<<gb, T, 0, st>>>(n, (const double4_32a*)s->vel, s->pos_r, s->prm.dt, s->prm.tau, s->hvw,
                                          s->p32, g, s->info, s->scene_of, s->scene_vmax);
     k_grid_setup<<<1, 1, 0, st>>>(g, s->info);
     cudaMemsetAsync(s->cell_end, 0, (size_t)s->max_cells * sizeof(uint32_t), st);   // cell counts
@@ -1008,7 +1035,8 @@ nbgs_status run_detect(nbgs_scene* s)
     rc = exclusive_scan_u32(s, s->cell_end, s->cell_start, s->max_cells, nullptr);
     if (rc != NBGS_OK) return rc;
     k_gather_sorted<<<gb, T, 0, st>>>(n, s->vals[0], s->p32, s->p32s);
-    k_narrow<<<grid_for(n, 128, 16, s->num_sms), 128, 0, st>>>(n, s->keys[0], s->vals[0], s->pos_r, s->hull,
+    const HullView H{s->composite ? s->hull : nullptr, s->hvw, s->prm.dt, s->prm.tau};
+    k_narrow<<<grid_for(n, 128, 16, s->num_sms), 128, 0, st>>>(n, s->keys[0], s->vals[0], s->pos_r, H,
                                                                  s->p32s, s->cell_start, g, s->planes,
                                                                  scene_view(s), s->info, s->cand, s->sph_cnt,
                                                                  s->row_cnt);
@@ -1020,7 +1048,7 @@ nbgs_status run_detect(nbgs_scene* s)
         // sets an error bit (the writes past it are skipped), and every
         // later kernel reads the count on the device
         k_check_contacts<<<1, 1, 0, st>>>(s->info, s->ccap);
-        k_write_contacts<<<grid_for(n, T, 8, s->num_sms), T, 0, st>>>(n, s->ccap, s->vals[0], s->pos_r, s->hull,
+        k_write_contacts<<<grid_for(n, T, 8, s->num_sms), T, 0, st>>>(n, s->ccap, s->vals[0], s->pos_r,
                                                                       s->cand, s->sph_cnt, s->row_off, g, s->planes,
                                                                       scene_view(s), s->cj1, s->cj2, s->cgeo, s->clev);
         if (s->timing) {
@@ -1048,7 +1076,7 @@ nbgs_status run_detect(nbgs_scene* s)
         rc = grow_contacts(s, nc);
         if (rc != NBGS_OK) return rc;
     }
-    k_write_contacts<<<grid_for(n, T, 8, s->num_sms), T, 0, st>>>(n, s->ccap, s->vals[0], s->pos_r, s->hull, s->cand,
+    k_write_contacts<<<grid_for(n, T, 8, s->num_sms), T, 0, st>>>(n, s->ccap, s->vals[0], s->pos_r, s->cand,
                                                                   s->sph_cnt, s->row_off, g, s->planes, scene_view(s),
                                                                   s->cj1, s->cj2, s->cgeo, s->clev);
     if (s->timing) {

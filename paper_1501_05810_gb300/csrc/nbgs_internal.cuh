@@ -400,6 +400,7 @@ struct nbgs_scene {
     double4_32a* quat = nullptr;
     void* vel = nullptr;          // R4[2 (n + icap)]: (v, 1/m), (w, 1/I) per body, then extra instances
     double* hull = nullptr;
+    double2* hvw = nullptr;        // |v|^2, |w|^2 per sphere (the exact hulls' inputs)
     float4* p32 = nullptr;        // (x - lo, y - lo, z - lo, r + h) in FP32: cell keys and the narrow-phase pre-filter
     float4* p32s = nullptr;       // p32 in cell order (the narrow phase's candidate reads)
     uint8_t* finite = nullptr;    // body takes impulses (1/m > 0 or 1/I > 0)

@@ -1166,7 +1166,7 @@ __global__ void k_scene_vref(int64_t S, const unsigned long long* __restrict__ v
                              double* __restrict__ vref)
 {
     for (int64_t sc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sc < S; sc += (int64_t)gridDim.x * blockDim.x)
-        vref[sc] = fmax(fmax(__longlong_as_double((long long)vmax[sc]), gdt_norm), 1e-12);
+        vref[sc] = fmax(fmax(xsqrt(__longlong_as_double((long long)vmax[sc])), gdt_norm), 1e-12);   // max |v|^2 kept
 }
 
 // Canonical impulses (contact frame) and world-frame impulses for the next
