@@ -648,6 +648,7 @@ __device__ __forceinline__ void narrow_range(uint32_t t0, uint32_t t1, float sx,
 {
     for (uint32_t t = t0; t < t1; ++t) {
         const uint32_t j = svals[t];
+        const float4 qj = p32s[t];   // loaded with j: one dependent load fewer
         if (j <= i) continue;
         if (V.batch && V.scene_of[j] != si) continue;   // scenes never touch
         if (V.body_of && V.body_of[j] == V.body_of[i]) continue;   // members of one body never touch
@@ -662,7 +663,6 @@ __device__ __forceinline__ void narrow_range(uint32_t t0, uint32_t t1, float sx,
         // fl(d^2) < (fl(R) - margin)^2 only for pairs with d below R by more
         // than the FP64 keep rule's rounding: those are kept without it.
         // Only the pairs in the band between take the exact FP64 test.
-        const float4 qj = p32s[t];
         const float fx = (qi.x - qj.x) + sx, fy = (qi.y - qj.y) + sy, fz = (qi.z - qj.z) + sz;
         const float rs = qi.w + qj.w;
         const float rr = rs + g.margin, rl = rs - g.margin;
